@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for the Gaussian-state -> MPS method of arXiv:2512.10643.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously-correct
+restatement of what the paper defines.  Only the test-suite, the smoke check
+and the CPU-baseline leg of the benchmark may import it; the product library
+(``paper_2512_10643_gb300``) never does, and the two share no code.  Library
+primitives (numpy eigh/inv/det/matmul, sort) serve as steps; nothing is
+blocked, fused or reordered beyond what the paper states.
+
+Modules
+  gaussian : covariance <-> paired form, Williamson, Bogoliubov (U,V),
+             regularised Q_L, iterative GSVD chain           (Sec. II A-B, App. A)
+  basis    : kept subspace, truncation error, vector sets    (Sec. II C, App. B Alg. 1, 3)
+  pco      : projected-creation-operator tensor build        (Sec. II C, App. B Alg. 2, 4, 5)
+  mps      : full build, environments/normalisation, amplitudes, sampling,
+             fidelity
+  hafnian  : brute-force hafnian amplitudes (exact reference for tiny cases)
+
+Functions whose result is not pinned by an independent check say
+"parity unpinned" in their docstring.
+"""
+from . import gaussian, basis, pco, mps, hafnian  # noqa: F401
+from .mps import build_mps, amplitudes, sample, environments, fidelity, normalise  # noqa: F401
