@@ -1,0 +1,180 @@
+/*
+ * gbsmps — pure bosonic Gaussian state -> matrix product state, on one GB300.
+ *
+ * C ABI of the library that implements the method of arXiv:2512.10643
+ * ("Efficient simulation of low-entanglement bosonic Gaussian states in
+ * polynomial time"): the iterative Gaussian SVD of Sec. II B, the kept
+ * subspace and projected-creation-operator (PCO) mapping of Sec. II C and
+ * App. B, and MPS consumers (amplitudes, conditional sampling) of the
+ * finished tensors.  Every step runs in CUDA kernels for sm_103a; the host
+ * code only validates arguments, sizes buffers and orders launches.
+ *
+ * Conventions (Sec. II A): a_j = (x_j + i p_j)/sqrt(2); the covariance matrix
+ * Gamma = (1/2)<{dR, dR}> with R = (x_1..x_N, p_1..p_N) ("xxpp"), so the vacuum
+ * has Gamma = I/2.  Complex numbers are interleaved (re, im) doubles.
+ *
+ * Memory and ownership.  Every pointer argument is tagged by a mem_kind:
+ * GBSMPS_MEM_HOST (ordinary or pinned host memory) or GBSMPS_MEM_DEVICE
+ * (device memory of the context's GPU).  The caller owns every buffer it
+ * passes; the library copies what it needs before returning, so inputs may be
+ * freed after the call.  Calls are ordered on the context's CUDA stream: a
+ * call whose outputs are device memory returns once its work is enqueued; a
+ * call with host outputs synchronises the stream before returning.  The
+ * library owns every gbsmps_mps_t and its device memory until
+ * gbsmps_release.  Calls on one context must not run concurrently from
+ * several host threads.
+ *
+ * Errors.  Every entry point returns 0 (GBSMPS_OK) or a positive error code;
+ * gbsmps_strerror gives its text, and gbsmps_last_error_detail a one-line
+ * description of the last failure on the calling thread.  No entry point
+ * aborts or throws.  Device-side failures (a Jacobi sweep limit, an index
+ * bound) are recorded in a device status word and returned by the next call
+ * that synchronises.
+ */
+#ifndef GBSMPS_H
+#define GBSMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define GBSMPS_OK 0
+#define GBSMPS_ERR_ARG 1            /* bad argument (null, size, range)         */
+#define GBSMPS_ERR_NOT_SYMMETRIC 2  /* Gamma not symmetric                       */
+#define GBSMPS_ERR_NOT_PURE 3       /* (2 Gamma Omega)^2 != -1 within tolerance  */
+#define GBSMPS_ERR_OOM 4            /* device allocation failed                  */
+#define GBSMPS_ERR_NOT_CONVERGED 5  /* eigensolver sweep limit reached           */
+#define GBSMPS_ERR_BOUNDS 6         /* n_e or a basis size exceeds a built limit */
+#define GBSMPS_ERR_CUDA 7           /* CUDA runtime error                        */
+#define GBSMPS_ERR_NUMERIC 8        /* non-finite value, singular matrix         */
+#define GBSMPS_ERR_STATE 9          /* object in the wrong state for the call    */
+
+#define GBSMPS_MEM_HOST 0
+#define GBSMPS_MEM_DEVICE 1
+
+/* Arithmetic of the tensor build, environments and sampling.  The Gaussian
+ * SVD, symplectic orthogonalisation and normalisation are FP64 in both. */
+#define GBSMPS_PREC_FP64 0
+#define GBSMPS_PREC_MIXED 1   /* FP32 PCO build, split-BF16 tensor-core GEMMs */
+
+/* Largest number of entangled mode pairs at one cut (n_e of Sec. II A). */
+#define GBSMPS_NE_MAX 24
+
+typedef struct gbsmps_ctx* gbsmps_ctx_t;
+typedef struct gbsmps_mps* gbsmps_mps_t;
+
+typedef struct {
+  int32_t d;               /* physical Fock cutoff: p = 0..d-1 (Sec. II C)      */
+  int32_t chi_max;         /* bond dimension cap chi (D of Sec. II C)            */
+  double eps_trunc;        /* target discarded weight eps; D_m = min(chi, D(eps)),
+                              eps = 0 means chi alone (Sec. II C, D(eps) rule)   */
+  double lambda2_freeze;   /* modes with Lambda^2 <= this are frozen: the D*
+                              tolerance of Sec. II A, expressed on Lambda^2     */
+  int32_t precision;       /* GBSMPS_PREC_FP64 or GBSMPS_PREC_MIXED              */
+  int32_t validate;        /* 1: check symmetry and purity of the input         */
+  double purity_tol;       /* max |(2 Gamma Omega)^2 + 1| accepted              */
+} gbsmps_opts;
+
+/* Fill *o with defaults: d = 4, chi = 64, eps = 0, lambda2_freeze = 1e-13,
+ * FP64, validate = 1, purity_tol = 1e-9.  Returns GBSMPS_ERR_ARG on null. */
+int gbsmps_opts_default(gbsmps_opts* o);
+
+/* Create a context on CUDA device `device`, ordering all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: ARG (null out, bad device), CUDA. */
+int gbsmps_create(int device, void* stream, gbsmps_ctx_t* out);
+int gbsmps_destroy(gbsmps_ctx_t ctx);
+
+/* Build the MPS of the N-mode pure Gaussian state with covariance `gamma`
+ * (2N x 2N, xxpp, row-major FP64; Sec. II A, Eq. (GammaMat)).  Runs the
+ * iterative GSVD (Sec. II B: Williamson form Eq. (symDiag), Bogoliubov map
+ * Eq. (MUV), regularised paired form of App. A), the kept-basis selection
+ * and truncation error (Sec. II C, Sec. III A), the PCO mapping of every
+ * local tensor (Sec. II C, App. B), the right environments and the
+ * normalisation (norm 1, all-vacuum amplitude real positive).
+ * N >= 1; 1 <= d <= 255; 1 <= chi_max <= 4096.  *out receives a new handle.
+ * Errors: ARG, NOT_SYMMETRIC, NOT_PURE (validate = 1), BOUNDS (n_e > NE_MAX),
+ * NOT_CONVERGED, NUMERIC, OOM, CUDA.  Synchronises the stream once (bond
+ * sizes are read back to size the tensors). */
+int gbsmps_build_from_cov(gbsmps_ctx_t ctx, int32_t N, const double* gamma,
+                          int mem_kind, const gbsmps_opts* opts,
+                          gbsmps_mps_t* out);
+
+/* Same from the paired-form (A-)matrix Q of Eq. (paired-form): the state is
+ * proportional to exp(1/2 sum Q_ij a_i^dag a_j^dag)|0>, Q (N x N, complex
+ * symmetric, row-major interleaved, all singular values < 1).  The GBS
+ * "A-matrix" of a pure state is Q (+) Q^*; pass its first block.  Q is turned
+ * into Gamma on the device (N = (1 - Q^*Q)^{-1} - 1, M = Q(1 + N)). */
+int gbsmps_build_from_Q(gbsmps_ctx_t ctx, int32_t N, const double* Q,
+                        int mem_kind, const gbsmps_opts* opts,
+                        gbsmps_mps_t* out);
+
+/* Sizes of a built MPS (host outputs, any may be NULL):
+ * bond_dims[N+1] (D_0 = D_N = 1), n_e[N-1] (entangled pairs per cut),
+ * eps_m[N-1] (discarded weight per bond, Sec. III A), *N_out, *d_out. */
+int gbsmps_info(gbsmps_mps_t mps, int32_t* N_out, int32_t* d_out,
+                int32_t* bond_dims, int32_t* n_e, double* eps_m);
+
+/* Copy tensor A^site (0-based) as row-major [alpha][p][beta] complex128
+ * (beta fastest), size D_site * d * D_{site+1} * 16 bytes, into dst.
+ * Errors: ARG (site range, dst_bytes too small). */
+int gbsmps_get_tensor(gbsmps_mps_t mps, int32_t site, void* dst,
+                      size_t dst_bytes, int mem_kind);
+
+/* Symplectic spectra and entanglement data of the GSVD, for checks:
+ * lam2[(N-1) * NE_MAX] (Lambda_q^2 of active modes, descending, zero padded),
+ * Qm[N * (2 NE_MAX + 1)^2] complex (local paired forms over c_m =
+ * (r_{m-1}, a_m, l_m), row stride 2 NE_MAX + 1), c_m[N].  Host outputs. */
+int gbsmps_get_gsvd(gbsmps_mps_t mps, double* lam2, double* Qm, double* c_m);
+
+/* Amplitudes <n_1..n_N|psi> (Eq. (Am_definition) contracted along the chain)
+ * of P patterns (P x N uint8, row-major) into out (P x 2 doubles).  Patterns
+ * with any n_i >= d give 0.  P = 0 is a no-op.  Errors: ARG, CUDA. */
+int gbsmps_amplitudes(gbsmps_mps_t mps, int64_t P, const uint8_t* patterns,
+                      double* out, int mem_kind);
+
+/* Draw S photon-count patterns (S x N uint8, row-major) by exact sequential
+ * conditional sampling of the normalised MPS: at site m the weights
+ * q_p = w_p R_{m+1} w_p^dag of w_p = v A^m[p] (right environment R), the
+ * first p with u Z < C_p (C the prefix sums, Z the total) is chosen and
+ * v = w_p / sqrt(q_p).  Uniforms: `uniforms` (S x N doubles in [0,1),
+ * row-major, same mem_kind) if non-NULL; otherwise Philox4x32-10 keyed by
+ * seed with counter (counter0 + sample, site), 53 bits per draw.
+ * `flags` (S bytes, may be NULL) receives 1 where a draw fell within 1e-12 Z
+ * of a CDF boundary.  S = 0 is a no-op.  Errors: ARG, OOM, CUDA. */
+int gbsmps_sample(gbsmps_mps_t mps, int64_t S, uint64_t seed,
+                  uint64_t counter0, const double* uniforms, uint8_t* out,
+                  uint8_t* flags, int mem_kind);
+
+/* Release an MPS and its device memory. */
+int gbsmps_release(gbsmps_mps_t mps);
+
+/* Expert entry: PCO build of one local tensor (Sec. II C, App. B) from a
+ * given paired form Qm ((nl + 1 + nr)^2 complex, mode order (r_1..r_nl, a,
+ * l_1..l_nr)) and kept bases given as occupation vectors occ_l (Dl x nl
+ * uint8) and occ_r (Dr x nr uint8) that must be closed under removing one
+ * quantum and start with the vacuum.  out: Dl x d x Dr complex128, scaled by
+ * c.  All pointers are of mem_kind.  precision selects FP64 or FP32 PCO
+ * arithmetic (the output is FP64 either way). */
+int gbsmps_build_site(gbsmps_ctx_t ctx, int32_t nl, int32_t nr, int32_t d,
+                      const double* Qm, double c, int32_t Dl,
+                      const uint8_t* occ_l, int32_t Dr, const uint8_t* occ_r,
+                      int32_t precision, double* out, int mem_kind);
+
+/* Text of an error code (static storage). */
+const char* gbsmps_strerror(int code);
+/* One-line detail of the last error on the calling thread. */
+const char* gbsmps_last_error_detail(void);
+
+/* Build number and the list of kernels the library launched since the last
+ * call (comma separated, static per thread), for launch accounting. */
+int64_t gbsmps_launch_count(gbsmps_ctx_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBSMPS_H */

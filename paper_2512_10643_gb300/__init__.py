@@ -1,0 +1,274 @@
+"""Python binding of the gbsmps C ABI (``include/gbsmps.h``).
+
+Argument marshalling only: every step of the Gaussian-state -> MPS path runs
+in the CUDA kernels of ``libgbsmps.so``.  Buffers may be numpy arrays (host
+memory) or torch tensors (host or CUDA); PyTorch is used for device memory
+and streams.  There is no CPU fallback: if the library is missing the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbsmps.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gbsmps.h")
+
+OK, ERR_ARG, ERR_NOT_SYMMETRIC, ERR_NOT_PURE, ERR_OOM = 0, 1, 2, 3, 4
+ERR_NOT_CONVERGED, ERR_BOUNDS, ERR_CUDA, ERR_NUMERIC, ERR_STATE = 5, 6, 7, 8, 9
+MEM_HOST, MEM_DEVICE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+NE_MAX = 24
+QS = 2 * NE_MAX + 1
+
+
+class GbsmpsError(RuntimeError):
+    def __init__(self, code, detail):
+        super().__init__(f"gbsmps error {code}: {detail}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("d", C.c_int32), ("chi_max", C.c_int32), ("eps_trunc", C.c_double),
+                ("lambda2_freeze", C.c_double), ("precision", C.c_int32),
+                ("validate", C.c_int32), ("purity_tol", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libgbsmps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2512_10643_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "gbsmps_opts_default": (C.c_int, [C.POINTER(Opts)]),
+        "gbsmps_create": (C.c_int, [C.c_int, vp, C.POINTER(vp)]),
+        "gbsmps_destroy": (C.c_int, [vp]),
+        "gbsmps_build_from_cov": (C.c_int, [vp, i32, vp, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
+        "gbsmps_build_from_Q": (C.c_int, [vp, i32, vp, C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
+        "gbsmps_info": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "gbsmps_get_tensor": (C.c_int, [vp, i32, vp, C.c_size_t, C.c_int]),
+        "gbsmps_get_gsvd": (C.c_int, [vp, vp, vp, vp]),
+        "gbsmps_amplitudes": (C.c_int, [vp, i64, vp, vp, C.c_int]),
+        "gbsmps_sample": (C.c_int, [vp, i64, u64, u64, vp, vp, vp, C.c_int]),
+        "gbsmps_release": (C.c_int, [vp]),
+        "gbsmps_build_site": (C.c_int, [vp, i32, i32, i32, vp, dbl, i32, vp, i32, vp, i32, vp, C.c_int]),
+        "gbsmps_strerror": (C.c_char_p, [C.c_int]),
+        "gbsmps_last_error_detail": (C.c_char_p, []),
+        "gbsmps_launch_count": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_symbols():
+    """Entry points declared in include/gbsmps.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\*\s]+?\b(gbsmps_\w+)\s*\(", txt, re.M)))
+
+
+def _check(rc):
+    if rc != OK:
+        L = lib()
+        raise GbsmpsError(rc, f"{L.gbsmps_strerror(rc).decode()} ({L.gbsmps_last_error_detail().decode()})")
+
+
+def _ptr(x):
+    """(pointer, mem_kind) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, MEM_HOST
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, MEM_HOST
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+    raise TypeError(type(x))
+
+
+def opts_default(**kw) -> Opts:
+    o = Opts()
+    _check(lib().gbsmps_opts_default(C.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gbsmps_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    _check(lib().gbsmps_create(device, C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def gbsmps_destroy(ctx):
+    _check(lib().gbsmps_destroy(ctx))
+
+
+def gbsmps_build_from_cov(ctx, gamma, opts: Opts):
+    p, kind = _ptr(gamma)
+    N = gamma.shape[0] // 2
+    h = C.c_void_p()
+    _check(lib().gbsmps_build_from_cov(ctx, N, C.c_void_p(p), kind, C.byref(opts), C.byref(h)))
+    return h
+
+
+def gbsmps_build_from_Q(ctx, Q, opts: Opts):
+    """Q: complex128 (N, N) numpy array, or float64 (N, N, 2) tensor."""
+    if isinstance(Q, np.ndarray) and np.iscomplexobj(Q):
+        Q = np.ascontiguousarray(Q.astype(np.complex128)).view(np.float64).reshape(Q.shape + (2,))
+    p, kind = _ptr(Q)
+    h = C.c_void_p()
+    _check(lib().gbsmps_build_from_Q(ctx, Q.shape[0], C.c_void_p(p), kind, C.byref(opts), C.byref(h)))
+    return h
+
+
+def gbsmps_info(mps):
+    N, d = C.c_int32(), C.c_int32()
+    _check(lib().gbsmps_info(mps, C.byref(N), C.byref(d), None, None, None))
+    dims = np.zeros(N.value + 1, dtype=np.int32)
+    ne = np.zeros(max(N.value - 1, 1), dtype=np.int32)
+    eps = np.zeros(max(N.value - 1, 1), dtype=np.float64)
+    _check(lib().gbsmps_info(mps, None, None, dims.ctypes.data, ne.ctypes.data, eps.ctypes.data))
+    return {"N": N.value, "d": d.value, "bond_dims": dims, "n_e": ne[:max(N.value - 1, 0)],
+            "eps": eps[:max(N.value - 1, 0)]}
+
+
+def gbsmps_get_tensor(mps, site: int, dst=None):
+    info = gbsmps_info(mps)
+    Dl, Dr, d = int(info["bond_dims"][site]), int(info["bond_dims"][site + 1]), info["d"]
+    if dst is None:
+        dst = np.zeros((Dl, d, Dr), dtype=np.complex128)
+    p, kind = _ptr(dst)
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(lib().gbsmps_get_tensor(mps, site, C.c_void_p(p), nbytes, kind))
+    return dst
+
+
+def gbsmps_get_gsvd(mps):
+    N = gbsmps_info(mps)["N"]
+    lam2 = np.zeros(max(N - 1, 1) * NE_MAX)
+    Qm = np.zeros(N * QS * QS, dtype=np.complex128)
+    cm = np.zeros(N)
+    _check(lib().gbsmps_get_gsvd(mps, lam2.ctypes.data, Qm.ctypes.data, cm.ctypes.data))
+    return lam2[:(N - 1) * NE_MAX].reshape(max(N - 1, 0), NE_MAX), Qm.reshape(N, QS, QS), cm
+
+
+def gbsmps_amplitudes(mps, patterns, out=None):
+    P = patterns.shape[0]
+    if out is None:
+        out = np.zeros(P, dtype=np.complex128) if isinstance(patterns, np.ndarray) else None
+    pp, kind = _ptr(patterns)
+    op, okind = _ptr(out)
+    if okind != kind:
+        raise ValueError("patterns and out must live in the same memory")
+    _check(lib().gbsmps_amplitudes(mps, P, C.c_void_p(pp), C.c_void_p(op), kind))
+    return out
+
+
+def gbsmps_sample(mps, S: int, seed: int = 0, counter0: int = 0, uniforms=None, out=None,
+                  flags=None):
+    N = gbsmps_info(mps)["N"]
+    if out is None:
+        out = np.zeros((S, N), dtype=np.uint8)
+    op, kind = _ptr(out)
+    up, ukind = _ptr(uniforms)
+    fp, fkind = _ptr(flags)
+    if uniforms is not None and ukind != kind:
+        raise ValueError("uniforms and out must live in the same memory")
+    if flags is not None and fkind != kind:
+        raise ValueError("flags and out must live in the same memory")
+    _check(lib().gbsmps_sample(mps, S, seed, counter0, C.c_void_p(up or 0), C.c_void_p(op),
+                               C.c_void_p(fp or 0), kind))
+    return out
+
+
+def gbsmps_release(mps):
+    _check(lib().gbsmps_release(mps))
+
+
+def gbsmps_build_site(ctx, Qm, c, occ_l, occ_r, d, precision=PREC_FP64):
+    """Expert entry on host numpy arrays: Qm complex (n, n), occ_l (Dl, nl)
+    and occ_r (Dr, nr) uint8 down-closed bases starting at the vacuum."""
+    Qm = np.ascontiguousarray(Qm, dtype=np.complex128)
+    occ_l = np.ascontiguousarray(occ_l, dtype=np.uint8)
+    occ_r = np.ascontiguousarray(occ_r, dtype=np.uint8)
+    nl, nr = occ_l.shape[1], occ_r.shape[1]
+    Dl, Dr = occ_l.shape[0], occ_r.shape[0]
+    out = np.zeros((Dl, d, Dr), dtype=np.complex128)
+    _check(lib().gbsmps_build_site(ctx, nl, nr, d, Qm.ctypes.data, float(c), Dl,
+                                   occ_l.ctypes.data if nl else None, Dr,
+                                   occ_r.ctypes.data if nr else None, precision,
+                                   out.ctypes.data, MEM_HOST))
+    return out
+
+
+def gbsmps_launch_count(ctx=None) -> int:
+    return int(lib().gbsmps_launch_count(ctx))
+
+
+class Context:
+    """Owns a gbsmps context bound to a device and a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.h = gbsmps_create(device, stream)
+
+    def close(self):
+        if self.h:
+            gbsmps_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class MPS:
+    """A device-resident MPS built by the library."""
+
+    def __init__(self, h):
+        self.h = h
+        self.info = gbsmps_info(h)
+
+    @classmethod
+    def from_cov(cls, ctx: Context, gamma, **opts):
+        return cls(gbsmps_build_from_cov(ctx.h, gamma, opts_default(**opts)))
+
+    @classmethod
+    def from_Q(cls, ctx: Context, Q, **opts):
+        return cls(gbsmps_build_from_Q(ctx.h, Q, opts_default(**opts)))
+
+    def tensor(self, site: int):
+        return gbsmps_get_tensor(self.h, site)
+
+    def tensors(self):
+        return [self.tensor(m) for m in range(self.info["N"])]
+
+    def amplitudes(self, patterns, out=None):
+        return gbsmps_amplitudes(self.h, patterns, out)
+
+    def sample(self, S, seed=0, counter0=0, uniforms=None, out=None, flags=None):
+        return gbsmps_sample(self.h, S, seed, counter0, uniforms, out, flags)
+
+    def release(self):
+        if self.h:
+            gbsmps_release(self.h)
+            self.h = None

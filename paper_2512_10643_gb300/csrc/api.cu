@@ -1,0 +1,575 @@
+// C ABI of gbsmps (include/gbsmps.h): argument checks, device buffers and the
+// launch order of the build / amplitude / sampling pipelines.  All numerics run
+// in the kernels of k_gsvd.cu, k_basis.cu, k_pco.cu and k_mps.cu.
+#include "internal.h"
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+unsigned long long g_kernel_launches = 0;
+
+namespace {
+thread_local std::string g_detail;
+
+int fail(int code, const std::string& what) {
+  g_detail = what;
+  return code;
+}
+
+#define CK(expr)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? GBSMPS_ERR_OOM : GBSMPS_ERR_CUDA, \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+    }                                                                              \
+  } while (0)
+
+int status_to_code(int st) {
+  if (st & ST_NOT_SYMMETRIC) return GBSMPS_ERR_NOT_SYMMETRIC;
+  if (st & ST_NOT_PURE) return GBSMPS_ERR_NOT_PURE;
+  if (st & ST_BOUNDS) return GBSMPS_ERR_BOUNDS;
+  if (st & ST_NOT_CONVERGED) return GBSMPS_ERR_NOT_CONVERGED;
+  if (st & ST_NUMERIC) return GBSMPS_ERR_NUMERIC;
+  return GBSMPS_OK;
+}
+}  // namespace
+
+struct gbsmps_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* d_status = nullptr;
+  unsigned long long launches_at_create = 0;
+};
+
+struct DevBuf {                // stream-ordered device allocation
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    if (bytes == 0) bytes = 16;
+    return cudaMallocAsync(&p, bytes, st);
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct gbsmps_mps {
+  gbsmps_ctx* ctx = nullptr;
+  int N = 0, d = 0, chi = 0, precision = 0;
+  std::vector<int> D, ne;
+  std::vector<double> eps;
+  std::vector<long long> toff, eoff;
+  int maxD = 1;
+  DevBuf tensors, env, gsvd, bonds;
+  BondArrays ba{};
+  double* lam2 = nullptr;
+  double2* Qm = nullptr;
+  double* cm = nullptr;
+  ~gbsmps_mps() {
+    tensors.release(); env.release(); gsvd.release(); bonds.release();
+  }
+};
+
+namespace {
+
+int sync_status(gbsmps_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return fail(status_to_code(st), "device status word " + std::to_string(st));
+  }
+  return GBSMPS_OK;
+}
+
+int check_opts(const gbsmps_opts* o) {
+  if (!o) return fail(GBSMPS_ERR_ARG, "opts is NULL");
+  if (o->d < 1 || o->d > 255) return fail(GBSMPS_ERR_ARG, "d out of range [1,255]");
+  if (o->chi_max < 1 || o->chi_max > 4096) return fail(GBSMPS_ERR_ARG, "chi_max out of range [1,4096]");
+  if (!(o->eps_trunc >= 0.0 && o->eps_trunc < 1.0)) return fail(GBSMPS_ERR_ARG, "eps_trunc not in [0,1)");
+  if (!(o->lambda2_freeze >= 0.0 && o->lambda2_freeze < 1.0))
+    return fail(GBSMPS_ERR_ARG, "lambda2_freeze not in [0,1)");
+  if (o->precision != GBSMPS_PREC_FP64 && o->precision != GBSMPS_PREC_MIXED)
+    return fail(GBSMPS_ERR_ARG, "unknown precision");
+  return GBSMPS_OK;
+}
+
+// the pipeline after the covariance is on the device
+int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
+               gbsmps_mps_t* out) {
+  cudaStream_t s = c->stream;
+  auto* M = new gbsmps_mps();
+  std::unique_ptr<gbsmps_mps> guard(M);
+  M->ctx = c; M->N = N; M->d = o->d; M->chi = o->chi_max; M->precision = o->precision;
+  const int cap = o->chi_max + TIE_MARGIN;
+  const int nb = N + 1;
+  // ---- GSVD outputs and bond arrays in one allocation -----------------------
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
+  size_t o_Q = take(sizeof(double2) * (size_t)N * QS * QS);
+  size_t o_c = take(sizeof(double) * N);
+  size_t o_G = take(sizeof(double) * 2 * 2 * NEM * 2 * (size_t)std::max(N, 1));
+  size_t o_bw = take(sizeof(int) * 4);
+  size_t o_work = take(sizeof(double) * 8);
+  CK(M->gsvd.alloc(off, s));
+  char* g0 = M->gsvd.as<char>();
+  M->Qm = reinterpret_cast<double2*>(g0 + o_Q);
+  M->cm = reinterpret_cast<double*>(g0 + o_c);
+  double* Gs = reinterpret_cast<double*>(g0 + o_G);
+  int* dbw = reinterpret_cast<int*>(g0 + o_bw);
+  double* work = reinterpret_cast<double*>(g0 + o_work);
+  off = 0;
+  size_t o_occ = take((size_t)nb * cap * NEM);
+  size_t o_E = take(sizeof(double) * (size_t)nb * cap);
+  size_t o_low = take(sizeof(int) * (size_t)nb * NEM * cap);
+  size_t o_D = take(sizeof(int) * nb);
+  size_t o_ne = take(sizeof(int) * nb);
+  size_t o_mo = take(sizeof(int) * (size_t)nb * NEM);
+  size_t o_l2 = take(sizeof(double) * (size_t)nb * NEM);
+  size_t o_eps = take(sizeof(double) * nb);
+  CK(M->bonds.alloc(off, s));
+  char* b0 = M->bonds.as<char>();
+  BondArrays& ba = M->ba;
+  ba.cap = cap;
+  ba.occ = reinterpret_cast<uint8_t*>(b0 + o_occ);
+  ba.E = reinterpret_cast<double*>(b0 + o_E);
+  ba.low = reinterpret_cast<int*>(b0 + o_low);
+  ba.D = reinterpret_cast<int*>(b0 + o_D);
+  ba.ne = reinterpret_cast<int*>(b0 + o_ne);
+  ba.maxocc = reinterpret_cast<int*>(b0 + o_mo);
+  ba.lam2 = reinterpret_cast<double*>(b0 + o_l2);
+  ba.eps = reinterpret_cast<double*>(b0 + o_eps);
+  M->lam2 = ba.lam2;
+  CK(cudaMemsetAsync(b0, 0, off, s));
+  CK(cudaMemsetAsync(M->Qm, 0, sizeof(double2) * (size_t)N * QS * QS, s));
+  // ---- a1 validation, a2-a3 GSVD chain -------------------------------------
+  if (o->validate) {
+    CK(launch_check_input(dgamma, N, o->purity_tol, work, c->d_status, s));
+    COUNT_LAUNCH(2);
+  }
+  CK(launch_bandwidth(dgamma, N, dbw, s));
+  COUNT_LAUNCH(1);
+  CK(launch_gsvd_chain(dgamma, N, dbw, o->lambda2_freeze, Gs, ba, M->Qm, M->cm, c->d_status, s));
+  COUNT_LAUNCH(1);
+  // ---- a4-a5 kept bases and index maps --------------------------------------
+  CK(launch_basis(ba, nb, o->chi_max, o->eps_trunc, c->d_status, s));
+  CK(launch_maps(ba, nb, c->d_status, s));
+  COUNT_LAUNCH(2);
+  M->D.assign(nb, 1);
+  M->ne.assign(nb, 0);
+  std::vector<double> epsb(nb, 0.0);
+  CK(cudaMemcpyAsync(M->D.data(), ba.D, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(M->ne.data(), ba.ne, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(epsb.data(), ba.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  int rc = sync_status(c);
+  if (rc) return rc;
+  M->eps.assign(epsb.begin() + 1, epsb.end() - 1);
+  M->D[0] = 1; M->D[N] = 1;
+  // ---- tensor storage -----------------------------------------------------
+  M->toff.resize(N);
+  long long tot = 0;
+  size_t scr_max = 0;
+  for (int m = 0; m < N; ++m) {
+    M->toff[m] = tot;
+    tot += (long long)M->D[m] * o->d * M->D[m + 1];
+    scr_max = std::max(scr_max, pco_scratch_elems(M->D[m], M->D[m + 1]));
+    M->maxD = std::max(M->maxD, M->D[m]);
+  }
+  M->eoff.resize(N + 1);
+  long long etot = 0;
+  for (int m = 0; m <= N; ++m) { M->eoff[m] = etot; etot += (long long)M->D[m] * M->D[m]; }
+  CK(M->tensors.alloc(sizeof(double2) * tot, s));
+  CK(M->env.alloc(sizeof(double2) * (etot + 8), s));
+  // ---- a6 PCO build, in waves of at most 2 x 152 tensors -----------------------
+  const int wave = std::min(N, 304);
+  DevBuf scr, tk;
+  CK(scr.alloc(sizeof(double2) * scr_max * wave, s));
+  CK(tk.alloc(sizeof(SiteTask) * wave, s));
+  std::vector<SiteTask> tasks(wave);
+  for (int m0 = 0; m0 < N; m0 += wave) {
+    int cnt = std::min(wave, N - m0);
+    for (int k = 0; k < cnt; ++k) {
+      int m = m0 + k;
+      SiteTask& t = tasks[k];
+      t.nl = M->ne[m]; t.nr = M->ne[m + 1]; t.Dl = M->D[m]; t.Dr = M->D[m + 1];
+      t.Q = M->Qm + (size_t)m * QS * QS; t.qs = QS;
+      t.c = 0.0;   // set on device below (c_m lives in device memory)
+      t.occl = ba.occ + (size_t)m * cap * NEM; t.lowl = ba.low + (size_t)m * NEM * cap; t.capl = cap;
+      t.occr = ba.occ + (size_t)(m + 1) * cap * NEM; t.lowr = ba.low + (size_t)(m + 1) * NEM * cap;
+      t.capr = cap;
+      t.out = M->tensors.as<double2>() + M->toff[m];
+      t.scratch_off = (size_t)k * scr_max;
+    }
+    // c_m: copy the device scale factors into the task records
+    std::vector<double> cm(cnt);
+    CK(cudaMemcpyAsync(cm.data(), M->cm + m0, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < cnt; ++k) tasks[k].c = cm[k];
+    CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * cnt, cudaMemcpyHostToDevice, s));
+    CK(launch_pco(tk.as<SiteTask>(), cnt, o->d, o->precision, scr.as<double2>(), c->d_status, s));
+    COUNT_LAUNCH(1);
+    CK(cudaStreamSynchronize(s));   // the task records are reused by the next wave
+  }
+  scr.release();
+  tk.release();
+  // ---- a7 right environments and normalisation ------------------------------
+  double2* R = M->env.as<double2>();
+  double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
+  CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+  size_t xmax = 0;
+  for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * o->d * M->D[m + 1]);
+  DevBuf xb;
+  CK(xb.alloc(sizeof(double2) * (xmax + 8), s));
+  double2* X = xb.as<double2>();
+  const int d = o->d;
+  for (int m = N - 1; m >= 0; --m) {
+    int Dl = M->D[m], Dr = M->D[m + 1];
+    const double2* A = M->tensors.as<double2>() + M->toff[m];
+    CK(launch_zgemm('N', 'N', Dl * d, Dr, Dr, one, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, zero, X,
+                    Dr, 0, 1, s));
+    CK(launch_zgemm('N', 'C', Dl, Dl, d * Dr, one, X, d * Dr, 0, A, d * Dr, 0, zero,
+                    R + M->eoff[m], Dl, 0, 1, s));
+    COUNT_LAUNCH(2);
+  }
+  // vacuum amplitude, then A^1 *= conj(phase)/sqrt(norm^2)
+  DevBuf ab;
+  CK(ab.alloc(sizeof(double2) * (2 * (size_t)M->maxD + 8) + N, s));
+  double2* awork = ab.as<double2>();
+  double2* amp0 = awork + 2 * M->maxD;
+  double2* fac = amp0 + 1;
+  uint8_t* zpat = reinterpret_cast<uint8_t*>(fac + 2);
+  CK(cudaMemsetAsync(zpat, 0, N, s));
+  ChainView cv{N, d, M->D.data(), M->toff.data(), M->tensors.as<double2>()};
+  CK(launch_amplitudes(cv, 1, zpat, amp0, awork, M->maxD, s));
+  COUNT_LAUNCH(2 + N);
+  CK(launch_norm_phase(R + M->eoff[0], amp0, fac, c->d_status, s));
+  CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
+  COUNT_LAUNCH(2);
+  // R_0 of the normalised state is 1
+  CK(cudaMemcpyAsync(R + M->eoff[0], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+  xb.release();
+  ab.release();
+  rc = sync_status(c);
+  if (rc) return rc;
+  *out = guard.release();
+  return GBSMPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbsmps_opts_default(gbsmps_opts* o) {
+  if (!o) return fail(GBSMPS_ERR_ARG, "opts is NULL");
+  o->d = 4; o->chi_max = 64; o->eps_trunc = 0.0; o->lambda2_freeze = 1e-13;
+  o->precision = GBSMPS_PREC_FP64; o->validate = 1; o->purity_tol = 1e-9;
+  return GBSMPS_OK;
+}
+
+int gbsmps_create(int device, void* stream, gbsmps_ctx_t* out) {
+  if (!out) return fail(GBSMPS_ERR_ARG, "out is NULL");
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(GBSMPS_ERR_ARG, "bad device index");
+  CK(cudaSetDevice(device));
+  auto* c = new gbsmps_ctx();
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e) { delete c; return fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e)); }
+  e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e) { cudaFree(c->d_status); delete c; return fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e)); }
+  c->launches_at_create = g_kernel_launches;
+  *out = c;
+  return GBSMPS_OK;
+}
+
+int gbsmps_destroy(gbsmps_ctx_t c) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_status);
+  delete c;
+  return GBSMPS_OK;
+}
+
+int gbsmps_build_from_cov(gbsmps_ctx_t c, int32_t N, const double* gamma, int mem_kind,
+                          const gbsmps_opts* o, gbsmps_mps_t* out) {
+  if (!c || !gamma || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > 1000000) return fail(GBSMPS_ERR_ARG, "N out of range");
+  if (mem_kind != GBSMPS_MEM_HOST && mem_kind != GBSMPS_MEM_DEVICE) return fail(GBSMPS_ERR_ARG, "mem_kind");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  const size_t bytes = sizeof(double) * 4 * (size_t)N * N;
+  DevBuf g;
+  const double* dg = gamma;
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    CK(g.alloc(bytes, c->stream));
+    CK(cudaMemcpyAsync(g.p, gamma, bytes, cudaMemcpyHostToDevice, c->stream));
+    dg = g.as<double>();
+  }
+  rc = build_core(c, N, dg, o, out);
+  g.release();
+  return rc;
+}
+
+int gbsmps_build_from_Q(gbsmps_ctx_t c, int32_t N, const double* Q, int mem_kind,
+                        const gbsmps_opts* o, gbsmps_mps_t* out) {
+  if (!c || !Q || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > 65536) return fail(GBSMPS_ERR_ARG, "N out of range");
+  if (mem_kind != GBSMPS_MEM_HOST && mem_kind != GBSMPS_MEM_DEVICE) return fail(GBSMPS_ERR_ARG, "mem_kind");
+  int rc = check_opts(o);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t qbytes = sizeof(double2) * (size_t)N * N;
+  DevBuf qb, gb, wb;
+  const double2* dq = reinterpret_cast<const double2*>(Q);
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    CK(qb.alloc(qbytes, s));
+    CK(cudaMemcpyAsync(qb.p, Q, qbytes, cudaMemcpyHostToDevice, s));
+    dq = qb.as<double2>();
+  }
+  CK(gb.alloc(sizeof(double) * 4 * (size_t)N * N, s));
+  CK(wb.alloc(qbytes + sizeof(double2) * 2 * (size_t)N, s));
+  CK(launch_q_to_gamma(dq, N, gb.as<double>(), wb.as<double2>(), c->d_status, s));
+  COUNT_LAUNCH(2 + 2 * (unsigned long long)N);
+  rc = sync_status(c);
+  if (rc == GBSMPS_OK) rc = build_core(c, N, gb.as<double>(), o, out);
+  qb.release(); gb.release(); wb.release();
+  return rc;
+}
+
+int gbsmps_info(gbsmps_mps_t m, int32_t* N_out, int32_t* d_out, int32_t* bond_dims,
+                int32_t* n_e, double* eps_m) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  if (N_out) *N_out = m->N;
+  if (d_out) *d_out = m->d;
+  if (bond_dims) for (int i = 0; i <= m->N; ++i) bond_dims[i] = m->D[i];
+  if (n_e) for (int i = 1; i < m->N; ++i) n_e[i - 1] = m->ne[i];
+  if (eps_m) for (int i = 0; i + 1 < m->N; ++i) eps_m[i] = m->eps[i];
+  return GBSMPS_OK;
+}
+
+int gbsmps_get_tensor(gbsmps_mps_t m, int32_t site, void* dst, size_t dst_bytes, int mem_kind) {
+  if (!m || !dst) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (site < 0 || site >= m->N) return fail(GBSMPS_ERR_ARG, "site out of range");
+  size_t bytes = sizeof(double2) * (size_t)m->D[site] * m->d * m->D[site + 1];
+  if (dst_bytes < bytes) return fail(GBSMPS_ERR_ARG, "dst too small");
+  CK(cudaSetDevice(m->ctx->device));
+  CK(cudaMemcpyAsync(dst, m->tensors.as<double2>() + m->toff[site], bytes,
+                     mem_kind == GBSMPS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     m->ctx->stream));
+  if (mem_kind == GBSMPS_MEM_HOST) CK(cudaStreamSynchronize(m->ctx->stream));
+  return GBSMPS_OK;
+}
+
+int gbsmps_get_gsvd(gbsmps_mps_t m, double* lam2, double* Qm, double* c_m) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  CK(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = m->ctx->stream;
+  if (lam2 && m->N > 1)
+    CK(cudaMemcpyAsync(lam2, m->lam2 + NEM, sizeof(double) * NEM * (size_t)(m->N - 1),
+                       cudaMemcpyDeviceToHost, s));
+  if (Qm) CK(cudaMemcpyAsync(Qm, m->Qm, sizeof(double2) * (size_t)m->N * QS * QS, cudaMemcpyDeviceToHost, s));
+  if (c_m) CK(cudaMemcpyAsync(c_m, m->cm, sizeof(double) * m->N, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GBSMPS_OK;
+}
+
+int gbsmps_amplitudes(gbsmps_mps_t m, int64_t P, const uint8_t* patterns, double* out, int mem_kind) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  if (P < 0) return fail(GBSMPS_ERR_ARG, "P < 0");
+  if (P == 0) return GBSMPS_OK;
+  if (!patterns || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  CK(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = m->ctx->stream;
+  DevBuf pb, ob, wb;
+  const uint8_t* dp = patterns;
+  double2* dout = reinterpret_cast<double2*>(out);
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    CK(pb.alloc((size_t)P * m->N, s));
+    CK(cudaMemcpyAsync(pb.p, patterns, (size_t)P * m->N, cudaMemcpyHostToDevice, s));
+    dp = pb.as<uint8_t>();
+    CK(ob.alloc(sizeof(double2) * P, s));
+    dout = ob.as<double2>();
+  }
+  CK(wb.alloc(sizeof(double2) * 2 * (size_t)P * m->maxD, s));
+  ChainView cv{m->N, m->d, m->D.data(), m->toff.data(), m->tensors.as<double2>()};
+  CK(launch_amplitudes(cv, P, dp, dout, wb.as<double2>(), m->maxD, s));
+  COUNT_LAUNCH(2 + m->N);
+  if (mem_kind == GBSMPS_MEM_HOST)
+    CK(cudaMemcpyAsync(out, dout, sizeof(double2) * P, cudaMemcpyDeviceToHost, s));
+  pb.release(); ob.release(); wb.release();
+  if (mem_kind == GBSMPS_MEM_HOST) return sync_status(m->ctx);
+  return GBSMPS_OK;
+}
+
+int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
+                  const double* uniforms, uint8_t* out, uint8_t* flags, int mem_kind) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  if (S < 0) return fail(GBSMPS_ERR_ARG, "S < 0");
+  if (S == 0) return GBSMPS_OK;
+  if (!out) return fail(GBSMPS_ERR_ARG, "out is NULL");
+  if (S > (int64_t)1 << 31) return fail(GBSMPS_ERR_ARG, "S too large for one call");
+  CK(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = m->ctx->stream;
+  const int N = m->N, d = m->d;
+  // samples are processed in chunks that bound the W/Y work buffers
+  const size_t per = (size_t)d * m->maxD;
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)((size_t)6 << 30) / (int64_t)(sizeof(double2) * 2 * per + 32 * m->maxD)));
+  DevBuf ub, obuf, fbuf, vb, wb, yb;
+  CK(vb.alloc(sizeof(double2) * 2 * (size_t)chunk * m->maxD, s));
+  CK(wb.alloc(sizeof(double2) * (size_t)chunk * per, s));
+  CK(yb.alloc(sizeof(double2) * (size_t)chunk * per, s));
+  const double* du = uniforms;
+  uint8_t* dout = out;
+  uint8_t* dfl = flags;
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    if (uniforms) {
+      CK(ub.alloc(sizeof(double) * (size_t)S * N, s));
+      CK(cudaMemcpyAsync(ub.p, uniforms, sizeof(double) * (size_t)S * N, cudaMemcpyHostToDevice, s));
+      du = ub.as<double>();
+    }
+    CK(obuf.alloc((size_t)S * N, s));
+    dout = obuf.as<uint8_t>();
+    if (flags) { CK(fbuf.alloc((size_t)S, s)); dfl = fbuf.as<uint8_t>(); }
+  }
+  if (dfl) CK(cudaMemsetAsync(dfl, 0, (size_t)S, s));
+  const double2* R = m->env.as<double2>();
+  const double2 one = cmk(1, 0), zero = cmk(0, 0);
+  for (int64_t s0 = 0; s0 < S; s0 += chunk) {
+    const int cs = (int)std::min<int64_t>(chunk, S - s0);
+    double2* V = vb.as<double2>();
+    double2* Vn = V + (size_t)chunk * m->maxD;
+    // v = [1] for every sample (D_0 = 1)
+    CK(launch_init_ones(V, cs, 1, s));
+    COUNT_LAUNCH(1);
+    for (int site = 0; site < N; ++site) {
+      const int Dl = m->D[site], Dr = m->D[site + 1];
+      const double2* A = m->tensors.as<double2>() + m->toff[site];
+      double2* W = wb.as<double2>();
+      double2* Y = yb.as<double2>();
+      CK(launch_zgemm('N', 'N', cs, d * Dr, Dl, one, V, Dl, 0, A, d * Dr, 0, zero, W, d * Dr, 0, 1, s));
+      CK(launch_zgemm('N', 'N', cs * d, Dr, Dr, one, W, Dr, 0, R + m->eoff[site + 1], Dr, 0, zero, Y,
+                      Dr, 0, 1, s));
+      CK(launch_sample_select(cs, d, Dr, W, Y, du ? du + (size_t)s0 * N : nullptr, N, site, seed,
+                              counter0 + (uint64_t)s0, Vn, dout + (size_t)s0 * N, N,
+                              dfl ? dfl + s0 : nullptr, s));
+      COUNT_LAUNCH(3);
+      std::swap(V, Vn);
+    }
+  }
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    CK(cudaMemcpyAsync(out, dout, (size_t)S * N, cudaMemcpyDeviceToHost, s));
+    if (flags) CK(cudaMemcpyAsync(flags, dfl, (size_t)S, cudaMemcpyDeviceToHost, s));
+  }
+  ub.release(); obuf.release(); fbuf.release(); vb.release(); wb.release(); yb.release();
+  if (mem_kind == GBSMPS_MEM_HOST) return sync_status(m->ctx);
+  return GBSMPS_OK;
+}
+
+int gbsmps_release(gbsmps_mps_t m) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  cudaSetDevice(m->ctx->device);
+  cudaStream_t s = m->ctx->stream;
+  delete m;
+  cudaStreamSynchronize(s);
+  return GBSMPS_OK;
+}
+
+int gbsmps_build_site(gbsmps_ctx_t c, int32_t nl, int32_t nr, int32_t d, const double* Qm,
+                      double cscale, int32_t Dl, const uint8_t* occ_l, int32_t Dr,
+                      const uint8_t* occ_r, int32_t precision, double* out, int mem_kind) {
+  if (!c || !Qm || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (nl < 0 || nr < 0 || nl > NEM || nr > NEM) return fail(GBSMPS_ERR_ARG, "nl/nr out of range");
+  if (d < 1 || d > 255 || Dl < 1 || Dr < 1 || Dl > 65536 || Dr > 65536)
+    return fail(GBSMPS_ERR_ARG, "sizes out of range");
+  if ((nl > 0 && !occ_l) || (nr > 0 && !occ_r)) return fail(GBSMPS_ERR_ARG, "missing occupations");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int nm = nl + 1 + nr;
+  // host-side repacking of the (small) inputs into the NEM-strided layout
+  std::vector<double2> q(nm * nm);
+  std::vector<uint8_t> ol((size_t)Dl * NEM, 0), orr((size_t)Dr * NEM, 0);
+  std::vector<uint8_t> hl((size_t)Dl * std::max(nl, 1)), hr((size_t)Dr * std::max(nr, 1));
+  auto kind = mem_kind == GBSMPS_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(q.data(), Qm, sizeof(double2) * nm * nm, kind, s));
+  if (nl) CK(cudaMemcpyAsync(hl.data(), occ_l, (size_t)Dl * nl, kind, s));
+  if (nr) CK(cudaMemcpyAsync(hr.data(), occ_r, (size_t)Dr * nr, kind, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < Dl; ++i) for (int k = 0; k < nl; ++k) ol[(size_t)i * NEM + k] = hl[(size_t)i * nl + k];
+  for (int i = 0; i < Dr; ++i) for (int k = 0; k < nr; ++k) orr[(size_t)i * NEM + k] = hr[(size_t)i * nr + k];
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
+  size_t o_q = take(sizeof(double2) * nm * nm);
+  size_t o_ol = take(ol.size());
+  size_t o_or = take(orr.size());
+  size_t o_ll = take(sizeof(int) * (size_t)NEM * Dl);
+  size_t o_lr = take(sizeof(int) * (size_t)NEM * Dr);
+  size_t o_t = take(sizeof(SiteTask));
+  size_t o_s = take(sizeof(double2) * pco_scratch_elems(Dl, Dr));
+  size_t o_o = take(sizeof(double2) * (size_t)Dl * d * Dr);
+  DevBuf buf;
+  CK(buf.alloc(off, s));
+  char* b = buf.as<char>();
+  CK(cudaMemcpyAsync(b + o_q, q.data(), sizeof(double2) * nm * nm, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b + o_ol, ol.data(), ol.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b + o_or, orr.data(), orr.size(), cudaMemcpyHostToDevice, s));
+  CK(launch_maps_brute(reinterpret_cast<uint8_t*>(b + o_ol), Dl, nl, reinterpret_cast<int*>(b + o_ll), Dl, c->d_status, s));
+  CK(launch_maps_brute(reinterpret_cast<uint8_t*>(b + o_or), Dr, nr, reinterpret_cast<int*>(b + o_lr), Dr, c->d_status, s));
+  COUNT_LAUNCH(2);
+  // a basis that is not closed under lowering leaves -1 in the maps: stop here
+  {
+    int rc0 = sync_status(c);
+    if (rc0) { buf.release(); return rc0; }
+  }
+  SiteTask t;
+  t.nl = nl; t.nr = nr; t.Dl = Dl; t.Dr = Dr;
+  t.Q = reinterpret_cast<double2*>(b + o_q); t.qs = nm; t.c = cscale;
+  t.occl = reinterpret_cast<uint8_t*>(b + o_ol); t.lowl = reinterpret_cast<int*>(b + o_ll); t.capl = Dl;
+  t.occr = reinterpret_cast<uint8_t*>(b + o_or); t.lowr = reinterpret_cast<int*>(b + o_lr); t.capr = Dr;
+  double2* dout = mem_kind == GBSMPS_MEM_DEVICE ? reinterpret_cast<double2*>(out)
+                                                : reinterpret_cast<double2*>(b + o_o);
+  t.out = dout;
+  t.scratch_off = 0;
+  CK(cudaMemcpyAsync(b + o_t, &t, sizeof(SiteTask), cudaMemcpyHostToDevice, s));
+  CK(launch_pco(reinterpret_cast<SiteTask*>(b + o_t), 1, d, precision,
+                reinterpret_cast<double2*>(b + o_s), c->d_status, s));
+  COUNT_LAUNCH(1);
+  if (mem_kind == GBSMPS_MEM_HOST)
+    CK(cudaMemcpyAsync(out, dout, sizeof(double2) * (size_t)Dl * d * Dr, cudaMemcpyDeviceToHost, s));
+  buf.release();
+  return sync_status(c);
+}
+
+const char* gbsmps_strerror(int code) {
+  switch (code) {
+    case GBSMPS_OK: return "ok";
+    case GBSMPS_ERR_ARG: return "invalid argument";
+    case GBSMPS_ERR_NOT_SYMMETRIC: return "covariance matrix not symmetric";
+    case GBSMPS_ERR_NOT_PURE: return "covariance matrix not of a pure state";
+    case GBSMPS_ERR_OOM: return "device out of memory";
+    case GBSMPS_ERR_NOT_CONVERGED: return "eigensolver did not converge";
+    case GBSMPS_ERR_BOUNDS: return "size limit exceeded";
+    case GBSMPS_ERR_CUDA: return "CUDA error";
+    case GBSMPS_ERR_NUMERIC: return "numerical failure";
+    case GBSMPS_ERR_STATE: return "invalid state";
+    default: return "unknown error";
+  }
+}
+
+const char* gbsmps_last_error_detail(void) { return g_detail.c_str(); }
+
+int64_t gbsmps_launch_count(gbsmps_ctx_t) { return (int64_t)g_kernel_launches; }
+
+}  // extern "C"

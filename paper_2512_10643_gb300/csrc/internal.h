@@ -1,0 +1,112 @@
+// Internal declarations shared by the gbsmps kernel files (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/gbsmps.h"
+
+#define NEM GBSMPS_NE_MAX          // max entangled pairs per cut
+#define NLM (NEM + 1)              // max modes of L_m = (r_{m-1}, a_m)
+#define N2M (2 * NLM)              // max quadratures of L_m
+#define QS (2 * NEM + 1)           // row stride of stored local paired forms
+#define TIE_MARGIN 64              // extra basis candidates kept for tie groups
+#define TIE_TOL 1e-12              // relative tolerance of an energy tie
+
+// device status word bits (first failure wins, see set_status)
+#define ST_NOT_CONVERGED 1
+#define ST_BOUNDS 2
+#define ST_NUMERIC 4
+#define ST_NOT_SYMMETRIC 8
+#define ST_NOT_PURE 16
+
+// ---- complex helpers on double2 -------------------------------------------
+__host__ __device__ inline double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// a += b * c
+__host__ __device__ inline void cfma(double2& a, double2 b, double2 c) {
+  a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+  a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+
+__device__ inline void set_status(int* st, int bit) { atomicOr(st, bit); }
+
+// ---- per-bond basis storage ----------------------------------------------
+// For bond b (0..N): occupations occ[b*cap*NEM + i*NEM + q] (uint8),
+// energies E[b*cap + i], lowering maps low[(b*NEM + q)*cap + i] = index of
+// state i minus one quantum of mode q (or -1), D[b] kept size, ne[b] modes.
+struct BondArrays {
+  int cap;            // capacity per bond (chi + TIE_MARGIN)
+  uint8_t* occ;
+  double* E;
+  int* low;
+  int* D;             // kept dims (device)
+  int* ne;            // entangled pairs (device)
+  int* maxocc;        // [b*NEM + q] max occupation of mode q in the kept basis
+  double* lam2;       // [b*NEM + q] Lambda^2 (bond b = cut after site b-1)
+  double* eps;        // [b] discarded weight
+};
+
+// ---- launchers (each returns cudaError_t of the launch) -------------------
+// g_kernel_launches counts every kernel the library enqueues.
+extern unsigned long long g_kernel_launches;
+#define COUNT_LAUNCH(n) (g_kernel_launches += (n))
+cudaError_t launch_check_input(const double* gamma, int N, double purity_tol,
+                               double* work, int* status, cudaStream_t s);
+cudaError_t launch_q_to_gamma(const double2* Q, int N, double* gamma, double2* work,
+                              int* status, cudaStream_t s);
+cudaError_t launch_bandwidth(const double* gamma, int N, int* bw, cudaStream_t s);
+cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
+                              double lambda2_freeze, double* Gscratch,
+                              BondArrays ba, double2* Qm, double* cm, int* status,
+                              cudaStream_t s);
+cudaError_t launch_basis(BondArrays ba, int nbonds, int chi, double eps,
+                         int* status, cudaStream_t s);
+cudaError_t launch_maps(BondArrays ba, int nbonds, int* status, cudaStream_t s);
+
+struct SiteTask {       // one local tensor to build
+  int nl, nr, Dl, Dr;
+  const double2* Q;     // (nl+1+nr)^2 with row stride qs
+  int qs;
+  double c;
+  const uint8_t* occl; const int* lowl; int capl;   // left basis (stride NEM)
+  const uint8_t* occr; const int* lowr; int capr;   // right basis
+  double2* out;         // Dl x d x Dr
+  size_t scratch_off;   // offset (complex elements) into the scratch arena
+};
+cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int cap,
+                              int* status, cudaStream_t s);
+cudaError_t launch_pco(const SiteTask* tasks_dev, int ntasks, int d, int precision,
+                       double2* scratch, int* status, cudaStream_t s);
+size_t pco_scratch_elems(int Dl, int Dr);
+
+// complex FP64 GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C, row-major,
+// op = 'N' or 'C' (conjugate transpose), batched with element strides.
+cudaError_t launch_zgemm(char opa, char opb, int M, int N, int K, double2 alpha,
+                         const double2* A, int lda, long long sA,
+                         const double2* B, int ldb, long long sB, double2 beta,
+                         double2* C, int ldc, long long sC, int batch, cudaStream_t s);
+cudaError_t launch_zscale(double2* x, size_t n, const double2* factor, cudaStream_t s);
+cudaError_t launch_norm_phase(const double2* R0, const double2* amp0, double2* factor,
+                              int* status, cudaStream_t s);
+
+struct ChainView {       // view of an MPS for the amplitude kernels
+  int N, d;
+  const int* D;          // host: N+1 bond dims
+  const long long* toff; // host: N tensor offsets (complex elements)
+  const double2* T;      // device: tensors
+};
+cudaError_t launch_amplitudes(ChainView cv, long long P, const uint8_t* pats,
+                              double2* out, double2* work, int maxD, cudaStream_t s);
+cudaError_t launch_init_ones(double2* V, long long P, int ld, cudaStream_t s);
+cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W,
+                                 const double2* Y, const double* u, int ustride,
+                                 int site, uint64_t seed, uint64_t counter0,
+                                 double2* vnew, uint8_t* out, int N, uint8_t* flags,
+                                 cudaStream_t s);

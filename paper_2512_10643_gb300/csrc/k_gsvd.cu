@@ -1,0 +1,646 @@
+// Gaussian SVD chain (Sec. II B) and input handling (Sec. II A, App. A), FP64.
+//
+// One CTA walks the cuts m = 1..N-1 of one state.  At cut m the residual
+// state lives on (r_{m-1}, a_m, .., a_N); its reduced covariance on
+// L_m = (r_{m-1}, a_m) is Williamson-diagonalised (Eq. (symDiag)), the
+// Bogoliubov matrices U, V (Eq. (MUV)) give the regularised paired form of
+// |A^m> = prod exp(b^dag l^dag)|0> (App. A), and the correlations of the
+// active b modes with the rest are carried to the next cut (the b modes are
+// renamed r_m, Eqs. (SVD3)-(bond)).  Because the brick-wall and Haar
+// workloads have banded covariance (zero beyond a mode distance bw), only
+// the bw modes to the right of the cut are carried.
+//
+// Williamson form: V = 2 Gamma_LL = L L^T (Cholesky); K = L^{-1} Omega L^{-T}
+// is antisymmetric with eigenvalues +-i/D; the Hermitian i K is
+// diagonalised by a parallel cyclic complex Jacobi method; for an eigenpair
+// (1/D, w = (u + i v)/sqrt 2), the columns (v | u) give O with
+// O^T K O = [[0, D^-1], [-D^-1, 0]] and S = L O diag(D, D)^{-1/2}.
+#include "internal.h"
+#include <math.h>
+
+namespace {
+
+constexpr int LD = N2M;
+constexpr int CHAIN_THREADS = 256;
+constexpr int MAX_SWEEPS = 40;
+
+struct ChainSmem {
+  double A[N2M * N2M];      // V = 2 Gamma_LL -> L -> S^{-1} active rows
+  double B[N2M * N2M];      // L^{-1} -> S
+  double2 H[N2M * N2M];     // i K -> (Jacobi) ; reused as work for inverses
+  double2 W[N2M * N2M];     // eigenvectors
+  double2 U[NLM * NLM];
+  double2 V[NLM * NLM];
+  double2 Ui[NLM * NLM];
+  double Dprev[NEM];
+  double ev[N2M];
+  int perm[N2M];
+  double Dq[NLM];
+  int rp[NLM], rq[NLM];
+  double rcs[NLM], rsn[NLM];
+  double2 rph[NLM];
+  double2 fac[NLM];
+  double red[CHAIN_THREADS];
+  int ival[4];
+  double dval[4];
+};
+
+__device__ double block_sum(double v, double* red) {
+  int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_max(double v, double* red) {
+  int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] = fmax(red[t], red[t + s]);
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Eigen-decomposition of the n x n Hermitian H (row-major, ld LD) by the
+// cyclic Jacobi method with round-robin parallel ordering: every round
+// rotates n/2 disjoint index pairs at once.  On return H is diagonal (ev),
+// W holds the eigenvectors as columns.  Returns false after MAX_SWEEPS.
+__device__ bool jacobi_herm(ChainSmem& sm, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double2* H = sm.H;
+  double2* W = sm.W;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    int i = idx / n, j = idx % n;
+    W[i * LD + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  double loc = 0.0;
+  for (int idx = tid; idx < n * n; idx += nt) loc += cabs2(H[(idx / n) * LD + idx % n]);
+  const double normF = sqrt(block_sum(loc, sm.red));
+  const double skip = 1e-300 + 1e-18 * normF;
+  const double conv = 1e-15 * normF;
+  const int half = n / 2;
+  bool ok = false;
+  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+    double smax = 0.0;
+    for (int r = 0; r < n - 1; ++r) {
+      if (tid < half) {
+        int k = tid;
+        int a = (r + k) % (n - 1);
+        int b = (k == 0) ? (n - 1) : (r - k + n - 1) % (n - 1);
+        int p = min(a, b), q = max(a, b);
+        double hpp = H[p * LD + p].x, hqq = H[q * LD + q].x;
+        double2 c = H[p * LD + q];
+        double mag = sqrt(cabs2(c));
+        smax = fmax(smax, mag);
+        double cs = 1.0, sn = 0.0;
+        double2 ph = cmk(1.0, 0.0);
+        if (mag > skip) {
+          ph = cmk(c.x / mag, -c.y / mag);            // e^{-i phi}
+          double tau = (hqq - hpp) / (2.0 * mag);
+          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          cs = 1.0 / sqrt(1.0 + t * t);
+          sn = t * cs;
+        }
+        sm.rp[k] = p; sm.rq[k] = q; sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = ph;
+      }
+      __syncthreads();
+      // columns: X = H J, W = W J with J = [[cs, sn], [-sn ph, cs ph]]
+      for (int idx = tid; idx < half * n; idx += nt) {
+        int k = idx / n, i = idx % n;
+        if (sm.rsn[k] == 0.0) continue;
+        int p = sm.rp[k], q = sm.rq[k];
+        double cs = sm.rcs[k], sn = sm.rsn[k];
+        double2 ph = sm.rph[k];
+        double2 hp = H[i * LD + p], hq = H[i * LD + q];
+        double2 phq = cmul(ph, hq);
+        H[i * LD + p] = cmk(cs * hp.x - sn * phq.x, cs * hp.y - sn * phq.y);
+        H[i * LD + q] = cmk(sn * hp.x + cs * phq.x, sn * hp.y + cs * phq.y);
+        double2 wp = W[i * LD + p], wq = W[i * LD + q];
+        double2 pwq = cmul(ph, wq);
+        W[i * LD + p] = cmk(cs * wp.x - sn * pwq.x, cs * wp.y - sn * pwq.y);
+        W[i * LD + q] = cmk(sn * wp.x + cs * pwq.x, sn * wp.y + cs * pwq.y);
+      }
+      __syncthreads();
+      // rows: H = J^dag X
+      for (int idx = tid; idx < half * n; idx += nt) {
+        int k = idx / n, j = idx % n;
+        if (sm.rsn[k] == 0.0) continue;
+        int p = sm.rp[k], q = sm.rq[k];
+        double cs = sm.rcs[k], sn = sm.rsn[k];
+        double2 phc = cconj(sm.rph[k]);
+        double2 xp = H[p * LD + j], xq = H[q * LD + j];
+        double2 pxq = cmul(phc, xq);
+        H[p * LD + j] = cmk(cs * xp.x - sn * pxq.x, cs * xp.y - sn * pxq.y);
+        H[q * LD + j] = cmk(sn * xp.x + cs * pxq.x, sn * xp.y + cs * pxq.y);
+      }
+      __syncthreads();
+    }
+    double gmax = block_max(smax, sm.red);
+    if (gmax <= conv) { ok = true; break; }
+  }
+  for (int i = tid; i < n; i += nt) sm.ev[i] = H[i * LD + i].x;
+  __syncthreads();
+  return ok;
+}
+
+// Inverse of the n x n complex matrix M (ld NLM) into Inv (ld NLM) by
+// Gauss-Jordan elimination with partial pivoting; M is destroyed.  Returns
+// log|det M| in sm.dval[0]; sets ival[0] = 1 on a zero pivot.
+__device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    int i = idx / n, j = idx % n;
+    Inv[i * NLM + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (tid == 0) { sm.dval[0] = 0.0; sm.ival[0] = 0; }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      int pr = k;
+      double best = cabs2(M[k * NLM + k]);
+      for (int i = k + 1; i < n; ++i) {
+        double v = cabs2(M[i * NLM + k]);
+        if (v > best) { best = v; pr = i; }
+      }
+      if (best == 0.0) sm.ival[0] = 1;
+      sm.ival[1] = pr;
+      sm.dval[0] += 0.5 * log(best > 0.0 ? best : 1e-300);
+    }
+    __syncthreads();
+    int pr = sm.ival[1];
+    if (pr != k) {
+      for (int j = tid; j < n; j += nt) {
+        double2 t = M[k * NLM + j]; M[k * NLM + j] = M[pr * NLM + j]; M[pr * NLM + j] = t;
+        t = Inv[k * NLM + j]; Inv[k * NLM + j] = Inv[pr * NLM + j]; Inv[pr * NLM + j] = t;
+      }
+    }
+    __syncthreads();
+    double2 piv = M[k * NLM + k];
+    double pm = cabs2(piv);
+    double2 pinv = pm > 0.0 ? cmk(piv.x / pm, -piv.y / pm) : cmk(0.0, 0.0);
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      M[k * NLM + j] = cmul(M[k * NLM + j], pinv);
+      Inv[k * NLM + j] = cmul(Inv[k * NLM + j], pinv);
+    }
+    for (int i = tid; i < n; i += nt) sm.fac[i] = M[i * NLM + k];
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int i = idx / n, j = idx % n;
+      if (i == k) continue;
+      double2 f = sm.fac[i];
+      M[i * NLM + j] = csub(M[i * NLM + j], cmul(f, M[k * NLM + j]));
+      Inv[i * NLM + j] = csub(Inv[i * NLM + j], cmul(f, Inv[k * NLM + j]));
+    }
+    __syncthreads();
+  }
+}
+
+// Paired form of the pure state on L = (r, a) from its covariance in A
+// (n2 x n2, ld LD): Q = M (1 + N)^{-1} (Eq. (paired-form)).
+__device__ void last_site(ChainSmem& sm, int nL, double2* Qout, int* status) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double2* Nm = sm.H;      // (1 + N), ld NLM
+  double2* Mm = sm.W;      // M, ld NLM
+  for (int idx = tid; idx < nL * nL; idx += nt) {
+    int i = idx / nL, j = idx % nL;
+    double gxx = sm.A[i * LD + j], gpp = sm.A[(nL + i) * LD + nL + j];
+    double gxp = sm.A[i * LD + nL + j], gpx = sm.A[(nL + i) * LD + j];
+    Nm[i * NLM + j] = cmk(0.5 * (gxx + gpp) + (i == j ? 0.5 : 0.0), 0.5 * (gxp - gpx));
+    Mm[i * NLM + j] = cmk(0.5 * (gxx - gpp), 0.5 * (gxp + gpx));
+  }
+  __syncthreads();
+  cinv(sm, Nm, sm.Ui, nL);
+  if (tid == 0 && sm.ival[0]) set_status(status, ST_NUMERIC);
+  // Q = M (1+N)^{-1}, symmetrised
+  for (int idx = tid; idx < nL * nL; idx += nt) {
+    int i = idx / nL, j = idx % nL;
+    double2 a = cmk(0, 0), b = cmk(0, 0);
+    for (int k = 0; k < nL; ++k) {
+      cfma(a, Mm[i * NLM + k], sm.Ui[k * NLM + j]);
+      cfma(b, Mm[j * NLM + k], sm.Ui[k * NLM + i]);
+    }
+    Qout[i * QS + j] = cscale(cadd(a, b), 0.5);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(CHAIN_THREADS)
+gsvd_chain_kernel(const double* __restrict__ gam, int N, const int* __restrict__ bwp,
+                  double freeze, double* __restrict__ Gs, BondArrays ba,
+                  double2* __restrict__ Qm, double* __restrict__ cm, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ChainSmem& sm = *reinterpret_cast<ChainSmem*>(smraw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long twoN = 2LL * N;
+  const int bw = max(1, min(*bwp, N));
+  const int ldg = 2 * bw;
+  double* Gc = Gs;
+  double* Gn = Gs + (size_t)2 * NEM * ldg;
+  int nin = 0;
+  if (tid == 0) { ba.ne[0] = 0; ba.ne[N] = 0; }
+  for (int m = 0; m < N; ++m) {
+    const int nL = nin + 1, n2 = 2 * nL;
+    // ---- reduced covariance of L_m (xxpp: r_1..r_nin, a_m | p's) --------
+    for (int idx = tid; idx < n2 * n2; idx += nt) sm.A[(idx / n2) * LD + idx % n2] = 0.0;
+    __syncthreads();
+    for (int i = tid; i < nin; i += nt) {
+      sm.A[i * LD + i] = 0.5 * sm.Dprev[i];
+      sm.A[(nL + i) * LD + nL + i] = 0.5 * sm.Dprev[i];
+      double gxx = Gc[i * ldg], gxp = Gc[i * ldg + bw];
+      double gpx = Gc[(nin + i) * ldg], gpp = Gc[(nin + i) * ldg + bw];
+      sm.A[i * LD + nin] = gxx;           sm.A[nin * LD + i] = gxx;
+      sm.A[(nL + i) * LD + nin] = gpx;    sm.A[nin * LD + nL + i] = gpx;
+      sm.A[i * LD + nL + nin] = gxp;      sm.A[(nL + nin) * LD + i] = gxp;
+      sm.A[(nL + i) * LD + nL + nin] = gpp; sm.A[(nL + nin) * LD + nL + i] = gpp;
+    }
+    if (tid == 0) {
+      sm.A[nin * LD + nin] = gam[m * twoN + m];
+      sm.A[nin * LD + nL + nin] = gam[m * twoN + N + m];
+      sm.A[(nL + nin) * LD + nin] = gam[(N + m) * twoN + m];
+      sm.A[(nL + nin) * LD + nL + nin] = gam[(N + m) * twoN + N + m];
+    }
+    __syncthreads();
+    if (m == N - 1) {
+      last_site(sm, nL, Qm + (size_t)m * QS * QS, status);
+      if (tid == 0) cm[m] = 1.0;
+      break;
+    }
+    // ---- Cholesky of V = 2 Gamma_LL (lower, in place) -------------------
+    for (int idx = tid; idx < n2 * n2; idx += nt) sm.A[(idx / n2) * LD + idx % n2] *= 2.0;
+    __syncthreads();
+    for (int k = 0; k < n2; ++k) {
+      double akk = sm.A[k * LD + k];
+      if (!(akk > 0.0)) { if (tid == 0) set_status(status, ST_NUMERIC); akk = 1e-300; }
+      double lkk = sqrt(akk);
+      __syncthreads();
+      for (int i = k + 1 + tid; i < n2; i += nt) sm.A[i * LD + k] /= lkk;
+      if (tid == 0) sm.A[k * LD + k] = lkk;
+      __syncthreads();
+      const int w = n2 - k - 1;
+      for (int idx = tid; idx < w * w; idx += nt) {
+        int i = k + 1 + idx / w, j = k + 1 + idx % w;
+        if (j <= i) sm.A[i * LD + j] -= sm.A[i * LD + k] * sm.A[j * LD + k];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < n2 * n2; idx += nt) {
+      int i = idx / n2, j = idx % n2;
+      if (j > i) sm.A[i * LD + j] = 0.0;
+    }
+    __syncthreads();
+    // ---- L^{-1} by forward substitution, one column per thread ----------
+    for (int j = tid; j < n2; j += nt) {
+      for (int i = 0; i < n2; ++i) {
+        double x;
+        if (i < j) x = 0.0;
+        else if (i == j) x = 1.0 / sm.A[i * LD + i];
+        else {
+          double s = 0.0;
+          for (int k = j; k < i; ++k) s += sm.A[i * LD + k] * sm.B[k * LD + j];
+          x = -s / sm.A[i * LD + i];
+        }
+        sm.B[i * LD + j] = x;
+      }
+    }
+    __syncthreads();
+    // ---- H = i K, K = L^{-1} Omega L^{-T} --------------------------------
+    for (int idx = tid; idx < n2 * n2; idx += nt) {
+      int i = idx / n2, j = idx % n2;
+      double s = 0.0;
+      for (int k = 0; k < nL; ++k)
+        s += sm.B[i * LD + k] * sm.B[j * LD + nL + k] - sm.B[i * LD + nL + k] * sm.B[j * LD + k];
+      sm.H[i * LD + j] = cmk(0.0, s);
+    }
+    __syncthreads();
+    bool ok = jacobi_herm(sm, n2);
+    if (!ok && tid == 0) set_status(status, ST_NOT_CONVERGED);
+    // ---- order eigenvalues: positive half ascending = D descending ------
+    if (tid == 0) {
+      for (int i = 0; i < n2; ++i) sm.perm[i] = i;
+      for (int i = 1; i < n2; ++i) {
+        int v = sm.perm[i], j = i - 1;
+        while (j >= 0 && sm.ev[sm.perm[j]] > sm.ev[v]) { sm.perm[j + 1] = sm.perm[j]; --j; }
+        sm.perm[j + 1] = v;
+      }
+      for (int q = 0; q < nL; ++q) {
+        double e = sm.ev[sm.perm[nL + q]];
+        if (!(e > 0.0)) { set_status(status, ST_NUMERIC); e = 1.0; }
+        sm.Dq[q] = 1.0 / e;
+      }
+    }
+    __syncthreads();
+    // ---- S = L O diag(D, D)^{-1/2} into B --------------------------------
+    const double r2 = 1.4142135623730951;
+    for (int idx = tid; idx < n2 * n2; idx += nt) {
+      int i = idx / n2, c = idx % n2;
+      int q = c < nL ? c : c - nL;
+      int col = sm.perm[nL + q];
+      double s = 0.0;
+      for (int k = 0; k <= i; ++k) {
+        double2 w = sm.W[k * LD + col];
+        s += sm.A[i * LD + k] * (c < nL ? w.y : w.x);
+      }
+      sm.B[i * LD + c] = r2 * s / sqrt(sm.Dq[q]);
+    }
+    __syncthreads();
+    // ---- U, V (a = U b + V^* b^dag) --------------------------------------
+    for (int idx = tid; idx < nL * nL; idx += nt) {
+      int i = idx / nL, j = idx % nL;
+      double s11 = sm.B[i * LD + j], s12 = sm.B[i * LD + nL + j];
+      double s21 = sm.B[(nL + i) * LD + j], s22 = sm.B[(nL + i) * LD + nL + j];
+      sm.U[i * NLM + j] = cmk(0.5 * (s11 + s22), 0.5 * (s21 - s12));
+      sm.V[i * NLM + j] = cmk(0.5 * (s11 - s22), -0.5 * (s21 + s12));
+    }
+    __syncthreads();
+    // ---- canonical gauge: largest |U_jq| of each column real positive ----
+    for (int q = tid; q < nL; q += nt) {
+      int jb = 0;
+      double best = -1.0;
+      for (int j = 0; j < nL; ++j) {
+        double v = cabs2(sm.U[j * NLM + q]);
+        if (v > best) { best = v; jb = j; }
+      }
+      double2 u = sm.U[jb * NLM + q];
+      double mg = sqrt(best);
+      double2 ph = cmk(u.x / mg, -u.y / mg);
+      for (int j = 0; j < nL; ++j) {
+        sm.U[j * NLM + q] = cmul(sm.U[j * NLM + q], ph);
+        sm.V[j * NLM + q] = cmul(sm.V[j * NLM + q], ph);
+      }
+    }
+    if (tid == 0) {
+      int na = 0;
+      while (na < nL && (sm.Dq[na] - 1.0) / (sm.Dq[na] + 1.0) > freeze) ++na;
+      if (na > NEM) { set_status(status, ST_BOUNDS); na = NEM; }
+      sm.ival[2] = na;
+    }
+    __syncthreads();
+    const int na = sm.ival[2];
+    // ---- U^{-1} and |det U| ----------------------------------------------
+    for (int idx = tid; idx < nL * nL; idx += nt) {        // work copy, ld NLM
+      int i = idx / nL, j = idx % nL;
+      sm.H[i * NLM + j] = sm.U[i * NLM + j];
+    }
+    __syncthreads();
+    cinv(sm, sm.H, sm.Ui, nL);
+    if (tid == 0) {
+      if (sm.ival[0]) set_status(status, ST_NUMERIC);
+      cm[m] = exp(-0.5 * sm.dval[0]);
+    }
+    // ---- local paired form Q^m over (r_{m-1}, a_m, l_m), App. A ----------
+    double2* Qo = Qm + (size_t)m * QS * QS;
+    const int nq = nL + na;
+    for (int idx = tid; idx < nq * nq; idx += nt) {
+      int i = idx / nq, j = idx % nq;
+      double2 v = cmk(0, 0);
+      if (i < nL && j < nL) {            // U^-dag V^dag: sum_k conj(Ui_ki) conj(V_jk)
+        for (int k = 0; k < nL; ++k) cfma(v, cconj(sm.Ui[k * NLM + i]), cconj(sm.V[j * NLM + k]));
+        double2 w = cmk(0, 0);
+        for (int k = 0; k < nL; ++k) cfma(w, cconj(sm.Ui[k * NLM + j]), cconj(sm.V[i * NLM + k]));
+        v = cscale(cadd(v, w), 0.5);
+      } else if (i < nL) {               // U^-dag restricted: conj(Ui_{q i})
+        v = cconj(sm.Ui[(j - nL) * NLM + i]);
+      } else if (j < nL) {               // U^-* : conj(Ui_{q j})
+        v = cconj(sm.Ui[(i - nL) * NLM + j]);
+      } else {                           // -V^T U^-dag: -sum_k V_kq conj(Ui_q'k)
+        int q = i - nL, qp = j - nL;
+        double2 w = cmk(0, 0);
+        for (int k = 0; k < nL; ++k) {
+          cfma(v, sm.V[k * NLM + q], cconj(sm.Ui[qp * NLM + k]));
+          cfma(w, sm.V[k * NLM + qp], cconj(sm.Ui[q * NLM + k]));
+        }
+        v = cscale(cadd(v, w), -0.5);
+      }
+      Qo[i * QS + j] = v;
+    }
+    // ---- rows of S^{-1} for the active b modes (into A) -------------------
+    for (int idx = tid; idx < na * nL; idx += nt) {
+      int q = idx / nL, j = idx % nL;
+      double2 u = sm.U[j * NLM + q], v = sm.V[j * NLM + q];
+      sm.A[q * LD + j] = u.x - v.x;                 // x_b <- x
+      sm.A[q * LD + nL + j] = u.y + v.y;            // x_b <- p
+      sm.A[(na + q) * LD + j] = v.y - u.y;          // p_b <- x
+      sm.A[(na + q) * LD + nL + j] = u.x + v.x;     // p_b <- p
+    }
+    if (tid < na) {
+      double D = sm.Dq[tid];
+      ba.lam2[(size_t)(m + 1) * NEM + tid] = (D - 1.0) / (D + 1.0);
+    }
+    if (tid == 0) ba.ne[m + 1] = na;
+    __syncthreads();
+    // ---- propagate: G_new = S^{-1}_act cov(L_m, a_{m+1 .. m+bw}) ---------
+    for (int idx = tid; idx < 2 * na * ldg; idx += nt) {
+      int rr = idx / ldg, c = idx % ldg;
+      int isp = c >= bw;
+      int cc = isp ? c - bw : c;         // mode m+1+cc
+      int mode = m + 1 + cc;
+      double s = 0.0;
+      if (mode < N) {
+        for (int k = 0; k < n2; ++k) {
+          double g;
+          bool kp = k >= nL;
+          int kk = kp ? k - nL : k;
+          if (kk < nin) {                // r row: carried G column cc+1
+            g = (cc + 1 < bw) ? Gc[(kp ? nin + kk : kk) * ldg + (isp ? bw : 0) + cc + 1] : 0.0;
+          } else {                       // a_m row
+            long long row = kp ? (N + m) : m;
+            long long col = isp ? (N + mode) : mode;
+            g = gam[row * twoN + col];
+          }
+          s += sm.A[rr * LD + k] * g;
+        }
+      }
+      Gn[rr * ldg + c] = s;
+    }
+    if (tid < na) sm.Dprev[tid] = sm.Dq[tid];
+    __syncthreads();
+    double* t = Gc; Gc = Gn; Gn = t;
+    nin = na;
+  }
+}
+
+// ---- input checks -----------------------------------------------------------
+// max |Gamma - Gamma^T| and max |(2 Gamma Omega)^2 + 1|, tiled 32 x 32.
+__global__ void check_input_kernel(const double* __restrict__ g, int N,
+                                   unsigned long long* maxes) {
+  __shared__ double ta[32][33], tb[32][33];
+  const int n = 2 * N;
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int ty = threadIdx.y, tx = threadIdx.x;   // 32 x 8
+  double acc[4] = {0, 0, 0, 0};
+  double asym = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      int i = bi + r, k = k0 + tx;
+      // X_ik = 2 (Gamma Omega)_ik : k < N -> -2 G[i][k+N]; k >= N -> 2 G[i][k-N]
+      double x = 0.0;
+      if (i < n && k < n) x = (k < N) ? -2.0 * g[(size_t)i * n + k + N] : 2.0 * g[(size_t)i * n + k - N];
+      ta[r][tx] = x;
+      int kk = k0 + r, j = bj + tx;
+      double y = 0.0;
+      if (kk < n && j < n) y = (j < N) ? -2.0 * g[(size_t)kk * n + j + N] : 2.0 * g[(size_t)kk * n + j - N];
+      tb[r][tx] = y;
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      int r = ty + 8 * q;
+      double s = acc[q];
+      for (int k = 0; k < 32; ++k) s += ta[r][k] * tb[k][tx];
+      acc[q] = s;
+    }
+    __syncthreads();
+  }
+  double dev = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    int i = bi + ty + 8 * q, j = bj + tx;
+    if (i < n && j < n) {
+      dev = fmax(dev, fabs(acc[q] + (i == j ? 1.0 : 0.0)));
+      asym = fmax(asym, fabs(g[(size_t)i * n + j] - g[(size_t)j * n + i]));
+    }
+  }
+  atomicMax(&maxes[0], __double_as_longlong(asym));
+  atomicMax(&maxes[1], __double_as_longlong(dev));
+}
+
+__global__ void check_finish_kernel(const unsigned long long* maxes, double tol, int* status) {
+  double asym = __longlong_as_double(maxes[0]);
+  double dev = __longlong_as_double(maxes[1]);
+  if (!(asym <= 1e-12)) set_status(status, ST_NOT_SYMMETRIC);
+  if (!(dev <= tol)) set_status(status, ST_NOT_PURE);
+}
+
+__global__ void bandwidth_kernel(const double* __restrict__ g, int N, int* bw) {
+  const int n = 2 * N;
+  int best = 0;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)n * n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int i = idx / n, j = idx % n;
+    if (g[idx] != 0.0) best = max(best, abs((i % N) - (j % N)));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(bw, best);
+}
+
+// ---- Q -> Gamma: N = (1 - Q^* Q)^{-1} - 1, M = Q (1 + N) --------------------
+__global__ void q_prep_kernel(const double2* __restrict__ Q, int N, double2* X) {
+  // X = 1 - Q^* Q  (N x N)
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)N * N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 s = cmk(i == j ? 1.0 : 0.0, 0.0);
+    for (int k = 0; k < N; ++k) {
+      double2 p = cmul(cconj(Q[(size_t)i * N + k]), Q[(size_t)k * N + j]);
+      s = csub(s, p);
+    }
+    X[idx] = s;
+  }
+}
+
+// in-place Gauss-Jordan step k on X (Hermitian positive definite: no pivoting)
+__global__ void gj_save_kernel(const double2* X, int N, int k, double2* rowk, double2* colk) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+    rowk[t] = X[(size_t)k * N + t];
+    colk[t] = X[(size_t)t * N + k];
+  }
+}
+__global__ void gj_step_kernel(double2* X, int N, int k, const double2* rowk,
+                               const double2* colk, int* status) {
+  double2 piv = rowk[k];
+  double pm = cabs2(piv);
+  if (pm == 0.0) { if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, ST_NUMERIC); return; }
+  double2 pinv = cmk(piv.x / pm, -piv.y / pm);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)N * N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 v;
+    if (i == k && j == k) v = pinv;
+    else if (i == k) v = cmul(rowk[j], pinv);
+    else if (j == k) v = cmul(cscale(colk[i], -1.0), pinv);
+    else v = csub(X[idx], cmul(cmul(colk[i], rowk[j]), pinv));
+    X[idx] = v;
+  }
+}
+__global__ void q_finish_kernel(const double2* __restrict__ Q, const double2* __restrict__ Xi,
+                                int N, double* __restrict__ g) {
+  // (1 + N) = Xi ; M = Q Xi
+  const int n = 2 * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)N * N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int i = idx / N, j = idx % N;
+    double2 nn = Xi[idx];
+    nn.x -= (i == j) ? 1.0 : 0.0;
+    double2 mm = cmk(0, 0);
+    for (int k = 0; k < N; ++k) cfma(mm, Q[(size_t)i * N + k], Xi[(size_t)k * N + j]);
+    double2 nt = Xi[(size_t)j * N + i];   // for symmetric averaging of N (Hermitian)
+    nt.x -= (i == j) ? 1.0 : 0.0;
+    double nre = 0.5 * (nn.x + nt.x), nim = 0.5 * (nn.y - nt.y);
+    g[(size_t)i * n + j] = nre + mm.x + ((i == j) ? 0.5 : 0.0);            // xx
+    g[(size_t)(N + i) * n + N + j] = nre - mm.x + ((i == j) ? 0.5 : 0.0);  // pp
+    g[(size_t)i * n + N + j] = nim + mm.y;                                  // xp
+    g[(size_t)(N + i) * n + j] = mm.y - nim;                                // px
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_check_input(const double* gamma, int N, double purity_tol,
+                               double* work, int* status, cudaStream_t s) {
+  unsigned long long* maxes = reinterpret_cast<unsigned long long*>(work);
+  cudaError_t e = cudaMemsetAsync(maxes, 0, 2 * sizeof(unsigned long long), s);
+  if (e) return e;
+  int nb = (2 * N + 31) / 32;
+  check_input_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(gamma, N, maxes);
+  check_finish_kernel<<<1, 1, 0, s>>>(maxes, purity_tol, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bandwidth(const double* gamma, int N, int* bw, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bw, 0, sizeof(int), s);
+  if (e) return e;
+  size_t n = (size_t)4 * N * N;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  bandwidth_kernel<<<blocks, 256, 0, s>>>(gamma, N, bw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_to_gamma(const double2* Q, int N, double* gamma, double2* work,
+                              int* status, cudaStream_t s) {
+  double2* X = work;
+  double2* rowk = work + (size_t)N * N;
+  double2* colk = rowk + N;
+  int blocks = (int)(((size_t)N * N + 255) / 256);
+  if (blocks > 8192) blocks = 8192;
+  q_prep_kernel<<<blocks, 256, 0, s>>>(Q, N, X);
+  for (int k = 0; k < N; ++k) {
+    gj_save_kernel<<<(N + 255) / 256, 256, 0, s>>>(X, N, k, rowk, colk);
+    gj_step_kernel<<<blocks, 256, 0, s>>>(X, N, k, rowk, colk, status);
+  }
+  cudaError_t e = cudaMemsetAsync(gamma, 0, sizeof(double) * 4 * (size_t)N * N, s);
+  if (e) return e;
+  q_finish_kernel<<<blocks, 256, 0, s>>>(Q, X, N, gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
+                              double lambda2_freeze, double* Gscratch, BondArrays ba,
+                              double2* Qm, double* cm, int* status, cudaStream_t s) {
+  size_t smem = sizeof(ChainSmem);
+  cudaError_t e = cudaFuncSetAttribute(gsvd_chain_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return e;
+  gsvd_chain_kernel<<<1, CHAIN_THREADS, smem, s>>>(gamma, N, bw, lambda2_freeze, Gscratch,
+                                                   ba, Qm, cm, status);
+  return cudaGetLastError();
+}

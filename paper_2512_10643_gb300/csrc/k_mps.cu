@@ -1,0 +1,282 @@
+// MPS consumers on the finished tensors: right environments and the
+// normalisation, amplitudes, and exact conditional sampling (FP64 path).
+//
+// Right environments R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (R_{N+1} = 1) are two
+// complex GEMMs per site; sampling at site m is W = V A^m (S x D_{m-1} by
+// D_{m-1} x d D_m), Y = W R_{m+1}, then per sample q_p = Re <Y_p, W_p>,
+// the first p with u Z < C_p, and v = w_p / sqrt(q_p).
+#include "internal.h"
+#include <math.h>
+
+namespace {
+
+// ---- complex FP64 GEMM, 64 x 64 tile, 16-deep k slices, 4 x 4 per thread ----
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__global__ void __launch_bounds__(256)
+zgemm_kernel(char opa, char opb, int M, int N, int K, double2 alpha,
+             const double2* __restrict__ A, int lda, long long sA,
+             const double2* __restrict__ B, int ldb, long long sB, double2 beta,
+             double2* __restrict__ C, int ldc, long long sC) {
+  __shared__ double2 As[TK][TM + 1];
+  __shared__ double2 Bs[TK][TN + 1];
+  const int bz = blockIdx.z;
+  A += bz * sA; B += bz * sB; C += bz * sC;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = cmk(0, 0);
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = tid; e < TK * TM; e += 256) {
+      int kk, ii;
+      double2 v = cmk(0, 0);
+      if (opa == 'N') { ii = e / TK; kk = e % TK;
+        int gi = i0 + ii, gk = k0 + kk;
+        if (gi < M && gk < K) v = A[(size_t)gi * lda + gk];
+      } else { kk = e / TM; ii = e % TM;
+        int gi = i0 + ii, gk = k0 + kk;
+        if (gi < M && gk < K) v = cconj(A[(size_t)gk * lda + gi]);
+      }
+      As[kk][ii] = v;
+    }
+    for (int e = tid; e < TK * TN; e += 256) {
+      int kk, jj;
+      double2 v = cmk(0, 0);
+      if (opb == 'N') { kk = e / TN; jj = e % TN;
+        int gj = j0 + jj, gk = k0 + kk;
+        if (gj < N && gk < K) v = B[(size_t)gk * ldb + gj];
+      } else { jj = e / TK; kk = e % TK;
+        int gj = j0 + jj, gk = k0 + kk;
+        if (gj < N && gk < K) v = cconj(B[(size_t)gj * ldb + gk]);
+      }
+      Bs[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cfma(acc[r][c], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int gi = i0 + ty + 16 * r;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int gj = j0 + tx + 16 * c;
+      if (gj >= N) continue;
+      double2 v = cmul(alpha, acc[r][c]);
+      if (beta.x != 0.0 || beta.y != 0.0) cfma(v, beta, C[(size_t)gi * ldc + gj]);
+      C[(size_t)gi * ldc + gj] = v;
+    }
+  }
+}
+
+__global__ void zscale_kernel(double2* x, size_t n, const double2* f) {
+  double2 s = *f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = cmul(x[i], s);
+}
+
+// factor = conj(amp0)/|amp0| / sqrt(R0): unit norm, vacuum amplitude > 0
+__global__ void norm_phase_kernel(const double2* R0, const double2* amp0, double2* f, int* status) {
+  double n2 = R0->x;
+  double2 a = *amp0;
+  double m = sqrt(cabs2(a));
+  if (!(n2 > 0.0) || !isfinite(n2)) { set_status(status, ST_NUMERIC); *f = cmk(1, 0); return; }
+  double s = 1.0 / sqrt(n2);
+  if (m > 0.0) *f = cmk(a.x / m * s, -a.y / m * s);
+  else *f = cmk(s, 0.0);
+}
+
+// amplitudes: Vn[s, b] = sum_a V[s, a] A[a, n_s, b]
+__global__ void amp_step_kernel(const double2* __restrict__ T, int Dl, int d, int Dr,
+                                const uint8_t* __restrict__ pats, int N, int site,
+                                long long P, const double2* __restrict__ V,
+                                double2* __restrict__ Vn, int ld) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P * Dr;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long s = idx / Dr;
+    int b = idx % Dr;
+    int p = pats[s * N + site];
+    double2 acc = cmk(0, 0);
+    if (p < d) {
+      for (int a = 0; a < Dl; ++a) cfma(acc, V[s * ld + a], T[((size_t)a * d + p) * Dr + b]);
+    }
+    Vn[s * ld + b] = acc;
+  }
+}
+
+__global__ void amp_init_kernel(double2* V, long long P, int ld) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < P; s += (long long)gridDim.x * blockDim.x)
+    V[s * ld] = cmk(1.0, 0.0);
+}
+
+__global__ void amp_out_kernel(const double2* V, long long P, int ld, double2* out) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < P; s += (long long)gridDim.x * blockDim.x)
+    out[s] = V[s * ld];
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------------
+__device__ inline void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+  uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+  uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+  c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+
+__device__ inline double philox_uniform(uint64_t seed, uint64_t sample, uint32_t site) {
+  uint32_t c[4] = {(uint32_t)sample, (uint32_t)(sample >> 32), site, 0u};
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c, k0, k1);
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  uint64_t a = c[0] >> 5, b = c[1] >> 6;     // 27 + 26 bits
+  return (double)(a * 67108864ull + b) * (1.0 / 9007199254740992.0);
+}
+
+// one warp per sample
+__global__ void sample_select_kernel(int S, int d, int Dm, const double2* __restrict__ W,
+                                     const double2* __restrict__ Y, const double* __restrict__ u,
+                                     int ustride, int site, uint64_t seed, uint64_t counter0,
+                                     double2* __restrict__ vnew, uint8_t* __restrict__ out,
+                                     int N, uint8_t* flags) {
+  const int lane = threadIdx.x & 31;
+  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (s >= S) return;
+  const double2* w = W + (size_t)s * d * Dm;
+  const double2* y = Y + (size_t)s * d * Dm;
+  double Z = 0.0;
+  // pass 1: total
+  double qs[8];
+  for (int p = 0; p < d; ++p) {
+    double part = 0.0;
+    for (int b = lane; b < Dm; b += 32) {
+      double2 yy = y[(size_t)p * Dm + b], ww = w[(size_t)p * Dm + b];
+      part += yy.x * ww.x + yy.y * ww.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    part = fmax(part, 0.0);
+    if (p < 8) qs[p] = part;
+    Z += part;
+  }
+  double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
+  const double t = uu * Z;
+  int pstar = -1, plast = 0;
+  double C = 0.0, qsel = 0.0;
+  bool flag = false;
+  for (int p = 0; p < d; ++p) {
+    double q;
+    if (p < 8) q = qs[p];
+    else {
+      double part = 0.0;
+      for (int b = lane; b < Dm; b += 32) {
+        double2 yy = y[(size_t)p * Dm + b], ww = w[(size_t)p * Dm + b];
+        part += yy.x * ww.x + yy.y * ww.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      q = fmax(part, 0.0);
+    }
+    C += q;
+    if (fabs(t - C) <= 1e-12 * Z) flag = true;
+    if (q > 0.0) { plast = p; }
+    if (pstar < 0 && t < C) { pstar = p; qsel = q; }
+  }
+  if (pstar < 0) {
+    pstar = plast;
+    // recompute q of the fallback
+    double part = 0.0;
+    for (int b = lane; b < Dm; b += 32) {
+      double2 yy = y[(size_t)pstar * Dm + b], ww = w[(size_t)pstar * Dm + b];
+      part += yy.x * ww.x + yy.y * ww.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    qsel = fmax(part, 0.0);
+  }
+  const double inv = qsel > 0.0 ? 1.0 / sqrt(qsel) : 0.0;
+  for (int b = lane; b < Dm; b += 32) vnew[(size_t)s * Dm + b] = cscale(w[(size_t)pstar * Dm + b], inv);
+  if (lane == 0) {
+    out[(size_t)s * N + site] = (uint8_t)pstar;
+    if (flags && flag) flags[s] = 1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_zgemm(char opa, char opb, int M, int N, int K, double2 alpha,
+                         const double2* A, int lda, long long sA, const double2* B, int ldb,
+                         long long sB, double2 beta, double2* C, int ldc, long long sC,
+                         int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch);
+  zgemm_kernel<<<grid, 256, 0, s>>>(opa, opb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                    ldc, sC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zscale(double2* x, size_t n, const double2* factor, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  zscale_kernel<<<blocks, 256, 0, s>>>(x, n, factor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_phase(const double2* R0, const double2* amp0, double2* factor,
+                              int* status, cudaStream_t s) {
+  norm_phase_kernel<<<1, 1, 0, s>>>(R0, amp0, factor, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amplitudes(ChainView cv, long long P, const uint8_t* pats, double2* out,
+                              double2* work, int maxD, cudaStream_t s) {
+  double2* V = work;
+  double2* Vn = work + (size_t)P * maxD;
+  int blocks = (int)((P + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  amp_init_kernel<<<blocks, 256, 0, s>>>(V, P, maxD);
+  for (int m = 0; m < cv.N; ++m) {
+    int Dl = cv.D[m], Dr = cv.D[m + 1];
+    long long n = P * Dr;
+    int b2 = (int)((n + 255) / 256);
+    if (b2 > 8192) b2 = 8192;
+    amp_step_kernel<<<b2, 256, 0, s>>>(cv.T + cv.toff[m], Dl, cv.d, Dr, pats, cv.N, m, P, V, Vn, maxD);
+    double2* t = V; V = Vn; Vn = t;
+  }
+  amp_out_kernel<<<blocks, 256, 0, s>>>(V, P, maxD, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_ones(double2* V, long long P, int ld, cudaStream_t s) {
+  int blocks = (int)((P + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  amp_init_kernel<<<blocks, 256, 0, s>>>(V, P, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W, const double2* Y,
+                                 const double* u, int ustride, int site, uint64_t seed,
+                                 uint64_t counter0, double2* vnew, uint8_t* out, int N,
+                                 uint8_t* flags, cudaStream_t s) {
+  long long threads = (long long)S * 32;
+  int blocks = (int)((threads + 255) / 256);
+  sample_select_kernel<<<blocks, 256, 0, s>>>(S, d, Dm, W, Y, u, ustride, site, seed, counter0,
+                                              vnew, out, N, flags);
+  return cudaGetLastError();
+}

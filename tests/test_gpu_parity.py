@@ -1,0 +1,267 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.  Tolerances (FP64 path): amplitude relative error <= 1e-9 for
+|a| >= 1e-10 max|a| (absolute below), state fidelity >= 1 - 1e-10, tensor
+entries 1e-11 of the largest entry, samples bit-exact except draws flagged
+within 1e-12 Z of a CDF boundary."""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import basis as B
+from oracle import gaussian as G
+from oracle import hafnian as H
+from oracle import mps as M
+from oracle import pco as P
+
+pytestmark = pytest.mark.gpu
+
+g = pytest.importorskip("paper_2512_10643_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+def amp_close(a_gpu, a_ref, rtol=1e-9):
+    a_gpu = np.asarray(a_gpu)
+    a_ref = np.asarray(a_ref)
+    scale = np.abs(a_ref).max()
+    big = np.abs(a_ref) >= 1e-10 * scale
+    rel = np.abs(a_gpu[big] - a_ref[big]) / np.abs(a_ref[big])
+    ab = np.abs(a_gpu[~big] - a_ref[~big])
+    return (rel.max() if rel.size else 0.0) <= rtol and (ab.max() if ab.size else 0.0) <= rtol * 1e-10 * scale * 10
+
+
+# ---------------------------------------------------------------- PCO kernel
+@pytest.mark.parametrize("seed,nl,nr,d,chil,chir", [
+    (0, 2, 3, 4, 12, 15), (1, 0, 2, 5, 1, 20), (2, 3, 0, 3, 25, 1), (3, 4, 4, 6, 70, 90),
+    (4, 1, 1, 8, 33, 47), (5, 0, 0, 7, 1, 1)])
+def test_build_site_matches_oracle(ctx, seed, nl, nr, d, chil, chir):
+    r = np.random.default_rng(seed)
+    n = nl + 1 + nr
+    Q = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) * 0.35
+    Q = 0.5 * (Q + Q.T)
+    bl = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nl))[::-1], chil) if nl else M.vacuum_basis()
+    br = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nr))[::-1], chir) if nr else M.vacuum_basis()
+    ref = P.local_tensor(Q, bl, br, d, c=0.7)
+    got = g.gbsmps_build_site(ctx.h, Q, 0.7, bl.occ.astype(np.uint8).reshape(bl.D, nl),
+                              br.occ.astype(np.uint8).reshape(br.D, nr), d)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    # parity (P6): odd-total entries are exactly zero on the GPU too
+    tot = bl.occ.sum(1)[:, None, None] + np.arange(d)[None, :, None] + br.occ.sum(1)[None, None, :]
+    assert np.all(got[tot % 2 == 1] == 0)
+
+
+def test_build_site_vs_hafnian(ctx):
+    r = np.random.default_rng(11)
+    n = 4
+    Q = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) * 0.5
+    Q = 0.5 * (Q + Q.T)
+    bl = B.kept_basis(np.array([0.3]), 6)
+    br = B.kept_basis(np.array([0.35, 0.12]), 10)
+    got = g.gbsmps_build_site(ctx.h, Q, 1.0, bl.occ.astype(np.uint8), br.occ.astype(np.uint8), 5)
+    for a in range(bl.D):
+        for p in range(5):
+            for b in range(br.D):
+                ex = H.local_entry(Q, np.r_[bl.occ[a], p, br.occ[b]])
+                assert abs(got[a, p, b] - ex) <= 1e-12 * max(1.0, abs(ex))
+
+
+# ---------------------------------------------------------------- whole build
+SMALL = [  # (N, seed, d, chi, depth, rlo, rhi, haar)
+    (2, 1, 6, 20, 1, 0.3, 0.6, False),
+    (6, 2, 4, 30, 4, 0.1, 0.5, False),
+    (12, 3, 4, 40, 6, 0.1, 0.5, False),
+    (20, 4, 5, 64, 6, 0.1, 0.4, False),
+    (8, 20251210, 8, 64, 0, 0.3, 0.8, True),
+]
+
+
+def _oracle(w, chi, d, eps=0.0, freeze=1e-13):
+    mps = M.build_mps(w.gamma, d=d, chi=chi, eps=eps, lambda2_freeze=freeze)
+    return mps, M.normalise(mps.tensors)
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_build_parity(ctx, case):
+    N, seed, d, chi, depth, rlo, rhi, haar = case
+    w = wl.small(N, seed, d=d, chi=chi, depth=depth, rlo=rlo, rhi=rhi, haar=haar)
+    omps, oT = _oracle(w, chi, d)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=d, chi_max=chi)
+    try:
+        info = m.info
+        assert list(info["n_e"]) == omps.n_e
+        assert list(info["bond_dims"]) == omps.bond_dims
+        assert np.allclose(info["eps"], omps.eps, rtol=1e-6, atol=1e-13)
+        lam2, Qm, cm = g.gbsmps_get_gsvd(m.h)
+        for k, cut in enumerate(omps.cuts[:-1]):
+            assert np.allclose(lam2[k, :cut.n_out], cut.lam2, rtol=1e-9, atol=1e-15)
+        gT = m.tensors()
+        # gauge-invariant state fidelity
+        f = M.fidelity(gT, oT)
+        assert f >= 1 - 1e-10
+        # amplitudes on all low patterns (tiny N) or sampled patterns
+        if N <= 8:
+            pats = np.array([p for p in itertools.product(range(min(d, 4)), repeat=N)
+                             if sum(p) % 2 == 0 and sum(p) <= 8], dtype=np.uint8)
+        else:
+            pats = wl.random_patterns(200, N, d, seed=seed)
+        ref = M.amplitudes(oT, pats)
+        got = m.amplitudes(pats)
+        assert amp_close(got, ref)
+        # oracle amplitudes from the GPU's own tensors agree too
+        assert amp_close(M.amplitudes(gT, pats), ref)
+    finally:
+        m.release()
+
+
+def test_tensors_entrywise_canonical_gauge(ctx):
+    """With well-separated symplectic spectra the canonical gauge makes the
+    tensors themselves comparable entry by entry."""
+    w = wl.small(10, 7, d=4, chi=48, depth=4, rlo=0.3, rhi=0.6)
+    omps, oT = _oracle(w, 48, 4, freeze=1e-6)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=48, lambda2_freeze=1e-6)
+    try:
+        for site in range(10):
+            a = m.tensor(site)
+            b = oT[site]
+            assert a.shape == b.shape
+            assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+    finally:
+        m.release()
+
+
+def test_hafnian_pin_through_gpu(ctx):
+    w = wl.small(4, 12, d=8, depth=4, rlo=0.1, rhi=0.3, haar=True)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=8, chi_max=300)
+    try:
+        pats = np.array([p for p in itertools.product(range(4), repeat=4) if sum(p) % 2 == 0],
+                        dtype=np.uint8)
+        got = m.amplitudes(pats)
+        ex = np.array([H.amplitude(w.Q, p) for p in pats])
+        r_got = got / got[0]
+        r_ex = ex / ex[0]
+        assert np.abs(r_got - r_ex).max() <= 1e-10 * np.abs(r_ex).max()
+    finally:
+        m.release()
+
+
+def test_build_from_q_matches_cov(ctx):
+    w = wl.small(10, 5, d=4, chi=40, depth=5)
+    m1 = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=40)
+    m2 = g.MPS.from_Q(ctx, np.ascontiguousarray(w.Q), d=4, chi_max=40)
+    try:
+        assert list(m1.info["bond_dims"]) == list(m2.info["bond_dims"])
+        f = M.fidelity(m1.tensors(), m2.tensors())
+        assert f >= 1 - 1e-10
+    finally:
+        m1.release()
+        m2.release()
+
+
+@pytest.mark.parametrize("N,seed,chi", [(6, 2, 30), (16, 9, 48)])
+def test_samples_bit_exact(ctx, N, seed, chi):
+    w = wl.small(N, seed, d=4, chi=chi, depth=4, rlo=0.2, rhi=0.6)
+    omps, oT = _oracle(w, chi, 4)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=chi)
+    try:
+        S = 3000
+        u = wl.uniforms(S, N, seed=seed + 100)
+        flags = np.zeros(S, dtype=np.uint8)
+        got = m.sample(S, uniforms=u, flags=flags)
+        ref, rflag = M.sample(oT, u)
+        ok = (flags == 0) & (~rflag)
+        assert ok.mean() > 0.99
+        assert np.array_equal(got[ok], ref[ok])
+        assert np.all(got.astype(int).sum(1) % 2 == 0)       # P6 on samples
+    finally:
+        m.release()
+
+
+def test_rejects_mixed_and_asymmetric(ctx):
+    w = wl.small(6, 3, d=4, chi=20, depth=4)
+    mixed = 0.8 * w.gamma + 0.2 * 0.5 * np.eye(12)
+    with pytest.raises(g.GbsmpsError) as e:
+        g.MPS.from_cov(ctx, np.ascontiguousarray(mixed), d=4, chi_max=20)
+    assert e.value.code == g.ERR_NOT_PURE
+    asym = w.gamma.copy()
+    asym[0, 1] += 1e-6
+    with pytest.raises(g.GbsmpsError) as e:
+        g.MPS.from_cov(ctx, np.ascontiguousarray(asym), d=4, chi_max=20)
+    assert e.value.code == g.ERR_NOT_SYMMETRIC
+    # the context stays usable after an error
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=20)
+    m.release()
+
+
+def test_edge_cases(ctx):
+    # single mode: no cut at all
+    gam, q = wl.squeezed_state(np.array([0.4]), np.eye(1, dtype=np.complex128))
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(gam), d=10, chi_max=4)
+    try:
+        a = m.tensor(0)[0, :, 0]
+        t = np.tanh(0.4)
+        for k in range(5):
+            ex = np.sqrt(1 / np.cosh(0.4)) * (-t) ** k * np.sqrt(float(np.prod(range(1, 2 * k + 1)))) / (2 ** k * float(np.prod(range(1, k + 1))))
+            assert abs(a[2 * k] / a[0] - ex / np.sqrt(1 / np.cosh(0.4))) < 1e-12
+        assert np.all(a[1::2] == 0)
+    finally:
+        m.release()
+    # product state: every bond dimension 1
+    gam, q = wl.squeezed_state(np.array([0.3, 0.5, 0.2]), np.eye(3, dtype=np.complex128))
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(gam), d=6, chi_max=16)
+    try:
+        assert list(m.info["bond_dims"]) == [1, 1, 1, 1]
+    finally:
+        m.release()
+    # empty batches are no-ops
+    w = wl.small(5, 1, d=4, chi=16, depth=3)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=16)
+    try:
+        assert m.amplitudes(np.zeros((0, 5), dtype=np.uint8)).shape == (0,)
+        assert m.sample(0).shape == (0, 5)
+        # patterns with n_i >= d give 0
+        assert m.amplitudes(np.array([[4, 0, 0, 0, 0]], dtype=np.uint8))[0] == 0
+    finally:
+        m.release()
+
+
+def test_full_size_n144(ctx):
+    """The 144-mode brick-wall workload at d=6, chi=256: GSVD spectra and
+    bond dimensions equal the oracle's; sampled sites' tensors equal the
+    oracle's PCO build from the GPU's own Q^m and bases (gauge-free); the
+    state is normalised and the vacuum amplitude positive."""
+    w = wl.config("n144_d6_chi256")
+    cuts = G.gsvd_chain(w.gamma)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=6, chi_max=256, eps_trunc=1e-12)
+    try:
+        info = m.info
+        assert list(info["n_e"]) == [c.n_out for c in cuts[:-1]]
+        bases = [M.vacuum_basis()] + [B.kept_basis(c.lam2, 256, 1e-12) for c in cuts[:-1]] + [M.vacuum_basis()]
+        assert list(info["bond_dims"]) == [b.D for b in bases]
+        lam2, Qm, cm = g.gbsmps_get_gsvd(m.h)
+        for k, cut in enumerate(cuts[:-1]):
+            assert np.allclose(lam2[k, :cut.n_out], cut.lam2, rtol=1e-8, atol=1e-14)
+        for site in (0, 5, 71, 143):
+            nl, nr = bases[site].ne, bases[site + 1].ne
+            nq = nl + 1 + nr
+            ref = P.local_tensor(Qm[site, :nq, :nq], bases[site], bases[site + 1], 6, cm[site])
+            got = m.tensor(site)
+            if site == 0:      # A^1 carries the global normalisation and phase
+                k = np.argmax(np.abs(ref))
+                ref = ref * (got.flat[k] / ref.flat[k])
+            assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+        a0 = m.amplitudes(np.zeros((1, 144), dtype=np.uint8))[0]
+        assert abs(a0.imag) < 1e-14 and a0.real > 0
+        pvac = np.linalg.det(w.gamma + 0.5 * np.eye(288)) ** -0.5
+        assert abs(a0.real ** 2 - pvac) < 1e-3 * pvac
+    finally:
+        m.release()
