@@ -29,6 +29,36 @@ int fail(int code, const std::string& what) {
     }                                                                              \
   } while (0)
 
+// Opt-in stage tracing: with GBSMPS_PROFILE=1 every pipeline records CUDA
+// events between its stages and prints the elapsed times to stderr.
+struct StageTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<std::string, cudaEvent_t>> ev;
+  explicit StageTimer(cudaStream_t st) : s(st) {
+    const char* e = getenv("GBSMPS_PROFILE");
+    on = e && e[0] == '1';
+    mark("start");
+  }
+  void mark(const char* name) {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.emplace_back(name, e);
+  }
+  ~StageTimer() {
+    if (!on) return;
+    cudaEventSynchronize(ev.back().second);
+    for (size_t i = 1; i < ev.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
+      fprintf(stderr, "[gbsmps] %-14s %9.3f ms\n", ev[i].first.c_str(), ms);
+    }
+    for (auto& p : ev) cudaEventDestroy(p.second);
+  }
+};
+
 int status_to_code(int st) {
   if (st & ST_NOT_SYMMETRIC) return GBSMPS_ERR_NOT_SYMMETRIC;
   if (st & ST_NOT_PURE) return GBSMPS_ERR_NOT_PURE;
@@ -107,6 +137,7 @@ int check_opts(const gbsmps_opts* o) {
 int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                gbsmps_mps_t* out) {
   cudaStream_t s = c->stream;
+  StageTimer tm(s);
   auto* M = new gbsmps_mps();
   std::unique_ptr<gbsmps_mps> guard(M);
   M->ctx = c; M->N = N; M->d = o->d; M->chi = o->chi_max; M->precision = o->precision;
@@ -156,14 +187,18 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     CK(launch_check_input(dgamma, N, o->purity_tol, work, c->d_status, s));
     COUNT_LAUNCH(2);
   }
+  tm.mark("validate");
   CK(launch_bandwidth(dgamma, N, dbw, s));
   COUNT_LAUNCH(1);
   CK(launch_gsvd_chain(dgamma, N, dbw, o->lambda2_freeze, Gs, ba, M->Qm, M->cm, c->d_status, s));
   COUNT_LAUNCH(1);
+  tm.mark("gsvd_chain");
   // ---- a4-a5 kept bases and index maps --------------------------------------
   CK(launch_basis(ba, nb, o->chi_max, o->eps_trunc, c->d_status, s));
+  tm.mark("basis");
   CK(launch_maps(ba, nb, c->d_status, s));
   COUNT_LAUNCH(2);
+  tm.mark("maps");
   M->D.assign(nb, 1);
   M->ne.assign(nb, 0);
   std::vector<double> epsb(nb, 0.0);
@@ -221,6 +256,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   }
   scr.release();
   tk.release();
+  tm.mark("pco");
   // ---- a7 right environments and normalisation ------------------------------
   double2* R = M->env.as<double2>();
   double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
@@ -240,6 +276,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                     R + M->eoff[m], Dl, 0, 1, s));
     COUNT_LAUNCH(2);
   }
+  tm.mark("environments");
   // vacuum amplitude, then A^1 *= conj(phase)/sqrt(norm^2)
   DevBuf ab;
   CK(ab.alloc(sizeof(double2) * (2 * (size_t)M->maxD + 8) + N, s));
@@ -258,6 +295,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   CK(cudaMemcpyAsync(R + M->eoff[0], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
   xb.release();
   ab.release();
+  tm.mark("normalise");
   rc = sync_status(c);
   if (rc) return rc;
   *out = guard.release();
@@ -447,6 +485,7 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   if (dfl) CK(cudaMemsetAsync(dfl, 0, (size_t)S, s));
   const double2* R = m->env.as<double2>();
   const double2 one = cmk(1, 0), zero = cmk(0, 0);
+  StageTimer tm(s);
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
     double2* V = vb.as<double2>();
@@ -469,6 +508,7 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
       std::swap(V, Vn);
     }
   }
+  tm.mark("sample");
   if (mem_kind == GBSMPS_MEM_HOST) {
     CK(cudaMemcpyAsync(out, dout, (size_t)S * N, cudaMemcpyDeviceToHost, s));
     if (flags) CK(cudaMemcpyAsync(flags, dfl, (size_t)S, cudaMemcpyDeviceToHost, s));
