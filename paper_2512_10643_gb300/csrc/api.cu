@@ -99,12 +99,13 @@ struct gbsmps_mps {
   std::vector<long long> toff, eoff;
   int maxD = 1;
   DevBuf tensors, env, gsvd, bonds;
+  DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
   BondArrays ba{};
   double* lam2 = nullptr;
   double2* Qm = nullptr;
   double* cm = nullptr;
   ~gbsmps_mps() {
-    tensors.release(); env.release(); gsvd.release(); bonds.release();
+    tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
   }
 };
 
@@ -267,14 +268,37 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   CK(xb.alloc(sizeof(double2) * (xmax + 8), s));
   double2* X = xb.as<double2>();
   const int d = o->d;
-  for (int m = N - 1; m >= 0; --m) {
-    int Dl = M->D[m], Dr = M->D[m + 1];
-    const double2* A = M->tensors.as<double2>() + M->toff[m];
-    CK(launch_zgemm('N', 'N', Dl * d, Dr, Dr, one, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, zero, X,
-                    Dr, 0, 1, s));
-    CK(launch_zgemm('N', 'C', Dl, Dl, d * Dr, one, X, d * Dr, 0, A, d * Dr, 0, zero,
-                    R + M->eoff[m], Dl, 0, 1, s));
-    COUNT_LAUNCH(2);
+  const bool mixed = o->precision == GBSMPS_PREC_MIXED;
+  if (mixed) {
+    // energy gauge (float2 tensors) and split-BF16 tensor-core environments
+    CK(M->tens_mixed.alloc(sizeof(float2) * tot, s));
+    float2* Ah = M->tens_mixed.as<float2>();
+    for (int m = 0; m < N; ++m) {
+      CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
+                             ba.E + (size_t)m * cap, ba.E + (size_t)(m + 1) * cap,
+                             Ah + M->toff[m], s));
+      COUNT_LAUNCH(1);
+    }
+    tm.mark("energy_gauge");
+    float2* Xf = reinterpret_cast<float2*>(X);
+    for (int m = N - 1; m >= 0; --m) {
+      int Dl = M->D[m], Dr = M->D[m + 1];
+      const float2* A = Ah + M->toff[m];
+      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, A, 0, Dr, 0, R + M->eoff[m + 1], 1, Dr, 0,
+                         Xf, 0, Dr, 0, 1, s));
+      CK(launch_zgemm_tc(6, 'N', 'C', Dl, Dl, d * Dr, Xf, 0, d * Dr, 0, A, 0, d * Dr, 0,
+                         R + M->eoff[m], 1, Dl, 0, 1, s));
+    }
+  } else {
+    for (int m = N - 1; m >= 0; --m) {
+      int Dl = M->D[m], Dr = M->D[m + 1];
+      const double2* A = M->tensors.as<double2>() + M->toff[m];
+      CK(launch_zgemm('N', 'N', Dl * d, Dr, Dr, one, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, zero, X,
+                      Dr, 0, 1, s));
+      CK(launch_zgemm('N', 'C', Dl, Dl, d * Dr, one, X, d * Dr, 0, A, d * Dr, 0, zero,
+                      R + M->eoff[m], Dl, 0, 1, s));
+      COUNT_LAUNCH(2);
+    }
   }
   tm.mark("environments");
   // vacuum amplitude, then A^1 *= conj(phase)/sqrt(norm^2)
@@ -291,6 +315,11 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   CK(launch_norm_phase(R + M->eoff[0], amp0, fac, c->d_status, s));
   CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
   COUNT_LAUNCH(2);
+  if (mixed) {   // the normalised first tensor in the energy gauge (D_0 = 1)
+    CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], ba.E, ba.E + cap,
+                           M->tens_mixed.as<float2>(), s));
+    COUNT_LAUNCH(1);
+  }
   // R_0 of the normalised state is 1
   CK(cudaMemcpyAsync(R + M->eoff[0], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
   xb.release();
@@ -488,6 +517,29 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   StageTimer tm(s);
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
+    if (m->precision == GBSMPS_PREC_MIXED) {
+      // split-BF16 tensor-core GEMMs on the energy-gauge tensors, FP32 state
+      float2* V = vb.as<float2>();
+      float2* Vn = V + (size_t)chunk * m->maxD;
+      CK(launch_init_ones_f(V, cs, s));
+      COUNT_LAUNCH(1);
+      for (int site = 0; site < N; ++site) {
+        const int Dl = m->D[site], Dr = m->D[site + 1];
+        const float2* A = m->tens_mixed.as<float2>() + m->toff[site];
+        float2* W = wb.as<float2>();
+        float2* Y = yb.as<float2>();
+        CK(launch_zgemm_tc(6, 'N', 'N', cs, d * Dr, Dl, V, 0, Dl, 0, A, 0, d * Dr, 0, W, 0, d * Dr,
+                           0, 1, s));
+        CK(launch_zgemm_tc(6, 'N', 'N', cs * d, Dr, Dr, W, 0, Dr, 0, R + m->eoff[site + 1], 1, Dr,
+                           0, Y, 0, Dr, 0, 1, s));
+        CK(launch_sample_select_mixed(cs, d, Dr, W, Y, du ? du + (size_t)s0 * N : nullptr, N, site,
+                                      seed, counter0 + (uint64_t)s0, Vn, dout + (size_t)s0 * N, N,
+                                      dfl ? dfl + s0 : nullptr, 1e-5, s));
+        COUNT_LAUNCH(1);
+        std::swap(V, Vn);
+      }
+      continue;
+    }
     double2* V = vb.as<double2>();
     double2* Vn = V + (size_t)chunk * m->maxD;
     // v = [1] for every sample (D_0 = 1)

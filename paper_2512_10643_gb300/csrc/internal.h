@@ -35,6 +35,29 @@ __host__ __device__ inline void cfma(double2& a, double2 b, double2 c) {
   a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
 }
 
+// float2 versions (FP32 arithmetic of the mixed-precision path)
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ inline void cfma(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+
+// complex type of a real type
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+template <typename C2> __host__ __device__ inline C2 to_c(double2 v);
+template <> __host__ __device__ inline double2 to_c<double2>(double2 v) { return v; }
+template <> __host__ __device__ inline float2 to_c<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__host__ __device__ inline double2 to_d(double2 v) { return v; }
+__host__ __device__ inline double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+
 __device__ inline void set_status(int* st, int bit) { atomicOr(st, bit); }
 
 // ---- per-bond basis storage ----------------------------------------------
@@ -105,6 +128,20 @@ struct ChainView {       // view of an MPS for the amplitude kernels
 cudaError_t launch_amplitudes(ChainView cv, long long P, const uint8_t* pats,
                               double2* out, double2* work, int maxD, cudaStream_t s);
 cudaError_t launch_init_ones(double2* V, long long P, int ld, cudaStream_t s);
+cudaError_t launch_init_ones_f(float2* V, long long P, cudaStream_t s);
+cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, const float2* Y,
+                                       const double* u, int ustride, int site, uint64_t seed,
+                                       uint64_t counter0, float2* vnew, uint8_t* out, int N,
+                                       uint8_t* flags, double flag_tol, cudaStream_t s);
+cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
+                                const double* Er, float2* Ah, cudaStream_t s);
+// split-BF16 tensor-core complex GEMM (nterms 3 or 6), operands FP64 or FP32
+// complex (a64/b64/c64 flags), op 'N' or 'C'; counts its own launch
+cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
+                            const void* A, int a64, long long lda, long long sA,
+                            const void* B, int b64, long long ldb, long long sB,
+                            void* C, int c64, long long ldc, long long sC, int batch,
+                            cudaStream_t s);
 cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W,
                                  const double2* Y, const double* u, int ustride,
                                  int site, uint64_t seed, uint64_t counter0,

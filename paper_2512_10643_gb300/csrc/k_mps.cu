@@ -125,6 +125,11 @@ __global__ void amp_init_kernel(double2* V, long long P, int ld) {
     V[s * ld] = cmk(1.0, 0.0);
 }
 
+__global__ void init_ones_f_kernel(float2* V, long long P) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < P; s += (long long)gridDim.x * blockDim.x)
+    V[s] = make_float2(1.f, 0.f);
+}
+
 __global__ void amp_out_kernel(const double2* V, long long P, int ld, double2* out) {
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < P; s += (long long)gridDim.x * blockDim.x)
     out[s] = V[s * ld];
@@ -150,30 +155,34 @@ __device__ inline double philox_uniform(uint64_t seed, uint64_t sample, uint32_t
   return (double)(a * 67108864ull + b) * (1.0 / 9007199254740992.0);
 }
 
-// one warp per sample
-__global__ void sample_select_kernel(int S, int d, int Dm, const double2* __restrict__ W,
-                                     const double2* __restrict__ Y, const double* __restrict__ u,
+// one warp per sample; C2 = double2 (FP64 path) or float2 (mixed path),
+// probabilities accumulated in FP64 either way
+template <typename C2>
+__global__ void sample_select_kernel(int S, int d, int Dm, const C2* __restrict__ W,
+                                     const C2* __restrict__ Y, const double* __restrict__ u,
                                      int ustride, int site, uint64_t seed, uint64_t counter0,
-                                     double2* __restrict__ vnew, uint8_t* __restrict__ out,
-                                     int N, uint8_t* flags) {
+                                     C2* __restrict__ vnew, uint8_t* __restrict__ out,
+                                     int N, uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
   const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (s >= S) return;
-  const double2* w = W + (size_t)s * d * Dm;
-  const double2* y = Y + (size_t)s * d * Dm;
-  double Z = 0.0;
-  // pass 1: total
-  double qs[8];
-  for (int p = 0; p < d; ++p) {
+  const C2* w = W + (size_t)s * d * Dm;
+  const C2* y = Y + (size_t)s * d * Dm;
+  auto qof = [&](int p) {
     double part = 0.0;
     for (int b = lane; b < Dm; b += 32) {
-      double2 yy = y[(size_t)p * Dm + b], ww = w[(size_t)p * Dm + b];
+      double2 yy = to_d(y[(size_t)p * Dm + b]), ww = to_d(w[(size_t)p * Dm + b]);
       part += yy.x * ww.x + yy.y * ww.y;
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    part = fmax(part, 0.0);
-    if (p < 8) qs[p] = part;
-    Z += part;
+    return fmax(part, 0.0);
+  };
+  double Z = 0.0;
+  double qs[8];
+  for (int p = 0; p < d; ++p) {
+    double q = qof(p);
+    if (p < 8) qs[p] = q;
+    Z += q;
   }
   double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
   const double t = uu * Z;
@@ -181,35 +190,18 @@ __global__ void sample_select_kernel(int S, int d, int Dm, const double2* __rest
   double C = 0.0, qsel = 0.0;
   bool flag = false;
   for (int p = 0; p < d; ++p) {
-    double q;
-    if (p < 8) q = qs[p];
-    else {
-      double part = 0.0;
-      for (int b = lane; b < Dm; b += 32) {
-        double2 yy = y[(size_t)p * Dm + b], ww = w[(size_t)p * Dm + b];
-        part += yy.x * ww.x + yy.y * ww.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      q = fmax(part, 0.0);
-    }
+    double q = p < 8 ? qs[p] : qof(p);
     C += q;
-    if (fabs(t - C) <= 1e-12 * Z) flag = true;
-    if (q > 0.0) { plast = p; }
+    if (fabs(t - C) <= flag_tol * Z) flag = true;
+    if (q > 0.0) plast = p;
     if (pstar < 0 && t < C) { pstar = p; qsel = q; }
   }
-  if (pstar < 0) {
-    pstar = plast;
-    // recompute q of the fallback
-    double part = 0.0;
-    for (int b = lane; b < Dm; b += 32) {
-      double2 yy = y[(size_t)pstar * Dm + b], ww = w[(size_t)pstar * Dm + b];
-      part += yy.x * ww.x + yy.y * ww.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    qsel = fmax(part, 0.0);
-  }
+  if (pstar < 0) { pstar = plast; qsel = qof(pstar); }
   const double inv = qsel > 0.0 ? 1.0 / sqrt(qsel) : 0.0;
-  for (int b = lane; b < Dm; b += 32) vnew[(size_t)s * Dm + b] = cscale(w[(size_t)pstar * Dm + b], inv);
+  for (int b = lane; b < Dm; b += 32) {
+    double2 v = to_d(w[(size_t)pstar * Dm + b]);
+    vnew[(size_t)s * Dm + b] = to_c<C2>(cscale(v, inv));
+  }
   if (lane == 0) {
     out[(size_t)s * N + site] = (uint8_t)pstar;
     if (flags && flag) flags[s] = 1;
@@ -276,7 +268,26 @@ cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W, const d
                                  uint8_t* flags, cudaStream_t s) {
   long long threads = (long long)S * 32;
   int blocks = (int)((threads + 255) / 256);
-  sample_select_kernel<<<blocks, 256, 0, s>>>(S, d, Dm, W, Y, u, ustride, site, seed, counter0,
-                                              vnew, out, N, flags);
+  sample_select_kernel<double2><<<blocks, 256, 0, s>>>(S, d, Dm, W, Y, u, ustride, site, seed,
+                                                       counter0, vnew, out, N, flags, 1e-12);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, const float2* Y,
+                                       const double* u, int ustride, int site, uint64_t seed,
+                                       uint64_t counter0, float2* vnew, uint8_t* out, int N,
+                                       uint8_t* flags, double flag_tol, cudaStream_t s) {
+  long long threads = (long long)S * 32;
+  int blocks = (int)((threads + 255) / 256);
+  sample_select_kernel<float2><<<blocks, 256, 0, s>>>(S, d, Dm, W, Y, u, ustride, site, seed,
+                                                      counter0, vnew, out, N, flags, flag_tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_ones_f(float2* V, long long P, cudaStream_t s) {
+  int blocks = (int)((P + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  init_ones_f_kernel<<<blocks, 256, 0, s>>>(V, P);
   return cudaGetLastError();
 }

@@ -19,6 +19,8 @@
 // of low_q and low_q'; coefficients g^kappa/kappa! sqrt(n!/(n-kappa)!) are
 // built as running products.  Each pass is out of place (double buffered);
 // the paper's in-place reverse-ordered loop computes the same numbers.
+// T = double is the FP64 path; T = float runs the same passes in FP32 (the
+// mixed-precision build) and accumulates the output tensor in FP64.
 #include "internal.h"
 #include <math.h>
 
@@ -36,9 +38,11 @@ struct PcoSmem {
 
 __device__ inline int occ_of(const uint8_t* occ, int idx, int q) { return occ[(size_t)idx * NEM + q]; }
 
+template <typename T>
 __global__ void __launch_bounds__(PCO_THREADS)
-pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scratch,
+pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scratch_base,
            int* status) {
+  using C2 = typename Cx<T>::type;
   __shared__ PcoSmem sm;
   const SiteTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -57,12 +61,14 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
   for (int q = tid; q < nr; q += nt) if (sm.mor[q] >= SQ_N - 4) set_status(status, ST_BOUNDS);
 
   const size_t DD = (size_t)Dl * Dr;
-  double2* base = scratch + t.scratch_off;
-  double2* u = base;
-  double2* u2 = u + Dl;
-  double2* w = u2 + Dl;
-  double2* w2 = w + Dr;
-  double2* Bf[4] = {w2 + Dr, w2 + Dr + DD, w2 + Dr + 2 * DD, w2 + Dr + 3 * DD};
+  C2* base = reinterpret_cast<C2*>(scratch_base + t.scratch_off);
+  C2* u = base;
+  C2* u2 = u + Dl;
+  C2* w = u2 + Dl;
+  C2* w2 = w + Dr;
+  C2* Bf[4] = {w2 + Dr, w2 + Dr + DD, w2 + Dr + 2 * DD, w2 + Dr + 3 * DD};
+  const C2 zero = to_c<C2>(cmk(0.0, 0.0));
+  const C2 one = to_c<C2>(cmk(1.0, 0.0));
 
   // ---- 1. one-sided PCOs on vectors --------------------------------------
   for (int side = 0; side < 2; ++side) {
@@ -73,19 +79,19 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
     const int cap = side == 0 ? t.capl : t.capr;
     const int* mo = side == 0 ? sm.mol : sm.mor;
     const int off = side == 0 ? 0 : nl + 1;
-    double2* x = side == 0 ? u : w;
-    double2* y = side == 0 ? u2 : w2;
-    for (int i = tid; i < D; i += nt) x[i] = cmk(i == 0 ? 1.0 : 0.0, 0.0);
+    C2* x = side == 0 ? u : w;
+    C2* y = side == 0 ? u2 : w2;
+    for (int i = tid; i < D; i += nt) x[i] = i == 0 ? one : zero;
     __syncthreads();
     for (int q = 0; q < n; ++q) {
       for (int q2 = q; q2 < n; ++q2) {
         if (q == q2 ? mo[q] < 2 : (mo[q] == 0 || mo[q2] == 0)) continue;
-        const double2 g = sm.Q[(off + q) * QS + off + q2];
+        const C2 g = to_c<C2>(sm.Q[(off + q) * QS + off + q2]);
         const int* lq = low + (size_t)q * cap;
         const int* lq2 = low + (size_t)q2 * cap;
         for (int mu = tid; mu < D; mu += nt) {
-          double2 acc = x[mu];
-          double2 tk = cmk(1.0, 0.0);
+          C2 acc = x[mu];
+          C2 tk = one;
           int s = mu;
           const int a = occ_of(occ, mu, q);
           if (q != q2) {
@@ -93,28 +99,28 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
             const int kmax = min(a, b);
             for (int k = 1; k <= kmax; ++k) {
               s = lq2[lq[s]];
-              tk = cscale(cmul(tk, g), sm.sq[a - k + 1] * sm.sq[b - k + 1] / k);
+              tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] / k));
               cfma(acc, tk, x[s]);
             }
           } else {
-            const double2 gh = cscale(g, 0.5);
+            const C2 gh = cscale(g, (T)0.5);
             for (int j = 1; 2 * j <= a; ++j) {
               s = lq[lq[s]];
-              tk = cscale(cmul(tk, gh), sm.sq[a - 2 * j + 2] * sm.sq[a - 2 * j + 1] / j);
+              tk = cscale(cmul(tk, gh), (T)(sm.sq[a - 2 * j + 2] * sm.sq[a - 2 * j + 1] / j));
               cfma(acc, tk, x[s]);
             }
           }
           y[mu] = acc;
         }
         __syncthreads();
-        double2* tt = x; x = y; y = tt;
+        C2* tt = x; x = y; y = tt;
       }
     }
     if (side == 0) { u = x; u2 = y; } else { w = x; w2 = y; }
   }
   // ---- C0 = u w^T ----------------------------------------------------------
-  double2* cur = Bf[0];
-  double2* nxt = Bf[1];
+  C2* cur = Bf[0];
+  C2* nxt = Bf[1];
   for (size_t idx = tid; idx < DD; idx += nt) cur[idx] = cmul(u[idx / Dr], w[idx % Dr]);
   __syncthreads();
   // ---- 2. cross PCOs -------------------------------------------------------
@@ -123,54 +129,54 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
     const int* lq = t.lowl + (size_t)q * t.capl;
     for (int q2 = 0; q2 < nr; ++q2) {
       if (sm.mor[q2] == 0) continue;
-      const double2 g = sm.Q[q * QS + nl + 1 + q2];
+      const C2 g = to_c<C2>(sm.Q[q * QS + nl + 1 + q2]);
       const int* lr = t.lowr + (size_t)q2 * t.capr;
       for (size_t idx = tid; idx < DD; idx += nt) {
         const int mu = idx / Dr, nu = idx % Dr;
         const int a = occ_of(t.occl, mu, q), b = occ_of(t.occr, nu, q2);
         const int kmax = min(a, b);
-        double2 acc = cur[idx];
-        double2 tk = cmk(1.0, 0.0);
+        C2 acc = cur[idx];
+        C2 tk = one;
         int s = mu, r = nu;
         for (int k = 1; k <= kmax; ++k) {
           s = lq[s];
           r = lr[r];
-          tk = cscale(cmul(tk, g), sm.sq[a - k + 1] * sm.sq[b - k + 1] / k);
+          tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] / k));
           cfma(acc, tk, cur[(size_t)s * Dr + r]);
         }
         nxt[idx] = acc;
       }
       __syncthreads();
-      double2* tt = cur; cur = nxt; nxt = tt;
+      C2* tt = cur; cur = nxt; nxt = tt;
     }
   }
   // ---- 3. physical PCOs: A[., p, .] ----------------------------------------
   double2* A = t.out;
   for (size_t idx = tid; idx < DD * d; idx += nt) A[idx] = cmk(0.0, 0.0);
   const double2 gaa2 = cscale(sm.Q[ia * QS + ia], 0.5);
-  double2* P = cur;              // l_L^i C0
-  double2* Pn = nxt;
-  double2* Ya = Bf[2];
-  double2* Yb = Bf[3];
+  C2* P = cur;              // l_L^i C0
+  C2* Pn = nxt;
+  C2* Ya = Bf[2];
+  C2* Yb = Bf[3];
   for (int i = 0; i < d; ++i) {
     if (i > 0) {
       if (nl == 0) break;
       __syncthreads();
       for (size_t idx = tid; idx < DD; idx += nt) {
         const int mu = idx / Dr, nu = idx % Dr;
-        double2 acc = cmk(0.0, 0.0);
+        C2 acc = zero;
         for (int q = 0; q < nl; ++q) {
           const int a = occ_of(t.occl, mu, q);
           if (a == 0) continue;
           const int s = t.lowl[(size_t)q * t.capl + mu];
-          cfma(acc, cscale(sm.Q[q * QS + ia], sm.sq[a]), P[(size_t)s * Dr + nu]);
+          cfma(acc, to_c<C2>(cscale(sm.Q[q * QS + ia], sm.sq[a])), P[(size_t)s * Dr + nu]);
         }
         Pn[idx] = acc;
       }
       __syncthreads();
-      double2* tt = P; P = Pn; Pn = tt;
+      C2* tt = P; P = Pn; Pn = tt;
     }
-    const double2* Ysrc = P;
+    const C2* Ysrc = P;
     for (int j = 0; i + j < d; ++j) {
       // coefficients of this (i, j): c sqrt(p!) (g/2)^k / (k! i! j!), p = i + j + 2k
       const int kmx = (d - 1 - i - j) / 2;
@@ -186,15 +192,15 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
       }
       if (j > 0) {
         if (nr == 0) break;
-        double2* Yn = (Ysrc == Ya) ? Yb : Ya;
+        C2* Yn = (Ysrc == Ya) ? Yb : Ya;
         for (size_t idx = tid; idx < DD; idx += nt) {
           const int mu = idx / Dr, nu = idx % Dr;
-          double2 acc = cmk(0.0, 0.0);
+          C2 acc = zero;
           for (int q = 0; q < nr; ++q) {
             const int b = occ_of(t.occr, nu, q);
             if (b == 0) continue;
             const int r = t.lowr[(size_t)q * t.capr + nu];
-            cfma(acc, cscale(sm.Q[ia * QS + nl + 1 + q], sm.sq[b]), Ysrc[(size_t)mu * Dr + r]);
+            cfma(acc, to_c<C2>(cscale(sm.Q[ia * QS + nl + 1 + q], sm.sq[b])), Ysrc[(size_t)mu * Dr + r]);
           }
           Yn[idx] = acc;
         }
@@ -205,7 +211,7 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
       }
       for (size_t idx = tid; idx < DD; idx += nt) {
         const int mu = idx / Dr, nu = idx % Dr;
-        const double2 y = Ysrc[idx];
+        const double2 y = to_d(Ysrc[idx]);
         for (int k = 0; k <= kmx; ++k) {
           const int p = i + j + 2 * k;
           double2* dst = A + ((size_t)mu * d + p) * Dr + nu;
@@ -238,6 +244,23 @@ __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n,
   }
 }
 
+// energy gauge of the mixed path: Ahat[a, p, b] = A[a, p, b] e^{-(E_b - E_a)/2}
+// (the right environment of bond m is close to diag(e^{-E}), Eq. (SVD3), so
+// this diagonal gauge makes the environments well conditioned in FP32)
+__global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d, int Dr,
+                                    const double* __restrict__ El, const double* __restrict__ Er,
+                                    float2* __restrict__ Ah) {
+  size_t n = (size_t)Dl * d * Dr;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int a = idx / ((size_t)d * Dr), b = idx % Dr;
+    double el = Dl > 1 ? El[a] : 0.0, er = Dr > 1 ? Er[b] : 0.0;
+    double s = exp(-0.5 * (er - el));
+    double2 v = A[idx];
+    Ah[idx] = make_float2((float)(v.x * s), (float)(v.y * s));
+  }
+}
+
 }  // namespace
 
 size_t pco_scratch_elems(int Dl, int Dr) {
@@ -246,8 +269,10 @@ size_t pco_scratch_elems(int Dl, int Dr) {
 
 cudaError_t launch_pco(const SiteTask* tasks_dev, int ntasks, int d, int precision,
                        double2* scratch, int* status, cudaStream_t s) {
-  (void)precision;
-  pco_kernel<<<ntasks, PCO_THREADS, 0, s>>>(tasks_dev, d, scratch, status);
+  if (precision == GBSMPS_PREC_MIXED)
+    pco_kernel<float><<<ntasks, PCO_THREADS, 0, s>>>(tasks_dev, d, scratch, status);
+  else
+    pco_kernel<double><<<ntasks, PCO_THREADS, 0, s>>>(tasks_dev, d, scratch, status);
   return cudaGetLastError();
 }
 
@@ -256,5 +281,15 @@ cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int ca
   int blocks = (D * n + 255) / 256;
   if (blocks < 1) blocks = 1;
   maps_brute_kernel<<<blocks, 256, 0, s>>>(occ, D, n, low, cap, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
+                                const double* Er, float2* Ah, cudaStream_t s) {
+  size_t n = (size_t)Dl * d * Dr;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  energy_gauge_kernel<<<blocks, 256, 0, s>>>(A, Dl, d, Dr, El, Er, Ah);
   return cudaGetLastError();
 }

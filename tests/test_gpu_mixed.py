@@ -1,0 +1,98 @@
+"""Mixed-precision path (FP32 PCO build, split-BF16 tensor-core environments
+and sampling in the energy gauge, FP64 Gaussian SVD) against the FP64 oracle.
+Tolerances: amplitude error <= 1e-5 relative (floor 1e-8 of the largest
+amplitude), fidelity >= 1 - 1e-8, samples bit-exact except draws flagged
+within 1e-5 Z of a CDF boundary."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import basis as B
+from oracle import mps as M
+from oracle import pco as P
+
+pytestmark = pytest.mark.gpu
+
+g = pytest.importorskip("paper_2512_10643_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+def mixed_close(a, b, rtol=1e-5, floor=1e-8):
+    a, b = np.asarray(a), np.asarray(b)
+    return bool(np.all(np.abs(a - b) <= rtol * np.abs(b) + floor * np.abs(b).max()))
+
+
+@pytest.mark.parametrize("seed,nl,nr,d,chil,chir", [(0, 2, 3, 4, 12, 15), (3, 4, 4, 6, 70, 90)])
+def test_fp32_pco_matches_oracle(ctx, seed, nl, nr, d, chil, chir):
+    r = np.random.default_rng(seed)
+    n = nl + 1 + nr
+    Q = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) * 0.35
+    Q = 0.5 * (Q + Q.T)
+    bl = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nl))[::-1], chil)
+    br = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nr))[::-1], chir)
+    ref = P.local_tensor(Q, bl, br, d, c=1.0)
+    got = g.gbsmps_build_site(ctx.h, Q, 1.0, bl.occ.astype(np.uint8), br.occ.astype(np.uint8), d,
+                              precision=g.PREC_MIXED)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,seed,chi,d", [(12, 3, 40, 4), (24, 4, 64, 5)])
+def test_mixed_build_amplitudes_and_samples(ctx, N, seed, chi, d):
+    w = wl.small(N, seed, d=d, chi=chi, depth=6, rlo=0.1, rhi=0.45)
+    omps = M.build_mps(w.gamma, d=d, chi=chi, eps=1e-12, lambda2_freeze=1e-9)
+    oT = M.normalise(omps.tensors)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=d, chi_max=chi, eps_trunc=1e-12,
+                       lambda2_freeze=1e-9, precision=g.PREC_MIXED)
+    try:
+        assert list(m.info["bond_dims"]) == omps.bond_dims
+        gT = m.tensors()
+        assert M.fidelity(gT, oT) >= 1 - 1e-8
+        pats = wl.random_patterns(300, N, d, seed=seed)
+        assert mixed_close(m.amplitudes(pats), M.amplitudes(oT, pats))
+        S = 4000
+        u = wl.uniforms(S, N, seed=seed + 7)
+        flags = np.zeros(S, dtype=np.uint8)
+        got = m.sample(S, uniforms=u, flags=flags)
+        ref, rflag = M.sample(oT, u)
+        ok = flags == 0
+        assert ok.mean() > 0.98
+        assert np.array_equal(got[ok], ref[ok])
+        assert np.all(got.astype(int).sum(1) % 2 == 0)
+    finally:
+        m.release()
+
+
+def test_mixed_vs_fp64_gpu_full_size(ctx):
+    """144 modes, d=6, chi=256: the mixed build and the FP64 build agree on
+    the bond dimensions, amplitudes (1e-5) and, with shared uniforms, on the
+    samples away from flagged boundaries."""
+    w = wl.config("n144_d6_chi256")
+    kw = dict(d=6, chi_max=256, eps_trunc=w.eps, lambda2_freeze=w.freeze)
+    m64 = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **kw)
+    mmx = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), precision=g.PREC_MIXED, **kw)
+    try:
+        assert list(m64.info["bond_dims"]) == list(mmx.info["bond_dims"])
+        pats = wl.random_patterns(200, 144, 6, seed=5)
+        pats[0] = 0
+        assert mixed_close(mmx.amplitudes(pats), m64.amplitudes(pats))
+        S = 500
+        u = wl.uniforms(S, 144, seed=11)
+        f64 = np.zeros(S, dtype=np.uint8)
+        fmx = np.zeros(S, dtype=np.uint8)
+        s64 = m64.sample(S, uniforms=u, flags=f64)
+        smx = mmx.sample(S, uniforms=u, flags=fmx)
+        ok = (fmx == 0) & (f64 == 0)
+        assert ok.mean() > 0.9
+        assert np.array_equal(s64[ok], smx[ok])
+    finally:
+        m64.release()
+        mmx.release()

@@ -75,6 +75,7 @@ class Workload:
     d: int
     chi: int
     eps: float = 1e-12
+    freeze: float = 1e-13     # lambda2_freeze (the D* tolerance of Sec. II A)
     seed: int = 0
     meta: dict = field(default_factory=dict)
 
@@ -92,24 +93,29 @@ def squeezed_state(r: np.ndarray, U: np.ndarray):
     return gamma, q
 
 
-def _make(name, N, rlo, rhi, depth, d, chi, seed, eps=1e-12, haar=False):
+def _make(name, N, rlo, rhi, depth, d, chi, seed, eps=1e-12, haar=False, freeze=1e-13):
     g = rng(seed)
     r = g.uniform(rlo, rhi, size=N)
     U = haar_unitary(N, g) if haar else brickwall_unitary(N, depth, g)
     gamma, q = squeezed_state(r, U)
     return Workload(name=name, N=N, gamma=gamma, Q=q, r=r, U=U, d=d, chi=chi,
-                    eps=eps, seed=seed,
+                    eps=eps, freeze=freeze, seed=seed,
                     meta={"depth": depth, "r_range": [rlo, rhi], "haar": haar})
 
 
 #: Workload recipes.  Seeds are 20251210 + index.
 CONFIGS = {
     # 8 modes, squeezed vacua r~U(0.3,0.8) through an 8x8 Haar unitary, d=8, chi=64
-    "pr1_n8": dict(N=8, rlo=0.3, rhi=0.8, depth=0, d=8, chi=64, seed=20251210, haar=True),
+    "pr1_n8": dict(N=8, rlo=0.3, rhi=0.8, depth=0, d=8, chi=64, seed=20251210, haar=True,
+                   eps=0.0),
     # 144 modes, r~U(0.1,0.4), brick-wall depth 12, d=6, chi=256
-    "n144_d6_chi256": dict(N=144, rlo=0.1, rhi=0.4, depth=12, d=6, chi=256, seed=20251211),
+    # (eps = 1e-12 and freeze = 1e-9: chi binds at the central bonds; modes with
+    # Lambda^2 <= 1e-9 are frozen)
+    "n144_d6_chi256": dict(N=144, rlo=0.1, rhi=0.4, depth=12, d=6, chi=256, seed=20251211,
+                           eps=1e-12, freeze=1e-9),
     # 1024 modes, r~U(0.05,0.25), brick-wall depth 32, d=4, chi=512
-    "n1024_d4_chi512": dict(N=1024, rlo=0.05, rhi=0.25, depth=32, d=4, chi=512, seed=20251213),
+    "n1024_d4_chi512": dict(N=1024, rlo=0.05, rhi=0.25, depth=32, d=4, chi=512, seed=20251213,
+                            eps=1e-12, freeze=1e-9),
 }
 
 
