@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the Gaussian-state -> MPS hot path on GB300.
+
+One step = the whole path on one synthetic state shaped like the paper's
+144-mode lossy-experiment workload (144 modes, squeezing r~U(0.1,0.4), depth-12
+brick-wall interferometer, d = 6, chi = 256, eps = 1e-12): input check, GSVD
+chain, kept bases, PCO tensor build, environments and normalisation, then
+100,000 photon-pattern samples (in-kernel Philox uniforms).  Inputs are
+resident in device memory when the timed region starts; the tensors (0.9 GB)
+and sampling work buffers (several GB) exceed the 129 MB L2, so no flush is
+needed between steps.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p50/p99 latency"
+WORKLOAD = "n144_d6_chi256"
+WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
+                 "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
+# dram bytes per launch of the dominant kernel from the committed ncu capture
+# (profiles/zgemm_tc_n144.md); None until a capture of the current kernel exists
+TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbsmps", choices=["gbsmps", "reference"])
+    ap.add_argument("--samples", type=int, default=100_000)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, local, ws, dist
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, local, ws, dist):
+    import numpy as np
+    import torch
+
+    import paper_2512_10643_gb300 as g
+    import workloads as wl
+
+    dev = local
+    torch.cuda.set_device(dev)
+    w = wl.config(WORKLOAD)
+    N, S = w.N, args.samples
+    prec = g.PREC_MIXED if args.precision == "mixed" else g.PREC_FP64
+    opts = dict(d=w.d, chi_max=w.chi, eps_trunc=w.eps, lambda2_freeze=w.freeze, precision=prec)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = g.Context(dev, stream.cuda_stream)
+    gam = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(f"cuda:{dev}")
+    out = torch.empty((S, N), dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def step(i, sample_count=S, precision=prec, dst=out):
+        m = g.MPS.from_cov(ctx, gam, **dict(opts, precision=precision))
+        m.sample(sample_count, seed=1234 + rank, counter0=i * sample_count, out=dst[:sample_count])
+        m.release()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    n0 = g.gbsmps_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(dev) as clk:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for i in range(args.steps):
+                step(args.warmup + i)
+                ev[i + 1].record(stream)
+        barrier()
+    launches = g.gbsmps_launch_count() - n0
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(total_s, dist)
+    value = N * args.steps * ws / total_s
+    samples_per_s = S * args.steps * ws / total_s
+
+    # dominant kernel, traced over one extra step outside the timed region
+    g.gbsmps_trace(ctx.h, True)
+    step(10_000)
+    torch.cuda.synchronize(dev)
+    tr = g.gbsmps_trace_read(ctx.h)
+    g.gbsmps_trace(ctx.h, False)
+    peaks, src = measured_peaks()
+    ach_tflops = tr["flops"] / (tr["ms"] / 1e3) / 1e12 if tr["ms"] > 0 else 0.0
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    roof = {"kernel": "zgemm_tc_kernel<6> (split-BF16 complex GEMM: environments + sampling)",
+            "bound": "tensor", "achieved": round(ach_tflops, 3), "peak": peak,
+            "peak_source": f"{src} bf16_tflops_sustained (of {src})",
+            "unit": "TFLOP/s", "frac": round(ach_tflops / peak, 5),
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+            "algorithmic_flops_per_launch": tr["flops"] / max(tr["launches"], 1),
+            "avg_launch_ms": tr["ms"] / max(tr["launches"], 1),
+            "launches_per_step": tr["launches"],
+            "share_of_step": round(tr["ms"] / (sum(step_ms) / len(step_ms)), 4),
+            "split_products": 6}
+
+    # build-only throughput and the FP64 GPU path for comparison
+    res = {}
+    if rank == 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            m = g.MPS.from_cov(ctx, gam, **opts)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res["build_ms"] = e0.elapsed_time(e1)
+        pats = wl.random_patterns(256, N, w.d, seed=3)
+        pats[0] = 0
+        pats_d = torch.from_numpy(pats).to(f"cuda:{dev}")
+        amp_mixed = m.amplitudes(pats)
+        m.release()
+        if not args.no_fp64:
+            S64 = 2000
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                m64 = g.MPS.from_cov(ctx, gam, **dict(opts, precision=g.PREC_FP64))
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
+            b64 = e0.elapsed_time(e1)
+            e2 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                m64.sample(S64, seed=1234, counter0=0, out=out[:S64])
+                e2.record(stream)
+            torch.cuda.synchronize(dev)
+            s64 = e1.elapsed_time(e2)
+            s64_ms_step = b64 + s64 * (S / S64)
+            amp64 = m64.amplitudes(pats)
+            rel = np.abs(amp_mixed - amp64) / np.maximum(np.abs(amp64), 1e-300)
+            big = np.abs(amp64) >= 1e-3 * np.abs(amp64).max()
+            # shared-seed sample agreement between the two paths
+            mref = g.MPS.from_cov(ctx, gam, **opts)
+            s_a = torch.empty((S64, N), dtype=torch.uint8, device=f"cuda:{dev}")
+            mref.sample(S64, seed=99, counter0=0, out=s_a)
+            s_b = torch.empty_like(s_a)
+            m64.sample(S64, seed=99, counter0=0, out=s_b)
+            agree = float((s_a == s_b).all(dim=1).float().mean().item())
+            mref.release()
+            m64.release()
+            res["fp64_gpu"] = {
+                "build_ms": round(b64, 3), "sample_ms_per_1k": round(s64 / S64 * 1e3, 3),
+                "ms_per_step_extrapolated": round(s64_ms_step, 1),
+                "tensors_per_s": round(N / (s64_ms_step / 1e3), 3),
+                "samples_per_s": round(S / (s64_ms_step / 1e3), 1),
+                "sample": f"FP64 build timed in full; sampling timed on {S64} samples and scaled to {S}",
+                "mixed_vs_fp64_amp_max_rel_err": float(rel[big].max()),
+                "mixed_vs_fp64_amp_max_abs_err_rel_to_max": float(np.abs(amp_mixed - amp64).max() / np.abs(amp64).max()),
+                "shared_seed_sample_agreement": agree}
+        del pats_d
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        gam_h = torch.from_numpy(np.ascontiguousarray(w.gamma)).pin_memory()
+        out_h = torch.empty((S, N), dtype=torch.uint8).pin_memory()
+        K2 = max(1, min(2, args.steps))
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(K2):
+            m = g.MPS.from_cov(ctx, gam_h, **opts)
+            m.sample(S, seed=4321 + rank, counter0=i * S, out=out_h)
+            m.release()
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        te = max_over_ranks(t1 - t0, dist)
+        e2e = {"value": round(N * K2 * ws / te, 3), "unit": "tensors/s",
+               "samples_per_s": round(S * K2 * ws / te, 1),
+               "h2d_bytes_per_step": int(gam_h.numel() * 8), "d2h_bytes_per_step": int(S * N),
+               "steps": K2}
+    ctx.close()
+    return dict(value=value, samples_per_s=samples_per_s, step_ms=step_ms, launches=launches,
+                roof=roof, clocks=clk.summary(), e2e=e2e, **res)
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+def oracle_step_estimate(budget_s=20.0):
+    """Time the FP64 oracle on a bounded sample of the same workload and scale
+    to one step (all 144 tensors + 100k samples)."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle import basis as B
+    from oracle import gaussian as G
+    from oracle import mps as M
+    from oracle import pco as P
+
+    w = wl.config(WORKLOAD)
+    t0 = time.perf_counter()
+    cuts = G.gsvd_chain(w.gamma, lambda2_freeze=w.freeze)
+    bases = [M.vacuum_basis()] + [B.kept_basis(c.lam2, w.chi, w.eps) for c in cuts[:-1]] + [M.vacuum_basis()]
+    t_chain = time.perf_counter() - t0
+    sites = [71, 36, 108, 72, 20, 124]
+    t_pco, n_pco, tensors = 0.0, 0, {}
+    for s in sites:
+        t = time.perf_counter()
+        tensors[s] = P.local_tensor(cuts[s].Q, bases[s], bases[s + 1], w.d, cuts[s].c)
+        t_pco += time.perf_counter() - t
+        n_pco += 1
+        if t_pco > budget_s * 0.5:
+            break
+    per_site_pco = t_pco / n_pco
+    A = tensors[71]
+    Dl, Dr = A.shape[0], A.shape[2]
+    # one right-environment step through a central tensor
+    t = time.perf_counter()
+    for _ in range(3):
+        M.environments([A, np.ones((Dr, 1, 1), dtype=np.complex128)])
+    per_site_env = (time.perf_counter() - t) / 3
+    # conditional sampling through the same tensor: a 1 x 1 x Dl opening
+    # tensor then A, with identity environments (cost is shape-determined)
+    S0 = 200
+    u = wl.uniforms(S0, 2, seed=1)
+    TT = [np.ones((1, 1, Dl), dtype=np.complex128) / np.sqrt(Dl), A]
+    Rs = [None, np.eye(Dl, dtype=np.complex128), np.eye(Dr, dtype=np.complex128)]
+    t = time.perf_counter()
+    M.sample(TT, u, R=Rs)
+    per_sample_site = (time.perf_counter() - t) / S0
+    full_sites = sum(1 for b in bases[1:-1] if b.D == w.chi)
+    step_s = (t_chain + w.N * (per_site_pco + per_site_env) + 100_000 * full_sites * per_sample_site)
+    sample_desc = (f"oracle GSVD chain + kept bases over all {w.N - 1} cuts ({t_chain:.2f}s), PCO build of "
+                   f"{n_pco} central sites ({per_site_pco:.2f}s/site), one environment step and "
+                   f"{S0} conditional samples through one central site, scaled to {w.N} sites and "
+                   f"100000 samples per step")
+    return {"step_s": step_s, "value": w.N / step_s, "samples_per_s": 100_000 / step_s,
+            "sample": sample_desc, "cores": os.cpu_count(), "measured_s": time.perf_counter() - t0}
+
+
+def main():
+    args = parse()
+    rank, local, ws, dist = dist_init()
+    base = {"metric": METRIC, "unit": "tensors/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic (seeded Philox; paper's experimental data not available)"}
+    cfg = {"workload": WORKLOAD_DESC, "name": WORKLOAD, "samples_per_step": args.samples,
+           "precision": args.precision, "inputs": "device-resident; working set > L2 (no flush needed)",
+           "parallelism": f"replicas x{ws}"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        est = oracle_step_estimate()
+        line = dict(base, impl="reference", value=round(est["value"], 6),
+                    ms_per_step=round(est["step_s"] * 1e3, 1), dtype="f64", config=cfg,
+                    samples_per_s=round(est["samples_per_s"], 3),
+                    cpu_baseline={"value": round(est["value"], 6), "unit": "tensors/s",
+                                  "cores": est["cores"], "kind": "oracle", "sample": est["sample"]},
+                    e2e={"value": round(est["value"], 6), "unit": "tensors/s",
+                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+        print(json.dumps(line))
+        return
+    r = run_gpu(args, rank, local, ws, dist)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        est = oracle_step_estimate()
+        cpu = {"value": round(est["value"], 6), "unit": "tensors/s", "cores": est["cores"],
+               "kind": "oracle", "sample": est["sample"],
+               "samples_per_s": round(est["samples_per_s"], 3)}
+    sm = sorted(r["step_ms"])
+    line = dict(base, value=round(r["value"], 3), ms_per_step=round(sum(sm) / len(sm), 3),
+                dtype="f64 gsvd + f32 pco + bf16x6/fp32 tensor-core gemm" if args.precision == "mixed" else "f64",
+                config=cfg, samples_per_s=round(r["samples_per_s"], 1),
+                latency_ms={"p50": round(statistics.median(sm), 3),
+                            "p99": round(sm[min(len(sm) - 1, int(0.99 * len(sm)))], 3)},
+                build_ms=round(r.get("build_ms", 0.0), 3),
+                roofline=r["roof"], cpu_baseline=cpu, e2e=r["e2e"], gpu_launches=r["launches"],
+                clocks=r["clocks"])
+    if "fp64_gpu" in r:
+        line["fp64_gpu"] = r["fp64_gpu"]
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

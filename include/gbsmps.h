@@ -170,9 +170,21 @@ const char* gbsmps_strerror(int code);
 /* One-line detail of the last error on the calling thread. */
 const char* gbsmps_last_error_detail(void);
 
-/* Build number and the list of kernels the library launched since the last
- * call (comma separated, static per thread), for launch accounting. */
+/* Number of kernels the library has enqueued since it was loaded (all
+ * contexts), for launch accounting. */
 int64_t gbsmps_launch_count(gbsmps_ctx_t ctx);
+
+/* Tracing of the dominant kernel, the split-BF16 tensor-core complex GEMM
+ * (environments and sampling of the mixed path): gbsmps_trace(ctx, 1) clears
+ * the record and records a CUDA event pair around every later launch on the
+ * launching stream; gbsmps_trace(ctx, 0) stops recording.  gbsmps_trace_read
+ * synchronises on the recorded events and returns the summed device time,
+ * the launch count, and the launches' algorithmic work: 8 M N K real flops
+ * per complex M x N x K product and the operand/result bytes at their storage
+ * width.  Outputs may be NULL.  Not part of the numerical path. */
+int gbsmps_trace(gbsmps_ctx_t ctx, int enable);
+int gbsmps_trace_read(gbsmps_ctx_t ctx, double* total_ms, int64_t* launches,
+                      double* flops, double* bytes);
 
 #ifdef __cplusplus
 }

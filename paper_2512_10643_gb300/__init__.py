@@ -66,6 +66,8 @@ def lib():
         "gbsmps_strerror": (C.c_char_p, [C.c_int]),
         "gbsmps_last_error_detail": (C.c_char_p, []),
         "gbsmps_launch_count": (i64, [vp]),
+        "gbsmps_trace": (C.c_int, [vp, C.c_int]),
+        "gbsmps_trace_read": (C.c_int, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -221,6 +223,17 @@ def gbsmps_build_site(ctx, Qm, c, occ_l, occ_r, d, precision=PREC_FP64):
 
 def gbsmps_launch_count(ctx=None) -> int:
     return int(lib().gbsmps_launch_count(ctx))
+
+
+def gbsmps_trace(ctx, enable: bool):
+    _check(lib().gbsmps_trace(ctx, int(bool(enable))))
+
+
+def gbsmps_trace_read(ctx):
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    _check(lib().gbsmps_trace_read(ctx, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)))
+    return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
 
 
 class Context:

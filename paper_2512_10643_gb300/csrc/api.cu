@@ -664,4 +664,21 @@ const char* gbsmps_last_error_detail(void) { return g_detail.c_str(); }
 
 int64_t gbsmps_launch_count(gbsmps_ctx_t) { return (int64_t)g_kernel_launches; }
 
+int gbsmps_trace(gbsmps_ctx_t c, int enable) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  g_tc_trace.reset();
+  g_tc_trace.on = enable != 0;
+  return GBSMPS_OK;
+}
+
+int gbsmps_trace_read(gbsmps_ctx_t c, double* total_ms, int64_t* launches, double* flops,
+                      double* bytes) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  if (total_ms) *total_ms = g_tc_trace.total_ms();
+  if (launches) *launches = g_tc_trace.launches;
+  if (flops) *flops = g_tc_trace.flops;
+  if (bytes) *bytes = g_tc_trace.bytes;
+  return GBSMPS_OK;
+}
+
 }  // extern "C"

@@ -76,6 +76,46 @@ struct BondArrays {
   double* eps;        // [b] discarded weight
 };
 
+// ---- opt-in kernel tracing: CUDA events around every launch of one kernel
+// family on its own stream, summed with the launches' algorithmic work -------
+#include <vector>
+struct KernelTrace {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // begin/end pairs
+  double flops = 0.0, bytes = 0.0;
+  long long launches = 0;
+  cudaEvent_t pending = nullptr;
+  void begin(cudaStream_t s) {
+    if (!on) return;
+    cudaEventCreate(&pending);
+    cudaEventRecord(pending, s);
+  }
+  void end(cudaStream_t s, double f, double b) {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(pending);
+    ev.push_back(e);
+    flops += f; bytes += b; ++launches;
+  }
+  double total_ms() {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      cudaEventSynchronize(ev[i + 1]);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      t += ms;
+    }
+    return t;
+  }
+  void reset() {
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear(); flops = bytes = 0.0; launches = 0;
+  }
+};
+extern KernelTrace g_tc_trace;    // the split-BF16 tensor-core GEMM
+
 // ---- launchers (each returns cudaError_t of the launch) -------------------
 // g_kernel_launches counts every kernel the library enqueues.
 extern unsigned long long g_kernel_launches;

@@ -225,6 +225,8 @@ cudaError_t run(const TcArgs& a, int batch, cudaStream_t s) {
 
 }  // namespace
 
+KernelTrace g_tc_trace;
+
 cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
                             const void* A, int a64, long long lda, long long sA,
                             const void* B, int b64, long long ldb, long long sB,
@@ -234,5 +236,13 @@ cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
   TcArgs a{M, N, K, A, lda, sA, a64, opa == 'C' ? 1 : 0, B, ldb, sB, b64, opb == 'C' ? 1 : 0,
            C, ldc, sC, c64};
   COUNT_LAUNCH(1);
-  return nterms == 3 ? run<3>(a, batch, s) : run<6>(a, batch, s);
+  // algorithmic work of the complex product: 8 M N K real flops; bytes: one
+  // read of each operand and one write of C at their storage widths
+  double flops = 8.0 * M * (double)N * K * batch;
+  double bytes = ((double)M * K * (a64 ? 16 : 8) + (double)K * N * (b64 ? 16 : 8) +
+                  (double)M * N * (c64 ? 16 : 8)) * batch;
+  g_tc_trace.begin(s);
+  cudaError_t e = nterms == 3 ? run<3>(a, batch, s) : run<6>(a, batch, s);
+  g_tc_trace.end(s, flops, bytes);
+  return e;
 }
