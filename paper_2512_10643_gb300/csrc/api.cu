@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <memory>
 #include <string>
 #include <vector>
@@ -100,12 +101,19 @@ struct gbsmps_mps {
   int maxD = 1;
   DevBuf tensors, env, gsvd, bonds;
   DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
+  // mixed path, right-canonical sampler: Cholesky factors of the environments,
+  // their inverses, and every site's canonical tensor as bf16 planes + TMA map
+  DevBuf eoff_dev, lchol, linv, bpack;
+  std::vector<int> Drp, Kp, Np;
+  std::vector<long long> bpoff;
+  std::vector<std::array<unsigned char, 128>> bmaps;
   BondArrays ba{};
   double* lam2 = nullptr;
   double2* Qm = nullptr;
   double* cm = nullptr;
   ~gbsmps_mps() {
     tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
+    eoff_dev.release(); lchol.release(); linv.release(); bpack.release();
   }
 };
 
@@ -281,14 +289,18 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     }
     tm.mark("energy_gauge");
     float2* Xf = reinterpret_cast<float2*>(X);
+    const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
+    DevBuf kw;
+    CK(kw.alloc(wbytes, s));
     for (int m = N - 1; m >= 0; --m) {
       int Dl = M->D[m], Dr = M->D[m + 1];
       const float2* A = Ah + M->toff[m];
       CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, A, 0, Dr, 0, R + M->eoff[m + 1], 1, Dr, 0,
-                         Xf, 0, Dr, 0, 1, s));
+                         Xf, 0, Dr, 0, 1, s, kw.p, wbytes));
       CK(launch_zgemm_tc(6, 'N', 'C', Dl, Dl, d * Dr, Xf, 0, d * Dr, 0, A, 0, d * Dr, 0,
-                         R + M->eoff[m], 1, Dl, 0, 1, s));
+                         R + M->eoff[m], 1, Dl, 0, 1, s, kw.p, wbytes));
     }
+    kw.release();
   } else {
     for (int m = N - 1; m >= 0; --m) {
       int Dl = M->D[m], Dr = M->D[m + 1];
@@ -319,6 +331,67 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], ba.E, ba.E + cap,
                            M->tens_mixed.as<float2>(), s));
     COUNT_LAUNCH(1);
+  }
+  tm.mark("normalise");
+  if (mixed) {
+    // ---- right-canonical form for the tensor-core sampler -----------------
+    // R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
+    // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as bf16 planes per site
+    CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
+    CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
+                       cudaMemcpyHostToDevice, s));
+    CK(M->lchol.alloc(sizeof(double2) * (etot + 8), s));
+    CK(M->linv.alloc(sizeof(double2) * (etot + 8), s));
+    CK(cudaMemcpyAsync(M->lchol.p, R, sizeof(double2) * etot, cudaMemcpyDeviceToDevice, s));
+    CK(launch_chol(M->lchol.as<double2>(), M->eoff_dev.as<long long>(), ba.D, 1, N - 1,
+                   c->d_status, s));
+    CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
+                    ba.D, 1, N - 1, s));
+    COUNT_LAUNCH(2);
+    for (int b : {0, N}) {
+      CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
+                         cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(M->linv.as<double2>() + M->eoff[b], &one, sizeof(double2),
+                         cudaMemcpyHostToDevice, s));
+    }
+    tm.mark("cholesky");
+    M->Drp.resize(N); M->Kp.resize(N); M->Np.resize(N); M->bpoff.resize(N); M->bmaps.resize(N);
+    long long btot = 0;
+    for (int m = 0; m < N; ++m) {
+      M->Drp[m] = (M->D[m + 1] + 63) / 64 * 64;
+      M->Kp[m] = (2 * M->D[m] + 63) / 64 * 64;
+      M->Np[m] = 2 * d * M->Drp[m];
+      M->bpoff[m] = btot;
+      btot += 3LL * M->Np[m] * M->Kp[m];
+    }
+    CK(M->bpack.alloc(sizeof(__nv_bfloat16) * (btot + 64), s));
+    DevBuf tb, ab2, kw2;
+    const size_t wbytes2 = (size_t)64 << 20;
+    CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
+    CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
+    CK(kw2.alloc(wbytes2, s));
+    const float2* Ah = M->tens_mixed.as<float2>();
+    for (int m = 0; m < N; ++m) {
+      const int Dl = M->D[m], Dr = M->D[m + 1];
+      float2* T = tb.as<float2>();
+      float2* At = ab2.as<float2>();
+      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 0, Dr, 0,
+                         M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
+                         kw2.p, wbytes2));
+      const float2* src = T;
+      if (m > 0) {
+        CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
+                           T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, kw2.p, wbytes2));
+        src = At;
+      }
+      __nv_bfloat16* Bp = M->bpack.as<__nv_bfloat16>() + M->bpoff[m];
+      CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
+      COUNT_LAUNCH(1);
+      if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
+        return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+    }
+    tb.release(); ab2.release(); kw2.release();
+    tm.mark("canonical_pack");
   }
   // R_0 of the normalised state is 1
   CK(cudaMemcpyAsync(R + M->eoff[0], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
@@ -495,9 +568,11 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   const size_t per = (size_t)d * m->maxD;
   int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)((size_t)6 << 30) / (int64_t)(sizeof(double2) * 2 * per + 32 * m->maxD)));
   DevBuf ub, obuf, fbuf, vb, wb, yb;
-  CK(vb.alloc(sizeof(double2) * 2 * (size_t)chunk * m->maxD, s));
-  CK(wb.alloc(sizeof(double2) * (size_t)chunk * per, s));
-  CK(yb.alloc(sizeof(double2) * (size_t)chunk * per, s));
+  if (m->precision != GBSMPS_PREC_MIXED) {
+    CK(vb.alloc(sizeof(double2) * 2 * (size_t)chunk * m->maxD, s));
+    CK(wb.alloc(sizeof(double2) * (size_t)chunk * per, s));
+    CK(yb.alloc(sizeof(double2) * (size_t)chunk * per, s));
+  }
   const double* du = uniforms;
   uint8_t* dout = out;
   uint8_t* dfl = flags;
@@ -515,26 +590,41 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   const double2* R = m->env.as<double2>();
   const double2 one = cmk(1, 0), zero = cmk(0, 0);
   StageTimer tm(s);
+  DevBuf cv0, cv1, cw, cpart;        // mixed path: bf16 state planes, W, tile norms
+  const char* tce = getenv("GBSMPS_TC");
+  const int use_tc = !(tce && tce[0] == '0');
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
     if (m->precision == GBSMPS_PREC_MIXED) {
-      // split-BF16 tensor-core GEMMs on the energy-gauge tensors, FP32 state
-      float2* V = vb.as<float2>();
-      float2* Vn = V + (size_t)chunk * m->maxD;
-      CK(launch_init_ones_f(V, cs, s));
+      // right-canonical tensors: one tensor-core GEMM per site, q_p = |w_p|^2
+      const int Spad = (int)((chunk + 127) / 128 * 128);
+      int Kpmax = 64, Npmax = 128;
+      for (int i = 0; i < N; ++i) { Kpmax = std::max(Kpmax, m->Kp[i]); Npmax = std::max(Npmax, m->Np[i]); }
+      if (!cw.p) {
+        CK(cv0.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)Spad * Kpmax, s));
+        CK(cv1.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)Spad * Kpmax, s));
+        CK(cw.alloc(sizeof(float2) * (size_t)chunk * (Npmax / 2), s));
+        CK(cpart.alloc(sizeof(float) * (size_t)chunk * (Npmax / 128), s));
+      }
+      __nv_bfloat16* V = cv0.as<__nv_bfloat16>();
+      __nv_bfloat16* Vn = cv1.as<__nv_bfloat16>();
+      CK(launch_vinit(V, (long long)Spad * m->Kp[0], Spad, m->Kp[0], s));
       COUNT_LAUNCH(1);
       for (int site = 0; site < N; ++site) {
         const int Dl = m->D[site], Dr = m->D[site + 1];
-        const float2* A = m->tens_mixed.as<float2>() + m->toff[site];
-        float2* W = wb.as<float2>();
-        float2* Y = yb.as<float2>();
-        CK(launch_zgemm_tc(6, 'N', 'N', cs, d * Dr, Dl, V, 0, Dl, 0, A, 0, d * Dr, 0, W, 0, d * Dr,
-                           0, 1, s));
-        CK(launch_zgemm_tc(6, 'N', 'N', cs * d, Dr, Dr, W, 0, Dr, 0, R + m->eoff[site + 1], 1, Dr,
-                           0, Y, 0, Dr, 0, 1, s));
-        CK(launch_sample_select_mixed(cs, d, Dr, W, Y, du ? du + (size_t)s0 * N : nullptr, N, site,
-                                      seed, counter0 + (uint64_t)s0, Vn, dout + (size_t)s0 * N, N,
-                                      dfl ? dfl + s0 : nullptr, 1e-5, s));
+        const int Kp = m->Kp[site], Np = m->Np[site];
+        const int Kpn = site + 1 < N ? m->Kp[site + 1] : 64;
+        unsigned char mapA[128];
+        if (canon_make_map(mapA, V, Kp, Spad))
+          return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
+        CK(launch_canon_gemm(mapA, m->bmaps[site].data(), V, (long long)Spad * Kp,
+                             m->bpack.as<__nv_bfloat16>() + m->bpoff[site], (long long)Np * Kp, Kp,
+                             Np, cs, Spad, 6, cw.as<float2>(), cpart.as<float>(), use_tc,
+                             8.0 * cs * Dl * (double)d * Dr, m->ctx->d_status, s));
+        CK(launch_select_canon(cs, d, Dr, m->Drp[site], cw.as<float2>(), cpart.as<float>(), Np / 128,
+                               du ? du + (size_t)s0 * N : nullptr, N, site, seed,
+                               counter0 + (uint64_t)s0, Vn, (long long)Spad * Kpn, Kpn,
+                               dout + (size_t)s0 * N, N, dfl ? dfl + s0 : nullptr, 1e-5, s));
         COUNT_LAUNCH(1);
         std::swap(V, Vn);
       }
@@ -566,6 +656,7 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
     if (flags) CK(cudaMemcpyAsync(flags, dfl, (size_t)S, cudaMemcpyDeviceToHost, s));
   }
   ub.release(); obuf.release(); fbuf.release(); vb.release(); wb.release(); yb.release();
+  cv0.release(); cv1.release(); cw.release(); cpart.release();
   if (mem_kind == GBSMPS_MEM_HOST) return sync_status(m->ctx);
   return GBSMPS_OK;
 }

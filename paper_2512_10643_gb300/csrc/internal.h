@@ -18,6 +18,28 @@
 #define ST_NUMERIC 4
 #define ST_NOT_SYMMETRIC 8
 #define ST_NOT_PURE 16
+#define ST_TIMEOUT 32
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): uniform in [0,1)
+// with 53 bits from the first two output words; key = seed, counter =
+// (sample lo, sample hi, site, 0) ---------------------------------------------
+__device__ inline void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+  uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+  uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+  c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+__device__ inline double philox_uniform(uint64_t seed, uint64_t sample, uint32_t site) {
+  uint32_t c[4] = {(uint32_t)sample, (uint32_t)(sample >> 32), site, 0u};
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c, k0, k1);
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  uint64_t a = c[0] >> 5, b = c[1] >> 6;     // 27 + 26 bits
+  return (double)(a * 67108864ull + b) * (1.0 / 9007199254740992.0);
+}
 
 // ---- complex helpers on double2 -------------------------------------------
 __host__ __device__ inline double2 cmk(double r, double i) { return make_double2(r, i); }
@@ -175,13 +197,32 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
                                 const double* Er, float2* Ah, cudaStream_t s);
+// right-canonical mixed sampling (k_canon.cu)
+#include <cuda_bf16.h>
+int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
+cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __nv_bfloat16* Ap,
+                              long long apl, const __nv_bfloat16* Bp, long long bpl, int Kp,
+                              int Np, int M, int Mpad, int nterms, float2* W, float* part,
+                              int use_tc, double alg_flops, int* status, cudaStream_t s);
+cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
+                          __nv_bfloat16* Bp, long long bpl, cudaStream_t s);
+cudaError_t launch_vinit(__nv_bfloat16* V, long long vpl, int Spad, int Kp, cudaStream_t s);
+cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, const float* part,
+                                int ntiles, const double* u, int ustride, int site, uint64_t seed,
+                                uint64_t counter0, __nv_bfloat16* V, long long vpl, int Kpn,
+                                uint8_t* out, int N, uint8_t* flags, double flag_tol,
+                                cudaStream_t s);
+cudaError_t launch_chol(double2* base, const long long* off, const int* Dv, int b0, int nb,
+                        int* status, cudaStream_t s);
+cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
+                         int nb, cudaStream_t s);
 // split-BF16 tensor-core complex GEMM (nterms 3 or 6), operands FP64 or FP32
 // complex (a64/b64/c64 flags), op 'N' or 'C'; counts its own launch
 cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
                             const void* A, int a64, long long lda, long long sA,
                             const void* B, int b64, long long ldb, long long sB,
                             void* C, int c64, long long ldc, long long sC, int batch,
-                            cudaStream_t s);
+                            cudaStream_t s, void* work = nullptr, size_t work_bytes = 0);
 cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W,
                                  const double2* Y, const double* u, int ustride,
                                  int site, uint64_t seed, uint64_t counter0,

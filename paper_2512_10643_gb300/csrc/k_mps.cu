@@ -135,26 +135,6 @@ __global__ void amp_out_kernel(const double2* V, long long P, int ld, double2* o
     out[s] = V[s * ld];
 }
 
-// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------------
-__device__ inline void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-  uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-  uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
-  c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
-}
-
-__device__ inline double philox_uniform(uint64_t seed, uint64_t sample, uint32_t site) {
-  uint32_t c[4] = {(uint32_t)sample, (uint32_t)(sample >> 32), site, 0u};
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  for (int r = 0; r < 10; ++r) {
-    philox_round(c, k0, k1);
-    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
-  }
-  uint64_t a = c[0] >> 5, b = c[1] >> 6;     // 27 + 26 bits
-  return (double)(a * 67108864ull + b) * (1.0 / 9007199254740992.0);
-}
-
 // one warp per sample; C2 = double2 (FP64 path) or float2 (mixed path),
 // probabilities accumulated in FP64 either way
 template <typename C2>

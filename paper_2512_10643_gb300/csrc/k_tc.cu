@@ -11,6 +11,7 @@
 // registers while the current one is multiplied.
 #include "internal.h"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace {
 
@@ -25,6 +26,8 @@ struct TcArgs {
   const void* A; long long lda, sA; int a64, opa;
   const void* B; long long ldb, sB; int b64, opb;
   void* C; long long ldc, sC; int c64;
+  int ksplit, kchunk;            // split-K: partial products reduced in FP64
+  float2* part;
 };
 
 __device__ __forceinline__ float2 ld_c(const void* p, long long idx, int is64) {
@@ -65,7 +68,9 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wm = warp & 1, wn = warp >> 1;
-  const long long bz = blockIdx.z;
+  const long long bz = blockIdx.z / p.ksplit;
+  const int kz = blockIdx.z % p.ksplit;
+  const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
   const int i0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
   const void* A = p.a64 ? (const void*)(reinterpret_cast<const double2*>(p.A) + bz * p.sA)
                         : (const void*)(reinterpret_cast<const float2*>(p.A) + bz * p.sA);
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
       else { kc = tid >> 4; i = (tid & 15) * 8 + j; }
       int gi = i0 + i, gk = k0 + kc;
       float2 v = make_float2(0.f, 0.f);
-      if (gi < p.M && gk < p.K) {
+      if (gi < p.M && gk < kend) {
         if (p.opa == 0) v = ld_c(A, (long long)gi * p.lda + gk, p.a64);
         else { v = ld_c(A, (long long)gk * p.lda + gi, p.a64); v.y = -v.y; }
       }
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
       else { nc = tid >> 2; kc = (tid & 3) * 4 + j; }
       int gn = n0 + nc, gk = k0 + kc;
       float2 v = make_float2(0.f, 0.f);
-      if (gn < p.N && gk < p.K) {
+      if (gn < p.N && gk < kend) {
         if (p.opb == 0) v = ld_c(B, (long long)gk * p.ldb + gn, p.b64);
         else { v = ld_c(B, (long long)gn * p.ldb + gk, p.b64); v.y = -v.y; }
       }
@@ -145,12 +150,12 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
     }
   };
 
-  load_stage(0);
-  for (int k0 = 0; k0 < p.K; k0 += BKC) {
+  load_stage(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BKC) {
     __syncthreads();
     store_stage();
     __syncthreads();
-    if (k0 + BKC < p.K) load_stage(k0 + BKC);
+    if (k0 + BKC < kend) load_stage(k0 + BKC);
 #pragma unroll
     for (int kk = 0; kk < BKR; kk += 16) {
       uint32_t af[NS][4][4], bf[NS][4][2];
@@ -198,12 +203,36 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
       for (int h = 0; h < 2; ++h) {
         int row = i0 + wm * 64 + mt * 16 + g + 8 * h;
         if (row >= p.M) continue;
-        long long idx = bz * p.sC + (long long)row * p.ldc + colc;
         float re = acc[mt][nt][2 * h], im = acc[mt][nt][2 * h + 1];
+        if (p.ksplit > 1) {
+          p.part[((long long)blockIdx.z * p.M + row) * p.N + colc] = make_float2(re, im);
+          continue;
+        }
+        long long idx = bz * p.sC + (long long)row * p.ldc + colc;
         if (p.c64) reinterpret_cast<double2*>(p.C)[idx] = make_double2(re, im);
         else reinterpret_cast<float2*>(p.C)[idx] = make_float2(re, im);
       }
     }
+  }
+}
+
+// C = sum over k-chunks of the FP32 partial products, summed in FP64 in a
+// fixed order (deterministic)
+__global__ void splitk_reduce_kernel(const float2* __restrict__ part, int ksplit, int batch,
+                                     int M, int N, void* C, int c64, long long ldc, long long sC) {
+  long long n = (long long)batch * M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long b = i / ((long long)M * N), r = (i / N) % M, c = i % N;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < ksplit; ++k) {
+      float2 v = part[((b * ksplit + k) * M + r) * N + c];
+      re += v.x;
+      im += v.y;
+    }
+    long long idx = b * sC + r * ldc + c;
+    if (c64) reinterpret_cast<double2*>(C)[idx] = make_double2(re, im);
+    else reinterpret_cast<float2*>(C)[idx] = make_float2((float)re, (float)im);
   }
 }
 
@@ -218,8 +247,15 @@ cudaError_t run(const TcArgs& a, int batch, cudaStream_t s) {
     if (e) return e;
     attr = true;
   }
-  dim3 grid((a.N + BNC - 1) / BNC, (a.M + BM - 1) / BM, batch);
+  dim3 grid((a.N + BNC - 1) / BNC, (a.M + BM - 1) / BM, batch * a.ksplit);
   zgemm_tc_kernel<NT><<<grid, 256, smem, s>>>(a);
+  if (a.ksplit > 1) {
+    long long n = (long long)batch * a.M * a.N;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(a.part, a.ksplit, batch, a.M, a.N, a.C, a.c64,
+                                                a.ldc, a.sC);
+    COUNT_LAUNCH(1);
+  }
   return cudaGetLastError();
 }
 
@@ -231,10 +267,22 @@ cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
                             const void* A, int a64, long long lda, long long sA,
                             const void* B, int b64, long long ldb, long long sB,
                             void* C, int c64, long long ldc, long long sC, int batch,
-                            cudaStream_t s) {
+                            cudaStream_t s, void* work, size_t work_bytes) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  // split K when the output tiles alone cannot fill the GPU, or K is long:
+  // each chunk keeps >= 4 stages, the partials are summed in FP64
+  long long tiles = (long long)((N + BNC - 1) / BNC) * ((M + BM - 1) / BM) * batch;
+  int ksplit = 1;
+  if (work && K > 4 * BKC) {
+    int want = (int)std::max<long long>(1, (304 + tiles - 1) / tiles);
+    if (K > 64 * BKC) want = std::max(want, K / (32 * BKC));
+    ksplit = std::min(want, K / (4 * BKC));
+    while (ksplit > 1 && sizeof(float2) * (size_t)ksplit * batch * M * N > work_bytes) --ksplit;
+  }
+  int kchunk = ((K + ksplit - 1) / ksplit + BKC - 1) / BKC * BKC;
+  ksplit = (K + kchunk - 1) / kchunk;
   TcArgs a{M, N, K, A, lda, sA, a64, opa == 'C' ? 1 : 0, B, ldb, sB, b64, opb == 'C' ? 1 : 0,
-           C, ldc, sC, c64};
+           C, ldc, sC, c64, ksplit, kchunk, reinterpret_cast<float2*>(work)};
   COUNT_LAUNCH(1);
   // algorithmic work of the complex product: 8 M N K real flops; bytes: one
   // read of each operand and one write of C at their storage widths
