@@ -374,8 +374,11 @@ __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2*
 }
 
 // ---------------------------------------------------------------- Cholesky
-// one CTA per bond: R = L L^dag (lower, FP64 complex), R overwritten by L;
-// pivots below tiny * max diag are floored and flagged numerically
+// one CTA per bond: R + delta 1 = L L^dag (lower, FP64 complex), R overwritten
+// by L.  delta = 1e-12 max diag(R) regularises bond states the truncated right
+// part cannot reach (null directions of R that a sampled state never
+// occupies); the weights q_p then change by O(delta / lambda) relative.  A
+// pivot that is still not positive flags ST_NUMERIC.
 __global__ void chol_kernel(double2* __restrict__ base, const long long* __restrict__ off,
                             const int* __restrict__ Dv, int b0, int* status) {
   const int b = b0 + blockIdx.x;
@@ -389,11 +392,14 @@ __global__ void chol_kernel(double2* __restrict__ base, const long long* __restr
     dmax = m;
   }
   __syncthreads();
+  const double delta = 1e-12 * dmax;
+  for (int i = tid; i < D; i += nt) R[(long long)i * D + i].x += delta;
+  __syncthreads();
   for (int k = 0; k < D; ++k) {
     double akk = R[(long long)k * D + k].x;
-    if (!(akk > 1e-14 * dmax)) {
+    if (!(akk > 0.0)) {
       if (tid == 0) set_status(status, ST_NUMERIC);
-      akk = fmax(1e-14 * dmax, 1e-300);
+      akk = fmax(delta, 1e-300);
     }
     const double lkk = sqrt(akk), il = 1.0 / lkk;
     __syncthreads();
