@@ -41,7 +41,18 @@ struct StageTimer {
     on = e && e[0] == '1';
     mark("start");
   }
+  int* dbg_status = nullptr;       // GBSMPS_DEBUG=1: status word checked at every mark
+  std::string failed_stage;
   void mark(const char* name) {
+    if (dbg_status && failed_stage.empty()) {
+      int st = 0;
+      cudaMemcpyAsync(&st, dbg_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      if (st) {
+        failed_stage = name;
+        fprintf(stderr, "[gbsmps] device status %d raised in stage '%s'\n", st, name);
+      }
+    }
     if (!on) return;
     cudaEvent_t e;
     cudaEventCreate(&e);
@@ -147,6 +158,10 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                gbsmps_mps_t* out) {
   cudaStream_t s = c->stream;
   StageTimer tm(s);
+  {
+    const char* dbg = getenv("GBSMPS_DEBUG");
+    if (dbg && dbg[0] == '1') tm.dbg_status = c->d_status;
+  }
   auto* M = new gbsmps_mps();
   std::unique_ptr<gbsmps_mps> guard(M);
   M->ctx = c; M->N = N; M->d = o->d; M->chi = o->chi_max; M->precision = o->precision;
