@@ -375,12 +375,13 @@ __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2*
 
 // ---------------------------------------------------------------- Cholesky
 // one CTA per bond: R + delta 1 = L L^dag (lower, FP64 complex), R overwritten
-// by L.  delta = 1e-12 max diag(R) regularises bond states the truncated right
-// part cannot reach (null directions of R that a sampled state never
-// occupies); the weights q_p then change by O(delta / lambda) relative.  A
-// pivot that is still not positive flags ST_NUMERIC.
+// by L.  delta = reg * max diag(R) regularises the bond states the truncated
+// right part barely reaches (near-null directions of R, which the mixed
+// path's FP32-accurate environments resolve only to ~1e-7 |R|): a sampled
+// state carries no weight there, so the weights q_p / Z move by O(delta)
+// absolute.  A pivot that is still not positive flags ST_NUMERIC.
 __global__ void chol_kernel(double2* __restrict__ base, const long long* __restrict__ off,
-                            const int* __restrict__ Dv, int b0, int* status) {
+                            const int* __restrict__ Dv, int b0, double reg, int* status) {
   const int b = b0 + blockIdx.x;
   const int D = Dv[b];
   double2* R = base + off[b];
@@ -392,7 +393,7 @@ __global__ void chol_kernel(double2* __restrict__ base, const long long* __restr
     dmax = m;
   }
   __syncthreads();
-  const double delta = 1e-12 * dmax;
+  const double delta = reg * dmax;
   for (int i = tid; i < D; i += nt) R[(long long)i * D + i].x += delta;
   __syncthreads();
   for (int k = 0; k < D; ++k) {
@@ -545,7 +546,7 @@ cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, 
 cudaError_t launch_chol(double2* base, const long long* off, const int* Dv, int b0, int nb,
                         int* status, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  chol_kernel<<<nb, 512, 0, s>>>(base, off, Dv, b0, status);
+  chol_kernel<<<nb, 512, 0, s>>>(base, off, Dv, b0, 1e-6, status);
   return cudaGetLastError();
 }
 
