@@ -274,7 +274,9 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     CK(cudaStreamSynchronize(s));
     for (int k = 0; k < cnt; ++k) tasks[k].c = cm[k];
     CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * cnt, cudaMemcpyHostToDevice, s));
-    CK(launch_pco(tk.as<SiteTask>(), cnt, o->d, o->precision, scr.as<double2>(), c->d_status, s));
+    // the PCO build stays FP64 in both precisions: on this part it is a few
+    // percent of a step, and the tensors feed FP64 amplitudes and the norm
+    CK(launch_pco(tk.as<SiteTask>(), cnt, o->d, GBSMPS_PREC_FP64, scr.as<double2>(), c->d_status, s));
     COUNT_LAUNCH(1);
     CK(cudaStreamSynchronize(s));   // the task records are reused by the next wave
   }

@@ -273,11 +273,14 @@ cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
   // each chunk keeps >= 4 stages, the partials are summed in FP64
   long long tiles = (long long)((N + BNC - 1) / BNC) * ((M + BM - 1) / BM) * batch;
   int ksplit = 1;
-  if (work && K > 4 * BKC) {
-    int want = (int)std::max<long long>(1, (304 + tiles - 1) / tiles);
-    if (K > 64 * BKC) want = std::max(want, K / (32 * BKC));
-    ksplit = std::min(want, K / (4 * BKC));
-    while (ksplit > 1 && sizeof(float2) * (size_t)ksplit * batch * M * N > work_bytes) --ksplit;
+  (void)tiles;
+  if (work && K > BKC) {
+    // FP64 reduction of every 16-deep stage: the FP32 tensor-core
+    // accumulation never runs longer than one stage (halved while the
+    // partials do not fit the workspace)
+    ksplit = (K + BKC - 1) / BKC;
+    while (ksplit > 1 && sizeof(float2) * (size_t)ksplit * batch * M * N > work_bytes)
+      ksplit = (ksplit + 1) / 2;
   }
   int kchunk = ((K + ksplit - 1) / ksplit + BKC - 1) / BKC * BKC;
   ksplit = (K + kchunk - 1) / kchunk;
