@@ -295,9 +295,12 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   const int d = o->d;
   const bool mixed = o->precision == GBSMPS_PREC_MIXED;
   if (mixed) {
-    // energy gauge (float2 tensors) and split-BF16 tensor-core environments
-    CK(M->tens_mixed.alloc(sizeof(float2) * tot, s));
-    float2* Ah = M->tens_mixed.as<float2>();
+    // energy gauge (FP64) and tensor-core environments: four bf16 planes per
+    // operand (32-bit operands, the 10 products of total order <= 3), FP32
+    // accumulation per 16-deep stage, stages summed in FP64; the error per
+    // environment step (~1e-9) no longer limits the norm of a 1000-site chain
+    CK(M->tens_mixed.alloc(sizeof(double2) * tot, s));
+    double2* Ah = M->tens_mixed.as<double2>();
     for (int m = 0; m < N; ++m) {
       CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
                              ba.E + (size_t)m * cap, ba.E + (size_t)(m + 1) * cap,
@@ -305,16 +308,15 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
       COUNT_LAUNCH(1);
     }
     tm.mark("energy_gauge");
-    float2* Xf = reinterpret_cast<float2*>(X);
     const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
     DevBuf kw;
     CK(kw.alloc(wbytes, s));
     for (int m = N - 1; m >= 0; --m) {
       int Dl = M->D[m], Dr = M->D[m + 1];
-      const float2* A = Ah + M->toff[m];
-      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, A, 0, Dr, 0, R + M->eoff[m + 1], 1, Dr, 0,
-                         Xf, 0, Dr, 0, 1, s, kw.p, wbytes));
-      CK(launch_zgemm_tc(6, 'N', 'C', Dl, Dl, d * Dr, Xf, 0, d * Dr, 0, A, 0, d * Dr, 0,
+      const double2* A = Ah + M->toff[m];
+      CK(launch_zgemm_tc(10, 'N', 'N', Dl * d, Dr, Dr, A, 1, Dr, 0, R + M->eoff[m + 1], 1, Dr, 0,
+                         X, 1, Dr, 0, 1, s, kw.p, wbytes));
+      CK(launch_zgemm_tc(10, 'N', 'C', Dl, Dl, d * Dr, X, 1, d * Dr, 0, A, 1, d * Dr, 0,
                          R + M->eoff[m], 1, Dl, 0, 1, s, kw.p, wbytes));
     }
     kw.release();
@@ -346,7 +348,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   COUNT_LAUNCH(2);
   if (mixed) {   // the normalised first tensor in the energy gauge (D_0 = 1)
     CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], ba.E, ba.E + cap,
-                           M->tens_mixed.as<float2>(), s));
+                           M->tens_mixed.as<double2>(), s));
     COUNT_LAUNCH(1);
   }
   tm.mark("normalise");
@@ -387,12 +389,12 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
     CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
     CK(kw2.alloc(wbytes2, s));
-    const float2* Ah = M->tens_mixed.as<float2>();
+    const double2* Ah = M->tens_mixed.as<double2>();
     for (int m = 0; m < N; ++m) {
       const int Dl = M->D[m], Dr = M->D[m + 1];
       float2* T = tb.as<float2>();
       float2* At = ab2.as<float2>();
-      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 0, Dr, 0,
+      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
                          M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
                          kw2.p, wbytes2));
       const float2* src = T;

@@ -196,7 +196,7 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        uint64_t counter0, float2* vnew, uint8_t* out, int N,
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
-                                const double* Er, float2* Ah, cudaStream_t s);
+                                const double* Er, double2* Ah, cudaStream_t s);
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_bf16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);

@@ -546,7 +546,7 @@ cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, 
 cudaError_t launch_chol(double2* base, const long long* off, const int* Dv, int b0, int nb,
                         int* status, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  chol_kernel<<<nb, 512, 0, s>>>(base, off, Dv, b0, 1e-6, status);
+  chol_kernel<<<nb, 512, 0, s>>>(base, off, Dv, b0, 1e-9, status);
   return cudaGetLastError();
 }
 

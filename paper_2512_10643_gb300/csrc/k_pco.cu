@@ -249,15 +249,13 @@ __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n,
 // this diagonal gauge makes the environments well conditioned in FP32)
 __global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d, int Dr,
                                     const double* __restrict__ El, const double* __restrict__ Er,
-                                    float2* __restrict__ Ah) {
+                                    double2* __restrict__ Ah) {
   size_t n = (size_t)Dl * d * Dr;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
        idx += (size_t)gridDim.x * blockDim.x) {
     int a = idx / ((size_t)d * Dr), b = idx % Dr;
     double el = Dl > 1 ? El[a] : 0.0, er = Dr > 1 ? Er[b] : 0.0;
-    double s = exp(-0.5 * (er - el));
-    double2 v = A[idx];
-    Ah[idx] = make_float2((float)(v.x * s), (float)(v.y * s));
+    Ah[idx] = cscale(A[idx], exp(-0.5 * (er - el)));
   }
 }
 
@@ -285,7 +283,7 @@ cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int ca
 }
 
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
-                                const double* Er, float2* Ah, cudaStream_t s) {
+                                const double* Er, double2* Ah, cudaStream_t s) {
   size_t n = (size_t)Dl * d * Dr;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 4096) blocks = 4096;

@@ -30,23 +30,22 @@ struct TcArgs {
   float2* part;
 };
 
-__device__ __forceinline__ float2 ld_c(const void* p, long long idx, int is64) {
-  if (is64) {
-    double2 v = reinterpret_cast<const double2*>(p)[idx];
-    return make_float2((float)v.x, (float)v.y);
-  }
-  return reinterpret_cast<const float2*>(p)[idx];
+__device__ __forceinline__ double2 ld_c(const void* p, long long idx, int is64) {
+  if (is64) return reinterpret_cast<const double2*>(p)[idx];
+  float2 v = reinterpret_cast<const float2*>(p)[idx];
+  return make_double2(v.x, v.y);
 }
 
+// x = o[0] + o[1] + ... (each a bf16 rounding of the remaining residual,
+// residuals formed exactly in FP64): NS planes carry ~8 NS bits
 template <int NS>
-__device__ __forceinline__ void split(float x, __nv_bfloat16 (&o)[NS]) {
-  __nv_bfloat16 h = __float2bfloat16_rn(x);
-  o[0] = h;
-  float r = x - __bfloat162float(h);
-  if (NS > 1) {
-    __nv_bfloat16 m = __float2bfloat16_rn(r);
-    o[1] = m;
-    if (NS > 2) o[2] = __float2bfloat16_rn(r - __bfloat162float(m));
+__device__ __forceinline__ void split(double x, __nv_bfloat16 (&o)[NS]) {
+  double r = x;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    __nv_bfloat16 h = __double2bfloat16(r);
+    o[s] = h;
+    r -= (double)__bfloat162float(h);
   }
 }
 
@@ -61,7 +60,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 
 template <int NT>
 __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
-  constexpr int NS = NT == 3 ? 2 : 3;
+  constexpr int NS = NT == 3 ? 2 : (NT == 6 ? 3 : 4);
   extern __shared__ __align__(16) unsigned char smraw[];
   auto As = reinterpret_cast<__nv_bfloat16(*)[BM][LDS]>(smraw);
   auto Bs = reinterpret_cast<__nv_bfloat16(*)[BNR][LDS]>(smraw + sizeof(__nv_bfloat16) * NS * BM * LDS);
@@ -85,7 +84,7 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
 
-  float2 ra[8], rb[4];
+  double2 ra[8], rb[4];
   // element coordinates owned by this thread
   auto load_stage = [&](int k0) {
 #pragma unroll
@@ -94,7 +93,7 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
       if (p.opa == 0) { i = tid >> 1; kc = (tid & 1) * 8 + j; }
       else { kc = tid >> 4; i = (tid & 15) * 8 + j; }
       int gi = i0 + i, gk = k0 + kc;
-      float2 v = make_float2(0.f, 0.f);
+      double2 v = make_double2(0.0, 0.0);
       if (gi < p.M && gk < kend) {
         if (p.opa == 0) v = ld_c(A, (long long)gi * p.lda + gk, p.a64);
         else { v = ld_c(A, (long long)gk * p.lda + gi, p.a64); v.y = -v.y; }
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
       if (p.opb == 0) { kc = tid >> 4; nc = (tid & 15) * 4 + j; }
       else { nc = tid >> 2; kc = (tid & 3) * 4 + j; }
       int gn = n0 + nc, gk = k0 + kc;
-      float2 v = make_float2(0.f, 0.f);
+      double2 v = make_double2(0.0, 0.0);
       if (gn < p.N && gk < kend) {
         if (p.opb == 0) v = ld_c(B, (long long)gk * p.ldb + gn, p.b64);
         else { v = ld_c(B, (long long)gn * p.ldb + gk, p.b64); v.y = -v.y; }
@@ -176,12 +175,12 @@ __global__ void __launch_bounds__(256) zgemm_tc_kernel(TcArgs p) {
           bf[s][nt][1] = *reinterpret_cast<const uint32_t*>(&Bs[s][c][kk + 8 + 2 * t]);
         }
       }
-      // small terms first
-      constexpr int NTERM = NT;
-      constexpr int ta[6] = {2, 1, 0, 1, 0, 0};
-      constexpr int tb[6] = {0, 1, 2, 0, 1, 0};
+      // products of total order < NS, small terms first (NT = 3, 6, 10 keep
+      // the last NT entries)
+      constexpr int ta[10] = {3, 2, 1, 0, 2, 1, 0, 1, 0, 0};
+      constexpr int tb[10] = {0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
 #pragma unroll
-      for (int q = (NTERM == 6 ? 0 : 3); q < 6; ++q) {
+      for (int q = 10 - NT; q < 10; ++q) {
         const int sa = ta[q], sb = tb[q];
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt)
@@ -238,7 +237,7 @@ __global__ void splitk_reduce_kernel(const float2* __restrict__ part, int ksplit
 
 template <int NT>
 cudaError_t run(const TcArgs& a, int batch, cudaStream_t s) {
-  constexpr int NS = NT == 3 ? 2 : 3;
+  constexpr int NS = NT == 3 ? 2 : (NT == 6 ? 3 : 4);
   size_t smem = sizeof(__nv_bfloat16) * NS * (BM + BNR) * LDS;
   static bool attr = false;
   if (!attr) {
@@ -293,7 +292,8 @@ cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
   double bytes = ((double)M * K * (a64 ? 16 : 8) + (double)K * N * (b64 ? 16 : 8) +
                   (double)M * N * (c64 ? 16 : 8)) * batch;
   g_tc_trace.begin(s);
-  cudaError_t e = nterms == 3 ? run<3>(a, batch, s) : run<6>(a, batch, s);
+  cudaError_t e = nterms == 3 ? run<3>(a, batch, s)
+                : nterms == 6 ? run<6>(a, batch, s) : run<10>(a, batch, s);
   g_tc_trace.end(s, flops, bytes);
   return e;
 }
