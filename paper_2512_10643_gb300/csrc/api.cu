@@ -361,9 +361,20 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                        cudaMemcpyHostToDevice, s));
     CK(M->lchol.alloc(sizeof(double2) * (etot + 8), s));
     CK(M->linv.alloc(sizeof(double2) * (etot + 8), s));
-    CK(cudaMemcpyAsync(M->lchol.p, R, sizeof(double2) * etot, cudaMemcpyDeviceToDevice, s));
-    CK(launch_chol(M->lchol.as<double2>(), M->eoff_dev.as<long long>(), ba.D, 1, N - 1,
-                   c->d_status, s));
+    DevBuf du;                     // regulariser each bond needed (relative)
+    CK(du.alloc(sizeof(double) * (N + 1), s));
+    CK(cudaMemsetAsync(du.p, 0, sizeof(double) * (N + 1), s));
+    CK(launch_chol(R, M->lchol.as<double2>(), M->eoff_dev.as<long long>(), ba.D, 1, N - 1,
+                   du.as<double>(), c->d_status, s));
+    if (tm.on) {
+      std::vector<double> h(N + 1);
+      cudaMemcpyAsync(h.data(), du.p, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      double mx = 0.0;
+      for (double v : h) mx = std::max(mx, v);
+      fprintf(stderr, "[gbsmps] largest Cholesky regulariser: %.1e of max diag\n", mx);
+    }
+    du.release();
     CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
                     ba.D, 1, N - 1, s));
     COUNT_LAUNCH(2);

@@ -212,8 +212,8 @@ cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, 
                                 uint64_t counter0, __nv_bfloat16* V, long long vpl, int Kpn,
                                 uint8_t* out, int N, uint8_t* flags, double flag_tol,
                                 cudaStream_t s);
-cudaError_t launch_chol(double2* base, const long long* off, const int* Dv, int b0, int nb,
-                        int* status, cudaStream_t s);
+cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
+                        int b0, int nb, double* dused, int* status, cudaStream_t s);
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
                          int nb, cudaStream_t s);
 // split-BF16 tensor-core complex GEMM (nterms 3 or 6), operands FP64 or FP32

@@ -380,29 +380,38 @@ __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2*
 // path's FP32-accurate environments resolve only to ~1e-7 |R|): a sampled
 // state carries no weight there, so the weights q_p / Z move by O(delta)
 // absolute.  A pivot that is still not positive flags ST_NUMERIC.
-__global__ void chol_kernel(double2* __restrict__ base, const long long* __restrict__ off,
-                            const int* __restrict__ Dv, int b0, double reg, int* status) {
+__global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+                            const long long* __restrict__ off, const int* __restrict__ Dv, int b0,
+                            double* __restrict__ dused, int* status) {
   const int b = b0 + blockIdx.x;
   const int D = Dv[b];
-  double2* R = base + off[b];
+  const double2* Sm = src + off[b];
+  double2* R = dst + off[b];
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double dmax;
   if (tid == 0) {
     double m = 0.0;
-    for (int i = 0; i < D; ++i) m = fmax(m, R[(long long)i * D + i].x);
+    for (int i = 0; i < D; ++i) m = fmax(m, Sm[(long long)i * D + i].x);
     dmax = m;
   }
   __syncthreads();
-  const double delta = reg * dmax;
-  for (int i = tid; i < D; i += nt) R[(long long)i * D + i].x += delta;
-  __syncthreads();
-  for (int k = 0; k < D; ++k) {
-    double akk = R[(long long)k * D + k].x;
-    if (!(akk > 0.0)) {
-      if (tid == 0) set_status(status, ST_NUMERIC);
-      akk = fmax(delta, 1e-300);
+  // the smallest regulariser in 1e-12 .. 1e-4 (x100 steps) that factorises
+  double reg = 1e-12;
+  bool okf = false;
+  double delta = 0.0;
+  for (int attempt = 0; attempt < 5 && !okf; ++attempt, reg *= 100.0) {
+    delta = reg * dmax;
+    for (long long idx = tid; idx < (long long)D * D; idx += nt) {
+      double2 v = Sm[idx];
+      if (idx / D == idx % D) v.x += delta;
+      R[idx] = v;
     }
-    const double lkk = sqrt(akk), il = 1.0 / lkk;
+    __syncthreads();
+    okf = true;
+    for (int k = 0; k < D; ++k) {
+      const double akk = R[(long long)k * D + k].x;
+      if (!(akk > 0.0)) { okf = false; break; }   // same value in every thread
+      const double lkk = sqrt(akk), il = 1.0 / lkk;
     __syncthreads();
     for (int i = k + 1 + tid; i < D; i += nt) R[(long long)i * D + k] = cscale(R[(long long)i * D + k], il);
     if (tid == 0) R[(long long)k * D + k] = cmk(lkk, 0.0);
@@ -417,7 +426,11 @@ __global__ void chol_kernel(double2* __restrict__ base, const long long* __restr
       R[(long long)i * D + j] = v;
     }
     __syncthreads();
+    }
+    __syncthreads();
   }
+  if (!okf && tid == 0) set_status(status, ST_NUMERIC);
+  if (tid == 0) dused[b] = okf ? delta / fmax(dmax, 1e-300) : -1.0;
   for (long long idx = tid; idx < (long long)D * D; idx += nt) {
     const int i = idx / D, j = idx % D;
     if (j > i) R[idx] = cmk(0.0, 0.0);
@@ -543,10 +556,10 @@ cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol(double2* base, const long long* off, const int* Dv, int b0, int nb,
-                        int* status, cudaStream_t s) {
+cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
+                        int b0, int nb, double* dused, int* status, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  chol_kernel<<<nb, 512, 0, s>>>(base, off, Dv, b0, 1e-9, status);
+  chol_kernel<<<nb, 512, 0, s>>>(src, dst, off, Dv, b0, dused, status);
   return cudaGetLastError();
 }
 
