@@ -295,10 +295,10 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   const int d = o->d;
   const bool mixed = o->precision == GBSMPS_PREC_MIXED;
   if (mixed) {
-    // energy gauge (FP64) and tensor-core environments: four bf16 planes per
-    // operand (32-bit operands, the 10 products of total order <= 3), FP32
-    // accumulation per 16-deep stage, stages summed in FP64; the error per
-    // environment step (~1e-9) no longer limits the norm of a 1000-site chain
+    // energy gauge (FP64) and environments in double-float arithmetic on the
+    // FP32 pipes (~44-bit): the chain of N dependent products sets the norm,
+    // so its per-step error must stay far below the tensor cores' FP32
+    // accumulation error
     CK(M->tens_mixed.alloc(sizeof(double2) * tot, s));
     double2* Ah = M->tens_mixed.as<double2>();
     for (int m = 0; m < N; ++m) {
@@ -314,10 +314,10 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
     for (int m = N - 1; m >= 0; --m) {
       int Dl = M->D[m], Dr = M->D[m + 1];
       const double2* A = Ah + M->toff[m];
-      CK(launch_zgemm_tc(10, 'N', 'N', Dl * d, Dr, Dr, A, 1, Dr, 0, R + M->eoff[m + 1], 1, Dr, 0,
-                         X, 1, Dr, 0, 1, s, kw.p, wbytes));
-      CK(launch_zgemm_tc(10, 'N', 'C', Dl, Dl, d * Dr, X, 1, d * Dr, 0, A, 1, d * Dr, 0,
-                         R + M->eoff[m], 1, Dl, 0, 1, s, kw.p, wbytes));
+      CK(launch_zgemm_df64('N', 'N', Dl * d, Dr, Dr, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, X, Dr, 0,
+                           1, s, kw.p, wbytes));
+      CK(launch_zgemm_df64('N', 'C', Dl, Dl, d * Dr, X, d * Dr, 0, A, d * Dr, 0, R + M->eoff[m], Dl,
+                           0, 1, s, kw.p, wbytes));
     }
     kw.release();
   } else {

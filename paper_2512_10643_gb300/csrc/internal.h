@@ -197,6 +197,11 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
                                 const double* Er, double2* Ah, cudaStream_t s);
+// complex GEMM in double-float arithmetic (k_df64.cu), FP64 operands/result
+cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
+                              long long sA, const double2* B, long long ldb, long long sB,
+                              double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
+                              void* work = nullptr, size_t work_bytes = 0);
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_bf16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);

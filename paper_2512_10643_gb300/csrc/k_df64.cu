@@ -1,0 +1,179 @@
+// Complex GEMM in double-float arithmetic on the FP32 pipes.
+//
+// The right environments R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag are a chain of
+// N dependent products; the norm of the state is R_0, so a one-sided error
+// per step (the tensor cores' FP32 accumulation) compounds over the chain.
+// GB300 runs FP64 at a small fraction of its FP32 rate, so these products use
+// double-float numbers x = hi + lo (two FP32 words, ~44 significant bits):
+// every real multiply-add forms the product exactly with FMA (p = ah bh,
+// e = fma(ah, bh, -p) + ah bl + al bh) and adds it with Knuth's TwoSum.
+// Operands are read in FP64 and split into (hi, lo) on the way to shared
+// memory; partial sums over k-chunks (split-K, for parallelism in the short
+// sequential products) are written as FP64 and reduced in FP64.
+// Tile: 64 x 64 complex outputs, 8 complex k per stage, 256 threads of 4 x 4.
+#include "internal.h"
+#include <algorithm>
+
+namespace {
+
+constexpr int DM = 64, DN = 64, DK = 8;
+
+struct Df { float h, l; };
+
+__device__ __forceinline__ void df_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float t = h + p;
+  const float v = t - h;
+  const float err = (h - (t - v)) + (p - v);
+  l += err + e;
+  h = t;
+}
+
+__device__ __forceinline__ Df df_split(double x) {
+  Df r;
+  r.h = (float)x;
+  r.l = (float)(x - (double)r.h);
+  return r;
+}
+
+struct DfArgs {
+  int M, N, K, opa, opb;
+  const double2* A; long long lda, sA;
+  const double2* B; long long ldb, sB;
+  double2* C; long long ldc, sC;
+  int ksplit, kchunk;
+  double2* part;
+};
+
+__global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
+  // re/im, hi/lo split operands
+  __shared__ float As[DK][DM][4];
+  __shared__ float Bs[DK][DN][4];
+  const long long bz = blockIdx.z / p.ksplit;
+  const int kz = blockIdx.z % p.ksplit;
+  const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
+  const int i0 = blockIdx.y * DM, j0 = blockIdx.x * DN;
+  const double2* A = p.A + bz * p.sA;
+  const double2* B = p.B + bz * p.sB;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float ah[4][4][2], al[4][4][2];   // [row][col][re/im] hi and lo accumulators
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      ah[r][c][0] = ah[r][c][1] = 0.f;
+      al[r][c][0] = al[r][c][1] = 0.f;
+    }
+  for (int k0 = kbeg; k0 < kend; k0 += DK) {
+    for (int e = tid; e < DK * DM; e += 256) {
+      int kk, ii;
+      if (p.opa == 0) { ii = e / DK; kk = e % DK; } else { kk = e / DM; ii = e % DM; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (gi < p.M && gk < kend) {
+        if (p.opa == 0) v = A[(long long)gi * p.lda + gk];
+        else { v = A[(long long)gk * p.lda + gi]; v.y = -v.y; }
+      }
+      const Df re = df_split(v.x), im = df_split(v.y);
+      As[kk][ii][0] = re.h; As[kk][ii][1] = re.l; As[kk][ii][2] = im.h; As[kk][ii][3] = im.l;
+    }
+    for (int e = tid; e < DK * DN; e += 256) {
+      int kk, jj;
+      if (p.opb == 0) { kk = e / DN; jj = e % DN; } else { jj = e / DK; kk = e % DK; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (gj < p.N && gk < kend) {
+        if (p.opb == 0) v = B[(long long)gk * p.ldb + gj];
+        else { v = B[(long long)gj * p.ldb + gk]; v.y = -v.y; }
+      }
+      const Df re = df_split(v.x), im = df_split(v.y);
+      Bs[kk][jj][0] = re.h; Bs[kk][jj][1] = re.l; Bs[kk][jj][2] = im.h; Bs[kk][jj][3] = im.l;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < DK; ++kk) {
+      float a[4][4], b[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 v = *reinterpret_cast<const float4*>(&As[kk][ty + 16 * r][0]);
+        a[r][0] = v.x; a[r][1] = v.y; a[r][2] = v.z; a[r][3] = v.w;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx + 16 * c][0]);
+        b[c][0] = v.x; b[c][1] = v.y; b[c][2] = v.z; b[c][3] = v.w;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          // re += ar br - ai bi ; im += ar bi + ai br
+          df_mac(ah[r][c][0], al[r][c][0], a[r][0], a[r][1], b[c][0], b[c][1]);
+          df_mac(ah[r][c][0], al[r][c][0], -a[r][2], -a[r][3], b[c][2], b[c][3]);
+          df_mac(ah[r][c][1], al[r][c][1], a[r][0], a[r][1], b[c][2], b[c][3]);
+          df_mac(ah[r][c][1], al[r][c][1], a[r][2], a[r][3], b[c][0], b[c][1]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gi = i0 + ty + 16 * r;
+    if (gi >= p.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gj = j0 + tx + 16 * c;
+      if (gj >= p.N) continue;
+      const double2 v = make_double2((double)ah[r][c][0] + (double)al[r][c][0],
+                                     (double)ah[r][c][1] + (double)al[r][c][1]);
+      if (p.ksplit > 1) p.part[((long long)blockIdx.z * p.M + gi) * p.N + gj] = v;
+      else p.C[bz * p.sC + (long long)gi * p.ldc + gj] = v;
+    }
+  }
+}
+
+__global__ void df_reduce_kernel(const double2* __restrict__ part, int ksplit, int batch, int M,
+                                 int N, double2* C, long long ldc, long long sC) {
+  const long long n = (long long)batch * M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / ((long long)M * N), r = (i / N) % M, c = i % N;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < ksplit; ++k) s = cadd(s, part[((b * ksplit + k) * M + r) * N + c]);
+    C[b * sC + r * ldc + c] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
+                              long long sA, const double2* B, long long ldb, long long sB,
+                              double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
+                              void* work, size_t work_bytes) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  const long long tiles = (long long)((M + DM - 1) / DM) * ((N + DN - 1) / DN) * batch;
+  int ksplit = 1;
+  if (work && K > 4 * DK) {
+    // enough CTAs to cover the GPU twice, chunks of >= 4 stages
+    ksplit = (int)std::max<long long>(1, (304 + tiles - 1) / tiles);
+    ksplit = std::min(ksplit, K / (4 * DK));
+    while (ksplit > 1 && sizeof(double2) * (size_t)ksplit * batch * M * N > work_bytes) --ksplit;
+  }
+  int kchunk = ((K + ksplit - 1) / ksplit + DK - 1) / DK * DK;
+  ksplit = (K + kchunk - 1) / kchunk;
+  DfArgs a{M, N, K, opa == 'C' ? 1 : 0, opb == 'C' ? 1 : 0, A, lda, sA, B, ldb, sB, C, ldc, sC,
+           ksplit, kchunk, reinterpret_cast<double2*>(work)};
+  dim3 grid((N + DN - 1) / DN, (M + DM - 1) / DM, batch * ksplit);
+  zgemm_df64_kernel<<<grid, 256, 0, s>>>(a);
+  COUNT_LAUNCH(1);
+  if (ksplit > 1) {
+    const long long n = (long long)batch * M * N;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
+    df_reduce_kernel<<<blocks, 256, 0, s>>>(a.part, ksplit, batch, M, N, C, ldc, sC);
+    COUNT_LAUNCH(1);
+  }
+  return cudaGetLastError();
+}
