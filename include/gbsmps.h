@@ -165,6 +165,36 @@ int gbsmps_build_site(gbsmps_ctx_t ctx, int32_t nl, int32_t nr, int32_t d,
                       const uint8_t* occ_l, int32_t Dr, const uint8_t* occ_r,
                       int32_t precision, double* out, int mem_kind);
 
+/* Allocation-free variant of gbsmps_build_site.  The paper has no
+ * counterpart; this is a service of the library.  It computes exactly what
+ * gbsmps_build_site computes, but performs no device allocation, for callers
+ * that must not allocate while they run: a serving process that reserved its
+ * device memory up front (for resident tensors and admission by free memory)
+ * and must not have a call fail or fragment that reserve, latency-critical
+ * loops for which cudaMalloc / cudaFree are unacceptable because they can
+ * synchronise the device and stall other streams, and hosts whose own
+ * allocator owns all device memory.
+ * All pointers are device memory of the context's GPU: Qm ((nl+1+nr)^2
+ * complex, row-major, mode order (r_1..r_nl, a, l_1..l_nr)), occ_l (Dl x nl
+ * uint8) and occ_r (Dr x nr uint8), vacuum first and closed under removing
+ * one quantum, out (Dl x d x Dr complex128, scaled by c).
+ * Working memory is one static device array of GBSMPS_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits.
+ * Limit: Dl and Dr <= GBSMPS_NOALLOC_MAX_D; larger sizes are rejected with
+ * GBSMPS_ERR_BOUNDS before any GPU work.  The first call on a device looks up
+ * the array's device address once (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * reuses the same array, which keeps the previous call's contents (a call
+ * rewrites everything it reads), so calls that overlap on the GPU (from
+ * several streams or host threads) race and must be serialised by the
+ * caller.  Synchronises the context's stream.  Errors: ARG, BOUNDS, CUDA. */
+#define GBSMPS_NOALLOC_MAX_D 128
+#define GBSMPS_NOALLOC_SCRATCH_BYTES (1280 * 1024)
+int gbsmps_build_site_noalloc(gbsmps_ctx_t ctx, int32_t nl, int32_t nr, int32_t d,
+                              const double* Qm, double c, int32_t Dl, const uint8_t* occ_l,
+                              int32_t Dr, const uint8_t* occ_r, int32_t precision,
+                              double* out);
+
 /* Text of an error code (static storage). */
 const char* gbsmps_strerror(int code);
 /* One-line detail of the last error on the calling thread. */

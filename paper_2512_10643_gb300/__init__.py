@@ -66,6 +66,7 @@ def lib():
         "gbsmps_strerror": (C.c_char_p, [C.c_int]),
         "gbsmps_last_error_detail": (C.c_char_p, []),
         "gbsmps_launch_count": (i64, [vp]),
+        "gbsmps_build_site_noalloc": (C.c_int, [vp, i32, i32, i32, vp, dbl, i32, vp, i32, vp, i32, vp]),
         "gbsmps_trace": (C.c_int, [vp, C.c_int]),
         "gbsmps_trace_read": (C.c_int, [vp, vp, vp, vp, vp]),
     }
@@ -218,6 +219,22 @@ def gbsmps_build_site(ctx, Qm, c, occ_l, occ_r, d, precision=PREC_FP64):
                                    occ_l.ctypes.data if nl else None, Dr,
                                    occ_r.ctypes.data if nr else None, precision,
                                    out.ctypes.data, MEM_HOST))
+    return out
+
+
+def gbsmps_build_site_noalloc(ctx, Qm, c, occ_l, occ_r, d, out, precision=PREC_FP64):
+    """Allocation-free single-site build.  Qm (complex (n, n) as float64
+    (n, n, 2)), occ_l (Dl, nl) and occ_r (Dr, nr) uint8, and out (Dl, d, Dr, 2)
+    float64 are contiguous CUDA tensors; the library allocates nothing."""
+    nl, nr = occ_l.shape[1], occ_r.shape[1]
+    Dl, Dr = occ_l.shape[0], occ_r.shape[0]
+    ptrs = [_ptr(x) for x in (Qm, occ_l, occ_r, out)]
+    if any(k != MEM_DEVICE for _, k in ptrs):
+        raise ValueError("all buffers must be device tensors")
+    _check(lib().gbsmps_build_site_noalloc(ctx, nl, nr, d, C.c_void_p(ptrs[0][0]), float(c), Dl,
+                                           C.c_void_p(ptrs[1][0] if nl else 0), Dr,
+                                           C.c_void_p(ptrs[2][0] if nr else 0), precision,
+                                           C.c_void_p(ptrs[3][0])))
     return out
 
 

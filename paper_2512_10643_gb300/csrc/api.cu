@@ -765,6 +765,17 @@ int gbsmps_build_site(gbsmps_ctx_t c, int32_t nl, int32_t nr, int32_t d, const d
   return sync_status(c);
 }
 
+int gbsmps_build_site_noalloc(gbsmps_ctx_t c, int32_t nl, int32_t nr, int32_t d, const double* Qm,
+                              double cscale, int32_t Dl, const uint8_t* occ_l, int32_t Dr,
+                              const uint8_t* occ_r, int32_t precision, double* out) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  const char* detail = "";
+  int rc = noalloc_build_site(c->device, c->stream, c->d_status, nl, nr, d, Qm, cscale, Dl, occ_l,
+                              Dr, occ_r, precision, out, &detail);
+  if (rc) return fail(rc, detail);
+  return GBSMPS_OK;
+}
+
 const char* gbsmps_strerror(int code) {
   switch (code) {
     case GBSMPS_OK: return "ok";

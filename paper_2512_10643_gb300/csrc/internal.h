@@ -197,6 +197,11 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
                                 const double* Er, double2* Ah, cudaStream_t s);
+// allocation-free single-site build (noalloc.cu)
+int noalloc_build_site(int device, cudaStream_t s, int* status_dev, int32_t nl, int32_t nr,
+                       int32_t d, const double* Qm, double cscale, int32_t Dl,
+                       const uint8_t* occ_l, int32_t Dr, const uint8_t* occ_r, int32_t precision,
+                       double* out, const char** detail);
 // complex GEMM in double-float arithmetic (k_df64.cu), FP64 operands/result
 cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
                               long long sA, const double2* B, long long ldb, long long sB,
