@@ -204,8 +204,8 @@ const char* gbsmps_last_error_detail(void);
  * contexts), for launch accounting. */
 int64_t gbsmps_launch_count(gbsmps_ctx_t ctx);
 
-/* Tracing of the dominant kernel, the split-BF16 tensor-core complex GEMM
- * (environments and sampling of the mixed path): gbsmps_trace(ctx, 1) clears
+/* Tracing of the dominant kernel, the tcgen05 split-BF16 complex GEMM of the
+ * mixed-precision sampler (one launch per site): gbsmps_trace(ctx, 1) clears
  * the record and records a CUDA event pair around every later launch on the
  * launching stream; gbsmps_trace(ctx, 0) stops recording.  gbsmps_trace_read
  * synchronises on the recorded events and returns the summed device time,

@@ -136,7 +136,7 @@ struct KernelTrace {
     ev.clear(); flops = bytes = 0.0; launches = 0;
   }
 };
-extern KernelTrace g_tc_trace;    // the split-BF16 tensor-core GEMM
+extern KernelTrace g_tc_trace;    // the tcgen05 sampler GEMM (dominant kernel)
 
 // ---- launchers (each returns cudaError_t of the launch) -------------------
 // g_kernel_launches counts every kernel the library enqueues.

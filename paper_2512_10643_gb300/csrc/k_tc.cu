@@ -291,9 +291,7 @@ cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
   double flops = 8.0 * M * (double)N * K * batch;
   double bytes = ((double)M * K * (a64 ? 16 : 8) + (double)K * N * (b64 ? 16 : 8) +
                   (double)M * N * (c64 ? 16 : 8)) * batch;
-  g_tc_trace.begin(s);
-  cudaError_t e = nterms == 3 ? run<3>(a, batch, s)
-                : nterms == 6 ? run<6>(a, batch, s) : run<10>(a, batch, s);
-  g_tc_trace.end(s, flops, bytes);
-  return e;
+  (void)flops;
+  (void)bytes;
+  return nterms == 3 ? run<3>(a, batch, s) : nterms == 6 ? run<6>(a, batch, s) : run<10>(a, batch, s);
 }
