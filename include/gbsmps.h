@@ -52,6 +52,8 @@ extern "C" {
 #define GBSMPS_ERR_CUDA 7           /* CUDA runtime error                        */
 #define GBSMPS_ERR_NUMERIC 8        /* non-finite value, singular matrix         */
 #define GBSMPS_ERR_STATE 9          /* object in the wrong state for the call    */
+#define GBSMPS_ERR_TIMEOUT 10       /* a bounded wait (device mbarrier, server
+                                       wait) ran out                            */
 
 #define GBSMPS_MEM_HOST 0
 #define GBSMPS_MEM_DEVICE 1
@@ -59,7 +61,9 @@ extern "C" {
 /* Arithmetic of the tensor build, environments and sampling.  The Gaussian
  * SVD, symplectic orthogonalisation and normalisation are FP64 in both. */
 #define GBSMPS_PREC_FP64 0
-#define GBSMPS_PREC_MIXED 1   /* FP32 PCO build, split-BF16 tensor-core GEMMs */
+#define GBSMPS_PREC_MIXED 1   /* double-float environments (FP32 pipes) and
+                                 split-FP16 tcgen05 sampling GEMMs; the PCO
+                                 build stays FP64 */
 
 /* Largest number of entangled mode pairs at one cut (n_e of Sec. II A). */
 #define GBSMPS_NE_MAX 24
@@ -204,7 +208,7 @@ const char* gbsmps_last_error_detail(void);
  * contexts), for launch accounting. */
 int64_t gbsmps_launch_count(gbsmps_ctx_t ctx);
 
-/* Tracing of the dominant kernel, the tcgen05 split-BF16 complex GEMM of the
+/* Tracing of the dominant kernel, the tcgen05 split-FP16 complex GEMM of the
  * mixed-precision sampler (one launch per site): gbsmps_trace(ctx, 1) clears
  * the record and records a CUDA event pair around every later launch on the
  * launching stream; gbsmps_trace(ctx, 0) stops recording.  gbsmps_trace_read
@@ -215,6 +219,79 @@ int64_t gbsmps_launch_count(gbsmps_ctx_t ctx);
 int gbsmps_trace(gbsmps_ctx_t ctx, int enable);
 int gbsmps_trace_read(gbsmps_ctx_t ctx, double* total_ms, int64_t* launches,
                       double* flops, double* bytes);
+
+/* ---- serving: continuous batching of build + sampling requests -----------
+ * Not a step of the paper's method: a request loop around it.  A server owns
+ * `slots` worker threads, each with its own non-blocking CUDA stream and
+ * context on `device`.  Requests queue in arrival order; a free slot admits
+ * the first of the next 8 queued requests whose device-memory estimate
+ * (gbsmps_estimate_bytes) fits the budget that the jobs on the device leave
+ * free, and a request passed over 32 times blocks later ones until it fits.
+ * An admitted job runs build (gbsmps_build_from_cov, host Gamma) and sampling
+ * (gbsmps_sample, Philox keyed by seed/counter0) on its slot's stream, with
+ * the MPS resident on the device in between, and writes the S x N patterns to
+ * req.out; jobs on different slots overlap on the GPU, and a job's result is
+ * bitwise the result of the same calls made alone.  The caller keeps
+ * req.gamma and req.out valid until the job is done.  Latency is submit ->
+ * done on the server's monotonic clock. */
+typedef struct gbsmps_server* gbsmps_server_t;
+
+typedef struct {
+  int32_t slots;                 /* concurrent jobs (1..64), default 4          */
+  size_t hbm_budget;             /* bytes the admitted jobs may hold together;
+                                    0: 80% of the free device memory at creation;
+                                    capped at 90% of it                          */
+  double simulate_s_per_tensor;  /* > 0: jobs do not touch a GPU, each sleeps
+                                    N x this many seconds and writes zeros
+                                    (tests of the scheduler without a device);
+                                    needs hbm_budget > 0                        */
+} gbsmps_server_opts;
+
+typedef struct {
+  const double* gamma;   /* host 2N x 2N covariance (xxpp, row-major)           */
+  int32_t N;
+  gbsmps_opts opts;
+  int64_t samples;       /* S >= 0                                              */
+  uint64_t seed, counter0;
+  uint8_t* out;          /* host S x N uint8, written by the job                */
+} gbsmps_request;
+
+typedef struct {
+  int32_t state;         /* 0 queued, 1 running, 2 done, 3 failed               */
+  int32_t error;         /* the job's error code (0 when done)                  */
+  int32_t slot;          /* slot that ran it, -1 before admission               */
+  double t_submit, t_admit, t_done;   /* seconds since server creation          */
+  size_t hbm_bytes;      /* admission estimate                                  */
+  char detail[128];      /* error detail of a failed job                        */
+} gbsmps_job_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, running, queued;
+  double p50_ms, p99_ms, mean_ms;   /* submit -> done, completed jobs (nearest rank) */
+  double busy_s;                    /* first admission -> last completion       */
+  double tensors, samples;          /* totals over completed jobs               */
+  size_t hbm_in_use, hbm_budget, hbm_peak;
+} gbsmps_server_stats;
+
+int gbsmps_server_opts_default(gbsmps_server_opts* o);
+/* Errors: ARG (slots out of range, bad device), CUDA. */
+int gbsmps_server_create(int device, const gbsmps_server_opts* o, gbsmps_server_t* out);
+/* Queue a request; *id identifies it.  Errors: ARG, OOM (estimate larger than
+ * the whole budget), STATE (server stopping). */
+int gbsmps_server_submit(gbsmps_server_t srv, const gbsmps_request* req, int64_t* id);
+/* Wait for request `id` (timeout_s < 0: no limit); returns the job's error
+ * code, or TIMEOUT.  info (may be NULL) receives its record. */
+int gbsmps_server_wait(gbsmps_server_t srv, int64_t id, double timeout_s, gbsmps_job_info* info);
+/* Wait until no request is queued or running.  Errors: TIMEOUT. */
+int gbsmps_server_drain(gbsmps_server_t srv, double timeout_s);
+int gbsmps_server_stats_read(gbsmps_server_t srv, gbsmps_server_stats* st);
+/* Finish every queued request, stop the workers, free the contexts. */
+int gbsmps_server_destroy(gbsmps_server_t srv);
+
+/* Upper bound of the device bytes one build + sampling call of this size
+ * holds at its peak (every bond at chi_max), as used for admission; 0 for
+ * invalid arguments. */
+size_t gbsmps_estimate_bytes(int32_t N, const gbsmps_opts* opts, int64_t samples);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgbsmps.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "gbsmps.h")
 
 OK, ERR_ARG, ERR_NOT_SYMMETRIC, ERR_NOT_PURE, ERR_OOM = 0, 1, 2, 3, 4
-ERR_NOT_CONVERGED, ERR_BOUNDS, ERR_CUDA, ERR_NUMERIC, ERR_STATE = 5, 6, 7, 8, 9
+ERR_NOT_CONVERGED, ERR_BOUNDS, ERR_CUDA, ERR_NUMERIC, ERR_STATE, ERR_TIMEOUT = 5, 6, 7, 8, 9, 10
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 NE_MAX = 24

@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-unsigned long long g_kernel_launches = 0;
+std::atomic<unsigned long long> g_kernel_launches{0};
 
 namespace {
 thread_local std::string g_detail;
@@ -77,7 +77,8 @@ int status_to_code(int st) {
   if (st & ST_BOUNDS) return GBSMPS_ERR_BOUNDS;
   if (st & ST_NOT_CONVERGED) return GBSMPS_ERR_NOT_CONVERGED;
   if (st & ST_NUMERIC) return GBSMPS_ERR_NUMERIC;
-  return GBSMPS_OK;
+  if (st & ST_TIMEOUT) return GBSMPS_ERR_TIMEOUT;
+  return st ? GBSMPS_ERR_CUDA : GBSMPS_OK;
 }
 }  // namespace
 
@@ -113,7 +114,7 @@ struct gbsmps_mps {
   DevBuf tensors, env, gsvd, bonds;
   DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
   // mixed path, right-canonical sampler: Cholesky factors of the environments,
-  // their inverses, and every site's canonical tensor as bf16 planes + TMA map
+  // their inverses, and every site's canonical tensor as fp16 planes + TMA map
   DevBuf eoff_dev, lchol, linv, bpack;
   std::vector<int> Drp, Kp, Np;
   std::vector<long long> bpoff;
@@ -355,7 +356,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
   if (mixed) {
     // ---- right-canonical form for the tensor-core sampler -----------------
     // R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
-    // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as bf16 planes per site
+    // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as fp16 planes per site
     CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
     CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
                        cudaMemcpyHostToDevice, s));
@@ -392,11 +393,11 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
       M->Kp[m] = (2 * M->D[m] + 63) / 64 * 64;
       M->Np[m] = 2 * d * M->Drp[m];
       M->bpoff[m] = btot;
-      btot += 3LL * M->Np[m] * M->Kp[m];
+      btot += 2LL * M->Np[m] * M->Kp[m];
     }
-    CK(M->bpack.alloc(sizeof(__nv_bfloat16) * (btot + 64), s));
+    CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
     DevBuf tb, ab2, kw2;
-    const size_t wbytes2 = (size_t)64 << 20;
+    const size_t wbytes2 = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
     CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
     CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
     CK(kw2.alloc(wbytes2, s));
@@ -405,6 +406,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
       const int Dl = M->D[m], Dr = M->D[m + 1];
       float2* T = tb.as<float2>();
       float2* At = ab2.as<float2>();
+      // the canonical tensors feed fp16x2 planes: FP32-level products suffice
       CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
                          M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
                          kw2.p, wbytes2));
@@ -414,7 +416,7 @@ int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                            T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, kw2.p, wbytes2));
         src = At;
       }
-      __nv_bfloat16* Bp = M->bpack.as<__nv_bfloat16>() + M->bpoff[m];
+      __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
       CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
       COUNT_LAUNCH(1);
       if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
@@ -458,7 +460,7 @@ int gbsmps_create(int device, void* stream, gbsmps_ctx_t* out) {
   if (e) { delete c; return fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e)); }
   e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e) { cudaFree(c->d_status); delete c; return fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e)); }
-  c->launches_at_create = g_kernel_launches;
+  c->launches_at_create = g_kernel_launches.load();
   *out = c;
   return GBSMPS_OK;
 }
@@ -620,7 +622,7 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   const double2* R = m->env.as<double2>();
   const double2 one = cmk(1, 0), zero = cmk(0, 0);
   StageTimer tm(s);
-  DevBuf cv0, cv1, cw, cpart;        // mixed path: bf16 state planes, W, tile norms
+  DevBuf cv0, cv1, cw, cpart;        // mixed path: fp16 state planes, W, tile norms
   const char* tce = getenv("GBSMPS_TC");
   const int use_tc = !(tce && tce[0] == '0');
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
@@ -631,13 +633,13 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
       int Kpmax = 64, Npmax = 128;
       for (int i = 0; i < N; ++i) { Kpmax = std::max(Kpmax, m->Kp[i]); Npmax = std::max(Npmax, m->Np[i]); }
       if (!cw.p) {
-        CK(cv0.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)Spad * Kpmax, s));
-        CK(cv1.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)Spad * Kpmax, s));
+        CK(cv0.alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
+        CK(cv1.alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
         CK(cw.alloc(sizeof(float2) * (size_t)chunk * (Npmax / 2), s));
         CK(cpart.alloc(sizeof(float) * (size_t)chunk * (Npmax / 128), s));
       }
-      __nv_bfloat16* V = cv0.as<__nv_bfloat16>();
-      __nv_bfloat16* Vn = cv1.as<__nv_bfloat16>();
+      __half* V = cv0.as<__half>();
+      __half* Vn = cv1.as<__half>();
       CK(launch_vinit(V, (long long)Spad * m->Kp[0], Spad, m->Kp[0], s));
       COUNT_LAUNCH(1);
       for (int site = 0; site < N; ++site) {
@@ -648,8 +650,8 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
         if (canon_make_map(mapA, V, Kp, Spad))
           return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
         CK(launch_canon_gemm(mapA, m->bmaps[site].data(), V, (long long)Spad * Kp,
-                             m->bpack.as<__nv_bfloat16>() + m->bpoff[site], (long long)Np * Kp, Kp,
-                             Np, cs, Spad, 6, cw.as<float2>(), cpart.as<float>(), use_tc,
+                             m->bpack.as<__half>() + m->bpoff[site], (long long)Np * Kp, Kp,
+                             Np, cs, Spad, cw.as<float2>(), cpart.as<float>(), use_tc,
                              8.0 * cs * Dl * (double)d * Dr, m->ctx->d_status, s));
         CK(launch_select_canon(cs, d, Dr, m->Drp[site], cw.as<float2>(), cpart.as<float>(), Np / 128,
                                du ? du + (size_t)s0 * N : nullptr, N, site, seed,
@@ -776,6 +778,36 @@ int gbsmps_build_site_noalloc(gbsmps_ctx_t c, int32_t nl, int32_t nr, int32_t d,
   return GBSMPS_OK;
 }
 
+size_t gbsmps_estimate_bytes(int32_t N, const gbsmps_opts* o, int64_t S) {
+  // mirrors the allocations of build_core and gbsmps_sample with every bond
+  // at chi_max (D_m <= chi); transient buffers are counted as if all were live
+  if (N < 1 || S < 0 || check_opts(o) != GBSMPS_OK) return 0;
+  const double n = N, d = o->d, chi = o->chi_max, cap = chi + TIE_MARGIN;
+  const double c2 = chi * chi, site = 16.0 * d * c2;          // one complex128 tensor
+  double b = 0.0;
+  b += 16.0 * n * QS * QS + 64.0 * NEM * n;                   // GSVD outputs and carried block
+  b += (n + 1) * cap * (NEM + 8.0 + 4.0 * NEM) + 64.0 * NEM * (n + 1);   // bases, maps
+  b += n * site + 16.0 * (n + 1) * c2;                        // tensors, environments
+  b += std::min(n, 304.0) * 16.0 * (4.0 * chi + 4.0 * c2);    // PCO scratch (one wave)
+  b += site;                                                  // environment step product
+  const double chip = std::ceil(chi / 64.0) * 64.0, kp = std::ceil(2.0 * chi / 64.0) * 64.0;
+  if (o->precision == GBSMPS_PREC_MIXED) {
+    b += n * site + 2.0 * 16.0 * (n + 1) * c2;                // energy gauge, L, L^-1
+    b += n * 2.0 * (2.0 * d * chip) * kp * 2.0;               // packed fp16 planes
+    b += 2.0 * 8.0 * d * c2 + 2.0 * (64 << 20);               // transform buffers, split-K
+    const double sp = std::ceil(S / 128.0) * 128.0;
+    b += 2.0 * 2.0 * sp * kp * 2.0;                           // sample state planes
+    b += S * (d * chip) * 8.0 + S * (2.0 * d * chip / 128.0) * 4.0;   // W, tile norms
+  } else {
+    const double per = d * chi;
+    const double chunk = std::max(1.0, std::min((double)S, 6.0 * (1 << 30) / (32.0 * per + 32.0 * chi)));
+    b += 32.0 * chunk * chi + 32.0 * chunk * per;
+  }
+  b += (double)S * n * 2.0 + S;                               // patterns, flags
+  b = b * 1.1 + (64 << 20);                                   // allocator granularity
+  return (size_t)b;
+}
+
 const char* gbsmps_strerror(int code) {
   switch (code) {
     case GBSMPS_OK: return "ok";
@@ -788,13 +820,14 @@ const char* gbsmps_strerror(int code) {
     case GBSMPS_ERR_CUDA: return "CUDA error";
     case GBSMPS_ERR_NUMERIC: return "numerical failure";
     case GBSMPS_ERR_STATE: return "invalid state";
+    case GBSMPS_ERR_TIMEOUT: return "bounded device wait timed out";
     default: return "unknown error";
   }
 }
 
 const char* gbsmps_last_error_detail(void) { return g_detail.c_str(); }
 
-int64_t gbsmps_launch_count(gbsmps_ctx_t) { return (int64_t)g_kernel_launches; }
+int64_t gbsmps_launch_count(gbsmps_ctx_t) { return (int64_t)g_kernel_launches.load(); }
 
 int gbsmps_trace(gbsmps_ctx_t c, int enable) {
   if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");

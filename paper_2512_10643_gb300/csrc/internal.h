@@ -100,28 +100,34 @@ struct BondArrays {
 
 // ---- opt-in kernel tracing: CUDA events around every launch of one kernel
 // family on its own stream, summed with the launches' algorithmic work -------
+#include <atomic>
+#include <mutex>
 #include <vector>
 struct KernelTrace {
-  bool on = false;
+  std::atomic<bool> on{false};
+  std::mutex mu;
   std::vector<cudaEvent_t> ev;   // begin/end pairs
   double flops = 0.0, bytes = 0.0;
   long long launches = 0;
-  cudaEvent_t pending = nullptr;
-  void begin(cudaStream_t s) {
-    if (!on) return;
-    cudaEventCreate(&pending);
-    cudaEventRecord(pending, s);
-  }
-  void end(cudaStream_t s, double f, double b) {
-    if (!on) return;
-    cudaEvent_t e;
-    cudaEventCreate(&e);
+  cudaEvent_t begin(cudaStream_t s) {
+    if (!on.load()) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     cudaEventRecord(e, s);
-    ev.push_back(pending);
+    return e;
+  }
+  void end(cudaEvent_t b0, cudaStream_t s, double f, double b) {
+    if (!b0) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaEventDestroy(b0); return; }
+    cudaEventRecord(e, s);
+    std::lock_guard<std::mutex> lk(mu);
+    ev.push_back(b0);
     ev.push_back(e);
     flops += f; bytes += b; ++launches;
   }
   double total_ms() {
+    std::lock_guard<std::mutex> lk(mu);
     double t = 0.0;
     for (size_t i = 0; i + 1 < ev.size(); i += 2) {
       cudaEventSynchronize(ev[i + 1]);
@@ -132,6 +138,7 @@ struct KernelTrace {
     return t;
   }
   void reset() {
+    std::lock_guard<std::mutex> lk(mu);
     for (auto e : ev) cudaEventDestroy(e);
     ev.clear(); flops = bytes = 0.0; launches = 0;
   }
@@ -140,7 +147,7 @@ extern KernelTrace g_tc_trace;    // the tcgen05 sampler GEMM (dominant kernel)
 
 // ---- launchers (each returns cudaError_t of the launch) -------------------
 // g_kernel_launches counts every kernel the library enqueues.
-extern unsigned long long g_kernel_launches;
+extern std::atomic<unsigned long long> g_kernel_launches;
 #define COUNT_LAUNCH(n) (g_kernel_launches += (n))
 cudaError_t launch_check_input(const double* gamma, int N, double purity_tol,
                                double* work, int* status, cudaStream_t s);
@@ -208,18 +215,18 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
                               double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
                               void* work = nullptr, size_t work_bytes = 0);
 // right-canonical mixed sampling (k_canon.cu)
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
-cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __nv_bfloat16* Ap,
-                              long long apl, const __nv_bfloat16* Bp, long long bpl, int Kp,
-                              int Np, int M, int Mpad, int nterms, float2* W, float* part,
-                              int use_tc, double alg_flops, int* status, cudaStream_t s);
+cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
+                              const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
+                              float2* W, float* part, int use_tc, double alg_flops, int* status,
+                              cudaStream_t s);
 cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
-                          __nv_bfloat16* Bp, long long bpl, cudaStream_t s);
-cudaError_t launch_vinit(__nv_bfloat16* V, long long vpl, int Spad, int Kp, cudaStream_t s);
+                          __half* Bp, long long bpl, cudaStream_t s);
+cudaError_t launch_vinit(__half* V, long long vpl, int Spad, int Kp, cudaStream_t s);
 cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, const float* part,
                                 int ntiles, const double* u, int ustride, int site, uint64_t seed,
-                                uint64_t counter0, __nv_bfloat16* V, long long vpl, int Kpn,
+                                uint64_t counter0, __half* V, long long vpl, int Kpn,
                                 uint8_t* out, int N, uint8_t* flags, double flag_tol,
                                 cudaStream_t s);
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,

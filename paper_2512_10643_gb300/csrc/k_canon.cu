@@ -9,28 +9,44 @@
 // single complex GEMM W = Vt At^m (S x D_{m-1} by D_{m-1} x d D_m) followed by
 // a selection pass that reads only the chosen block of W.
 //
-// The GEMM runs on the 5th-generation tensor cores: operands are stored as
-// three bf16 planes (x = h + m + l), K-major, in global memory; TMA copies
-// 128 x 64 tiles of every plane into 128-byte-swizzled shared memory; one
-// thread issues tcgen05.mma (M = 128, N = 128, K = 16, FP32 accumulators in
-// tensor memory) for the six cross products hh, hm, mh, hl, mm, lh; the four
-// warps read the accumulators back with tcgen05.ld and write W plus the
-// per-tile row norms.  Every wait on an mbarrier is bounded in time; on a
-// timeout the kernel records ST_TIMEOUT and releases its tensor memory.
+// The GEMM runs on the 5th-generation tensor cores.  Both operands are
+// bounded by 1 in magnitude (vt is a unit vector, the rows of the packed At
+// are orthonormal), and each is stored as two fp16 planes, x = h + 2^-11 l
+// with h = fp16(x), l = fp16(2^11 (x - h)): 22 significant bits above the
+// fp16 normal range and an absolute floor near 2^-35 below it.  The product
+// is h_a h_b + 2^-11 (h_a l_b + l_a h_b) (the dropped l_a l_b term is
+// 2^-22 of the scale), three tcgen05.mma per K step into two FP32
+// accumulators in tensor memory.  The kernel is persistent and
+// warp-specialised: one thread issues TMA loads of 128 x 64 tiles of both
+// planes (128-byte swizzle) into a three-stage ring, one thread issues the
+// MMAs (M = N = 128, K = 16), and four epilogue warps drain the other of two
+// accumulator buffers (tcgen05.ld, W = hh + 2^-11 x, per-tile row norms,
+// rows transposed through shared memory into 128-byte coalesced stores), so
+// the epilogue of one tile overlaps the MMAs of the next.  Every wait on an
+// mbarrier is bounded in time; on a timeout the kernel records ST_TIMEOUT,
+// waits (bounded) for its own copies and MMAs in flight, and frees its
+// tensor memory.
 #include "internal.h"
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include <cstring>
 
 namespace {
 
-constexpr int TBM = 128, TBN = 128, TBK = 64;     // tile in bf16 elements (real)
-constexpr int NPL = 3;                            // bf16 planes per operand
-constexpr int TSTAGES = 2;
+constexpr int TBM = 128, TBN = 128, TBK = 64;     // tile in fp16 elements (real)
+constexpr int NPL = 2;                            // fp16 planes per operand: h, l
+constexpr int TSTAGES = 3;
 constexpr int PLANE_BYTES = TBM * TBK * 2;        // 16 KB (TBN == TBM)
 constexpr int STAGE_BYTES = 2 * NPL * PLANE_BYTES;
-constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_WARPS = 4;
+constexpr int EPI_LD = 36;                        // floats per staged row: 16-byte rows, no bank conflicts
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_LD * 4;
+constexpr int NBAR = 2 * TSTAGES + 2 + 2 + 1;     // full, empty, acc full, acc empty, drain
+constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue warps
+constexpr int TMEM_COLS = 4 * TBN;                // 2 buffers x (hh, cross) accumulators
+constexpr float LO_SCALE = 2048.f, LO_INV = 1.f / 2048.f;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 
 // ---------------------------------------------------------------- PTX helpers
@@ -43,6 +59,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -93,7 +112,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                           uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -119,40 +138,47 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m,
-                                       __nv_bfloat16& l) {
-  h = __float2bfloat16_rn(x);
-  float r = x - __bfloat162float(h);
-  m = __float2bfloat16_rn(r);
-  l = __float2bfloat16_rn(r - __bfloat162float(m));
+__device__ __forceinline__ void split2(float x, __half& h, __half& l) {
+  h = __float2half_rn(x);
+  l = __float2half_rn((x - __half2float(h)) * LO_SCALE);
 }
 
 // ---------------------------------------------------------------- tcgen05 GEMM
-// W[row, n] (complex, row-major, ldw complex) and part[row, tile] = sum |W|^2
-// over the tile's 64 complex columns.
-__global__ void __launch_bounds__(128, 1)
+// W[row, n] (real view: row-major, ldw floats; complex pairs interleaved)
+// and part[row, tile n] = sum of W^2 over the tile's 128 real columns.
+// Tile t of the ntm x ntn grid is (t / ntn, t % ntn): consecutive tiles
+// share the A row block, so the streamed operand is read from HBM once while
+// the packed tensor (a few MB) stays in L2.
+__global__ void __launch_bounds__(TC_THREADS, 1)
 canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     int nkb, int nterms, float2* __restrict__ W, long long ldw, int M,
-                     float* __restrict__ part, int ntiles, int* status) {
+                     int nkb, int ntm, int ntn, float* __restrict__ W, long long ldw, int M,
+                     float* __restrict__ part, int* status) {
   extern __shared__ __align__(1024) uint8_t smraw[];
   const uint32_t raw = su32(smraw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* sp = smraw + (sbase - raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sp + TSTAGES * STAGE_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * TSTAGES + 1);
+  float* epi = reinterpret_cast<float*>(sp + TSTAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sp + TSTAGES * STAGE_BYTES + EPI_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
-  const uint32_t full0 = su32(bars), empty0 = full0 + 8 * TSTAGES, accb = full0 + 16 * TSTAGES;
+  const uint32_t full0 = su32(bars), empty0 = full0 + 8 * TSTAGES;
+  const uint32_t afull0 = empty0 + 8 * TSTAGES, aempty0 = afull0 + 16, drain = aempty0 + 16;
+  const int ntiles = ntm * ntn;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TSTAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(afull0 + 8 * b, 1);
+      mbar_init(aempty0 + 8 * b, EPI_WARPS);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(su32(tslot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -160,98 +186,153 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  // product terms (plane of A, plane of B), small first; nterms 3 keeps the last 3
-  const int ta[6] = {2, 1, 0, 1, 0, 0};
-  const int tb[6] = {0, 1, 2, 0, 1, 0};
-  const int q0 = nterms == 3 ? 3 : 0;
-  if (warp == 0 && lane == 0) {                       // TMA producer
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int st = kb % TSTAGES, r = kb / TSTAGES;
-      if (r > 0 && !mbar_wait(empty0 + 8 * st, (r - 1) & 1)) { set_status(status, ST_TIMEOUT); break; }
-      mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-      const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
-      for (int p = 0; p < NPL; ++p) {
-        tma_load_3d(sA + p * PLANE_BYTES, &tmA, full0 + 8 * st, kb * TBK, m0, p);
-        tma_load_3d(sB + p * PLANE_BYTES, &tmB, full0 + 8 * st, kb * TBK, n0, p);
-      }
-    }
-  } else if (warp == 1 && lane == 0) {                // MMA issuer
-    // D f32, A bf16, B bf16, both K-major, N = 128, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
-                           ((uint32_t)(TBM >> 4) << 24);
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int st = kb % TSTAGES, r = kb / TSTAGES;
-      if (!mbar_wait(full0 + 8 * st, r & 1)) { set_status(status, ST_TIMEOUT); ok = false; break; }
-      tc_fence_after();
-      const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
-      for (int k16 = 0; k16 < TBK / 16; ++k16) {
-        for (int q = q0; q < 6; ++q) {
-          const uint64_t ad = sdesc(sA + ta[q] * PLANE_BYTES + k16 * 32);
-          const uint64_t bd = sdesc(sB + tb[q] * PLANE_BYTES + k16 * 32);
-          umma_bf16(tmem, ad, bd, idesc, (kb | k16 | (q - q0)) != 0 ? 1u : 0u);
+  if (warp == 0) {
+    if (lane == 0) {                                  // TMA producer
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t / ntn) * TBM, n0 = (t % ntn) * TBN;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int st = g % TSTAGES, r = g / TSTAGES;
+          if (r > 0 && !mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
+            set_status(status, ST_TIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+          const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
+          tma_load_3d(sA, &tmA, full0 + 8 * st, kb * TBK, m0, 0);    // box: both planes
+          tma_load_3d(sB, &tmB, full0 + 8 * st, kb * TBK, n0, 0);
         }
       }
-      umma_commit(empty0 + 8 * st);
+      // the last copy issued into each stage has landed before the CTA exits
+      for (int st = 0; st < TSTAGES && st < g; ++st) {
+        const int last = st + TSTAGES * ((g - 1 - st) / TSTAGES);
+        if (!mbar_wait(full0 + 8 * st, (last / TSTAGES) & 1)) set_status(status, ST_TIMEOUT);
+      }
     }
-    if (ok) umma_commit(accb);
-  }
-  __syncwarp();
-  // epilogue: every warp reads its 32 TMEM lanes (= tile rows)
-  const bool got = mbar_wait(accb, 0);
-  __syncwarp();
-  tc_fence_after();
-  if (got) {
-    const int row = m0 + warp * 32 + lane;
-    float nrm = 0.f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TBN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) {
-        float2* dst = W + (long long)row * ldw + (n0 + c0) / 2;
+  } else if (warp == 1) {
+    if (lane == 0) {                                  // MMA issuer
+      // D f32, A f16, B f16, both K-major, N = 128, M = 128
+      const uint32_t idesc =
+          (1u << 4) | ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int buf = i & 1, u = i >> 1;
+        if (u > 0 && !mbar_wait(aempty0 + 8 * buf, (u - 1) & 1)) {
+          set_status(status, ST_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dhh = tmem + (uint32_t)(buf * 2 * TBN), dx = dhh + TBN;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int st = g % TSTAGES, r = g / TSTAGES;
+          if (!mbar_wait(full0 + 8 * st, r & 1)) {
+            set_status(status, ST_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
-          dst[j] = make_float2(re, im);
-          nrm = fmaf(re, re, fmaf(im, im, nrm));
+          for (int k16 = 0; k16 < TBK / 16; ++k16) {
+            const uint64_t ah = sdesc(sA + k16 * 32), al = sdesc(sA + PLANE_BYTES + k16 * 32);
+            const uint64_t bh = sdesc(sB + k16 * 32), bl = sdesc(sB + PLANE_BYTES + k16 * 32);
+            const uint32_t acc = (kb | k16) != 0 ? 1u : 0u;
+            umma_f16(dhh, ah, bh, idesc, acc);
+            umma_f16(dx, ah, bl, idesc, acc);
+            umma_f16(dx, al, bh, idesc, 1u);
+          }
+          umma_commit(empty0 + 8 * st);
         }
+        if (!ok) break;
+        umma_commit(afull0 + 8 * buf);
       }
+      umma_commit(drain);                             // every MMA issued here has completed
+      if (!mbar_wait(drain, 0)) set_status(status, ST_TIMEOUT);
     }
-    if (row < M) part[(long long)row * ntiles + blockIdx.x] = nrm;
-  } else if (threadIdx.x == 0) {
-    set_status(status, ST_TIMEOUT);
+  } else {                                            // epilogue warps
+    const int q = warp & 3;                           // TMEM lanes 32q .. 32q + 31
+    float* stg = epi + (warp - 2) * 32 * EPI_LD;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int buf = i & 1, u = i >> 1;
+      const bool got = __all_sync(0xffffffffu, mbar_wait(afull0 + 8 * buf, u & 1));
+      if (!got) {
+        if (lane == 0) set_status(status, ST_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (t / ntn) * TBM, nb = t % ntn, n0 = nb * TBN;
+      const int rbase = m0 + q * 32;
+      float nrm = 0.f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TBN; c0 += 32) {
+        uint32_t h[32], x[32];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * TBN + c0);
+        tmem_ld32(ta, h);
+        tmem_ld32(ta + TBN, x);
+        float4* srow = reinterpret_cast<float4*>(stg + lane * EPI_LD);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            v[e] = fmaf(LO_INV, __uint_as_float(x[4 * j + e]), __uint_as_float(h[4 * j + e]));
+            nrm = fmaf(v[e], v[e], nrm);
+          }
+          srow[j] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = it * 4 + (lane >> 3), c4 = lane & 7;
+          const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + c4 * 4);
+          if (rbase + r < M)
+            *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + c4 * 4) = val;
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(aempty0 + 8 * buf);  // buffer free for tile i + 2
+      if (rbase + lane < M) part[(long long)(rbase + lane) * ntn + nb] = nrm;
+    }
   }
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
   }
 }
 
-// SIMT reference on the same packed planes (cross-check of the tcgen05 path)
-__global__ void canon_gemm_ref_kernel(const __nv_bfloat16* __restrict__ Ap, long long apl, int Kp,
-                                      const __nv_bfloat16* __restrict__ Bp, long long bpl, int Np,
-                                      int nterms, float2* __restrict__ W, long long ldw, int M) {
-  const int ta[6] = {2, 1, 0, 1, 0, 0};
-  const int tb[6] = {0, 1, 2, 0, 1, 0};
-  const int q0 = nterms == 3 ? 3 : 0;
+// SIMT reference on the same packed planes (cross-check of the tcgen05 path):
+// the same three products, FP32 accumulation in k order
+__global__ void canon_gemm_ref_kernel(const __half* __restrict__ Ap, long long apl, int Kp,
+                                      const __half* __restrict__ Bp, long long bpl, int Np,
+                                      float2* __restrict__ W, long long ldw, int M) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * (Np / 2);
        idx += (long long)gridDim.x * blockDim.x) {
     const int row = idx / (Np / 2), nc = idx % (Np / 2);
-    float re = 0.f, im = 0.f;
-    for (int q = q0; q < 6; ++q) {
-      const __nv_bfloat16* a = Ap + ta[q] * apl + (long long)row * Kp;
-      const __nv_bfloat16* b0 = Bp + tb[q] * bpl + (long long)(2 * nc) * Kp;
-      const __nv_bfloat16* b1 = b0 + Kp;
+    const __half* ah = Ap + (long long)row * Kp;
+    const __half* al = ah + apl;
+    float hh[2] = {0.f, 0.f}, xx[2] = {0.f, 0.f};
+    for (int c = 0; c < 2; ++c) {
+      const __half* bh = Bp + (long long)(2 * nc + c) * Kp;
+      const __half* bl = bh + bpl;
       for (int k = 0; k < Kp; ++k) {
-        float av = __bfloat162float(a[k]);
-        re = fmaf(av, __bfloat162float(b0[k]), re);
-        im = fmaf(av, __bfloat162float(b1[k]), im);
+        const float a0 = __half2float(ah[k]), a1 = __half2float(al[k]);
+        const float b0 = __half2float(bh[k]), b1 = __half2float(bl[k]);
+        hh[c] = fmaf(a0, b0, hh[c]);
+        xx[c] = fmaf(a0, b1, fmaf(a1, b0, xx[c]));
       }
     }
-    W[(long long)row * ldw + nc] = make_float2(re, im);
+    W[(long long)row * ldw + nc] = make_float2(fmaf(LO_INV, xx[0], hh[0]), fmaf(LO_INV, xx[1], hh[1]));
   }
 }
 
@@ -273,7 +354,7 @@ __global__ void canon_part_ref_kernel(const float2* __restrict__ W, long long ld
 // B planes of one site: row n_r = 2 (p Drp + b) + c, column k_r = 2 a + e;
 // [[Re, -Im], [Im, Re]] blocks of At[a, p, b] (zero in the padding)
 __global__ void pack_b_kernel(const float2* __restrict__ At, int Dl, int d, int Dr, int Drp, int Kp,
-                              __nv_bfloat16* __restrict__ Bp, long long bpl) {
+                              __half* __restrict__ Bp, long long bpl) {
   const long long ncx = (long long)d * Drp;                 // complex columns
   const long long total = ncx * (Kp / 2);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -283,39 +364,38 @@ __global__ void pack_b_kernel(const float2* __restrict__ At, int Dl, int d, int 
     const int p = nc / Drp, b = nc % Drp;
     float2 v = make_float2(0.f, 0.f);
     if (a < Dl && b < Dr) v = At[((long long)a * d + p) * Dr + b];
-    __nv_bfloat16 rh, rm, rl, ih, im_, il;
-    split3(v.x, rh, rm, rl);
-    split3(v.y, ih, im_, il);
-    const __nv_bfloat16 rr[3] = {rh, rm, rl}, ii[3] = {ih, im_, il};
+    __half rr[NPL], ii[NPL];
+    split2(v.x, rr[0], rr[1]);
+    split2(v.y, ii[0], ii[1]);
     for (int s = 0; s < NPL; ++s) {
-      __nv_bfloat16* row0 = Bp + s * bpl + (2 * nc) * Kp + 2 * a;
-      __nv_bfloat16* row1 = row0 + Kp;
-      __nv_bfloat162 x0, x1;
+      __half* row0 = Bp + s * bpl + (2 * nc) * Kp + 2 * a;
+      __half* row1 = row0 + Kp;
+      __half2 x0, x1;
       x0.x = rr[s]; x0.y = __hneg(ii[s]);
       x1.x = ii[s]; x1.y = rr[s];
-      *reinterpret_cast<__nv_bfloat162*>(row0) = x0;
-      *reinterpret_cast<__nv_bfloat162*>(row1) = x1;
+      *reinterpret_cast<__half2*>(row0) = x0;
+      *reinterpret_cast<__half2*>(row1) = x1;
     }
   }
 }
 
 // first site: vt = [1] (D_0 = 1) for every sample, zero padding
-__global__ void vinit_kernel(__nv_bfloat16* V, long long vpl, int Spad, int Kp) {
+__global__ void vinit_kernel(__half* V, long long vpl, int Spad, int Kp) {
   const long long total = (long long)Spad * Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int k = idx % Kp;
     for (int s = 0; s < NPL; ++s)
-      V[s * vpl + idx] = __float2bfloat16_rn((s == 0 && k == 0) ? 1.f : 0.f);
+      V[s * vpl + idx] = __float2half_rn((s == 0 && k == 0) ? 1.f : 0.f);
   }
 }
 
 // one warp per sample: q_p from the tile norms (fixed order), choose p*,
-// write vt' = w_{p*} / sqrt(q_{p*}) as bf16 planes for the next site
+// write vt' = w_{p*} / sqrt(q_{p*}) as fp16 planes for the next site
 __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2* __restrict__ W,
                                     const float* __restrict__ part, int ntiles,
                                     const double* __restrict__ u, int ustride, int site,
-                                    uint64_t seed, uint64_t counter0, __nv_bfloat16* __restrict__ V,
+                                    uint64_t seed, uint64_t counter0, __half* __restrict__ V,
                                     long long vpl, int Kpn, uint8_t* __restrict__ out, int N,
                                     uint8_t* flags, double flag_tol);
 
@@ -325,46 +405,76 @@ namespace {
 __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2* __restrict__ W,
                                     const float* __restrict__ part, int ntiles,
                                     const double* __restrict__ u, int ustride, int site,
-                                    uint64_t seed, uint64_t counter0, __nv_bfloat16* __restrict__ V,
+                                    uint64_t seed, uint64_t counter0, __half* __restrict__ V,
                                     long long vpl, int Kpn, uint8_t* __restrict__ out, int N,
                                     uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
   const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (s >= S) return;
+  // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
+  // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway.
+  // Lane j of a 32-wide chunk owns q_{c0 + j}; an inclusive warp scan gives
+  // the CDF; Z is the last CDF value, so the scan and Z agree exactly.
   const int tpp = Drp / 64;
-  double Z = 0.0;
-  for (int p = 0; p < d; ++p)
-    for (int t = 0; t < tpp; ++t) Z += part[s * ntiles + p * tpp + t];
+  const float* ps = part + s * ntiles;
+  float Z = 0.f;
+  for (int c0 = 0; c0 < d; c0 += 32) {
+    const int p = c0 + lane;
+    float q = 0.f;
+    if (p < d)
+      for (int t = 0; t < tpp; ++t) q += ps[p * tpp + t];
+    float C = q;
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, C, o);
+      if (lane >= o) C += y;
+    }
+    Z += __shfl_sync(0xffffffffu, C, 31);
+  }
   const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
-  const double tt = uu * Z;
+  const float tt = (float)uu * Z;
+  const float ftol = (float)flag_tol * Z;
   int pstar = -1, plast = 0;
-  double C = 0.0, qsel = 0.0;
+  float qsel = 0.f, base = 0.f;
   bool flag = false;
-  for (int p = 0; p < d; ++p) {
-    double q = 0.0;
-    for (int t = 0; t < tpp; ++t) q += part[s * ntiles + p * tpp + t];
-    C += q;
-    if (fabs(tt - C) <= flag_tol * Z) flag = true;
-    if (q > 0.0) plast = p;
-    if (pstar < 0 && tt < C) { pstar = p; qsel = q; }
+  for (int c0 = 0; c0 < d; c0 += 32) {
+    const int p = c0 + lane;
+    float q = 0.f;
+    if (p < d)
+      for (int t = 0; t < tpp; ++t) q += ps[p * tpp + t];
+    float C = q;
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, C, o);
+      if (lane >= o) C += y;
+    }
+    C += base;
+    base = __shfl_sync(0xffffffffu, C, 31);
+    const bool live = p < d;
+    if (__any_sync(0xffffffffu, live && fabsf(tt - C) <= ftol)) flag = true;
+    const unsigned pos = __ballot_sync(0xffffffffu, live && q > 0.f);
+    if (pos) plast = c0 + 31 - __clz(pos);
+    const unsigned hit = __ballot_sync(0xffffffffu, live && tt < C);
+    if (pstar < 0 && hit) {
+      const int j = __ffs(hit) - 1;
+      pstar = c0 + j;
+      qsel = __shfl_sync(0xffffffffu, q, j);
+    }
   }
   if (pstar < 0) {
     pstar = plast;
-    qsel = 0.0;
-    for (int t = 0; t < tpp; ++t) qsel += part[s * ntiles + pstar * tpp + t];
+    qsel = 0.f;
+    for (int t = 0; t < tpp; ++t) qsel += ps[pstar * tpp + t];
   }
-  const float inv = qsel > 0.0 ? (float)(1.0 / sqrt(qsel)) : 0.f;
+  const float inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
   const float2* w = W + s * (long long)d * Drp + (long long)pstar * Drp;
   for (int b = lane; b < Kpn / 2; b += 32) {
     float2 v = b < Dr ? w[b] : make_float2(0.f, 0.f);
-    __nv_bfloat16 h0, m0_, l0, h1, m1, l1;
-    split3(v.x * inv, h0, m0_, l0);
-    split3(v.y * inv, h1, m1, l1);
-    const __nv_bfloat16 rr[3] = {h0, m0_, l0}, ii[3] = {h1, m1, l1};
+    __half rr[NPL], ii[NPL];
+    split2(v.x * inv, rr[0], rr[1]);
+    split2(v.y * inv, ii[0], ii[1]);
     for (int pl = 0; pl < NPL; ++pl) {
-      __nv_bfloat162 x;
+      __half2 x;
       x.x = rr[pl]; x.y = ii[pl];
-      *reinterpret_cast<__nv_bfloat162*>(V + pl * vpl + s * Kpn + 2 * b) = x;
+      *reinterpret_cast<__half2*>(V + pl * vpl + s * Kpn + 2 * b) = x;
     }
   }
   if (lane == 0) {
@@ -462,15 +572,15 @@ typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void
                              CUtensorMapFloatOOBfill);
 
 EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  static const EncodeFn fn = [] {               // thread-safe one-time lookup
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
-  }
+      return reinterpret_cast<EncodeFn>(p);
+    return static_cast<EncodeFn>(nullptr);
+  }();
   return fn;
 }
 
@@ -484,60 +594,66 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows) {
   if ((reinterpret_cast<uintptr_t>(planes) & 15) || (Kp % TBK) || (rows % TBM)) return 2;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NPL};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
-  cuuint32_t box[3] = {TBK, TBM, 1};
+  cuuint32_t box[3] = {TBK, TBM, NPL};                      // both planes in one copy
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map128), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                   const_cast<void*>(planes), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : 3;
 }
 
-cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __nv_bfloat16* Ap,
-                              long long apl, const __nv_bfloat16* Bp, long long bpl, int Kp,
-                              int Np, int M, int Mpad, int nterms, float2* W, float* part,
-                              int use_tc, double alg_flops, int* status, cudaStream_t s) {
-  const int ntiles = Np / TBN;
+cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
+                              const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
+                              float2* W, float* part, int use_tc, double alg_flops, int* status,
+                              cudaStream_t s) {
+  const int ntn = Np / TBN, ntm = Mpad / TBM;
   COUNT_LAUNCH(1);
-  double flops = alg_flops;
-  double bytes = (double)NPL * 2 * ((double)Mpad * Kp + (double)Np * Kp) + (double)M * Np * 4;
-  g_tc_trace.begin(s);
+  const double bytes = (double)NPL * 2 * ((double)Mpad * Kp + (double)Np * Kp) + (double)M * Np * 4;
+  cudaEvent_t tr0 = g_tc_trace.begin(s);
   if (use_tc) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(canon_gemm_tc_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    static std::atomic<int> nsm[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!nsm[dev].load()) {
+      e = cudaFuncSetAttribute(canon_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TC_SMEM);
       if (e) return e;
-      attr = true;
+      int n = 0;
+      e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      if (e) return e;
+      nsm[dev].store(n);
     }
     CUtensorMap a, b;
     memcpy(&a, mapA, sizeof(CUtensorMap));
     memcpy(&b, mapB, sizeof(CUtensorMap));
-    dim3 grid(ntiles, Mpad / TBM);
-    canon_gemm_tc_kernel<<<grid, 128, TC_SMEM, s>>>(a, b, Kp / TBK, nterms, W, Np / 2, M, part,
-                                                    ntiles, status);
+    const int grid = std::min(nsm[dev].load(), ntm * ntn);
+    canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(
+        a, b, Kp / TBK, ntm, ntn, reinterpret_cast<float*>(W), Np, M, part, status);
   } else {
     long long n = (long long)M * (Np / 2);
     int blocks = (int)std::min<long long>((n + 255) / 256, 16384);
-    canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(Ap, apl, Kp, Bp, bpl, Np, nterms, W, Np / 2, M);
-    long long n2 = (long long)M * ntiles;
+    canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(Ap, apl, Kp, Bp, bpl, Np, W, Np / 2, M);
+    long long n2 = (long long)M * ntn;
     int b2 = (int)std::min<long long>((n2 + 255) / 256, 8192);
-    canon_part_ref_kernel<<<b2, 256, 0, s>>>(W, Np / 2, M, part, ntiles);
+    canon_part_ref_kernel<<<b2, 256, 0, s>>>(W, Np / 2, M, part, ntn);
     COUNT_LAUNCH(1);
   }
-  g_tc_trace.end(s, flops, bytes);
+  g_tc_trace.end(tr0, s, alg_flops, bytes);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
-                          __nv_bfloat16* Bp, long long bpl, cudaStream_t s) {
+                          __half* Bp, long long bpl, cudaStream_t s) {
   long long total = (long long)d * Drp * (Kp / 2);
   int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
   pack_b_kernel<<<blocks, 256, 0, s>>>(At, Dl, d, Dr, Drp, Kp, Bp, bpl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vinit(__nv_bfloat16* V, long long vpl, int Spad, int Kp, cudaStream_t s) {
+cudaError_t launch_vinit(__half* V, long long vpl, int Spad, int Kp, cudaStream_t s) {
   long long total = (long long)Spad * Kp;
   int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
   vinit_kernel<<<blocks, 256, 0, s>>>(V, vpl, Spad, Kp);
@@ -546,7 +662,7 @@ cudaError_t launch_vinit(__nv_bfloat16* V, long long vpl, int Spad, int Kp, cuda
 
 cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, const float* part,
                                 int ntiles, const double* u, int ustride, int site, uint64_t seed,
-                                uint64_t counter0, __nv_bfloat16* V, long long vpl, int Kpn,
+                                uint64_t counter0, __half* V, long long vpl, int Kpn,
                                 uint8_t* out, int N, uint8_t* flags, double flag_tol,
                                 cudaStream_t s) {
   long long threads = (long long)S * 32;

@@ -29,6 +29,7 @@ struct ChainSmem {
   double B[N2M * N2M];      // L^{-1} -> S
   double2 H[N2M * N2M];     // i K -> (Jacobi) ; reused as work for inverses
   double2 W[N2M * N2M];     // eigenvectors
+  double2 T[N2M * N2M];     // Jacobi scratch: FP32 copies of H, W; products
   double2 U[NLM * NLM];
   double2 V[NLM * NLM];
   double2 Ui[NLM * NLM];
@@ -46,108 +47,212 @@ struct ChainSmem {
 };
 
 __device__ double block_sum(double v, double* red) {
-  int t = threadIdx.x;
-  red[t] = v;
+  const int t = threadIdx.x, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) red[t >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] += red[t + s];
-    __syncthreads();
-  }
-  double r = red[0];
+  double r = 0.0;
+  for (int w = 0; w < nw; ++w) r += red[w];
   __syncthreads();
   return r;
 }
 
 __device__ double block_max(double v, double* red) {
-  int t = threadIdx.x;
-  red[t] = v;
+  const int t = threadIdx.x, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((t & 31) == 0) red[t >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) red[t] = fmax(red[t], red[t + s]);
-    __syncthreads();
-  }
   double r = red[0];
+  for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
 }
 
-// Eigen-decomposition of the n x n Hermitian H (row-major, ld LD) by the
-// cyclic Jacobi method with round-robin parallel ordering: every round
-// rotates n/2 disjoint index pairs at once.  On return H is diagonal (ev),
-// W holds the eigenvectors as columns.  Returns false after MAX_SWEEPS.
-__device__ bool jacobi_herm(ChainSmem& sm, int n) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  double2* H = sm.H;
-  double2* W = sm.W;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    int i = idx / n, j = idx % n;
-    W[i * LD + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
-  }
-  double loc = 0.0;
-  for (int idx = tid; idx < n * n; idx += nt) loc += cabs2(H[(idx / n) * LD + idx % n]);
-  const double normF = sqrt(block_sum(loc, sm.red));
-  const double skip = 1e-300 + 1e-18 * normF;
-  const double conv = 1e-15 * normF;
+// Sweeps of the cyclic complex Jacobi method on the n x n Hermitian H (ld LD,
+// storage precision of T2), accumulating W <- W J.  Round-robin ordering:
+// every round rotates n/2 disjoint index pairs at once.  Before each sweep
+// the largest off-diagonal |Re| + |Im| is compared with conv; returns true
+// once it is below, false after max_sweeps sweeps.
+//
+// The rotation for a pair is computed in FP32 from the current 2x2 block
+// (angle accurate to ~1e-7 relative).  In the FP64 stage its (cos, sin) and
+// phase are then brought to unit modulus by two Newton steps in FP64, so
+// every applied J is unitary to FP64 rounding and the similarity is exact;
+// an approximate angle only leaves ~1e-7 of the rotated element behind,
+// which the next sweep removes.
+template <typename T2, bool WARP>
+__device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, double skip,
+                              int max_sweeps) {
+  using R = decltype(T2{}.x);
+  constexpr bool wide = sizeof(R) == 8;
+  // WARP: warp 0 alone runs the sweeps; otherwise the whole block.  (The
+  // block form is faster for both stages at these sizes: the phases are
+  // latency-bound, and more threads means fewer dependent steps per thread.)
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nt = WARP ? 32 : blockDim.x;
   const int half = n / 2;
-  bool ok = false;
-  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-    double smax = 0.0;
-    for (int r = 0; r < n - 1; ++r) {
-      if (tid < half) {
-        int k = tid;
-        int a = (r + k) % (n - 1);
-        int b = (k == 0) ? (n - 1) : (r - k + n - 1) % (n - 1);
-        int p = min(a, b), q = max(a, b);
-        double hpp = H[p * LD + p].x, hqq = H[q * LD + q].x;
-        double2 c = H[p * LD + q];
-        double mag = sqrt(cabs2(c));
-        smax = fmax(smax, mag);
-        double cs = 1.0, sn = 0.0;
-        double2 ph = cmk(1.0, 0.0);
-        if (mag > skip) {
-          ph = cmk(c.x / mag, -c.y / mag);            // e^{-i phi}
-          double tau = (hqq - hpp) / (2.0 * mag);
-          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          cs = 1.0 / sqrt(1.0 + t * t);
-          sn = t * cs;
-        }
-        sm.rp[k] = p; sm.rq[k] = q; sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = ph;
+  auto team_sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+  for (int sweep = 0;; ++sweep) {
+    double loc = 0.0;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int i = idx / n, j = idx % n;
+      if (i < j) {
+        T2 v = H[i * LD + j];
+        loc = fmax(loc, (double)(fabs(v.x) + fabs(v.y)));
       }
-      __syncthreads();
+    }
+    double gmax;
+    if (WARP) {
+      for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
+      gmax = loc;
+    } else {
+      gmax = block_max(loc, sm.red);
+    }
+    if (gmax <= conv) return true;
+    if (sweep == max_sweeps) return false;
+    for (int r = 0; r < n - 1; ++r) {
+      const int k = tid;
+      if (k < half) {
+        const int a = (r + k) % (n - 1);
+        const int b = (k == 0) ? (n - 1) : (r - k + n - 1) % (n - 1);
+        const int p = min(a, b), q = max(a, b);
+        const T2 c = H[p * LD + q];
+        const float fx = (float)c.x, fy = (float)c.y;
+        const float mf = hypotf(fx, fy);
+        double cs = 1.0, sn = 0.0, phx = 1.0, phy = 0.0;
+        if (mf > (float)skip) {
+          const float gx = fx / mf, gy = -fy / mf;              // e^{-i phi}
+          float tau = (float)((double)H[q * LD + q].x - (double)H[p * LD + p].x) / (2.0f * mf);
+          float t;
+          if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+          else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+          const float fc = rsqrtf(fmaf(t, t, 1.0f));
+          cs = fc; sn = t * fc; phx = gx; phy = gy;
+          if (wide) {
+            for (int it = 0; it < 2; ++it) {
+              double g = 1.5 - 0.5 * (cs * cs + sn * sn);
+              cs *= g; sn *= g;
+              double h = 1.5 - 0.5 * (phx * phx + phy * phy);
+              phx *= h; phy *= h;
+            }
+          }
+        }
+        sm.rp[k] = p; sm.rq[k] = q; sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = cmk(phx, phy);
+      }
+      team_sync();
       // columns: X = H J, W = W J with J = [[cs, sn], [-sn ph, cs ph]]
       for (int idx = tid; idx < half * n; idx += nt) {
-        int k = idx / n, i = idx % n;
+        const int k = idx / n, i = idx % n;
         if (sm.rsn[k] == 0.0) continue;
-        int p = sm.rp[k], q = sm.rq[k];
-        double cs = sm.rcs[k], sn = sm.rsn[k];
-        double2 ph = sm.rph[k];
-        double2 hp = H[i * LD + p], hq = H[i * LD + q];
-        double2 phq = cmul(ph, hq);
-        H[i * LD + p] = cmk(cs * hp.x - sn * phq.x, cs * hp.y - sn * phq.y);
-        H[i * LD + q] = cmk(sn * hp.x + cs * phq.x, sn * hp.y + cs * phq.y);
-        double2 wp = W[i * LD + p], wq = W[i * LD + q];
-        double2 pwq = cmul(ph, wq);
-        W[i * LD + p] = cmk(cs * wp.x - sn * pwq.x, cs * wp.y - sn * pwq.y);
-        W[i * LD + q] = cmk(sn * wp.x + cs * pwq.x, sn * wp.y + cs * pwq.y);
+        const int p = sm.rp[k], q = sm.rq[k];
+        const R cs = (R)sm.rcs[k], sn = (R)sm.rsn[k];
+        const R px = (R)sm.rph[k].x, py = (R)sm.rph[k].y;
+        T2 hp = H[i * LD + p], hq = H[i * LD + q];
+        R qx = px * hq.x - py * hq.y, qy = px * hq.y + py * hq.x;
+        H[i * LD + p] = T2{cs * hp.x - sn * qx, cs * hp.y - sn * qy};
+        H[i * LD + q] = T2{sn * hp.x + cs * qx, sn * hp.y + cs * qy};
+        T2 wp = W[i * LD + p], wq = W[i * LD + q];
+        qx = px * wq.x - py * wq.y; qy = px * wq.y + py * wq.x;
+        W[i * LD + p] = T2{cs * wp.x - sn * qx, cs * wp.y - sn * qy};
+        W[i * LD + q] = T2{sn * wp.x + cs * qx, sn * wp.y + cs * qy};
       }
-      __syncthreads();
+      team_sync();
       // rows: H = J^dag X
       for (int idx = tid; idx < half * n; idx += nt) {
-        int k = idx / n, j = idx % n;
+        const int k = idx / n, j = idx % n;
         if (sm.rsn[k] == 0.0) continue;
-        int p = sm.rp[k], q = sm.rq[k];
-        double cs = sm.rcs[k], sn = sm.rsn[k];
-        double2 phc = cconj(sm.rph[k]);
-        double2 xp = H[p * LD + j], xq = H[q * LD + j];
-        double2 pxq = cmul(phc, xq);
-        H[p * LD + j] = cmk(cs * xp.x - sn * pxq.x, cs * xp.y - sn * pxq.y);
-        H[q * LD + j] = cmk(sn * xp.x + cs * pxq.x, sn * xp.y + cs * pxq.y);
+        const int p = sm.rp[k], q = sm.rq[k];
+        const R cs = (R)sm.rcs[k], sn = (R)sm.rsn[k];
+        const R px = (R)sm.rph[k].x, py = -(R)sm.rph[k].y;
+        T2 xp = H[p * LD + j], xq = H[q * LD + j];
+        R qx = px * xq.x - py * xq.y, qy = px * xq.y + py * xq.x;
+        H[p * LD + j] = T2{cs * xp.x - sn * qx, cs * xp.y - sn * qy};
+        H[q * LD + j] = T2{sn * xp.x + cs * qx, sn * xp.y + cs * qy};
       }
-      __syncthreads();
+      team_sync();
     }
-    double gmax = block_max(smax, sm.red);
-    if (gmax <= conv) { ok = true; break; }
   }
+}
+
+// Eigen-decomposition of the n x n Hermitian H (FP64, ld LD).  On return H is
+// diagonal (ev), W holds the eigenvectors as columns.  Stage 1: Jacobi in
+// FP32 on a copy until the off-diagonal falls to ~4e-6 of ||H||_F (FP32
+// updates run at the full FP32 rate).  Stage 2: the FP32 eigenvectors are
+// made unitary in FP64 by two Newton-Schulz steps W <- W (3 - W^dag W) / 2,
+// H is transformed to W^dag H W, and FP64 Jacobi sweeps (typically two)
+// finish the diagonalisation with W accumulating.  Returns false if the
+// FP64 stage does not reach 2.5e-16 n ||H||_F within MAX_SWEEPS.
+__device__ bool jacobi_herm(ChainSmem& sm, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double2* H = sm.H;
+  double2* W = sm.W;
+  double2* T = sm.T;
+  float2* H32 = reinterpret_cast<float2*>(sm.T);
+  float2* W32 = H32 + N2M * N2M;
+  double loc = 0.0;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    const double2 h = H[i * LD + j];
+    loc += cabs2(h);
+    H32[i * LD + j] = make_float2((float)h.x, (float)h.y);
+    W32[i * LD + j] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+  }
+  const double normF = sqrt(block_sum(loc, sm.red));
+  const double skip = 1e-300 + 1e-18 * normF;
+  jacobi_sweeps<float2, false>(sm, H32, W32, n, 4e-6 * normF, skip, 12);
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    const float2 w = W32[i * LD + j];
+    W[i * LD + j] = cmk(w.x, w.y);
+  }
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    for (int idx = tid; idx < n * n; idx += nt) {          // T = W^dag W
+      const int i = idx / n, j = idx % n;
+      double2 s = cmk(0, 0);
+      for (int k = 0; k < n; ++k) cfma(s, cconj(W[k * LD + i]), W[k * LD + j]);
+      T[i * LD + j] = s;
+    }
+    __syncthreads();
+    for (int row = warp; row < n; row += nw) {               // W <- W (3 - T) / 2, row-wise
+      double2 o0 = cmk(0, 0), o1 = cmk(0, 0);
+      const int j0 = lane, j1 = lane + 32;
+      for (int k = 0; k < n; ++k) {
+        const double2 w = W[row * LD + k];
+        if (j0 < n) {
+          double2 m = cscale(T[k * LD + j0], -0.5);
+          if (k == j0) m.x += 1.5;
+          cfma(o0, w, m);
+        }
+        if (j1 < n) {
+          double2 m = cscale(T[k * LD + j1], -0.5);
+          if (k == j1) m.x += 1.5;
+          cfma(o1, w, m);
+        }
+      }
+      __syncwarp();
+      if (j0 < n) W[row * LD + j0] = o0;
+      if (j1 < n) W[row * LD + j1] = o1;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {            // T = H W
+    const int i = idx / n, j = idx % n;
+    double2 s = cmk(0, 0);
+    for (int k = 0; k < n; ++k) cfma(s, H[i * LD + k], W[k * LD + j]);
+    T[i * LD + j] = s;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) {            // H = W^dag T
+    const int i = idx / n, j = idx % n;
+    double2 s = cmk(0, 0);
+    for (int k = 0; k < n; ++k) cfma(s, cconj(W[k * LD + i]), T[k * LD + j]);
+    H[i * LD + j] = s;
+  }
+  __syncthreads();
+  // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
+  const bool ok = jacobi_sweeps<double2, false>(sm, H, W, n, 2.5e-16 * n * normF, skip, MAX_SWEEPS);
   for (int i = tid; i < n; i += nt) sm.ev[i] = H[i * LD + i].x;
   __syncthreads();
   return ok;
@@ -162,7 +267,7 @@ __device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
     int i = idx / n, j = idx % n;
     Inv[i * NLM + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
   }
-  if (tid == 0) { sm.dval[0] = 0.0; sm.ival[0] = 0; }
+  if (tid == 0) { sm.dval[0] = 0.0; sm.dval[1] = 1.0; sm.ival[0] = 0; }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
@@ -174,7 +279,8 @@ __device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
       }
       if (best == 0.0) sm.ival[0] = 1;
       sm.ival[1] = pr;
-      sm.dval[0] += 0.5 * log(best > 0.0 ? best : 1e-300);
+      sm.dval[1] *= (best > 0.0 ? best : 1e-300);    // |pivots|^2 of a near-unitary-scale U
+      if (k == n - 1) sm.dval[0] = 0.5 * log(sm.dval[1]);
     }
     __syncthreads();
     int pr = sm.ival[1];

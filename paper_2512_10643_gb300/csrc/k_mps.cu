@@ -120,6 +120,27 @@ __global__ void amp_step_kernel(const double2* __restrict__ T, int Dl, int d, in
   }
 }
 
+// small pattern batches: one warp per output (s, b), lanes split the sum over a
+__global__ void amp_step_warp_kernel(const double2* __restrict__ T, int Dl, int d, int Dr,
+                                     const uint8_t* __restrict__ pats, int N, int site,
+                                     long long P, const double2* __restrict__ V,
+                                     double2* __restrict__ Vn, int ld) {
+  const int lane = threadIdx.x & 31;
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (w >= P * Dr) return;
+  const long long s = w / Dr;
+  const int b = w % Dr;
+  const int p = pats[s * N + site];
+  double2 acc = cmk(0, 0);
+  if (p < d)
+    for (int a = lane; a < Dl; a += 32) cfma(acc, V[s * ld + a], T[((size_t)a * d + p) * Dr + b]);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) Vn[s * ld + b] = acc;
+}
+
 __global__ void amp_init_kernel(double2* V, long long P, int ld) {
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < P; s += (long long)gridDim.x * blockDim.x)
     V[s * ld] = cmk(1.0, 0.0);
@@ -225,9 +246,16 @@ cudaError_t launch_amplitudes(ChainView cv, long long P, const uint8_t* pats, do
   for (int m = 0; m < cv.N; ++m) {
     int Dl = cv.D[m], Dr = cv.D[m + 1];
     long long n = P * Dr;
-    int b2 = (int)((n + 255) / 256);
-    if (b2 > 8192) b2 = 8192;
-    amp_step_kernel<<<b2, 256, 0, s>>>(cv.T + cv.toff[m], Dl, cv.d, Dr, pats, cv.N, m, P, V, Vn, maxD);
+    if (n * 32 <= (1LL << 24) && Dl >= 32) {
+      int bw = (int)((n * 32 + 255) / 256);
+      amp_step_warp_kernel<<<bw, 256, 0, s>>>(cv.T + cv.toff[m], Dl, cv.d, Dr, pats, cv.N, m, P, V,
+                                              Vn, maxD);
+    } else {
+      int b2 = (int)((n + 255) / 256);
+      if (b2 > 8192) b2 = 8192;
+      amp_step_kernel<<<b2, 256, 0, s>>>(cv.T + cv.toff[m], Dl, cv.d, Dr, pats, cv.N, m, P, V, Vn,
+                                         maxD);
+    }
     double2* t = V; V = Vn; Vn = t;
   }
   amp_out_kernel<<<blocks, 256, 0, s>>>(V, P, maxD, out);

@@ -239,12 +239,16 @@ template <int NT>
 cudaError_t run(const TcArgs& a, int batch, cudaStream_t s) {
   constexpr int NS = NT == 3 ? 2 : (NT == 6 ? 3 : 4);
   size_t smem = sizeof(__nv_bfloat16) * NS * (BM + BNR) * LDS;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr[64];
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0) return e0;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev].load()) {
     cudaError_t e = cudaFuncSetAttribute(zgemm_tc_kernel<NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    attr = true;
+    attr[dev].store(true);
   }
   dim3 grid((a.N + BNC - 1) / BNC, (a.M + BM - 1) / BM, batch * a.ksplit);
   zgemm_tc_kernel<NT><<<grid, 256, smem, s>>>(a);
