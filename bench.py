@@ -32,9 +32,10 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# dram bytes per launch of the dominant kernel from the committed ncu capture
-# (profiles/zgemm_tc_n144.md); None until a capture of the current kernel exists
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes per launch of the dominant kernel at 100,000 samples: the ncu
+# capture of the same kernel at 20,000 samples (dram read + write = 234.8 MB,
+# profiles/canon_gemm_tc_n144_d6_chi256.md) scaled by the samples processed
+TRAFFIC_BYTES_PER_LAUNCH = 234.8e6 * 5
 
 
 def parse():
@@ -48,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batch-states", type=int, default=64)
+    ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--serving-rate", type=float, default=4.0)
+    ap.add_argument("--serving-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -196,7 +201,7 @@ def run_gpu(args, rank, local, ws, dist):
             "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json x 1 "
                             "(nominal dense fp16/bf16 ratio)"),
             "unit": "TFLOP/s", "frac": round(ach_tflops / peak, 5),
-            "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None
+            "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None or S != 100_000
                         else TRAFFIC_BYTES_PER_LAUNCH),
             "algorithmic_flops_per_launch": tr["flops"] / n_launch,
             "algorithmic_flops_def": "8 S D_{m-1} d D_m real flops per site (complex MACs x 8)",
@@ -282,6 +287,97 @@ def run_gpu(args, rank, local, ws, dist):
     ctx.close()
     return dict(value=value, samples_per_s=samples_per_s, step_ms=step_ms, launches=launches,
                 roof=roof, clocks=clk.summary(), e2e=e2e, **res)
+
+
+# --------------------------------------------------------------------------- batched build
+def run_batched(args, dev):
+    """Many independent states built in one batched call (all GSVD chains in
+    one launch, all PCO tensors together, the environment chains in one
+    persistent launch) against the same states built one call at a time."""
+    import torch
+
+    import paper_2512_10643_gb300 as g
+    import workloads as wl
+
+    states = wl.batch(args.batch_states)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = g.Context(dev, stream.cuda_stream)
+    gams = [torch.from_numpy(np.ascontiguousarray(w.gamma)).to(f"cuda:{dev}") for w in states]
+    opts = [dict(d=w.d, chi_max=w.chi, eps_trunc=w.eps, lambda2_freeze=w.freeze,
+                 precision=g.PREC_MIXED) for w in states]
+    tensors = sum(w.N for w in states)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            ms = fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        for m in ms:
+            m.release()
+        return e0.elapsed_time(e1)
+
+    batch_fn = lambda: g.MPS.batch(ctx, gams, opts)
+    seq_fn = lambda: [g.MPS.from_cov(ctx, x, **o) for x, o in zip(gams, opts)]
+    timed(batch_fn)                                   # warm-up
+    n0 = g.gbsmps_launch_count()
+    t_b = min(timed(batch_fn) for _ in range(2))
+    n_b = (g.gbsmps_launch_count() - n0) // 2
+    n0 = g.gbsmps_launch_count()
+    t_s = timed(seq_fn)
+    n_s = g.gbsmps_launch_count() - n0
+    ctx.close()
+    return {"states": len(states), "tensors": tensors,
+            "batched_ms": round(t_b, 2), "sequential_ms": round(t_s, 2),
+            "tensors_per_s_batched": round(tensors / (t_b / 1e3), 1),
+            "tensors_per_s_sequential": round(tensors / (t_s / 1e3), 1),
+            "speedup": round(t_s / t_b, 2), "launches_batched": int(n_b),
+            "launches_sequential": int(n_s),
+            "workload": ("N~U{16..144}, r~U(0.1,0.5), brick-wall depth N/8, d=6, "
+                         "chi in {32,64,128,256}, eps 1e-12, lambda2_freeze 1e-9; mixed precision; "
+                         "build only (Gamma on the device)")}
+
+
+# --------------------------------------------------------------------------- serving
+def run_serving(args, dev):
+    """Poisson-arriving build + sampling requests through the library's
+    request loop (gbsmps_server_*): N log-uniform in [32, 512], r~U(0.05,0.4),
+    depth N/16, d in {4, 6}, chi in {64..512}, 1e3..1e5 samples each.
+    Reports latency quantiles and throughput over the busy period."""
+    import paper_2512_10643_gb300 as g
+    import workloads as wl
+
+    reqs = wl.serving(args.serving_requests, args.serving_rate)
+    t0 = time.perf_counter()
+    ids = []
+    with g.Server(dev, slots=args.serving_slots) as srv:
+        start = time.perf_counter()
+        for t_arr, w, S in reqs:
+            delay = t_arr - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(w.gamma, S, seed=17, counter0=0, d=w.d, chi_max=w.chi,
+                                  eps_trunc=w.eps, lambda2_freeze=w.freeze,
+                                  precision=g.PREC_MIXED))
+        srv.drain()
+        infos = [srv.wait(i)[1] for i in ids]
+        st = srv.stats()
+    busy = st["busy_s"]
+    return {"requests": len(reqs), "arrival_rate_hz": args.serving_rate,
+            "slots": args.serving_slots, "completed": st["completed"], "failed": st["failed"],
+            "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2),
+                           "mean": round(st["mean_ms"], 2)},
+            "tensors_per_s": round(st["tensors"] / busy, 2) if busy > 0 else None,
+            "samples_per_s": round(st["samples"] / busy, 1) if busy > 0 else None,
+            "busy_s": round(busy, 3), "wall_s": round(time.perf_counter() - t0, 3),
+            "max_concurrent": max(sum(1 for y in infos if y["t_admit"] <= x["t_admit"] < y["t_done"])
+                                  for x in infos) if infos else 0,
+            "hbm_peak_gb": round(st["hbm_peak"] / 1e9, 2),
+            "workload": ("Poisson arrivals; N log-U[32,512], r~U(0.05,0.4), brick-wall depth N/16, "
+                         "d in {4,6}, chi in {64,128,256,512}, samples U{1e3..1e5}; mixed precision; "
+                         "latency = submit -> patterns in host memory")}
 
 
 # --------------------------------------------------------------------------- oracle (CPU)
@@ -380,6 +476,10 @@ def main():
                 clocks=r["clocks"])
     if "fp64_gpu" in r:
         line["fp64_gpu"] = r["fp64_gpu"]
+    if ws == 1 and args.batch_states > 0:
+        line["batched"] = run_batched(args, local)
+    if ws == 1 and args.serving_requests > 0:
+        line["serving"] = run_serving(args, local)
     print(json.dumps(line))
 
 

@@ -117,6 +117,19 @@ int gbsmps_build_from_Q(gbsmps_ctx_t ctx, int32_t N, const double* Q,
                         int mem_kind, const gbsmps_opts* opts,
                         gbsmps_mps_t* out);
 
+/* Build `count` MPSs of independent states in one pass (same results as
+ * gbsmps_build_from_cov on each, up to the rounding order of the environment
+ * products).  Ns[i], gammas[i] (all in mem_kind memory) and opts[i] describe
+ * state i; out[i] receives its handle.  The sequential parts of the method run
+ * side by side across the batch: all GSVD chains (Sec. II B) in one launch,
+ * the PCO tensors of all sites together (Sec. II C), and the right-
+ * environment chains of the mixed-precision states in one persistent launch;
+ * bond sizes are read back once.  On error no handle is returned.  Errors as
+ * gbsmps_build_from_cov.  count = 0 is a no-op. */
+int gbsmps_build_batch(gbsmps_ctx_t ctx, int32_t count, const int32_t* Ns,
+                       const double* const* gammas, int mem_kind,
+                       const gbsmps_opts* opts, gbsmps_mps_t* out);
+
 /* Sizes of a built MPS (host outputs, any may be NULL):
  * bond_dims[N+1] (D_0 = D_N = 1), n_e[N-1] (entangled pairs per cut),
  * eps_m[N-1] (discarded weight per bond, Sec. III A), *N_out, *d_out. */

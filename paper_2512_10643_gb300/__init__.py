@@ -26,6 +26,25 @@ NE_MAX = 24
 QS = 2 * NE_MAX + 1
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_size_t),
+                ("simulate_s_per_tensor", C.c_double)]
+
+
+class JobInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("slot", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("hbm_bytes", C.c_size_t), ("detail", C.c_char * 128)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("running", C.c_int64), ("queued", C.c_int64), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("busy_s", C.c_double),
+                ("tensors", C.c_double), ("samples", C.c_double), ("hbm_in_use", C.c_size_t),
+                ("hbm_budget", C.c_size_t), ("hbm_peak", C.c_size_t)]
+
+
 class GbsmpsError(RuntimeError):
     def __init__(self, code, detail):
         super().__init__(f"gbsmps error {code}: {detail}")
@@ -36,6 +55,11 @@ class Opts(C.Structure):
     _fields_ = [("d", C.c_int32), ("chi_max", C.c_int32), ("eps_trunc", C.c_double),
                 ("lambda2_freeze", C.c_double), ("precision", C.c_int32),
                 ("validate", C.c_int32), ("purity_tol", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("gamma", C.c_void_p), ("N", C.c_int32), ("opts", Opts), ("samples", C.c_int64),
+                ("seed", C.c_uint64), ("counter0", C.c_uint64), ("out", C.c_void_p)]
 
 
 _lib = None
@@ -69,6 +93,15 @@ def lib():
         "gbsmps_build_site_noalloc": (C.c_int, [vp, i32, i32, i32, vp, dbl, i32, vp, i32, vp, i32, vp]),
         "gbsmps_trace": (C.c_int, [vp, C.c_int]),
         "gbsmps_trace_read": (C.c_int, [vp, vp, vp, vp, vp]),
+        "gbsmps_server_opts_default": (C.c_int, [C.POINTER(ServerOpts)]),
+        "gbsmps_server_create": (C.c_int, [C.c_int, C.POINTER(ServerOpts), C.POINTER(vp)]),
+        "gbsmps_server_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(i64)]),
+        "gbsmps_server_wait": (C.c_int, [vp, i64, dbl, C.POINTER(JobInfo)]),
+        "gbsmps_server_drain": (C.c_int, [vp, dbl]),
+        "gbsmps_server_stats_read": (C.c_int, [vp, C.POINTER(ServerStats)]),
+        "gbsmps_server_destroy": (C.c_int, [vp]),
+        "gbsmps_estimate_bytes": (C.c_size_t, [i32, C.POINTER(Opts), i64]),
+        "gbsmps_build_batch": (C.c_int, [vp, i32, vp, vp, C.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -130,6 +163,27 @@ def gbsmps_build_from_cov(ctx, gamma, opts: Opts):
     h = C.c_void_p()
     _check(lib().gbsmps_build_from_cov(ctx, N, C.c_void_p(p), kind, C.byref(opts), C.byref(h)))
     return h
+
+
+def gbsmps_build_batch(ctx, gammas, opts_list):
+    """Build many states at once: gammas is a list of (2N, 2N) float64 numpy
+    arrays (host) or CUDA tensors (device), opts_list one Opts per state.
+    Returns the list of handles."""
+    n = len(gammas)
+    if n != len(opts_list):
+        raise ValueError("one Opts per state")
+    if n == 0:
+        return []
+    ptrs = [_ptr(x) for x in gammas]
+    kinds = {k for _, k in ptrs}
+    if len(kinds) != 1:
+        raise ValueError("all covariances must live in the same memory")
+    Ns = (C.c_int32 * n)(*[x.shape[0] // 2 for x in gammas])
+    gp = (C.c_void_p * n)(*[p for p, _ in ptrs])
+    op = (Opts * n)(*opts_list)
+    hs = (C.c_void_p * n)()
+    _check(lib().gbsmps_build_batch(ctx, n, Ns, gp, kinds.pop(), op, hs))
+    return [C.c_void_p(h) for h in hs]
 
 
 def gbsmps_build_from_Q(ctx, Q, opts: Opts):
@@ -283,6 +337,12 @@ class MPS:
         return cls(gbsmps_build_from_cov(ctx.h, gamma, opts_default(**opts)))
 
     @classmethod
+    def batch(cls, ctx: Context, gammas, opts_list):
+        """Batched build; opts_list holds one keyword dict per state."""
+        return [cls(h) for h in gbsmps_build_batch(ctx.h, gammas,
+                                                    [opts_default(**o) for o in opts_list])]
+
+    @classmethod
     def from_Q(cls, ctx: Context, Q, **opts):
         return cls(gbsmps_build_from_Q(ctx.h, Q, opts_default(**opts)))
 
@@ -302,3 +362,69 @@ class MPS:
         if self.h:
             gbsmps_release(self.h)
             self.h = None
+
+
+def gbsmps_estimate_bytes(N: int, opts: Opts, samples: int) -> int:
+    return int(lib().gbsmps_estimate_bytes(N, C.byref(opts), samples))
+
+
+class Server:
+    """Continuous-batching request loop of the library (gbsmps_server_*):
+    requests (host Gamma, options, sample count) are admitted by free device
+    memory into `slots` concurrent streams; results land in host arrays."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 0,
+                 simulate_s_per_tensor: float = 0.0):
+        o = ServerOpts()
+        _check(lib().gbsmps_server_opts_default(C.byref(o)))
+        o.slots, o.hbm_budget, o.simulate_s_per_tensor = slots, hbm_budget, simulate_s_per_tensor
+        self.h = C.c_void_p()
+        _check(lib().gbsmps_server_create(device, C.byref(o), C.byref(self.h)))
+        self._keep = {}
+
+    def submit(self, gamma, samples: int, seed: int = 0, counter0: int = 0, N: int | None = None,
+               **opts) -> int:
+        """Queue one request; returns its id.  gamma: host float64 (2N, 2N)
+        numpy array or None (simulation mode, then N is required)."""
+        if gamma is not None:
+            gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+            N = gamma.shape[0] // 2
+        out = np.zeros((samples, N), dtype=np.uint8)
+        r = Request()
+        r.gamma = gamma.ctypes.data if gamma is not None else None
+        r.N, r.opts, r.samples, r.seed, r.counter0 = N, opts_default(**opts), samples, seed, counter0
+        r.out = out.ctypes.data if samples else None
+        jid = C.c_int64()
+        _check(lib().gbsmps_server_submit(self.h, C.byref(r), C.byref(jid)))
+        self._keep[jid.value] = (gamma, out)
+        return jid.value
+
+    def wait(self, jid: int, timeout_s: float = -1.0):
+        """(samples, info dict) of request jid; raises on a failed job."""
+        info = JobInfo()
+        rc = lib().gbsmps_server_wait(self.h, jid, timeout_s, C.byref(info))
+        d = {k: getattr(info, k) for k, _ in JobInfo._fields_ if k != "detail"}
+        d["detail"] = info.detail.decode(errors="replace")
+        if rc != OK:
+            raise GbsmpsError(rc, f"{lib().gbsmps_strerror(rc).decode()} ({d['detail']})")
+        gamma, out = self._keep.pop(jid)
+        return out, d
+
+    def drain(self, timeout_s: float = -1.0):
+        _check(lib().gbsmps_server_drain(self.h, timeout_s))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().gbsmps_server_stats_read(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().gbsmps_server_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,7 +1,7 @@
 // C ABI of gbsmps (include/gbsmps.h): argument checks, device buffers and the
 // launch order of the build / amplitude / sampling pipelines.  All numerics run
 // in the kernels of k_gsvd.cu, k_basis.cu, k_pco.cu and k_mps.cu.
-#include "internal.h"
+#include "objects.h"
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -13,430 +13,7 @@
 
 std::atomic<unsigned long long> g_kernel_launches{0};
 
-namespace {
 thread_local std::string g_detail;
-
-int fail(int code, const std::string& what) {
-  g_detail = what;
-  return code;
-}
-
-#define CK(expr)                                                                   \
-  do {                                                                             \
-    cudaError_t e_ = (expr);                                                       \
-    if (e_ != cudaSuccess) {                                                       \
-      return fail(e_ == cudaErrorMemoryAllocation ? GBSMPS_ERR_OOM : GBSMPS_ERR_CUDA, \
-                  std::string(#expr) + ": " + cudaGetErrorString(e_));            \
-    }                                                                              \
-  } while (0)
-
-// Opt-in stage tracing: with GBSMPS_PROFILE=1 every pipeline records CUDA
-// events between its stages and prints the elapsed times to stderr.
-struct StageTimer {
-  bool on = false;
-  cudaStream_t s = nullptr;
-  std::vector<std::pair<std::string, cudaEvent_t>> ev;
-  explicit StageTimer(cudaStream_t st) : s(st) {
-    const char* e = getenv("GBSMPS_PROFILE");
-    on = e && e[0] == '1';
-    mark("start");
-  }
-  int* dbg_status = nullptr;       // GBSMPS_DEBUG=1: status word checked at every mark
-  std::string failed_stage;
-  void mark(const char* name) {
-    if (dbg_status && failed_stage.empty()) {
-      int st = 0;
-      cudaMemcpyAsync(&st, dbg_status, sizeof(int), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      if (st) {
-        failed_stage = name;
-        fprintf(stderr, "[gbsmps] device status %d raised in stage '%s'\n", st, name);
-      }
-    }
-    if (!on) return;
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    cudaEventRecord(e, s);
-    ev.emplace_back(name, e);
-  }
-  ~StageTimer() {
-    if (!on) return;
-    cudaEventSynchronize(ev.back().second);
-    for (size_t i = 1; i < ev.size(); ++i) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
-      fprintf(stderr, "[gbsmps] %-14s %9.3f ms\n", ev[i].first.c_str(), ms);
-    }
-    for (auto& p : ev) cudaEventDestroy(p.second);
-  }
-};
-
-int status_to_code(int st) {
-  if (st & ST_NOT_SYMMETRIC) return GBSMPS_ERR_NOT_SYMMETRIC;
-  if (st & ST_NOT_PURE) return GBSMPS_ERR_NOT_PURE;
-  if (st & ST_BOUNDS) return GBSMPS_ERR_BOUNDS;
-  if (st & ST_NOT_CONVERGED) return GBSMPS_ERR_NOT_CONVERGED;
-  if (st & ST_NUMERIC) return GBSMPS_ERR_NUMERIC;
-  if (st & ST_TIMEOUT) return GBSMPS_ERR_TIMEOUT;
-  return st ? GBSMPS_ERR_CUDA : GBSMPS_OK;
-}
-}  // namespace
-
-struct gbsmps_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int* d_status = nullptr;
-  unsigned long long launches_at_create = 0;
-};
-
-struct DevBuf {                // stream-ordered device allocation
-  void* p = nullptr;
-  cudaStream_t s = nullptr;
-  cudaError_t alloc(size_t bytes, cudaStream_t st) {
-    s = st;
-    if (bytes == 0) bytes = 16;
-    return cudaMallocAsync(&p, bytes, st);
-  }
-  void release() {
-    if (p) cudaFreeAsync(p, s);
-    p = nullptr;
-  }
-  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
-};
-
-struct gbsmps_mps {
-  gbsmps_ctx* ctx = nullptr;
-  int N = 0, d = 0, chi = 0, precision = 0;
-  std::vector<int> D, ne;
-  std::vector<double> eps;
-  std::vector<long long> toff, eoff;
-  int maxD = 1;
-  DevBuf tensors, env, gsvd, bonds;
-  DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
-  // mixed path, right-canonical sampler: Cholesky factors of the environments,
-  // their inverses, and every site's canonical tensor as fp16 planes + TMA map
-  DevBuf eoff_dev, lchol, linv, bpack;
-  std::vector<int> Drp, Kp, Np;
-  std::vector<long long> bpoff;
-  std::vector<std::array<unsigned char, 128>> bmaps;
-  BondArrays ba{};
-  double* lam2 = nullptr;
-  double2* Qm = nullptr;
-  double* cm = nullptr;
-  ~gbsmps_mps() {
-    tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
-    eoff_dev.release(); lchol.release(); linv.release(); bpack.release();
-  }
-};
-
-namespace {
-
-int sync_status(gbsmps_ctx* c) {
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (st) {
-    CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
-    return fail(status_to_code(st), "device status word " + std::to_string(st));
-  }
-  return GBSMPS_OK;
-}
-
-int check_opts(const gbsmps_opts* o) {
-  if (!o) return fail(GBSMPS_ERR_ARG, "opts is NULL");
-  if (o->d < 1 || o->d > 255) return fail(GBSMPS_ERR_ARG, "d out of range [1,255]");
-  if (o->chi_max < 1 || o->chi_max > 4096) return fail(GBSMPS_ERR_ARG, "chi_max out of range [1,4096]");
-  if (!(o->eps_trunc >= 0.0 && o->eps_trunc < 1.0)) return fail(GBSMPS_ERR_ARG, "eps_trunc not in [0,1)");
-  if (!(o->lambda2_freeze >= 0.0 && o->lambda2_freeze < 1.0))
-    return fail(GBSMPS_ERR_ARG, "lambda2_freeze not in [0,1)");
-  if (o->precision != GBSMPS_PREC_FP64 && o->precision != GBSMPS_PREC_MIXED)
-    return fail(GBSMPS_ERR_ARG, "unknown precision");
-  return GBSMPS_OK;
-}
-
-// the pipeline after the covariance is on the device
-int build_core(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
-               gbsmps_mps_t* out) {
-  cudaStream_t s = c->stream;
-  StageTimer tm(s);
-  {
-    const char* dbg = getenv("GBSMPS_DEBUG");
-    if (dbg && dbg[0] == '1') tm.dbg_status = c->d_status;
-  }
-  auto* M = new gbsmps_mps();
-  std::unique_ptr<gbsmps_mps> guard(M);
-  M->ctx = c; M->N = N; M->d = o->d; M->chi = o->chi_max; M->precision = o->precision;
-  const int cap = o->chi_max + TIE_MARGIN;
-  const int nb = N + 1;
-  // ---- GSVD outputs and bond arrays in one allocation -----------------------
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
-  size_t o_Q = take(sizeof(double2) * (size_t)N * QS * QS);
-  size_t o_c = take(sizeof(double) * N);
-  size_t o_G = take(sizeof(double) * 2 * 2 * NEM * 2 * (size_t)std::max(N, 1));
-  size_t o_bw = take(sizeof(int) * 4);
-  size_t o_work = take(sizeof(double) * 8);
-  CK(M->gsvd.alloc(off, s));
-  char* g0 = M->gsvd.as<char>();
-  M->Qm = reinterpret_cast<double2*>(g0 + o_Q);
-  M->cm = reinterpret_cast<double*>(g0 + o_c);
-  double* Gs = reinterpret_cast<double*>(g0 + o_G);
-  int* dbw = reinterpret_cast<int*>(g0 + o_bw);
-  double* work = reinterpret_cast<double*>(g0 + o_work);
-  off = 0;
-  size_t o_occ = take((size_t)nb * cap * NEM);
-  size_t o_E = take(sizeof(double) * (size_t)nb * cap);
-  size_t o_low = take(sizeof(int) * (size_t)nb * NEM * cap);
-  size_t o_D = take(sizeof(int) * nb);
-  size_t o_ne = take(sizeof(int) * nb);
-  size_t o_mo = take(sizeof(int) * (size_t)nb * NEM);
-  size_t o_l2 = take(sizeof(double) * (size_t)nb * NEM);
-  size_t o_eps = take(sizeof(double) * nb);
-  CK(M->bonds.alloc(off, s));
-  char* b0 = M->bonds.as<char>();
-  BondArrays& ba = M->ba;
-  ba.cap = cap;
-  ba.occ = reinterpret_cast<uint8_t*>(b0 + o_occ);
-  ba.E = reinterpret_cast<double*>(b0 + o_E);
-  ba.low = reinterpret_cast<int*>(b0 + o_low);
-  ba.D = reinterpret_cast<int*>(b0 + o_D);
-  ba.ne = reinterpret_cast<int*>(b0 + o_ne);
-  ba.maxocc = reinterpret_cast<int*>(b0 + o_mo);
-  ba.lam2 = reinterpret_cast<double*>(b0 + o_l2);
-  ba.eps = reinterpret_cast<double*>(b0 + o_eps);
-  M->lam2 = ba.lam2;
-  CK(cudaMemsetAsync(b0, 0, off, s));
-  CK(cudaMemsetAsync(M->Qm, 0, sizeof(double2) * (size_t)N * QS * QS, s));
-  // ---- a1 validation, a2-a3 GSVD chain -------------------------------------
-  if (o->validate) {
-    CK(launch_check_input(dgamma, N, o->purity_tol, work, c->d_status, s));
-    COUNT_LAUNCH(2);
-  }
-  tm.mark("validate");
-  CK(launch_bandwidth(dgamma, N, dbw, s));
-  COUNT_LAUNCH(1);
-  CK(launch_gsvd_chain(dgamma, N, dbw, o->lambda2_freeze, Gs, ba, M->Qm, M->cm, c->d_status, s));
-  COUNT_LAUNCH(1);
-  tm.mark("gsvd_chain");
-  // ---- a4-a5 kept bases and index maps --------------------------------------
-  CK(launch_basis(ba, nb, o->chi_max, o->eps_trunc, c->d_status, s));
-  tm.mark("basis");
-  CK(launch_maps(ba, nb, c->d_status, s));
-  COUNT_LAUNCH(2);
-  tm.mark("maps");
-  M->D.assign(nb, 1);
-  M->ne.assign(nb, 0);
-  std::vector<double> epsb(nb, 0.0);
-  CK(cudaMemcpyAsync(M->D.data(), ba.D, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(M->ne.data(), ba.ne, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(epsb.data(), ba.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
-  int rc = sync_status(c);
-  if (rc) return rc;
-  M->eps.assign(epsb.begin() + 1, epsb.end() - 1);
-  M->D[0] = 1; M->D[N] = 1;
-  // ---- tensor storage -----------------------------------------------------
-  M->toff.resize(N);
-  long long tot = 0;
-  size_t scr_max = 0;
-  for (int m = 0; m < N; ++m) {
-    M->toff[m] = tot;
-    tot += (long long)M->D[m] * o->d * M->D[m + 1];
-    scr_max = std::max(scr_max, pco_scratch_elems(M->D[m], M->D[m + 1]));
-    M->maxD = std::max(M->maxD, M->D[m]);
-  }
-  M->eoff.resize(N + 1);
-  long long etot = 0;
-  for (int m = 0; m <= N; ++m) { M->eoff[m] = etot; etot += (long long)M->D[m] * M->D[m]; }
-  CK(M->tensors.alloc(sizeof(double2) * tot, s));
-  CK(M->env.alloc(sizeof(double2) * (etot + 8), s));
-  // ---- a6 PCO build, in waves of at most 2 x 152 tensors -----------------------
-  const int wave = std::min(N, 304);
-  DevBuf scr, tk;
-  CK(scr.alloc(sizeof(double2) * scr_max * wave, s));
-  CK(tk.alloc(sizeof(SiteTask) * wave, s));
-  std::vector<SiteTask> tasks(wave);
-  for (int m0 = 0; m0 < N; m0 += wave) {
-    int cnt = std::min(wave, N - m0);
-    for (int k = 0; k < cnt; ++k) {
-      int m = m0 + k;
-      SiteTask& t = tasks[k];
-      t.nl = M->ne[m]; t.nr = M->ne[m + 1]; t.Dl = M->D[m]; t.Dr = M->D[m + 1];
-      t.Q = M->Qm + (size_t)m * QS * QS; t.qs = QS;
-      t.c = 0.0;   // set on device below (c_m lives in device memory)
-      t.occl = ba.occ + (size_t)m * cap * NEM; t.lowl = ba.low + (size_t)m * NEM * cap; t.capl = cap;
-      t.occr = ba.occ + (size_t)(m + 1) * cap * NEM; t.lowr = ba.low + (size_t)(m + 1) * NEM * cap;
-      t.capr = cap;
-      t.out = M->tensors.as<double2>() + M->toff[m];
-      t.scratch_off = (size_t)k * scr_max;
-    }
-    // c_m: copy the device scale factors into the task records
-    std::vector<double> cm(cnt);
-    CK(cudaMemcpyAsync(cm.data(), M->cm + m0, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int k = 0; k < cnt; ++k) tasks[k].c = cm[k];
-    CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * cnt, cudaMemcpyHostToDevice, s));
-    // the PCO build stays FP64 in both precisions: on this part it is a few
-    // percent of a step, and the tensors feed FP64 amplitudes and the norm
-    CK(launch_pco(tk.as<SiteTask>(), cnt, o->d, GBSMPS_PREC_FP64, scr.as<double2>(), c->d_status, s));
-    COUNT_LAUNCH(1);
-    CK(cudaStreamSynchronize(s));   // the task records are reused by the next wave
-  }
-  scr.release();
-  tk.release();
-  tm.mark("pco");
-  // ---- a7 right environments and normalisation ------------------------------
-  double2* R = M->env.as<double2>();
-  double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
-  CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
-  size_t xmax = 0;
-  for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * o->d * M->D[m + 1]);
-  DevBuf xb;
-  CK(xb.alloc(sizeof(double2) * (xmax + 8), s));
-  double2* X = xb.as<double2>();
-  const int d = o->d;
-  const bool mixed = o->precision == GBSMPS_PREC_MIXED;
-  if (mixed) {
-    // energy gauge (FP64) and environments in double-float arithmetic on the
-    // FP32 pipes (~44-bit): the chain of N dependent products sets the norm,
-    // so its per-step error must stay far below the tensor cores' FP32
-    // accumulation error
-    CK(M->tens_mixed.alloc(sizeof(double2) * tot, s));
-    double2* Ah = M->tens_mixed.as<double2>();
-    for (int m = 0; m < N; ++m) {
-      CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
-                             ba.E + (size_t)m * cap, ba.E + (size_t)(m + 1) * cap,
-                             Ah + M->toff[m], s));
-      COUNT_LAUNCH(1);
-    }
-    tm.mark("energy_gauge");
-    const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
-    DevBuf kw;
-    CK(kw.alloc(wbytes, s));
-    for (int m = N - 1; m >= 0; --m) {
-      int Dl = M->D[m], Dr = M->D[m + 1];
-      const double2* A = Ah + M->toff[m];
-      CK(launch_zgemm_df64('N', 'N', Dl * d, Dr, Dr, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, X, Dr, 0,
-                           1, s, kw.p, wbytes));
-      CK(launch_zgemm_df64('N', 'C', Dl, Dl, d * Dr, X, d * Dr, 0, A, d * Dr, 0, R + M->eoff[m], Dl,
-                           0, 1, s, kw.p, wbytes));
-    }
-    kw.release();
-  } else {
-    for (int m = N - 1; m >= 0; --m) {
-      int Dl = M->D[m], Dr = M->D[m + 1];
-      const double2* A = M->tensors.as<double2>() + M->toff[m];
-      CK(launch_zgemm('N', 'N', Dl * d, Dr, Dr, one, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, zero, X,
-                      Dr, 0, 1, s));
-      CK(launch_zgemm('N', 'C', Dl, Dl, d * Dr, one, X, d * Dr, 0, A, d * Dr, 0, zero,
-                      R + M->eoff[m], Dl, 0, 1, s));
-      COUNT_LAUNCH(2);
-    }
-  }
-  tm.mark("environments");
-  // vacuum amplitude, then A^1 *= conj(phase)/sqrt(norm^2)
-  DevBuf ab;
-  CK(ab.alloc(sizeof(double2) * (2 * (size_t)M->maxD + 8) + N, s));
-  double2* awork = ab.as<double2>();
-  double2* amp0 = awork + 2 * M->maxD;
-  double2* fac = amp0 + 1;
-  uint8_t* zpat = reinterpret_cast<uint8_t*>(fac + 2);
-  CK(cudaMemsetAsync(zpat, 0, N, s));
-  ChainView cv{N, d, M->D.data(), M->toff.data(), M->tensors.as<double2>()};
-  CK(launch_amplitudes(cv, 1, zpat, amp0, awork, M->maxD, s));
-  COUNT_LAUNCH(2 + N);
-  CK(launch_norm_phase(R + M->eoff[0], amp0, fac, c->d_status, s));
-  CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
-  COUNT_LAUNCH(2);
-  if (mixed) {   // the normalised first tensor in the energy gauge (D_0 = 1)
-    CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], ba.E, ba.E + cap,
-                           M->tens_mixed.as<double2>(), s));
-    COUNT_LAUNCH(1);
-  }
-  tm.mark("normalise");
-  if (mixed) {
-    // ---- right-canonical form for the tensor-core sampler -----------------
-    // R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
-    // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as fp16 planes per site
-    CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
-    CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
-                       cudaMemcpyHostToDevice, s));
-    CK(M->lchol.alloc(sizeof(double2) * (etot + 8), s));
-    CK(M->linv.alloc(sizeof(double2) * (etot + 8), s));
-    DevBuf du;                     // regulariser each bond needed (relative)
-    CK(du.alloc(sizeof(double) * (N + 1), s));
-    CK(cudaMemsetAsync(du.p, 0, sizeof(double) * (N + 1), s));
-    CK(launch_chol(R, M->lchol.as<double2>(), M->eoff_dev.as<long long>(), ba.D, 1, N - 1,
-                   du.as<double>(), c->d_status, s));
-    if (tm.on) {
-      std::vector<double> h(N + 1);
-      cudaMemcpyAsync(h.data(), du.p, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      double mx = 0.0;
-      for (double v : h) mx = std::max(mx, v);
-      fprintf(stderr, "[gbsmps] largest Cholesky regulariser: %.1e of max diag\n", mx);
-    }
-    du.release();
-    CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
-                    ba.D, 1, N - 1, s));
-    COUNT_LAUNCH(2);
-    for (int b : {0, N}) {
-      CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
-                         cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(M->linv.as<double2>() + M->eoff[b], &one, sizeof(double2),
-                         cudaMemcpyHostToDevice, s));
-    }
-    tm.mark("cholesky");
-    M->Drp.resize(N); M->Kp.resize(N); M->Np.resize(N); M->bpoff.resize(N); M->bmaps.resize(N);
-    long long btot = 0;
-    for (int m = 0; m < N; ++m) {
-      M->Drp[m] = (M->D[m + 1] + 63) / 64 * 64;
-      M->Kp[m] = (2 * M->D[m] + 63) / 64 * 64;
-      M->Np[m] = 2 * d * M->Drp[m];
-      M->bpoff[m] = btot;
-      btot += 2LL * M->Np[m] * M->Kp[m];
-    }
-    CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
-    DevBuf tb, ab2, kw2;
-    const size_t wbytes2 = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
-    CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
-    CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
-    CK(kw2.alloc(wbytes2, s));
-    const double2* Ah = M->tens_mixed.as<double2>();
-    for (int m = 0; m < N; ++m) {
-      const int Dl = M->D[m], Dr = M->D[m + 1];
-      float2* T = tb.as<float2>();
-      float2* At = ab2.as<float2>();
-      // the canonical tensors feed fp16x2 planes: FP32-level products suffice
-      CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
-                         M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
-                         kw2.p, wbytes2));
-      const float2* src = T;
-      if (m > 0) {
-        CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
-                           T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, kw2.p, wbytes2));
-        src = At;
-      }
-      __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
-      CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
-      COUNT_LAUNCH(1);
-      if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
-        return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
-    }
-    tb.release(); ab2.release(); kw2.release();
-    tm.mark("canonical_pack");
-  }
-  // R_0 of the normalised state is 1
-  CK(cudaMemcpyAsync(R + M->eoff[0], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
-  xb.release();
-  ab.release();
-  tm.mark("normalise");
-  rc = sync_status(c);
-  if (rc) return rc;
-  *out = guard.release();
-  return GBSMPS_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -489,7 +66,7 @@ int gbsmps_build_from_cov(gbsmps_ctx_t c, int32_t N, const double* gamma, int me
     CK(cudaMemcpyAsync(g.p, gamma, bytes, cudaMemcpyHostToDevice, c->stream));
     dg = g.as<double>();
   }
-  rc = build_core(c, N, dg, o, out);
+  rc = gbs::build_single(c, N, dg, o, out);
   g.release();
   return rc;
 }
@@ -516,7 +93,7 @@ int gbsmps_build_from_Q(gbsmps_ctx_t c, int32_t N, const double* Q, int mem_kind
   CK(launch_q_to_gamma(dq, N, gb.as<double>(), wb.as<double2>(), c->d_status, s));
   COUNT_LAUNCH(2 + 2 * (unsigned long long)N);
   rc = sync_status(c);
-  if (rc == GBSMPS_OK) rc = build_core(c, N, gb.as<double>(), o, out);
+  if (rc == GBSMPS_OK) rc = gbs::build_single(c, N, gb.as<double>(), o, out);
   qb.release(); gb.release(); wb.release();
   return rc;
 }
@@ -779,7 +356,7 @@ int gbsmps_build_site_noalloc(gbsmps_ctx_t c, int32_t nl, int32_t nr, int32_t d,
 }
 
 size_t gbsmps_estimate_bytes(int32_t N, const gbsmps_opts* o, int64_t S) {
-  // mirrors the allocations of build_core and gbsmps_sample with every bond
+  // mirrors the allocations of the build pipeline and gbsmps_sample with every bond
   // at chi_max (D_m <= chi); transient buffers are counted as if all were live
   if (N < 1 || S < 0 || check_opts(o) != GBSMPS_OK) return 0;
   const double n = N, d = o->d, chi = o->chi_max, cap = chi + TIE_MARGIN;

@@ -1,0 +1,194 @@
+// Batched build of many independent states (gbsmps_build_batch).
+//
+// The per-state pipeline has two sequential chains, the GSVD over the cuts
+// (left to right) and the right environments (right to left); everything
+// else is parallel over sites.  A batch runs the chains of all states side by
+// side instead of one after another: every GSVD chain in one launch (one CTA
+// per state), the PCO tensors of all sites of all states in waves of one
+// launch each, the energy gauge of all sites in one launch, the environment
+// chains of all mixed-precision states in one persistent cooperative launch
+// (step k takes site N_s - 1 - k of every state, grid-wide barriers between
+// the two products of a step), and the normalisations in one launch (one CTA
+// per state).  Bond sizes are read back once for the whole batch.  The
+// right-canonical packing of the sampler then runs per state.
+#include "objects.h"
+#include <algorithm>
+#include <map>
+
+namespace {
+
+template <class T>
+int upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
+  CK(b.alloc(sizeof(T) * std::max<size_t>(v.size(), 1), s));
+  if (!v.empty()) CK(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+  return GBSMPS_OK;
+}
+
+}  // namespace
+
+extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
+                                  const double* const* gammas, int mem_kind,
+                                  const gbsmps_opts* opts, gbsmps_mps_t* out) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  if (count < 0) return fail(GBSMPS_ERR_ARG, "count < 0");
+  if (count == 0) return GBSMPS_OK;
+  if (!Ns || !gammas || !opts || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (mem_kind != GBSMPS_MEM_HOST && mem_kind != GBSMPS_MEM_DEVICE) return fail(GBSMPS_ERR_ARG, "mem_kind");
+  for (int i = 0; i < count; ++i) {
+    if (!gammas[i]) return fail(GBSMPS_ERR_ARG, "gammas[" + std::to_string(i) + "] is NULL");
+    if (Ns[i] < 1 || Ns[i] > 1000000) return fail(GBSMPS_ERR_ARG, "N out of range");
+    int rc = check_opts(&opts[i]);
+    if (rc) return rc;
+    out[i] = nullptr;
+  }
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  StageTimer tm(s);
+  std::vector<DevBuf> gin(count);
+  std::vector<const double*> dg(count);
+  for (int i = 0; i < count; ++i) {
+    dg[i] = gammas[i];
+    if (mem_kind == GBSMPS_MEM_HOST) {
+      const size_t bytes = sizeof(double) * 4 * (size_t)Ns[i] * Ns[i];
+      CK(gin[i].alloc(bytes, s));
+      CK(cudaMemcpyAsync(gin[i].p, gammas[i], bytes, cudaMemcpyHostToDevice, s));
+      dg[i] = gin[i].as<double>();
+    }
+  }
+  auto release_inputs = [&] { for (auto& b : gin) b.release(); };
+  std::vector<std::unique_ptr<gbsmps_mps>> Ms(count);
+  std::vector<gbs::Front> F(count);
+  int rc = GBSMPS_OK;
+  for (int i = 0; i < count && !rc; ++i) {
+    Ms[i].reset(new gbsmps_mps());
+    rc = gbs::alloc_front(Ms[i].get(), c, Ns[i], &opts[i], &F[i]);
+    if (!rc) rc = gbs::launch_checks(c, Ms[i].get(), dg[i], &opts[i], F[i]);
+  }
+  if (rc) { release_inputs(); return rc; }
+  tm.mark("validate");
+  // a2-a3: all GSVD chains in one launch
+  {
+    std::vector<ChainJob> cj(count);
+    for (int i = 0; i < count; ++i) {
+      gbsmps_mps* M = Ms[i].get();
+      cj[i] = ChainJob{dg[i], Ns[i], F[i].dbw, opts[i].lambda2_freeze, F[i].Gs, M->ba, M->Qm, M->cm};
+    }
+    DevBuf jb;
+    rc = upload(jb, cj, s);
+    if (rc) { release_inputs(); return rc; }
+    CK(launch_gsvd_chain_batch(jb.as<ChainJob>(), count, c->d_status, s));
+    COUNT_LAUNCH(1);
+    jb.release();
+  }
+  tm.mark("gsvd_chain");
+  // a4-a5 kept bases and maps; one read-back of the bond sizes for the batch
+  for (int i = 0; i < count && !rc; ++i) rc = gbs::launch_bases(c, Ms[i].get(), &opts[i]);
+  if (rc) { release_inputs(); return rc; }
+  std::vector<gbs::Readback> rb(count);
+  for (int i = 0; i < count && !rc; ++i) rc = gbs::enqueue_readback(Ms[i].get(), &rb[i], s);
+  if (!rc) rc = sync_status(c);
+  release_inputs();
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) gbs::finish_readback(Ms[i].get(), rb[i]);
+  tm.mark("basis_maps");
+  // a6: PCO tensors of every site of every state (one wave set per cutoff d)
+  size_t scr_max = 0;
+  for (int i = 0; i < count && !rc; ++i) rc = gbs::alloc_tensors(Ms[i].get(), s, &scr_max);
+  if (rc) return rc;
+  {
+    std::map<int, std::vector<SiteTask>> by_d;
+    for (int i = 0; i < count; ++i) gbs::site_tasks(Ms[i].get(), rb[i].cm, by_d[opts[i].d]);
+    for (auto& kv : by_d) {
+      rc = gbs::run_pco(c, kv.second, scr_max, kv.first);
+      if (rc) return rc;
+    }
+  }
+  tm.mark("pco");
+  // a7: environments and normalisation
+  std::vector<int> mixed;
+  for (int i = 0; i < count; ++i) {
+    gbsmps_mps* M = Ms[i].get();
+    if (opts[i].precision == GBSMPS_PREC_MIXED) {
+      mixed.push_back(i);
+      continue;
+    }
+    rc = gbs::env_single(c, M, tm);
+    if (!rc) rc = gbs::normalise_single(c, M);
+    if (rc) return rc;
+  }
+  if (!mixed.empty()) {
+    // energy gauge of every site, one launch per cutoff d
+    std::map<int, std::vector<GaugeTask>> gt;
+    std::map<int, int> gmax;
+    for (int i : mixed) {
+      gbsmps_mps* M = Ms[i].get();
+      CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
+      const int cap = M->ba.cap;
+      for (int m = 0; m < M->N; ++m) {
+        gt[M->d].push_back(GaugeTask{M->tensors.as<double2>() + M->toff[m], M->D[m], M->D[m + 1],
+                                     M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
+                                     M->tens_mixed.as<double2>() + M->toff[m]});
+        gmax[M->d] = std::max(gmax[M->d], M->D[m] * M->d * M->D[m + 1]);
+      }
+    }
+    std::vector<DevBuf> gb(gt.size());
+    int gi = 0;
+    for (auto& kv : gt) {
+      rc = upload(gb[gi], kv.second, s);
+      if (rc) return rc;
+      CK(launch_energy_gauge_batch(gb[gi].as<GaugeTask>(), (int)kv.second.size(), kv.first,
+                                   gmax[kv.first], s));
+      COUNT_LAUNCH(1);
+      ++gi;
+    }
+    tm.mark("energy_gauge");
+    // per-state device offset tables and product scratch
+    const size_t nm = mixed.size();
+    std::vector<DevBuf> offs(nm), xs(nm);
+    std::vector<EnvJob> ej(nm);
+    std::vector<NormJob> nj(nm);
+    int maxN = 0, maxD = 1;
+    const double2 one = cmk(1.0, 0.0);
+    for (size_t k = 0; k < nm; ++k) {
+      gbsmps_mps* M = Ms[mixed[k]].get();
+      const int N = M->N;
+      std::vector<long long> tab(M->toff);
+      tab.insert(tab.end(), M->eoff.begin(), M->eoff.end());
+      rc = upload(offs[k], tab, s);
+      if (rc) return rc;
+      CK(xs[k].alloc(sizeof(double2) * ((size_t)M->d * M->maxD * M->maxD + 8), s));
+      double2* R = M->env.as<double2>();
+      CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+      const long long* toff_d = offs[k].as<long long>();
+      ej[k] = EnvJob{N, M->d, M->ba.D, toff_d, toff_d + N, M->tens_mixed.as<double2>(), R,
+                     xs[k].as<double2>()};
+      nj[k] = NormJob{N, M->d, M->ba.D, toff_d, M->tensors.as<double2>(), R,
+                      M->tens_mixed.as<double2>(), M->ba.E + M->ba.cap};
+      maxN = std::max(maxN, N);
+      maxD = std::max(maxD, M->maxD);
+    }
+    DevBuf ejb, njb;
+    rc = upload(ejb, ej, s);
+    if (!rc) rc = upload(njb, nj, s);
+    if (rc) return rc;
+    CK(launch_env_chain_batch(ejb.as<EnvJob>(), (int)nm, maxN, s));
+    tm.mark("environments");
+    CK(launch_vac_norm_batch(njb.as<NormJob>(), (int)nm, maxD, c->d_status, s));
+    tm.mark("normalise");
+    // stream order keeps the scratch alive until the launches above are done
+    for (auto& b : xs) b.release();
+    for (auto& b : offs) b.release();
+    for (auto& b : gb) b.release();
+    ejb.release();
+    njb.release();
+    for (int i : mixed) {
+      rc = gbs::canonical_stage(c, Ms[i].get(), tm);
+      if (rc) return rc;
+    }
+  }
+  for (int i = 0; i < count && !rc; ++i) rc = gbs::finish(c, Ms[i].get());
+  if (!rc) rc = sync_status(c);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) out[i] = Ms[i].release();
+  return GBSMPS_OK;
+}

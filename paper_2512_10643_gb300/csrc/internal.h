@@ -154,6 +154,19 @@ cudaError_t launch_check_input(const double* gamma, int N, double purity_tol,
 cudaError_t launch_q_to_gamma(const double2* Q, int N, double* gamma, double2* work,
                               int* status, cudaStream_t s);
 cudaError_t launch_bandwidth(const double* gamma, int N, int* bw, cudaStream_t s);
+// one state of a batched GSVD chain launch (device pointers of that state)
+struct ChainJob {
+  const double* gamma;
+  int N;
+  const int* bw;
+  double freeze;
+  double* G;
+  BondArrays ba;
+  double2* Qm;
+  double* cm;
+};
+cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int* status,
+                                    cudaStream_t s);
 cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
                               double lambda2_freeze, double* Gscratch,
                               BondArrays ba, double2* Qm, double* cm, int* status,
@@ -188,6 +201,17 @@ cudaError_t launch_zscale(double2* x, size_t n, const double2* factor, cudaStrea
 cudaError_t launch_norm_phase(const double2* R0, const double2* amp0, double2* factor,
                               int* status, cudaStream_t s);
 
+struct NormJob {         // one state of the batched normalisation
+  int N, d;
+  const int* D;            // bond dimensions [N + 1] (device)
+  const long long* toff;   // tensor offsets [N] (device)
+  double2* T;              // FP64 tensors; A^1 is rescaled in place
+  const double2* R0;       // norm^2
+  double2* Ah;             // mixed path: energy-gauge tensors (A^1 rewritten), else null
+  const double* E1;        // energies of bond 1 (mixed path)
+};
+cudaError_t launch_vac_norm_batch(const NormJob* jobs_dev, int count, int maxD, int* status,
+                                  cudaStream_t s);
 struct ChainView {       // view of an MPS for the amplitude kernels
   int N, d;
   const int* D;          // host: N+1 bond dims
@@ -202,6 +226,15 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        const double* u, int ustride, int site, uint64_t seed,
                                        uint64_t counter0, float2* vnew, uint8_t* out, int N,
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
+struct GaugeTask {        // one site of a batched energy-gauge launch
+  const double2* A;
+  int Dl, Dr;
+  const double* El;
+  const double* Er;
+  double2* Ah;
+};
+cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, int d, int max_elems,
+                                      cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
                                 const double* Er, double2* Ah, cudaStream_t s);
 // allocation-free single-site build (noalloc.cu)
@@ -214,6 +247,17 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
                               long long sA, const double2* B, long long ldb, long long sB,
                               double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
                               void* work = nullptr, size_t work_bytes = 0);
+// one state of the batched persistent environment chain (device pointers)
+struct EnvJob {
+  int N, d;
+  const int* D;            // bond dimensions [N + 1]
+  const long long* toff;   // tensor offsets [N]
+  const long long* eoff;   // environment offsets [N + 1]
+  const double2* Ah;       // energy-gauge tensors
+  double2* R;              // environments (R^N = 1 on entry)
+  double2* X;              // scratch, >= d maxD^2 complex
+};
+cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s);
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_fp16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);

@@ -13,6 +13,9 @@
 // Tile: 64 x 64 complex outputs, 8 complex k per stage, 256 threads of 4 x 4.
 #include "internal.h"
 #include <algorithm>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -48,16 +51,19 @@ struct DfArgs {
   double2* part;
 };
 
-__global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
-  // re/im, hi/lo split operands
-  __shared__ float As[DK][DM][4];
-  __shared__ float Bs[DK][DN][4];
-  const long long bz = blockIdx.z / p.ksplit;
-  const int kz = blockIdx.z % p.ksplit;
-  const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
-  const int i0 = blockIdx.y * DM, j0 = blockIdx.x * DN;
-  const double2* A = p.A + bz * p.sA;
-  const double2* B = p.B + bz * p.sB;
+// one 64 x 64 complex output tile of C = op(A) op(B) over k in [kbeg, kend),
+// written to C[gi * ldc + gj] (the whole CTA calls it together)
+struct DfTile {
+  int M, N, opa, opb;
+  const double2* A; long long lda;
+  const double2* B; long long ldb;
+  double2* C; long long ldc;
+};
+
+__device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbeg, int kend,
+                                        float (*As)[DM][4], float (*Bs)[DN][4]) {
+  const double2* A = p.A;
+  const double2* B = p.B;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float ah[4][4][2], al[4][4][2];   // [row][col][re/im] hi and lo accumulators
 #pragma unroll
@@ -127,10 +133,65 @@ __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
     for (int c = 0; c < 4; ++c) {
       const int gj = j0 + tx + 16 * c;
       if (gj >= p.N) continue;
-      const double2 v = make_double2((double)ah[r][c][0] + (double)al[r][c][0],
-                                     (double)ah[r][c][1] + (double)al[r][c][1]);
-      if (p.ksplit > 1) p.part[((long long)blockIdx.z * p.M + gi) * p.N + gj] = v;
-      else p.C[bz * p.sC + (long long)gi * p.ldc + gj] = v;
+      p.C[(long long)gi * p.ldc + gj] =
+          make_double2((double)ah[r][c][0] + (double)al[r][c][0],
+                       (double)ah[r][c][1] + (double)al[r][c][1]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
+  // re/im, hi/lo split operands
+  __shared__ float As[DK][DM][4];
+  __shared__ float Bs[DK][DN][4];
+  const long long bz = blockIdx.z / p.ksplit;
+  const int kz = blockIdx.z % p.ksplit;
+  const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
+  DfTile t{p.M, p.N, p.opa, p.opb, p.A + bz * p.sA, p.lda, p.B + bz * p.sB, p.ldb,
+           p.ksplit > 1 ? p.part + (long long)blockIdx.z * p.M * p.N : p.C + bz * p.sC,
+           p.ksplit > 1 ? (long long)p.N : p.ldc};
+  df_tile(t, blockIdx.y * DM, blockIdx.x * DN, kbeg, kend, As, Bs);
+}
+
+// Right-environment chains of many states in one persistent cooperative
+// launch.  Step k handles site m = N_s - 1 - k of every state s with N_s > k:
+// phase 0: X_s = Ahat^m (D_m d x D_{m+1}) R^{m+1}; phase 1: R^m = X_s
+// (D_m x d D_{m+1}) Ahat^m^dag.  The output tiles of all states in a phase are
+// dealt round-robin to the CTAs, and a grid-wide barrier separates phases
+// (all CTAs are co-resident by construction of the cooperative launch).
+__global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict__ jobs, int count,
+                                                       int maxN) {
+  __shared__ float As[DK][DM][4];
+  __shared__ float Bs[DK][DN][4];
+  cg::grid_group grid = cg::this_grid();
+  for (int k = 0; k < maxN; ++k) {
+    for (int phase = 0; phase < 2; ++phase) {
+      long long base = 0, t = blockIdx.x;
+      for (int j = 0; j < count; ++j) {
+        const EnvJob J = jobs[j];
+        if (k >= J.N) continue;
+        const int m = J.N - 1 - k;
+        const int Dl = J.D[m], Dr = J.D[m + 1];
+        const double2* A = J.Ah + J.toff[m];
+        DfTile p;
+        int K;
+        if (phase == 0) {
+          p = DfTile{Dl * J.d, Dr, 0, 0, A, Dr, J.R + J.eoff[m + 1], Dr, J.X, Dr};
+          K = Dr;
+        } else {
+          p = DfTile{Dl, Dl, 0, 1, J.X, (long long)J.d * Dr, A, (long long)J.d * Dr,
+                     J.R + J.eoff[m], Dl};
+          K = J.d * Dr;
+        }
+        const long long tn = (p.N + DN - 1) / DN;
+        const long long nt = ((p.M + DM - 1) / DM) * tn;
+        for (; t < base + nt; t += gridDim.x) {
+          const long long l = t - base;
+          df_tile(p, (int)(l / tn) * DM, (int)(l % tn) * DN, 0, K, As, Bs);
+        }
+        base += nt;
+      }
+      grid.sync();
     }
   }
 }
@@ -176,4 +237,20 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
     COUNT_LAUNCH(1);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s) {
+  if (count <= 0 || maxN <= 0) return cudaSuccess;
+  int dev = 0, nsm = 0, per = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev))) return e;
+  if (!coop) return cudaErrorNotSupported;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, env_chain_kernel, 256, 0))) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {(void*)&jobs_dev, (void*)&count, (void*)&maxN};
+  e = cudaLaunchCooperativeKernel((const void*)env_chain_kernel, dim3(nsm * per), dim3(256), args, 0, s);
+  COUNT_LAUNCH(1);
+  return e;
 }

@@ -341,12 +341,10 @@ __device__ void last_site(ChainSmem& sm, int nL, double2* Qout, int* status) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(CHAIN_THREADS)
-gsvd_chain_kernel(const double* __restrict__ gam, int N, const int* __restrict__ bwp,
-                  double freeze, double* __restrict__ Gs, BondArrays ba,
-                  double2* __restrict__ Qm, double* __restrict__ cm, int* status) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  ChainSmem& sm = *reinterpret_cast<ChainSmem*>(smraw);
+__device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
+                           const int* __restrict__ bwp, double freeze, double* __restrict__ Gs,
+                           BondArrays ba, double2* __restrict__ Qm, double* __restrict__ cm,
+                           int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long twoN = 2LL * N;
   const int bw = max(1, min(*bwp, N));
@@ -576,6 +574,24 @@ gsvd_chain_kernel(const double* __restrict__ gam, int N, const int* __restrict__
   }
 }
 
+__global__ void __launch_bounds__(CHAIN_THREADS)
+gsvd_chain_kernel(const double* __restrict__ gam, int N, const int* __restrict__ bwp,
+                  double freeze, double* __restrict__ Gs, BondArrays ba,
+                  double2* __restrict__ Qm, double* __restrict__ cm, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  chain_body(*reinterpret_cast<ChainSmem*>(smraw), gam, N, bwp, freeze, Gs, ba, Qm, cm, status);
+}
+
+// many states at once: CTA b walks the chain of state b (the chains are
+// independent, so a batch runs them side by side, one SM each)
+__global__ void __launch_bounds__(CHAIN_THREADS)
+gsvd_chain_batch_kernel(const ChainJob* __restrict__ jobs, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ChainJob j = jobs[blockIdx.x];
+  chain_body(*reinterpret_cast<ChainSmem*>(smraw), j.gamma, j.N, j.bw, j.freeze, j.G, j.ba, j.Qm,
+             j.cm, status);
+}
+
 // ---- input checks -----------------------------------------------------------
 // max |Gamma - Gamma^T| and max |(2 Gamma Omega)^2 + 1|, tiled 32 x 32.
 __global__ void check_input_kernel(const double* __restrict__ g, int N,
@@ -748,5 +764,16 @@ cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
   if (e) return e;
   gsvd_chain_kernel<<<1, CHAIN_THREADS, smem, s>>>(gamma, N, bw, lambda2_freeze, Gscratch,
                                                    ba, Qm, cm, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int* status,
+                                    cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  size_t smem = sizeof(ChainSmem);
+  cudaError_t e = cudaFuncSetAttribute(gsvd_chain_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return e;
+  gsvd_chain_batch_kernel<<<count, CHAIN_THREADS, smem, s>>>(jobs_dev, status);
   return cudaGetLastError();
 }

@@ -102,6 +102,56 @@ __global__ void norm_phase_kernel(const double2* R0, const double2* amp0, double
   else *f = cmk(s, 0.0);
 }
 
+// Normalisation of many states in one launch (CTA = state): the all-vacuum
+// amplitude v = A^1[0] A^2[0] .. A^N[0] by a chain of vector-matrix products
+// in shared memory, the factor conj(v)/|v| / sqrt(R_0) applied to A^1
+// (unit norm, vacuum amplitude real positive), and, for the mixed path, the
+// energy-gauge copy of the rescaled A^1 (D_0 = 1, so its left energy is 0).
+__global__ void vac_norm_kernel(const NormJob* __restrict__ jobs, int maxD, int* status) {
+  extern __shared__ double2 vsm[];
+  const NormJob J = jobs[blockIdx.x];
+  double2* v = vsm;
+  double2* vn = vsm + maxD;
+  const int tid = threadIdx.x, nt = blockDim.x, d = J.d;
+  if (tid == 0) v[0] = cmk(1.0, 0.0);
+  __syncthreads();
+  for (int m = 0; m < J.N; ++m) {
+    const int Dl = J.D[m], Dr = J.D[m + 1];
+    const double2* T = J.T + J.toff[m];
+    for (int b = tid; b < Dr; b += nt) {
+      double2 acc = cmk(0.0, 0.0);
+      for (int a = 0; a < Dl; ++a) cfma(acc, v[a], T[((size_t)a * d) * Dr + b]);
+      vn[b] = acc;
+    }
+    __syncthreads();
+    double2* t = v; v = vn; vn = t;
+  }
+  __shared__ double2 fac;
+  if (tid == 0) {
+    const double n2 = J.R0->x;
+    const double2 a = v[0];
+    const double mg = sqrt(cabs2(a));
+    if (!(n2 > 0.0) || !isfinite(n2)) {
+      set_status(status, ST_NUMERIC);
+      fac = cmk(1.0, 0.0);
+    } else {
+      const double s = 1.0 / sqrt(n2);
+      fac = mg > 0.0 ? cmk(a.x / mg * s, -a.y / mg * s) : cmk(s, 0.0);
+    }
+  }
+  __syncthreads();
+  const int D1 = J.D[1];
+  for (int i = tid; i < d * D1; i += nt) {
+    const double2 x = cmul(J.T[i], fac);
+    J.T[i] = x;
+    if (J.Ah) {
+      const int b = i % D1;
+      const double er = D1 > 1 ? J.E1[b] : 0.0;
+      J.Ah[i] = cscale(x, exp(-0.5 * er));
+    }
+  }
+}
+
 // amplitudes: Vn[s, b] = sum_a V[s, a] A[a, n_s, b]
 __global__ void amp_step_kernel(const double2* __restrict__ T, int Dl, int d, int Dr,
                                 const uint8_t* __restrict__ pats, int N, int site,
@@ -297,5 +347,17 @@ cudaError_t launch_init_ones_f(float2* V, long long P, cudaStream_t s) {
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   init_ones_f_kernel<<<blocks, 256, 0, s>>>(V, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vac_norm_batch(const NormJob* jobs_dev, int count, int maxD, int* status,
+                                  cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double2) * 2 * (size_t)std::max(maxD, 1);
+  cudaError_t e = cudaFuncSetAttribute(vac_norm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e) return e;
+  vac_norm_kernel<<<count, 256, smem, s>>>(jobs_dev, maxD, status);
+  COUNT_LAUNCH(1);
   return cudaGetLastError();
 }

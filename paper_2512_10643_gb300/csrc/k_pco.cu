@@ -22,6 +22,7 @@
 // T = double is the FP64 path; T = float runs the same passes in FP32 (the
 // mixed-precision build) and accumulates the output tensor in FP64.
 #include "internal.h"
+#include <algorithm>
 #include <math.h>
 
 namespace {
@@ -259,7 +260,31 @@ __global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d
   }
 }
 
+// the same over many sites (blockIdx.y = task) in one launch
+__global__ void energy_gauge_batch_kernel(const GaugeTask* __restrict__ tasks, int d) {
+  const GaugeTask t = tasks[blockIdx.y];
+  const size_t n = (size_t)t.Dl * d * t.Dr;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = idx / ((size_t)d * t.Dr), b = idx % t.Dr;
+    const double el = t.Dl > 1 ? t.El[a] : 0.0, er = t.Dr > 1 ? t.Er[b] : 0.0;
+    t.Ah[idx] = cscale(t.A[idx], exp(-0.5 * (er - el)));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, int d, int max_elems,
+                                      cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  int bx = (max_elems + 255) / 256;
+  bx = std::max(1, std::min(bx, 64));
+  for (int t0 = 0; t0 < ntasks; t0 += 65535) {
+    dim3 grid(bx, std::min(65535, ntasks - t0));
+    energy_gauge_batch_kernel<<<grid, 256, 0, s>>>(tasks_dev + t0, d);
+  }
+  return cudaGetLastError();
+}
 
 size_t pco_scratch_elems(int Dl, int Dr) {
   return 2 * (size_t)Dl + 2 * (size_t)Dr + 4 * (size_t)Dl * Dr;

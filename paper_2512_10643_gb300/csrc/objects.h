@@ -1,0 +1,179 @@
+// Library objects shared by the host translation units (api.cu, batch.cu):
+// contexts, stream-ordered device buffers, MPS handles, error reporting and
+// the opt-in stage timer.  Host code only.
+#pragma once
+#include "internal.h"
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <memory>
+#include <string>
+#include <vector>
+
+extern thread_local std::string g_detail;
+
+
+inline int fail(int code, const std::string& what) {
+  g_detail = what;
+  return code;
+}
+
+#define CK(expr)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? GBSMPS_ERR_OOM : GBSMPS_ERR_CUDA, \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+    }                                                                              \
+  } while (0)
+
+// Opt-in stage tracing: with GBSMPS_PROFILE=1 every pipeline records CUDA
+// events between its stages and prints the elapsed times to stderr.
+struct StageTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<std::string, cudaEvent_t>> ev;
+  explicit StageTimer(cudaStream_t st) : s(st) {
+    const char* e = getenv("GBSMPS_PROFILE");
+    on = e && e[0] == '1';
+    mark("start");
+  }
+  int* dbg_status = nullptr;       // GBSMPS_DEBUG=1: status word checked at every mark
+  std::string failed_stage;
+  void mark(const char* name) {
+    if (dbg_status && failed_stage.empty()) {
+      int st = 0;
+      cudaMemcpyAsync(&st, dbg_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      if (st) {
+        failed_stage = name;
+        fprintf(stderr, "[gbsmps] device status %d raised in stage '%s'\n", st, name);
+      }
+    }
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.emplace_back(name, e);
+  }
+  ~StageTimer() {
+    if (!on) return;
+    cudaEventSynchronize(ev.back().second);
+    for (size_t i = 1; i < ev.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
+      fprintf(stderr, "[gbsmps] %-14s %9.3f ms\n", ev[i].first.c_str(), ms);
+    }
+    for (auto& p : ev) cudaEventDestroy(p.second);
+  }
+};
+
+inline int status_to_code(int st) {
+  if (st & ST_NOT_SYMMETRIC) return GBSMPS_ERR_NOT_SYMMETRIC;
+  if (st & ST_NOT_PURE) return GBSMPS_ERR_NOT_PURE;
+  if (st & ST_BOUNDS) return GBSMPS_ERR_BOUNDS;
+  if (st & ST_NOT_CONVERGED) return GBSMPS_ERR_NOT_CONVERGED;
+  if (st & ST_NUMERIC) return GBSMPS_ERR_NUMERIC;
+  if (st & ST_TIMEOUT) return GBSMPS_ERR_TIMEOUT;
+  return st ? GBSMPS_ERR_CUDA : GBSMPS_OK;
+}
+
+struct gbsmps_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* d_status = nullptr;
+  unsigned long long launches_at_create = 0;
+};
+
+struct DevBuf {                // stream-ordered device allocation
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    if (bytes == 0) bytes = 16;
+    return cudaMallocAsync(&p, bytes, st);
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct gbsmps_mps {
+  gbsmps_ctx* ctx = nullptr;
+  int N = 0, d = 0, chi = 0, precision = 0;
+  std::vector<int> D, ne;
+  std::vector<double> eps;
+  std::vector<long long> toff, eoff;
+  int maxD = 1;
+  long long ttot = 0, etot = 0;   // complex elements of all tensors / all environments
+  DevBuf tensors, env, gsvd, bonds;
+  DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
+  // mixed path, right-canonical sampler: Cholesky factors of the environments,
+  // their inverses, and every site's canonical tensor as fp16 planes + TMA map
+  DevBuf eoff_dev, lchol, linv, bpack;
+  std::vector<int> Drp, Kp, Np;
+  std::vector<long long> bpoff;
+  std::vector<std::array<unsigned char, 128>> bmaps;
+  BondArrays ba{};
+  double* lam2 = nullptr;
+  double2* Qm = nullptr;
+  double* cm = nullptr;
+  ~gbsmps_mps() {
+    tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
+    eoff_dev.release(); lchol.release(); linv.release(); bpack.release();
+  }
+};
+
+inline int sync_status(gbsmps_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return fail(status_to_code(st), "device status word " + std::to_string(st));
+  }
+  return GBSMPS_OK;
+}
+
+inline int check_opts(const gbsmps_opts* o) {
+  if (!o) return fail(GBSMPS_ERR_ARG, "opts is NULL");
+  if (o->d < 1 || o->d > 255) return fail(GBSMPS_ERR_ARG, "d out of range [1,255]");
+  if (o->chi_max < 1 || o->chi_max > 4096) return fail(GBSMPS_ERR_ARG, "chi_max out of range [1,4096]");
+  if (!(o->eps_trunc >= 0.0 && o->eps_trunc < 1.0)) return fail(GBSMPS_ERR_ARG, "eps_trunc not in [0,1)");
+  if (!(o->lambda2_freeze >= 0.0 && o->lambda2_freeze < 1.0))
+    return fail(GBSMPS_ERR_ARG, "lambda2_freeze not in [0,1)");
+  if (o->precision != GBSMPS_PREC_FP64 && o->precision != GBSMPS_PREC_MIXED)
+    return fail(GBSMPS_ERR_ARG, "unknown precision");
+  return GBSMPS_OK;
+}
+
+
+// ---- build pipeline stages (pipeline.cu), shared by single and batched builds
+namespace gbs {
+struct Front {                  // per-state device scratch of the GSVD stage
+  double* Gs = nullptr;
+  int* dbw = nullptr;
+  double* work = nullptr;
+};
+struct Readback {               // host copies of the bond sizes and scale factors
+  std::vector<int> D, ne;
+  std::vector<double> eps, cm;
+};
+int alloc_front(gbsmps_mps* M, gbsmps_ctx* c, int N, const gbsmps_opts* o, Front* f);
+int launch_checks(gbsmps_ctx* c, gbsmps_mps* M, const double* dgamma, const gbsmps_opts* o,
+                  const Front& f);
+int launch_bases(gbsmps_ctx* c, gbsmps_mps* M, const gbsmps_opts* o);
+int enqueue_readback(gbsmps_mps* M, Readback* r, cudaStream_t s);
+void finish_readback(gbsmps_mps* M, const Readback& r);
+int alloc_tensors(gbsmps_mps* M, cudaStream_t s, size_t* scr_max);
+void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTask>& out);
+int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d);
+int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
+int normalise_single(gbsmps_ctx* c, gbsmps_mps* M);
+int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
+int finish(gbsmps_ctx* c, gbsmps_mps* M);
+int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
+                 gbsmps_mps_t* out);
+}  // namespace gbs

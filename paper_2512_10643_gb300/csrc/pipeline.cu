@@ -1,0 +1,390 @@
+// Stages of the build pipeline (Gamma on the device -> normalised MPS), shared
+// by the single-state entry points and the batched build: allocation of the
+// GSVD and bond arrays, input checks, kept bases, the host read-back of the
+// bond sizes, tensor storage, the PCO waves, the per-state environment chain
+// and normalisation, and the right-canonical packing of the mixed sampler.
+#include "objects.h"
+#include <algorithm>
+#include <cstring>
+
+namespace gbs {
+
+int alloc_front(gbsmps_mps* M, gbsmps_ctx* c, int N, const gbsmps_opts* o, Front* f) {
+  cudaStream_t s = c->stream;
+  M->ctx = c; M->N = N; M->d = o->d; M->chi = o->chi_max; M->precision = o->precision;
+  const int cap = o->chi_max + TIE_MARGIN;
+  const int nb = N + 1;
+  // GSVD outputs and the carried correlation block in one allocation
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
+  size_t o_Q = take(sizeof(double2) * (size_t)N * QS * QS);
+  size_t o_c = take(sizeof(double) * N);
+  size_t o_G = take(sizeof(double) * 2 * 2 * NEM * 2 * (size_t)std::max(N, 1));
+  size_t o_bw = take(sizeof(int) * 4);
+  size_t o_work = take(sizeof(double) * 8);
+  CK(M->gsvd.alloc(off, s));
+  char* g0 = M->gsvd.as<char>();
+  M->Qm = reinterpret_cast<double2*>(g0 + o_Q);
+  M->cm = reinterpret_cast<double*>(g0 + o_c);
+  f->Gs = reinterpret_cast<double*>(g0 + o_G);
+  f->dbw = reinterpret_cast<int*>(g0 + o_bw);
+  f->work = reinterpret_cast<double*>(g0 + o_work);
+  // kept bases, maps and per-bond scalars in one allocation
+  off = 0;
+  size_t o_occ = take((size_t)nb * cap * NEM);
+  size_t o_E = take(sizeof(double) * (size_t)nb * cap);
+  size_t o_low = take(sizeof(int) * (size_t)nb * NEM * cap);
+  size_t o_D = take(sizeof(int) * nb);
+  size_t o_ne = take(sizeof(int) * nb);
+  size_t o_mo = take(sizeof(int) * (size_t)nb * NEM);
+  size_t o_l2 = take(sizeof(double) * (size_t)nb * NEM);
+  size_t o_eps = take(sizeof(double) * nb);
+  CK(M->bonds.alloc(off, s));
+  char* b0 = M->bonds.as<char>();
+  BondArrays& ba = M->ba;
+  ba.cap = cap;
+  ba.occ = reinterpret_cast<uint8_t*>(b0 + o_occ);
+  ba.E = reinterpret_cast<double*>(b0 + o_E);
+  ba.low = reinterpret_cast<int*>(b0 + o_low);
+  ba.D = reinterpret_cast<int*>(b0 + o_D);
+  ba.ne = reinterpret_cast<int*>(b0 + o_ne);
+  ba.maxocc = reinterpret_cast<int*>(b0 + o_mo);
+  ba.lam2 = reinterpret_cast<double*>(b0 + o_l2);
+  ba.eps = reinterpret_cast<double*>(b0 + o_eps);
+  M->lam2 = ba.lam2;
+  CK(cudaMemsetAsync(b0, 0, off, s));
+  CK(cudaMemsetAsync(M->Qm, 0, sizeof(double2) * (size_t)N * QS * QS, s));
+  return GBSMPS_OK;
+}
+
+int launch_checks(gbsmps_ctx* c, gbsmps_mps* M, const double* dgamma, const gbsmps_opts* o,
+                  const Front& f) {
+  cudaStream_t s = c->stream;
+  if (o->validate) {
+    CK(launch_check_input(dgamma, M->N, o->purity_tol, f.work, c->d_status, s));
+    COUNT_LAUNCH(2);
+  }
+  CK(launch_bandwidth(dgamma, M->N, f.dbw, s));
+  COUNT_LAUNCH(1);
+  return GBSMPS_OK;
+}
+
+int launch_bases(gbsmps_ctx* c, gbsmps_mps* M, const gbsmps_opts* o) {
+  cudaStream_t s = c->stream;
+  const int nb = M->N + 1;
+  CK(launch_basis(M->ba, nb, o->chi_max, o->eps_trunc, c->d_status, s));
+  CK(launch_maps(M->ba, nb, c->d_status, s));
+  COUNT_LAUNCH(2);
+  return GBSMPS_OK;
+}
+
+int enqueue_readback(gbsmps_mps* M, Readback* r, cudaStream_t s) {
+  const int N = M->N, nb = N + 1;
+  r->D.assign(nb, 1);
+  r->ne.assign(nb, 0);
+  r->eps.assign(nb, 0.0);
+  r->cm.assign(N, 0.0);
+  CK(cudaMemcpyAsync(r->D.data(), M->ba.D, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r->ne.data(), M->ba.ne, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r->eps.data(), M->ba.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r->cm.data(), M->cm, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  return GBSMPS_OK;
+}
+
+void finish_readback(gbsmps_mps* M, const Readback& r) {
+  const int N = M->N;
+  M->D = r.D;
+  M->ne = r.ne;
+  M->eps.assign(r.eps.begin() + 1, r.eps.end() - 1);
+  M->D[0] = 1; M->D[N] = 1;
+}
+
+int alloc_tensors(gbsmps_mps* M, cudaStream_t s, size_t* scr_max) {
+  const int N = M->N, d = M->d;
+  M->toff.resize(N);
+  long long tot = 0;
+  size_t sm = 0;
+  M->maxD = 1;
+  for (int m = 0; m < N; ++m) {
+    M->toff[m] = tot;
+    tot += (long long)M->D[m] * d * M->D[m + 1];
+    sm = std::max(sm, pco_scratch_elems(M->D[m], M->D[m + 1]));
+    M->maxD = std::max(M->maxD, M->D[m]);
+  }
+  M->eoff.resize(N + 1);
+  long long etot = 0;
+  for (int m = 0; m <= N; ++m) { M->eoff[m] = etot; etot += (long long)M->D[m] * M->D[m]; }
+  M->ttot = tot;
+  M->etot = etot;
+  CK(M->tensors.alloc(sizeof(double2) * tot, s));
+  CK(M->env.alloc(sizeof(double2) * (etot + 8), s));
+  if (scr_max) *scr_max = std::max(*scr_max, sm);
+  return GBSMPS_OK;
+}
+
+void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTask>& out) {
+  const int N = M->N, cap = M->ba.cap;
+  for (int m = 0; m < N; ++m) {
+    SiteTask t;
+    t.nl = M->ne[m]; t.nr = M->ne[m + 1]; t.Dl = M->D[m]; t.Dr = M->D[m + 1];
+    t.Q = M->Qm + (size_t)m * QS * QS; t.qs = QS;
+    t.c = cm[m];
+    t.occl = M->ba.occ + (size_t)m * cap * NEM; t.lowl = M->ba.low + (size_t)m * NEM * cap; t.capl = cap;
+    t.occr = M->ba.occ + (size_t)(m + 1) * cap * NEM; t.lowr = M->ba.low + (size_t)(m + 1) * NEM * cap;
+    t.capr = cap;
+    t.out = M->tensors.as<double2>() + M->toff[m];
+    t.scratch_off = 0;
+    out.push_back(t);
+  }
+}
+
+int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) {
+  // waves of at most 2 x 152 tensors share one scratch arena (stream order
+  // separates the waves); the PCO build is FP64 in both precisions: it is a
+  // few percent of a step and its tensors feed FP64 amplitudes and the norm
+  cudaStream_t s = c->stream;
+  const int n = (int)tasks.size();
+  if (n == 0) return GBSMPS_OK;
+  const int wave = std::min(n, 304);
+  for (int k = 0; k < n; ++k) tasks[k].scratch_off = (size_t)(k % wave) * scr_max;
+  DevBuf scr, tk;
+  CK(scr.alloc(sizeof(double2) * scr_max * wave, s));
+  CK(tk.alloc(sizeof(SiteTask) * n, s));
+  CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
+  for (int k0 = 0; k0 < n; k0 += wave) {
+    const int cnt = std::min(wave, n - k0);
+    CK(launch_pco(tk.as<SiteTask>() + k0, cnt, d, GBSMPS_PREC_FP64, scr.as<double2>(), c->d_status, s));
+    COUNT_LAUNCH(1);
+  }
+  scr.release();
+  tk.release();
+  return GBSMPS_OK;
+}
+
+int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
+  cudaStream_t s = c->stream;
+  const int N = M->N, d = M->d, cap = M->ba.cap;
+  double2* R = M->env.as<double2>();
+  const double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
+  CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+  size_t xmax = 0;
+  for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
+  DevBuf xb;
+  CK(xb.alloc(sizeof(double2) * (xmax + 8), s));
+  double2* X = xb.as<double2>();
+  if (M->precision == GBSMPS_PREC_MIXED) {
+    // energy gauge (FP64) and environments in double-float arithmetic on the
+    // FP32 pipes (~44-bit): the chain of N dependent products sets the norm,
+    // so its per-step error must stay far below the tensor cores' FP32
+    // accumulation error
+    CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
+    double2* Ah = M->tens_mixed.as<double2>();
+    for (int m = 0; m < N; ++m) {
+      CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
+                             M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
+                             Ah + M->toff[m], s));
+      COUNT_LAUNCH(1);
+    }
+    tm.mark("energy_gauge");
+    const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
+    DevBuf kw;
+    CK(kw.alloc(wbytes, s));
+    for (int m = N - 1; m >= 0; --m) {
+      int Dl = M->D[m], Dr = M->D[m + 1];
+      const double2* A = Ah + M->toff[m];
+      CK(launch_zgemm_df64('N', 'N', Dl * d, Dr, Dr, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, X, Dr, 0,
+                           1, s, kw.p, wbytes));
+      CK(launch_zgemm_df64('N', 'C', Dl, Dl, d * Dr, X, d * Dr, 0, A, d * Dr, 0, R + M->eoff[m], Dl,
+                           0, 1, s, kw.p, wbytes));
+    }
+    kw.release();
+  } else {
+    for (int m = N - 1; m >= 0; --m) {
+      int Dl = M->D[m], Dr = M->D[m + 1];
+      const double2* A = M->tensors.as<double2>() + M->toff[m];
+      CK(launch_zgemm('N', 'N', Dl * d, Dr, Dr, one, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, zero, X,
+                      Dr, 0, 1, s));
+      CK(launch_zgemm('N', 'C', Dl, Dl, d * Dr, one, X, d * Dr, 0, A, d * Dr, 0, zero,
+                      R + M->eoff[m], Dl, 0, 1, s));
+      COUNT_LAUNCH(2);
+    }
+  }
+  xb.release();
+  return GBSMPS_OK;
+}
+
+int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
+  // vacuum amplitude, then A^1 *= conj(phase)/sqrt(norm^2)
+  cudaStream_t s = c->stream;
+  const int N = M->N, d = M->d, cap = M->ba.cap;
+  double2* R = M->env.as<double2>();
+  DevBuf ab;
+  CK(ab.alloc(sizeof(double2) * (2 * (size_t)M->maxD + 8) + N, s));
+  double2* awork = ab.as<double2>();
+  double2* amp0 = awork + 2 * M->maxD;
+  double2* fac = amp0 + 1;
+  uint8_t* zpat = reinterpret_cast<uint8_t*>(fac + 2);
+  CK(cudaMemsetAsync(zpat, 0, N, s));
+  ChainView cv{N, d, M->D.data(), M->toff.data(), M->tensors.as<double2>()};
+  CK(launch_amplitudes(cv, 1, zpat, amp0, awork, M->maxD, s));
+  COUNT_LAUNCH(2 + N);
+  CK(launch_norm_phase(R + M->eoff[0], amp0, fac, c->d_status, s));
+  CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
+  COUNT_LAUNCH(2);
+  if (M->precision == GBSMPS_PREC_MIXED) {   // the normalised first tensor in the energy gauge
+    CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], M->ba.E, M->ba.E + cap,
+                           M->tens_mixed.as<double2>(), s));
+    COUNT_LAUNCH(1);
+  }
+  ab.release();
+  return GBSMPS_OK;
+}
+
+int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
+  // R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
+  // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as fp16 planes per site
+  cudaStream_t s = c->stream;
+  const int N = M->N, d = M->d;
+  const double2 one = cmk(1.0, 0.0);
+  double2* R = M->env.as<double2>();
+  CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
+  CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
+                     cudaMemcpyHostToDevice, s));
+  CK(M->lchol.alloc(sizeof(double2) * (M->etot + 8), s));
+  CK(M->linv.alloc(sizeof(double2) * (M->etot + 8), s));
+  DevBuf du;                     // regulariser each bond needed (relative)
+  CK(du.alloc(sizeof(double) * (N + 1), s));
+  CK(cudaMemsetAsync(du.p, 0, sizeof(double) * (N + 1), s));
+  CK(launch_chol(R, M->lchol.as<double2>(), M->eoff_dev.as<long long>(), M->ba.D, 1, N - 1,
+                 du.as<double>(), c->d_status, s));
+  if (tm.on) {
+    std::vector<double> h(N + 1);
+    cudaMemcpyAsync(h.data(), du.p, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    double mx = 0.0;
+    for (double v : h) mx = std::max(mx, v);
+    fprintf(stderr, "[gbsmps] largest Cholesky regulariser: %.1e of max diag\n", mx);
+  }
+  du.release();
+  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
+                  M->ba.D, 1, N - 1, s));
+  COUNT_LAUNCH(2);
+  for (int b : {0, N}) {
+    CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(M->linv.as<double2>() + M->eoff[b], &one, sizeof(double2),
+                       cudaMemcpyHostToDevice, s));
+  }
+  tm.mark("cholesky");
+  M->Drp.resize(N); M->Kp.resize(N); M->Np.resize(N); M->bpoff.resize(N); M->bmaps.resize(N);
+  long long btot = 0;
+  size_t xmax = 0;
+  for (int m = 0; m < N; ++m) {
+    M->Drp[m] = (M->D[m + 1] + 63) / 64 * 64;
+    M->Kp[m] = (2 * M->D[m] + 63) / 64 * 64;
+    M->Np[m] = 2 * d * M->Drp[m];
+    M->bpoff[m] = btot;
+    btot += 2LL * M->Np[m] * M->Kp[m];
+    xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
+  }
+  CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
+  DevBuf tb, ab2, kw2;
+  const size_t wbytes2 = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
+  CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
+  CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
+  CK(kw2.alloc(wbytes2, s));
+  const double2* Ah = M->tens_mixed.as<double2>();
+  for (int m = 0; m < N; ++m) {
+    const int Dl = M->D[m], Dr = M->D[m + 1];
+    float2* T = tb.as<float2>();
+    float2* At = ab2.as<float2>();
+    // the canonical tensors feed fp16x2 planes: FP32-level products suffice
+    CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
+                       M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
+                       kw2.p, wbytes2));
+    const float2* src = T;
+    if (m > 0) {
+      CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
+                         T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, kw2.p, wbytes2));
+      src = At;
+    }
+    __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
+    CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
+    COUNT_LAUNCH(1);
+    if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
+      return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+  }
+  tb.release(); ab2.release(); kw2.release();
+  tm.mark("canonical_pack");
+  return GBSMPS_OK;
+}
+
+int finish(gbsmps_ctx* c, gbsmps_mps* M) {
+  // R_0 of the normalised state is 1
+  const double2 one = cmk(1.0, 0.0);
+  CK(cudaMemcpyAsync(M->env.as<double2>() + M->eoff[0], &one, sizeof(double2),
+                     cudaMemcpyHostToDevice, c->stream));
+  return GBSMPS_OK;
+}
+
+// the whole pipeline for one state whose covariance is on the device
+int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
+                 gbsmps_mps_t* out) {
+  cudaStream_t s = c->stream;
+  StageTimer tm(s);
+  {
+    const char* dbg = getenv("GBSMPS_DEBUG");
+    if (dbg && dbg[0] == '1') tm.dbg_status = c->d_status;
+  }
+  auto* M = new gbsmps_mps();
+  std::unique_ptr<gbsmps_mps> guard(M);
+  Front f;
+  int rc = alloc_front(M, c, N, o, &f);
+  if (rc) return rc;
+  // a1 validation, a2-a3 GSVD chain
+  rc = launch_checks(c, M, dgamma, o, f);
+  if (rc) return rc;
+  tm.mark("validate");
+  CK(launch_gsvd_chain(dgamma, N, f.dbw, o->lambda2_freeze, f.Gs, M->ba, M->Qm, M->cm,
+                       c->d_status, s));
+  COUNT_LAUNCH(1);
+  tm.mark("gsvd_chain");
+  // a4-a5 kept bases and index maps
+  rc = launch_bases(c, M, o);
+  if (rc) return rc;
+  tm.mark("basis_maps");
+  Readback rb;
+  rc = enqueue_readback(M, &rb, s);
+  if (rc) return rc;
+  rc = sync_status(c);
+  if (rc) return rc;
+  finish_readback(M, rb);
+  // a6 PCO build
+  size_t scr_max = 0;
+  rc = alloc_tensors(M, s, &scr_max);
+  if (rc) return rc;
+  std::vector<SiteTask> tasks;
+  site_tasks(M, rb.cm, tasks);
+  rc = run_pco(c, tasks, scr_max, o->d);
+  if (rc) return rc;
+  tm.mark("pco");
+  // a7 environments and normalisation
+  rc = env_single(c, M, tm);
+  if (rc) return rc;
+  tm.mark("environments");
+  rc = normalise_single(c, M);
+  if (rc) return rc;
+  tm.mark("normalise");
+  if (o->precision == GBSMPS_PREC_MIXED) {
+    rc = canonical_stage(c, M, tm);
+    if (rc) return rc;
+  }
+  rc = finish(c, M);
+  if (rc) return rc;
+  rc = sync_status(c);
+  if (rc) return rc;
+  *out = guard.release();
+  return GBSMPS_OK;
+}
+
+}  // namespace gbs

@@ -136,14 +136,36 @@ def small(N: int, seed: int, d: int = 4, chi: int = 32, depth: int = 4,
 
 def batch(count: int, seed: int = 20251212):
     """Many independent states of uneven size: N~U{16..144}, r~U(0.1,0.5),
-    depth N/8, d=6, chi in {32,64,128,256}."""
+    depth N/8, d=6, chi in {32,64,128,256} (eps 1e-12, freeze 1e-9)."""
     g = rng(seed)
     out = []
     for i in range(count):
         N = int(g.integers(16, 145))
         chi = int(g.choice([32, 64, 128, 256]))
         out.append(_make(f"batch{i}", N, 0.1, 0.5, max(1, N // 8), 6, chi,
-                         seed * 1000 + i))
+                         seed * 1000 + i, eps=1e-12, freeze=1e-9))
+    return out
+
+
+def serving(count: int, rate_hz: float, seed: int = 20251214, n_range=(32, 512),
+            chis=(64, 128, 256, 512), ds=(4, 6), s_range=(1000, 100000)):
+    """A stream of build + sampling requests: Poisson arrivals at rate_hz;
+    N log-uniform in n_range, r~U(0.05,0.4), brick-wall depth N/16, d from
+    ds, chi from chis, sample count uniform in s_range.  Returns a list of
+    (arrival time in s, Workload, samples); the Workload's Gamma is built when
+    the item is generated."""
+    g = rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(g.exponential(1.0 / rate_hz))
+        N = int(round(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        d = int(g.choice(ds))
+        chi = int(g.choice(chis))
+        S = int(g.integers(s_range[0], s_range[1] + 1))
+        w = _make(f"req{i}", N, 0.05, 0.4, max(1, N // 16), d, chi, seed * 1000 + i,
+                  eps=1e-12, freeze=1e-9)
+        out.append((t, w, S))
     return out
 
 
