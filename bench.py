@@ -294,6 +294,7 @@ def run_batched(args, dev):
     """Many independent states built in one batched call (all GSVD chains in
     one launch, all PCO tensors together, the environment chains in one
     persistent launch) against the same states built one call at a time."""
+    import numpy as np
     import torch
 
     import paper_2512_10643_gb300 as g
@@ -476,10 +477,17 @@ def main():
                 clocks=r["clocks"])
     if "fp64_gpu" in r:
         line["fp64_gpu"] = r["fp64_gpu"]
+    # supplementary sections: a failure is recorded in the line, not fatal
     if ws == 1 and args.batch_states > 0:
-        line["batched"] = run_batched(args, local)
+        try:
+            line["batched"] = run_batched(args, local)
+        except Exception as e:          # noqa: BLE001
+            line["batched"] = {"error": f"{type(e).__name__}: {e}"}
     if ws == 1 and args.serving_requests > 0:
-        line["serving"] = run_serving(args, local)
+        try:
+            line["serving"] = run_serving(args, local)
+        except Exception as e:          # noqa: BLE001
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
     print(json.dumps(line))
 
 

@@ -4,13 +4,14 @@
 // (left to right) and the right environments (right to left); everything
 // else is parallel over sites.  A batch runs the chains of all states side by
 // side instead of one after another: every GSVD chain in one launch (one CTA
-// per state), the PCO tensors of all sites of all states in waves of one
-// launch each, the energy gauge of all sites in one launch, the environment
+// per state), the PCO tensors of all sites of all states in one persistent
+// launch (largest sites first), the energy gauge of all sites in one launch, the environment
 // chains of all mixed-precision states in one persistent cooperative launch
 // (step k takes site N_s - 1 - k of every state, grid-wide barriers between
 // the two products of a step), and the normalisations in one launch (one CTA
 // per state).  Bond sizes are read back once for the whole batch.  The
-// right-canonical packing of the sampler then runs per state.
+// right-canonical packing of the sampler then runs per state, the states
+// spread over side streams.
 #include "objects.h"
 #include <algorithm>
 #include <map>
@@ -171,7 +172,10 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
     rc = upload(ejb, ej, s);
     if (!rc) rc = upload(njb, nj, s);
     if (rc) return rc;
-    CK(launch_env_chain_batch(ejb.as<EnvJob>(), (int)nm, maxN, s));
+    int cfg = -1;                                   // autotuned tile shape
+    if (const char* e = getenv("GBSMPS_ENV_TILE")) cfg = atoi(e);
+    if (cfg >= env_chain_tile_configs()) return fail(GBSMPS_ERR_ARG, "GBSMPS_ENV_TILE out of range");
+    CK(launch_env_chain_batch(ejb.as<EnvJob>(), (int)nm, maxN, maxD, cfg, s, nullptr));
     tm.mark("environments");
     CK(launch_vac_norm_batch(njb.as<NormJob>(), (int)nm, maxD, c->d_status, s));
     tm.mark("normalise");
@@ -181,10 +185,47 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
     for (auto& b : gb) b.release();
     ejb.release();
     njb.release();
-    for (int i : mixed) {
-      rc = gbs::canonical_stage(c, Ms[i].get(), tm);
+    // right-canonical packing: the states' factorisations and transforms are
+    // independent, so they are spread over side streams (storage is allocated
+    // on the main stream first; the main stream waits for every side stream
+    // before the temporaries are freed)
+    constexpr int NSIDE = 8;
+    std::vector<std::unique_ptr<gbs::CanonWork>> cw(nm);
+    for (size_t k = 0; k < nm; ++k) {
+      cw[k].reset(new gbs::CanonWork());
+      rc = gbs::canon_prepare(Ms[mixed[k]].get(), cw[k].get(), s);
       if (rc) return rc;
     }
+    const int nside = (int)std::min<size_t>(NSIDE, nm);
+    std::vector<cudaEvent_t> evs(nside + 1, nullptr);
+    for (auto& e : evs)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
+    auto drop_events = [&] { for (auto e : evs) if (e) cudaEventDestroy(e); };
+    if (std::any_of(evs.begin(), evs.end(), [](cudaEvent_t e) { return e == nullptr; })) {
+      drop_events();
+      return fail(GBSMPS_ERR_CUDA, "event creation failed");
+    }
+    std::vector<cudaStream_t> side(nside);
+    cudaEventRecord(evs[nside], s);
+    for (int j = 0; j < nside; ++j) {
+      side[j] = c->side_stream(j);
+      if (!side[j]) { drop_events(); return fail(GBSMPS_ERR_CUDA, "could not create a side stream"); }
+      cudaStreamWaitEvent(side[j], evs[nside], 0);
+    }
+    for (size_t k = 0; k < nm && !rc; ++k) {
+      gbsmps_mps* M = Ms[mixed[k]].get();
+      cudaStream_t st = side[k % nside];
+      rc = gbs::canon_bonds(c, M, cw[k].get(), 1, M->N - 1, st);
+      for (int m = 0; m < M->N && !rc; ++m) rc = gbs::canon_site(M, cw[k].get(), m, st);
+    }
+    for (int j = 0; j < nside; ++j) {           // join (also on an error above)
+      cudaEventRecord(evs[j], side[j]);
+      cudaStreamWaitEvent(s, evs[j], 0);
+    }
+    drop_events();
+    cw.clear();
+    if (rc) return rc;
+    tm.mark("canonical_pack");
   }
   for (int i = 0; i < count && !rc; ++i) rc = gbs::finish(c, Ms[i].get());
   if (!rc) rc = sync_status(c);

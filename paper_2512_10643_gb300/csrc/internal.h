@@ -190,6 +190,12 @@ cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int ca
 cudaError_t launch_pco(const SiteTask* tasks_dev, int ntasks, int d, int precision,
                        double2* scratch, int* status, cudaStream_t s);
 size_t pco_scratch_elems(int Dl, int Dr);
+// persistent variant for many sites: `grid` CTAs (pco_dynamic_grid(): as many
+// as fit on the GPU at once), each with a scratch slot of slot_elems
+int pco_dynamic_grid();
+cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, double2* scratch,
+                               size_t slot_elems, int grid, int* counter, int* status,
+                               cudaStream_t s);
 
 // complex FP64 GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C, row-major,
 // op = 'N' or 'C' (conjugate transpose), batched with element strides.
@@ -257,7 +263,11 @@ struct EnvJob {
   double2* R;              // environments (R^N = 1 on entry)
   double2* X;              // scratch, >= d maxD^2 complex
 };
-cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s);
+// cfg: tile shape 0 = 64x64, 1 = 32x64, 2 = 32x32 (all give the same result);
+// cfg < 0 picks the fastest for the batch class, measured once per process
+cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, int maxD, int cfg,
+                                   cudaStream_t s, int* chosen);
+int env_chain_tile_configs();
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_fp16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);

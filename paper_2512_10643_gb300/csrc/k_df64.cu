@@ -14,6 +14,9 @@
 #include "internal.h"
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <array>
+#include <map>
+#include <mutex>
 
 namespace cg = cooperative_groups;
 
@@ -22,6 +25,8 @@ namespace {
 constexpr int DM = 64, DN = 64, DK = 8;
 
 struct Df { float h, l; };
+
+inline int pow2i(long long x) { int r = 0; while ((1LL << r) < x) ++r; return r; }
 
 __device__ __forceinline__ void df_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
   const float p = xh * yh;
@@ -60,23 +65,28 @@ struct DfTile {
   double2* C; long long ldc;
 };
 
+// TM x TN tile on 16 x 16 threads, (TM/16) x (TN/16) outputs each.  Every
+// output sums k in the same order whatever the tile shape, so the result does
+// not depend on it (the shape is a pure performance choice).
+template <int TM, int TN>
 __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbeg, int kend,
-                                        float (*As)[DM][4], float (*Bs)[DN][4]) {
+                                        float (*As)[TM][4], float (*Bs)[TN][4]) {
+  constexpr int RM = TM / 16, RN = TN / 16;
   const double2* A = p.A;
   const double2* B = p.B;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  float ah[4][4][2], al[4][4][2];   // [row][col][re/im] hi and lo accumulators
+  float ah[RM][RN][2], al[RM][RN][2];   // [row][col][re/im] hi and lo accumulators
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < RN; ++c) {
       ah[r][c][0] = ah[r][c][1] = 0.f;
       al[r][c][0] = al[r][c][1] = 0.f;
     }
   for (int k0 = kbeg; k0 < kend; k0 += DK) {
-    for (int e = tid; e < DK * DM; e += 256) {
+    for (int e = tid; e < DK * TM; e += 256) {
       int kk, ii;
-      if (p.opa == 0) { ii = e / DK; kk = e % DK; } else { kk = e / DM; ii = e % DM; }
+      if (p.opa == 0) { ii = e / DK; kk = e % DK; } else { kk = e / TM; ii = e % TM; }
       const int gi = i0 + ii, gk = k0 + kk;
       double2 v = make_double2(0.0, 0.0);
       if (gi < p.M && gk < kend) {
@@ -86,9 +96,9 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
       const Df re = df_split(v.x), im = df_split(v.y);
       As[kk][ii][0] = re.h; As[kk][ii][1] = re.l; As[kk][ii][2] = im.h; As[kk][ii][3] = im.l;
     }
-    for (int e = tid; e < DK * DN; e += 256) {
+    for (int e = tid; e < DK * TN; e += 256) {
       int kk, jj;
-      if (p.opb == 0) { kk = e / DN; jj = e % DN; } else { jj = e / DK; kk = e % DK; }
+      if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / DK; kk = e % DK; }
       const int gj = j0 + jj, gk = k0 + kk;
       double2 v = make_double2(0.0, 0.0);
       if (gj < p.N && gk < kend) {
@@ -101,21 +111,21 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < DK; ++kk) {
-      float a[4][4], b[4][4];
+      float a[RM][4], b[RN][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < RM; ++r) {
         const float4 v = *reinterpret_cast<const float4*>(&As[kk][ty + 16 * r][0]);
         a[r][0] = v.x; a[r][1] = v.y; a[r][2] = v.z; a[r][3] = v.w;
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < RN; ++c) {
         const float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx + 16 * c][0]);
         b[c][0] = v.x; b[c][1] = v.y; b[c][2] = v.z; b[c][3] = v.w;
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < RN; ++c) {
           // re += ar br - ai bi ; im += ar bi + ai br
           df_mac(ah[r][c][0], al[r][c][0], a[r][0], a[r][1], b[c][0], b[c][1]);
           df_mac(ah[r][c][0], al[r][c][0], -a[r][2], -a[r][3], b[c][2], b[c][3]);
@@ -126,11 +136,11 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RM; ++r) {
     const int gi = i0 + ty + 16 * r;
     if (gi >= p.M) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < RN; ++c) {
       const int gj = j0 + tx + 16 * c;
       if (gj >= p.N) continue;
       p.C[(long long)gi * p.ldc + gj] =
@@ -140,17 +150,18 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
   }
 }
 
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
   // re/im, hi/lo split operands
-  __shared__ float As[DK][DM][4];
-  __shared__ float Bs[DK][DN][4];
+  __shared__ float As[DK][TM][4];
+  __shared__ float Bs[DK][TN][4];
   const long long bz = blockIdx.z / p.ksplit;
   const int kz = blockIdx.z % p.ksplit;
   const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
   DfTile t{p.M, p.N, p.opa, p.opb, p.A + bz * p.sA, p.lda, p.B + bz * p.sB, p.ldb,
            p.ksplit > 1 ? p.part + (long long)blockIdx.z * p.M * p.N : p.C + bz * p.sC,
            p.ksplit > 1 ? (long long)p.N : p.ldc};
-  df_tile(t, blockIdx.y * DM, blockIdx.x * DN, kbeg, kend, As, Bs);
+  df_tile<TM, TN>(t, blockIdx.y * TM, blockIdx.x * TN, kbeg, kend, As, Bs);
 }
 
 // Right-environment chains of many states in one persistent cooperative
@@ -159,10 +170,11 @@ __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
 // (D_m x d D_{m+1}) Ahat^m^dag.  The output tiles of all states in a phase are
 // dealt round-robin to the CTAs, and a grid-wide barrier separates phases
 // (all CTAs are co-resident by construction of the cooperative launch).
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict__ jobs, int count,
                                                        int maxN) {
-  __shared__ float As[DK][DM][4];
-  __shared__ float Bs[DK][DN][4];
+  __shared__ float As[DK][TM][4];
+  __shared__ float Bs[DK][TN][4];
   cg::grid_group grid = cg::this_grid();
   for (int k = 0; k < maxN; ++k) {
     for (int phase = 0; phase < 2; ++phase) {
@@ -183,11 +195,11 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
                      J.R + J.eoff[m], Dl};
           K = J.d * Dr;
         }
-        const long long tn = (p.N + DN - 1) / DN;
-        const long long nt = ((p.M + DM - 1) / DM) * tn;
+        const long long tn = (p.N + TN - 1) / TN;
+        const long long nt = ((p.M + TM - 1) / TM) * tn;
         for (; t < base + nt; t += gridDim.x) {
           const long long l = t - base;
-          df_tile(p, (int)(l / tn) * DM, (int)(l % tn) * DN, 0, K, As, Bs);
+          df_tile<TM, TN>(p, (int)(l / tn) * TM, (int)(l % tn) * TN, 0, K, As, Bs);
         }
         base += nt;
       }
@@ -210,11 +222,37 @@ __global__ void df_reduce_kernel(const double2* __restrict__ part, int ksplit, i
 
 }  // namespace
 
+namespace {
+
+cudaError_t df64_launch(int cfg, const DfArgs& a, int batch, cudaStream_t s) {
+  const int M = a.M, N = a.N, z = batch * a.ksplit;
+  switch (cfg) {
+    case 0:
+      zgemm_df64_kernel<64, 64><<<dim3((N + 63) / 64, (M + 63) / 64, z), 256, 0, s>>>(a);
+      break;
+    case 1:
+      zgemm_df64_kernel<32, 64><<<dim3((N + 63) / 64, (M + 31) / 32, z), 256, 0, s>>>(a);
+      break;
+    default:
+      zgemm_df64_kernel<32, 32><<<dim3((N + 31) / 32, (M + 31) / 32, z), 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// tile shape per problem class (op pair and power-of-two buckets of M, N, K,
+// batch), measured on the first call of the class; every shape gives the same
+// result because the k split and each output's k order do not depend on it
+std::mutex g_df_mu;
+std::map<std::array<int, 6>, int> g_df_tune;
+
+}  // namespace
+
 cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
                               long long sA, const double2* B, long long ldb, long long sB,
                               double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
                               void* work, size_t work_bytes) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  // the k split follows from the 64 x 64 tiling whatever tile shape then runs
   const long long tiles = (long long)((M + DM - 1) / DM) * ((N + DN - 1) / DN) * batch;
   int ksplit = 1;
   if (work && K > 4 * DK) {
@@ -227,9 +265,42 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
   ksplit = (K + kchunk - 1) / kchunk;
   DfArgs a{M, N, K, opa == 'C' ? 1 : 0, opb == 'C' ? 1 : 0, A, lda, sA, B, ldb, sB, C, ldc, sC,
            ksplit, kchunk, reinterpret_cast<double2*>(work)};
-  dim3 grid((N + DN - 1) / DN, (M + DM - 1) / DM, batch * ksplit);
-  zgemm_df64_kernel<<<grid, 256, 0, s>>>(a);
-  COUNT_LAUNCH(1);
+  int cfg = -1;
+  if (const char* e = getenv("GBSMPS_DF64_TILE")) cfg = std::max(0, std::min(2, atoi(e)));
+  const std::array<int, 6> key{a.opa * 2 + a.opb, pow2i(M), pow2i(N), pow2i(K), pow2i(batch), ksplit};
+  if (cfg < 0) {
+    std::lock_guard<std::mutex> lk(g_df_mu);
+    auto it = g_df_tune.find(key);
+    if (it != g_df_tune.end()) cfg = it->second;
+  }
+  if (cfg < 0) {
+    // first call of this class: run every shape once (each overwrites C with
+    // the same values) and keep the fastest
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bi = 0;
+    for (int c = 0; c < 3; ++c) {
+      cudaEventRecord(e0, s);
+      cudaError_t e = df64_launch(c, a, batch, s);
+      cudaEventRecord(e1, s);
+      COUNT_LAUNCH(1);
+      if (e) { cudaEventDestroy(e0); cudaEventDestroy(e1); return e; }
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bi = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_df_mu);
+    g_df_tune[key] = bi;
+  } else {
+    cudaError_t e = df64_launch(cfg, a, batch, s);
+    COUNT_LAUNCH(1);
+    if (e) return e;
+  }
   if (ksplit > 1) {
     const long long n = (long long)batch * M * N;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
@@ -239,18 +310,83 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s) {
-  if (count <= 0 || maxN <= 0) return cudaSuccess;
+namespace {
+
+template <int TM, int TN>
+cudaError_t env_chain_launch(const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s) {
   int dev = 0, nsm = 0, per = 0, coop = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e) return e;
   if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev))) return e;
   if (!coop) return cudaErrorNotSupported;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, env_chain_kernel, 256, 0))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, env_chain_kernel<TM, TN>, 256, 0)))
+    return e;
   if (per < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&jobs_dev, (void*)&count, (void*)&maxN};
-  e = cudaLaunchCooperativeKernel((const void*)env_chain_kernel, dim3(nsm * per), dim3(256), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void*)env_chain_kernel<TM, TN>, dim3(nsm * per), dim3(256),
+                                  args, 0, s);
   COUNT_LAUNCH(1);
   return e;
+}
+
+cudaError_t env_chain_cfg(int cfg, const EnvJob* jobs_dev, int count, int maxN, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return env_chain_launch<64, 64>(jobs_dev, count, maxN, s);
+    case 1: return env_chain_launch<32, 64>(jobs_dev, count, maxN, s);
+    default: return env_chain_launch<32, 32>(jobs_dev, count, maxN, s);
+  }
+}
+
+// tile-shape choices per batch class (count, largest bond, longest chain,
+// each rounded up to a power of two), measured on the first batch of a class
+std::mutex g_tune_mu;
+std::map<std::array<int, 3>, int> g_tune;
+
+int pow2(int x) { int r = 1; while (r < x) r <<= 1; return r; }
+
+}  // namespace
+
+int env_chain_tile_configs() { return 3; }
+
+cudaError_t launch_env_chain_batch(const EnvJob* jobs_dev, int count, int maxN, int maxD, int cfg,
+                                   cudaStream_t s, int* chosen) {
+  if (count <= 0 || maxN <= 0) return cudaSuccess;
+  if (cfg < 0) {
+    const std::array<int, 3> key{pow2(count), pow2(maxD), pow2(maxN)};
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) cfg = it->second;
+    }
+    if (cfg < 0) {
+      // every shape computes the same result, so the candidates simply run on
+      // the batch itself; the last run leaves the environments in place
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      int bi = 0;
+      for (int c = 0; c < env_chain_tile_configs(); ++c) {
+        cudaEventRecord(e0, s);
+        cudaError_t e = env_chain_cfg(c, jobs_dev, count, maxN, s);
+        cudaEventRecord(e1, s);
+        if (e) { cudaEventDestroy(e0); cudaEventDestroy(e1); return e; }
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bi = c; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = bi;
+      }
+      if (chosen) *chosen = bi;
+      return cudaGetLastError();
+    }
+  }
+  if (chosen) *chosen = cfg;
+  return env_chain_cfg(cfg, jobs_dev, count, maxN, s);
 }

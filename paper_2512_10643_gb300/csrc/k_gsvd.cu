@@ -199,8 +199,10 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
     W32[i * LD + j] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
   }
   const double normF = sqrt(block_sum(loc, sm.red));
-  const double skip = 1e-300 + 1e-18 * normF;
-  jacobi_sweeps<float2, false>(sm, H32, W32, n, 4e-6 * normF, skip, 12);
+  // threshold Jacobi: a pair whose element is already far below the stage's
+  // stop criterion is left alone (no work), the check still covers it
+  const double conv32 = 4e-6 * normF, conv64 = 2.5e-16 * n * normF;
+  jacobi_sweeps<float2, false>(sm, H32, W32, n, conv32, 1e-300 + 0.025 * conv32, 12);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
     const float2 w = W32[i * LD + j];
@@ -252,7 +254,8 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   }
   __syncthreads();
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
-  const bool ok = jacobi_sweeps<double2, false>(sm, H, W, n, 2.5e-16 * n * normF, skip, MAX_SWEEPS);
+  const bool ok = jacobi_sweeps<double2, false>(sm, H, W, n, conv64, 1e-300 + 0.25 * conv64,
+                                                MAX_SWEEPS);
   for (int i = tid; i < n; i += nt) sm.ev[i] = H[i * LD + i].x;
   __syncthreads();
   return ok;

@@ -40,12 +40,9 @@ struct PcoSmem {
 __device__ inline int occ_of(const uint8_t* occ, int idx, int q) { return occ[(size_t)idx * NEM + q]; }
 
 template <typename T>
-__global__ void __launch_bounds__(PCO_THREADS)
-pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scratch_base,
-           int* status) {
+__device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restrict__ scratch,
+                         int* status) {
   using C2 = typename Cx<T>::type;
-  __shared__ PcoSmem sm;
-  const SiteTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nl = t.nl, nr = t.nr, Dl = t.Dl, Dr = t.Dr;
   const int nm = nl + 1 + nr;
@@ -62,7 +59,7 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
   for (int q = tid; q < nr; q += nt) if (sm.mor[q] >= SQ_N - 4) set_status(status, ST_BOUNDS);
 
   const size_t DD = (size_t)Dl * Dr;
-  C2* base = reinterpret_cast<C2*>(scratch_base + t.scratch_off);
+  C2* base = reinterpret_cast<C2*>(scratch);
   C2* u = base;
   C2* u2 = u + Dl;
   C2* w = u2 + Dl;
@@ -225,6 +222,37 @@ pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scra
   }
 }
 
+// one CTA per site, scratch at the task's own offset
+template <typename T>
+__global__ void __launch_bounds__(PCO_THREADS)
+pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scratch_base,
+           int* status) {
+  __shared__ PcoSmem sm;
+  const SiteTask t = tasks[blockIdx.x];
+  pco_site<T>(sm, t, d, scratch_base + t.scratch_off, status);
+}
+
+// many sites of uneven size: persistent CTAs take the next task from a
+// counter (the host orders tasks largest first), each with its own scratch slot
+template <typename T>
+__global__ void __launch_bounds__(PCO_THREADS)
+pco_dynamic_kernel(const SiteTask* __restrict__ tasks, int ntasks, int d,
+                   double2* __restrict__ scratch_base, size_t slot_elems, int* counter,
+                   int* status) {
+  __shared__ PcoSmem sm;
+  __shared__ int next;
+  double2* slot = scratch_base + (size_t)blockIdx.x * slot_elems;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = next;
+    if (k >= ntasks) break;
+    const SiteTask t = tasks[k];
+    pco_site<T>(sm, t, d, slot, status);
+    __syncthreads();                 // shared memory and the slot are reused
+  }
+}
+
 // lowering maps of an arbitrary down-closed basis (expert entry): brute search
 __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n, int* low,
                                   int cap, int* status) {
@@ -296,6 +324,25 @@ cudaError_t launch_pco(const SiteTask* tasks_dev, int ntasks, int d, int precisi
     pco_kernel<float><<<ntasks, PCO_THREADS, 0, s>>>(tasks_dev, d, scratch, status);
   else
     pco_kernel<double><<<ntasks, PCO_THREADS, 0, s>>>(tasks_dev, d, scratch, status);
+  return cudaGetLastError();
+}
+
+int pco_dynamic_grid() {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pco_dynamic_kernel<double>, PCO_THREADS, 0))
+    return 0;
+  return nsm * std::max(per, 1);
+}
+
+cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, double2* scratch,
+                               size_t slot_elems, int grid, int* counter, int* status,
+                               cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e) return e;
+  pco_dynamic_kernel<double><<<grid, PCO_THREADS, 0, s>>>(tasks_dev, ntasks, d, scratch, slot_elems,
+                                                          counter, status);
   return cudaGetLastError();
 }
 

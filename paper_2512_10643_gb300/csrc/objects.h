@@ -83,6 +83,19 @@ struct gbsmps_ctx {
   cudaStream_t stream = nullptr;
   int* d_status = nullptr;
   unsigned long long launches_at_create = 0;
+  // extra streams for work that overlaps the main chain, created on first use
+  std::vector<cudaStream_t> sides;
+  cudaStream_t side_stream(int k = 0) {
+    while ((int)sides.size() <= k) {
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      sides.push_back(st);
+    }
+    return sides[k];
+  }
+  ~gbsmps_ctx() {
+    for (auto st : sides) cudaStreamDestroy(st);
+  }
 };
 
 struct DevBuf {                // stream-ordered device allocation
@@ -172,7 +185,16 @@ void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTa
 int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d);
 int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int normalise_single(gbsmps_ctx* c, gbsmps_mps* M);
+struct CanonWork {               // temporaries of the right-canonical packing
+  DevBuf du, tb, ab, kw;
+  size_t wbytes = 0;
+  ~CanonWork() { du.release(); tb.release(); ab.release(); kw.release(); }
+};
+int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s);
+int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s);
+int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s);
 int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
+int canon_sites_parallel(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w0, int nside, StageTimer& tm);
 int finish(gbsmps_ctx* c, gbsmps_mps* M);
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                  gbsmps_mps_t* out);

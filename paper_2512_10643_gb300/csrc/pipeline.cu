@@ -139,12 +139,33 @@ void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTa
 }
 
 int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) {
-  // waves of at most 2 x 152 tensors share one scratch arena (stream order
-  // separates the waves); the PCO build is FP64 in both precisions: it is a
-  // few percent of a step and its tensors feed FP64 amplitudes and the norm
+  // the PCO build is FP64 in both precisions: it is a few percent of a step
+  // and its tensors feed FP64 amplitudes and the norm.  Up to one resident
+  // wave of sites: one CTA per site; more: persistent CTAs (below)
   cudaStream_t s = c->stream;
   const int n = (int)tasks.size();
   if (n == 0) return GBSMPS_OK;
+  const int grid = pco_dynamic_grid();
+  if (grid > 0 && n > grid) {
+    // more sites than resident CTAs (a batch, or a long chain): persistent
+    // CTAs pull the sites largest first, each with its own scratch slot
+    std::sort(tasks.begin(), tasks.end(), [](const SiteTask& a, const SiteTask& b) {
+      const double ca = (double)a.Dl * a.Dr * (a.nl + a.nr + 1), cb = (double)b.Dl * b.Dr * (b.nl + b.nr + 1);
+      return ca > cb;
+    });
+    DevBuf scr, tk, ctr;
+    CK(scr.alloc(sizeof(double2) * scr_max * grid, s));
+    CK(tk.alloc(sizeof(SiteTask) * n, s));
+    CK(ctr.alloc(sizeof(int), s));
+    CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
+    CK(launch_pco_dynamic(tk.as<SiteTask>(), n, d, scr.as<double2>(), scr_max, grid, ctr.as<int>(),
+                          c->d_status, s));
+    COUNT_LAUNCH(1);
+    scr.release();
+    tk.release();
+    ctr.release();
+    return GBSMPS_OK;
+  }
   const int wave = std::min(n, 304);
   for (int k = 0; k < n; ++k) tasks[k].scratch_off = (size_t)(k % wave) * scr_max;
   DevBuf scr, tk;
@@ -240,42 +261,27 @@ int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
   return GBSMPS_OK;
 }
 
-int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
-  // R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
-  // At^m = L_m^{-1} Ahat^m L_{m+1}; packed as fp16 planes per site
-  cudaStream_t s = c->stream;
+// ---- right-canonical form for the tensor-core sampler ----------------------
+// R_m = L_m L_m^dag (bonds 1..N-1), L_0 = L_N = 1 for the normalised state;
+// At^m = L_m^{-1} Ahat^m L_{m+1}; packed as fp16 planes per site.  Bond b
+// needs only R_b, site m only L_m, L_m^{-1}, L_{m+1} and Ahat^m, so the
+// stages below can run per bond / per site as soon as their inputs exist.
+int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
   const int N = M->N, d = M->d;
-  const double2 one = cmk(1.0, 0.0);
-  double2* R = M->env.as<double2>();
   CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
   CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
                      cudaMemcpyHostToDevice, s));
   CK(M->lchol.alloc(sizeof(double2) * (M->etot + 8), s));
   CK(M->linv.alloc(sizeof(double2) * (M->etot + 8), s));
-  DevBuf du;                     // regulariser each bond needed (relative)
-  CK(du.alloc(sizeof(double) * (N + 1), s));
-  CK(cudaMemsetAsync(du.p, 0, sizeof(double) * (N + 1), s));
-  CK(launch_chol(R, M->lchol.as<double2>(), M->eoff_dev.as<long long>(), M->ba.D, 1, N - 1,
-                 du.as<double>(), c->d_status, s));
-  if (tm.on) {
-    std::vector<double> h(N + 1);
-    cudaMemcpyAsync(h.data(), du.p, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    double mx = 0.0;
-    for (double v : h) mx = std::max(mx, v);
-    fprintf(stderr, "[gbsmps] largest Cholesky regulariser: %.1e of max diag\n", mx);
-  }
-  du.release();
-  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
-                  M->ba.D, 1, N - 1, s));
-  COUNT_LAUNCH(2);
+  CK(w->du.alloc(sizeof(double) * (N + 1), s));
+  CK(cudaMemsetAsync(w->du.p, 0, sizeof(double) * (N + 1), s));
+  const double2 one = cmk(1.0, 0.0);
   for (int b : {0, N}) {
     CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(M->linv.as<double2>() + M->eoff[b], &one, sizeof(double2),
                        cudaMemcpyHostToDevice, s));
   }
-  tm.mark("cholesky");
   M->Drp.resize(N); M->Kp.resize(N); M->Np.resize(N); M->bpoff.resize(N); M->bmaps.resize(N);
   long long btot = 0;
   size_t xmax = 0;
@@ -288,33 +294,115 @@ int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
   }
   CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
-  DevBuf tb, ab2, kw2;
-  const size_t wbytes2 = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
-  CK(tb.alloc(sizeof(float2) * (xmax + 8), s));
-  CK(ab2.alloc(sizeof(float2) * (xmax + 8), s));
-  CK(kw2.alloc(wbytes2, s));
+  w->wbytes = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
+  CK(w->tb.alloc(sizeof(float2) * (xmax + 8), s));
+  CK(w->ab.alloc(sizeof(float2) * (xmax + 8), s));
+  CK(w->kw.alloc(w->wbytes, s));
+  return GBSMPS_OK;
+}
+
+int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s) {
+  if (nb <= 0) return GBSMPS_OK;
+  CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), M->eoff_dev.as<long long>(),
+                 M->ba.D, b0, nb, w->du.as<double>(), c->d_status, s));
+  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
+                  M->ba.D, b0, nb, s));
+  COUNT_LAUNCH(2);
+  return GBSMPS_OK;
+}
+
+int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
+  const int d = M->d, Dl = M->D[m], Dr = M->D[m + 1];
   const double2* Ah = M->tens_mixed.as<double2>();
-  for (int m = 0; m < N; ++m) {
-    const int Dl = M->D[m], Dr = M->D[m + 1];
-    float2* T = tb.as<float2>();
-    float2* At = ab2.as<float2>();
-    // the canonical tensors feed fp16x2 planes: FP32-level products suffice
-    CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
-                       M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
-                       kw2.p, wbytes2));
-    const float2* src = T;
-    if (m > 0) {
-      CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
-                         T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, kw2.p, wbytes2));
-      src = At;
-    }
-    __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
-    CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
-    COUNT_LAUNCH(1);
-    if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
-      return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+  float2* T = w->tb.as<float2>();
+  float2* At = w->ab.as<float2>();
+  // the canonical tensors feed fp16x2 planes: FP32-level products suffice
+  CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
+                     M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
+                     w->kw.p, w->wbytes));
+  const float2* src = T;
+  if (m > 0) {
+    CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
+                       T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, w->kw.p, w->wbytes));
+    src = At;
   }
-  tb.release(); ab2.release(); kw2.release();
+  __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
+  CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
+  COUNT_LAUNCH(1);
+  if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
+    return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+  return GBSMPS_OK;
+}
+
+void canon_report(gbsmps_mps* M, CanonWork* w, StageTimer& tm, cudaStream_t s) {
+  if (!tm.on) return;
+  std::vector<double> h(M->N + 1);
+  cudaMemcpyAsync(h.data(), w->du.p, sizeof(double) * (M->N + 1), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  double mx = 0.0;
+  for (double v : h) mx = std::max(mx, v);
+  fprintf(stderr, "[gbsmps] largest Cholesky regulariser: %.1e of max diag\n", mx);
+}
+
+int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
+  cudaStream_t s = c->stream;
+  CanonWork w;
+  int rc = canon_prepare(M, &w, s);
+  if (!rc) rc = canon_bonds(c, M, &w, 1, M->N - 1, s);
+  if (rc) return rc;
+  canon_report(M, &w, tm, s);
+  tm.mark("cholesky");
+  for (int m = 0; m < M->N && !rc; ++m) rc = canon_site(M, &w, m, s);
+  if (rc) return rc;
+  tm.mark("canonical_pack");
+  return GBSMPS_OK;
+}
+
+// Spread the per-site transforms and packing of one state over side streams
+// (each with its own temporaries): the sites are independent once every
+// bond's factor exists, and each site's work is a few small launches.
+int canon_sites_parallel(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w0, int nside, StageTimer& tm) {
+  cudaStream_t s = c->stream;
+  const int N = M->N;
+  nside = std::max(1, std::min(nside, N));
+  std::vector<std::unique_ptr<CanonWork>> ws(nside);
+  std::vector<cudaStream_t> side(nside);
+  std::vector<cudaEvent_t> ev(nside + 1, nullptr);
+  auto drop = [&] { for (auto e : ev) if (e) cudaEventDestroy(e); };
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      drop();
+      return fail(GBSMPS_ERR_CUDA, "event creation failed");
+    }
+  // temporaries of the extra workers come from the main stream
+  for (int j = 1; j < nside; ++j) {
+    ws[j].reset(new CanonWork());
+    ws[j]->wbytes = w0->wbytes;
+    size_t xmax = 0;
+    for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * M->d * M->D[m + 1]);
+    cudaError_t e = ws[j]->tb.alloc(sizeof(float2) * (xmax + 8), s);
+    if (!e) e = ws[j]->ab.alloc(sizeof(float2) * (xmax + 8), s);
+    if (!e) e = ws[j]->kw.alloc(ws[j]->wbytes, s);
+    if (e) { drop(); return fail(GBSMPS_ERR_OOM, "canonical transform temporaries"); }
+  }
+  cudaEventRecord(ev[nside], s);
+  for (int j = 0; j < nside; ++j) {
+    side[j] = c->side_stream(j);
+    if (!side[j]) { drop(); return fail(GBSMPS_ERR_CUDA, "could not create a side stream"); }
+    cudaStreamWaitEvent(side[j], ev[nside], 0);
+  }
+  int rc = GBSMPS_OK;
+  for (int m = 0; m < N && !rc; ++m) {
+    const int j = m % nside;
+    rc = canon_site(M, j == 0 ? w0 : ws[j].get(), m, side[j]);
+  }
+  for (int j = 0; j < nside; ++j) {              // join, also after an error
+    cudaEventRecord(ev[j], side[j]);
+    cudaStreamWaitEvent(s, ev[j], 0);
+  }
+  drop();
+  ws.clear();                                     // frees on the main stream, after the join
+  if (rc) return rc;
   tm.mark("canonical_pack");
   return GBSMPS_OK;
 }
@@ -376,7 +464,15 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
   if (rc) return rc;
   tm.mark("normalise");
   if (o->precision == GBSMPS_PREC_MIXED) {
-    rc = canonical_stage(c, M, tm);
+    // the sampler's right-canonical form: every bond's factor in one launch
+    // (one SM per bond), then the sites' transforms spread over side streams
+    CanonWork w;
+    rc = canon_prepare(M, &w, s);
+    if (!rc) rc = canon_bonds(c, M, &w, 1, N - 1, s);
+    if (rc) return rc;
+    canon_report(M, &w, tm, s);
+    tm.mark("cholesky");
+    rc = canon_sites_parallel(c, M, &w, 4, tm);
     if (rc) return rc;
   }
   rc = finish(c, M);

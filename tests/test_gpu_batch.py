@@ -118,3 +118,48 @@ def test_batch_edge_cases(ctx):
     # the context stays usable
     m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=4, chi_max=16)
     m.release()
+
+
+def test_env_tile_shapes_give_identical_results(ctx, monkeypatch):
+    """The persistent environment chain sums every output in the same k order
+    whatever its tile shape, so the autotuner's choice cannot change a bit."""
+    states = _batch_states()[:5]
+    gams = [np.ascontiguousarray(w.gamma) for w, _ in states]
+    opts = [o for _, o in states]
+    results = []
+    for cfg in ("0", "1", "2"):
+        monkeypatch.setenv("GBSMPS_ENV_TILE", cfg)
+        batch = g.MPS.batch(ctx, gams, opts)
+        try:
+            res = []
+            for k, ((w, o), m) in enumerate(zip(states, batch)):
+                u = wl.uniforms(300, w.N, seed=7 + k)
+                res.append((m.tensor(0), m.sample(300, uniforms=u)))
+            results.append(res)
+        finally:
+            for m in batch:
+                m.release()
+    for other in results[1:]:
+        for (t0, s0), (t1, s1) in zip(results[0], other):
+            assert np.array_equal(t0, t1)
+            assert np.array_equal(s0, s1)
+
+
+def test_df64_tile_shapes_give_identical_results(ctx, monkeypatch):
+    """The single-state environment GEMM's tile shape (autotuned per problem
+    class) cannot change a bit either: the k split and every output's k order
+    are fixed by the problem, not by the tile."""
+    w = wl.small(24, 31, d=5, chi=64, depth=4, rlo=0.1, rhi=0.5)
+    opts = dict(d=5, chi_max=64, eps_trunc=1e-12, lambda2_freeze=1e-8, precision=g.PREC_MIXED)
+    u = wl.uniforms(300, 24, seed=3)
+    res = []
+    for cfg in ("0", "1", "2"):
+        monkeypatch.setenv("GBSMPS_DF64_TILE", cfg)
+        m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **opts)
+        try:
+            res.append((m.tensor(0), m.sample(300, uniforms=u)))
+        finally:
+            m.release()
+    for t, smp in res[1:]:
+        assert np.array_equal(t, res[0][0])
+        assert np.array_equal(smp, res[0][1])
