@@ -70,7 +70,7 @@ struct DfTile {
 // not depend on it (the shape is a pure performance choice).
 template <int TM, int TN>
 __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbeg, int kend,
-                                        float (*As)[TM][4], float (*Bs)[TN][4]) {
+                                        float (*As)[TM + 1][4], float (*Bs)[TN + 1][4]) {
   constexpr int RM = TM / 16, RN = TN / 16;
   const double2* A = p.A;
   const double2* B = p.B;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
         else { v = A[(long long)gk * p.lda + gi]; v.y = -v.y; }
       }
       const Df re = df_split(v.x), im = df_split(v.y);
-      As[kk][ii][0] = re.h; As[kk][ii][1] = re.l; As[kk][ii][2] = im.h; As[kk][ii][3] = im.l;
+      *reinterpret_cast<float4*>(&As[kk][ii][0]) = make_float4(re.h, re.l, im.h, im.l);
     }
     for (int e = tid; e < DK * TN; e += 256) {
       int kk, jj;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
         else { v = B[(long long)gj * p.ldb + gk]; v.y = -v.y; }
       }
       const Df re = df_split(v.x), im = df_split(v.y);
-      Bs[kk][jj][0] = re.h; Bs[kk][jj][1] = re.l; Bs[kk][jj][2] = im.h; Bs[kk][jj][3] = im.l;
+      *reinterpret_cast<float4*>(&Bs[kk][jj][0]) = make_float4(re.h, re.l, im.h, im.l);
     }
     __syncthreads();
 #pragma unroll 2
@@ -153,8 +153,10 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
 template <int TM, int TN>
 __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
   // re/im, hi/lo split operands
-  __shared__ float As[DK][TM][4];
-  __shared__ float Bs[DK][TN][4];
+  // rows padded by one 16-byte element: the k-major fills of A (and of B^dag)
+  // then fall into different banks
+  __shared__ __align__(16) float As[DK][TM + 1][4];
+  __shared__ __align__(16) float Bs[DK][TN + 1][4];
   const long long bz = blockIdx.z / p.ksplit;
   const int kz = blockIdx.z % p.ksplit;
   const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
@@ -173,8 +175,10 @@ __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
 template <int TM, int TN>
 __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict__ jobs, int count,
                                                        int maxN) {
-  __shared__ float As[DK][TM][4];
-  __shared__ float Bs[DK][TN][4];
+  // rows padded by one 16-byte element: the k-major fills of A (and of B^dag)
+  // then fall into different banks
+  __shared__ __align__(16) float As[DK][TM + 1][4];
+  __shared__ __align__(16) float Bs[DK][TN + 1][4];
   cg::grid_group grid = cg::this_grid();
   for (int k = 0; k < maxN; ++k) {
     for (int phase = 0; phase < 2; ++phase) {

@@ -37,9 +37,13 @@ struct ChainSmem {
   double ev[N2M];
   int perm[N2M];
   double Dq[NLM];
+  double rsD[NLM];          // sqrt(2 / D_q)
+  double2 pinv;             // Gauss-Jordan: inverse of the current pivot
   int rp[NLM], rq[NLM];
   double rcs[NLM], rsn[NLM];
   double2 rph[NLM];
+  float fcs[NLM], fsn[NLM];  // FP32 stage: the same, kept in FP32 (no conversions)
+  float2 fph[NLM];
   double2 fac[NLM];
   double red[CHAIN_THREADS];
   int ival[4];
@@ -92,26 +96,35 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, d
   const int nt = WARP ? 32 : blockDim.x;
   const int half = n / 2;
   auto team_sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+  // rotation parameters live in FP64 for the FP64 stage and in FP32 for the
+  // FP32 stage, so neither stage converts between the two in its loops
+  auto rot = [&](int k, R& cs, R& sn, R& px, R& py) {
+    if constexpr (wide) { cs = sm.rcs[k]; sn = sm.rsn[k]; px = sm.rph[k].x; py = sm.rph[k].y; }
+    else { cs = sm.fcs[k]; sn = sm.fsn[k]; px = sm.fph[k].x; py = sm.fph[k].y; }
+  };
   for (int sweep = 0;; ++sweep) {
-    double loc = 0.0;
+    R loc = 0;
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx / n, j = idx % n;
       if (i < j) {
         T2 v = H[i * LD + j];
-        loc = fmax(loc, (double)(fabs(v.x) + fabs(v.y)));
+        loc = fmax(loc, fabs(v.x) + fabs(v.y));
       }
     }
     double gmax;
     if (WARP) {
-      for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
-      gmax = loc;
+      double l = loc;
+      for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
+      gmax = l;
     } else {
-      gmax = block_max(loc, sm.red);
+      gmax = block_max((double)loc, sm.red);
     }
     if (gmax <= conv) return true;
     if (sweep == max_sweeps) return false;
     for (int r = 0; r < n - 1; ++r) {
-      const int k = tid;
+      // pair k is set up by lane k / 4 of warp k % 4 (block form): the
+      // set-up's FP64 steps then run on all four SM sub-partitions
+      const int k = WARP ? tid : (tid < 128 ? (((tid & 31) << 2) | (tid >> 5)) : half);
       if (k < half) {
         const int a = (r + k) % (n - 1);
         const int b = (k == 0) ? (n - 1) : (r - k + n - 1) % (n - 1);
@@ -119,16 +132,20 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, d
         const T2 c = H[p * LD + q];
         const float fx = (float)c.x, fy = (float)c.y;
         const float mf = hypotf(fx, fy);
-        double cs = 1.0, sn = 0.0, phx = 1.0, phy = 0.0;
+        float fc = 1.0f, fs = 0.0f, gx = 1.0f, gy = 0.0f;
         if (mf > (float)skip) {
-          const float gx = fx / mf, gy = -fy / mf;              // e^{-i phi}
-          float tau = (float)((double)H[q * LD + q].x - (double)H[p * LD + p].x) / (2.0f * mf);
+          gx = fx / mf; gy = -fy / mf;                          // e^{-i phi}
+          float tau = (float)(H[q * LD + q].x - H[p * LD + p].x) / (2.0f * mf);
           float t;
           if (fabsf(tau) > 1e18f) t = 0.5f / tau;
           else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-          const float fc = rsqrtf(fmaf(t, t, 1.0f));
-          cs = fc; sn = t * fc; phx = gx; phy = gy;
-          if (wide) {
+          fc = rsqrtf(fmaf(t, t, 1.0f));
+          fs = t * fc;
+        }
+        sm.rp[k] = p; sm.rq[k] = q;
+        if constexpr (wide) {
+          double cs = fc, sn = fs, phx = gx, phy = gy;
+          if (fs != 0.0f) {
             for (int it = 0; it < 2; ++it) {
               double g = 1.5 - 0.5 * (cs * cs + sn * sn);
               cs *= g; sn *= g;
@@ -136,17 +153,19 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, d
               phx *= h; phy *= h;
             }
           }
+          sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = cmk(phx, phy);
+        } else {
+          sm.fcs[k] = fc; sm.fsn[k] = fs; sm.fph[k] = make_float2(gx, gy);
         }
-        sm.rp[k] = p; sm.rq[k] = q; sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = cmk(phx, phy);
       }
       team_sync();
       // columns: X = H J, W = W J with J = [[cs, sn], [-sn ph, cs ph]]
       for (int idx = tid; idx < half * n; idx += nt) {
         const int k = idx / n, i = idx % n;
-        if (sm.rsn[k] == 0.0) continue;
+        R cs, sn, px, py;
+        rot(k, cs, sn, px, py);
+        if (sn == (R)0) continue;
         const int p = sm.rp[k], q = sm.rq[k];
-        const R cs = (R)sm.rcs[k], sn = (R)sm.rsn[k];
-        const R px = (R)sm.rph[k].x, py = (R)sm.rph[k].y;
         T2 hp = H[i * LD + p], hq = H[i * LD + q];
         R qx = px * hq.x - py * hq.y, qy = px * hq.y + py * hq.x;
         H[i * LD + p] = T2{cs * hp.x - sn * qx, cs * hp.y - sn * qy};
@@ -160,10 +179,11 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, d
       // rows: H = J^dag X
       for (int idx = tid; idx < half * n; idx += nt) {
         const int k = idx / n, j = idx % n;
-        if (sm.rsn[k] == 0.0) continue;
+        R cs, sn, px, py;
+        rot(k, cs, sn, px, py);
+        if (sn == (R)0) continue;
+        py = -py;
         const int p = sm.rp[k], q = sm.rq[k];
-        const R cs = (R)sm.rcs[k], sn = (R)sm.rsn[k];
-        const R px = (R)sm.rph[k].x, py = -(R)sm.rph[k].y;
         T2 xp = H[p * LD + j], xq = H[q * LD + j];
         R qx = px * xq.x - py * xq.y, qy = px * xq.y + py * xq.x;
         H[p * LD + j] = T2{cs * xp.x - sn * qx, cs * xp.y - sn * qy};
@@ -282,6 +302,9 @@ __device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
       }
       if (best == 0.0) sm.ival[0] = 1;
       sm.ival[1] = pr;
+      const double2 pv = M[pr * NLM + k];       // the pivot after the row swap
+      const double pm = cabs2(pv);
+      sm.pinv = pm > 0.0 ? cmk(pv.x / pm, -pv.y / pm) : cmk(0.0, 0.0);
       sm.dval[1] *= (best > 0.0 ? best : 1e-300);    // |pivots|^2 of a near-unitary-scale U
       if (k == n - 1) sm.dval[0] = 0.5 * log(sm.dval[1]);
     }
@@ -294,10 +317,7 @@ __device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
       }
     }
     __syncthreads();
-    double2 piv = M[k * NLM + k];
-    double pm = cabs2(piv);
-    double2 pinv = pm > 0.0 ? cmk(piv.x / pm, -piv.y / pm) : cmk(0.0, 0.0);
-    __syncthreads();
+    const double2 pinv = sm.pinv;
     for (int j = tid; j < n; j += nt) {
       M[k * NLM + j] = cmul(M[k * NLM + j], pinv);
       Inv[k * NLM + j] = cmul(Inv[k * NLM + j], pinv);
@@ -387,12 +407,17 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     for (int idx = tid; idx < n2 * n2; idx += nt) sm.A[(idx / n2) * LD + idx % n2] *= 2.0;
     __syncthreads();
     for (int k = 0; k < n2; ++k) {
-      double akk = sm.A[k * LD + k];
-      if (!(akk > 0.0)) { if (tid == 0) set_status(status, ST_NUMERIC); akk = 1e-300; }
-      double lkk = sqrt(akk);
+      if (tid == 0) {                  // one thread takes the FP64 square root
+        double akk = sm.A[k * LD + k];
+        if (!(akk > 0.0)) { set_status(status, ST_NUMERIC); akk = 1e-300; }
+        const double lkk = sqrt(akk);
+        sm.dval[2] = lkk;
+        sm.dval[3] = 1.0 / lkk;
+      }
       __syncthreads();
-      for (int i = k + 1 + tid; i < n2; i += nt) sm.A[i * LD + k] /= lkk;
-      if (tid == 0) sm.A[k * LD + k] = lkk;
+      const double ilkk = sm.dval[3];
+      for (int i = k + 1 + tid; i < n2; i += nt) sm.A[i * LD + k] *= ilkk;
+      if (tid == 0) sm.A[k * LD + k] = sm.dval[2];
       __syncthreads();
       const int w = n2 - k - 1;
       for (int idx = tid; idx < w * w; idx += nt) {
@@ -444,11 +469,11 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
         double e = sm.ev[sm.perm[nL + q]];
         if (!(e > 0.0)) { set_status(status, ST_NUMERIC); e = 1.0; }
         sm.Dq[q] = 1.0 / e;
+        sm.rsD[q] = 1.4142135623730951 * sqrt(e);     // sqrt(2) / sqrt(D_q)
       }
     }
     __syncthreads();
     // ---- S = L O diag(D, D)^{-1/2} into B --------------------------------
-    const double r2 = 1.4142135623730951;
     for (int idx = tid; idx < n2 * n2; idx += nt) {
       int i = idx / n2, c = idx % n2;
       int q = c < nL ? c : c - nL;
@@ -458,7 +483,7 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
         double2 w = sm.W[k * LD + col];
         s += sm.A[i * LD + k] * (c < nL ? w.y : w.x);
       }
-      sm.B[i * LD + c] = r2 * s / sqrt(sm.Dq[q]);
+      sm.B[i * LD + c] = s * sm.rsD[q];
     }
     __syncthreads();
     // ---- U, V (a = U b + V^* b^dag) --------------------------------------

@@ -465,7 +465,10 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
   tm.mark("normalise");
   if (o->precision == GBSMPS_PREC_MIXED) {
     // the sampler's right-canonical form: every bond's factor in one launch
-    // (one SM per bond), then the sites' transforms spread over side streams
+    // (one SM per bond), then the sites' transforms spread over side streams.
+    // (Factoring bond groups on a side stream while the environment chain
+    // still runs was measured no faster: the chain's split-K GEMMs already
+    // occupy the GPU.)
     CanonWork w;
     rc = canon_prepare(M, &w, s);
     if (!rc) rc = canon_bonds(c, M, &w, 1, N - 1, s);
