@@ -216,7 +216,7 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       gbsmps_mps* M = Ms[mixed[k]].get();
       cudaStream_t st = side[k % nside];
       rc = gbs::canon_bonds(c, M, cw[k].get(), 1, M->N - 1, st);
-      for (int m = 0; m < M->N && !rc; ++m) rc = gbs::canon_site(M, cw[k].get(), m, st);
+      if (!rc) rc = gbs::canon_sites_grouped(M, cw[k].get(), st);
     }
     for (int j = 0; j < nside; ++j) {           // join (also on an error above)
       cudaEventRecord(evs[j], side[j]);

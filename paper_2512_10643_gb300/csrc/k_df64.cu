@@ -49,6 +49,7 @@ __device__ __forceinline__ Df df_split(double x) {
 
 struct DfArgs {
   int M, N, K, opa, opb;
+  int herm;                     // C is Hermitian: compute i >= j, mirror the rest
   const double2* A; long long lda, sA;
   const double2* B; long long ldb, sB;
   double2* C; long long ldc, sC;
@@ -63,6 +64,8 @@ struct DfTile {
   const double2* A; long long lda;
   const double2* B; long long ldb;
   double2* C; long long ldc;
+  int herm = 0;     // Hermitian C: only elements i >= j are stored from this tile...
+  int mirror = 0;   // ...and, if set, C[j][i] = conj(C[i][j]) for i > j as well
 };
 
 // TM x TN tile on 16 x 16 threads, (TM/16) x (TN/16) outputs each.  Every
@@ -72,6 +75,9 @@ template <int TM, int TN>
 __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbeg, int kend,
                                         float (*As)[TM + 1][4], float (*Bs)[TN + 1][4]) {
   constexpr int RM = TM / 16, RN = TN / 16;
+  // Hermitian result: a tile strictly above the diagonal is never needed
+  // (its elements are the mirrors of lower ones), whatever the tile shape
+  if (p.herm && i0 + TM - 1 < j0) return;
   const double2* A = p.A;
   const double2* B = p.B;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -143,9 +149,13 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
     for (int c = 0; c < RN; ++c) {
       const int gj = j0 + tx + 16 * c;
       if (gj >= p.N) continue;
-      p.C[(long long)gi * p.ldc + gj] =
-          make_double2((double)ah[r][c][0] + (double)al[r][c][0],
-                       (double)ah[r][c][1] + (double)al[r][c][1]);
+      const double2 v = make_double2((double)ah[r][c][0] + (double)al[r][c][0],
+                                     (double)ah[r][c][1] + (double)al[r][c][1]);
+      if (p.herm) {
+        if (gi < gj) continue;
+        if (p.mirror && gi > gj) p.C[(long long)gj * p.ldc + gi] = cconj(v);
+      }
+      p.C[(long long)gi * p.ldc + gj] = v;
     }
   }
 }
@@ -162,7 +172,7 @@ __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
   const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
   DfTile t{p.M, p.N, p.opa, p.opb, p.A + bz * p.sA, p.lda, p.B + bz * p.sB, p.ldb,
            p.ksplit > 1 ? p.part + (long long)blockIdx.z * p.M * p.N : p.C + bz * p.sC,
-           p.ksplit > 1 ? (long long)p.N : p.ldc};
+           p.ksplit > 1 ? (long long)p.N : p.ldc, p.herm, p.ksplit > 1 ? 0 : 1};
   df_tile<TM, TN>(t, blockIdx.y * TM, blockIdx.x * TN, kbeg, kend, As, Bs);
 }
 
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
           K = Dr;
         } else {
           p = DfTile{Dl, Dl, 0, 1, J.X, (long long)J.d * Dr, A, (long long)J.d * Dr,
-                     J.R + J.eoff[m], Dl};
+                     J.R + J.eoff[m], Dl, 1, 1};            // R^m is Hermitian
           K = J.d * Dr;
         }
         const long long tn = (p.N + TN - 1) / TN;
@@ -213,14 +223,16 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
 }
 
 __global__ void df_reduce_kernel(const double2* __restrict__ part, int ksplit, int batch, int M,
-                                 int N, double2* C, long long ldc, long long sC) {
+                                 int N, double2* C, long long ldc, long long sC, int herm) {
   const long long n = (long long)batch * M * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / ((long long)M * N), r = (i / N) % M, c = i % N;
+    if (herm && r < c) continue;
     double2 s = make_double2(0.0, 0.0);
     for (int k = 0; k < ksplit; ++k) s = cadd(s, part[((b * ksplit + k) * M + r) * N + c]);
     C[b * sC + r * ldc + c] = s;
+    if (herm && r > c) C[b * sC + c * ldc + r] = cconj(s);
   }
 }
 
@@ -254,8 +266,9 @@ std::map<std::array<int, 6>, int> g_df_tune;
 cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
                               long long sA, const double2* B, long long ldb, long long sB,
                               double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
-                              void* work, size_t work_bytes) {
+                              void* work, size_t work_bytes, int herm) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (herm && M != N) return cudaErrorInvalidValue;
   // the k split follows from the 64 x 64 tiling whatever tile shape then runs
   const long long tiles = (long long)((M + DM - 1) / DM) * ((N + DN - 1) / DN) * batch;
   int ksplit = 1;
@@ -267,11 +280,12 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
   }
   int kchunk = ((K + ksplit - 1) / ksplit + DK - 1) / DK * DK;
   ksplit = (K + kchunk - 1) / kchunk;
-  DfArgs a{M, N, K, opa == 'C' ? 1 : 0, opb == 'C' ? 1 : 0, A, lda, sA, B, ldb, sB, C, ldc, sC,
-           ksplit, kchunk, reinterpret_cast<double2*>(work)};
+  DfArgs a{M, N, K, opa == 'C' ? 1 : 0, opb == 'C' ? 1 : 0, herm ? 1 : 0, A, lda, sA, B, ldb, sB, C,
+           ldc, sC, ksplit, kchunk, reinterpret_cast<double2*>(work)};
   int cfg = -1;
   if (const char* e = getenv("GBSMPS_DF64_TILE")) cfg = std::max(0, std::min(2, atoi(e)));
-  const std::array<int, 6> key{a.opa * 2 + a.opb, pow2i(M), pow2i(N), pow2i(K), pow2i(batch), ksplit};
+  const std::array<int, 6> key{(a.opa * 2 + a.opb) * 2 + a.herm, pow2i(M), pow2i(N), pow2i(K),
+                               pow2i(batch), ksplit};
   if (cfg < 0) {
     std::lock_guard<std::mutex> lk(g_df_mu);
     auto it = g_df_tune.find(key);
@@ -308,7 +322,7 @@ cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const dou
   if (ksplit > 1) {
     const long long n = (long long)batch * M * N;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
-    df_reduce_kernel<<<blocks, 256, 0, s>>>(a.part, ksplit, batch, M, N, C, ldc, sC);
+    df_reduce_kernel<<<blocks, 256, 0, s>>>(a.part, ksplit, batch, M, N, C, ldc, sC, a.herm);
     COUNT_LAUNCH(1);
   }
   return cudaGetLastError();

@@ -33,6 +33,7 @@ constexpr int SQ_N = 260;
 struct PcoSmem {
   double2 Q[QS * QS];
   double sq[SQ_N];
+  double ik[SQ_N];          // 1 / k: the loops multiply instead of dividing in FP64
   int mol[NEM], mor[NEM];
   double2 coef[130];
 };
@@ -49,7 +50,10 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
   const int ia = nl;                         // index of a_m in c_m
   for (int idx = tid; idx < nm * nm; idx += nt)
     sm.Q[(idx / nm) * QS + idx % nm] = t.Q[(size_t)(idx / nm) * t.qs + idx % nm];
-  for (int k = tid; k < SQ_N; k += nt) sm.sq[k] = sqrt((double)k);
+  for (int k = tid; k < SQ_N; k += nt) {
+    sm.sq[k] = sqrt((double)k);
+    sm.ik[k] = k > 0 ? 1.0 / k : 0.0;
+  }
   if (tid < NEM) { sm.mol[tid] = 0; sm.mor[tid] = 0; }
   __syncthreads();
   for (int idx = tid; idx < Dl * nl; idx += nt) atomicMax(&sm.mol[idx % nl], occ_of(t.occl, idx / nl, idx % nl));
@@ -97,14 +101,14 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
             const int kmax = min(a, b);
             for (int k = 1; k <= kmax; ++k) {
               s = lq2[lq[s]];
-              tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] / k));
+              tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] * sm.ik[k]));
               cfma(acc, tk, x[s]);
             }
           } else {
             const C2 gh = cscale(g, (T)0.5);
             for (int j = 1; 2 * j <= a; ++j) {
               s = lq[lq[s]];
-              tk = cscale(cmul(tk, gh), (T)(sm.sq[a - 2 * j + 2] * sm.sq[a - 2 * j + 1] / j));
+              tk = cscale(cmul(tk, gh), (T)(sm.sq[a - 2 * j + 2] * sm.sq[a - 2 * j + 1] * sm.ik[j]));
               cfma(acc, tk, x[s]);
             }
           }
@@ -139,7 +143,7 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
         for (int k = 1; k <= kmax; ++k) {
           s = lq[s];
           r = lr[r];
-          tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] / k));
+          tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] * sm.ik[k]));
           cfma(acc, tk, cur[(size_t)s * Dr + r]);
         }
         nxt[idx] = acc;

@@ -193,8 +193,8 @@ struct CanonWork {               // temporaries of the right-canonical packing
 int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s);
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s);
 int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s);
+int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st);
 int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
-int canon_sites_parallel(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w0, int nside, StageTimer& tm);
 int finish(gbsmps_ctx* c, gbsmps_mps* M);
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                  gbsmps_mps_t* out);

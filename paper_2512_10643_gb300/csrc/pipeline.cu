@@ -216,7 +216,7 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
       CK(launch_zgemm_df64('N', 'N', Dl * d, Dr, Dr, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, X, Dr, 0,
                            1, s, kw.p, wbytes));
       CK(launch_zgemm_df64('N', 'C', Dl, Dl, d * Dr, X, d * Dr, 0, A, d * Dr, 0, R + M->eoff[m], Dl,
-                           0, 1, s, kw.p, wbytes));
+                           0, 1, s, kw.p, wbytes, /*herm=*/1));
     }
     kw.release();
   } else {
@@ -302,6 +302,9 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
 }
 
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s) {
+  // FP64, one SM per bond (a double-float form on the FP32 pipes was measured
+  // slower: these loops are bound by dependency latency and barriers, and
+  // double-float multiplies the instructions on the critical path)
   if (nb <= 0) return GBSMPS_OK;
   CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), M->eoff_dev.as<long long>(),
                  M->ba.D, b0, nb, w->du.as<double>(), c->d_status, s));
@@ -352,58 +355,66 @@ int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
   if (rc) return rc;
   canon_report(M, &w, tm, s);
   tm.mark("cholesky");
-  for (int m = 0; m < M->N && !rc; ++m) rc = canon_site(M, &w, m, s);
+  rc = canon_sites_grouped(M, &w, s);
   if (rc) return rc;
   tm.mark("canonical_pack");
   return GBSMPS_OK;
 }
 
-// Spread the per-site transforms and packing of one state over side streams
-// (each with its own temporaries): the sites are independent once every
-// bond's factor exists, and each site's work is a few small launches.
-int canon_sites_parallel(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w0, int nside, StageTimer& tm) {
-  cudaStream_t s = c->stream;
-  const int N = M->N;
-  nside = std::max(1, std::min(nside, N));
-  std::vector<std::unique_ptr<CanonWork>> ws(nside);
-  std::vector<cudaStream_t> side(nside);
-  std::vector<cudaEvent_t> ev(nside + 1, nullptr);
-  auto drop = [&] { for (auto e : ev) if (e) cudaEventDestroy(e); };
-  for (auto& e : ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      drop();
-      return fail(GBSMPS_ERR_CUDA, "event creation failed");
-    }
-  // temporaries of the extra workers come from the main stream
-  for (int j = 1; j < nside; ++j) {
-    ws[j].reset(new CanonWork());
-    ws[j]->wbytes = w0->wbytes;
-    size_t xmax = 0;
-    for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * M->d * M->D[m + 1]);
-    cudaError_t e = ws[j]->tb.alloc(sizeof(float2) * (xmax + 8), s);
-    if (!e) e = ws[j]->ab.alloc(sizeof(float2) * (xmax + 8), s);
-    if (!e) e = ws[j]->kw.alloc(ws[j]->wbytes, s);
-    if (e) { drop(); return fail(GBSMPS_ERR_OOM, "canonical transform temporaries"); }
-  }
-  cudaEventRecord(ev[nside], s);
-  for (int j = 0; j < nside; ++j) {
-    side[j] = c->side_stream(j);
-    if (!side[j]) { drop(); return fail(GBSMPS_ERR_CUDA, "could not create a side stream"); }
-    cudaStreamWaitEvent(side[j], ev[nside], 0);
-  }
-  int rc = GBSMPS_OK;
-  for (int m = 0; m < N && !rc; ++m) {
-    const int j = m % nside;
-    rc = canon_site(M, j == 0 ? w0 : ws[j].get(), m, side[j]);
-  }
-  for (int j = 0; j < nside; ++j) {              // join, also after an error
-    cudaEventRecord(ev[j], side[j]);
-    cudaStreamWaitEvent(s, ev[j], 0);
-  }
-  drop();
-  ws.clear();                                     // frees on the main stream, after the join
+// The transforms of runs of consecutive sites with the same bond dimensions
+// (all the interior sites once chi binds) as batched GEMMs: T = Ahat^m L_{m+1}
+// for every site of a run in one launch, then At = L_m^{-1} T (one GEMM with
+// N = d D_{m+1} per site) in one launch, then the packing.  The workspace
+// keeps the k split at one 16-deep stage per partial (FP64-reduced), exactly
+// as the per-site launches do, so the results are the same.
+int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
+  const int N = M->N, d = M->d;
+  int rc = canon_site(M, w0, 0, st);
   if (rc) return rc;
-  tm.mark("canonical_pack");
+  const size_t budget = (size_t)2 << 30;          // split-K partials of one group
+  size_t tmax = 0, kmax = 0;
+  for (int m = 1; m < N; ++m) {
+    const size_t el = (size_t)M->D[m] * d * M->D[m + 1];
+    const size_t ks = (size_t)std::max((M->D[m] + 15) / 16, (M->D[m + 1] + 15) / 16);
+    const size_t cnt = std::max<size_t>(1, std::min<size_t>(32, budget / (ks * el * sizeof(float2))));
+    tmax = std::max(tmax, cnt * el);
+    kmax = std::max(kmax, cnt * el * ks);
+  }
+  if (N < 2) return GBSMPS_OK;
+  DevBuf Tg, Ag, kw;
+  CK(Tg.alloc(sizeof(float2) * (tmax + 8), st));
+  CK(Ag.alloc(sizeof(float2) * (tmax + 8), st));
+  CK(kw.alloc(sizeof(float2) * (kmax + 8), st));
+  const double2* Ah = M->tens_mixed.as<double2>();
+  for (int m0 = 1; m0 < N;) {
+    const int Dl = M->D[m0], Dr = M->D[m0 + 1];
+    const size_t el = (size_t)Dl * d * Dr;
+    const size_t ks = (size_t)std::max((Dl + 15) / 16, (Dr + 15) / 16);
+    const int cmax = (int)std::max<size_t>(1, std::min<size_t>(32, budget / (ks * el * sizeof(float2))));
+    int cnt = 1;
+    while (m0 + cnt < N && cnt < cmax && M->D[m0 + cnt] == Dl && M->D[m0 + cnt + 1] == Dr) ++cnt;
+    // equal dimensions make the tensor and factor offsets uniform strides
+    const long long sT = (long long)el, sE = (long long)Dr * Dr, sEl = (long long)Dl * Dl;
+    CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m0], 1, Dr, sT,
+                       M->lchol.as<double2>() + M->eoff[m0 + 1], 1, Dr, sE, Tg.p, 0, Dr, sT, cnt, st,
+                       kw.p, sizeof(float2) * (kmax + 8)));
+    CK(launch_zgemm_tc(6, 'N', 'N', Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m0], 1, Dl, sEl,
+                       Tg.p, 0, d * Dr, sT, Ag.p, 0, d * Dr, sT, cnt, st, kw.p,
+                       sizeof(float2) * (kmax + 8)));
+    for (int k = 0; k < cnt; ++k) {
+      const int m = m0 + k;
+      __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
+      CK(launch_pack_b(Ag.as<float2>() + (size_t)k * el, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp,
+                       (long long)M->Np[m] * M->Kp[m], st));
+      COUNT_LAUNCH(1);
+      if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
+        return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+    }
+    m0 += cnt;
+  }
+  Tg.release();
+  Ag.release();
+  kw.release();
   return GBSMPS_OK;
 }
 
@@ -475,8 +486,9 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
     if (rc) return rc;
     canon_report(M, &w, tm, s);
     tm.mark("cholesky");
-    rc = canon_sites_parallel(c, M, &w, 4, tm);
+    rc = canon_sites_grouped(M, &w, s);
     if (rc) return rc;
+    tm.mark("canonical_pack");
   }
   rc = finish(c, M);
   if (rc) return rc;

@@ -123,3 +123,4 @@ def test_tcgen05_gemm_matches_simt_reference(ctx, monkeypatch):
         assert np.all(s_ph.astype(int).sum(1) % 2 == 0)
     finally:
         m.release()
+
