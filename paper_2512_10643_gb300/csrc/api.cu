@@ -12,6 +12,7 @@
 #include <vector>
 
 std::atomic<unsigned long long> g_kernel_launches{0};
+KernelTrace g_tc_trace;
 
 thread_local std::string g_detail;
 

@@ -288,13 +288,11 @@ cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, 
                         int b0, int nb, double* dused, int* status, cudaStream_t s);
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
                          int nb, cudaStream_t s);
-// split-BF16 tensor-core complex GEMM (nterms 3 or 6), operands FP64 or FP32
-// complex (a64/b64/c64 flags), op 'N' or 'C'; counts its own launch
-cudaError_t launch_zgemm_tc(int nterms, char opa, char opb, int M, int N, int K,
-                            const void* A, int a64, long long lda, long long sA,
-                            const void* B, int b64, long long ldb, long long sB,
-                            void* C, int c64, long long ldc, long long sC, int batch,
-                            cudaStream_t s, void* work = nullptr, size_t work_bytes = 0);
+// complex GEMM in FP32 on the CUDA cores (k_f32gemm.cu): C (FP32) = A B with
+// A, B FP64 (a64/b64 = 1) or FP32, row-major, batched by strides
+cudaError_t launch_zgemm_f32(int M, int N, int K, const void* A, int a64, long long lda, long long sA,
+                             const void* B, int b64, long long ldb, long long sB, float2* C,
+                             long long ldc, long long sC, int batch, cudaStream_t s);
 cudaError_t launch_sample_select(int S, int d, int Dm, const double2* W,
                                  const double2* Y, const double* u, int ustride,
                                  int site, uint64_t seed, uint64_t counter0,

@@ -498,7 +498,8 @@ __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict
   const double2* Sm = src + off[b];
   double2* R = dst + off[b];
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ double dmax;
+  __shared__ double dmax, lkk_s, il_s;
+  __shared__ bool piv_ok;
   if (tid == 0) {
     double m = 0.0;
     for (int i = 0; i < D; ++i) m = fmax(m, Sm[(long long)i * D + i].x);
@@ -519,12 +520,16 @@ __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict
     __syncthreads();
     okf = true;
     for (int k = 0; k < D; ++k) {
-      const double akk = R[(long long)k * D + k].x;
-      if (!(akk > 0.0)) { okf = false; break; }   // same value in every thread
-      const double lkk = sqrt(akk), il = 1.0 / lkk;
-    __syncthreads();
+      if (tid == 0) {                    // one thread takes the FP64 square root
+        const double akk = R[(long long)k * D + k].x;
+        piv_ok = akk > 0.0;
+        if (piv_ok) { lkk_s = sqrt(akk); il_s = 1.0 / lkk_s; }
+      }
+      __syncthreads();
+      if (!piv_ok) { okf = false; break; }   // same value in every thread
+      const double il = il_s;
     for (int i = k + 1 + tid; i < D; i += nt) R[(long long)i * D + k] = cscale(R[(long long)i * D + k], il);
-    if (tid == 0) R[(long long)k * D + k] = cmk(lkk, 0.0);
+    if (tid == 0) R[(long long)k * D + k] = cmk(lkk_s, 0.0);
     __syncthreads();
     const int w = D - k - 1;
     for (long long idx = tid; idx < (long long)w * w; idx += nt) {
@@ -554,14 +559,16 @@ __global__ void trinv_kernel(const double2* __restrict__ Lb, double2* __restrict
   const int D = Dv[b];
   const double2* L = Lb + off[b];
   double2* X = Xb + off[b];
+  extern __shared__ double nidiag[];       // -1 / L_ii, one FP64 division per row
+  for (int i = threadIdx.x; i < D; i += blockDim.x) nidiag[i] = -1.0 / L[(long long)i * D + i].x;
+  __syncthreads();
   for (int j = threadIdx.x; j < D; j += blockDim.x) {
     for (int i = 0; i < j; ++i) X[(long long)i * D + j] = cmk(0.0, 0.0);
-    const double2 ljj = L[(long long)j * D + j];
-    X[(long long)j * D + j] = cmk(1.0 / ljj.x, 0.0);
+    X[(long long)j * D + j] = cmk(-nidiag[j], 0.0);
     for (int i = j + 1; i < D; ++i) {
       double2 s = cmk(0.0, 0.0);
       for (int k = j; k < i; ++k) cfma(s, L[(long long)i * D + k], X[(long long)k * D + j]);
-      X[(long long)i * D + j] = cscale(s, -1.0 / L[(long long)i * D + i].x);
+      X[(long long)i * D + j] = cscale(s, nidiag[i]);
     }
   }
 }
@@ -682,6 +689,6 @@ cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, 
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
                          int nb, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  trinv_kernel<<<nb, 256, 0, s>>>(L, X, off, Dv, b0);
+  trinv_kernel<<<nb, 256, sizeof(double) * 4096, s>>>(L, X, off, Dv, b0);
   return cudaGetLastError();
 }

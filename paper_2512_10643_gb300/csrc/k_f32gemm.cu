@@ -1,0 +1,97 @@
+// Complex GEMM in FP32 on the CUDA cores, for the right-canonical transforms
+// of the mixed sampler (T = Ahat^m L_{m+1}, At = L_m^{-1} T).  Their output
+// feeds the sampler's split-FP16 planes (2^-22 of the unit scale) and the
+// sampler normalises every sample's weights by their sum, so FP32 products
+// with round-to-nearest accumulation (relative error ~ sqrt(K) 2^-24, no
+// bias) are accurate enough; the tensor cores' FP32 accumulation would need
+// one FP64-reduced partial per 16-deep stage to match that, which costs far
+// more than it saves on these small products.  Operands are FP64 or FP32 in
+// memory and FP32 in shared memory; output FP32.  Batched by strides.
+// Tile: 64 x 64 complex outputs, 16 complex k per stage, 256 threads of 4 x 4.
+#include "internal.h"
+#include <algorithm>
+
+namespace {
+
+constexpr int FM = 64, FN = 64, FK = 16;
+
+struct F32Args {
+  int M, N, K;
+  const void* A; long long lda, sA;
+  const void* B; long long ldb, sB;
+  float2* C; long long ldc, sC;
+};
+
+__device__ __forceinline__ float2 tof(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 tof(float2 v) { return v; }
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
+  __shared__ float2 As[FK][FM + 1];     // padded rows: the k-fastest fills hit distinct banks
+  __shared__ float2 Bs[FK][FN + 1];
+  const long long bz = blockIdx.z;
+  const TA* A = reinterpret_cast<const TA*>(p.A) + bz * p.sA;
+  const TB* B = reinterpret_cast<const TB*>(p.B) + bz * p.sB;
+  float2* C = p.C + bz * p.sC;
+  const int i0 = blockIdx.y * FM, j0 = blockIdx.x * FN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < p.K; k0 += FK) {
+    for (int e = tid; e < FM * FK; e += 256) {
+      const int ii = e / FK, kk = e % FK, gi = i0 + ii, gk = k0 + kk;
+      As[kk][ii] = (gi < p.M && gk < p.K) ? tof(A[(long long)gi * p.lda + gk]) : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < FK * FN; e += 256) {
+      const int kk = e / FN, jj = e % FN, gj = j0 + jj, gk = k0 + kk;
+      Bs[kk][jj] = (gj < p.N && gk < p.K) ? tof(B[(long long)gk * p.ldb + gj]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < FK; ++kk) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][c].x = fmaf(a[r].x, b[c].x, fmaf(-a[r].y, b[c].y, acc[r][c].x));
+          acc[r][c].y = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acc[r][c].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gi = i0 + ty + 16 * r;
+    if (gi >= p.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gj = j0 + tx + 16 * c;
+      if (gj < p.N) C[(long long)gi * p.ldc + gj] = acc[r][c];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_zgemm_f32(int M, int N, int K, const void* A, int a64, long long lda, long long sA,
+                             const void* B, int b64, long long ldb, long long sB, float2* C,
+                             long long ldc, long long sC, int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  F32Args a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC};
+  dim3 grid((N + FN - 1) / FN, (M + FM - 1) / FM, batch);
+  if (a64 && b64) zgemm_f32_kernel<double2, double2><<<grid, 256, 0, s>>>(a);
+  else if (a64) zgemm_f32_kernel<double2, float2><<<grid, 256, 0, s>>>(a);
+  else if (b64) zgemm_f32_kernel<float2, double2><<<grid, 256, 0, s>>>(a);
+  else zgemm_f32_kernel<float2, float2><<<grid, 256, 0, s>>>(a);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}

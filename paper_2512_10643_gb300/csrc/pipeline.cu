@@ -319,14 +319,13 @@ int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
   const double2* Ah = M->tens_mixed.as<double2>();
   float2* T = w->tb.as<float2>();
   float2* At = w->ab.as<float2>();
-  // the canonical tensors feed fp16x2 planes: FP32-level products suffice
-  CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
-                     M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, 0, Dr, 0, 1, s,
-                     w->kw.p, w->wbytes));
+  // the canonical tensors feed fp16x2 planes: FP32 products suffice
+  CK(launch_zgemm_f32(Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
+                      M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, Dr, 0, 1, s));
   const float2* src = T;
   if (m > 0) {
-    CK(launch_zgemm_tc(6, 'N', 'N', Dl, Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0,
-                       T, 0, d * Dr, Dr, At, 0, d * Dr, Dr, d, s, w->kw.p, w->wbytes));
+    CK(launch_zgemm_f32(Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0, T, 0, d * Dr,
+                        0, At, d * Dr, 0, 1, s));
     src = At;
   }
   __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
@@ -364,43 +363,36 @@ int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
 // The transforms of runs of consecutive sites with the same bond dimensions
 // (all the interior sites once chi binds) as batched GEMMs: T = Ahat^m L_{m+1}
 // for every site of a run in one launch, then At = L_m^{-1} T (one GEMM with
-// N = d D_{m+1} per site) in one launch, then the packing.  The workspace
-// keeps the k split at one 16-deep stage per partial (FP64-reduced), exactly
-// as the per-site launches do, so the results are the same.
+// N = d D_{m+1} per site) in one launch, then the packing.
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
   const int N = M->N, d = M->d;
   int rc = canon_site(M, w0, 0, st);
   if (rc) return rc;
-  const size_t budget = (size_t)2 << 30;          // split-K partials of one group
-  size_t tmax = 0, kmax = 0;
+  const size_t budget = (size_t)1 << 30;          // bytes of T (and of At) per group
+  size_t tmax = 0;
   for (int m = 1; m < N; ++m) {
     const size_t el = (size_t)M->D[m] * d * M->D[m + 1];
-    const size_t ks = (size_t)std::max((M->D[m] + 15) / 16, (M->D[m + 1] + 15) / 16);
-    const size_t cnt = std::max<size_t>(1, std::min<size_t>(32, budget / (ks * el * sizeof(float2))));
+    const size_t cnt = std::max<size_t>(1, std::min<size_t>(64, budget / (el * sizeof(float2))));
     tmax = std::max(tmax, cnt * el);
-    kmax = std::max(kmax, cnt * el * ks);
   }
   if (N < 2) return GBSMPS_OK;
-  DevBuf Tg, Ag, kw;
+  DevBuf Tg, Ag;
   CK(Tg.alloc(sizeof(float2) * (tmax + 8), st));
   CK(Ag.alloc(sizeof(float2) * (tmax + 8), st));
-  CK(kw.alloc(sizeof(float2) * (kmax + 8), st));
   const double2* Ah = M->tens_mixed.as<double2>();
   for (int m0 = 1; m0 < N;) {
     const int Dl = M->D[m0], Dr = M->D[m0 + 1];
     const size_t el = (size_t)Dl * d * Dr;
-    const size_t ks = (size_t)std::max((Dl + 15) / 16, (Dr + 15) / 16);
-    const int cmax = (int)std::max<size_t>(1, std::min<size_t>(32, budget / (ks * el * sizeof(float2))));
+    const int cmax = (int)std::max<size_t>(1, std::min<size_t>(64, budget / (el * sizeof(float2))));
     int cnt = 1;
     while (m0 + cnt < N && cnt < cmax && M->D[m0 + cnt] == Dl && M->D[m0 + cnt + 1] == Dr) ++cnt;
     // equal dimensions make the tensor and factor offsets uniform strides
     const long long sT = (long long)el, sE = (long long)Dr * Dr, sEl = (long long)Dl * Dl;
-    CK(launch_zgemm_tc(6, 'N', 'N', Dl * d, Dr, Dr, Ah + M->toff[m0], 1, Dr, sT,
-                       M->lchol.as<double2>() + M->eoff[m0 + 1], 1, Dr, sE, Tg.p, 0, Dr, sT, cnt, st,
-                       kw.p, sizeof(float2) * (kmax + 8)));
-    CK(launch_zgemm_tc(6, 'N', 'N', Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m0], 1, Dl, sEl,
-                       Tg.p, 0, d * Dr, sT, Ag.p, 0, d * Dr, sT, cnt, st, kw.p,
-                       sizeof(float2) * (kmax + 8)));
+    CK(launch_zgemm_f32(Dl * d, Dr, Dr, Ah + M->toff[m0], 1, Dr, sT,
+                        M->lchol.as<double2>() + M->eoff[m0 + 1], 1, Dr, sE, Tg.as<float2>(), Dr, sT,
+                        cnt, st));
+    CK(launch_zgemm_f32(Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m0], 1, Dl, sEl, Tg.p, 0,
+                        d * Dr, sT, Ag.as<float2>(), d * Dr, sT, cnt, st));
     for (int k = 0; k < cnt; ++k) {
       const int m = m0 + k;
       __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
@@ -414,7 +406,6 @@ int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
   }
   Tg.release();
   Ag.release();
-  kw.release();
   return GBSMPS_OK;
 }
 
