@@ -16,23 +16,26 @@ namespace {
 constexpr int FM = 64, FN = 64, FK = 16;
 
 struct F32Args {
-  int M, N, K;
+  int M, N, K, opb;
   const void* A; long long lda, sA;
   const void* B; long long ldb, sB;
-  float2* C; long long ldc, sC;
+  void* C; long long ldc, sC;
 };
 
 __device__ __forceinline__ float2 tof(double2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ float2 tof(float2 v) { return v; }
 
-template <typename TA, typename TB>
+__device__ __forceinline__ void store(float2* c, float2 v) { *c = v; }
+__device__ __forceinline__ void store(double2* c, float2 v) { *c = make_double2(v.x, v.y); }
+
+template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
   __shared__ float2 As[FK][FM + 1];     // padded rows: the k-fastest fills hit distinct banks
   __shared__ float2 Bs[FK][FN + 1];
   const long long bz = blockIdx.z;
   const TA* A = reinterpret_cast<const TA*>(p.A) + bz * p.sA;
   const TB* B = reinterpret_cast<const TB*>(p.B) + bz * p.sB;
-  float2* C = p.C + bz * p.sC;
+  TC* C = reinterpret_cast<TC*>(p.C) + bz * p.sC;
   const int i0 = blockIdx.y * FM, j0 = blockIdx.x * FN;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float2 acc[4][4];
@@ -46,8 +49,15 @@ __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
       As[kk][ii] = (gi < p.M && gk < p.K) ? tof(A[(long long)gi * p.lda + gk]) : make_float2(0.f, 0.f);
     }
     for (int e = tid; e < FK * FN; e += 256) {
-      const int kk = e / FN, jj = e % FN, gj = j0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < p.N && gk < p.K) ? tof(B[(long long)gk * p.ldb + gj]) : make_float2(0.f, 0.f);
+      int kk, jj;
+      if (p.opb == 0) { kk = e / FN; jj = e % FN; } else { jj = e / FK; kk = e % FK; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gj < p.N && gk < p.K) {
+        if (p.opb == 0) v = tof(B[(long long)gk * p.ldb + gj]);
+        else { v = tof(B[(long long)gj * p.ldb + gk]); v.y = -v.y; }   // B^dag
+      }
+      Bs[kk][jj] = v;
     }
     __syncthreads();
 #pragma unroll 4
@@ -74,7 +84,7 @@ __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int gj = j0 + tx + 16 * c;
-      if (gj < p.N) C[(long long)gi * p.ldc + gj] = acc[r][c];
+      if (gj < p.N) store(C + (long long)gi * p.ldc + gj, acc[r][c]);
     }
   }
 }
@@ -86,12 +96,12 @@ cudaError_t launch_zgemm_f32(int M, int N, int K, const void* A, int a64, long l
                              long long ldc, long long sC, int batch, cudaStream_t s) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
-  F32Args a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC};
+  F32Args a{M, N, K, 0, A, lda, sA, B, ldb, sB, C, ldc, sC};
   dim3 grid((N + FN - 1) / FN, (M + FM - 1) / FM, batch);
-  if (a64 && b64) zgemm_f32_kernel<double2, double2><<<grid, 256, 0, s>>>(a);
-  else if (a64) zgemm_f32_kernel<double2, float2><<<grid, 256, 0, s>>>(a);
-  else if (b64) zgemm_f32_kernel<float2, double2><<<grid, 256, 0, s>>>(a);
-  else zgemm_f32_kernel<float2, float2><<<grid, 256, 0, s>>>(a);
+  if (a64 && b64) zgemm_f32_kernel<double2, double2, float2><<<grid, 256, 0, s>>>(a);
+  else if (a64) zgemm_f32_kernel<double2, float2, float2><<<grid, 256, 0, s>>>(a);
+  else if (b64) zgemm_f32_kernel<float2, double2, float2><<<grid, 256, 0, s>>>(a);
+  else zgemm_f32_kernel<float2, float2, float2><<<grid, 256, 0, s>>>(a);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
