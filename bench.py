@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--batch-states", type=int, default=64)
+    ap.add_argument("--ref-budget", type=float, default=20.0,
+                    help="seconds of oracle work behind the CPU baseline / reference arm")
     ap.add_argument("--serving-requests", type=int, default=24)
     ap.add_argument("--serving-rate", type=float, default=4.0)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -69,6 +71,13 @@ def dist_init():
         torch.cuda.set_device(local)
     dist.init_process_group(backend)
     return rank, local, ws, dist
+
+
+def replica_stream(rank, step, samples):
+    """(seed, counter0) of one replica's sampling in one step: every rank has
+    its own Philox key and every step its own counter range, so the replicas
+    draw disjoint streams and no step repeats another's draws."""
+    return 1234 + rank, step * samples
 
 
 def max_over_ranks(x, dist):
@@ -158,7 +167,8 @@ def run_gpu(args, rank, local, ws, dist):
 
     def step(i, sample_count=S, precision=prec, dst=out):
         m = g.MPS.from_cov(ctx, gam, **dict(opts, precision=precision))
-        m.sample(sample_count, seed=1234 + rank, counter0=i * sample_count, out=dst[:sample_count])
+        seed, counter0 = replica_stream(rank, i, sample_count)
+        m.sample(sample_count, seed=seed, counter0=counter0, out=dst[:sample_count])
         m.release()
 
     def barrier():
@@ -446,7 +456,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        est = oracle_step_estimate()
+        est = oracle_step_estimate(args.ref_budget)
         line = dict(base, impl="reference", value=round(est["value"], 6),
                     ms_per_step=round(est["step_s"] * 1e3, 1), dtype="f64", config=cfg,
                     samples_per_s=round(est["samples_per_s"], 3),
@@ -461,7 +471,7 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        est = oracle_step_estimate()
+        est = oracle_step_estimate(args.ref_budget)
         cpu = {"value": round(est["value"], 6), "unit": "tensors/s", "cores": est["cores"],
                "kind": "oracle", "sample": est["sample"],
                "samples_per_s": round(est["samples_per_s"], 3)}
