@@ -266,11 +266,14 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
     T[i * LD + j] = s;
   }
   __syncthreads();
-  for (int idx = tid; idx < n * n; idx += nt) {            // H = W^dag T
+  for (int idx = tid; idx < n * n; idx += nt) {            // H = W^dag T (Hermitian: i <= j)
     const int i = idx / n, j = idx % n;
+    if (i > j) continue;
     double2 s = cmk(0, 0);
     for (int k = 0; k < n; ++k) cfma(s, cconj(W[k * LD + i]), T[k * LD + j]);
+    if (i == j) s.y = 0.0;
     H[i * LD + j] = s;
+    H[j * LD + i] = cconj(s);
   }
   __syncthreads();
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
@@ -432,17 +435,25 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     }
     __syncthreads();
     // ---- L^{-1} by forward substitution, one column per thread ----------
-    for (int j = tid; j < n2; j += nt) {
-      for (int i = 0; i < n2; ++i) {
-        double x;
-        if (i < j) x = 0.0;
-        else if (i == j) x = 1.0 / sm.A[i * LD + i];
-        else {
-          double s = 0.0;
-          for (int k = j; k < i; ++k) s += sm.A[i * LD + k] * sm.B[k * LD + j];
-          x = -s / sm.A[i * LD + i];
+    // (the diagonal's inverses first, one FP64 division each; column j runs
+    // on lane j / 8 of warp j % 8, so the columns' FP64 work is spread over
+    // the SM's four sub-partitions)
+    for (int i = tid; i < n2; i += nt) sm.ev[i] = 1.0 / sm.A[i * LD + i];
+    __syncthreads();
+    {
+      const int j = (tid >> 5) + 8 * (tid & 31);
+      if (j < n2 && tid < 256) {
+        for (int i = 0; i < n2; ++i) {
+          double x;
+          if (i < j) x = 0.0;
+          else if (i == j) x = sm.ev[i];
+          else {
+            double acc = 0.0;
+            for (int k = j; k < i; ++k) acc += sm.A[i * LD + k] * sm.B[k * LD + j];
+            x = -acc * sm.ev[i];
+          }
+          sm.B[i * LD + j] = x;
         }
-        sm.B[i * LD + j] = x;
       }
     }
     __syncthreads();
