@@ -22,6 +22,7 @@ namespace {
 
 constexpr int LD = N2M;
 constexpr int CHAIN_THREADS = 256;
+static_assert(CHAIN_THREADS == 256, "the spreads over sub-partitions, q = 8 lane + warp, assume 8 warps");
 constexpr int MAX_SWEEPS = 40;
 
 struct ChainSmem {
@@ -70,6 +71,23 @@ __device__ double block_max(double v, double* red) {
   for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
+}
+
+// 1/sqrt(a) and 1/a in FP64 from the FP32 estimate and Newton steps (each
+// doubles the correct bits: 3 steps from ~24 bits reach FP64 rounding); GB300
+// runs FP64 division and square root as long FP64 instruction sequences on
+// its slow FP64 pipe, these take a few FP64 multiply-adds
+__device__ __forceinline__ double rsqrt_fp64(double a) {
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
+  double r = (double)rsqrtf((float)a);
+  for (int it = 0; it < 3; ++it) r = r * (1.5 - 0.5 * a * r * r);
+  return r;
+}
+__device__ __forceinline__ double rcp_fp64(double a) {
+  if (!(fabs(a) > 1e-30 && fabs(a) < 1e30)) return 1.0 / a;
+  double x = (double)(1.0f / (float)a);
+  for (int it = 0; it < 3; ++it) x = x * (2.0 - a * x);
+  return x;
 }
 
 // Sweeps of the cyclic complex Jacobi method on the n x n Hermitian H (ld LD,
@@ -307,7 +325,8 @@ __device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
       sm.ival[1] = pr;
       const double2 pv = M[pr * NLM + k];       // the pivot after the row swap
       const double pm = cabs2(pv);
-      sm.pinv = pm > 0.0 ? cmk(pv.x / pm, -pv.y / pm) : cmk(0.0, 0.0);
+      const double ipm = pm > 0.0 ? rcp_fp64(pm) : 0.0;
+      sm.pinv = cmk(pv.x * ipm, -pv.y * ipm);
       sm.dval[1] *= (best > 0.0 ? best : 1e-300);    // |pivots|^2 of a near-unitary-scale U
       if (k == n - 1) sm.dval[0] = 0.5 * log(sm.dval[1]);
     }
@@ -410,12 +429,12 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     for (int idx = tid; idx < n2 * n2; idx += nt) sm.A[(idx / n2) * LD + idx % n2] *= 2.0;
     __syncthreads();
     for (int k = 0; k < n2; ++k) {
-      if (tid == 0) {                  // one thread takes the FP64 square root
+      if (tid == 0) {                  // one thread: 1/sqrt(akk) by Newton from FP32
         double akk = sm.A[k * LD + k];
         if (!(akk > 0.0)) { set_status(status, ST_NUMERIC); akk = 1e-300; }
-        const double lkk = sqrt(akk);
-        sm.dval[2] = lkk;
-        sm.dval[3] = 1.0 / lkk;
+        const double r = rsqrt_fp64(akk);
+        sm.dval[2] = akk * r;
+        sm.dval[3] = r;
       }
       __syncthreads();
       const double ilkk = sm.dval[3];
@@ -469,18 +488,25 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     bool ok = jacobi_herm(sm, n2);
     if (!ok && tid == 0) set_status(status, ST_NOT_CONVERGED);
     // ---- order eigenvalues: positive half ascending = D descending ------
-    if (tid == 0) {
-      for (int i = 0; i < n2; ++i) sm.perm[i] = i;
-      for (int i = 1; i < n2; ++i) {
-        int v = sm.perm[i], j = i - 1;
-        while (j >= 0 && sm.ev[sm.perm[j]] > sm.ev[v]) { sm.perm[j + 1] = sm.perm[j]; --j; }
-        sm.perm[j + 1] = v;
-      }
-      for (int q = 0; q < nL; ++q) {
+    // (a rank per eigenvalue, ties by index: the same order as a stable sort;
+    // a NaN eigenvalue flags the cut and keeps every index in range)
+    for (int i = tid; i < n2; i += nt) sm.perm[i] = i;
+    __syncthreads();
+    for (int i = tid; i < n2; i += nt) {
+      const double e = sm.ev[i];
+      if (e != e) { set_status(status, ST_NUMERIC); continue; }
+      int rank = 0;
+      for (int j = 0; j < n2; ++j) rank += (sm.ev[j] < e || (sm.ev[j] == e && j < i)) ? 1 : 0;
+      sm.perm[rank] = i;
+    }
+    __syncthreads();
+    {
+      const int q = (tid & 31) * 8 + (tid >> 5);     // spread over the sub-partitions
+      if (q < nL) {
         double e = sm.ev[sm.perm[nL + q]];
         if (!(e > 0.0)) { set_status(status, ST_NUMERIC); e = 1.0; }
-        sm.Dq[q] = 1.0 / e;
-        sm.rsD[q] = 1.4142135623730951 * sqrt(e);     // sqrt(2) / sqrt(D_q)
+        sm.Dq[q] = rcp_fp64(e);
+        sm.rsD[q] = 1.4142135623730951 * e * rsqrt_fp64(e);   // sqrt(2) / sqrt(D_q)
       }
     }
     __syncthreads();
@@ -507,7 +533,7 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     }
     __syncthreads();
     // ---- canonical gauge: largest |U_jq| of each column real positive ----
-    for (int q = tid; q < nL; q += nt) {
+    for (int q = (tid & 31) * 8 + (tid >> 5); q < nL; q += nt) {   // spread over sub-partitions
       int jb = 0;
       double best = -1.0;
       for (int j = 0; j < nL; ++j) {
@@ -515,8 +541,8 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
         if (v > best) { best = v; jb = j; }
       }
       double2 u = sm.U[jb * NLM + q];
-      double mg = sqrt(best);
-      double2 ph = cmk(u.x / mg, -u.y / mg);
+      const double img = rsqrt_fp64(best);
+      double2 ph = cmk(u.x * img, -u.y * img);
       for (int j = 0; j < nL; ++j) {
         sm.U[j * NLM + q] = cmul(sm.U[j * NLM + q], ph);
         sm.V[j * NLM + q] = cmul(sm.V[j * NLM + q], ph);
@@ -524,7 +550,8 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     }
     if (tid == 0) {
       int na = 0;
-      while (na < nL && (sm.Dq[na] - 1.0) / (sm.Dq[na] + 1.0) > freeze) ++na;
+      // Lambda^2 = (D - 1) / (D + 1) > freeze, without the division (D + 1 > 0)
+      while (na < nL && sm.Dq[na] - 1.0 > freeze * (sm.Dq[na] + 1.0)) ++na;
       if (na > NEM) { set_status(status, ST_BOUNDS); na = NEM; }
       sm.ival[2] = na;
     }

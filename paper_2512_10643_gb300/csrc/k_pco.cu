@@ -7,18 +7,24 @@
 // the GPU:
 //   1. left-only PCOs (r_q r_q' and r_q r_q) on a D_l vector u = P exp(X_LL)|0>,
 //      right-only PCOs on a D_r vector w; C0 = u w^T is their product state;
-//   2. cross PCOs exp(g r_q^dag l_q'^dag) on the D_l x D_r matrix C0;
+//   2. cross PCOs exp(g r_q^dag l_q'^dag) on the D_l x D_r matrix C0, in place
+//      and only on the entries they change (both modes occupied);
 //   3. the physical PCOs last: with l_L = sum_q Q_{r_q a} r_q^dag and
-//      l_R = sum_q' Q_{a l_q'} l_q'^dag,
+//      l_R = sum_q' Q_{a l_q'} l_q'^dag (they commute),
 //        exp(a^dag (l_L + l_R) + g_aa a^dag^2 / 2) =
-//        sum_p (a^dag)^p sum_k (g_aa/2)^k/k! sum_{i+j=p-2k} l_L^i l_R^j/(i! j!),
-//      so A[., p, .] = c sqrt(p!) sum_k (g_aa/2)^k/k! sum_{i+j=p-2k}
-//      (l_L^i C0 (l_R^T)^j)/(i! j!).
+//        sum_p (a^dag)^p sum_k (g_aa/2)^k/k! (l_L + l_R)^(p-2k) / (p-2k)!,
+//      so A[., p, .] = c sqrt(p!) sum_k (g_aa/2)^k/k! W_{p-2k} with
+//      W_s = (l_L + l_R)^s C0 / s!, built by d - 1 passes of l_L + l_R.
 // Every PCO update is a pull along the lowering maps: the source of a target
 // state with kappa quanta added to modes (q, q') is reached by kappa steps
 // of low_q and low_q'; coefficients g^kappa/kappa! sqrt(n!/(n-kappa)!) are
-// built as running products.  Each pass is out of place (double buffered);
-// the paper's in-place reverse-ordered loop computes the same numbers.
+// built as running products.  The one-sided passes are out of place (double
+// buffered); the cross passes run in place, ordered by level, like the
+// paper's in-place loop ordered from high occupation down.  GB300 runs FP64
+// at about 2 fused multiply-adds per clock per SM, so the grouping is chosen
+// for few FP64 operations: d - 1 passes of l_L + l_R instead of d(d+1)/2 - 1
+// one-sided ones, term lists without empty modes, and the output written
+// once per (s, k) instead of read and written per (i, j, k).
 // T = double is the FP64 path; T = float runs the same passes in FP32 (the
 // mixed-precision build) and accumulates the output tensor in FP64.
 #include "internal.h"
@@ -29,13 +35,14 @@ namespace {
 
 constexpr int PCO_THREADS = 512;
 constexpr int SQ_N = 260;
+constexpr int GE = 258;     // occupation-count table per mode: v = 0..257
 
 struct PcoSmem {
   double2 Q[QS * QS];
   double sq[SQ_N];
   double ik[SQ_N];          // 1 / k: the loops multiply instead of dividing in FP64
   int mol[NEM], mor[NEM];
-  double2 coef[130];
+  double2 gk[SQ_N];         // cross phase: g^k / k!; physical phase: plane coefficients
 };
 
 __device__ inline int occ_of(const uint8_t* occ, int idx, int q) { return occ[(size_t)idx * NEM + q]; }
@@ -68,10 +75,20 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
   C2* u2 = u + Dl;
   C2* w = u2 + Dl;
   C2* w2 = w + Dr;
-  C2* Bf[4] = {w2 + Dr, w2 + Dr + DD, w2 + Dr + 2 * DD, w2 + Dr + 3 * DD};
+  C2* W0 = w2 + Dr;                       // C0, then the cross PCOs in place
+  C2* W1 = W0 + DD;
+  C2* lc = W1 + DD;                       // physical-pass terms of each row / column
+  C2* rc = lc + (size_t)Dl * NEM;
+  int* ls = reinterpret_cast<int*>(rc + (size_t)Dr * NEM);
+  int* rs = ls + (size_t)Dl * NEM;
+  int* lcnt = rs + (size_t)Dr * NEM;
+  int* rcnt = lcnt + Dl;
+  int* listl = rcnt + Dr;                 // occupied rows per mode, occupation descending
+  int* listr = listl + (size_t)NEM * Dl;
+  int* gel = listr + (size_t)NEM * Dr;    // gel[q*GE + v] = rows with occupation >= v
+  int* ger = gel + NEM * GE;
   const C2 zero = to_c<C2>(cmk(0.0, 0.0));
   const C2 one = to_c<C2>(cmk(1.0, 0.0));
-
   // ---- 1. one-sided PCOs on vectors --------------------------------------
   for (int side = 0; side < 2; ++side) {
     const int n = side == 0 ? nl : nr;
@@ -120,109 +137,146 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
     }
     if (side == 0) { u = x; u2 = y; } else { w = x; w2 = y; }
   }
-  // ---- C0 = u w^T ----------------------------------------------------------
-  C2* cur = Bf[0];
-  C2* nxt = Bf[1];
-  for (size_t idx = tid; idx < DD; idx += nt) cur[idx] = cmul(u[idx / Dr], w[idx % Dr]);
+  // ---- C0 = u w^T; term lists for the passes below ----------------------
+  for (size_t idx = tid; idx < DD; idx += nt) W0[idx] = cmul(u[idx / Dr], w[idx % Dr]);
+  for (int side = 0; side < 2; ++side) {
+    const int n = side == 0 ? nl : nr, D = side == 0 ? Dl : Dr;
+    const uint8_t* occ = side == 0 ? t.occl : t.occr;
+    const int* low = side == 0 ? t.lowl : t.lowr;
+    const int cap = side == 0 ? t.capl : t.capr;
+    const int off = side == 0 ? 0 : nl + 1;
+    C2* cf = side == 0 ? lc : rc;
+    int* src = side == 0 ? ls : rs;
+    int* cnt = side == 0 ? lcnt : rcnt;
+    // row mu of l_L (column nu of l_R): sum over occupied modes q of
+    // Q_{q a} sqrt(n_q) times the entry one quantum lower in q
+    for (int i = tid; i < D; i += nt) {
+      int c = 0;
+      for (int q = 0; q < n; ++q) {
+        const int a = occ_of(occ, i, q);
+        const double2 g = sm.Q[(off + q) * QS + ia];
+        if (a == 0 || (g.x == 0.0 && g.y == 0.0)) continue;
+        src[(size_t)i * NEM + c] = low[(size_t)q * cap + i];
+        cf[(size_t)i * NEM + c] = to_c<C2>(cscale(g, sm.sq[a]));
+        ++c;
+      }
+      cnt[i] = c;
+    }
+    // one warp per mode: the occupied entries by occupation, descending
+    const int lane = tid & 31;
+    for (int q = tid >> 5; q < n; q += nt >> 5) {
+      const int mo = side == 0 ? sm.mol[q] : sm.mor[q];
+      int* list = (side == 0 ? listl : listr) + (size_t)q * D;
+      int* ge = (side == 0 ? gel : ger) + q * GE;
+      int k = 0;
+      for (int v = mo; v >= 1; --v) {
+        for (int i0 = 0; i0 < D; i0 += 32) {
+          const int i = i0 + lane;
+          const bool hit = i < D && occ_of(occ, i, q) == v;
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (hit) list[k + __popc(m & ((1u << lane) - 1u))] = i;
+          k += __popc(m);
+        }
+        if (lane == 0) ge[v] = k;
+      }
+      if (lane == 0) ge[mo + 1] = 0;
+    }
+  }
   __syncthreads();
-  // ---- 2. cross PCOs -------------------------------------------------------
+  // ---- 2. cross PCOs, in place ---------------------------------------------
+  // exp(g r_q^dag l_q'^dag) adds to a target with occupations (a, b) the
+  // entries (a - k, b - k), k = 1..min(a, b).  Only targets with both modes
+  // occupied change.  Level m = min(a, b): a target of level m reads only
+  // entries of lower levels, so taking the levels from the top down, with a
+  // barrier between them, updates the buffer in place and gives the same
+  // numbers as an out-of-place pass.
   for (int q = 0; q < nl; ++q) {
     if (sm.mol[q] == 0) continue;
     const int* lq = t.lowl + (size_t)q * t.capl;
     for (int q2 = 0; q2 < nr; ++q2) {
-      if (sm.mor[q2] == 0) continue;
-      const C2 g = to_c<C2>(sm.Q[q * QS + nl + 1 + q2]);
+      const int mq = min(sm.mol[q], sm.mor[q2]);
+      const double2 g = sm.Q[q * QS + nl + 1 + q2];
+      if (mq == 0 || (g.x == 0.0 && g.y == 0.0)) continue;
       const int* lr = t.lowr + (size_t)q2 * t.capr;
-      for (size_t idx = tid; idx < DD; idx += nt) {
-        const int mu = idx / Dr, nu = idx % Dr;
-        const int a = occ_of(t.occl, mu, q), b = occ_of(t.occr, nu, q2);
-        const int kmax = min(a, b);
-        C2 acc = cur[idx];
-        C2 tk = one;
-        int s = mu, r = nu;
-        for (int k = 1; k <= kmax; ++k) {
-          s = lq[s];
-          r = lr[r];
-          tk = cscale(cmul(tk, g), (T)(sm.sq[a - k + 1] * sm.sq[b - k + 1] * sm.ik[k]));
-          cfma(acc, tk, cur[(size_t)s * Dr + r]);
-        }
-        nxt[idx] = acc;
+      if (tid == 0) {                       // g^k / k!
+        double2 gk = cmk(1.0, 0.0);
+        sm.gk[0] = gk;
+        for (int k = 1; k <= mq; ++k) { gk = cscale(cmul(gk, g), sm.ik[k]); sm.gk[k] = gk; }
       }
       __syncthreads();
-      C2* tt = cur; cur = nxt; nxt = tt;
+      const int* la = listl + (size_t)q * Dl;
+      const int* lb = listr + (size_t)q2 * Dr;
+      for (int m = mq; m >= 1; --m) {
+        const long long nA = gel[q * GE + m], nB = ger[q2 * GE + m];
+        const long long nA1 = gel[q * GE + m + 1], nB1 = ger[q2 * GE + m + 1];
+        for (long long e = tid; e < nA * nB; e += nt) {
+          const long long i = e / nB, j = e - i * nB;
+          if (i < nA1 && j < nB1) continue;            // a higher level
+          const int mu = la[i], nu = lb[j];
+          const int a = occ_of(t.occl, mu, q), b = occ_of(t.occr, nu, q2);
+          C2 acc = W0[(size_t)mu * Dr + nu];
+          double r = 1.0;
+          int s = mu, rr = nu;
+          for (int k = 1; k <= m; ++k) {
+            s = lq[s];
+            rr = lr[rr];
+            r *= sm.sq[a - k + 1] * sm.sq[b - k + 1];
+            cfma(acc, to_c<C2>(cscale(sm.gk[k], r)), W0[(size_t)s * Dr + rr]);
+          }
+          W0[(size_t)mu * Dr + nu] = acc;
+        }
+        __syncthreads();
+      }
     }
   }
-  // ---- 3. physical PCOs: A[., p, .] ----------------------------------------
+  // ---- 3. physical PCOs ----------------------------------------------------
+  // l_L and l_R act on different bonds and commute, so the double sum over
+  // l_L^i C0 (l_R^T)^j / (i! j!) with i + j = s is (l_L + l_R)^s C0 / s!:
+  //   W_0 = C0,  W_s = (l_L W_{s-1} + W_{s-1} l_R^T) / s,
+  //   A[., p, .] = c sqrt(p!) sum_k (g_aa/2)^k / k!  W_{p-2k}.
+  // Each pass builds W_s and adds it to the planes p = s + 2k at once; plane
+  // p is first reached at s = p mod 2, which writes it.
   double2* A = t.out;
-  for (size_t idx = tid; idx < DD * d; idx += nt) A[idx] = cmk(0.0, 0.0);
   const double2 gaa2 = cscale(sm.Q[ia * QS + ia], 0.5);
-  C2* P = cur;              // l_L^i C0
-  C2* Pn = nxt;
-  C2* Ya = Bf[2];
-  C2* Yb = Bf[3];
-  for (int i = 0; i < d; ++i) {
-    if (i > 0) {
-      if (nl == 0) break;
-      __syncthreads();
-      for (size_t idx = tid; idx < DD; idx += nt) {
-        const int mu = idx / Dr, nu = idx % Dr;
-        C2 acc = zero;
-        for (int q = 0; q < nl; ++q) {
-          const int a = occ_of(t.occl, mu, q);
-          if (a == 0) continue;
-          const int s = t.lowl[(size_t)q * t.capl + mu];
-          cfma(acc, to_c<C2>(cscale(sm.Q[q * QS + ia], sm.sq[a])), P[(size_t)s * Dr + nu]);
-        }
-        Pn[idx] = acc;
+  C2* Wp = W0;
+  C2* Wn = W1;
+  for (int s = 0; s < d; ++s) {
+    const int kmx = (d - 1 - s) / 2;
+    __syncthreads();
+    if (tid == 0) {
+      double2 gp = cmk(1.0, 0.0);
+      for (int k = 0; k <= kmx; ++k) {
+        const int p = s + 2 * k;
+        sm.gk[k] = cscale(gp, t.c * exp(0.5 * lgamma(p + 1.0) - lgamma(k + 1.0)));
+        gp = cmul(gp, gaa2);
       }
-      __syncthreads();
-      C2* tt = P; P = Pn; Pn = tt;
     }
-    const C2* Ysrc = P;
-    for (int j = 0; i + j < d; ++j) {
-      // coefficients of this (i, j): c sqrt(p!) (g/2)^k / (k! i! j!), p = i + j + 2k
-      const int kmx = (d - 1 - i - j) / 2;
-      __syncthreads();
-      if (tid == 0) {
-        double2 gp = cmk(1.0, 0.0);
-        for (int k = 0; k <= kmx && k < 130; ++k) {
-          const int p = i + j + 2 * k;
-          double lg = 0.5 * lgamma(p + 1.0) - lgamma(k + 1.0) - lgamma(i + 1.0) - lgamma(j + 1.0);
-          sm.coef[k] = cscale(gp, t.c * exp(lg));
-          gp = cmul(gp, gaa2);
-        }
-      }
-      if (j > 0) {
-        if (nr == 0) break;
-        C2* Yn = (Ysrc == Ya) ? Yb : Ya;
-        for (size_t idx = tid; idx < DD; idx += nt) {
-          const int mu = idx / Dr, nu = idx % Dr;
-          C2 acc = zero;
-          for (int q = 0; q < nr; ++q) {
-            const int b = occ_of(t.occr, nu, q);
-            if (b == 0) continue;
-            const int r = t.lowr[(size_t)q * t.capr + nu];
-            cfma(acc, to_c<C2>(cscale(sm.Q[ia * QS + nl + 1 + q], sm.sq[b])), Ysrc[(size_t)mu * Dr + r]);
-          }
-          Yn[idx] = acc;
-        }
-        __syncthreads();
-        Ysrc = Yn;
+    __syncthreads();
+    const T inv_s = s > 0 ? (T)sm.ik[s] : (T)1;
+    for (size_t idx = tid; idx < DD; idx += nt) {
+      const int mu = idx / Dr, nu = idx % Dr;
+      C2 y;
+      if (s == 0) {
+        y = Wp[idx];
       } else {
-        __syncthreads();
+        C2 acc = zero;
+        const int cl = lcnt[mu], cr = rcnt[nu];
+        for (int e = 0; e < cl; ++e)
+          cfma(acc, lc[(size_t)mu * NEM + e], Wp[(size_t)ls[(size_t)mu * NEM + e] * Dr + nu]);
+        for (int e = 0; e < cr; ++e)
+          cfma(acc, rc[(size_t)nu * NEM + e], Wp[(size_t)mu * Dr + rs[(size_t)nu * NEM + e]]);
+        y = cscale(acc, inv_s);
+        if (s + 1 < d) Wn[idx] = y;
       }
-      for (size_t idx = tid; idx < DD; idx += nt) {
-        const int mu = idx / Dr, nu = idx % Dr;
-        const double2 y = to_d(Ysrc[idx]);
-        for (int k = 0; k <= kmx; ++k) {
-          const int p = i + j + 2 * k;
-          double2* dst = A + ((size_t)mu * d + p) * Dr + nu;
-          double2 v = *dst;
-          cfma(v, sm.coef[k], y);
-          *dst = v;
-        }
+      const double2 yd = to_d(y);
+      for (int k = 0; k <= kmx; ++k) {
+        double2* dst = A + ((size_t)mu * d + s + 2 * k) * Dr + nu;
+        double2 v = s < 2 ? cmk(0.0, 0.0) : *dst;
+        cfma(v, sm.gk[k], yd);
+        *dst = v;
       }
     }
+    if (s > 0) { C2* tt = Wp; Wp = Wn; Wn = tt; }
   }
 }
 
@@ -319,7 +373,9 @@ cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, in
 }
 
 size_t pco_scratch_elems(int Dl, int Dr) {
-  return 2 * (size_t)Dl + 2 * (size_t)Dr + 4 * (size_t)Dl * Dr;
+  const size_t D = (size_t)Dl + Dr;
+  const size_t ints = 2 * NEM * D + D + 2 * (size_t)NEM * GE;
+  return 2 * D + 2 * (size_t)Dl * Dr + NEM * D + (ints * sizeof(int) + 15) / 16 + 1;
 }
 
 cudaError_t launch_pco(const SiteTask* tasks_dev, int ntasks, int d, int precision,
