@@ -167,6 +167,24 @@ int gbsmps_sample(gbsmps_mps_t mps, int64_t S, uint64_t seed,
                   uint64_t counter0, const double* uniforms, uint8_t* out,
                   uint8_t* flags, int mem_kind);
 
+/* Build and sample a stream of `count` states: state k is built as by
+ * gbsmps_build_from_cov (Ns[k], gammas[k], opts[k]) and S patterns are drawn
+ * from it as by gbsmps_sample with Philox keys seeds[k], counters from
+ * counter0s[k] (no uniforms, no flags) into outs[k] (S x Ns[k] bytes).  The
+ * Gaussian SVD chain of Sec. II B is sequential and runs on one SM; here the
+ * chain of state k+1 runs while state k is sampled on the other SMs, and the
+ * rest of build k+1 waits for that sampling to finish.  The patterns are
+ * the ones the two separate calls give.  gammas and outs are in mem_kind
+ * memory (host buffers are best page-locked: pageable copies block the
+ * overlap).  Returns when every state is sampled; the handles are released
+ * internally.  On error the remaining states are skipped.  Errors as
+ * gbsmps_build_from_cov and gbsmps_sample.  count = 0 is a no-op. */
+int gbsmps_build_sample_stream(gbsmps_ctx_t ctx, int32_t count, const int32_t* Ns,
+                               const double* const* gammas, const gbsmps_opts* opts,
+                               int64_t S, const uint64_t* seeds,
+                               const uint64_t* counter0s, uint8_t* const* outs,
+                               int mem_kind);
+
 /* Release an MPS and its device memory. */
 int gbsmps_release(gbsmps_mps_t mps);
 

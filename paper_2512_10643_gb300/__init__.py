@@ -102,6 +102,7 @@ def lib():
         "gbsmps_server_destroy": (C.c_int, [vp]),
         "gbsmps_estimate_bytes": (C.c_size_t, [i32, C.POINTER(Opts), i64]),
         "gbsmps_build_batch": (C.c_int, [vp, i32, vp, vp, C.c_int, vp, vp]),
+        "gbsmps_build_sample_stream": (C.c_int, [vp, i32, vp, vp, vp, i64, vp, vp, vp, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -184,6 +185,33 @@ def gbsmps_build_batch(ctx, gammas, opts_list):
     hs = (C.c_void_p * n)()
     _check(lib().gbsmps_build_batch(ctx, n, Ns, gp, kinds.pop(), op, hs))
     return [C.c_void_p(h) for h in hs]
+
+
+def gbsmps_build_sample_stream(ctx, gammas, opts_list, S: int, seeds, counter0s, outs):
+    """Build and sample a stream of states (the next state's Gaussian-SVD
+    chain runs beside the current state's sampling).  gammas: (2N, 2N)
+    float64 arrays or tensors, outs: (S, N) uint8 arrays or tensors, all in
+    the same memory; seeds / counter0s: one Philox key and first counter per
+    state.  Patterns equal those of separate build + sample calls."""
+    n = len(gammas)
+    if not (n == len(opts_list) == len(seeds) == len(counter0s) == len(outs)):
+        raise ValueError("one Opts, seed, counter0 and output per state")
+    if n == 0:
+        return
+    ptrs = [_ptr(x) for x in gammas] + [_ptr(x) for x in outs]
+    kinds = {k for _, k in ptrs}
+    if len(kinds) != 1:
+        raise ValueError("all covariances and outputs must live in the same memory")
+    for x, o in zip(gammas, outs):
+        if tuple(o.shape) != (S, x.shape[0] // 2):
+            raise ValueError("outs[k] must have shape (S, N_k)")
+    Ns = (C.c_int32 * n)(*[x.shape[0] // 2 for x in gammas])
+    gp = (C.c_void_p * n)(*[p for p, _ in ptrs[:n]])
+    op = (Opts * n)(*opts_list)
+    sd = (C.c_uint64 * n)(*[int(v) for v in seeds])
+    c0 = (C.c_uint64 * n)(*[int(v) for v in counter0s])
+    outp = (C.c_void_p * n)(*[p for p, _ in ptrs[n:]])
+    _check(lib().gbsmps_build_sample_stream(ctx, n, Ns, gp, op, int(S), sd, c0, outp, kinds.pop()))
 
 
 def gbsmps_build_from_Q(ctx, Q, opts: Opts):

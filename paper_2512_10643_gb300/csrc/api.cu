@@ -164,15 +164,22 @@ int gbsmps_amplitudes(gbsmps_mps_t m, int64_t P, const uint8_t* patterns, double
   return GBSMPS_OK;
 }
 
-int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
-                  const double* uniforms, uint8_t* out, uint8_t* flags, int mem_kind) {
+}  // extern "C"
+
+namespace gbs {
+// Sampling of a built MPS on stream s; device errors go to status.  sm_reserve
+// SMs are left free of the tensor-core GEMM's persistent CTAs (another
+// stream's single-SM chain kernel runs there).  With sync_host = 0 a host
+// output is copied asynchronously and the caller synchronises s.
+int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int sync_host,
+                int64_t S, uint64_t seed, uint64_t counter0, const double* uniforms, uint8_t* out,
+                uint8_t* flags, int mem_kind) {
   if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
   if (S < 0) return fail(GBSMPS_ERR_ARG, "S < 0");
   if (S == 0) return GBSMPS_OK;
   if (!out) return fail(GBSMPS_ERR_ARG, "out is NULL");
   if (S > (int64_t)1 << 31) return fail(GBSMPS_ERR_ARG, "S too large for one call");
   CK(cudaSetDevice(m->ctx->device));
-  cudaStream_t s = m->ctx->stream;
   const int N = m->N, d = m->d;
   // samples are processed in chunks that bound the W/Y work buffers
   const size_t per = (size_t)d * m->maxD;
@@ -230,7 +237,7 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
         CK(launch_canon_gemm(mapA, m->bmaps[site].data(), V, (long long)Spad * Kp,
                              m->bpack.as<__half>() + m->bpoff[site], (long long)Np * Kp, Kp,
                              Np, cs, Spad, cw.as<float2>(), cpart.as<float>(), use_tc,
-                             8.0 * cs * Dl * (double)d * Dr, m->ctx->d_status, s));
+                             8.0 * cs * Dl * (double)d * Dr, status, sm_reserve, s));
         CK(launch_select_canon(cs, d, Dr, m->Drp[site], cw.as<float2>(), cpart.as<float>(), Np / 128,
                                du ? du + (size_t)s0 * N : nullptr, N, site, seed,
                                counter0 + (uint64_t)s0, Vn, (long long)Spad * Kpn, Kpn,
@@ -267,8 +274,93 @@ int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
   }
   ub.release(); obuf.release(); fbuf.release(); vb.release(); wb.release(); yb.release();
   cv0.release(); cv1.release(); cw.release(); cpart.release();
-  if (mem_kind == GBSMPS_MEM_HOST) return sync_status(m->ctx);
+  if (mem_kind == GBSMPS_MEM_HOST && sync_host) return sync_status(m->ctx);
   return GBSMPS_OK;
+}
+}  // namespace gbs
+
+extern "C" {
+
+int gbsmps_sample(gbsmps_mps_t m, int64_t S, uint64_t seed, uint64_t counter0,
+                  const double* uniforms, uint8_t* out, uint8_t* flags, int mem_kind) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  return gbs::sample_impl(m, m->ctx->stream, m->ctx->d_status, 0, 1, S, seed, counter0, uniforms,
+                          out, flags, mem_kind);
+}
+
+int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
+                               const double* const* gammas, const gbsmps_opts* opts, int64_t S,
+                               const uint64_t* seeds, const uint64_t* counter0s,
+                               uint8_t* const* outs, int mem_kind) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  if (count < 0) return fail(GBSMPS_ERR_ARG, "count < 0");
+  if (count == 0) return GBSMPS_OK;
+  if (!Ns || !gammas || !opts || !seeds || !counter0s || !outs)
+    return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (mem_kind != GBSMPS_MEM_HOST && mem_kind != GBSMPS_MEM_DEVICE) return fail(GBSMPS_ERR_ARG, "mem_kind");
+  if (S < 0) return fail(GBSMPS_ERR_ARG, "S < 0");
+  size_t gmax = 0;
+  for (int k = 0; k < count; ++k) {
+    if (Ns[k] < 1 || Ns[k] > 1000000) return fail(GBSMPS_ERR_ARG, "N out of range");
+    if (!gammas[k] || (S > 0 && !outs[k])) return fail(GBSMPS_ERR_ARG, "NULL gamma or out");
+    const int rc = check_opts(&opts[k]);
+    if (rc) return rc;
+    gmax = std::max(gmax, sizeof(double) * 4 * (size_t)Ns[k] * Ns[k]);
+  }
+  CK(cudaSetDevice(c->device));
+  // sampling runs on its own stream with its own status word; the build
+  // stream waits (the gate) for the previous state's sampling after its chain
+  cudaStream_t ss = nullptr;
+  cudaEvent_t built = nullptr, sampled = nullptr;
+  CK(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
+  int rc = GBSMPS_OK;
+  DevBuf st, g;
+  gbsmps_mps* prev = nullptr;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == GBSMPS_OK) rc = fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  if (ck(cudaEventCreateWithFlags(&built, cudaEventDisableTiming)) &&
+      ck(cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming)) &&
+      ck(st.alloc(sizeof(int), c->stream)) && ck(cudaMemsetAsync(st.p, 0, sizeof(int), c->stream)) &&
+      (mem_kind == GBSMPS_MEM_DEVICE || ck(g.alloc(gmax, c->stream))) &&
+      ck(cudaStreamSynchronize(c->stream))) {
+    for (int k = 0; k < count && rc == GBSMPS_OK; ++k) {
+      const double* dg = gammas[k];
+      if (mem_kind == GBSMPS_MEM_HOST) {
+        if (!ck(cudaMemcpyAsync(g.p, gammas[k], sizeof(double) * 4 * (size_t)Ns[k] * Ns[k],
+                                cudaMemcpyHostToDevice, c->stream)))
+          break;
+        dg = g.as<double>();
+      }
+      gbsmps_mps_t M = nullptr;
+      rc = gbs::build_single(c, Ns[k], dg, &opts[k], &M, prev ? sampled : nullptr);
+      if (rc) break;
+      // the build stream has waited for the previous sampling: its frees are ordered after it
+      delete prev;
+      prev = M;
+      if (!ck(cudaEventRecord(built, c->stream)) || !ck(cudaStreamWaitEvent(ss, built, 0))) break;
+      rc = gbs::sample_impl(M, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k], counter0s[k],
+                            nullptr, outs[k], nullptr, mem_kind);
+      if (rc) break;
+      if (!ck(cudaEventRecord(sampled, ss))) break;
+    }
+  }
+  ck(cudaStreamSynchronize(ss));
+  delete prev;
+  int hst = 0;
+  if (st.p) {
+    ck(cudaMemcpyAsync(&hst, st.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+  }
+  if (hst && rc == GBSMPS_OK) rc = fail(status_to_code(hst), "device status word " + std::to_string(hst));
+  st.release();
+  g.release();
+  ck(cudaStreamSynchronize(c->stream));
+  if (sampled) cudaEventDestroy(sampled);
+  if (built) cudaEventDestroy(built);
+  cudaStreamDestroy(ss);
+  return rc;
 }
 
 int gbsmps_release(gbsmps_mps_t m) {

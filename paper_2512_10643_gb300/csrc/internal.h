@@ -275,7 +275,7 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
 cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
                               const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
                               float2* W, float* part, int use_tc, double alg_flops, int* status,
-                              cudaStream_t s);
+                              int sm_reserve, cudaStream_t s);
 cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
                           __half* Bp, long long bpl, cudaStream_t s);
 cudaError_t launch_vinit(__half* V, long long vpl, int Spad, int Kp, cudaStream_t s);

@@ -613,7 +613,7 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows) {
 cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
                               const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
                               float2* W, float* part, int use_tc, double alg_flops, int* status,
-                              cudaStream_t s) {
+                              int sm_reserve, cudaStream_t s) {
   const int ntn = Np / TBN, ntm = Mpad / TBM;
   COUNT_LAUNCH(1);
   const double bytes = (double)NPL * 2 * ((double)Mpad * Kp + (double)Np * Kp) + (double)M * Np * 4;
@@ -636,7 +636,7 @@ cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* 
     CUtensorMap a, b;
     memcpy(&a, mapA, sizeof(CUtensorMap));
     memcpy(&b, mapB, sizeof(CUtensorMap));
-    const int grid = std::min(nsm[dev].load(), ntm * ntn);
+    const int grid = std::min(std::max(1, nsm[dev].load() - std::max(0, sm_reserve)), ntm * ntn);
     canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(
         a, b, Kp / TBK, ntm, ntn, reinterpret_cast<float*>(W), Np, M, part, status);
   } else {

@@ -196,6 +196,11 @@ int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s);
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st);
 int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int finish(gbsmps_ctx* c, gbsmps_mps* M);
+// gate (may be null): the stream waits for it after the GSVD chain and the
+// bond read-back, before the stages that occupy every SM
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
-                 gbsmps_mps_t* out);
+                 gbsmps_mps_t* out, cudaEvent_t gate = nullptr);
+int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int sync_host,
+                int64_t S, uint64_t seed, uint64_t counter0, const double* uniforms, uint8_t* out,
+                uint8_t* flags, int mem_kind);
 }  // namespace gbs

@@ -421,7 +421,7 @@ int finish(gbsmps_ctx* c, gbsmps_mps* M) {
 
 // the whole pipeline for one state whose covariance is on the device
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
-                 gbsmps_mps_t* out) {
+                 gbsmps_mps_t* out, cudaEvent_t gate) {
   cudaStream_t s = c->stream;
   StageTimer tm(s);
   {
@@ -451,6 +451,7 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
   rc = sync_status(c);
   if (rc) return rc;
   finish_readback(M, rb);
+  if (gate) CK(cudaStreamWaitEvent(s, gate, 0));
   // a6 PCO build
   size_t scr_max = 0;
   rc = alloc_tensors(M, s, &scr_max);
