@@ -207,43 +207,86 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   const double2* R = m->env.as<double2>();
   const double2 one = cmk(1, 0), zero = cmk(0, 0);
   StageTimer tm(s);
-  DevBuf cv0, cv1, cw, cpart;        // mixed path: fp16 state planes, W, tile norms
+  // mixed path: per parity group the fp16 state planes (current and next
+  // bond), sample indices, W and chunk norms; group row counts per bond
+  DevBuf cv[4], csid[4], cw[2], cpart[2], ccnt;
   const char* tce = getenv("GBSMPS_TC");
   const int use_tc = !(tce && tce[0] == '0');
+  std::vector<int> hcnt;                  // group row counts, read back for the trace
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
     if (m->precision == GBSMPS_PREC_MIXED) {
-      // right-canonical tensors: one tensor-core GEMM per site, q_p = |w_p|^2
+      // right-canonical tensors: one two-group tensor-core GEMM per site,
+      // q_p = |w_p|^2 from the chunk norms, each sample appended to the group
+      // of its next parity class
       const int Spad = (int)((chunk + 127) / 128 * 128);
       int Kpmax = 64, Npmax = 128;
-      for (int i = 0; i < N; ++i) { Kpmax = std::max(Kpmax, m->Kp[i]); Npmax = std::max(Npmax, m->Np[i]); }
-      if (!cw.p) {
-        CK(cv0.alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
-        CK(cv1.alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
-        CK(cw.alloc(sizeof(float2) * (size_t)chunk * (Npmax / 2), s));
-        CK(cpart.alloc(sizeof(float) * (size_t)chunk * (Npmax / 128), s));
+      for (int i = 0; i < N; ++i)
+        for (int pi = 0; pi < 2; ++pi) {
+          Kpmax = std::max(Kpmax, m->sg[i].Kp[pi]);
+          Npmax = std::max(Npmax, m->sg[i].Np[pi]);
+        }
+      if (!ccnt.p) {
+        for (int k = 0; k < 4; ++k) {
+          CK(cv[k].alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
+          CK(csid[k].alloc(sizeof(int) * (size_t)Spad, s));
+        }
+        for (int k = 0; k < 2; ++k) {
+          CK(cw[k].alloc(sizeof(float) * (size_t)chunk * Npmax, s));
+          CK(cpart[k].alloc(sizeof(float) * (size_t)chunk * (Npmax / 32), s));
+        }
+        CK(ccnt.alloc(sizeof(int) * 2 * (size_t)(N + 1), s));
       }
-      __half* V = cv0.as<__half>();
-      __half* Vn = cv1.as<__half>();
-      CK(launch_vinit(V, (long long)Spad * m->Kp[0], Spad, m->Kp[0], s));
+      int* cnt = ccnt.as<int>();
+      CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
+      int cur[2] = {0, 1}, nxt[2] = {2, 3};
+      CK(launch_sampler_init(cv[cur[0]].as<__half>(), (long long)Spad * m->sg[0].Kp[0], Spad,
+                             m->sg[0].Kp[0], csid[cur[0]].as<int>(), cnt, cs, s));
       COUNT_LAUNCH(1);
       for (int site = 0; site < N; ++site) {
-        const int Dl = m->D[site], Dr = m->D[site + 1];
-        const int Kp = m->Kp[site], Np = m->Np[site];
-        const int Kpn = site + 1 < N ? m->Kp[site + 1] : 64;
-        unsigned char mapA[128];
-        if (canon_make_map(mapA, V, Kp, Spad))
-          return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
-        CK(launch_canon_gemm(mapA, m->bmaps[site].data(), V, (long long)Spad * Kp,
-                             m->bpack.as<__half>() + m->bpoff[site], (long long)Np * Kp, Kp,
-                             Np, cs, Spad, cw.as<float2>(), cpart.as<float>(), use_tc,
-                             8.0 * cs * Dl * (double)d * Dr, status, sm_reserve, s));
-        CK(launch_select_canon(cs, d, Dr, m->Drp[site], cw.as<float2>(), cpart.as<float>(), Np / 128,
-                               du ? du + (size_t)s0 * N : nullptr, N, site, seed,
-                               counter0 + (uint64_t)s0, Vn, (long long)Spad * Kpn, Kpn,
-                               dout + (size_t)s0 * N, N, dfl ? dfl + s0 : nullptr, 1e-5, s));
+        const gbsmps_mps::SiteGroups& G = m->sg[site];
+        unsigned char mapA[2][128];
+        TcGroup tg[2];
+        SelGroup sl[2];
+        NextGroup ng[2];
+        for (int pi = 0; pi < 2; ++pi) {
+          if (canon_make_map(mapA[pi], cv[cur[pi]].p, G.Kp[pi], Spad))
+            return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
+          tg[pi] = TcGroup{G.Kp[pi] / 64, G.Np[pi] / 128, cnt + 2 * site + pi, cs, cw[pi].as<float>(),
+                           (long long)G.Np[pi], cpart[pi].as<float>(), (long long)(G.Np[pi] / 32)};
+          sl[pi] = SelGroup{cnt + 2 * site + pi, csid[cur[pi]].as<int>(), cw[pi].as<float2>(),
+                            (long long)(G.Np[pi] / 2), cpart[pi].as<float>(),
+                            (long long)(G.Np[pi] / 32), G.w[pi], G.w[pi ^ 1]};
+          const int Kpn = site + 1 < N ? m->sg[site + 1].Kp[pi] : 64;
+          ng[pi] = NextGroup{cv[nxt[pi]].as<__half>(), (long long)Spad * Kpn, Kpn,
+                             csid[nxt[pi]].as<int>(), m->pcnt[2 * (site + 1) + pi]};
+        }
+        CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), tg[0], tg[1],
+                             cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0], cv[cur[1]].as<__half>(),
+                             (long long)Spad * G.Kp[1], m->bpack.as<__half>() + G.boff[0],
+                             (long long)G.Np[0] * G.Kp[0], m->bpack.as<__half>() + G.boff[1],
+                             (long long)G.Np[1] * G.Kp[1], use_tc, status, sm_reserve, s));
+        CK(launch_select_groups(cs, d, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1),
+                                du ? du + (size_t)s0 * N : nullptr, N, site, seed,
+                                counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
+                                dfl ? dfl + s0 : nullptr, 1e-5, s));
         COUNT_LAUNCH(1);
-        std::swap(V, Vn);
+        std::swap(cur, nxt);
+      }
+      if (g_tc_trace.on.load()) {
+        // algorithmic work of the GEMMs: 8 real flops per complex product of a
+        // sample's class-pi state with the nonzero blocks of At
+        hcnt.assign(2 * (N + 1), 0);
+        CK(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double f = 0.0;
+        for (int site = 0; site < N; ++site)
+          for (int pi = 0; pi < 2; ++pi) {
+            double cols = 0.0;
+            for (int p = 0; p < d; ++p) cols += m->pcnt[2 * (site + 1) + (pi ^ (p & 1))];
+            f += 8.0 * hcnt[2 * site + pi] * (double)m->pcnt[2 * site + pi] * cols;
+          }
+        g_tc_trace.add_work(f, 0.0);
       }
       continue;
     }
@@ -273,7 +316,11 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
     if (flags) CK(cudaMemcpyAsync(flags, dfl, (size_t)S, cudaMemcpyDeviceToHost, s));
   }
   ub.release(); obuf.release(); fbuf.release(); vb.release(); wb.release(); yb.release();
-  cv0.release(); cv1.release(); cw.release(); cpart.release();
+  for (auto& b : cv) b.release();
+  for (auto& b : csid) b.release();
+  for (auto& b : cw) b.release();
+  for (auto& b : cpart) b.release();
+  ccnt.release();
   if (mem_kind == GBSMPS_MEM_HOST && sync_host) return sync_status(m->ctx);
   return GBSMPS_OK;
 }
@@ -460,14 +507,16 @@ size_t gbsmps_estimate_bytes(int32_t N, const gbsmps_opts* o, int64_t S) {
   b += n * site + 16.0 * (n + 1) * c2;                        // tensors, environments
   b += std::min(n, 304.0) * 16.0 * (4.0 * chi + 4.0 * c2);    // PCO scratch (one wave)
   b += site;                                                  // environment step product
-  const double chip = std::ceil(chi / 64.0) * 64.0, kp = std::ceil(2.0 * chi / 64.0) * 64.0;
+  const double kp = std::ceil(2.0 * chi / 64.0) * 64.0;
   if (o->precision == GBSMPS_PREC_MIXED) {
     b += n * site + 2.0 * 16.0 * (n + 1) * c2;                // energy gauge, L, L^-1
-    b += n * 2.0 * (2.0 * d * chip) * kp * 2.0;               // packed fp16 planes
+    // two parity groups per site, each bounded by one class holding all chi states
+    const double npg = std::ceil(2.0 * d * std::ceil(chi / 16.0) * 16.0 / 128.0) * 128.0;
+    b += n * 2.0 * 2.0 * npg * kp * 2.0;                      // packed fp16 planes
     b += 2.0 * 8.0 * d * c2 + 2.0 * (64 << 20);               // transform buffers, split-K
     const double sp = std::ceil(S / 128.0) * 128.0;
-    b += 2.0 * 2.0 * sp * kp * 2.0;                           // sample state planes
-    b += S * (d * chip) * 8.0 + S * (2.0 * d * chip / 128.0) * 4.0;   // W, tile norms
+    b += 4.0 * (2.0 * sp * kp * 2.0 + 4.0 * sp);              // state planes, sample indices
+    b += 2.0 * (S * npg * 4.0 + S * (npg / 32.0) * 4.0);      // W, chunk norms
   } else {
     const double per = d * chi;
     const double chunk = std::max(1.0, std::min((double)S, 6.0 * (1 << 30) / (32.0 * per + 32.0 * chi)));

@@ -96,6 +96,9 @@ struct BondArrays {
   int* maxocc;        // [b*NEM + q] max occupation of mode q in the kept basis
   double* lam2;       // [b*NEM + q] Lambda^2 (bond b = cut after site b-1)
   double* eps;        // [b] discarded weight
+  int* pidx;          // [b*cap + j]: kept states of bond b, even total photon number
+                      // first, the E order kept within each class
+  int* pcnt;          // [2b + c]: kept states of bond b with photon-number parity c
 };
 
 // ---- opt-in kernel tracing: CUDA events around every launch of one kernel
@@ -125,6 +128,11 @@ struct KernelTrace {
     ev.push_back(b0);
     ev.push_back(e);
     flops += f; bytes += b; ++launches;
+  }
+  void add_work(double f, double b) {        // work known only after the launches ran
+    if (!on.load()) return;
+    std::lock_guard<std::mutex> lk(mu);
+    flops += f; bytes += b;
   }
   double total_ms() {
     std::lock_guard<std::mutex> lk(mu);
@@ -272,18 +280,47 @@ int env_chain_tile_configs();
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_fp16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
-cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
-                              const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
-                              float2* W, float* part, int use_tc, double alg_flops, int* status,
-                              int sm_reserve, cudaStream_t s);
-cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
-                          __half* Bp, long long bpl, cudaStream_t s);
-cudaError_t launch_vinit(__half* V, long long vpl, int Spad, int Kp, cudaStream_t s);
-cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, const float* part,
-                                int ntiles, const double* u, int ustride, int site, uint64_t seed,
-                                uint64_t counter0, __half* V, long long vpl, int Kpn,
-                                uint8_t* out, int N, uint8_t* flags, double flag_tol,
+// Parity groups.  Every PCO adds two quanta, so A^m[alpha, p, beta] = 0
+// unless n_alpha + p + n_beta is even; the environments, their Cholesky
+// factors and the canonical tensors inherit the block structure, and a
+// sampled state lies in one parity class of its bond.  The sampler keeps the
+// samples of each class in a group of its own and multiplies only the
+// nonzero blocks.  Within group pi of site m the K index runs over the class
+// pi states of bond m, and column block p over the class pi^(p&1) states of
+// bond m+1, padded to 16 complex columns (widths wself for even p, wother for
+// odd p, blocks in p order).
+struct TcGroup {          // one group of the two-group sampler GEMM
+  int nkb, ntn;           // K blocks of 64 and N tiles of 128 (real fp16 elements)
+  const int* cnt;         // rows of the group (device; nullptr: mcap)
+  int mcap;               // row capacity
+  float* W; long long ldw;       // output rows, real floats per row
+  float* part; long long ldp;    // per-row norms of 32-real-column chunks
+};
+struct SelGroup {         // one group as the selection pass reads it
+  const int* cnt; const int* sid;
+  const float2* W; long long ldw;  // complex per row
+  const float* part; long long ldp;
+  int wself, wother;
+};
+struct NextGroup {        // one class of the next bond as the selection pass writes it
+  __half* V; long long vpl; int Kp; int* sid; int D;
+};
+cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s);
+cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* mapA1,
+                              const void* mapB1, const TcGroup& g0, const TcGroup& g1,
+                              const __half* A0, long long apl0, const __half* A1, long long apl1,
+                              const __half* B0, long long bpl0, const __half* B1, long long bpl1,
+                              int use_tc, int* status, int sm_reserve, cudaStream_t s);
+cudaError_t launch_pack_group(const float2* At, int Dl, int d, int Dr, const int* lidx, int kc,
+                              const int* ridx0, int rc0, const int* ridx1, int rc1, int w0, int w1,
+                              int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s);
+cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
                                 cudaStream_t s);
+cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,
+                                 const NextGroup& n0, const NextGroup& n1, int* cnt_next,
+                                 const double* u, int ustride, int site, uint64_t seed,
+                                 uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
+                                 double flag_tol, cudaStream_t s);
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, int* status, cudaStream_t s);
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,

@@ -144,15 +144,32 @@ __device__ __forceinline__ void split2(float x, __half& h, __half& l) {
 }
 
 // ---------------------------------------------------------------- tcgen05 GEMM
-// W[row, n] (real view: row-major, ldw floats; complex pairs interleaved)
-// and part[row, tile n] = sum of W^2 over the tile's 128 real columns.
-// Tile t of the ntm x ntn grid is (t / ntn, t % ntn): consecutive tiles
-// share the A row block, so the streamed operand is read from HBM once while
-// the packed tensor (a few MB) stays in L2.
+// Two independent GEMMs (the parity groups) in one persistent launch.  For
+// group g: W_g[row, n] (real view: row-major, ldw floats; complex pairs
+// interleaved) and part_g[row, c] = sum of W_g^2 over real columns
+// 32c .. 32c + 31.  The row counts are read on the device (the previous
+// selection pass wrote them).  Tiles run over group 0, then group 1; tile t
+// of a group's ntm x ntn grid is (t / ntn, t % ntn): consecutive tiles share
+// the A row block, so the streamed operand is read from HBM once while the
+// packed tensor (a few MB) stays in L2.
+struct TileRef { int g, m0, nb; };
+__device__ __forceinline__ TileRef tile_of(int t, int T0, int ntn0, int ntn1) {
+  TileRef r;
+  r.g = t >= T0 ? 1 : 0;
+  const int tt = r.g ? t - T0 : t, ntn = r.g ? ntn1 : ntn0;
+  r.m0 = (tt / ntn) * TBM;
+  r.nb = tt % ntn;
+  return r;
+}
+__device__ __forceinline__ int group_rows(const TcGroup& g) {
+  const int m = g.cnt ? *g.cnt : g.mcap;
+  return max(0, min(m, g.mcap));
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     int nkb, int ntm, int ntn, float* __restrict__ W, long long ldw, int M,
-                     float* __restrict__ part, int* status) {
+canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
+                     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
+                     const TcGroup g0, const TcGroup g1, int* status) {
   extern __shared__ __align__(1024) uint8_t smraw[];
   const uint32_t raw = su32(smraw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -163,7 +180,9 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = su32(bars), empty0 = full0 + 8 * TSTAGES;
   const uint32_t afull0 = empty0 + 8 * TSTAGES, aempty0 = afull0 + 16, drain = aempty0 + 16;
-  const int ntiles = ntm * ntn;
+  const int M0 = group_rows(g0), M1 = group_rows(g1);
+  const int T0 = ((M0 + TBM - 1) / TBM) * g0.ntn;
+  const int ntiles = T0 + ((M1 + TBM - 1) / TBM) * g1.ntn;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TSTAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
@@ -191,7 +210,10 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = (t / ntn) * TBM, n0 = (t % ntn) * TBN;
+        const TileRef tr = tile_of(t, T0, g0.ntn, g1.ntn);
+        const int m0 = tr.m0, n0 = tr.nb * TBN, nkb = tr.g ? g1.nkb : g0.nkb;
+        const CUtensorMap* mA = tr.g ? &tmA1 : &tmA0;
+        const CUtensorMap* mB = tr.g ? &tmB1 : &tmB0;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int st = g % TSTAGES, r = g / TSTAGES;
           if (r > 0 && !mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
@@ -201,8 +223,8 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
           }
           mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
           const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
-          tma_load_3d(sA, &tmA, full0 + 8 * st, kb * TBK, m0, 0);    // box: both planes
-          tma_load_3d(sB, &tmB, full0 + 8 * st, kb * TBK, n0, 0);
+          tma_load_3d(sA, mA, full0 + 8 * st, kb * TBK, m0, 0);    // box: both planes
+          tma_load_3d(sB, mB, full0 + 8 * st, kb * TBK, n0, 0);
         }
       }
       // the last copy issued into each stage has landed before the CTA exits
@@ -226,6 +248,7 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         }
         tc_fence_after();
         const uint32_t dhh = tmem + (uint32_t)(buf * 2 * TBN), dx = dhh + TBN;
+        const int nkb = tile_of(t, T0, g0.ntn, g1.ntn).g ? g1.nkb : g0.nkb;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int st = g % TSTAGES, r = g / TSTAGES;
           if (!mbar_wait(full0 + 8 * st, r & 1)) {
@@ -249,8 +272,10 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         if (!ok) break;
         umma_commit(afull0 + 8 * buf);
       }
-      umma_commit(drain);                             // every MMA issued here has completed
-      if (!mbar_wait(drain, 0)) set_status(status, ST_TIMEOUT);
+      if (g > 0) {                                    // every MMA issued here has completed
+        umma_commit(drain);
+        if (!mbar_wait(drain, 0)) set_status(status, ST_TIMEOUT);
+      }
     }
   } else {                                            // epilogue warps
     const int q = warp & 3;                           // TMEM lanes 32q .. 32q + 31
@@ -264,11 +289,16 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         break;
       }
       tc_fence_after();
-      const int m0 = (t / ntn) * TBM, nb = t % ntn, n0 = nb * TBN;
-      const int rbase = m0 + q * 32;
-      float nrm = 0.f;
+      const TileRef tr = tile_of(t, T0, g0.ntn, g1.ntn);
+      const TcGroup& gg = tr.g ? g1 : g0;
+      const int M = tr.g ? M1 : M0;
+      float* __restrict__ W = gg.W;
+      const long long ldw = gg.ldw;
+      const int nb = tr.nb, n0 = nb * TBN;
+      const int rbase = tr.m0 + q * 32;
 #pragma unroll 1
       for (int c0 = 0; c0 < TBN; c0 += 32) {
+        float nrm = 0.f;
         uint32_t h[32], x[32];
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * TBN + c0);
         tmem_ld32(ta, h);
@@ -293,11 +323,11 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + c4 * 4) = val;
         }
         __syncwarp();
+        if (rbase + lane < M) gg.part[(long long)(rbase + lane) * gg.ldp + (n0 + c0) / 32] = nrm;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(aempty0 + 8 * buf);  // buffer free for tile i + 2
-      if (rbase + lane < M) part[(long long)(rbase + lane) * ntn + nb] = nrm;
     }
   }
   __syncwarp();
@@ -312,10 +342,12 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
 }
 
 // SIMT reference on the same packed planes (cross-check of the tcgen05 path):
-// the same three products, FP32 accumulation in k order
+// the same three products, FP32 accumulation in k order; rows beyond the
+// group's device-side count are skipped
 __global__ void canon_gemm_ref_kernel(const __half* __restrict__ Ap, long long apl, int Kp,
                                       const __half* __restrict__ Bp, long long bpl, int Np,
-                                      float2* __restrict__ W, long long ldw, int M) {
+                                      float2* __restrict__ W, long long ldw, const TcGroup g) {
+  const int M = group_rows(g);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * (Np / 2);
        idx += (long long)gridDim.x * blockDim.x) {
     const int row = idx / (Np / 2), nc = idx % (Np / 2);
@@ -336,94 +368,140 @@ __global__ void canon_gemm_ref_kernel(const __half* __restrict__ Ap, long long a
   }
 }
 
-__global__ void canon_part_ref_kernel(const float2* __restrict__ W, long long ldw, int M,
-                                      float* __restrict__ part, int ntiles) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * ntiles;
+__global__ void canon_part_ref_kernel(const float2* __restrict__ W, long long ldw, int nchunks,
+                                      const TcGroup g) {
+  const int M = group_rows(g);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * nchunks;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int row = idx / ntiles, t = idx % ntiles;
+    const int row = idx / nchunks, c = idx % nchunks;
     float s = 0.f;
-    for (int j = 0; j < 64; ++j) {
-      float2 v = W[(long long)row * ldw + t * 64 + j];
+    for (int j = 0; j < 16; ++j) {
+      float2 v = W[(long long)row * ldw + c * 16 + j];
       s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
     }
-    part[idx] = s;
+    g.part[(long long)row * g.ldp + c] = s;
+  }
+}
+
+// ---------------------------------------------------------------- parity classes
+// one warp per bond: the kept states by photon-number parity (sum of the
+// occupations), even class first, each class in the kept (E) order
+__global__ void parity_classes_kernel(BondArrays ba, int nb) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  const bool edge = b == 0 || b == nb - 1;       // vacuum-only end bonds
+  const int D = edge ? 1 : ba.D[b];
+  const int ne = edge ? 0 : ba.ne[b];
+  const uint8_t* occ = ba.occ + (size_t)b * ba.cap * NEM;
+  int* out = ba.pidx + (size_t)b * ba.cap;
+  int k = 0;
+  for (int c = 0; c < 2; ++c) {
+    const int k0 = k;
+    for (int i0 = 0; i0 < D; i0 += 32) {
+      const int i = i0 + lane;
+      bool hit = false;
+      if (i < D) {
+        int n = 0;
+        for (int q = 0; q < ne; ++q) n += occ[(size_t)i * NEM + q];
+        hit = (n & 1) == c;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) out[k + __popc(m & ((1u << lane) - 1u))] = i;
+      k += __popc(m);
+    }
+    if (lane == 0) ba.pcnt[2 * b + c] = k - k0;
   }
 }
 
 // ---------------------------------------------------------------- packing
-// B planes of one site: row n_r = 2 (p Drp + b) + c, column k_r = 2 a + e;
-// [[Re, -Im], [Im, Re]] blocks of At[a, p, b] (zero in the padding)
-__global__ void pack_b_kernel(const float2* __restrict__ At, int Dl, int d, int Dr, int Drp, int Kp,
-                              __half* __restrict__ Bp, long long bpl) {
-  const long long ncx = (long long)d * Drp;                 // complex columns
+// B planes of group pi of one site: complex column nc = (p, j) in the group's
+// block layout, real rows 2 nc + c; K index a (real 2a + e) = class pi state
+// lidx[a] of the left bond; [[Re, -Im], [Im, Re]] blocks of At[alpha, p,
+// beta] with beta the j-th state of class pi^(p&1) of the right bond (ridx0
+// for even p, ridx1 for odd p); zero in the padding
+__global__ void pack_group_kernel(const float2* __restrict__ At, int Dl, int d, int Dr,
+                                  const int* __restrict__ lidx, int kc, const int* __restrict__ ridx0,
+                                  int rc0, const int* __restrict__ ridx1, int rc1, int w0, int w1,
+                                  int Kp, int Np, __half* __restrict__ Bp, long long bpl) {
+  const long long ncx = Np / 2;
   const long long total = ncx * (Kp / 2);
+  const int P2 = w0 + w1;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long nc = idx / (Kp / 2);
-    const int a = idx % (Kp / 2);
-    const int p = nc / Drp, b = nc % Drp;
+    const int nc = (int)(idx / (Kp / 2));
+    const int a = (int)(idx % (Kp / 2));
+    const int pp = nc / P2, rem = nc - pp * P2;
+    const bool odd = rem >= w0;
+    const int p = 2 * pp + (odd ? 1 : 0), j = odd ? rem - w0 : rem;
     float2 v = make_float2(0.f, 0.f);
-    if (a < Dl && b < Dr) v = At[((long long)a * d + p) * Dr + b];
+    if (p < d && a < kc && j < (odd ? rc1 : rc0)) {
+      const int al = lidx[a], be = odd ? ridx1[j] : ridx0[j];
+      if (al >= 0 && al < Dl && be >= 0 && be < Dr) v = At[((long long)al * d + p) * Dr + be];
+    }
     __half rr[NPL], ii[NPL];
     split2(v.x, rr[0], rr[1]);
     split2(v.y, ii[0], ii[1]);
-    for (int s = 0; s < NPL; ++s) {
-      __half* row0 = Bp + s * bpl + (2 * nc) * Kp + 2 * a;
+    for (int sp = 0; sp < NPL; ++sp) {
+      __half* row0 = Bp + sp * bpl + (2LL * nc) * Kp + 2 * a;
       __half* row1 = row0 + Kp;
       __half2 x0, x1;
-      x0.x = rr[s]; x0.y = __hneg(ii[s]);
-      x1.x = ii[s]; x1.y = rr[s];
+      x0.x = rr[sp]; x0.y = __hneg(ii[sp]);
+      x1.x = ii[sp]; x1.y = rr[sp];
       *reinterpret_cast<__half2*>(row0) = x0;
       *reinterpret_cast<__half2*>(row1) = x1;
     }
   }
 }
 
-// first site: vt = [1] (D_0 = 1) for every sample, zero padding
-__global__ void vinit_kernel(__half* V, long long vpl, int Spad, int Kp) {
+// first site: every sample in group 0 (D_0 = 1, the vacuum) with vt = [1]
+__global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt,
+                                    int S) {
   const long long total = (long long)Spad * Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int k = idx % Kp;
-    for (int s = 0; s < NPL; ++s)
-      V[s * vpl + idx] = __float2half_rn((s == 0 && k == 0) ? 1.f : 0.f);
+    for (int sp = 0; sp < NPL; ++sp)
+      V[sp * vpl + idx] = __float2half_rn((sp == 0 && k == 0) ? 1.f : 0.f);
+    if (k == 0 && idx / Kp < S) sid[idx / Kp] = (int)(idx / Kp);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) { cnt[0] = S; cnt[1] = 0; }
 }
 
-// one warp per sample: q_p from the tile norms (fixed order), choose p*,
-// write vt' = w_{p*} / sqrt(q_{p*}) as fp16 planes for the next site
-__global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2* __restrict__ W,
-                                    const float* __restrict__ part, int ntiles,
-                                    const double* __restrict__ u, int ustride, int site,
-                                    uint64_t seed, uint64_t counter0, __half* __restrict__ V,
-                                    long long vpl, int Kpn, uint8_t* __restrict__ out, int N,
-                                    uint8_t* flags, double flag_tol);
-
-}  // namespace
-
-namespace {
-__global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2* __restrict__ W,
-                                    const float* __restrict__ part, int ntiles,
-                                    const double* __restrict__ u, int ustride, int site,
-                                    uint64_t seed, uint64_t counter0, __half* __restrict__ V,
-                                    long long vpl, int Kpn, uint8_t* __restrict__ out, int N,
-                                    uint8_t* flags, double flag_tol) {
+// one warp per (group, row): q_p from the chunk norms (fixed order), choose
+// p*, append vt' = w_{p*} / sqrt(q_{p*}) as fp16 planes to the group of its
+// class at the next bond (class pi ^ (p* & 1)).  The row order inside a
+// group depends on the order of the appends; every row carries its sample
+// index, and no arithmetic depends on the row.
+__global__ void select_groups_kernel(int Scap, int d, const SelGroup g0, const SelGroup g1,
+                                     const NextGroup n0, const NextGroup n1, int* cnt_next,
+                                     const double* __restrict__ u, int ustride, int site,
+                                     uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out,
+                                     int N, uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
-  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (s >= S) return;
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (w >= 2LL * Scap) return;
+  const int grp = w >= Scap ? 1 : 0;
+  const int r = (int)(w - (long long)grp * Scap);
+  const SelGroup& g = grp ? g1 : g0;
+  if (r >= min(*g.cnt, Scap)) return;
+  const int s = g.sid[r];
+  const float* ps = g.part + (long long)r * g.ldp;
+  const int P2 = g.wself + g.wother;
   // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
   // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway.
   // Lane j of a 32-wide chunk owns q_{c0 + j}; an inclusive warp scan gives
   // the CDF; Z is the last CDF value, so the scan and Z agree exactly.
-  const int tpp = Drp / 64;
-  const float* ps = part + s * ntiles;
+  auto qp = [&](int p) {
+    float q = 0.f;
+    if (p < d) {
+      const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
+      const int nch = ((p & 1) ? g.wother : g.wself) / 16;
+      for (int t = 0; t < nch; ++t) q += ps[c0 + t];
+    }
+    return q;
+  };
   float Z = 0.f;
   for (int c0 = 0; c0 < d; c0 += 32) {
-    const int p = c0 + lane;
-    float q = 0.f;
-    if (p < d)
-      for (int t = 0; t < tpp; ++t) q += ps[p * tpp + t];
-    float C = q;
+    float C = qp(c0 + lane);
     for (int o = 1; o < 32; o <<= 1) {
       const float y = __shfl_up_sync(0xffffffffu, C, o);
       if (lane >= o) C += y;
@@ -438,9 +516,7 @@ __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2*
   bool flag = false;
   for (int c0 = 0; c0 < d; c0 += 32) {
     const int p = c0 + lane;
-    float q = 0.f;
-    if (p < d)
-      for (int t = 0; t < tpp; ++t) q += ps[p * tpp + t];
+    const float q = qp(p);
     float C = q;
     for (int o = 1; o < 32; o <<= 1) {
       const float y = __shfl_up_sync(0xffffffffu, C, o);
@@ -461,23 +537,30 @@ __global__ void select_canon_kernel(int S, int d, int Dr, int Drp, const float2*
   }
   if (pstar < 0) {
     pstar = plast;
-    qsel = 0.f;
-    for (int t = 0; t < tpp; ++t) qsel += ps[pstar * tpp + t];
+    qsel = qp(pstar);
   }
   const float inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
-  const float2* w = W + s * (long long)d * Drp + (long long)pstar * Drp;
-  for (int b = lane; b < Kpn / 2; b += 32) {
-    float2 v = b < Dr ? w[b] : make_float2(0.f, 0.f);
+  const int np = grp ^ (pstar & 1);
+  const NextGroup& ng = np ? n1 : n0;
+  int pos = 0;
+  if (lane == 0) pos = atomicAdd(cnt_next + np, 1);
+  pos = __shfl_sync(0xffffffffu, pos, 0);
+  if (pos >= Scap) return;                      // cannot happen: one row per sample
+  const float2* wr = g.W + (long long)r * g.ldw + (long long)(pstar >> 1) * P2 +
+                     ((pstar & 1) ? g.wself : 0);
+  for (int b = lane; b < ng.Kp / 2; b += 32) {
+    const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
     __half rr[NPL], ii[NPL];
     split2(v.x * inv, rr[0], rr[1]);
     split2(v.y * inv, ii[0], ii[1]);
     for (int pl = 0; pl < NPL; ++pl) {
       __half2 x;
       x.x = rr[pl]; x.y = ii[pl];
-      *reinterpret_cast<__half2*>(V + pl * vpl + s * Kpn + 2 * b) = x;
+      *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)pos * ng.Kp + 2 * b) = x;
     }
   }
   if (lane == 0) {
+    ng.sid[pos] = s;
     out[(size_t)s * N + site] = (uint8_t)pstar;
     if (flags && flag) flags[s] = 1;
   }
@@ -610,13 +693,15 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows) {
   return r == CUDA_SUCCESS ? 0 : 3;
 }
 
-cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* Ap, long long apl,
-                              const __half* Bp, long long bpl, int Kp, int Np, int M, int Mpad,
-                              float2* W, float* part, int use_tc, double alg_flops, int* status,
-                              int sm_reserve, cudaStream_t s) {
-  const int ntn = Np / TBN, ntm = Mpad / TBM;
+cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* mapA1,
+                              const void* mapB1, const TcGroup& g0, const TcGroup& g1,
+                              const __half* A0, long long apl0, const __half* A1, long long apl1,
+                              const __half* B0, long long bpl0, const __half* B1, long long bpl1,
+                              int use_tc, int* status, int sm_reserve, cudaStream_t s) {
   COUNT_LAUNCH(1);
-  const double bytes = (double)NPL * 2 * ((double)Mpad * Kp + (double)Np * Kp) + (double)M * Np * 4;
+  // the row counts live on the device: the launch is sized for the capacity
+  // and the kernel's tiles stop at the counts (the trace adds the
+  // algorithmic work once the counts are known)
   cudaEvent_t tr0 = g_tc_trace.begin(s);
   if (use_tc) {
     static std::atomic<int> nsm[64];
@@ -633,49 +718,70 @@ cudaError_t launch_canon_gemm(const void* mapA, const void* mapB, const __half* 
       if (e) return e;
       nsm[dev].store(n);
     }
-    CUtensorMap a, b;
-    memcpy(&a, mapA, sizeof(CUtensorMap));
-    memcpy(&b, mapB, sizeof(CUtensorMap));
-    const int grid = std::min(std::max(1, nsm[dev].load() - std::max(0, sm_reserve)), ntm * ntn);
-    canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(
-        a, b, Kp / TBK, ntm, ntn, reinterpret_cast<float*>(W), Np, M, part, status);
+    CUtensorMap a0, b0, a1, b1;
+    memcpy(&a0, mapA0, sizeof(CUtensorMap));
+    memcpy(&b0, mapB0, sizeof(CUtensorMap));
+    memcpy(&a1, mapA1, sizeof(CUtensorMap));
+    memcpy(&b1, mapB1, sizeof(CUtensorMap));
+    const long long cap = ((long long)(g0.mcap + TBM - 1) / TBM) * g0.ntn +
+                          ((long long)(g1.mcap + TBM - 1) / TBM) * g1.ntn;
+    const int grid = (int)std::max<long long>(
+        1, std::min<long long>(std::max(1, nsm[dev].load() - std::max(0, sm_reserve)), cap));
+    canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(a0, b0, a1, b1, g0, g1, status);
   } else {
-    long long n = (long long)M * (Np / 2);
-    int blocks = (int)std::min<long long>((n + 255) / 256, 16384);
-    canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(Ap, apl, Kp, Bp, bpl, Np, W, Np / 2, M);
-    long long n2 = (long long)M * ntn;
-    int b2 = (int)std::min<long long>((n2 + 255) / 256, 8192);
-    canon_part_ref_kernel<<<b2, 256, 0, s>>>(W, Np / 2, M, part, ntn);
-    COUNT_LAUNCH(1);
+    for (int gi = 0; gi < 2; ++gi) {
+      const TcGroup& g = gi ? g1 : g0;
+      const int Kp = g.nkb * TBK, Np = g.ntn * TBN;
+      long long n = (long long)g.mcap * (Np / 2);
+      int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 16384));
+      canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(gi ? A1 : A0, gi ? apl1 : apl0, Kp, gi ? B1 : B0,
+                                                    gi ? bpl1 : bpl0, Np,
+                                                    reinterpret_cast<float2*>(g.W), g.ldw / 2, g);
+      long long n2 = (long long)g.mcap * (Np / 32);
+      int b2 = (int)std::max<long long>(1, std::min<long long>((n2 + 255) / 256, 8192));
+      canon_part_ref_kernel<<<b2, 256, 0, s>>>(reinterpret_cast<const float2*>(g.W), g.ldw / 2,
+                                               Np / 32, g);
+      COUNT_LAUNCH(gi ? 2 : 1);
+    }
   }
-  g_tc_trace.end(tr0, s, alg_flops, bytes);
+  g_tc_trace.end(tr0, s, 0.0, 0.0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_b(const float2* At, int Dl, int d, int Dr, int Drp, int Kp,
-                          __half* Bp, long long bpl, cudaStream_t s) {
-  long long total = (long long)d * Drp * (Kp / 2);
-  int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
-  pack_b_kernel<<<blocks, 256, 0, s>>>(At, Dl, d, Dr, Drp, Kp, Bp, bpl);
+cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  parity_classes_kernel<<<nb, 32, 0, s>>>(ba, nb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vinit(__half* V, long long vpl, int Spad, int Kp, cudaStream_t s) {
-  long long total = (long long)Spad * Kp;
-  int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
-  vinit_kernel<<<blocks, 256, 0, s>>>(V, vpl, Spad, Kp);
+cudaError_t launch_pack_group(const float2* At, int Dl, int d, int Dr, const int* lidx, int kc,
+                              const int* ridx0, int rc0, const int* ridx1, int rc1, int w0, int w1,
+                              int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s) {
+  if (w0 + w1 <= 0) return cudaErrorInvalidValue;
+  long long total = (long long)(Np / 2) * (Kp / 2);
+  int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8192));
+  pack_group_kernel<<<blocks, 256, 0, s>>>(At, Dl, d, Dr, lidx, kc, ridx0, rc0, ridx1, rc1, w0, w1,
+                                           Kp, Np, Bp, bpl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_select_canon(int S, int d, int Dr, int Drp, const float2* W, const float* part,
-                                int ntiles, const double* u, int ustride, int site, uint64_t seed,
-                                uint64_t counter0, __half* V, long long vpl, int Kpn,
-                                uint8_t* out, int N, uint8_t* flags, double flag_tol,
+cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
                                 cudaStream_t s) {
-  long long threads = (long long)S * 32;
+  long long total = (long long)Spad * Kp;
+  int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8192));
+  sampler_init_kernel<<<blocks, 256, 0, s>>>(V, vpl, Spad, Kp, sid, cnt, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,
+                                 const NextGroup& n0, const NextGroup& n1, int* cnt_next,
+                                 const double* u, int ustride, int site, uint64_t seed,
+                                 uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
+                                 double flag_tol, cudaStream_t s) {
+  long long threads = 2LL * Scap * 32;
   int blocks = (int)((threads + 255) / 256);
-  select_canon_kernel<<<blocks, 256, 0, s>>>(S, d, Dr, Drp, W, part, ntiles, u, ustride, site, seed,
-                                             counter0, V, vpl, Kpn, out, N, flags, flag_tol);
+  select_groups_kernel<<<blocks, 256, 0, s>>>(Scap, d, g0, g1, n0, n1, cnt_next, u, ustride, site,
+                                              seed, counter0, out, N, flags, flag_tol);
   return cudaGetLastError();
 }
 

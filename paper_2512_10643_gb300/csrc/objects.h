@@ -126,9 +126,15 @@ struct gbsmps_mps {
   // mixed path, right-canonical sampler: Cholesky factors of the environments,
   // their inverses, and every site's canonical tensor as fp16 planes + TMA map
   DevBuf eoff_dev, lchol, linv, bpack;
-  std::vector<int> Drp, Kp, Np;
-  std::vector<long long> bpoff;
-  std::vector<std::array<unsigned char, 128>> bmaps;
+  std::vector<int> pcnt;          // [2b + c]: kept states of bond b with parity c
+  struct SiteGroups {             // the two parity groups of one site's sampler GEMM
+    int Kp[2], Np[2];             // group pi: K (real, multiple of 64), N (real, of 128)
+    int w[2];                     // column-block width (complex, multiple of 16) of the
+                                  // class c states of the right bond
+    long long boff[2];            // group pi's packed planes in bpack (halves)
+    std::array<unsigned char, 128> map[2];
+  };
+  std::vector<SiteGroups> sg;
   BondArrays ba{};
   double* lam2 = nullptr;
   double2* Qm = nullptr;
@@ -171,7 +177,7 @@ struct Front {                  // per-state device scratch of the GSVD stage
   double* work = nullptr;
 };
 struct Readback {               // host copies of the bond sizes and scale factors
-  std::vector<int> D, ne;
+  std::vector<int> D, ne, pcnt;
   std::vector<double> eps, cm;
 };
 int alloc_front(gbsmps_mps* M, gbsmps_ctx* c, int N, const gbsmps_opts* o, Front* f);

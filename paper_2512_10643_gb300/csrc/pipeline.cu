@@ -39,6 +39,8 @@ int alloc_front(gbsmps_mps* M, gbsmps_ctx* c, int N, const gbsmps_opts* o, Front
   size_t o_mo = take(sizeof(int) * (size_t)nb * NEM);
   size_t o_l2 = take(sizeof(double) * (size_t)nb * NEM);
   size_t o_eps = take(sizeof(double) * nb);
+  size_t o_pidx = take(sizeof(int) * (size_t)nb * cap);
+  size_t o_pcnt = take(sizeof(int) * 2 * (size_t)nb);
   CK(M->bonds.alloc(off, s));
   char* b0 = M->bonds.as<char>();
   BondArrays& ba = M->ba;
@@ -51,6 +53,8 @@ int alloc_front(gbsmps_mps* M, gbsmps_ctx* c, int N, const gbsmps_opts* o, Front
   ba.maxocc = reinterpret_cast<int*>(b0 + o_mo);
   ba.lam2 = reinterpret_cast<double*>(b0 + o_l2);
   ba.eps = reinterpret_cast<double*>(b0 + o_eps);
+  ba.pidx = reinterpret_cast<int*>(b0 + o_pidx);
+  ba.pcnt = reinterpret_cast<int*>(b0 + o_pcnt);
   M->lam2 = ba.lam2;
   CK(cudaMemsetAsync(b0, 0, off, s));
   CK(cudaMemsetAsync(M->Qm, 0, sizeof(double2) * (size_t)N * QS * QS, s));
@@ -74,7 +78,8 @@ int launch_bases(gbsmps_ctx* c, gbsmps_mps* M, const gbsmps_opts* o) {
   const int nb = M->N + 1;
   CK(launch_basis(M->ba, nb, o->chi_max, o->eps_trunc, c->d_status, s));
   CK(launch_maps(M->ba, nb, c->d_status, s));
-  COUNT_LAUNCH(2);
+  CK(launch_parity_classes(M->ba, nb, s));
+  COUNT_LAUNCH(3);
   return GBSMPS_OK;
 }
 
@@ -84,7 +89,9 @@ int enqueue_readback(gbsmps_mps* M, Readback* r, cudaStream_t s) {
   r->ne.assign(nb, 0);
   r->eps.assign(nb, 0.0);
   r->cm.assign(N, 0.0);
+  r->pcnt.assign(2 * nb, 0);
   CK(cudaMemcpyAsync(r->D.data(), M->ba.D, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r->pcnt.data(), M->ba.pcnt, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r->ne.data(), M->ba.ne, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r->eps.data(), M->ba.eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r->cm.data(), M->cm, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -95,6 +102,7 @@ void finish_readback(gbsmps_mps* M, const Readback& r) {
   const int N = M->N;
   M->D = r.D;
   M->ne = r.ne;
+  M->pcnt = r.pcnt;
   M->eps.assign(r.eps.begin() + 1, r.eps.end() - 1);
   M->D[0] = 1; M->D[N] = 1;
 }
@@ -284,15 +292,26 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
     CK(cudaMemcpyAsync(M->linv.as<double2>() + M->eoff[b], &one, sizeof(double2),
                        cudaMemcpyHostToDevice, s));
   }
-  M->Drp.resize(N); M->Kp.resize(N); M->Np.resize(N); M->bpoff.resize(N); M->bmaps.resize(N);
+  // the sampler's two parity groups per site: group pi multiplies the class
+  // pi rows of the left bond into column blocks p of the class pi^(p&1)
+  // states of the right bond
+  if ((int)M->pcnt.size() != 2 * (N + 1)) return fail(GBSMPS_ERR_CUDA, "parity classes missing");
+  for (int b = 0; b <= N; ++b)
+    if (M->pcnt[2 * b] + M->pcnt[2 * b + 1] != M->D[b] || M->pcnt[2 * b] < 0 || M->pcnt[2 * b + 1] < 0)
+      return fail(GBSMPS_ERR_CUDA, "parity class sizes do not add up to the bond dimension");
+  M->sg.resize(N);
   long long btot = 0;
   size_t xmax = 0;
   for (int m = 0; m < N; ++m) {
-    M->Drp[m] = (M->D[m + 1] + 63) / 64 * 64;
-    M->Kp[m] = (2 * M->D[m] + 63) / 64 * 64;
-    M->Np[m] = 2 * d * M->Drp[m];
-    M->bpoff[m] = btot;
-    btot += 2LL * M->Np[m] * M->Kp[m];
+    gbsmps_mps::SiteGroups& G = M->sg[m];
+    for (int c = 0; c < 2; ++c) G.w[c] = (M->pcnt[2 * (m + 1) + c] + 15) / 16 * 16;
+    for (int pi = 0; pi < 2; ++pi) {
+      G.Kp[pi] = std::max(64, (2 * M->pcnt[2 * m + pi] + 63) / 64 * 64);
+      const long long ncx = (long long)((d + 1) / 2) * G.w[pi] + (long long)(d / 2) * G.w[pi ^ 1];
+      G.Np[pi] = (int)std::max<long long>(128, (2 * ncx + 127) / 128 * 128);
+      G.boff[pi] = btot;
+      btot += 2LL * G.Np[pi] * G.Kp[pi];
+    }
     xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
   }
   CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
@@ -316,6 +335,28 @@ int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cuda
   return GBSMPS_OK;
 }
 
+// pack site m's canonical tensor At (E order, Dl x d x Dr) as the planes of
+// both parity groups, with their TMA maps
+int pack_site_groups(gbsmps_mps* M, const float2* At, int m, cudaStream_t s) {
+  const int d = M->d, Dl = M->D[m], Dr = M->D[m + 1], cap = M->ba.cap;
+  const int* pl = M->ba.pidx + (size_t)m * cap;
+  const int* pr = M->ba.pidx + (size_t)(m + 1) * cap;
+  const int kl[2] = {M->pcnt[2 * m], M->pcnt[2 * m + 1]};
+  const int kr[2] = {M->pcnt[2 * (m + 1)], M->pcnt[2 * (m + 1) + 1]};
+  gbsmps_mps::SiteGroups& G = M->sg[m];
+  for (int pi = 0; pi < 2; ++pi) {
+    __half* Bp = M->bpack.as<__half>() + G.boff[pi];
+    const int c0 = pi, c1 = pi ^ 1;                 // right-bond class of even / odd p
+    CK(launch_pack_group(At, Dl, d, Dr, pl + (pi ? kl[0] : 0), kl[pi], pr + (c0 ? kr[0] : 0), kr[c0],
+                         pr + (c1 ? kr[0] : 0), kr[c1], G.w[c0], G.w[c1], G.Kp[pi], G.Np[pi], Bp,
+                         (long long)G.Np[pi] * G.Kp[pi], s));
+    COUNT_LAUNCH(1);
+    if (canon_make_map(G.map[pi].data(), Bp, G.Kp[pi], G.Np[pi]))
+      return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+  }
+  return GBSMPS_OK;
+}
+
 int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
   const int d = M->d, Dl = M->D[m], Dr = M->D[m + 1];
   const double2* Ah = M->tens_mixed.as<double2>();
@@ -330,12 +371,7 @@ int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
                         0, At, d * Dr, 0, 1, s));
     src = At;
   }
-  __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
-  CK(launch_pack_b(src, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp, (long long)M->Np[m] * M->Kp[m], s));
-  COUNT_LAUNCH(1);
-  if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
-    return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
-  return GBSMPS_OK;
+  return pack_site_groups(M, src, m, s);
 }
 
 void canon_report(gbsmps_mps* M, CanonWork* w, StageTimer& tm, cudaStream_t s) {
@@ -396,13 +432,8 @@ int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
     CK(launch_zgemm_f32(Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m0], 1, Dl, sEl, Tg.p, 0,
                         d * Dr, sT, Ag.as<float2>(), d * Dr, sT, cnt, st));
     for (int k = 0; k < cnt; ++k) {
-      const int m = m0 + k;
-      __half* Bp = M->bpack.as<__half>() + M->bpoff[m];
-      CK(launch_pack_b(Ag.as<float2>() + (size_t)k * el, Dl, d, Dr, M->Drp[m], M->Kp[m], Bp,
-                       (long long)M->Np[m] * M->Kp[m], st));
-      COUNT_LAUNCH(1);
-      if (canon_make_map(M->bmaps[m].data(), Bp, M->Kp[m], M->Np[m]))
-        return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+      const int rc = pack_site_groups(M, Ag.as<float2>() + (size_t)k * el, m0 + k, st);
+      if (rc) return rc;
     }
     m0 += cnt;
   }
