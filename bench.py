@@ -32,10 +32,9 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# DRAM bytes per launch of the dominant kernel at 100,000 samples: the ncu
-# capture of the same kernel at 20,000 samples (dram read + write = 234.8 MB,
-# profiles/canon_gemm_tc_n144_d6_chi256.md) scaled by the samples processed
-TRAFFIC_BYTES_PER_LAUNCH = 234.8e6 * 5
+# DRAM bytes per launch of the dominant kernel at 100,000 samples from an ncu
+# capture of the current kernel (None until one is taken)
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -240,7 +239,8 @@ def run_gpu(args, rank, local, ws, dist):
     ach_tflops = tr["flops"] / (tr["ms"] / 1e3) / 1e12 if tr["ms"] > 0 else 0.0
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     n_launch = max(tr["launches"], 1)
-    roof = {"kernel": "canon_gemm_tc_kernel (persistent tcgen05 + TMA split-FP16 complex GEMM, "
+    roof = {"kernel": "canon_gemm_tc_kernel (persistent tcgen05 + TMA split-FP16 complex GEMM over "
+                      "both photon-parity groups, "
                       "one launch per site: W = Vt At^m over 100k samples)",
             "bound": "tensor", "achieved": round(ach_tflops, 3), "peak": peak,
             "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json x 1 "
@@ -249,7 +249,9 @@ def run_gpu(args, rank, local, ws, dist):
             "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None or S != 100_000
                         else TRAFFIC_BYTES_PER_LAUNCH),
             "algorithmic_flops_per_launch": tr["flops"] / n_launch,
-            "algorithmic_flops_def": "8 S D_{m-1} d D_m real flops per site (complex MACs x 8)",
+            "algorithmic_flops_def": ("8 real flops per complex product of the nonzero parity blocks: "
+                                      "sum over samples s of 8 D_{m-1,c_s} sum_p D_{m,c_s^(p&1)} per "
+                                      "site (about a quarter of the dense 8 S D_{m-1} d D_m)"),
             "avg_launch_ms": tr["ms"] / n_launch,
             "launches_per_step": tr["launches"],
             "share_of_step": round(tr["ms"] / (total_ms / args.steps), 4),
