@@ -128,7 +128,8 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       for (int m = 0; m < M->N; ++m) {
         gt[M->d].push_back(GaugeTask{M->tensors.as<double2>() + M->toff[m], M->D[m], M->D[m + 1],
                                      M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
-                                     M->tens_mixed.as<double2>() + M->toff[m]});
+                                     M->tens_mixed.as<double2>() + M->toff[m],
+                                     gbs::parity_site(M, m)});
         gmax[M->d] = std::max(gmax[M->d], M->D[m] * M->d * M->D[m + 1]);
       }
     }
@@ -162,9 +163,9 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
       const long long* toff_d = offs[k].as<long long>();
       ej[k] = EnvJob{N, M->d, M->ba.D, toff_d, toff_d + N, M->tens_mixed.as<double2>(), R,
-                     xs[k].as<double2>()};
+                     xs[k].as<double2>(), M->ba.pcnt};
       nj[k] = NormJob{N, M->d, M->ba.D, toff_d, M->tensors.as<double2>(), R,
-                      M->tens_mixed.as<double2>(), M->ba.E + M->ba.cap};
+                      M->tens_mixed.as<double2>(), M->ba.E + M->ba.cap, gbs::parity_site(M, 0)};
       maxN = std::max(maxN, N);
       maxD = std::max(maxD, M->maxD);
     }

@@ -215,6 +215,47 @@ cudaError_t launch_zscale(double2* x, size_t n, const double2* factor, cudaStrea
 cudaError_t launch_norm_phase(const double2* R0, const double2* amp0, double2* factor,
                               int* status, cudaStream_t s);
 
+// Parity-compact layout of the mixed path's per-site tensors (energy gauge,
+// environment products, canonical transforms).  A^m[alpha, p, beta] is zero
+// unless n_alpha + p + n_beta is even, so site m is stored as two class
+// blocks: rows = the class-c states of the left bond (kl[c] of them, in the
+// order of the bond's parity list), row length K_c = ceil(d/2) kr[c] +
+// floor(d/2) kr[c^1], and column block p = the class c^(p&1) states of the
+// right bond, starting at floor(p/2) D_r + (p odd ? kr[c] : 0).  Class 0
+// rows come first.  Environments and their factors are stored per bond as
+// two diagonal blocks (class 0 then class 1, each row-major with its own
+// leading dimension).
+struct ParitySite {
+  const int* pl;           // parity list of the left bond (class 0 then class 1), device
+  const int* pr;           // the same for the right bond
+  int kl[2], kr[2];
+};
+__host__ __device__ inline long long pk_len(int d, const int* kr, int c) {
+  return (long long)((d + 1) / 2) * kr[c] + (long long)(d / 2) * kr[c ^ 1];
+}
+__host__ __device__ inline long long pk_off(int p, int Dr, const int* kr, int c) {
+  return (long long)(p >> 1) * Dr + ((p & 1) ? kr[c] : 0);
+}
+__host__ __device__ inline long long pk_size(int d, const int* kl, const int* kr) {
+  return (long long)kl[0] * pk_len(d, kr, 0) + (long long)kl[1] * pk_len(d, kr, 1);
+}
+// compact index idx of a site -> (class c, row a, p, column j, right class cr)
+__device__ inline void pk_locate(const ParitySite& P, int d, long long idx, int& c, int& a, int& p,
+                                 int& j, int& cr) {
+  const long long n0 = (long long)P.kl[0] * pk_len(d, P.kr, 0);
+  const int Dr = P.kr[0] + P.kr[1];
+  c = idx < n0 ? 0 : 1;
+  const long long loc = c ? idx - n0 : idx;
+  const long long K = pk_len(d, P.kr, c);
+  a = (int)(loc / K);
+  const long long k = loc - (long long)a * K;
+  const int pp = (int)(k / Dr), rem = (int)(k - (long long)pp * Dr);
+  const int odd = rem >= P.kr[c] ? 1 : 0;
+  p = 2 * pp + odd;
+  j = odd ? rem - P.kr[c] : rem;
+  cr = c ^ odd;
+}
+
 struct NormJob {         // one state of the batched normalisation
   int N, d;
   const int* D;            // bond dimensions [N + 1] (device)
@@ -223,6 +264,7 @@ struct NormJob {         // one state of the batched normalisation
   const double2* R0;       // norm^2
   double2* Ah;             // mixed path: energy-gauge tensors (A^1 rewritten), else null
   const double* E1;        // energies of bond 1 (mixed path)
+  ParitySite P0;           // mixed path: parity-compact layout of site 0
 };
 cudaError_t launch_vac_norm_batch(const NormJob* jobs_dev, int count, int maxD, int* status,
                                   cudaStream_t s);
@@ -241,22 +283,34 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
                                        uint64_t counter0, float2* vnew, uint8_t* out, int N,
                                        uint8_t* flags, double flag_tol, cudaStream_t s);
 struct GaugeTask {        // one site of a batched energy-gauge launch
-  const double2* A;
+  const double2* A;       // FP64 tensor, E order
   int Dl, Dr;
   const double* El;
   const double* Er;
-  double2* Ah;
+  double2* Ah;            // parity-compact output
+  ParitySite P;
 };
 cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, int d, int max_elems,
                                       cudaStream_t s);
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
-                                const double* Er, double2* Ah, cudaStream_t s);
+                                const double* Er, const ParitySite& P, double2* Ah, cudaStream_t s);
 // allocation-free single-site build (noalloc.cu)
 int noalloc_build_site(int device, cudaStream_t s, int* status_dev, int32_t nl, int32_t nr,
                        int32_t d, const double* Qm, double cscale, int32_t Dl,
                        const uint8_t* occ_l, int32_t Dr, const uint8_t* occ_r, int32_t precision,
                        double* out, const char** detail);
 // complex GEMM in double-float arithmetic (k_df64.cu), FP64 operands/result
+// many independent double-float products in one launch (grouped k split,
+// partials reduced in FP64 in k order); products with M or N = 0 are skipped
+struct DfSub {
+  int opa, opb, M, N, K;
+  const double2* A; long long lda;
+  const double2* B; long long ldb;
+  double2* C; long long ldc;
+  int herm;                // C Hermitian (M == N): lower triangle computed, mirrored
+};
+cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
+                                      size_t work_bytes);
 cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
                               long long sA, const double2* B, long long ldb, long long sB,
                               double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
@@ -269,8 +323,9 @@ struct EnvJob {
   const long long* toff;   // tensor offsets [N]
   const long long* eoff;   // environment offsets [N + 1]
   const double2* Ah;       // energy-gauge tensors
-  double2* R;              // environments (R^N = 1 on entry)
+  double2* R;              // environments (R^N = 1 on entry), two parity blocks per bond
   double2* X;              // scratch, >= d maxD^2 complex
+  const int* pc;           // parity class sizes [2 (N + 1)] (device); Ah is parity-compact
 };
 // cfg: tile shape 0 = 64x64, 1 = 32x64, 2 = 32x32 (all give the same result);
 // cfg < 0 picks the fastest for the batch class, measured once per process
@@ -311,9 +366,8 @@ cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* 
                               const __half* A0, long long apl0, const __half* A1, long long apl1,
                               const __half* B0, long long bpl0, const __half* B1, long long bpl1,
                               int use_tc, int* status, int sm_reserve, cudaStream_t s);
-cudaError_t launch_pack_group(const float2* At, int Dl, int d, int Dr, const int* lidx, int kc,
-                              const int* ridx0, int rc0, const int* ridx1, int rc1, int w0, int w1,
-                              int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s);
+cudaError_t launch_pack_compact(const float2* At, int d, int kc, int kr0, int kr1, int K, int w0,
+                                int w1, int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s);
 cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
                                 cudaStream_t s);
 cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,

@@ -413,18 +413,18 @@ __global__ void parity_classes_kernel(BondArrays ba, int nb) {
 }
 
 // ---------------------------------------------------------------- packing
-// B planes of group pi of one site: complex column nc = (p, j) in the group's
-// block layout, real rows 2 nc + c; K index a (real 2a + e) = class pi state
-// lidx[a] of the left bond; [[Re, -Im], [Im, Re]] blocks of At[alpha, p,
-// beta] with beta the j-th state of class pi^(p&1) of the right bond (ridx0
-// for even p, ridx1 for odd p); zero in the padding
-__global__ void pack_group_kernel(const float2* __restrict__ At, int Dl, int d, int Dr,
-                                  const int* __restrict__ lidx, int kc, const int* __restrict__ ridx0,
-                                  int rc0, const int* __restrict__ ridx1, int rc1, int w0, int w1,
-                                  int Kp, int Np, __half* __restrict__ Bp, long long bpl) {
+// B planes of group pi of one site from its parity-compact canonical tensor
+// (At_pi: kc rows of length K): complex column nc = (p, j) in the group's
+// 16-padded block layout, real rows 2 nc + c; K index a (real 2a + e) = row
+// a; [[Re, -Im], [Im, Re]] blocks; zero in the padding.  Block p of a
+// compact row starts at floor(p/2) (kr0 + kr1) + (p odd ? kr0 : 0), with kr0
+// (kr1) states of the right bond in the class of even (odd) p.
+__global__ void pack_compact_kernel(const float2* __restrict__ At, int d, int kc, int kr0, int kr1,
+                                    int K, int w0, int w1, int Kp, int Np, __half* __restrict__ Bp,
+                                    long long bpl) {
   const long long ncx = Np / 2;
   const long long total = ncx * (Kp / 2);
-  const int P2 = w0 + w1;
+  const int P2 = w0 + w1, Dr = kr0 + kr1;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int nc = (int)(idx / (Kp / 2));
@@ -433,10 +433,8 @@ __global__ void pack_group_kernel(const float2* __restrict__ At, int Dl, int d, 
     const bool odd = rem >= w0;
     const int p = 2 * pp + (odd ? 1 : 0), j = odd ? rem - w0 : rem;
     float2 v = make_float2(0.f, 0.f);
-    if (p < d && a < kc && j < (odd ? rc1 : rc0)) {
-      const int al = lidx[a], be = odd ? ridx1[j] : ridx0[j];
-      if (al >= 0 && al < Dl && be >= 0 && be < Dr) v = At[((long long)al * d + p) * Dr + be];
-    }
+    if (p < d && a < kc && j < (odd ? kr1 : kr0))
+      v = At[(long long)a * K + (long long)pp * Dr + (odd ? kr0 : 0) + j];
     __half rr[NPL], ii[NPL];
     split2(v.x, rr[0], rr[1]);
     split2(v.y, ii[0], ii[1]);
@@ -754,14 +752,12 @@ cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_group(const float2* At, int Dl, int d, int Dr, const int* lidx, int kc,
-                              const int* ridx0, int rc0, const int* ridx1, int rc1, int w0, int w1,
-                              int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s) {
+cudaError_t launch_pack_compact(const float2* At, int d, int kc, int kr0, int kr1, int K, int w0,
+                                int w1, int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s) {
   if (w0 + w1 <= 0) return cudaErrorInvalidValue;
   long long total = (long long)(Np / 2) * (Kp / 2);
   int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8192));
-  pack_group_kernel<<<blocks, 256, 0, s>>>(At, Dl, d, Dr, lidx, kc, ridx0, rc0, ridx1, rc1, w0, w1,
-                                           Kp, Np, Bp, bpl);
+  pack_compact_kernel<<<blocks, 256, 0, s>>>(At, d, kc, kr0, kr1, K, w0, w1, Kp, Np, Bp, bpl);
   return cudaGetLastError();
 }
 

@@ -176,6 +176,64 @@ __global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
   df_tile<TM, TN>(t, blockIdx.y * TM, blockIdx.x * TN, kbeg, kend, As, Bs);
 }
 
+// Many independent products C_i = op(A_i) op(B_i) in one launch (the blocks
+// of a parity-compact environment step).  CTAs are dealt to the products in
+// order (c0 = first CTA of a product); each product has its own tile grid and
+// k split, and partials of split products go to a workspace that the grouped
+// reduction sums in k order.
+constexpr int DFG_MAX = 40;
+struct DfProb {
+  DfTile t;                 // operands, dims, ops; C / ldc = the final output
+  int K, ksplit, kchunk, tn;
+  long long c0;             // first CTA of this product
+  long long part;           // its partials in the workspace (ksplit > 1)
+};
+struct DfGroup {
+  int np;
+  double2* work;
+  DfProb p[DFG_MAX];
+};
+
+template <int TM, int TN>
+__global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_constant__ DfGroup g) {
+  __shared__ __align__(16) float As[DK][TM + 1][4];
+  __shared__ __align__(16) float Bs[DK][TN + 1][4];
+  const long long b = blockIdx.x;
+  int lo = 0, hi = g.np - 1;
+  while (lo < hi) {                           // last product with c0 <= b
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.p[mid].c0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const DfProb& P = g.p[lo];
+  const long long l = b - P.c0;
+  const int kz = (int)(l % P.ksplit);
+  const long long tl = l / P.ksplit;
+  const int i0 = (int)(tl / P.tn) * TM, j0 = (int)(tl % P.tn) * TN;
+  const int kbeg = kz * P.kchunk, kend = min(P.K, kbeg + P.kchunk);
+  DfTile t = P.t;
+  if (P.ksplit > 1) {
+    t.C = g.work + P.part + (long long)kz * t.M * t.N;
+    t.ldc = t.N;
+    t.mirror = 0;
+  }
+  df_tile<TM, TN>(t, i0, j0, kbeg, kend, As, Bs);
+}
+
+__global__ void df_reduce_grouped_kernel(const __grid_constant__ DfGroup g) {
+  const DfProb& P = g.p[blockIdx.y];
+  if (P.ksplit <= 1) return;
+  const long long M = P.t.M, N = P.t.N, n = M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / N, c = i % N;
+    if (P.t.herm && r < c) continue;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < P.ksplit; ++k) s = cadd(s, g.work[P.part + k * n + i]);
+    P.t.C[r * P.t.ldc + c] = s;
+    if (P.t.herm && r > c) P.t.C[c * P.t.ldc + r] = cconj(s);
+  }
+}
+
 // Right-environment chains of many states in one persistent cooperative
 // launch.  Step k handles site m = N_s - 1 - k of every state s with N_s > k:
 // phase 0: X_s = Ahat^m (D_m d x D_{m+1}) R^{m+1}; phase 1: R^m = X_s
@@ -197,25 +255,40 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
         const EnvJob J = jobs[j];
         if (k >= J.N) continue;
         const int m = J.N - 1 - k;
-        const int Dl = J.D[m], Dr = J.D[m + 1];
+        // parity blocks: phase 0 per class c and p, phase 1 per class c
+        const int kl[2] = {J.pc[2 * m], J.pc[2 * m + 1]};
+        const int kr[2] = {J.pc[2 * m + 2], J.pc[2 * m + 3]};
+        const int Dr = kr[0] + kr[1];
+        const long long Kc[2] = {pk_len(J.d, kr, 0), pk_len(J.d, kr, 1)};
+        const long long o1 = (long long)kl[0] * Kc[0];
         const double2* A = J.Ah + J.toff[m];
-        DfTile p;
-        int K;
-        if (phase == 0) {
-          p = DfTile{Dl * J.d, Dr, 0, 0, A, Dr, J.R + J.eoff[m + 1], Dr, J.X, Dr};
-          K = Dr;
-        } else {
-          p = DfTile{Dl, Dl, 0, 1, J.X, (long long)J.d * Dr, A, (long long)J.d * Dr,
-                     J.R + J.eoff[m], Dl, 1, 1};            // R^m is Hermitian
-          K = J.d * Dr;
+        const int nsub = phase == 0 ? 2 * J.d : 2;
+        for (int q = 0; q < nsub; ++q) {
+          DfTile p;
+          int K;
+          if (phase == 0) {
+            const int c = q / J.d, pp = q % J.d, cr = c ^ (pp & 1);
+            const long long off = (c ? o1 : 0) + pk_off(pp, Dr, kr, c);
+            p = DfTile{kl[c], kr[cr], 0, 0, A + off, Kc[c],
+                       J.R + J.eoff[m + 1] + (cr ? (long long)kr[0] * kr[0] : 0), kr[cr], J.X + off,
+                       Kc[c]};
+            K = kr[cr];
+          } else {
+            const int c = q;
+            const long long off = c ? o1 : 0;
+            p = DfTile{kl[c], kl[c], 0, 1, J.X + off, Kc[c], A + off, Kc[c],
+                       J.R + J.eoff[m] + (c ? (long long)kl[0] * kl[0] : 0), kl[c], 1, 1};
+            K = (int)Kc[c];                                  // R^m is Hermitian
+          }
+          if (p.M <= 0 || p.N <= 0) continue;
+          const long long tn = (p.N + TN - 1) / TN;
+          const long long nt = ((p.M + TM - 1) / TM) * tn;
+          for (; t < base + nt; t += gridDim.x) {
+            const long long l = t - base;
+            df_tile<TM, TN>(p, (int)(l / tn) * TM, (int)(l % tn) * TN, 0, K, As, Bs);
+          }
+          base += nt;
         }
-        const long long tn = (p.N + TN - 1) / TN;
-        const long long nt = ((p.M + TM - 1) / TM) * tn;
-        for (; t < base + nt; t += gridDim.x) {
-          const long long l = t - base;
-          df_tile<TM, TN>(p, (int)(l / tn) * TM, (int)(l % tn) * TN, 0, K, As, Bs);
-        }
-        base += nt;
       }
       grid.sync();
     }
@@ -262,6 +335,80 @@ std::mutex g_df_mu;
 std::map<std::array<int, 6>, int> g_df_tune;
 
 }  // namespace
+
+cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
+                                      size_t work_bytes) {
+  static std::atomic<int> nsm_cache{0};
+  int nsm = nsm_cache.load();
+  if (!nsm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e) return e;
+    nsm_cache.store(nsm);
+  }
+  std::vector<DfSub> live;
+  for (int i = 0; i < n; ++i)
+    if (subs[i].M > 0 && subs[i].N > 0) live.push_back(subs[i]);
+  for (size_t g0 = 0; g0 < live.size(); g0 += DFG_MAX) {
+    const int np = (int)std::min<size_t>(DFG_MAX, live.size() - g0);
+    // tile shape: 64 x 64 when that already gives two waves, else 32 x 32
+    long long t64 = 0;
+    for (int i = 0; i < np; ++i) {
+      const DfSub& u = live[g0 + i];
+      t64 += (long long)((u.M + 63) / 64) * ((u.N + 63) / 64);
+    }
+    const int T = t64 >= 2LL * nsm ? 64 : 32;
+    long long tiles = 0;
+    for (int i = 0; i < np; ++i) {
+      const DfSub& u = live[g0 + i];
+      tiles += (long long)((u.M + T - 1) / T) * ((u.N + T - 1) / T);
+    }
+    // k split toward two waves, chunks of >= 8 stages, within the workspace
+    int target = (int)std::max<long long>(1, (2LL * nsm + tiles - 1) / tiles);
+    DfGroup G;
+    G.np = np;
+    G.work = reinterpret_cast<double2*>(work);
+    for (;;) {
+      long long c0 = 0, part = 0;
+      for (int i = 0; i < np; ++i) {
+        const DfSub& u = live[g0 + i];
+        DfProb& P = G.p[i];
+        P.t = DfTile{u.M, u.N, u.opa, u.opb, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.herm, u.herm};
+        P.K = u.K;
+        int ks = std::max(1, std::min(target, u.K / (8 * DK)));
+        if (!work) ks = 1;
+        int kchunk = u.K > 0 ? ((u.K + ks - 1) / ks + DK - 1) / DK * DK : DK;
+        ks = u.K > 0 ? (u.K + kchunk - 1) / kchunk : 1;
+        P.ksplit = ks;
+        P.kchunk = kchunk;
+        P.tn = (u.N + T - 1) / T;
+        P.c0 = c0;
+        P.part = part;
+        c0 += (long long)((u.M + T - 1) / T) * P.tn * ks;
+        if (ks > 1) part += (long long)ks * u.M * u.N;
+      }
+      if ((size_t)part * sizeof(double2) <= work_bytes || target == 1) {
+        if ((size_t)part * sizeof(double2) > work_bytes) return cudaErrorInvalidValue;
+        if (c0 > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if (T == 64)
+          zgemm_df64_grouped_kernel<64, 64><<<(unsigned)c0, 256, 0, s>>>(G);
+        else
+          zgemm_df64_grouped_kernel<32, 32><<<(unsigned)c0, 256, 0, s>>>(G);
+        COUNT_LAUNCH(1);
+        if (part > 0) {
+          df_reduce_grouped_kernel<<<dim3(64, np), 256, 0, s>>>(G);
+          COUNT_LAUNCH(1);
+        }
+        break;
+      }
+      target = std::max(1, target / 2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
                               long long sA, const double2* B, long long ldb, long long sB,

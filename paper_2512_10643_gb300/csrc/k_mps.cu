@@ -141,15 +141,20 @@ __global__ void vac_norm_kernel(const NormJob* __restrict__ jobs, int maxD, int*
   }
   __syncthreads();
   const int D1 = J.D[1];
-  for (int i = tid; i < d * D1; i += nt) {
-    const double2 x = cmul(J.T[i], fac);
-    J.T[i] = x;
-    if (J.Ah) {
-      const int b = i % D1;
-      const double er = D1 > 1 ? J.E1[b] : 0.0;
-      J.Ah[i] = cscale(x, exp(-0.5 * er));
+  if (J.Ah) {
+    // the normalised first tensor in the energy gauge, parity-compact (read
+    // before the rescale below rewrites T)
+    const long long n = pk_size(d, J.P0.kl, J.P0.kr);
+    for (long long idx = tid; idx < n; idx += nt) {
+      int c, a, p, j, cr;
+      pk_locate(J.P0, d, idx, c, a, p, j, cr);
+      const int be = J.P0.pr[(cr ? J.P0.kr[0] : 0) + j];
+      const double er = D1 > 1 ? J.E1[be] : 0.0;
+      J.Ah[idx] = cscale(cmul(J.T[(size_t)p * D1 + be], fac), exp(-0.5 * er));
     }
+    __syncthreads();
   }
+  for (int i = tid; i < d * D1; i += nt) J.T[i] = cmul(J.T[i], fac);
 }
 
 // amplitudes: Vn[s, b] = sum_a V[s, a] A[a, n_s, b]

@@ -334,28 +334,36 @@ __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n,
 // energy gauge of the mixed path: Ahat[a, p, b] = A[a, p, b] e^{-(E_b - E_a)/2}
 // (the right environment of bond m is close to diag(e^{-E}), Eq. (SVD3), so
 // this diagonal gauge makes the environments well conditioned in FP32)
+// energy gauge of one site into the parity-compact layout:
+// Ahat[c][a][(p, j)] = A[alpha, p, beta] e^{-(E_beta - E_alpha)/2}, alpha the
+// a-th class-c state of the left bond, beta the j-th class-c^(p&1) state of
+// the right bond (an end bond's energy is 0)
+__device__ inline void gauge_entry(const double2* __restrict__ A, int Dl, int d, int Dr,
+                                   const double* __restrict__ El, const double* __restrict__ Er,
+                                   const ParitySite& P, long long idx, double2* __restrict__ Ah) {
+  int c, a, p, j, cr;
+  pk_locate(P, d, idx, c, a, p, j, cr);
+  const int al = P.pl[(c ? P.kl[0] : 0) + a], be = P.pr[(cr ? P.kr[0] : 0) + j];
+  const double el = Dl > 1 ? El[al] : 0.0, er = Dr > 1 ? Er[be] : 0.0;
+  Ah[idx] = cscale(A[((long long)al * d + p) * Dr + be], exp(-0.5 * (er - el)));
+}
+
 __global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d, int Dr,
                                     const double* __restrict__ El, const double* __restrict__ Er,
-                                    double2* __restrict__ Ah) {
-  size_t n = (size_t)Dl * d * Dr;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    int a = idx / ((size_t)d * Dr), b = idx % Dr;
-    double el = Dl > 1 ? El[a] : 0.0, er = Dr > 1 ? Er[b] : 0.0;
-    Ah[idx] = cscale(A[idx], exp(-0.5 * (er - el)));
-  }
+                                    const ParitySite P, double2* __restrict__ Ah) {
+  const long long n = pk_size(d, P.kl, P.kr);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    gauge_entry(A, Dl, d, Dr, El, Er, P, idx, Ah);
 }
 
 // the same over many sites (blockIdx.y = task) in one launch
 __global__ void energy_gauge_batch_kernel(const GaugeTask* __restrict__ tasks, int d) {
   const GaugeTask t = tasks[blockIdx.y];
-  const size_t n = (size_t)t.Dl * d * t.Dr;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int a = idx / ((size_t)d * t.Dr), b = idx % t.Dr;
-    const double el = t.Dl > 1 ? t.El[a] : 0.0, er = t.Dr > 1 ? t.Er[b] : 0.0;
-    t.Ah[idx] = cscale(t.A[idx], exp(-0.5 * (er - el)));
-  }
+  const long long n = pk_size(d, t.P.kl, t.P.kr);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    gauge_entry(t.A, t.Dl, d, t.Dr, t.El, t.Er, t.P, idx, t.Ah);
 }
 
 }  // namespace
@@ -415,11 +423,10 @@ cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int ca
 }
 
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
-                                const double* Er, double2* Ah, cudaStream_t s) {
-  size_t n = (size_t)Dl * d * Dr;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
+                                const double* Er, const ParitySite& P, double2* Ah, cudaStream_t s) {
+  const long long n = pk_size(d, P.kl, P.kr);
+  int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
-  energy_gauge_kernel<<<blocks, 256, 0, s>>>(A, Dl, d, Dr, El, Er, Ah);
+  energy_gauge_kernel<<<blocks, 256, 0, s>>>(A, Dl, d, Dr, El, Er, P, Ah);
   return cudaGetLastError();
 }

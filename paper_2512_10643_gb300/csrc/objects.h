@@ -196,6 +196,7 @@ struct CanonWork {               // temporaries of the right-canonical packing
   size_t wbytes = 0;
   ~CanonWork() { du.release(); tb.release(); ab.release(); kw.release(); }
 };
+ParitySite parity_site(const gbsmps_mps* M, int m);   // site m's parity-compact layout
 int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s);
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s);
 int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s);

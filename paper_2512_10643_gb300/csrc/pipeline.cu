@@ -190,6 +190,47 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) 
   return GBSMPS_OK;
 }
 
+ParitySite parity_site(const gbsmps_mps* M, int m) {
+  const int cap = M->ba.cap;
+  ParitySite P;
+  P.pl = M->ba.pidx + (size_t)m * cap;
+  P.pr = M->ba.pidx + (size_t)(m + 1) * cap;
+  P.kl[0] = M->pcnt[2 * m]; P.kl[1] = M->pcnt[2 * m + 1];
+  P.kr[0] = M->pcnt[2 * m + 2]; P.kr[1] = M->pcnt[2 * m + 3];
+  return P;
+}
+
+// one step of the parity-compact environment chain: R_m from R_{m+1}.
+// Product 1, per class c and p: X_c[:, block p] = Ahat_c[:, block p] R_{m+1, c^(p&1)};
+// product 2, per class c: R_{m, c} = X_c Ahat_c^dag (Hermitian)
+int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2* X, void* work,
+                    size_t wbytes, cudaStream_t s) {
+  const int d = M->d;
+  const ParitySite P = parity_site(M, m);
+  const int Dr = P.kr[0] + P.kr[1];
+  const long long K[2] = {pk_len(d, P.kr, 0), pk_len(d, P.kr, 1)};
+  const long long o1 = (long long)P.kl[0] * K[0];
+  const double2* A = Ah + M->toff[m];
+  const double2* Rr = R + M->eoff[m + 1];
+  std::vector<DfSub> sub;
+  for (int c = 0; c < 2; ++c)
+    for (int p = 0; p < d; ++p) {
+      const int cr = c ^ (p & 1);
+      const long long off = (c ? o1 : 0) + pk_off(p, Dr, P.kr, c);
+      sub.push_back(DfSub{0, 0, P.kl[c], P.kr[cr], P.kr[cr], A + off, K[c],
+                          Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0});
+    }
+  CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
+  sub.clear();
+  for (int c = 0; c < 2; ++c) {
+    const long long off = c ? o1 : 0;
+    sub.push_back(DfSub{0, 1, P.kl[c], P.kl[c], (int)K[c], X + off, K[c], A + off, K[c],
+                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1});
+  }
+  CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
+  return GBSMPS_OK;
+}
+
 int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
   cudaStream_t s = c->stream;
   const int N = M->N, d = M->d, cap = M->ba.cap;
@@ -206,12 +247,14 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     // FP32 pipes (~44-bit): the chain of N dependent products sets the norm,
     // so its per-step error must stay far below the tensor cores' FP32
     // accumulation error
+    // tensors in the parity-compact layout: the environments are then two
+    // diagonal blocks per bond and every product a quarter of the dense one
     CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
     double2* Ah = M->tens_mixed.as<double2>();
     for (int m = 0; m < N; ++m) {
       CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
                              M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
-                             Ah + M->toff[m], s));
+                             parity_site(M, m), Ah + M->toff[m], s));
       COUNT_LAUNCH(1);
     }
     tm.mark("energy_gauge");
@@ -221,12 +264,8 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     // (plain FP32 products were measured at 4.4e-5 (N = 144) and 2.8e-4
     // (N = 1024) amplitude error against FP64: the norm needs more bits)
     for (int m = N - 1; m >= 0; --m) {
-      int Dl = M->D[m], Dr = M->D[m + 1];
-      const double2* A = Ah + M->toff[m];
-      CK(launch_zgemm_df64('N', 'N', Dl * d, Dr, Dr, A, Dr, 0, R + M->eoff[m + 1], Dr, 0, X, Dr, 0,
-                           1, s, kw.p, wbytes));
-      CK(launch_zgemm_df64('N', 'C', Dl, Dl, d * Dr, X, d * Dr, 0, A, d * Dr, 0, R + M->eoff[m], Dl,
-                           0, 1, s, kw.p, wbytes, /*herm=*/1));
+      const int rc = env_step_blocks(M, m, Ah, R, X, kw.p, wbytes, s);
+      if (rc) return rc;
     }
     kw.release();
   } else {
@@ -264,7 +303,7 @@ int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
   COUNT_LAUNCH(2);
   if (M->precision == GBSMPS_PREC_MIXED) {   // the normalised first tensor in the energy gauge
     CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], M->ba.E, M->ba.E + cap,
-                           M->tens_mixed.as<double2>(), s));
+                           parity_site(M, 0), M->tens_mixed.as<double2>(), s));
     COUNT_LAUNCH(1);
   }
   ab.release();
@@ -278,13 +317,26 @@ int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
 // stages below can run per bond / per site as soon as their inputs exist.
 int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
   const int N = M->N, d = M->d;
-  CK(M->eoff_dev.alloc(sizeof(long long) * (N + 1), s));
-  CK(cudaMemcpyAsync(M->eoff_dev.p, M->eoff.data(), sizeof(long long) * (N + 1),
-                     cudaMemcpyHostToDevice, s));
+  if ((int)M->pcnt.size() != 2 * (N + 1)) return fail(GBSMPS_ERR_CUDA, "parity classes missing");
+  // the environments' diagonal blocks (bond b, class c at 2b + c): offsets,
+  // then sizes; the factors and inverses use the same places
+  {
+    const int nbk = 2 * (N + 1);
+    std::vector<long long> tab(nbk + (nbk + 1) / 2, 0);
+    int* dims = reinterpret_cast<int*>(tab.data() + nbk);
+    for (int b = 0; b <= N; ++b)
+      for (int c = 0; c < 2; ++c) {
+        tab[2 * b + c] = M->eoff[b] + (c ? (long long)M->pcnt[2 * b] * M->pcnt[2 * b] : 0);
+        dims[2 * b + c] = M->pcnt[2 * b + c];
+      }
+    CK(M->eoff_dev.alloc(sizeof(long long) * tab.size(), s));
+    CK(cudaMemcpyAsync(M->eoff_dev.p, tab.data(), sizeof(long long) * tab.size(),
+                       cudaMemcpyHostToDevice, s));
+  }
   CK(M->lchol.alloc(sizeof(double2) * (M->etot + 8), s));
   CK(M->linv.alloc(sizeof(double2) * (M->etot + 8), s));
-  CK(w->du.alloc(sizeof(double) * (N + 1), s));
-  CK(cudaMemsetAsync(w->du.p, 0, sizeof(double) * (N + 1), s));
+  CK(w->du.alloc(sizeof(double) * 2 * (N + 1), s));
+  CK(cudaMemsetAsync(w->du.p, 0, sizeof(double) * 2 * (N + 1), s));
   const double2 one = cmk(1.0, 0.0);
   for (int b : {0, N}) {
     CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
@@ -323,33 +375,32 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
 }
 
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s) {
-  // FP64, one SM per bond (a double-float form on the FP32 pipes was measured
-  // slower: these loops are bound by dependency latency and barriers, and
-  // double-float multiplies the instructions on the critical path)
+  // FP64, one SM per diagonal block of R (a double-float form on the FP32
+  // pipes was measured slower: these loops are bound by dependency latency
+  // and barriers, and double-float multiplies the instructions on the
+  // critical path)
   if (nb <= 0) return GBSMPS_OK;
-  CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), M->eoff_dev.as<long long>(),
-                 M->ba.D, b0, nb, w->du.as<double>(), c->d_status, s));
-  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), M->eoff_dev.as<long long>(),
-                  M->ba.D, b0, nb, s));
+  const long long* off = M->eoff_dev.as<long long>();
+  const int* dims = reinterpret_cast<const int*>(off + 2 * (M->N + 1));
+  CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), off, dims, 2 * b0, 2 * nb,
+                 w->du.as<double>(), c->d_status, s));
+  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, s));
   COUNT_LAUNCH(2);
   return GBSMPS_OK;
 }
 
-// pack site m's canonical tensor At (E order, Dl x d x Dr) as the planes of
+// pack site m's canonical tensor At (parity-compact, FP32) as the planes of
 // both parity groups, with their TMA maps
 int pack_site_groups(gbsmps_mps* M, const float2* At, int m, cudaStream_t s) {
-  const int d = M->d, Dl = M->D[m], Dr = M->D[m + 1], cap = M->ba.cap;
-  const int* pl = M->ba.pidx + (size_t)m * cap;
-  const int* pr = M->ba.pidx + (size_t)(m + 1) * cap;
-  const int kl[2] = {M->pcnt[2 * m], M->pcnt[2 * m + 1]};
-  const int kr[2] = {M->pcnt[2 * (m + 1)], M->pcnt[2 * (m + 1) + 1]};
+  const int d = M->d;
+  const ParitySite P = parity_site(M, m);
+  const long long o1 = (long long)P.kl[0] * pk_len(d, P.kr, 0);
   gbsmps_mps::SiteGroups& G = M->sg[m];
   for (int pi = 0; pi < 2; ++pi) {
     __half* Bp = M->bpack.as<__half>() + G.boff[pi];
-    const int c0 = pi, c1 = pi ^ 1;                 // right-bond class of even / odd p
-    CK(launch_pack_group(At, Dl, d, Dr, pl + (pi ? kl[0] : 0), kl[pi], pr + (c0 ? kr[0] : 0), kr[c0],
-                         pr + (c1 ? kr[0] : 0), kr[c1], G.w[c0], G.w[c1], G.Kp[pi], G.Np[pi], Bp,
-                         (long long)G.Np[pi] * G.Kp[pi], s));
+    CK(launch_pack_compact(At + (pi ? o1 : 0), d, P.kl[pi], P.kr[pi], P.kr[pi ^ 1],
+                           (int)pk_len(d, P.kr, pi), G.w[pi], G.w[pi ^ 1], G.Kp[pi], G.Np[pi], Bp,
+                           (long long)G.Np[pi] * G.Kp[pi], s));
     COUNT_LAUNCH(1);
     if (canon_make_map(G.map[pi].data(), Bp, G.Kp[pi], G.Np[pi]))
       return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
@@ -357,18 +408,38 @@ int pack_site_groups(gbsmps_mps* M, const float2* At, int m, cudaStream_t s) {
   return GBSMPS_OK;
 }
 
+// At^m = L_m^{-1} Ahat^m L_{m+1} on the parity blocks: per class c and p,
+// T_c[:, block p] = Ahat_c[:, block p] L_{m+1, c^(p&1)} (batched over the p
+// of one parity), then At_c = L_{m, c}^{-1} T_c
 int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
-  const int d = M->d, Dl = M->D[m], Dr = M->D[m + 1];
-  const double2* Ah = M->tens_mixed.as<double2>();
+  const int d = M->d;
+  const ParitySite P = parity_site(M, m);
+  const int Dr = P.kr[0] + P.kr[1];
+  const long long K[2] = {pk_len(d, P.kr, 0), pk_len(d, P.kr, 1)};
+  const long long o1 = (long long)P.kl[0] * K[0];
+  const double2* Ah = M->tens_mixed.as<double2>() + M->toff[m];
+  const double2* Lr = M->lchol.as<double2>() + M->eoff[m + 1];
   float2* T = w->tb.as<float2>();
   float2* At = w->ab.as<float2>();
   // the canonical tensors feed fp16x2 planes: FP32 products suffice
-  CK(launch_zgemm_f32(Dl * d, Dr, Dr, Ah + M->toff[m], 1, Dr, 0,
-                      M->lchol.as<double2>() + M->eoff[m + 1], 1, Dr, 0, T, Dr, 0, 1, s));
+  for (int c = 0; c < 2; ++c)
+    for (int e = 0; e < 2; ++e) {
+      const int cr = c ^ e, nb = (d - e + 1) / 2;
+      if (P.kl[c] == 0 || P.kr[cr] == 0 || nb <= 0) continue;
+      const long long off = (c ? o1 : 0) + pk_off(e, Dr, P.kr, c);
+      CK(launch_zgemm_f32(P.kl[c], P.kr[cr], P.kr[cr], Ah + off, 1, K[c], Dr,
+                          Lr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), 1, P.kr[cr], 0, T + off, K[c],
+                          Dr, nb, s));
+    }
   const float2* src = T;
   if (m > 0) {
-    CK(launch_zgemm_f32(Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m], 1, Dl, 0, T, 0, d * Dr,
-                        0, At, d * Dr, 0, 1, s));
+    const double2* Li = M->linv.as<double2>() + M->eoff[m];
+    for (int c = 0; c < 2; ++c) {
+      if (P.kl[c] == 0) continue;
+      const long long off = c ? o1 : 0;
+      CK(launch_zgemm_f32(P.kl[c], (int)K[c], P.kl[c], Li + (c ? (long long)P.kl[0] * P.kl[0] : 0), 1,
+                          P.kl[c], 0, T + off, 0, K[c], 0, At + off, K[c], 0, 1, s));
+    }
     src = At;
   }
   return pack_site_groups(M, src, m, s);
@@ -376,8 +447,8 @@ int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
 
 void canon_report(gbsmps_mps* M, CanonWork* w, StageTimer& tm, cudaStream_t s) {
   if (!tm.on) return;
-  std::vector<double> h(M->N + 1);
-  cudaMemcpyAsync(h.data(), w->du.p, sizeof(double) * (M->N + 1), cudaMemcpyDeviceToHost, s);
+  std::vector<double> h(2 * (M->N + 1));
+  cudaMemcpyAsync(h.data(), w->du.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   double mx = 0.0;
   for (double v : h) mx = std::max(mx, v);
@@ -398,47 +469,13 @@ int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
   return GBSMPS_OK;
 }
 
-// The transforms of runs of consecutive sites with the same bond dimensions
-// (all the interior sites once chi binds) as batched GEMMs: T = Ahat^m L_{m+1}
-// for every site of a run in one launch, then At = L_m^{-1} T (one GEMM with
-// N = d D_{m+1} per site) in one launch, then the packing.
+// the transforms and packing of every site (each a few small FP32 products
+// on the parity blocks)
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
-  const int N = M->N, d = M->d;
-  int rc = canon_site(M, w0, 0, st);
-  if (rc) return rc;
-  const size_t budget = (size_t)1 << 30;          // bytes of T (and of At) per group
-  size_t tmax = 0;
-  for (int m = 1; m < N; ++m) {
-    const size_t el = (size_t)M->D[m] * d * M->D[m + 1];
-    const size_t cnt = std::max<size_t>(1, std::min<size_t>(64, budget / (el * sizeof(float2))));
-    tmax = std::max(tmax, cnt * el);
+  for (int m = 0; m < M->N; ++m) {
+    const int rc = canon_site(M, w0, m, st);
+    if (rc) return rc;
   }
-  if (N < 2) return GBSMPS_OK;
-  DevBuf Tg, Ag;
-  CK(Tg.alloc(sizeof(float2) * (tmax + 8), st));
-  CK(Ag.alloc(sizeof(float2) * (tmax + 8), st));
-  const double2* Ah = M->tens_mixed.as<double2>();
-  for (int m0 = 1; m0 < N;) {
-    const int Dl = M->D[m0], Dr = M->D[m0 + 1];
-    const size_t el = (size_t)Dl * d * Dr;
-    const int cmax = (int)std::max<size_t>(1, std::min<size_t>(64, budget / (el * sizeof(float2))));
-    int cnt = 1;
-    while (m0 + cnt < N && cnt < cmax && M->D[m0 + cnt] == Dl && M->D[m0 + cnt + 1] == Dr) ++cnt;
-    // equal dimensions make the tensor and factor offsets uniform strides
-    const long long sT = (long long)el, sE = (long long)Dr * Dr, sEl = (long long)Dl * Dl;
-    CK(launch_zgemm_f32(Dl * d, Dr, Dr, Ah + M->toff[m0], 1, Dr, sT,
-                        M->lchol.as<double2>() + M->eoff[m0 + 1], 1, Dr, sE, Tg.as<float2>(), Dr, sT,
-                        cnt, st));
-    CK(launch_zgemm_f32(Dl, d * Dr, Dl, M->linv.as<double2>() + M->eoff[m0], 1, Dl, sEl, Tg.p, 0,
-                        d * Dr, sT, Ag.as<float2>(), d * Dr, sT, cnt, st));
-    for (int k = 0; k < cnt; ++k) {
-      const int rc = pack_site_groups(M, Ag.as<float2>() + (size_t)k * el, m0 + k, st);
-      if (rc) return rc;
-    }
-    m0 += cnt;
-  }
-  Tg.release();
-  Ag.release();
   return GBSMPS_OK;
 }
 
