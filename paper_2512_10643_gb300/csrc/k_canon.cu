@@ -464,86 +464,102 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
   if (blockIdx.x == 0 && threadIdx.x == 0) { cnt[0] = S; cnt[1] = 0; }
 }
 
-// one warp per (group, row): q_p from the chunk norms (fixed order), choose
-// p*, append vt' = w_{p*} / sqrt(q_{p*}) as fp16 planes to the group of its
-// class at the next bond (class pi ^ (p* & 1)).  The row order inside a
-// group depends on the order of the appends; every row carries its sample
-// index, and no arithmetic depends on the row.
-__global__ void select_groups_kernel(int Scap, int d, const SelGroup g0, const SelGroup g1,
-                                     const NextGroup n0, const NextGroup n1, int* cnt_next,
-                                     const double* __restrict__ u, int ustride, int site,
-                                     uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out,
-                                     int N, uint8_t* flags, double flag_tol) {
+// one warp per sample: warp w takes row w of group 0 or, past its count,
+// row w - count0 of group 1 (the counts add up to S).  q_p from the chunk
+// norms (fixed order), choose p*, append vt' = w_{p*} / sqrt(q_{p*}) as fp16
+// planes to the group of its class at the next bond (class pi ^ (p* & 1));
+// a block reserves its rows of each next group with one atomic per group.
+// The row order inside a group depends on the order of the reservations;
+// every row carries its sample index, and no arithmetic depends on the row.
+constexpr int SEL_THREADS = 512;
+__global__ void __launch_bounds__(SEL_THREADS)
+select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
+                     const NextGroup n1, int* cnt_next, const double* __restrict__ u, int ustride,
+                     int site, uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out, int N,
+                     uint8_t* flags, double flag_tol) {
+  __shared__ int sc[2], sbase[2];
   const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 2) sc[threadIdx.x] = 0;
+  __syncthreads();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (w >= 2LL * Scap) return;
-  const int grp = w >= Scap ? 1 : 0;
-  const int r = (int)(w - (long long)grp * Scap);
+  const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
+  const int grp = w >= M0 ? 1 : 0;
+  const int r = (int)(w - (grp ? M0 : 0));
+  const bool active = w < S && r < (grp ? M1 : M0);
   const SelGroup& g = grp ? g1 : g0;
-  if (r >= min(*g.cnt, Scap)) return;
-  const int s = g.sid[r];
-  const float* ps = g.part + (long long)r * g.ldp;
-  const int P2 = g.wself + g.wother;
-  // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
-  // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway.
-  // Lane j of a 32-wide chunk owns q_{c0 + j}; an inclusive warp scan gives
-  // the CDF; Z is the last CDF value, so the scan and Z agree exactly.
-  auto qp = [&](int p) {
-    float q = 0.f;
-    if (p < d) {
-      const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
-      const int nch = ((p & 1) ? g.wother : g.wself) / 16;
-      for (int t = 0; t < nch; ++t) q += ps[c0 + t];
-    }
-    return q;
-  };
-  float Z = 0.f;
-  for (int c0 = 0; c0 < d; c0 += 32) {
-    float C = qp(c0 + lane);
-    for (int o = 1; o < 32; o <<= 1) {
-      const float y = __shfl_up_sync(0xffffffffu, C, o);
-      if (lane >= o) C += y;
-    }
-    Z += __shfl_sync(0xffffffffu, C, 31);
-  }
-  const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
-  const float tt = (float)uu * Z;
-  const float ftol = (float)flag_tol * Z;
-  int pstar = -1, plast = 0;
-  float qsel = 0.f, base = 0.f;
+  int pstar = 0, np = 0, local = 0, s = 0;
+  float inv = 0.f;
   bool flag = false;
-  for (int c0 = 0; c0 < d; c0 += 32) {
-    const int p = c0 + lane;
-    const float q = qp(p);
-    float C = q;
-    for (int o = 1; o < 32; o <<= 1) {
-      const float y = __shfl_up_sync(0xffffffffu, C, o);
-      if (lane >= o) C += y;
+  if (active) {
+    s = g.sid[r];
+    const float* ps = g.part + (long long)r * g.ldp;
+    const int P2 = g.wself + g.wother;
+    // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
+    // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway.
+    // Lane j of a 32-wide chunk owns q_{c0 + j}; an inclusive warp scan gives
+    // the CDF; Z is the last CDF value, so the scan and Z agree exactly.
+    auto qp = [&](int p) {
+      float q = 0.f;
+      if (p < d) {
+        const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
+        const int nch = ((p & 1) ? g.wother : g.wself) / 16;
+        for (int t = 0; t < nch; ++t) q += ps[c0 + t];
+      }
+      return q;
+    };
+    float Z = 0.f;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+      float C = qp(c0 + lane);
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, C, o);
+        if (lane >= o) C += y;
+      }
+      Z += __shfl_sync(0xffffffffu, C, 31);
     }
-    C += base;
-    base = __shfl_sync(0xffffffffu, C, 31);
-    const bool live = p < d;
-    if (__any_sync(0xffffffffu, live && fabsf(tt - C) <= ftol)) flag = true;
-    const unsigned pos = __ballot_sync(0xffffffffu, live && q > 0.f);
-    if (pos) plast = c0 + 31 - __clz(pos);
-    const unsigned hit = __ballot_sync(0xffffffffu, live && tt < C);
-    if (pstar < 0 && hit) {
-      const int j = __ffs(hit) - 1;
-      pstar = c0 + j;
-      qsel = __shfl_sync(0xffffffffu, q, j);
+    const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
+    const float tt = (float)uu * Z;
+    const float ftol = (float)flag_tol * Z;
+    int plast = 0;
+    float qsel = 0.f, base = 0.f;
+    pstar = -1;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+      const int p = c0 + lane;
+      const float q = qp(p);
+      float C = q;
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, C, o);
+        if (lane >= o) C += y;
+      }
+      C += base;
+      base = __shfl_sync(0xffffffffu, C, 31);
+      const bool live = p < d;
+      if (__any_sync(0xffffffffu, live && fabsf(tt - C) <= ftol)) flag = true;
+      const unsigned pos = __ballot_sync(0xffffffffu, live && q > 0.f);
+      if (pos) plast = c0 + 31 - __clz(pos);
+      const unsigned hit = __ballot_sync(0xffffffffu, live && tt < C);
+      if (pstar < 0 && hit) {
+        const int j = __ffs(hit) - 1;
+        pstar = c0 + j;
+        qsel = __shfl_sync(0xffffffffu, q, j);
+      }
     }
+    if (pstar < 0) {
+      pstar = plast;
+      qsel = qp(pstar);
+    }
+    inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
+    np = grp ^ (pstar & 1);
+    if (lane == 0) local = atomicAdd(&sc[np], 1);
+    local = __shfl_sync(0xffffffffu, local, 0);
   }
-  if (pstar < 0) {
-    pstar = plast;
-    qsel = qp(pstar);
-  }
-  const float inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
-  const int np = grp ^ (pstar & 1);
+  __syncthreads();
+  if (threadIdx.x < 2 && sc[threadIdx.x] > 0) sbase[threadIdx.x] = atomicAdd(cnt_next + threadIdx.x, sc[threadIdx.x]);
+  __syncthreads();
+  if (!active) return;
+  const int pos = sbase[np] + local;
+  if (pos >= S) return;                         // cannot happen: one row per sample
   const NextGroup& ng = np ? n1 : n0;
-  int pos = 0;
-  if (lane == 0) pos = atomicAdd(cnt_next + np, 1);
-  pos = __shfl_sync(0xffffffffu, pos, 0);
-  if (pos >= Scap) return;                      // cannot happen: one row per sample
+  const int P2 = g.wself + g.wother;
   const float2* wr = g.W + (long long)r * g.ldw + (long long)(pstar >> 1) * P2 +
                      ((pstar & 1) ? g.wself : 0);
   for (int b = lane; b < ng.Kp / 2; b += 32) {
@@ -774,10 +790,10 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  const double* u, int ustride, int site, uint64_t seed,
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s) {
-  long long threads = 2LL * Scap * 32;
-  int blocks = (int)((threads + 255) / 256);
-  select_groups_kernel<<<blocks, 256, 0, s>>>(Scap, d, g0, g1, n0, n1, cnt_next, u, ustride, site,
-                                              seed, counter0, out, N, flags, flag_tol);
+  long long threads = (long long)Scap * 32;
+  int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
+  select_groups_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, d, g0, g1, n0, n1, cnt_next, u, ustride,
+                                                      site, seed, counter0, out, N, flags, flag_tol);
   return cudaGetLastError();
 }
 
