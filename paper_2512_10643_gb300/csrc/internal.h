@@ -366,8 +366,12 @@ cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* 
                               const __half* A0, long long apl0, const __half* A1, long long apl1,
                               const __half* B0, long long bpl0, const __half* B1, long long bpl1,
                               int use_tc, int* status, int sm_reserve, cudaStream_t s);
-cudaError_t launch_pack_compact(const float2* At, int d, int kc, int kr0, int kr1, int K, int w0,
-                                int w1, int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s);
+struct PackJob {          // the planes of one (site, group) from its compact tensor
+  const float2* At;       // kc rows of length K
+  int kc, kr0, kr1, K, w0, w1, Kp, Np;
+  __half* Bp; long long bpl;
+};
+cudaError_t launch_pack_compact_batch(const PackJob* jobs_dev, int njobs, int d, cudaStream_t s);
 cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
                                 cudaStream_t s);
 cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,
@@ -381,6 +385,20 @@ cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, con
                          int nb, cudaStream_t s);
 // complex GEMM in FP32 on the CUDA cores (k_f32gemm.cu): C (FP32) = A B with
 // A, B FP64 (a64/b64 = 1) or FP32, row-major, batched by strides
+// many independent FP32 products C = A B (A, B FP64 or FP32 as a64 / b64,
+// C FP32) in one launch; the device table is sorted by c0, the first CTA of
+// each product, with tn = its column tiles; ctas = the total
+struct F32Prob {
+  int M, N, K, tn;
+  const void* A; long long lda;
+  const void* B; long long ldb;
+  float2* C; long long ldc;
+  long long c0;
+};
+int f32_tile_rows();
+int f32_tile_cols();
+cudaError_t launch_zgemm_f32_grouped(const F32Prob* probs_dev, int np, long long ctas, int a64,
+                                     int b64, cudaStream_t s);
 cudaError_t launch_zgemm_f32(int M, int N, int K, const void* A, int a64, long long lda, long long sA,
                              const void* B, int b64, long long ldb, long long sB, float2* C,
                              long long ldc, long long sC, int batch, cudaStream_t s);

@@ -419,28 +419,27 @@ __global__ void parity_classes_kernel(BondArrays ba, int nb) {
 // a; [[Re, -Im], [Im, Re]] blocks; zero in the padding.  Block p of a
 // compact row starts at floor(p/2) (kr0 + kr1) + (p odd ? kr0 : 0), with kr0
 // (kr1) states of the right bond in the class of even (odd) p.
-__global__ void pack_compact_kernel(const float2* __restrict__ At, int d, int kc, int kr0, int kr1,
-                                    int K, int w0, int w1, int Kp, int Np, __half* __restrict__ Bp,
-                                    long long bpl) {
-  const long long ncx = Np / 2;
-  const long long total = ncx * (Kp / 2);
-  const int P2 = w0 + w1, Dr = kr0 + kr1;
+// the packing of many (site, group) planes in one launch: blockIdx.y = job
+__global__ void pack_compact_batch_kernel(const PackJob* __restrict__ jobs, int d) {
+  const PackJob J = jobs[blockIdx.y];
+  const long long total = (long long)(J.Np / 2) * (J.Kp / 2);
+  const int P2 = J.w0 + J.w1, Dr = J.kr0 + J.kr1;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int nc = (int)(idx / (Kp / 2));
-    const int a = (int)(idx % (Kp / 2));
+    const int nc = (int)(idx / (J.Kp / 2));
+    const int a = (int)(idx % (J.Kp / 2));
     const int pp = nc / P2, rem = nc - pp * P2;
-    const bool odd = rem >= w0;
-    const int p = 2 * pp + (odd ? 1 : 0), j = odd ? rem - w0 : rem;
+    const bool odd = rem >= J.w0;
+    const int p = 2 * pp + (odd ? 1 : 0), j = odd ? rem - J.w0 : rem;
     float2 v = make_float2(0.f, 0.f);
-    if (p < d && a < kc && j < (odd ? kr1 : kr0))
-      v = At[(long long)a * K + (long long)pp * Dr + (odd ? kr0 : 0) + j];
+    if (p < d && a < J.kc && j < (odd ? J.kr1 : J.kr0))
+      v = J.At[(long long)a * J.K + (long long)pp * Dr + (odd ? J.kr0 : 0) + j];
     __half rr[NPL], ii[NPL];
     split2(v.x, rr[0], rr[1]);
     split2(v.y, ii[0], ii[1]);
     for (int sp = 0; sp < NPL; ++sp) {
-      __half* row0 = Bp + sp * bpl + (2LL * nc) * Kp + 2 * a;
-      __half* row1 = row0 + Kp;
+      __half* row0 = J.Bp + sp * J.bpl + (2LL * nc) * J.Kp + 2 * a;
+      __half* row1 = row0 + J.Kp;
       __half2 x0, x1;
       x0.x = rr[sp]; x0.y = __hneg(ii[sp]);
       x1.x = ii[sp]; x1.y = rr[sp];
@@ -768,12 +767,11 @@ cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_compact(const float2* At, int d, int kc, int kr0, int kr1, int K, int w0,
-                                int w1, int Kp, int Np, __half* Bp, long long bpl, cudaStream_t s) {
-  if (w0 + w1 <= 0) return cudaErrorInvalidValue;
-  long long total = (long long)(Np / 2) * (Kp / 2);
-  int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8192));
-  pack_compact_kernel<<<blocks, 256, 0, s>>>(At, d, kc, kr0, kr1, K, w0, w1, Kp, Np, Bp, bpl);
+cudaError_t launch_pack_compact_batch(const PackJob* jobs_dev, int njobs, int d, cudaStream_t s) {
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {
+    pack_compact_batch_kernel<<<dim3(48, std::min(65535, njobs - j0)), 256, 0, s>>>(jobs_dev + j0, d);
+    COUNT_LAUNCH(1);
+  }
   return cudaGetLastError();
 }
 

@@ -26,17 +26,12 @@ __device__ __forceinline__ float2 tof(double2 v) { return make_float2((float)v.x
 __device__ __forceinline__ float2 tof(float2 v) { return v; }
 
 __device__ __forceinline__ void store(float2* c, float2 v) { *c = v; }
-__device__ __forceinline__ void store(double2* c, float2 v) { *c = make_double2(v.x, v.y); }
 
+// one 64 x 64 output tile of C = A op(B) (op: none, or conjugate transpose)
 template <typename TA, typename TB, typename TC>
-__global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
-  __shared__ float2 As[FK][FM + 1];     // padded rows: the k-fastest fills hit distinct banks
-  __shared__ float2 Bs[FK][FN + 1];
-  const long long bz = blockIdx.z;
-  const TA* A = reinterpret_cast<const TA*>(p.A) + bz * p.sA;
-  const TB* B = reinterpret_cast<const TB*>(p.B) + bz * p.sB;
-  TC* C = reinterpret_cast<TC*>(p.C) + bz * p.sC;
-  const int i0 = blockIdx.y * FM, j0 = blockIdx.x * FN;
+__device__ __forceinline__ void f32_tile(const F32Args& p, const TA* __restrict__ A,
+                                         const TB* __restrict__ B, TC* __restrict__ C, int i0, int j0,
+                                         float2 (*As)[FM + 1], float2 (*Bs)[FN + 1]) {
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float2 acc[4][4];
 #pragma unroll
@@ -89,7 +84,53 @@ __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
   }
 }
 
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
+  __shared__ float2 As[FK][FM + 1];     // padded rows: the k-fastest fills hit distinct banks
+  __shared__ float2 Bs[FK][FN + 1];
+  const long long bz = blockIdx.z;
+  f32_tile<TA, TB, TC>(p, reinterpret_cast<const TA*>(p.A) + bz * p.sA,
+                       reinterpret_cast<const TB*>(p.B) + bz * p.sB,
+                       reinterpret_cast<TC*>(p.C) + bz * p.sC, blockIdx.y * FM, blockIdx.x * FN, As, Bs);
+}
+
+// many independent products in one launch: CTA b works on the last product
+// whose first CTA c0 <= b (the table is in device memory, sorted by c0)
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) zgemm_f32_grouped_kernel(const F32Prob* __restrict__ probs,
+                                                                 int np) {
+  __shared__ float2 As[FK][FM + 1];
+  __shared__ float2 Bs[FK][FN + 1];
+  const long long b = blockIdx.x;
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].c0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const F32Prob q = probs[lo];
+  const long long l = b - q.c0;
+  const F32Args p{q.M, q.N, q.K, 0, q.A, q.lda, 0, q.B, q.ldb, 0, q.C, q.ldc, 0};
+  f32_tile<TA, TB, float2>(p, reinterpret_cast<const TA*>(q.A), reinterpret_cast<const TB*>(q.B),
+                           reinterpret_cast<float2*>(q.C), (int)(l / q.tn) * FM,
+                           (int)(l % q.tn) * FN, As, Bs);
+}
+
 }  // namespace
+
+int f32_tile_rows() { return FM; }
+int f32_tile_cols() { return FN; }
+
+cudaError_t launch_zgemm_f32_grouped(const F32Prob* probs_dev, int np, long long ctas, int a64,
+                                     int b64, cudaStream_t s) {
+  if (np <= 0 || ctas <= 0) return cudaSuccess;
+  if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (a64 && b64) zgemm_f32_grouped_kernel<double2, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  else if (a64) zgemm_f32_grouped_kernel<double2, float2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  else if (b64) zgemm_f32_grouped_kernel<float2, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  else zgemm_f32_grouped_kernel<float2, float2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_zgemm_f32(int M, int N, int K, const void* A, int a64, long long lda, long long sA,
                              const void* B, int b64, long long ldb, long long sB, float2* C,

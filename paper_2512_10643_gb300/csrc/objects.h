@@ -192,14 +192,12 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d);
 int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int normalise_single(gbsmps_ctx* c, gbsmps_mps* M);
 struct CanonWork {               // temporaries of the right-canonical packing
-  DevBuf du, tb, ab, kw;
-  size_t wbytes = 0;
-  ~CanonWork() { du.release(); tb.release(); ab.release(); kw.release(); }
+  DevBuf du;                     // regulariser used per diagonal block
+  ~CanonWork() { du.release(); }
 };
 ParitySite parity_site(const gbsmps_mps* M, int m);   // site m's parity-compact layout
 int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s);
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s);
-int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s);
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st);
 int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int finish(gbsmps_ctx* c, gbsmps_mps* M);

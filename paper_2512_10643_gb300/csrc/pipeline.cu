@@ -353,7 +353,6 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
       return fail(GBSMPS_ERR_CUDA, "parity class sizes do not add up to the bond dimension");
   M->sg.resize(N);
   long long btot = 0;
-  size_t xmax = 0;
   for (int m = 0; m < N; ++m) {
     gbsmps_mps::SiteGroups& G = M->sg[m];
     for (int c = 0; c < 2; ++c) G.w[c] = (M->pcnt[2 * (m + 1) + c] + 15) / 16 * 16;
@@ -364,13 +363,8 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
       G.boff[pi] = btot;
       btot += 2LL * G.Np[pi] * G.Kp[pi];
     }
-    xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
   }
   CK(M->bpack.alloc(sizeof(__half) * (btot + 64), s));
-  w->wbytes = (size_t)64 << 20;      // split-K partials: fills the GPU at D ~ 256
-  CK(w->tb.alloc(sizeof(float2) * (xmax + 8), s));
-  CK(w->ab.alloc(sizeof(float2) * (xmax + 8), s));
-  CK(w->kw.alloc(w->wbytes, s));
   return GBSMPS_OK;
 }
 
@@ -387,62 +381,6 @@ int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cuda
   CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, s));
   COUNT_LAUNCH(2);
   return GBSMPS_OK;
-}
-
-// pack site m's canonical tensor At (parity-compact, FP32) as the planes of
-// both parity groups, with their TMA maps
-int pack_site_groups(gbsmps_mps* M, const float2* At, int m, cudaStream_t s) {
-  const int d = M->d;
-  const ParitySite P = parity_site(M, m);
-  const long long o1 = (long long)P.kl[0] * pk_len(d, P.kr, 0);
-  gbsmps_mps::SiteGroups& G = M->sg[m];
-  for (int pi = 0; pi < 2; ++pi) {
-    __half* Bp = M->bpack.as<__half>() + G.boff[pi];
-    CK(launch_pack_compact(At + (pi ? o1 : 0), d, P.kl[pi], P.kr[pi], P.kr[pi ^ 1],
-                           (int)pk_len(d, P.kr, pi), G.w[pi], G.w[pi ^ 1], G.Kp[pi], G.Np[pi], Bp,
-                           (long long)G.Np[pi] * G.Kp[pi], s));
-    COUNT_LAUNCH(1);
-    if (canon_make_map(G.map[pi].data(), Bp, G.Kp[pi], G.Np[pi]))
-      return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
-  }
-  return GBSMPS_OK;
-}
-
-// At^m = L_m^{-1} Ahat^m L_{m+1} on the parity blocks: per class c and p,
-// T_c[:, block p] = Ahat_c[:, block p] L_{m+1, c^(p&1)} (batched over the p
-// of one parity), then At_c = L_{m, c}^{-1} T_c
-int canon_site(gbsmps_mps* M, CanonWork* w, int m, cudaStream_t s) {
-  const int d = M->d;
-  const ParitySite P = parity_site(M, m);
-  const int Dr = P.kr[0] + P.kr[1];
-  const long long K[2] = {pk_len(d, P.kr, 0), pk_len(d, P.kr, 1)};
-  const long long o1 = (long long)P.kl[0] * K[0];
-  const double2* Ah = M->tens_mixed.as<double2>() + M->toff[m];
-  const double2* Lr = M->lchol.as<double2>() + M->eoff[m + 1];
-  float2* T = w->tb.as<float2>();
-  float2* At = w->ab.as<float2>();
-  // the canonical tensors feed fp16x2 planes: FP32 products suffice
-  for (int c = 0; c < 2; ++c)
-    for (int e = 0; e < 2; ++e) {
-      const int cr = c ^ e, nb = (d - e + 1) / 2;
-      if (P.kl[c] == 0 || P.kr[cr] == 0 || nb <= 0) continue;
-      const long long off = (c ? o1 : 0) + pk_off(e, Dr, P.kr, c);
-      CK(launch_zgemm_f32(P.kl[c], P.kr[cr], P.kr[cr], Ah + off, 1, K[c], Dr,
-                          Lr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), 1, P.kr[cr], 0, T + off, K[c],
-                          Dr, nb, s));
-    }
-  const float2* src = T;
-  if (m > 0) {
-    const double2* Li = M->linv.as<double2>() + M->eoff[m];
-    for (int c = 0; c < 2; ++c) {
-      if (P.kl[c] == 0) continue;
-      const long long off = c ? o1 : 0;
-      CK(launch_zgemm_f32(P.kl[c], (int)K[c], P.kl[c], Li + (c ? (long long)P.kl[0] * P.kl[0] : 0), 1,
-                          P.kl[c], 0, T + off, 0, K[c], 0, At + off, K[c], 0, 1, s));
-    }
-    src = At;
-  }
-  return pack_site_groups(M, src, m, s);
 }
 
 void canon_report(gbsmps_mps* M, CanonWork* w, StageTimer& tm, cudaStream_t s) {
@@ -469,13 +407,104 @@ int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
   return GBSMPS_OK;
 }
 
-// the transforms and packing of every site (each a few small FP32 products
-// on the parity blocks)
+// The transforms and packing of every site as three grouped launches per
+// chunk of sites (the chunk's T and At fit a byte budget): all products
+// T_c[:, block p] = Ahat_c[:, block p] L_{m+1, c^(p&1)}, then all
+// At_c = L_{m, c}^{-1} T_c (site 0: At = T, L_0 = 1), then the planes.
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
-  for (int m = 0; m < M->N; ++m) {
-    const int rc = canon_site(M, w0, m, st);
-    if (rc) return rc;
+  (void)w0;
+  const int N = M->N, d = M->d;
+  const int TM = f32_tile_rows(), TN = f32_tile_cols();
+  const size_t budget = (size_t)1 << 27;          // complex elements of T (and of At) per chunk
+  std::vector<long long> cofs(N + 1, 0);          // compact offset of each site in a chunk
+  DevBuf Tg, Ag, tab;
+  size_t cap_el = 0;
+  for (int m = 0; m < N; ++m) {
+    const ParitySite P = parity_site(M, m);
+    cap_el = std::max(cap_el, (size_t)pk_size(d, P.kl, P.kr));
   }
+  cap_el = std::max(cap_el, std::min(budget, (size_t)M->ttot));
+  CK(Tg.alloc(sizeof(float2) * (cap_el + 8), st));
+  CK(Ag.alloc(sizeof(float2) * (cap_el + 8), st));
+  float2* T = Tg.as<float2>();
+  float2* At = Ag.as<float2>();
+  const double2* Ahb = M->tens_mixed.as<double2>();
+  const double2* Lb = M->lchol.as<double2>();
+  const double2* Lib = M->linv.as<double2>();
+  std::vector<F32Prob> pt, pa;
+  std::vector<PackJob> pj;
+  for (int m0 = 0; m0 < N;) {
+    // the chunk: sites m0 .. m1-1
+    int m1 = m0;
+    long long tot = 0;
+    while (m1 < N) {
+      const ParitySite P = parity_site(M, m1);
+      const long long sz = pk_size(d, P.kl, P.kr);
+      if (m1 > m0 && (size_t)(tot + sz) > cap_el) break;
+      cofs[m1 - m0] = tot;
+      tot += sz;
+      ++m1;
+    }
+    pt.clear(); pa.clear(); pj.clear();
+    long long ct = 0, ca = 0;
+    for (int m = m0; m < m1; ++m) {
+      const ParitySite P = parity_site(M, m);
+      const int Dr = P.kr[0] + P.kr[1];
+      const long long K[2] = {pk_len(d, P.kr, 0), pk_len(d, P.kr, 1)};
+      const long long o1 = (long long)P.kl[0] * K[0], base = cofs[m - m0];
+      const double2* Ah = Ahb + M->toff[m];
+      for (int c = 0; c < 2; ++c) {
+        if (P.kl[c] == 0) continue;
+        for (int p = 0; p < d; ++p) {
+          const int cr = c ^ (p & 1);
+          if (P.kr[cr] == 0) continue;
+          const long long off = (c ? o1 : 0) + pk_off(p, Dr, P.kr, c);
+          F32Prob q{P.kl[c], P.kr[cr], P.kr[cr], (P.kr[cr] + TN - 1) / TN, Ah + off, K[c],
+                    Lb + M->eoff[m + 1] + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr],
+                    T + base + off, K[c], ct};
+          ct += (long long)((q.M + TM - 1) / TM) * q.tn;
+          pt.push_back(q);
+        }
+        if (m > 0) {
+          F32Prob q{P.kl[c], (int)K[c], P.kl[c], (int)((K[c] + TN - 1) / TN),
+                    Lib + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c],
+                    T + base + (c ? o1 : 0), K[c], At + base + (c ? o1 : 0), K[c], ca};
+          ca += (long long)((q.M + TM - 1) / TM) * q.tn;
+          pa.push_back(q);
+        }
+      }
+      gbsmps_mps::SiteGroups& G = M->sg[m];
+      for (int pi = 0; pi < 2; ++pi) {
+        const float2* src = (m > 0 ? At : T) + base + (pi ? o1 : 0);
+        pj.push_back(PackJob{src, P.kl[pi], P.kr[pi], P.kr[pi ^ 1], (int)K[pi], G.w[pi], G.w[pi ^ 1],
+                             G.Kp[pi], G.Np[pi], M->bpack.as<__half>() + G.boff[pi],
+                             (long long)G.Np[pi] * G.Kp[pi]});
+      }
+    }
+    const size_t tb = sizeof(F32Prob) * (pt.size() + pa.size()) + sizeof(PackJob) * pj.size() + 64;
+    tab.release();
+    CK(tab.alloc(tb, st));
+    F32Prob* dpt = tab.as<F32Prob>();
+    F32Prob* dpa = dpt + pt.size();
+    PackJob* dpj = reinterpret_cast<PackJob*>(dpa + pa.size());
+    if (!pt.empty()) CK(cudaMemcpyAsync(dpt, pt.data(), sizeof(F32Prob) * pt.size(), cudaMemcpyHostToDevice, st));
+    if (!pa.empty()) CK(cudaMemcpyAsync(dpa, pa.data(), sizeof(F32Prob) * pa.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dpj, pj.data(), sizeof(PackJob) * pj.size(), cudaMemcpyHostToDevice, st));
+    // the canonical tensors feed fp16x2 planes: FP32 products suffice
+    CK(launch_zgemm_f32_grouped(dpt, (int)pt.size(), ct, 1, 1, st));
+    CK(launch_zgemm_f32_grouped(dpa, (int)pa.size(), ca, 1, 0, st));
+    CK(launch_pack_compact_batch(dpj, (int)pj.size(), d, st));
+    for (int m = m0; m < m1; ++m)
+      for (int pi = 0; pi < 2; ++pi) {
+        gbsmps_mps::SiteGroups& G = M->sg[m];
+        if (canon_make_map(G.map[pi].data(), M->bpack.as<__half>() + G.boff[pi], G.Kp[pi], G.Np[pi]))
+          return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the packed tensors");
+      }
+    m0 = m1;
+  }
+  tab.release();
+  Tg.release();
+  Ag.release();
   return GBSMPS_OK;
 }
 
