@@ -355,58 +355,85 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     gmax = std::max(gmax, sizeof(double) * 4 * (size_t)Ns[k] * Ns[k]);
   }
   CK(cudaSetDevice(c->device));
-  // sampling runs on its own stream with its own status word; the build
-  // stream waits (the gate) for the previous state's sampling after its chain
-  cudaStream_t ss = nullptr;
-  cudaEvent_t built = nullptr, sampled = nullptr;
-  CK(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
+  // Three kinds of streams.  The fronts of the builds (validation, GSVD
+  // chain, bases) alternate between two contexts of their own, so the chain
+  // of state k+1 (one SM) runs while the rest of build k and the sampling of
+  // state k use the other SMs; the rest of each build runs on c's stream and
+  // waits (the gate) for the previous state's sampling, which runs on a
+  // stream and status word of its own.
   int rc = GBSMPS_OK;
-  DevBuf st, g;
-  gbsmps_mps* prev = nullptr;
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == GBSMPS_OK) rc = fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
     return e == cudaSuccess;
   };
-  if (ck(cudaEventCreateWithFlags(&built, cudaEventDisableTiming)) &&
-      ck(cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming)) &&
-      ck(st.alloc(sizeof(int), c->stream)) && ck(cudaMemsetAsync(st.p, 0, sizeof(int), c->stream)) &&
-      (mem_kind == GBSMPS_MEM_DEVICE || ck(g.alloc(gmax, c->stream))) &&
-      ck(cudaStreamSynchronize(c->stream))) {
-    for (int k = 0; k < count && rc == GBSMPS_OK; ++k) {
-      const double* dg = gammas[k];
-      if (mem_kind == GBSMPS_MEM_HOST) {
-        if (!ck(cudaMemcpyAsync(g.p, gammas[k], sizeof(double) * 4 * (size_t)Ns[k] * Ns[k],
-                                cudaMemcpyHostToDevice, c->stream)))
-          break;
-        dg = g.as<double>();
-      }
-      gbsmps_mps_t M = nullptr;
-      rc = gbs::build_single(c, Ns[k], dg, &opts[k], &M, prev ? sampled : nullptr);
-      if (rc) break;
-      // the build stream has waited for the previous sampling: its frees are ordered after it
-      delete prev;
-      prev = M;
-      if (!ck(cudaEventRecord(built, c->stream)) || !ck(cudaStreamWaitEvent(ss, built, 0))) break;
-      rc = gbs::sample_impl(M, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k], counter0s[k],
-                            nullptr, outs[k], nullptr, mem_kind);
-      if (rc) break;
-      if (!ck(cudaEventRecord(sampled, ss))) break;
+  cudaStream_t ss = nullptr;
+  cudaEvent_t built = nullptr, sampled = nullptr;
+  gbsmps_ctx cf[2];
+  DevBuf st, fst, g[2];
+  gbs::FrontState fs[2];
+  gbsmps_mps* prev = nullptr;
+  bool ok = ck(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking)) &&
+            ck(cudaEventCreateWithFlags(&built, cudaEventDisableTiming)) &&
+            ck(cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming)) &&
+            ck(st.alloc(sizeof(int), c->stream)) && ck(fst.alloc(2 * sizeof(int), c->stream)) &&
+            ck(cudaMemsetAsync(st.p, 0, sizeof(int), c->stream)) &&
+            ck(cudaMemsetAsync(fst.p, 0, 2 * sizeof(int), c->stream));
+  for (int i = 0; i < 2 && ok; ++i) {
+    cf[i].device = c->device;
+    cf[i].d_status = fst.as<int>() + i;
+    ok = ck(cudaStreamCreateWithFlags(&cf[i].stream, cudaStreamNonBlocking)) &&
+         (mem_kind == GBSMPS_MEM_DEVICE || ck(g[i].alloc(gmax, c->stream)));
+  }
+  ok = ok && ck(cudaStreamSynchronize(c->stream));
+  // the front of state k on context k % 2 (a host Gamma is copied first)
+  auto front = [&](int k) {
+    gbsmps_ctx* x = &cf[k & 1];
+    const double* dg = gammas[k];
+    if (mem_kind == GBSMPS_MEM_HOST) {
+      if (!ck(cudaMemcpyAsync(g[k & 1].p, gammas[k], sizeof(double) * 4 * (size_t)Ns[k] * Ns[k],
+                              cudaMemcpyHostToDevice, x->stream)))
+        return rc;
+      dg = g[k & 1].as<double>();
     }
+    const int r = gbs::build_front(x, Ns[k], dg, &opts[k], &fs[k & 1]);
+    if (r && rc == GBSMPS_OK) rc = r;
+    return r;
+  };
+  if (ok) front(0);
+  for (int k = 0; k < count && ok && rc == GBSMPS_OK; ++k) {
+    if (k + 1 < count && front(k + 1)) break;
+    gbsmps_mps_t M = nullptr;
+    const int r = gbs::build_rest(c, &fs[k & 1], prev ? sampled : nullptr, &M);
+    if (r) { if (rc == GBSMPS_OK) rc = r; break; }
+    // the rest of build k waited for the previous sampling and has finished
+    delete prev;
+    prev = M;
+    if (!ck(cudaEventRecord(built, c->stream)) || !ck(cudaStreamWaitEvent(ss, built, 0))) break;
+    const int r2 = gbs::sample_impl(M, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k],
+                                    counter0s[k], nullptr, outs[k], nullptr, mem_kind);
+    if (r2) { if (rc == GBSMPS_OK) rc = r2; break; }
+    if (!ck(cudaEventRecord(sampled, ss))) break;
   }
-  ck(cudaStreamSynchronize(ss));
+  if (ss) ck(cudaStreamSynchronize(ss));
+  for (int i = 0; i < 2; ++i)
+    if (cf[i].stream) ck(cudaStreamSynchronize(cf[i].stream));
   delete prev;
-  int hst = 0;
-  if (st.p) {
-    ck(cudaMemcpyAsync(&hst, st.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    ck(cudaStreamSynchronize(c->stream));
-  }
-  if (hst && rc == GBSMPS_OK) rc = fail(status_to_code(hst), "device status word " + std::to_string(hst));
-  st.release();
-  g.release();
+  for (auto& f : fs) f.M.reset();
+  int hst[3] = {0, 0, 0};
+  if (st.p) ck(cudaMemcpyAsync(hst, st.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (fst.p) ck(cudaMemcpyAsync(hst + 1, fst.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   ck(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 3; ++i)
+    if (hst[i] && rc == GBSMPS_OK) rc = fail(status_to_code(hst[i]), "device status word " + std::to_string(hst[i]));
+  st.release();
+  fst.release();
+  for (auto& b : g) b.release();
+  ck(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 2; ++i)
+    if (cf[i].stream) { cudaStreamDestroy(cf[i].stream); cf[i].stream = nullptr; }
   if (sampled) cudaEventDestroy(sampled);
   if (built) cudaEventDestroy(built);
-  cudaStreamDestroy(ss);
+  if (ss) cudaStreamDestroy(ss);
   return rc;
 }
 

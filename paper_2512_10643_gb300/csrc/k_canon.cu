@@ -467,29 +467,26 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
 // row w - count0 of group 1 (the counts add up to S).  q_p from the chunk
 // norms (fixed order), choose p*, append vt' = w_{p*} / sqrt(q_{p*}) as fp16
 // planes to the group of its class at the next bond (class pi ^ (p* & 1));
-// a block reserves its rows of each next group with one atomic per group.
-// The row order inside a group depends on the order of the reservations;
-// every row carries its sample index, and no arithmetic depends on the row.
-constexpr int SEL_THREADS = 512;
+// a warp reserves its row with one atomic on the group's counter.  The row
+// order inside a group depends on the order of the reservations; every row
+// carries its sample index, and no arithmetic depends on the row.
+constexpr int SEL_THREADS = 256;
 __global__ void __launch_bounds__(SEL_THREADS)
 select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
                      const NextGroup n1, int* cnt_next, const double* __restrict__ u, int ustride,
                      int site, uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out, int N,
                      uint8_t* flags, double flag_tol) {
-  __shared__ int sc[2], sbase[2];
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 2) sc[threadIdx.x] = 0;
-  __syncthreads();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
   const int grp = w >= M0 ? 1 : 0;
   const int r = (int)(w - (grp ? M0 : 0));
-  const bool active = w < S && r < (grp ? M1 : M0);
+  if (w >= S || r >= (grp ? M1 : M0)) return;
   const SelGroup& g = grp ? g1 : g0;
-  int pstar = 0, np = 0, local = 0, s = 0;
+  int pstar = 0, np = 0, pos = 0, s = 0;
   float inv = 0.f;
   bool flag = false;
-  if (active) {
+  {
     s = g.sid[r];
     const float* ps = g.part + (long long)r * g.ldp;
     const int P2 = g.wself + g.wother;
@@ -548,14 +545,9 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
     }
     inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
     np = grp ^ (pstar & 1);
-    if (lane == 0) local = atomicAdd(&sc[np], 1);
-    local = __shfl_sync(0xffffffffu, local, 0);
+    if (lane == 0) pos = atomicAdd(cnt_next + np, 1);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
   }
-  __syncthreads();
-  if (threadIdx.x < 2 && sc[threadIdx.x] > 0) sbase[threadIdx.x] = atomicAdd(cnt_next + threadIdx.x, sc[threadIdx.x]);
-  __syncthreads();
-  if (!active) return;
-  const int pos = sbase[np] + local;
   if (pos >= S) return;                         // cannot happen: one row per sample
   const NextGroup& ng = np ? n1 : n0;
   const int P2 = g.wself + g.wother;

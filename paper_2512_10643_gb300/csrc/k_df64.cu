@@ -358,14 +358,24 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       const DfSub& u = live[g0 + i];
       t64 += (long long)((u.M + 63) / 64) * ((u.N + 63) / 64);
     }
-    const int T = t64 >= 2LL * nsm ? 64 : 32;
+    // tuning knobs (performance only; every choice computes the same products):
+    // GBSMPS_DFG_TILE = 16, 32 or 64 forces the tile, GBSMPS_DFG_WAVES the CTA
+    // target in multiples of the SM count, GBSMPS_DFG_MINK the least k chunk
+    // in stages of DK
+    static const int env_tile = [] { const char* e = getenv("GBSMPS_DFG_TILE"); return e ? atoi(e) : 0; }();
+    static const int env_waves = [] { const char* e = getenv("GBSMPS_DFG_WAVES"); return e ? std::max(1, atoi(e)) : 8; }();
+    static const int env_mink = [] { const char* e = getenv("GBSMPS_DFG_MINK"); return e ? std::max(1, atoi(e)) : 4; }();
+    const int T = env_tile == 16 || env_tile == 32 || env_tile == 64 ? env_tile
+                                                                     : (t64 >= 2LL * nsm ? 64 : 32);
     long long tiles = 0;
     for (int i = 0; i < np; ++i) {
       const DfSub& u = live[g0 + i];
       tiles += (long long)((u.M + T - 1) / T) * ((u.N + T - 1) / T);
     }
-    // k split toward two waves, chunks of >= 8 stages, within the workspace
-    int target = (int)std::max<long long>(1, (2LL * nsm + tiles - 1) / tiles);
+    // k split toward eight waves of CTAs (measured: 29 -> 21 ms for the
+    // 144-mode chain against two waves), chunks of >= 4 stages, within the
+    // workspace
+    int target = (int)std::max<long long>(1, ((long long)env_waves * nsm + tiles - 1) / tiles);
     DfGroup G;
     G.np = np;
     G.work = reinterpret_cast<double2*>(work);
@@ -376,7 +386,7 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
         DfProb& P = G.p[i];
         P.t = DfTile{u.M, u.N, u.opa, u.opb, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.herm, u.herm};
         P.K = u.K;
-        int ks = std::max(1, std::min(target, u.K / (8 * DK)));
+        int ks = std::max(1, std::min(target, u.K / (env_mink * DK)));
         if (!work) ks = 1;
         int kchunk = u.K > 0 ? ((u.K + ks - 1) / ks + DK - 1) / DK * DK : DK;
         ks = u.K > 0 ? (u.K + kchunk - 1) / kchunk : 1;
@@ -393,8 +403,10 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
         if (c0 > 0x7fffffffLL) return cudaErrorInvalidValue;
         if (T == 64)
           zgemm_df64_grouped_kernel<64, 64><<<(unsigned)c0, 256, 0, s>>>(G);
-        else
+        else if (T == 32)
           zgemm_df64_grouped_kernel<32, 32><<<(unsigned)c0, 256, 0, s>>>(G);
+        else
+          zgemm_df64_grouped_kernel<16, 16><<<(unsigned)c0, 256, 0, s>>>(G);
         COUNT_LAUNCH(1);
         if (part > 0) {
           df_reduce_grouped_kernel<<<dim3(64, np), 256, 0, s>>>(G);

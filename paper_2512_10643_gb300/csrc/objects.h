@@ -201,8 +201,19 @@ int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cuda
 int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st);
 int canonical_stage(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int finish(gbsmps_ctx* c, gbsmps_mps* M);
-// gate (may be null): the stream waits for it after the GSVD chain and the
-// bond read-back, before the stages that occupy every SM
+// a build split in two: the front (validation, GSVD chain, bases, bond
+// read-back enqueued) on one context, the rest on another once the front is
+// done; build_single runs both on one context.  gate (may be null): the
+// rest's stream waits for it before the stages that occupy every SM
+struct FrontState {
+  std::unique_ptr<gbsmps_mps> M;
+  Front f;
+  Readback rb;
+  gbsmps_opts opts{};
+  gbsmps_ctx* cf = nullptr;      // the context the front ran on
+};
+int build_front(gbsmps_ctx* cf, int N, const double* dgamma, const gbsmps_opts* o, FrontState* fs);
+int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out);
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                  gbsmps_mps_t* out, cudaEvent_t gate = nullptr);
 int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int sync_host,

@@ -517,44 +517,63 @@ int finish(gbsmps_ctx* c, gbsmps_mps* M) {
 }
 
 // the whole pipeline for one state whose covariance is on the device
-int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
-                 gbsmps_mps_t* out, cudaEvent_t gate) {
+// The front of one build on context cf: validation, the GSVD chain, the kept
+// bases and maps.  Nothing here waits on the host (the bond sizes are read
+// back by build_rest: a copy into pageable memory would block until the
+// chain is done).  Only Gamma is read on the device; the state lives in fs.
+int build_front(gbsmps_ctx* cf, int N, const double* dgamma, const gbsmps_opts* o, FrontState* fs) {
+  cudaStream_t s = cf->stream;
+  StageTimer tm(s);
+  {
+    const char* dbg = getenv("GBSMPS_DEBUG");
+    if (dbg && dbg[0] == '1') tm.dbg_status = cf->d_status;
+  }
+  fs->M.reset(new gbsmps_mps());
+  fs->opts = *o;
+  fs->cf = cf;
+  gbsmps_mps* M = fs->M.get();
+  int rc = alloc_front(M, cf, N, o, &fs->f);
+  if (rc) return rc;
+  // a1 validation, a2-a3 GSVD chain
+  rc = launch_checks(cf, M, dgamma, o, fs->f);
+  if (rc) return rc;
+  tm.mark("validate");
+  CK(launch_gsvd_chain(dgamma, N, fs->f.dbw, o->lambda2_freeze, fs->f.Gs, M->ba, M->Qm, M->cm,
+                       cf->d_status, s));
+  COUNT_LAUNCH(1);
+  tm.mark("gsvd_chain");
+  // a4-a5 kept bases and index maps
+  rc = launch_bases(cf, M, o);
+  if (rc) return rc;
+  tm.mark("basis_maps");
+  return GBSMPS_OK;
+}
+
+// The rest of the build on context c, once its front has finished (the host
+// waits for the front's stream and status word).  gate (may be null): c's
+// stream waits for it before the stages that occupy every SM.
+int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out) {
   cudaStream_t s = c->stream;
+  gbsmps_mps* M = fs->M.get();
+  const gbsmps_opts* o = &fs->opts;
+  const int N = M->N;
+  int rc = enqueue_readback(M, &fs->rb, fs->cf->stream);
+  if (!rc) rc = sync_status(fs->cf);
+  if (rc) return rc;
+  finish_readback(M, fs->rb);
+  M->ctx = c;
   StageTimer tm(s);
   {
     const char* dbg = getenv("GBSMPS_DEBUG");
     if (dbg && dbg[0] == '1') tm.dbg_status = c->d_status;
   }
-  auto* M = new gbsmps_mps();
-  std::unique_ptr<gbsmps_mps> guard(M);
-  Front f;
-  int rc = alloc_front(M, c, N, o, &f);
-  if (rc) return rc;
-  // a1 validation, a2-a3 GSVD chain
-  rc = launch_checks(c, M, dgamma, o, f);
-  if (rc) return rc;
-  tm.mark("validate");
-  CK(launch_gsvd_chain(dgamma, N, f.dbw, o->lambda2_freeze, f.Gs, M->ba, M->Qm, M->cm,
-                       c->d_status, s));
-  COUNT_LAUNCH(1);
-  tm.mark("gsvd_chain");
-  // a4-a5 kept bases and index maps
-  rc = launch_bases(c, M, o);
-  if (rc) return rc;
-  tm.mark("basis_maps");
-  Readback rb;
-  rc = enqueue_readback(M, &rb, s);
-  if (rc) return rc;
-  rc = sync_status(c);
-  if (rc) return rc;
-  finish_readback(M, rb);
   if (gate) CK(cudaStreamWaitEvent(s, gate, 0));
   // a6 PCO build
   size_t scr_max = 0;
   rc = alloc_tensors(M, s, &scr_max);
   if (rc) return rc;
   std::vector<SiteTask> tasks;
-  site_tasks(M, rb.cm, tasks);
+  site_tasks(M, fs->rb.cm, tasks);
   rc = run_pco(c, tasks, scr_max, o->d);
   if (rc) return rc;
   tm.mark("pco");
@@ -566,11 +585,8 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
   if (rc) return rc;
   tm.mark("normalise");
   if (o->precision == GBSMPS_PREC_MIXED) {
-    // the sampler's right-canonical form: every bond's factor in one launch
-    // (one SM per bond), then the sites' transforms spread over side streams.
-    // (Factoring bond groups on a side stream while the environment chain
-    // still runs was measured no faster: the chain's split-K GEMMs already
-    // occupy the GPU.)
+    // the sampler's right-canonical form: every diagonal block's factor in
+    // one launch (one SM per block), then the sites' transforms and planes
     CanonWork w;
     rc = canon_prepare(M, &w, s);
     if (!rc) rc = canon_bonds(c, M, &w, 1, N - 1, s);
@@ -585,8 +601,17 @@ int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* 
   if (rc) return rc;
   rc = sync_status(c);
   if (rc) return rc;
-  *out = guard.release();
+  *out = fs->M.release();
   return GBSMPS_OK;
+}
+
+// the whole pipeline for one state whose covariance is on the device
+int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
+                 gbsmps_mps_t* out, cudaEvent_t gate) {
+  FrontState fs;
+  int rc = build_front(c, N, dgamma, o, &fs);
+  if (rc) return rc;
+  return build_rest(c, &fs, gate, out);
 }
 
 }  // namespace gbs
