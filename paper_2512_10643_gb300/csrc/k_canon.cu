@@ -19,7 +19,8 @@
 // accumulators in tensor memory.  The kernel is persistent and
 // warp-specialised: one thread issues TMA loads of 128 x 64 tiles of both
 // planes (128-byte swizzle) into a three-stage ring, one thread issues the
-// MMAs (M = N = 128, K = 16), and four epilogue warps drain the other of two
+// MMAs (M = N = 128, K = 16), and eight epilogue warps (two per lane quadrant
+// of tensor memory, each with half the columns) drain the other of two
 // accumulator buffers (tcgen05.ld, W = hh + 2^-11 x, per-tile row norms,
 // rows transposed through shared memory into 128-byte coalesced stores), so
 // the epilogue of one tile overlaps the MMAs of the next.  Every wait on an
@@ -39,8 +40,8 @@ constexpr int NPL = 2;                            // fp16 planes per operand: h,
 constexpr int TSTAGES = 3;
 constexpr int PLANE_BYTES = TBM * TBK * 2;        // 16 KB (TBN == TBM)
 constexpr int STAGE_BYTES = 2 * NPL * PLANE_BYTES;
-constexpr int EPI_WARPS = 4;
-constexpr int EPI_LD = 36;                        // floats per staged row: 16-byte rows, no bank conflicts
+constexpr int EPI_WARPS = 8;                      // two per TMEM lane quadrant
+constexpr int EPI_LD = 20;                        // floats per staged row (16 columns + pad, 16-byte rows)
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_LD * 4;
 constexpr int NBAR = 2 * TSTAGES + 2 + 2 + 1;     // full, empty, acc full, acc empty, drain
 constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
@@ -279,6 +280,7 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
     }
   } else {                                            // epilogue warps
     const int q = warp & 3;                           // TMEM lanes 32q .. 32q + 31
+    const int cb = ((warp - 2) >> 2) * (TBN / 2);     // this warp's half of the columns
     float* stg = epi + (warp - 2) * 32 * EPI_LD;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
@@ -297,7 +299,7 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
       const int nb = tr.nb, n0 = nb * TBN;
       const int rbase = tr.m0 + q * 32;
 #pragma unroll 1
-      for (int c0 = 0; c0 < TBN; c0 += 32) {
+      for (int c0 = cb; c0 < cb + TBN / 2; c0 += 32) {
         float nrm = 0.f;
         uint32_t h[32], x[32];
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * TBN + c0);
@@ -305,24 +307,29 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
         tmem_ld32(ta + TBN, x);
         float4* srow = reinterpret_cast<float4*>(stg + lane * EPI_LD);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float v[4];
+        for (int hf = 0; hf < 2; ++hf) {                // 16 columns at a time through shared memory
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            v[e] = fmaf(LO_INV, __uint_as_float(x[4 * j + e]), __uint_as_float(h[4 * j + e]));
-            nrm = fmaf(v[e], v[e], nrm);
+          for (int j = 0; j < 4; ++j) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 16 * hf + 4 * j + e;
+              v[e] = fmaf(LO_INV, __uint_as_float(x[k]), __uint_as_float(h[k]));
+              nrm = fmaf(v[e], v[e], nrm);
+            }
+            srow[j] = make_float4(v[0], v[1], v[2], v[3]);
           }
-          srow[j] = make_float4(v[0], v[1], v[2], v[3]);
-        }
-        __syncwarp();
+          __syncwarp();
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int r = it * 4 + (lane >> 3), c4 = lane & 7;
-          const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + c4 * 4);
-          if (rbase + r < M)
-            *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + c4 * 4) = val;
+          for (int it = 0; it < 4; ++it) {
+            const int r = it * 8 + (lane >> 2), c4 = lane & 3;
+            const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + c4 * 4);
+            if (rbase + r < M)
+              *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + 16 * hf + c4 * 4) =
+                  val;
+          }
+          __syncwarp();
         }
-        __syncwarp();
         if (rbase + lane < M) gg.part[(long long)(rbase + lane) * gg.ldp + (n0 + c0) / 32] = nrm;
       }
       tc_fence_before();
@@ -499,13 +506,15 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
       if (p < d) {
         const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
         const int nch = ((p & 1) ? g.wother : g.wself) / 16;
-        for (int t = 0; t < nch; ++t) q += ps[c0 + t];
+#pragma unroll 8
+        for (int t = 0; t < nch; ++t) q += ps[c0 + t];   // independent loads, fixed order
       }
       return q;
     };
+    const float q0 = qp(lane);                    // p = lane: both passes reuse it
     float Z = 0.f;
     for (int c0 = 0; c0 < d; c0 += 32) {
-      float C = qp(c0 + lane);
+      float C = c0 == 0 ? q0 : qp(c0 + lane);
       for (int o = 1; o < 32; o <<= 1) {
         const float y = __shfl_up_sync(0xffffffffu, C, o);
         if (lane >= o) C += y;
@@ -520,7 +529,7 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
     pstar = -1;
     for (int c0 = 0; c0 < d; c0 += 32) {
       const int p = c0 + lane;
-      const float q = qp(p);
+      const float q = c0 == 0 ? q0 : qp(p);
       float C = q;
       for (int o = 1; o < 32; o <<= 1) {
         const float y = __shfl_up_sync(0xffffffffu, C, o);
