@@ -520,7 +520,7 @@ def main():
     sm = sorted(r["step_ms"])
     if r["pipelined"]:
         cfg["pipeline"] = ("one stream of steps: the next state's Gaussian-SVD chain (one SM) runs "
-                           "beside the rest of the current build and its sampling (the other SMs); "
+                           "and the next environments run beside the current sampling (the other SMs); "
                            "latency_ms is one state alone, build + sampling")
     line = dict(base, value=round(r["value"], 3), ms_per_step=round(r["ms_per_step"], 3),
                 dtype=("f64 gsvd/pco + df64 env + fp16x2 (3 products)/fp32 tensor-core sampling"

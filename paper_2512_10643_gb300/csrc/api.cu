@@ -355,84 +355,102 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     gmax = std::max(gmax, sizeof(double) * 4 * (size_t)Ns[k] * Ns[k]);
   }
   CK(cudaSetDevice(c->device));
-  // Three kinds of streams.  The fronts of the builds (validation, GSVD
-  // chain, bases) alternate between two contexts of their own, so the chain
-  // of state k+1 (one SM) runs while the rest of build k and the sampling of
-  // state k use the other SMs; the rest of each build runs on c's stream and
-  // waits (the gate) for the previous state's sampling, which runs on a
-  // stream and status word of its own.
+  // Per state the build runs in four parts: the front (validation, GSVD
+  // chain on one SM, bases) on one of three contexts of its own, launched two
+  // states ahead; then on c's stream the PCO build (long CTAs), the
+  // environments (short CTAs) and the canonical form.  Iteration k runs
+  // PCO(k+1), then the sampling of state k (its own stream, high priority,
+  // own status word) beside the environments of state k+1, then the
+  // canonical form of state k+1 once sampling k is done.  So neither the
+  // PCO's nor the factors' long CTAs ever share the GPU with the sampler's
+  // persistent GEMM, the environment chain (latency-bound on the FP32 pipes)
+  // fills what the sampler leaves, and the chain hides behind both.
   int rc = GBSMPS_OK;
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == GBSMPS_OK) rc = fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
     return e == cudaSuccess;
   };
+  constexpr int NF = 3;
   cudaStream_t ss = nullptr;
-  cudaEvent_t built = nullptr, sampled = nullptr;
-  gbsmps_ctx cf[2];
-  DevBuf st, fst, g[2];
-  gbs::FrontState fs[2];
-  gbsmps_mps* prev = nullptr;
-  bool ok = ck(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking)) &&
-            ck(cudaEventCreateWithFlags(&built, cudaEventDisableTiming)) &&
+  cudaEvent_t pco_done = nullptr, sampled = nullptr;
+  gbsmps_ctx cf[NF];
+  DevBuf st, fst, g[NF];
+  gbs::FrontState fs[NF];
+  gbsmps_mps* cur = nullptr;
+  int lo = 0, hi = 0;
+  bool ok = ck(cudaDeviceGetStreamPriorityRange(&lo, &hi)) &&
+            ck(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, hi)) &&
+            ck(cudaEventCreateWithFlags(&pco_done, cudaEventDisableTiming)) &&
             ck(cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming)) &&
-            ck(st.alloc(sizeof(int), c->stream)) && ck(fst.alloc(2 * sizeof(int), c->stream)) &&
+            ck(st.alloc(sizeof(int), c->stream)) && ck(fst.alloc(NF * sizeof(int), c->stream)) &&
             ck(cudaMemsetAsync(st.p, 0, sizeof(int), c->stream)) &&
-            ck(cudaMemsetAsync(fst.p, 0, 2 * sizeof(int), c->stream));
-  for (int i = 0; i < 2 && ok; ++i) {
+            ck(cudaMemsetAsync(fst.p, 0, NF * sizeof(int), c->stream));
+  for (int i = 0; i < NF && ok; ++i) {
     cf[i].device = c->device;
     cf[i].d_status = fst.as<int>() + i;
     ok = ck(cudaStreamCreateWithFlags(&cf[i].stream, cudaStreamNonBlocking)) &&
          (mem_kind == GBSMPS_MEM_DEVICE || ck(g[i].alloc(gmax, c->stream)));
   }
   ok = ok && ck(cudaStreamSynchronize(c->stream));
-  // the front of state k on context k % 2 (a host Gamma is copied first)
+  auto keep = [&](int r) {
+    if (r && rc == GBSMPS_OK) rc = r;
+    return r == GBSMPS_OK;
+  };
+  // the front of state k on context k % NF (a host Gamma is copied first)
   auto front = [&](int k) {
-    gbsmps_ctx* x = &cf[k & 1];
+    gbsmps_ctx* x = &cf[k % NF];
     const double* dg = gammas[k];
     if (mem_kind == GBSMPS_MEM_HOST) {
-      if (!ck(cudaMemcpyAsync(g[k & 1].p, gammas[k], sizeof(double) * 4 * (size_t)Ns[k] * Ns[k],
+      if (!ck(cudaMemcpyAsync(g[k % NF].p, gammas[k], sizeof(double) * 4 * (size_t)Ns[k] * Ns[k],
                               cudaMemcpyHostToDevice, x->stream)))
-        return rc;
-      dg = g[k & 1].as<double>();
+        return false;
+      dg = g[k % NF].as<double>();
     }
-    const int r = gbs::build_front(x, Ns[k], dg, &opts[k], &fs[k & 1]);
-    if (r && rc == GBSMPS_OK) rc = r;
-    return r;
+    return keep(gbs::build_front(x, Ns[k], dg, &opts[k], &fs[k % NF]));
   };
-  if (ok) front(0);
-  for (int k = 0; k < count && ok && rc == GBSMPS_OK; ++k) {
-    if (k + 1 < count && front(k + 1)) break;
-    gbsmps_mps_t M = nullptr;
-    const int r = gbs::build_rest(c, &fs[k & 1], prev ? sampled : nullptr, &M);
-    if (r) { if (rc == GBSMPS_OK) rc = r; break; }
-    // the rest of build k waited for the previous sampling and has finished
-    delete prev;
-    prev = M;
-    if (!ck(cudaEventRecord(built, c->stream)) || !ck(cudaStreamWaitEvent(ss, built, 0))) break;
-    const int r2 = gbs::sample_impl(M, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k],
-                                    counter0s[k], nullptr, outs[k], nullptr, mem_kind);
-    if (r2) { if (rc == GBSMPS_OK) rc = r2; break; }
+  if (ok) ok = front(0) && (count < 2 || front(1));
+  // state 0 alone
+  if (ok) ok = keep(gbs::rest_pco(c, &fs[0], nullptr)) && keep(gbs::rest_env(c, &fs[0])) &&
+               keep(gbs::rest_canon(c, &fs[0], nullptr, &cur));
+  for (int k = 0; k < count && ok; ++k) {
+    // state k is built; state k-1's sampling finished before it was handed over
+    if (k + 2 < count && !front(k + 2)) break;
+    if (k + 1 < count && !keep(gbs::rest_pco(c, &fs[(k + 1) % NF], nullptr))) break;
+    // the sampling starts after PCO(k+1): no long CTA beside the sampler
+    if (!ck(cudaEventRecord(pco_done, c->stream)) || !ck(cudaStreamWaitEvent(ss, pco_done, 0))) break;
+    if (!keep(gbs::sample_impl(cur, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k],
+                               counter0s[k], nullptr, outs[k], nullptr, mem_kind)))
+      break;
     if (!ck(cudaEventRecord(sampled, ss))) break;
+    gbsmps_mps_t next = nullptr;
+    if (k + 1 < count) {
+      if (!keep(gbs::rest_env(c, &fs[(k + 1) % NF]))) break;                 // beside sampling k
+      if (!keep(gbs::rest_canon(c, &fs[(k + 1) % NF], sampled, &next))) break;  // after it
+    }
+    // rest_canon waited for sampling k (and synchronised); the last one is awaited here
+    if (k + 1 == count && !ck(cudaStreamSynchronize(ss))) break;
+    delete cur;
+    cur = next;
   }
   if (ss) ck(cudaStreamSynchronize(ss));
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < NF; ++i)
     if (cf[i].stream) ck(cudaStreamSynchronize(cf[i].stream));
-  delete prev;
+  delete cur;
   for (auto& f : fs) f.M.reset();
-  int hst[3] = {0, 0, 0};
+  int hst[1 + NF] = {0};
   if (st.p) ck(cudaMemcpyAsync(hst, st.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  if (fst.p) ck(cudaMemcpyAsync(hst + 1, fst.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (fst.p) ck(cudaMemcpyAsync(hst + 1, fst.p, NF * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   ck(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 1 + NF; ++i)
     if (hst[i] && rc == GBSMPS_OK) rc = fail(status_to_code(hst[i]), "device status word " + std::to_string(hst[i]));
   st.release();
   fst.release();
   for (auto& b : g) b.release();
   ck(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < NF; ++i)
     if (cf[i].stream) { cudaStreamDestroy(cf[i].stream); cf[i].stream = nullptr; }
   if (sampled) cudaEventDestroy(sampled);
-  if (built) cudaEventDestroy(built);
+  if (pco_done) cudaEventDestroy(pco_done);
   if (ss) cudaStreamDestroy(ss);
   return rc;
 }

@@ -214,6 +214,11 @@ struct FrontState {
 };
 int build_front(gbsmps_ctx* cf, int N, const double* dgamma, const gbsmps_opts* o, FrontState* fs);
 int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out);
+// the rest in its three parts: PCO (long CTAs), environments (short CTAs:
+// may run beside a sampling), canonical form + hand-over
+int rest_pco(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate);
+int rest_env(gbsmps_ctx* c, FrontState* fs);
+int rest_canon(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out);
 int build_single(gbsmps_ctx* c, int N, const double* dgamma, const gbsmps_opts* o,
                  gbsmps_mps_t* out, cudaEvent_t gate = nullptr);
 int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int sync_host,

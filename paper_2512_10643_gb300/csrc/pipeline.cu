@@ -516,7 +516,6 @@ int finish(gbsmps_ctx* c, gbsmps_mps* M) {
   return GBSMPS_OK;
 }
 
-// the whole pipeline for one state whose covariance is on the device
 // The front of one build on context cf: validation, the GSVD chain, the kept
 // bases and maps.  Nothing here waits on the host (the bond sizes are read
 // back by build_rest: a copy into pageable memory would block until the
@@ -549,24 +548,20 @@ int build_front(gbsmps_ctx* cf, int N, const double* dgamma, const gbsmps_opts* 
   return GBSMPS_OK;
 }
 
-// The rest of the build on context c, once its front has finished (the host
-// waits for the front's stream and status word).  gate (may be null): c's
-// stream waits for it before the stages that occupy every SM.
-int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out) {
+// The rest of the build on context c, once its front has finished, in three
+// parts that the stream entry point schedules around the sampling of the
+// previous state.  (a) the bond read-back (the host waits for the front's
+// stream and status word), the tensors and the PCO build: long FP64 CTAs.
+// gate (may be null): c's stream waits for it first.
+int rest_pco(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate) {
   cudaStream_t s = c->stream;
   gbsmps_mps* M = fs->M.get();
-  const gbsmps_opts* o = &fs->opts;
-  const int N = M->N;
   int rc = enqueue_readback(M, &fs->rb, fs->cf->stream);
   if (!rc) rc = sync_status(fs->cf);
   if (rc) return rc;
   finish_readback(M, fs->rb);
   M->ctx = c;
   StageTimer tm(s);
-  {
-    const char* dbg = getenv("GBSMPS_DEBUG");
-    if (dbg && dbg[0] == '1') tm.dbg_status = c->d_status;
-  }
   if (gate) CK(cudaStreamWaitEvent(s, gate, 0));
   // a6 PCO build
   size_t scr_max = 0;
@@ -574,22 +569,40 @@ int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* ou
   if (rc) return rc;
   std::vector<SiteTask> tasks;
   site_tasks(M, fs->rb.cm, tasks);
-  rc = run_pco(c, tasks, scr_max, o->d);
+  rc = run_pco(c, tasks, scr_max, fs->opts.d);
   if (rc) return rc;
   tm.mark("pco");
-  // a7 environments and normalisation
-  rc = env_single(c, M, tm);
+  return GBSMPS_OK;
+}
+
+// (b) the energy gauge, the environments and the normalisation: short CTAs
+// only, so this part may run beside the sampling of another state
+int rest_env(gbsmps_ctx* c, FrontState* fs) {
+  gbsmps_mps* M = fs->M.get();
+  StageTimer tm(c->stream);
+  int rc = env_single(c, M, tm);
   if (rc) return rc;
   tm.mark("environments");
   rc = normalise_single(c, M);
   if (rc) return rc;
   tm.mark("normalise");
-  if (o->precision == GBSMPS_PREC_MIXED) {
-    // the sampler's right-canonical form: every diagonal block's factor in
-    // one launch (one SM per block), then the sites' transforms and planes
+  return GBSMPS_OK;
+}
+
+// (c) the sampler's right-canonical form (factors of the diagonal blocks,
+// one CTA per block, then the transforms and planes), then the host waits
+// for c's stream and hands the MPS over.  gate (may be null): c's stream
+// waits for it first.
+int rest_canon(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out) {
+  cudaStream_t s = c->stream;
+  gbsmps_mps* M = fs->M.get();
+  StageTimer tm(s);
+  if (gate) CK(cudaStreamWaitEvent(s, gate, 0));
+  int rc = GBSMPS_OK;
+  if (fs->opts.precision == GBSMPS_PREC_MIXED) {
     CanonWork w;
     rc = canon_prepare(M, &w, s);
-    if (!rc) rc = canon_bonds(c, M, &w, 1, N - 1, s);
+    if (!rc) rc = canon_bonds(c, M, &w, 1, M->N - 1, s);
     if (rc) return rc;
     canon_report(M, &w, tm, s);
     tm.mark("cholesky");
@@ -603,6 +616,13 @@ int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* ou
   if (rc) return rc;
   *out = fs->M.release();
   return GBSMPS_OK;
+}
+
+int build_rest(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate, gbsmps_mps_t* out) {
+  int rc = rest_pco(c, fs, gate);
+  if (!rc) rc = rest_env(c, fs);
+  if (!rc) rc = rest_canon(c, fs, nullptr, out);
+  return rc;
 }
 
 // the whole pipeline for one state whose covariance is on the device
