@@ -32,9 +32,10 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# DRAM bytes per launch of the dominant kernel at 100,000 samples from an ncu
-# capture of the current kernel (None until one is taken)
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one launch of the dominant kernel at 100,000
+# samples, central site: ncu capture at full size (one pass),
+# profiles/canon_gemm_tc_n144_d6_chi256.md
+TRAFFIC_BYTES_PER_LAUNCH = 106052864 + 630772480
 
 
 def parse():
@@ -258,6 +259,13 @@ def run_gpu(args, rank, local, ws, dist):
             "split_products": 3,
             "issued_fp16_tflops": round(3 * ach_tflops, 3),
             "issued_frac": round(3 * ach_tflops / peak, 5)}
+    if roof["traffic"] is not None and tr["ms"] > 0:
+        # the same launches against the HBM roof (the W stores dominate)
+        hbm, hsrc = peaks.get("hbm_gbs", 6800.0), src
+        gbs = roof["traffic"] / (tr["ms"] / n_launch / 1e3) / 1e9
+        roof["dram_gbs"] = round(gbs, 1)
+        roof["dram_frac"] = round(gbs / hbm, 4)
+        roof["dram_peak_source"] = f"hbm_gbs of {hsrc} MEASURED_PEAKS.json"
 
     # build-only throughput and the FP64 GPU path for comparison
     res = {}

@@ -311,10 +311,6 @@ struct DfSub {
 };
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes);
-cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
-                              long long sA, const double2* B, long long ldb, long long sB,
-                              double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
-                              void* work = nullptr, size_t work_bytes = 0, int herm = 0);
 // herm: C (square) is Hermitian; only i >= j is computed, C[j][i] = conj(C[i][j])
 // one state of the batched persistent environment chain (device pointers)
 struct EnvJob {

@@ -9,8 +9,11 @@
 // e = fma(ah, bh, -p) + ah bl + al bh) and adds it with Knuth's TwoSum.
 // Operands are read in FP64 and split into (hi, lo) on the way to shared
 // memory; partial sums over k-chunks (split-K, for parallelism in the short
-// sequential products) are written as FP64 and reduced in FP64.
-// Tile: 64 x 64 complex outputs, 8 complex k per stage, 256 threads of 4 x 4.
+// sequential products) are written as FP64 and reduced in FP64.  Tiles of
+// TM x TN complex outputs (16 to 64 square), 8 complex k per stage, 256
+// threads.  Two drivers: a grouped launch of many independent products (one
+// environment step of one state on its parity blocks), and a persistent
+// cooperative kernel that runs the whole chains of a batch of states.
 #include "internal.h"
 #include <algorithm>
 #include <cooperative_groups.h>
@@ -22,11 +25,9 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int DM = 64, DN = 64, DK = 8;
+constexpr int DK = 8;                         // k per shared-memory stage
 
 struct Df { float h, l; };
-
-inline int pow2i(long long x) { int r = 0; while ((1LL << r) < x) ++r; return r; }
 
 __device__ __forceinline__ void df_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
   const float p = xh * yh;
@@ -46,16 +47,6 @@ __device__ __forceinline__ Df df_split(double x) {
   r.l = (float)(x - (double)r.h);
   return r;
 }
-
-struct DfArgs {
-  int M, N, K, opa, opb;
-  int herm;                     // C is Hermitian: compute i >= j, mirror the rest
-  const double2* A; long long lda, sA;
-  const double2* B; long long ldb, sB;
-  double2* C; long long ldc, sC;
-  int ksplit, kchunk;
-  double2* part;
-};
 
 // one 64 x 64 complex output tile of C = op(A) op(B) over k in [kbeg, kend),
 // written to C[gi * ldc + gj] (the whole CTA calls it together)
@@ -158,22 +149,6 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
       p.C[(long long)gi * p.ldc + gj] = v;
     }
   }
-}
-
-template <int TM, int TN>
-__global__ void __launch_bounds__(256) zgemm_df64_kernel(DfArgs p) {
-  // re/im, hi/lo split operands
-  // rows padded by one 16-byte element: the k-major fills of A (and of B^dag)
-  // then fall into different banks
-  __shared__ __align__(16) float As[DK][TM + 1][4];
-  __shared__ __align__(16) float Bs[DK][TN + 1][4];
-  const long long bz = blockIdx.z / p.ksplit;
-  const int kz = blockIdx.z % p.ksplit;
-  const int kbeg = kz * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
-  DfTile t{p.M, p.N, p.opa, p.opb, p.A + bz * p.sA, p.lda, p.B + bz * p.sB, p.ldb,
-           p.ksplit > 1 ? p.part + (long long)blockIdx.z * p.M * p.N : p.C + bz * p.sC,
-           p.ksplit > 1 ? (long long)p.N : p.ldc, p.herm, p.ksplit > 1 ? 0 : 1};
-  df_tile<TM, TN>(t, blockIdx.y * TM, blockIdx.x * TN, kbeg, kend, As, Bs);
 }
 
 // Many independent products C_i = op(A_i) op(B_i) in one launch (the blocks
@@ -295,46 +270,8 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
   }
 }
 
-__global__ void df_reduce_kernel(const double2* __restrict__ part, int ksplit, int batch, int M,
-                                 int N, double2* C, long long ldc, long long sC, int herm) {
-  const long long n = (long long)batch * M * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long b = i / ((long long)M * N), r = (i / N) % M, c = i % N;
-    if (herm && r < c) continue;
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < ksplit; ++k) s = cadd(s, part[((b * ksplit + k) * M + r) * N + c]);
-    C[b * sC + r * ldc + c] = s;
-    if (herm && r > c) C[b * sC + c * ldc + r] = cconj(s);
-  }
-}
-
 }  // namespace
 
-namespace {
-
-cudaError_t df64_launch(int cfg, const DfArgs& a, int batch, cudaStream_t s) {
-  const int M = a.M, N = a.N, z = batch * a.ksplit;
-  switch (cfg) {
-    case 0:
-      zgemm_df64_kernel<64, 64><<<dim3((N + 63) / 64, (M + 63) / 64, z), 256, 0, s>>>(a);
-      break;
-    case 1:
-      zgemm_df64_kernel<32, 64><<<dim3((N + 63) / 64, (M + 31) / 32, z), 256, 0, s>>>(a);
-      break;
-    default:
-      zgemm_df64_kernel<32, 32><<<dim3((N + 31) / 32, (M + 31) / 32, z), 256, 0, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
-// tile shape per problem class (op pair and power-of-two buckets of M, N, K,
-// batch), measured on the first call of the class; every shape gives the same
-// result because the k split and each output's k order do not depend on it
-std::mutex g_df_mu;
-std::map<std::array<int, 6>, int> g_df_tune;
-
-}  // namespace
 
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes) {
@@ -358,24 +295,31 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       const DfSub& u = live[g0 + i];
       t64 += (long long)((u.M + 63) / 64) * ((u.N + 63) / 64);
     }
-    // tuning knobs (performance only; every choice computes the same products):
-    // GBSMPS_DFG_TILE = 16, 32 or 64 forces the tile, GBSMPS_DFG_WAVES the CTA
-    // target in multiples of the SM count, GBSMPS_DFG_MINK the least k chunk
-    // in stages of DK
-    static const int env_tile = [] { const char* e = getenv("GBSMPS_DFG_TILE"); return e ? atoi(e) : 0; }();
-    static const int env_waves = [] { const char* e = getenv("GBSMPS_DFG_WAVES"); return e ? std::max(1, atoi(e)) : 8; }();
-    static const int env_mink = [] { const char* e = getenv("GBSMPS_DFG_MINK"); return e ? std::max(1, atoi(e)) : 4; }();
+    // Knobs.  GBSMPS_DFG_TILE = 16, 32 or 64 forces the tile shape, a pure
+    // performance choice: every output sums k in the same order and the k
+    // split below does not depend on it.  GBSMPS_DFG_WAVES (CTA target in
+    // multiples of the SM count) and GBSMPS_DFG_MINK (least k chunk, in
+    // stages of DK) set the k split, and with it the FP64 partial sums'
+    // grouping: deterministic for each setting, equal to within rounding
+    // across settings.
+    auto knob = [](const char* name, int dflt) {
+      const char* e = getenv(name);
+      return e ? atoi(e) : dflt;
+    };
+    const int env_tile = knob("GBSMPS_DFG_TILE", 0);
+    const int env_waves = std::max(1, knob("GBSMPS_DFG_WAVES", 8));
+    const int env_mink = std::max(1, knob("GBSMPS_DFG_MINK", 4));
     const int T = env_tile == 16 || env_tile == 32 || env_tile == 64 ? env_tile
                                                                      : (t64 >= 2LL * nsm ? 64 : 32);
-    long long tiles = 0;
+    long long tref = 0;                           // the k split follows a fixed 32 x 32 tiling
     for (int i = 0; i < np; ++i) {
       const DfSub& u = live[g0 + i];
-      tiles += (long long)((u.M + T - 1) / T) * ((u.N + T - 1) / T);
+      tref += (long long)((u.M + 31) / 32) * ((u.N + 31) / 32);
     }
     // k split toward eight waves of CTAs (measured: 29 -> 21 ms for the
     // 144-mode chain against two waves), chunks of >= 4 stages, within the
     // workspace
-    int target = (int)std::max<long long>(1, ((long long)env_waves * nsm + tiles - 1) / tiles);
+    int target = (int)std::max<long long>(1, ((long long)env_waves * nsm + tref - 1) / tref);
     DfGroup G;
     G.np = np;
     G.work = reinterpret_cast<double2*>(work);
@@ -420,71 +364,6 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
     if (e) return e;
   }
   return cudaSuccess;
-}
-
-cudaError_t launch_zgemm_df64(char opa, char opb, int M, int N, int K, const double2* A, long long lda,
-                              long long sA, const double2* B, long long ldb, long long sB,
-                              double2* C, long long ldc, long long sC, int batch, cudaStream_t s,
-                              void* work, size_t work_bytes, int herm) {
-  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  if (herm && M != N) return cudaErrorInvalidValue;
-  // the k split follows from the 64 x 64 tiling whatever tile shape then runs
-  const long long tiles = (long long)((M + DM - 1) / DM) * ((N + DN - 1) / DN) * batch;
-  int ksplit = 1;
-  if (work && K > 4 * DK) {
-    // enough CTAs to cover the GPU twice, chunks of >= 4 stages
-    ksplit = (int)std::max<long long>(1, (304 + tiles - 1) / tiles);
-    ksplit = std::min(ksplit, K / (4 * DK));
-    while (ksplit > 1 && sizeof(double2) * (size_t)ksplit * batch * M * N > work_bytes) --ksplit;
-  }
-  int kchunk = ((K + ksplit - 1) / ksplit + DK - 1) / DK * DK;
-  ksplit = (K + kchunk - 1) / kchunk;
-  DfArgs a{M, N, K, opa == 'C' ? 1 : 0, opb == 'C' ? 1 : 0, herm ? 1 : 0, A, lda, sA, B, ldb, sB, C,
-           ldc, sC, ksplit, kchunk, reinterpret_cast<double2*>(work)};
-  int cfg = -1;
-  if (const char* e = getenv("GBSMPS_DF64_TILE")) cfg = std::max(0, std::min(2, atoi(e)));
-  const std::array<int, 6> key{(a.opa * 2 + a.opb) * 2 + a.herm, pow2i(M), pow2i(N), pow2i(K),
-                               pow2i(batch), ksplit};
-  if (cfg < 0) {
-    std::lock_guard<std::mutex> lk(g_df_mu);
-    auto it = g_df_tune.find(key);
-    if (it != g_df_tune.end()) cfg = it->second;
-  }
-  if (cfg < 0) {
-    // first call of this class: run every shape once (each overwrites C with
-    // the same values) and keep the fastest
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    int bi = 0;
-    for (int c = 0; c < 3; ++c) {
-      cudaEventRecord(e0, s);
-      cudaError_t e = df64_launch(c, a, batch, s);
-      cudaEventRecord(e1, s);
-      COUNT_LAUNCH(1);
-      if (e) { cudaEventDestroy(e0); cudaEventDestroy(e1); return e; }
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bi = c; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    std::lock_guard<std::mutex> lk(g_df_mu);
-    g_df_tune[key] = bi;
-  } else {
-    cudaError_t e = df64_launch(cfg, a, batch, s);
-    COUNT_LAUNCH(1);
-    if (e) return e;
-  }
-  if (ksplit > 1) {
-    const long long n = (long long)batch * M * N;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 8192);
-    df_reduce_kernel<<<blocks, 256, 0, s>>>(a.part, ksplit, batch, M, N, C, ldc, sC, a.herm);
-    COUNT_LAUNCH(1);
-  }
-  return cudaGetLastError();
 }
 
 namespace {

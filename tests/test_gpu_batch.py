@@ -146,20 +146,22 @@ def test_env_tile_shapes_give_identical_results(ctx, monkeypatch):
 
 
 def test_df64_tile_shapes_give_identical_results(ctx, monkeypatch):
-    """The single-state environment GEMM's tile shape (autotuned per problem
-    class) cannot change a bit either: the k split and every output's k order
-    are fixed by the problem, not by the tile."""
+    """The tile shape of the environment chain's grouped double-float launches
+    cannot change a bit: every output sums k in the same order, and the k
+    split follows a fixed reference tiling, not the tile."""
     w = wl.small(24, 31, d=5, chi=64, depth=4, rlo=0.1, rhi=0.5)
     opts = dict(d=5, chi_max=64, eps_trunc=1e-12, lambda2_freeze=1e-8, precision=g.PREC_MIXED)
     u = wl.uniforms(300, 24, seed=3)
     res = []
-    for cfg in ("0", "1", "2"):
-        monkeypatch.setenv("GBSMPS_DF64_TILE", cfg)
+    for cfg in ("16", "32", "64"):
+        monkeypatch.setenv("GBSMPS_DFG_TILE", cfg)
         m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **opts)
         try:
-            res.append((m.tensor(0), m.sample(300, uniforms=u)))
+            amp = m.amplitudes(np.zeros((1, 24), dtype=np.uint8))
+            res.append((m.tensor(0), amp, m.sample(300, uniforms=u)))
         finally:
             m.release()
-    for t, smp in res[1:]:
+    for t, a, smp in res[1:]:
         assert np.array_equal(t, res[0][0])
-        assert np.array_equal(smp, res[0][1])
+        assert np.array_equal(a, res[0][1])
+        assert np.array_equal(smp, res[0][2])
