@@ -470,13 +470,16 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
   if (blockIdx.x == 0 && threadIdx.x == 0) { cnt[0] = S; cnt[1] = 0; }
 }
 
-// one warp per sample: warp w takes row w of group 0 or, past its count,
-// row w - count0 of group 1 (the counts add up to S).  q_p from the chunk
-// norms (fixed order), choose p*, append vt' = w_{p*} / sqrt(q_{p*}) as fp16
-// planes to the group of its class at the next bond (class pi ^ (p* & 1));
-// a warp reserves its row with one atomic on the group's counter.  The row
-// order inside a group depends on the order of the reservations; every row
-// carries its sample index, and no arithmetic depends on the row.
+// One lane per sample for the draw, one warp per 32 samples for the copy.
+// Lane l of warp w takes global row t = 32 w + l: row t of group 0 or, past
+// its count, row t - count0 of group 1 (the counts add up to S).  The lane
+// sums q_p from the chunk norms (fixed order), draws u, takes the first p
+// with u Z < C_p (C the running sum in p order, Z the total), and flags the
+// draw if u Z lies within flag_tol Z of any C_p.  The warp reserves its rows
+// of each next group with one atomic per group, then copies the 32 chosen
+// blocks w_{p*} / sqrt(q_{p*}) as fp16 planes (coalesced, sample by sample).
+// The row order inside a group depends on the order of the reservations;
+// every row carries its sample index, and no arithmetic depends on the row.
 constexpr int SEL_THREADS = 256;
 __global__ void __launch_bounds__(SEL_THREADS)
 select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
@@ -484,99 +487,89 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
                      int site, uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out, int N,
                      uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if ((t & ~31LL) >= S) return;                 // whole warps only: the warp syncs below
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
-  const int grp = w >= M0 ? 1 : 0;
-  const int r = (int)(w - (grp ? M0 : 0));
-  if (w >= S || r >= (grp ? M1 : M0)) return;
+  const int grp = t >= M0 ? 1 : 0;
+  const int r = (int)(t - (grp ? M0 : 0));
+  const bool active = t < S && r < (grp ? M1 : M0);
   const SelGroup& g = grp ? g1 : g0;
-  int pstar = 0, np = 0, pos = 0, s = 0;
+  int pstar = 0, np = 0, s = 0;
   float inv = 0.f;
-  bool flag = false;
-  {
+  if (active) {
     s = g.sid[r];
     const float* ps = g.part + (long long)r * g.ldp;
     const int P2 = g.wself + g.wother;
-    // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
-    // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway.
-    // Lane j of a 32-wide chunk owns q_{c0 + j}; an inclusive warp scan gives
-    // the CDF; Z is the last CDF value, so the scan and Z agree exactly.
     auto qp = [&](int p) {
+      const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
+      const int nch = ((p & 1) ? g.wother : g.wself) / 16;
       float q = 0.f;
-      if (p < d) {
-        const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
-        const int nch = ((p & 1) ? g.wother : g.wself) / 16;
 #pragma unroll 8
-        for (int t = 0; t < nch; ++t) q += ps[c0 + t];   // independent loads, fixed order
-      }
+      for (int k = 0; k < nch; ++k) q += ps[c0 + k];
       return q;
     };
-    const float q0 = qp(lane);                    // p = lane: both passes reuse it
+    // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
+    // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway
     float Z = 0.f;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-      float C = c0 == 0 ? q0 : qp(c0 + lane);
-      for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, C, o);
-        if (lane >= o) C += y;
-      }
-      Z += __shfl_sync(0xffffffffu, C, 31);
-    }
+    for (int p = 0; p < d; ++p) Z += qp(p);
     const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
     const float tt = (float)uu * Z;
     const float ftol = (float)flag_tol * Z;
+    float C = 0.f, qsel = 0.f;
     int plast = 0;
-    float qsel = 0.f, base = 0.f;
+    bool flag = false;
     pstar = -1;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-      const int p = c0 + lane;
-      const float q = c0 == 0 ? q0 : qp(p);
-      float C = q;
-      for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, C, o);
-        if (lane >= o) C += y;
-      }
-      C += base;
-      base = __shfl_sync(0xffffffffu, C, 31);
-      const bool live = p < d;
-      if (__any_sync(0xffffffffu, live && fabsf(tt - C) <= ftol)) flag = true;
-      const unsigned pos = __ballot_sync(0xffffffffu, live && q > 0.f);
-      if (pos) plast = c0 + 31 - __clz(pos);
-      const unsigned hit = __ballot_sync(0xffffffffu, live && tt < C);
-      if (pstar < 0 && hit) {
-        const int j = __ffs(hit) - 1;
-        pstar = c0 + j;
-        qsel = __shfl_sync(0xffffffffu, q, j);
-      }
+    for (int p = 0; p < d; ++p) {
+      const float q = qp(p);
+      C += q;
+      if (fabsf(tt - C) <= ftol) flag = true;
+      if (q > 0.f) plast = p;
+      if (pstar < 0 && tt < C) { pstar = p; qsel = q; }
     }
-    if (pstar < 0) {
-      pstar = plast;
-      qsel = qp(pstar);
-    }
+    if (pstar < 0) { pstar = plast; qsel = qp(pstar); }
     inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
     np = grp ^ (pstar & 1);
-    if (lane == 0) pos = atomicAdd(cnt_next + np, 1);
-    pos = __shfl_sync(0xffffffffu, pos, 0);
-  }
-  if (pos >= S) return;                         // cannot happen: one row per sample
-  const NextGroup& ng = np ? n1 : n0;
-  const int P2 = g.wself + g.wother;
-  const float2* wr = g.W + (long long)r * g.ldw + (long long)(pstar >> 1) * P2 +
-                     ((pstar & 1) ? g.wself : 0);
-  for (int b = lane; b < ng.Kp / 2; b += 32) {
-    const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
-    __half rr[NPL], ii[NPL];
-    split2(v.x * inv, rr[0], rr[1]);
-    split2(v.y * inv, ii[0], ii[1]);
-    for (int pl = 0; pl < NPL; ++pl) {
-      __half2 x;
-      x.x = rr[pl]; x.y = ii[pl];
-      *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)pos * ng.Kp + 2 * b) = x;
-    }
-  }
-  if (lane == 0) {
-    ng.sid[pos] = s;
     out[(size_t)s * N + site] = (uint8_t)pstar;
     if (flags && flag) flags[s] = 1;
+  }
+  // rows in the next groups: one atomic per group and warp
+  int pos = 0;
+  for (int c = 0; c < 2; ++c) {
+    const unsigned m = __ballot_sync(0xffffffffu, active && np == c);
+    if (!m) continue;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(cnt_next + c, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (active && np == c) pos = base + __popc(m & ((1u << lane) - 1u));
+  }
+  // the warp copies each active lane's chosen block into its next group
+  unsigned todo = __ballot_sync(0xffffffffu, active && pos < S);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int rr = __shfl_sync(0xffffffffu, r, src);
+    const int gg = __shfl_sync(0xffffffffu, grp, src);
+    const int ps = __shfl_sync(0xffffffffu, pstar, src);
+    const int nn = __shfl_sync(0xffffffffu, np, src);
+    const int po = __shfl_sync(0xffffffffu, pos, src);
+    const int sd = __shfl_sync(0xffffffffu, s, src);
+    const float iv = __shfl_sync(0xffffffffu, inv, src);
+    const SelGroup& G = gg ? g1 : g0;
+    const NextGroup& ng = nn ? n1 : n0;
+    const int P2 = G.wself + G.wother;
+    const float2* wr = G.W + (long long)rr * G.ldw + (long long)(ps >> 1) * P2 + ((ps & 1) ? G.wself : 0);
+    for (int b = lane; b < ng.Kp / 2; b += 32) {
+      const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
+      __half hr[NPL], hi[NPL];
+      split2(v.x * iv, hr[0], hr[1]);
+      split2(v.y * iv, hi[0], hi[1]);
+      for (int pl = 0; pl < NPL; ++pl) {
+        __half2 x;
+        x.x = hr[pl]; x.y = hi[pl];
+        *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)po * ng.Kp + 2 * b) = x;
+      }
+    }
+    if (lane == 0) ng.sid[po] = sd;
   }
 }
 
@@ -789,7 +782,7 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  const double* u, int ustride, int site, uint64_t seed,
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s) {
-  long long threads = (long long)Scap * 32;
+  long long threads = ((long long)Scap + 31) / 32 * 32;     // one lane per sample
   int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
   select_groups_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, d, g0, g1, n0, n1, cnt_next, u, ustride,
                                                       site, seed, counter0, out, N, flags, flag_tol);
