@@ -528,7 +528,7 @@ def main():
     sm = sorted(r["step_ms"])
     if r["pipelined"]:
         cfg["pipeline"] = ("one stream of steps: the next states' Gaussian-SVD chains (one SM) and "
-                           "the next state's environments run beside the current sampling; "
+                           "the next state's environments and canonical form run beside the current sampling; "
                            "latency_ms is one state alone, build + sampling")
     line = dict(base, value=round(r["value"], 3), ms_per_step=round(r["ms_per_step"], 3),
                 dtype=("f64 gsvd/pco + df64 env + fp16x2 (3 products)/fp32 tensor-core sampling"

@@ -357,14 +357,14 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   CK(cudaSetDevice(c->device));
   // Per state the build runs in four parts: the front (validation, GSVD
   // chain on one SM, bases) on one of three contexts of its own, launched two
-  // states ahead; then on c's stream the PCO build (long CTAs), the
-  // environments (short CTAs) and the canonical form.  Iteration k runs
-  // PCO(k+1), then the sampling of state k (its own stream, high priority,
-  // own status word) beside the environments of state k+1, then the
-  // canonical form of state k+1 once sampling k is done.  So neither the
-  // PCO's nor the factors' long CTAs ever share the GPU with the sampler's
-  // persistent GEMM, the environment chain (latency-bound on the FP32 pipes)
-  // fills what the sampler leaves, and the chain hides behind both.
+  // states ahead; then on c's stream the PCO build, the environments and the
+  // canonical form.  Iteration k runs PCO(k+1) alone, then the sampling of
+  // state k (its own stream, high priority, own status word) beside the
+  // environments and the canonical form of state k+1.  The PCO's CTAs hold
+  // 47 KB of shared memory for milliseconds and would keep the sampler's
+  // persistent GEMM CTAs (218 KB) off their SMs, so the PCO never overlaps a
+  // sampling; every CTA of the other two parts is short, or fits on an SM
+  // beside a GEMM CTA.  The chain hides behind all of it.
   int rc = GBSMPS_OK;
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == GBSMPS_OK) rc = fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
@@ -415,6 +415,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   for (int k = 0; k < count && ok; ++k) {
     // state k is built; state k-1's sampling finished before it was handed over
     if (k + 2 < count && !front(k + 2)) break;
+    // (sampling k-1 has finished: the loop waited for it)
     if (k + 1 < count && !keep(gbs::rest_pco(c, &fs[(k + 1) % NF], nullptr))) break;
     // the sampling starts after PCO(k+1): no long CTA beside the sampler
     if (!ck(cudaEventRecord(pco_done, c->stream)) || !ck(cudaStreamWaitEvent(ss, pco_done, 0))) break;
@@ -424,11 +425,13 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     if (!ck(cudaEventRecord(sampled, ss))) break;
     gbsmps_mps_t next = nullptr;
     if (k + 1 < count) {
-      if (!keep(gbs::rest_env(c, &fs[(k + 1) % NF]))) break;                 // beside sampling k
-      if (!keep(gbs::rest_canon(c, &fs[(k + 1) % NF], sampled, &next))) break;  // after it
+      // beside sampling k: every CTA of these parts fits on an SM next to a
+      // sampler GEMM CTA, or is short
+      if (!keep(gbs::rest_env(c, &fs[(k + 1) % NF]))) break;
+      if (!keep(gbs::rest_canon(c, &fs[(k + 1) % NF], nullptr, &next))) break;
     }
-    // rest_canon waited for sampling k (and synchronised); the last one is awaited here
-    if (k + 1 == count && !ck(cudaStreamSynchronize(ss))) break;
+    // state k's MPS is freed once its sampling is done
+    if (!ck(cudaStreamSynchronize(ss))) break;
     delete cur;
     cur = next;
   }

@@ -378,7 +378,7 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, int* status, cudaStream_t s);
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
-                         int nb, cudaStream_t s);
+                         int nb, int maxd, cudaStream_t s);
 // complex GEMM in FP32 on the CUDA cores (k_f32gemm.cu): C (FP32) = A B with
 // A, B FP64 (a64/b64 = 1) or FP32, row-major, batched by strides
 // many independent FP32 products C = A B (A, B FP64 or FP32 as a64 / b64,

@@ -789,16 +789,21 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
   return cudaGetLastError();
 }
 
+// Both factor kernels fit on an SM beside a sampler GEMM CTA (218 KB of
+// shared memory, 320 threads x 112 registers), so they may run while another
+// state is sampled: 256 threads each, and shared memory for the largest
+// block only.
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, int* status, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  chol_kernel<<<nb, 512, 0, s>>>(src, dst, off, Dv, b0, dused, status);
+  chol_kernel<<<nb, 256, 0, s>>>(src, dst, off, Dv, b0, dused, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
-                         int nb, cudaStream_t s) {
+                         int nb, int maxd, cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  trinv_kernel<<<nb, 256, sizeof(double) * 4096, s>>>(L, X, off, Dv, b0);
+  if (maxd < 1 || maxd > 4096) return cudaErrorInvalidValue;
+  trinv_kernel<<<nb, 256, sizeof(double) * maxd, s>>>(L, X, off, Dv, b0);
   return cudaGetLastError();
 }

@@ -378,7 +378,9 @@ int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cuda
   const int* dims = reinterpret_cast<const int*>(off + 2 * (M->N + 1));
   CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), off, dims, 2 * b0, 2 * nb,
                  w->du.as<double>(), c->d_status, s));
-  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, s));
+  int maxd = 1;
+  for (int b = b0; b < b0 + nb; ++b) maxd = std::max({maxd, M->pcnt[2 * b], M->pcnt[2 * b + 1]});
+  CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, maxd, s));
   COUNT_LAUNCH(2);
   return GBSMPS_OK;
 }
