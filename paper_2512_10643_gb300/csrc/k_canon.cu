@@ -41,7 +41,8 @@ constexpr int TSTAGES = 3;
 constexpr int PLANE_BYTES = TBM * TBK * 2;        // 16 KB (TBN == TBM)
 constexpr int STAGE_BYTES = 2 * NPL * PLANE_BYTES;
 constexpr int EPI_WARPS = 8;                      // two per TMEM lane quadrant
-constexpr int EPI_LD = 20;                        // floats per staged row (16 columns + pad, 16-byte rows)
+constexpr int EPI_LD = 16;                        // floats per staged row (16 columns; float4 index
+                                                  // XOR-swizzled by row, conflict-free without a pad)
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_LD * 4;
 constexpr int NBAR = 2 * TSTAGES + 2 + 2 + 1;     // full, empty, acc full, acc empty, drain
 constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
@@ -317,13 +318,13 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
               v[e] = fmaf(LO_INV, __uint_as_float(x[k]), __uint_as_float(h[k]));
               nrm = fmaf(v[e], v[e], nrm);
             }
-            srow[j] = make_float4(v[0], v[1], v[2], v[3]);
+            srow[j ^ ((lane >> 1) & 3)] = make_float4(v[0], v[1], v[2], v[3]);
           }
           __syncwarp();
 #pragma unroll
           for (int it = 0; it < 4; ++it) {
             const int r = it * 8 + (lane >> 2), c4 = lane & 3;
-            const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + c4 * 4);
+            const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + 4 * (c4 ^ ((r >> 1) & 3)));
             if (rbase + r < M)
               *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + 16 * hf + c4 * 4) =
                   val;
