@@ -32,10 +32,9 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# DRAM bytes (read + write) of one launch of the dominant kernel at 100,000
-# samples, central site: ncu capture at full size (one pass),
-# profiles/canon_gemm_tc_n144_d6_chi256.md
-TRAFFIC_BYTES_PER_LAUNCH = 106052864 + 630772480
+# DRAM bytes (read + write) per launch of the dominant kernel at 100,000
+# samples from an ncu capture of the current kernel (None until one is taken)
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -241,8 +240,8 @@ def run_gpu(args, rank, local, ws, dist):
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     n_launch = max(tr["launches"], 1)
     roof = {"kernel": "canon_gemm_tc_kernel (persistent tcgen05 + TMA split-FP16 complex GEMM over "
-                      "both photon-parity groups, "
-                      "one launch per site: W = Vt At^m over 100k samples)",
+                      "both photon-parity groups, two launches per site: W_0 = Vt At^m[0] for every "
+                      "sample, then W = Vt At^m for the samples the p = 0 pre-pass leaves; 100k samples)",
             "bound": "tensor", "achieved": round(ach_tflops, 3), "peak": peak,
             "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json x 1 "
                             "(nominal dense fp16/bf16 ratio)"),
@@ -250,9 +249,11 @@ def run_gpu(args, rank, local, ws, dist):
             "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None or S != 100_000
                         else TRAFFIC_BYTES_PER_LAUNCH),
             "algorithmic_flops_per_launch": tr["flops"] / n_launch,
-            "algorithmic_flops_def": ("8 real flops per complex product of the nonzero parity blocks: "
-                                      "sum over samples s of 8 D_{m-1,c_s} sum_p D_{m,c_s^(p&1)} per "
-                                      "site (about a quarter of the dense 8 S D_{m-1} d D_m)"),
+            "algorithmic_flops_def": ("8 real flops per complex product of the nonzero parity blocks "
+                                      "the sampler multiplies: block p = 0 of every sample "
+                                      "(8 D_{m-1,c} D_{m,c}) plus all blocks of the samples the p = 0 "
+                                      "pre-pass leaves (8 D_{m-1,c} sum_p D_{m,c^(p&1)}); two launches "
+                                      "per site"),
             "avg_launch_ms": tr["ms"] / n_launch,
             "launches_per_step": tr["launches"],
             "share_of_step": round(tr["ms"] / (total_ms / args.steps), 4),

@@ -209,9 +209,14 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   StageTimer tm(s);
   // mixed path: per parity group the fp16 state planes (current and next
   // bond), sample indices, W and chunk norms; group row counts per bond
-  DevBuf cv[4], csid[4], cw[2], cpart[2], ccnt;
+  DevBuf cv[6], csid[6], cw[2], cpart[2], ccnt, crest;
   const char* tce = getenv("GBSMPS_TC");
   const int use_tc = !(tce && tce[0] == '0');
+  // the p = 0 pre-pass (on unless GBSMPS_P0PASS=0): block 0 of every sample
+  // first, the full product only for the samples it cannot decide
+  const char* p0e = getenv("GBSMPS_P0PASS");
+  const bool p0pass = !(p0e && p0e[0] == '0') && d > 1;
+  std::vector<int> hrest;
   std::vector<int> hcnt;                  // group row counts, read back for the trace
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
@@ -227,7 +232,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           Npmax = std::max(Npmax, m->sg[i].Np[pi]);
         }
       if (!ccnt.p) {
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < (p0pass ? 6 : 4); ++k) {
           CK(cv[k].alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
           CK(csid[k].alloc(sizeof(int) * (size_t)Spad, s));
         }
@@ -236,9 +241,12 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           CK(cpart[k].alloc(sizeof(float) * (size_t)chunk * (Npmax / 32), s));
         }
         CK(ccnt.alloc(sizeof(int) * 2 * (size_t)(N + 1), s));
+        CK(crest.alloc(sizeof(int) * 2 * (size_t)(N + 1), s));
       }
       int* cnt = ccnt.as<int>();
+      int* rcnt = crest.as<int>();
       CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
+      CK(cudaMemsetAsync(rcnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
       int cur[2] = {0, 1}, nxt[2] = {2, 3};
       CK(launch_sampler_init(cv[cur[0]].as<__half>(), (long long)Spad * m->sg[0].Kp[0], Spad,
                              m->sg[0].Kp[0], csid[cur[0]].as<int>(), cnt, cs, s));
@@ -261,30 +269,78 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           ng[pi] = NextGroup{cv[nxt[pi]].as<__half>(), (long long)Spad * Kpn, Kpn,
                              csid[nxt[pi]].as<int>(), m->pcnt[2 * (site + 1) + pi]};
         }
-        CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), tg[0], tg[1],
-                             cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0], cv[cur[1]].as<__half>(),
-                             (long long)Spad * G.Kp[1], m->bpack.as<__half>() + G.boff[0],
-                             (long long)G.Np[0] * G.Kp[0], m->bpack.as<__half>() + G.boff[1],
-                             (long long)G.Np[1] * G.Kp[1], use_tc, status, sm_reserve, s));
-        CK(launch_select_groups(cs, d, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1),
-                                du ? du + (size_t)s0 * N : nullptr, N, site, seed,
-                                counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
-                                dfl ? dfl + s0 : nullptr, 1e-5, s));
-        COUNT_LAUNCH(1);
+        const __half* B0 = m->bpack.as<__half>() + G.boff[0];
+        const __half* B1 = m->bpack.as<__half>() + G.boff[1];
+        const long long bpl0 = (long long)G.Np[0] * G.Kp[0], bpl1 = (long long)G.Np[1] * G.Kp[1];
+        const double* uu = du ? du + (size_t)s0 * N : nullptr;
+        if (p0pass) {
+          // block 0 only (the first column tiles of each group's planes)
+          TcGroup ta[2] = {tg[0], tg[1]};
+          RestGroup rg[2];
+          unsigned char mapR[2][128];
+          for (int pi = 0; pi < 2; ++pi) {
+            ta[pi].ntn = std::min(G.Np[pi] / 128, (2 * G.w[pi] + 127) / 128);
+            rg[pi] = RestGroup{cv[cur[pi]].as<__half>(), cv[4 + pi].as<__half>(), (long long)Spad * G.Kp[pi],
+                               G.Kp[pi], csid[4 + pi].as<int>(), rcnt + 2 * site + pi};
+            if (canon_make_map(mapR[pi], cv[4 + pi].p, G.Kp[pi], Spad))
+              return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
+          }
+          CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), ta[0], ta[1],
+                               cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0],
+                               cv[cur[1]].as<__half>(), (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1,
+                               use_tc, status, sm_reserve, s));
+          CK(launch_select_pre(cs, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), rg[0], rg[1],
+                               m->creg.as<unsigned long long>(), 1e-10, uu, N, site, seed,
+                               counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N, 1e-5, s));
+          COUNT_LAUNCH(1);
+          // the full product and selection for the rest
+          TcGroup tb[2] = {tg[0], tg[1]};
+          SelGroup sb[2] = {sl[0], sl[1]};
+          for (int pi = 0; pi < 2; ++pi) {
+            tb[pi].cnt = rcnt + 2 * site + pi;
+            sb[pi].cnt = rcnt + 2 * site + pi;
+            sb[pi].sid = csid[4 + pi].as<int>();
+          }
+          CK(launch_canon_gemm(mapR[0], G.map[0].data(), mapR[1], G.map[1].data(), tb[0], tb[1],
+                               cv[4].as<__half>(), (long long)Spad * G.Kp[0], cv[5].as<__half>(),
+                               (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1, use_tc, status,
+                               sm_reserve, s));
+          CK(launch_select_groups(cs, d, sb[0], sb[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
+                                  site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
+                                  dfl ? dfl + s0 : nullptr, 1e-5, s));
+          COUNT_LAUNCH(1);
+        } else {
+          CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), tg[0], tg[1],
+                               cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0],
+                               cv[cur[1]].as<__half>(), (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1,
+                               use_tc, status, sm_reserve, s));
+          CK(launch_select_groups(cs, d, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
+                                  site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
+                                  dfl ? dfl + s0 : nullptr, 1e-5, s));
+          COUNT_LAUNCH(1);
+        }
         std::swap(cur, nxt);
       }
       if (g_tc_trace.on.load()) {
         // algorithmic work of the GEMMs: 8 real flops per complex product of a
         // sample's class-pi state with the nonzero blocks of At
+        // (with the pre-pass: block 0 of every sample, all blocks of the rest)
         hcnt.assign(2 * (N + 1), 0);
+        hrest.assign(2 * (N + 1), 0);
         CK(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hrest.data(), rcnt, sizeof(int) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         double f = 0.0;
         for (int site = 0; site < N; ++site)
           for (int pi = 0; pi < 2; ++pi) {
             double cols = 0.0;
             for (int p = 0; p < d; ++p) cols += m->pcnt[2 * (site + 1) + (pi ^ (p & 1))];
-            f += 8.0 * hcnt[2 * site + pi] * (double)m->pcnt[2 * site + pi] * cols;
+            const double kl = m->pcnt[2 * site + pi];
+            if (p0pass)
+              f += 8.0 * kl * (hcnt[2 * site + pi] * (double)m->pcnt[2 * (site + 1) + pi] +
+                               hrest[2 * site + pi] * cols);
+            else
+              f += 8.0 * hcnt[2 * site + pi] * kl * cols;
           }
         g_tc_trace.add_work(f, 0.0);
       }
@@ -321,6 +377,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   for (auto& b : cw) b.release();
   for (auto& b : cpart) b.release();
   ccnt.release();
+  crest.release();
   if (mem_kind == GBSMPS_MEM_HOST && sync_host) return sync_status(m->ctx);
   return GBSMPS_OK;
 }

@@ -356,6 +356,17 @@ struct SelGroup {         // one group as the selection pass reads it
 struct NextGroup {        // one class of the next bond as the selection pass writes it
   __half* V; long long vpl; int Kp; int* sid; int D;
 };
+struct RestGroup {        // the samples of one group that the p = 0 pre-pass leaves
+  const __half* Vc;       // the group's current state planes (plane stride vpl, row Kp)
+  __half* V;              // their copies for the full pass (same layout)
+  long long vpl; int Kp;
+  int* sid; int* cnt;
+};
+cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, const NextGroup& n0,
+                              const NextGroup& n1, int* cnt_next, const RestGroup& r0,
+                              const RestGroup& r1, const unsigned long long* regmax, double reg_ok,
+                              const double* u, int ustride, int site, uint64_t seed,
+                              uint64_t counter0, uint8_t* out, int N, double margin, cudaStream_t s);
 cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s);
 cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* mapA1,
                               const void* mapB1, const TcGroup& g0, const TcGroup& g1,
@@ -376,7 +387,8 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s);
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
-                        int b0, int nb, double* dused, int* status, cudaStream_t s);
+                        int b0, int nb, double* dused, unsigned long long* regmax, int* status,
+                        cudaStream_t s);
 cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, const int* Dv, int b0,
                          int nb, int maxd, cudaStream_t s);
 // complex GEMM in FP32 on the CUDA cores (k_f32gemm.cu): C (FP32) = A B with

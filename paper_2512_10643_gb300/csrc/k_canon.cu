@@ -574,6 +574,98 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
   }
 }
 
+// The p = 0 pre-pass of a site.  In right-canonical form the weights of a
+// sample add up to its squared norm, sum_p q_p = |vt|^2 = 1 (to the rounding
+// of the planes and transforms), so the rule "first p with u Z < C_p" picks
+// p = 0 whenever u < q_0 - margin, margin >= |Z - 1|.  Here only block 0 of
+// each group has been multiplied (W holds it, and its chunk norms).  One
+// lane per sample: a draw below q_0 - margin emits p = 0 and appends
+// w_0 / sqrt(q_0) to the next group of the same class; every other sample
+// (and every sample when the build's largest Cholesky regulariser exceeds
+// reg_ok, which bounds |Z - 1|) is copied to a rest group for the full pass.
+// Such a sample's draw is not flagged here; the full pass flags it.  One
+// atomic per destination and warp; the warp copies the rows.
+__global__ void __launch_bounds__(SEL_THREADS)
+select_pre_kernel(int S, const SelGroup g0, const SelGroup g1, const NextGroup n0,
+                  const NextGroup n1, int* cnt_next, const RestGroup r0, const RestGroup r1,
+                  const unsigned long long* __restrict__ regmax, double reg_ok,
+                  const double* __restrict__ u, int ustride, int site, uint64_t seed,
+                  uint64_t counter0, uint8_t* __restrict__ out, int N, double margin) {
+  const int lane = threadIdx.x & 31;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if ((t & ~31LL) >= S) return;                 // whole warps only: the warp syncs below
+  const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
+  const int grp = t >= M0 ? 1 : 0;
+  const int r = (int)(t - (grp ? M0 : 0));
+  const bool active = t < S && r < (grp ? M1 : M0);
+  const SelGroup& g = grp ? g1 : g0;
+  const bool reg_good = __longlong_as_double((long long)*regmax) <= reg_ok;
+  bool cut = false;
+  int s = 0;
+  float inv = 0.f;
+  if (active) {
+    s = g.sid[r];
+    const float* ps = g.part + (long long)r * g.ldp;
+    float q0 = 0.f;
+    const int nch = g.wself / 16;
+#pragma unroll 8
+    for (int k = 0; k < nch; ++k) q0 += ps[k];
+    const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
+    cut = reg_good && q0 > 0.f && uu < (double)q0 - margin;
+    if (cut) {
+      inv = rsqrtf(q0);
+      out[(size_t)s * N + site] = 0;
+    }
+  }
+  // rows: the next group of the same class (cut) or the rest group (not cut)
+  int pos = 0;
+  for (int c = 0; c < 4; ++c) {
+    const bool mine = active && grp == (c & 1) && cut == (c < 2);
+    const unsigned m = __ballot_sync(0xffffffffu, mine);
+    if (!m) continue;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(c < 2 ? cnt_next + (c & 1) : ((c & 1) ? r1.cnt : r0.cnt), __popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (mine) pos = base + __popc(m & ((1u << lane) - 1u));
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, active && pos < S);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int rr = __shfl_sync(0xffffffffu, r, src);
+    const int gg = __shfl_sync(0xffffffffu, grp, src);
+    const int po = __shfl_sync(0xffffffffu, pos, src);
+    const int sd = __shfl_sync(0xffffffffu, s, src);
+    const bool ct = __shfl_sync(0xffffffffu, cut ? 1 : 0, src) != 0;
+    const float iv = __shfl_sync(0xffffffffu, inv, src);
+    if (ct) {                                     // w_0 / sqrt(q_0) into the next group gg
+      const SelGroup& G = gg ? g1 : g0;
+      const NextGroup& ng = gg ? n1 : n0;
+      const float2* wr = G.W + (long long)rr * G.ldw;
+      for (int b = lane; b < ng.Kp / 2; b += 32) {
+        const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
+        __half hr[NPL], hi[NPL];
+        split2(v.x * iv, hr[0], hr[1]);
+        split2(v.y * iv, hi[0], hi[1]);
+        for (int pl = 0; pl < NPL; ++pl) {
+          __half2 x;
+          x.x = hr[pl]; x.y = hi[pl];
+          *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)po * ng.Kp + 2 * b) = x;
+        }
+      }
+      if (lane == 0) ng.sid[po] = sd;
+    } else {                                      // the state row into the rest group gg
+      const RestGroup& R = gg ? r1 : r0;
+      for (int pl = 0; pl < NPL; ++pl) {
+        const uint4* a = reinterpret_cast<const uint4*>(R.Vc + pl * R.vpl + (long long)rr * R.Kp);
+        uint4* b = reinterpret_cast<uint4*>(R.V + pl * R.vpl + (long long)po * R.Kp);
+        for (int k = lane; k < R.Kp / 8; k += 32) b[k] = a[k];
+      }
+      if (lane == 0) R.sid[po] = sd;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- Cholesky
 // one CTA per bond: R + delta 1 = L L^dag (lower, FP64 complex), R overwritten
 // by L.  delta = reg * max diag(R) regularises the bond states the truncated
@@ -583,7 +675,7 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
 // absolute.  A pivot that is still not positive flags ST_NUMERIC.
 __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
                             const long long* __restrict__ off, const int* __restrict__ Dv, int b0,
-                            double* __restrict__ dused, int* status) {
+                            double* __restrict__ dused, unsigned long long* regmax, int* status) {
   const int b = b0 + blockIdx.x;
   const int D = Dv[b];
   const double2* Sm = src + off[b];
@@ -636,7 +728,13 @@ __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict
     __syncthreads();
   }
   if (!okf && tid == 0) set_status(status, ST_NUMERIC);
-  if (tid == 0) dused[b] = okf ? delta / fmax(dmax, 1e-300) : -1.0;
+  if (tid == 0) {
+    const double rel = okf ? delta / fmax(dmax, 1e-300) : -1.0;
+    dused[b] = rel;
+    // the largest relative regulariser of the build (bit patterns of
+    // non-negative doubles order like the integers; a failure counts as huge)
+    if (regmax) atomicMax(regmax, (unsigned long long)__double_as_longlong(okf ? rel : 1e300));
+  }
   for (long long idx = tid; idx < (long long)D * D; idx += nt) {
     const int i = idx / D, j = idx % D;
     if (j > i) R[idx] = cmk(0.0, 0.0);
@@ -794,10 +892,24 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
 // shared memory, 320 threads x 112 registers), so they may run while another
 // state is sampled: 256 threads each, and shared memory for the largest
 // block only.
+cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, const NextGroup& n0,
+                              const NextGroup& n1, int* cnt_next, const RestGroup& r0,
+                              const RestGroup& r1, const unsigned long long* regmax, double reg_ok,
+                              const double* u, int ustride, int site, uint64_t seed,
+                              uint64_t counter0, uint8_t* out, int N, double margin, cudaStream_t s) {
+  long long threads = ((long long)Scap + 31) / 32 * 32;
+  int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
+  select_pre_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, g0, g1, n0, n1, cnt_next, r0, r1, regmax,
+                                                   reg_ok, u, ustride, site, seed, counter0, out, N,
+                                                   margin);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
-                        int b0, int nb, double* dused, int* status, cudaStream_t s) {
+                        int b0, int nb, double* dused, unsigned long long* regmax, int* status,
+                        cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  chol_kernel<<<nb, 256, 0, s>>>(src, dst, off, Dv, b0, dused, status);
+  chol_kernel<<<nb, 256, 0, s>>>(src, dst, off, Dv, b0, dused, regmax, status);
   return cudaGetLastError();
 }
 

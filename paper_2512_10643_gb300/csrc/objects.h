@@ -126,6 +126,7 @@ struct gbsmps_mps {
   // mixed path, right-canonical sampler: Cholesky factors of the environments,
   // their inverses, and every site's canonical tensor as fp16 planes + TMA map
   DevBuf eoff_dev, lchol, linv, bpack;
+  DevBuf creg;                    // largest relative Cholesky regulariser (double bits, device)
   std::vector<int> pcnt;          // [2b + c]: kept states of bond b with parity c
   struct SiteGroups {             // the two parity groups of one site's sampler GEMM
     int Kp[2], Np[2];             // group pi: K (real, multiple of 64), N (real, of 128)
@@ -141,7 +142,7 @@ struct gbsmps_mps {
   double* cm = nullptr;
   ~gbsmps_mps() {
     tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
-    eoff_dev.release(); lchol.release(); linv.release(); bpack.release();
+    eoff_dev.release(); lchol.release(); linv.release(); bpack.release(); creg.release();
   }
 };
 

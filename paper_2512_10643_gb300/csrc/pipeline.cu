@@ -337,6 +337,8 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
   CK(M->linv.alloc(sizeof(double2) * (M->etot + 8), s));
   CK(w->du.alloc(sizeof(double) * 2 * (N + 1), s));
   CK(cudaMemsetAsync(w->du.p, 0, sizeof(double) * 2 * (N + 1), s));
+  CK(M->creg.alloc(sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(M->creg.p, 0, sizeof(unsigned long long), s));
   const double2 one = cmk(1.0, 0.0);
   for (int b : {0, N}) {
     CK(cudaMemcpyAsync(M->lchol.as<double2>() + M->eoff[b], &one, sizeof(double2),
@@ -377,7 +379,7 @@ int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cuda
   const long long* off = M->eoff_dev.as<long long>();
   const int* dims = reinterpret_cast<const int*>(off + 2 * (M->N + 1));
   CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), off, dims, 2 * b0, 2 * nb,
-                 w->du.as<double>(), c->d_status, s));
+                 w->du.as<double>(), M->creg.as<unsigned long long>(), c->d_status, s));
   int maxd = 1;
   for (int b = b0; b < b0 + nb; ++b) maxd = std::max({maxd, M->pcnt[2 * b], M->pcnt[2 * b + 1]});
   CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, maxd, s));

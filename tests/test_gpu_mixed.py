@@ -124,3 +124,36 @@ def test_tcgen05_gemm_matches_simt_reference(ctx, monkeypatch):
     finally:
         m.release()
 
+
+
+def test_p0_prepass_draws_the_full_pass_patterns(ctx, monkeypatch):
+    """The p = 0 pre-pass multiplies only block 0 of every sample and decides
+    p = 0 when u < q_0 - 1e-5 (sum_p q_p = |vt|^2 = 1 in right-canonical
+    form); everything else goes through the full pass.  From the same
+    uniforms it must draw exactly the patterns of the single full pass,
+    except draws the full pass flags."""
+    w = wl.small(30, 12, d=6, chi=96, depth=6, rlo=0.1, rhi=0.45)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=6, chi_max=96, eps_trunc=1e-12,
+                       lambda2_freeze=1e-9, precision=g.PREC_MIXED)
+    try:
+        S = 6000
+        u = wl.uniforms(S, 30, seed=44)
+        f_full = np.zeros(S, dtype=np.uint8)
+        f_pre = np.zeros(S, dtype=np.uint8)
+        monkeypatch.setenv("GBSMPS_P0PASS", "0")
+        s_full = m.sample(S, uniforms=u, flags=f_full)
+        monkeypatch.setenv("GBSMPS_P0PASS", "1")
+        s_pre = m.sample(S, uniforms=u, flags=f_pre)
+        ok = (f_full == 0) & (f_pre == 0)
+        assert ok.mean() > 0.98
+        assert np.array_equal(s_full[ok], s_pre[ok])
+        assert np.all(s_pre.astype(int).sum(1) % 2 == 0)
+        # the in-kernel Philox path as well, twice in a row
+        a = m.sample(S, seed=9)
+        b = m.sample(S, seed=9)
+        assert np.array_equal(a, b)
+        monkeypatch.setenv("GBSMPS_P0PASS", "0")
+        c = m.sample(S, seed=9)
+        assert (a == c).all(axis=1).mean() > 0.98
+    finally:
+        m.release()
