@@ -482,7 +482,7 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
 // The row order inside a group depends on the order of the reservations;
 // every row carries its sample index, and no arithmetic depends on the row.
 constexpr int SEL_THREADS = 256;
-constexpr int SEL_SPW = 8;        // samples per warp: the warp copies their rows one by one
+constexpr int SEL_SPW = 4;        // samples per warp: the warp copies their rows one by one
 __global__ void __launch_bounds__(SEL_THREADS)
 select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
                      const NextGroup n1, int* cnt_next, const double* __restrict__ u, int ustride,
