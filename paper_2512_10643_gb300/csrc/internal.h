@@ -215,6 +215,19 @@ cudaError_t launch_zscale(double2* x, size_t n, const double2* factor, cudaStrea
 cudaError_t launch_norm_phase(const double2* R0, const double2* amp0, double2* factor,
                               int* status, cudaStream_t s);
 
+// A complex double as a double-float pair (hi, lo) per part: float4
+// (re_hi, re_lo, im_hi, im_lo), 16 bytes like a double2.  The mixed path
+// stores the energy-gauge tensors and the environment products' first
+// factor this way, so the double-float GEMM loads them without converting
+// on GB300's slow FP64 pipe.
+__device__ __forceinline__ float4 df_pack(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+__host__ __device__ __forceinline__ double2 df_unpack(float4 w) {
+  return make_double2((double)w.x + (double)w.y, (double)w.z + (double)w.w);
+}
+
 // Parity-compact layout of the mixed path's per-site tensors (energy gauge,
 // environment products, canonical transforms).  A^m[alpha, p, beta] is zero
 // unless n_alpha + p + n_beta is even, so site m is stored as two class
@@ -287,7 +300,7 @@ struct GaugeTask {        // one site of a batched energy-gauge launch
   int Dl, Dr;
   const double* El;
   const double* Er;
-  double2* Ah;            // parity-compact output
+  double2* Ah;            // parity-compact output, double-float pairs (df_pack)
   ParitySite P;
 };
 cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, int d, int max_elems,
@@ -308,6 +321,7 @@ struct DfSub {
   const double2* B; long long ldb;
   double2* C; long long ldc;
   int herm;                // C Hermitian (M == N): lower triangle computed, mirrored
+  int asplit = 0, bsplit = 0, csplit = 0;   // A, B, C as double-float pairs (df_pack)
 };
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes);
@@ -394,7 +408,7 @@ cudaError_t launch_trinv(const double2* L, double2* X, const long long* off, con
 // complex GEMM in FP32 on the CUDA cores (k_f32gemm.cu): C (FP32) = A B with
 // A, B FP64 (a64/b64 = 1) or FP32, row-major, batched by strides
 // many independent FP32 products C = A B (A, B FP64 or FP32 as a64 / b64,
-// C FP32) in one launch; the device table is sorted by c0, the first CTA of
+// a64 = 2: A as double-float pairs; C FP32) in one launch; the device table is sorted by c0, the first CTA of
 // each product, with tn = its column tiles; ctas = the total
 struct F32Prob {
   int M, N, K, tn;

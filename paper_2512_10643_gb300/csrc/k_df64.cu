@@ -57,6 +57,7 @@ struct DfTile {
   double2* C; long long ldc;
   int herm = 0;     // Hermitian C: only elements i >= j are stored from this tile...
   int mirror = 0;   // ...and, if set, C[j][i] = conj(C[i][j]) for i > j as well
+  int asplit = 0, bsplit = 0, csplit = 0;   // stored as double-float pairs (df_pack)
 };
 
 // TM x TN tile on 16 x 16 threads, (TM/16) x (TN/16) outputs each.  Every
@@ -85,25 +86,37 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
       int kk, ii;
       if (p.opa == 0) { ii = e / DK; kk = e % DK; } else { kk = e / TM; ii = e % TM; }
       const int gi = i0 + ii, gk = k0 + kk;
-      double2 v = make_double2(0.0, 0.0);
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gi < p.M && gk < kend) {
-        if (p.opa == 0) v = A[(long long)gi * p.lda + gk];
-        else { v = A[(long long)gk * p.lda + gi]; v.y = -v.y; }
+        const long long at = p.opa == 0 ? (long long)gi * p.lda + gk : (long long)gk * p.lda + gi;
+        if (p.asplit) {
+          w = reinterpret_cast<const float4*>(A)[at];
+        } else {
+          const double2 v = A[at];
+          const Df re = df_split(v.x), im = df_split(v.y);
+          w = make_float4(re.h, re.l, im.h, im.l);
+        }
+        if (p.opa) { w.z = -w.z; w.w = -w.w; }
       }
-      const Df re = df_split(v.x), im = df_split(v.y);
-      *reinterpret_cast<float4*>(&As[kk][ii][0]) = make_float4(re.h, re.l, im.h, im.l);
+      *reinterpret_cast<float4*>(&As[kk][ii][0]) = w;
     }
     for (int e = tid; e < DK * TN; e += 256) {
       int kk, jj;
       if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / DK; kk = e % DK; }
       const int gj = j0 + jj, gk = k0 + kk;
-      double2 v = make_double2(0.0, 0.0);
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gj < p.N && gk < kend) {
-        if (p.opb == 0) v = B[(long long)gk * p.ldb + gj];
-        else { v = B[(long long)gj * p.ldb + gk]; v.y = -v.y; }
+        const long long at = p.opb == 0 ? (long long)gk * p.ldb + gj : (long long)gj * p.ldb + gk;
+        if (p.bsplit) {
+          w = reinterpret_cast<const float4*>(B)[at];
+        } else {
+          const double2 v = B[at];
+          const Df re = df_split(v.x), im = df_split(v.y);
+          w = make_float4(re.h, re.l, im.h, im.l);
+        }
+        if (p.opb) { w.z = -w.z; w.w = -w.w; }
       }
-      const Df re = df_split(v.x), im = df_split(v.y);
-      *reinterpret_cast<float4*>(&Bs[kk][jj][0]) = make_float4(re.h, re.l, im.h, im.l);
+      *reinterpret_cast<float4*>(&Bs[kk][jj][0]) = w;
     }
     __syncthreads();
 #pragma unroll 2
@@ -144,9 +157,13 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
                                      (double)ah[r][c][1] + (double)al[r][c][1]);
       if (p.herm) {
         if (gi < gj) continue;
-        if (p.mirror && gi > gj) p.C[(long long)gj * p.ldc + gi] = cconj(v);
+        if (p.mirror && gi > gj) {
+          if (p.csplit) reinterpret_cast<float4*>(p.C)[(long long)gj * p.ldc + gi] = df_pack(cconj(v));
+          else p.C[(long long)gj * p.ldc + gi] = cconj(v);
+        }
       }
-      p.C[(long long)gi * p.ldc + gj] = v;
+      if (p.csplit) reinterpret_cast<float4*>(p.C)[(long long)gi * p.ldc + gj] = df_pack(v);
+      else p.C[(long long)gi * p.ldc + gj] = v;
     }
   }
 }
@@ -190,6 +207,7 @@ __global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_co
     t.C = g.work + P.part + (long long)kz * t.M * t.N;
     t.ldc = t.N;
     t.mirror = 0;
+    t.csplit = 0;
   }
   df_tile<TM, TN>(t, i0, j0, kbeg, kend, As, Bs);
 }
@@ -204,8 +222,14 @@ __global__ void df_reduce_grouped_kernel(const __grid_constant__ DfGroup g) {
     if (P.t.herm && r < c) continue;
     double2 s = make_double2(0.0, 0.0);
     for (int k = 0; k < P.ksplit; ++k) s = cadd(s, g.work[P.part + k * n + i]);
-    P.t.C[r * P.t.ldc + c] = s;
-    if (P.t.herm && r > c) P.t.C[c * P.t.ldc + r] = cconj(s);
+    if (P.t.csplit) {
+      float4* C4 = reinterpret_cast<float4*>(P.t.C);
+      C4[r * P.t.ldc + c] = df_pack(s);
+      if (P.t.herm && r > c) C4[c * P.t.ldc + r] = df_pack(cconj(s));
+    } else {
+      P.t.C[r * P.t.ldc + c] = s;
+      if (P.t.herm && r > c) P.t.C[c * P.t.ldc + r] = cconj(s);
+    }
   }
 }
 
@@ -247,12 +271,16 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
             p = DfTile{kl[c], kr[cr], 0, 0, A + off, Kc[c],
                        J.R + J.eoff[m + 1] + (cr ? (long long)kr[0] * kr[0] : 0), kr[cr], J.X + off,
                        Kc[c]};
+            p.asplit = 1;                                    // Ahat and X as pairs, R in FP64
+            p.csplit = 1;
             K = kr[cr];
           } else {
             const int c = q;
             const long long off = c ? o1 : 0;
             p = DfTile{kl[c], kl[c], 0, 1, J.X + off, Kc[c], A + off, Kc[c],
                        J.R + J.eoff[m] + (c ? (long long)kl[0] * kl[0] : 0), kl[c], 1, 1};
+            p.asplit = 1;
+            p.bsplit = 1;
             K = (int)Kc[c];                                  // R^m is Hermitian
           }
           if (p.M <= 0 || p.N <= 0) continue;
@@ -328,7 +356,8 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       for (int i = 0; i < np; ++i) {
         const DfSub& u = live[g0 + i];
         DfProb& P = G.p[i];
-        P.t = DfTile{u.M, u.N, u.opa, u.opb, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.herm, u.herm};
+        P.t = DfTile{u.M, u.N, u.opa, u.opb, u.A, u.lda, u.B, u.ldb, u.C, u.ldc, u.herm, u.herm,
+                     u.asplit, u.bsplit, u.csplit};
         P.K = u.K;
         int ks = std::max(1, std::min(target, u.K / (env_mink * DK)));
         if (!work) ks = 1;

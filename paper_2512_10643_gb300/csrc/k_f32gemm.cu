@@ -24,6 +24,8 @@ struct F32Args {
 
 __device__ __forceinline__ float2 tof(double2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ float2 tof(float2 v) { return v; }
+// a double-float pair (df_pack): its hi words are the FP64 value rounded to FP32
+__device__ __forceinline__ float2 tof(float4 v) { return make_float2(v.x, v.z); }
 
 __device__ __forceinline__ void store(float2* c, float2 v) { *c = v; }
 
@@ -124,7 +126,8 @@ cudaError_t launch_zgemm_f32_grouped(const F32Prob* probs_dev, int np, long long
                                      int b64, cudaStream_t s) {
   if (np <= 0 || ctas <= 0) return cudaSuccess;
   if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (a64 && b64) zgemm_f32_grouped_kernel<double2, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  if (a64 == 2 && b64) zgemm_f32_grouped_kernel<float4, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
+  else if (a64 && b64) zgemm_f32_grouped_kernel<double2, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
   else if (a64) zgemm_f32_grouped_kernel<double2, float2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
   else if (b64) zgemm_f32_grouped_kernel<float2, double2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);
   else zgemm_f32_grouped_kernel<float2, float2><<<(unsigned)ctas, 256, 0, s>>>(probs_dev, np);

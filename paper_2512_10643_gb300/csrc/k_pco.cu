@@ -334,7 +334,8 @@ __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n,
 // energy gauge of the mixed path: Ahat[a, p, b] = A[a, p, b] e^{-(E_b - E_a)/2}
 // (the right environment of bond m is close to diag(e^{-E}), Eq. (SVD3), so
 // this diagonal gauge makes the environments well conditioned in FP32)
-// energy gauge of one site into the parity-compact layout:
+// energy gauge of one site into the parity-compact layout, as double-float
+// pairs (df_pack):
 // Ahat[c][a][(p, j)] = A[alpha, p, beta] e^{-(E_beta - E_alpha)/2}, alpha the
 // a-th class-c state of the left bond, beta the j-th class-c^(p&1) state of
 // the right bond (an end bond's energy is 0)
@@ -345,7 +346,7 @@ __device__ inline void gauge_entry(const double2* __restrict__ A, int Dl, int d,
   pk_locate(P, d, idx, c, a, p, j, cr);
   const int al = P.pl[(c ? P.kl[0] : 0) + a], be = P.pr[(cr ? P.kr[0] : 0) + j];
   const double el = Dl > 1 ? El[al] : 0.0, er = Dr > 1 ? Er[be] : 0.0;
-  Ah[idx] = cscale(A[((long long)al * d + p) * Dr + be], exp(-0.5 * (er - el)));
+  reinterpret_cast<float4*>(Ah)[idx] = df_pack(cscale(A[((long long)al * d + p) * Dr + be], exp(-0.5 * (er - el))));
 }
 
 __global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d, int Dr,

@@ -217,15 +217,17 @@ int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2
     for (int p = 0; p < d; ++p) {
       const int cr = c ^ (p & 1);
       const long long off = (c ? o1 : 0) + pk_off(p, Dr, P.kr, c);
+      // Ahat and X as double-float pairs, R in FP64
       sub.push_back(DfSub{0, 0, P.kl[c], P.kr[cr], P.kr[cr], A + off, K[c],
-                          Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0});
+                          Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0,
+                          1, 0, 1});
     }
   CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
   sub.clear();
   for (int c = 0; c < 2; ++c) {
     const long long off = c ? o1 : 0;
     sub.push_back(DfSub{0, 1, P.kl[c], P.kl[c], (int)K[c], X + off, K[c], A + off, K[c],
-                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1});
+                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1, 1, 1, 0});
   }
   CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
   return GBSMPS_OK;
@@ -495,7 +497,7 @@ int canon_sites_grouped(gbsmps_mps* M, CanonWork* w0, cudaStream_t st) {
     if (!pa.empty()) CK(cudaMemcpyAsync(dpa, pa.data(), sizeof(F32Prob) * pa.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dpj, pj.data(), sizeof(PackJob) * pj.size(), cudaMemcpyHostToDevice, st));
     // the canonical tensors feed fp16x2 planes: FP32 products suffice
-    CK(launch_zgemm_f32_grouped(dpt, (int)pt.size(), ct, 1, 1, st));
+    CK(launch_zgemm_f32_grouped(dpt, (int)pt.size(), ct, 2, 1, st));   // Ahat as pairs
     CK(launch_zgemm_f32_grouped(dpa, (int)pa.size(), ca, 1, 0, st));
     CK(launch_pack_compact_batch(dpj, (int)pj.size(), d, st));
     for (int m = m0; m < m1; ++m)
