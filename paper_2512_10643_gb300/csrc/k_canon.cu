@@ -471,8 +471,8 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
   if (blockIdx.x == 0 && threadIdx.x == 0) { cnt[0] = S; cnt[1] = 0; }
 }
 
-// One lane per sample for the draw, one warp per SEL_SPW samples for the copy.
-// Lane l < SEL_SPW of warp w takes global row t = SEL_SPW w + l: row t of group 0 or, past
+// One lane per sample for the draw, one warp per spw samples for the copy.
+// Lane l < spw of warp w takes global row t = spw w + l: row t of group 0 or, past
 // its count, row t - count0 of group 1 (the counts add up to S).  The lane
 // sums q_p from the chunk norms (fixed order), draws u, takes the first p
 // with u Z < C_p (C the running sum in p order, Z the total), and flags the
@@ -482,20 +482,20 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
 // The row order inside a group depends on the order of the reservations;
 // every row carries its sample index, and no arithmetic depends on the row.
 constexpr int SEL_THREADS = 256;
-constexpr int SEL_SPW = 4;        // samples per warp: the warp copies their rows one by one
+constexpr int SEL_SPW_DEFAULT = 4;   // samples per warp (the warp copies their rows one by one)
 __global__ void __launch_bounds__(SEL_THREADS)
-select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
+select_groups_kernel(int S, int spw, int d, const SelGroup g0, const SelGroup g1, const NextGroup n0,
                      const NextGroup n1, int* cnt_next, const double* __restrict__ u, int ustride,
                      int site, uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out, int N,
                      uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long t = wg * SEL_SPW + lane;      // lanes 0 .. SEL_SPW-1 take a sample each
-  if (wg * SEL_SPW >= S) return;                // whole warps only: the warp syncs below
+  const long long t = wg * spw + lane;          // lanes 0 .. spw-1 take a sample each
+  if (wg * spw >= S) return;                    // whole warps only: the warp syncs below
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
   const int grp = t >= M0 ? 1 : 0;
   const int r = (int)(t - (grp ? M0 : 0));
-  const bool active = lane < SEL_SPW && t < S && r < (grp ? M1 : M0);
+  const bool active = lane < spw && t < S && r < (grp ? M1 : M0);
   const SelGroup& g = grp ? g1 : g0;
   int pstar = 0, np = 0, s = 0;
   float inv = 0.f;
@@ -581,26 +581,26 @@ select_groups_kernel(int S, int d, const SelGroup g0, const SelGroup g1, const N
 // of the planes and transforms), so the rule "first p with u Z < C_p" picks
 // p = 0 whenever u < q_0 - margin, margin >= |Z - 1|.  Here only block 0 of
 // each group has been multiplied (W holds it, and its chunk norms).  One
-// lane per sample (SEL_SPW per warp): a draw below q_0 - margin emits p = 0 and appends
+// lane per sample (spw per warp): a draw below q_0 - margin emits p = 0 and appends
 // w_0 / sqrt(q_0) to the next group of the same class; every other sample
 // (and every sample when the build's largest Cholesky regulariser exceeds
 // reg_ok, which bounds |Z - 1|) is copied to a rest group for the full pass.
 // Such a sample's draw is not flagged here; the full pass flags it.  One
 // atomic per destination and warp; the warp copies the rows.
 __global__ void __launch_bounds__(SEL_THREADS)
-select_pre_kernel(int S, const SelGroup g0, const SelGroup g1, const NextGroup n0,
+select_pre_kernel(int S, int spw, const SelGroup g0, const SelGroup g1, const NextGroup n0,
                   const NextGroup n1, int* cnt_next, const RestGroup r0, const RestGroup r1,
                   const unsigned long long* __restrict__ regmax, double reg_ok,
                   const double* __restrict__ u, int ustride, int site, uint64_t seed,
                   uint64_t counter0, uint8_t* __restrict__ out, int N, double margin) {
   const int lane = threadIdx.x & 31;
   const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long t = wg * SEL_SPW + lane;      // lanes 0 .. SEL_SPW-1 take a sample each
-  if (wg * SEL_SPW >= S) return;                // whole warps only: the warp syncs below
+  const long long t = wg * spw + lane;          // lanes 0 .. spw-1 take a sample each
+  if (wg * spw >= S) return;                    // whole warps only: the warp syncs below
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
   const int grp = t >= M0 ? 1 : 0;
   const int r = (int)(t - (grp ? M0 : 0));
-  const bool active = lane < SEL_SPW && t < S && r < (grp ? M1 : M0);
+  const bool active = lane < spw && t < S && r < (grp ? M1 : M0);
   const SelGroup& g = grp ? g1 : g0;
   const bool reg_good = __longlong_as_double((long long)*regmax) <= reg_ok;
   bool cut = false;
@@ -879,15 +879,25 @@ cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int*
   return cudaGetLastError();
 }
 
+// samples per warp of the selection passes (a performance knob: every value
+// draws the same patterns): GBSMPS_SEL_SPW in 1 .. 32, default 4
+static int sel_spw() {
+  const char* e = getenv("GBSMPS_SEL_SPW");
+  const int v = e ? atoi(e) : SEL_SPW_DEFAULT;
+  return v < 1 ? 1 : (v > 32 ? 32 : v);
+}
+
 cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,
                                  const NextGroup& n0, const NextGroup& n1, int* cnt_next,
                                  const double* u, int ustride, int site, uint64_t seed,
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s) {
-  long long threads = ((long long)Scap + SEL_SPW - 1) / SEL_SPW * 32;   // SEL_SPW samples per warp
+  const int spw = sel_spw();
+  long long threads = ((long long)Scap + spw - 1) / spw * 32;   // spw samples per warp
   int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
-  select_groups_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, d, g0, g1, n0, n1, cnt_next, u, ustride,
-                                                      site, seed, counter0, out, N, flags, flag_tol);
+  select_groups_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, spw, d, g0, g1, n0, n1, cnt_next, u,
+                                                      ustride, site, seed, counter0, out, N, flags,
+                                                      flag_tol);
   return cudaGetLastError();
 }
 
@@ -900,9 +910,10 @@ cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, 
                               const RestGroup& r1, const unsigned long long* regmax, double reg_ok,
                               const double* u, int ustride, int site, uint64_t seed,
                               uint64_t counter0, uint8_t* out, int N, double margin, cudaStream_t s) {
-  long long threads = ((long long)Scap + SEL_SPW - 1) / SEL_SPW * 32;
+  const int spw = sel_spw();
+  long long threads = ((long long)Scap + spw - 1) / spw * 32;
   int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
-  select_pre_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, g0, g1, n0, n1, cnt_next, r0, r1, regmax,
+  select_pre_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, spw, g0, g1, n0, n1, cnt_next, r0, r1, regmax,
                                                    reg_ok, u, ustride, site, seed, counter0, out, N,
                                                    margin);
   return cudaGetLastError();

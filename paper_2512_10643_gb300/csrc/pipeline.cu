@@ -253,11 +253,22 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     // diagonal blocks per bond and every product a quarter of the dense one
     CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
     double2* Ah = M->tens_mixed.as<double2>();
-    for (int m = 0; m < N; ++m) {
-      CK(launch_energy_gauge(M->tensors.as<double2>() + M->toff[m], M->D[m], d, M->D[m + 1],
-                             M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
-                             parity_site(M, m), Ah + M->toff[m], s));
+    {
+      // every site in one launch
+      std::vector<GaugeTask> gt(N);
+      int gmax = 1;
+      for (int m = 0; m < N; ++m) {
+        gt[m] = GaugeTask{M->tensors.as<double2>() + M->toff[m], M->D[m], M->D[m + 1],
+                          M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap, Ah + M->toff[m],
+                          parity_site(M, m)};
+        gmax = std::max(gmax, M->D[m] * d * M->D[m + 1]);
+      }
+      DevBuf gb;
+      CK(gb.alloc(sizeof(GaugeTask) * N, s));
+      CK(cudaMemcpyAsync(gb.p, gt.data(), sizeof(GaugeTask) * N, cudaMemcpyHostToDevice, s));
+      CK(launch_energy_gauge_batch(gb.as<GaugeTask>(), N, d, gmax, s));
       COUNT_LAUNCH(1);
+      gb.release();
     }
     tm.mark("energy_gauge");
     const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
