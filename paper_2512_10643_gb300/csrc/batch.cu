@@ -125,9 +125,15 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       gbsmps_mps* M = Ms[i].get();
       CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
       const int cap = M->ba.cap;
+      const long long ne = (long long)(M->N + 1) * cap;
+      CK(M->gscale.alloc(sizeof(double) * 2 * ne, s));
+      CK(launch_gauge_scale(M->ba.E, ne, M->gscale.as<double>(), s));
+      COUNT_LAUNCH(1);
+      const double* Gup = M->gscale.as<double>();
+      const double* Gdn = Gup + ne;
       for (int m = 0; m < M->N; ++m) {
         gt[M->d].push_back(GaugeTask{M->tensors.as<double2>() + M->toff[m], M->D[m], M->D[m + 1],
-                                     M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap,
+                                     Gup + (size_t)m * cap, Gdn + (size_t)(m + 1) * cap,
                                      M->tens_mixed.as<double2>() + M->toff[m],
                                      gbs::parity_site(M, m)});
         gmax[M->d] = std::max(gmax[M->d], M->D[m] * M->d * M->D[m + 1]);
@@ -165,7 +171,9 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       ej[k] = EnvJob{N, M->d, M->ba.D, toff_d, toff_d + N, M->tens_mixed.as<double2>(), R,
                      xs[k].as<double2>(), M->ba.pcnt};
       nj[k] = NormJob{N, M->d, M->ba.D, toff_d, M->tensors.as<double2>(), R,
-                      M->tens_mixed.as<double2>(), M->ba.E + M->ba.cap, gbs::parity_site(M, 0)};
+                      M->tens_mixed.as<double2>(),
+                      M->gscale.as<double>() + (long long)(N + 1) * M->ba.cap + M->ba.cap,
+                      gbs::parity_site(M, 0)};
       maxN = std::max(maxN, N);
       maxD = std::max(maxD, M->maxD);
     }

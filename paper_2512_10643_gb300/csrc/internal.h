@@ -276,7 +276,7 @@ struct NormJob {         // one state of the batched normalisation
   double2* T;              // FP64 tensors; A^1 is rescaled in place
   const double2* R0;       // norm^2
   double2* Ah;             // mixed path: energy-gauge tensors (A^1 rewritten), else null
-  const double* E1;        // energies of bond 1 (mixed path)
+  const double* E1;        // e^{-E/2} of bond 1's states (mixed path)
   ParitySite P0;           // mixed path: parity-compact layout of site 0
 };
 cudaError_t launch_vac_norm_batch(const NormJob* jobs_dev, int count, int maxD, int* status,
@@ -298,13 +298,16 @@ cudaError_t launch_sample_select_mixed(int S, int d, int Dm, const float2* W, co
 struct GaugeTask {        // one site of a batched energy-gauge launch
   const double2* A;       // FP64 tensor, E order
   int Dl, Dr;
-  const double* El;
-  const double* Er;
+  const double* El;       // e^{+E/2} of the left bond's states (launch_gauge_scale)
+  const double* Er;       // e^{-E/2} of the right bond's states
   double2* Ah;            // parity-compact output, double-float pairs (df_pack)
   ParitySite P;
 };
 cudaError_t launch_energy_gauge_batch(const GaugeTask* tasks_dev, int ntasks, int d, int max_elems,
                                       cudaStream_t s);
+// G[i] = e^{E[i]/2}, G[n + i] = e^{-E[i]/2}: the energy gauge's factors
+cudaError_t launch_gauge_scale(const double* E, long long n, double* G, cudaStream_t s);
+// El, Er: e^{+E/2} of the left bond's states, e^{-E/2} of the right bond's
 cudaError_t launch_energy_gauge(const double2* A, int Dl, int d, int Dr, const double* El,
                                 const double* Er, const ParitySite& P, double2* Ah, cudaStream_t s);
 // allocation-free single-site build (noalloc.cu)

@@ -149,8 +149,8 @@ __global__ void vac_norm_kernel(const NormJob* __restrict__ jobs, int maxD, int*
       int c, a, p, j, cr;
       pk_locate(J.P0, d, idx, c, a, p, j, cr);
       const int be = J.P0.pr[(cr ? J.P0.kr[0] : 0) + j];
-      const double er = D1 > 1 ? J.E1[be] : 0.0;
-      reinterpret_cast<float4*>(J.Ah)[idx] = df_pack(cscale(cmul(J.T[(size_t)p * D1 + be], fac), exp(-0.5 * er)));
+      const double g = D1 > 1 ? J.E1[be] : 1.0;
+      reinterpret_cast<float4*>(J.Ah)[idx] = df_pack(cscale(cmul(J.T[(size_t)p * D1 + be], fac), g));
     }
     __syncthreads();
   }

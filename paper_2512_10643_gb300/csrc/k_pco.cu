@@ -339,14 +339,27 @@ __global__ void maps_brute_kernel(const uint8_t* __restrict__ occ, int D, int n,
 // Ahat[c][a][(p, j)] = A[alpha, p, beta] e^{-(E_beta - E_alpha)/2}, alpha the
 // a-th class-c state of the left bond, beta the j-th class-c^(p&1) state of
 // the right bond (an end bond's energy is 0)
+// (the factor e^{-(E_beta - E_alpha)/2} as e^{E_alpha/2} e^{-E_beta/2} from
+// per-bond tables: an FP64 exponential per element would run on GB300's slow
+// FP64 pipe)
 __device__ inline void gauge_entry(const double2* __restrict__ A, int Dl, int d, int Dr,
-                                   const double* __restrict__ El, const double* __restrict__ Er,
+                                   const double* __restrict__ Gup, const double* __restrict__ Gdn,
                                    const ParitySite& P, long long idx, double2* __restrict__ Ah) {
   int c, a, p, j, cr;
   pk_locate(P, d, idx, c, a, p, j, cr);
   const int al = P.pl[(c ? P.kl[0] : 0) + a], be = P.pr[(cr ? P.kr[0] : 0) + j];
-  const double el = Dl > 1 ? El[al] : 0.0, er = Dr > 1 ? Er[be] : 0.0;
-  reinterpret_cast<float4*>(Ah)[idx] = df_pack(cscale(A[((long long)al * d + p) * Dr + be], exp(-0.5 * (er - el))));
+  const double f = (Dl > 1 ? Gup[al] : 1.0) * (Dr > 1 ? Gdn[be] : 1.0);
+  reinterpret_cast<float4*>(Ah)[idx] = df_pack(cscale(A[((long long)al * d + p) * Dr + be], f));
+}
+
+// per kept state of every bond: e^{+E/2} (first nb * cap entries), e^{-E/2} (next)
+__global__ void gauge_scale_kernel(const double* __restrict__ E, long long n, double* __restrict__ G) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double h = 0.5 * E[i];
+    G[i] = exp(h);
+    G[n + i] = exp(-h);
+  }
 }
 
 __global__ void energy_gauge_kernel(const double2* __restrict__ A, int Dl, int d, int Dr,
@@ -420,6 +433,13 @@ cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int ca
   int blocks = (D * n + 255) / 256;
   if (blocks < 1) blocks = 1;
   maps_brute_kernel<<<blocks, 256, 0, s>>>(occ, D, n, low, cap, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauge_scale(const double* E, long long n, double* G, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+  gauge_scale_kernel<<<blocks, 256, 0, s>>>(E, n, G);
   return cudaGetLastError();
 }
 

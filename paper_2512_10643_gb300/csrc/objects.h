@@ -122,7 +122,8 @@ struct gbsmps_mps {
   int maxD = 1;
   long long ttot = 0, etot = 0;   // complex elements of all tensors / all environments
   DevBuf tensors, env, gsvd, bonds;
-  DevBuf tens_mixed;        // mixed path: tensors in the energy gauge, complex64
+  DevBuf tens_mixed;        // mixed path: tensors in the energy gauge (parity-compact pairs)
+  DevBuf gscale;            // mixed path: e^{+E/2} then e^{-E/2} of every bond's states
   // mixed path, right-canonical sampler: Cholesky factors of the environments,
   // their inverses, and every site's canonical tensor as fp16 planes + TMA map
   DevBuf eoff_dev, lchol, linv, bpack;
@@ -142,6 +143,7 @@ struct gbsmps_mps {
   double* cm = nullptr;
   ~gbsmps_mps() {
     tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
+    gscale.release();
     eoff_dev.release(); lchol.release(); linv.release(); bpack.release(); creg.release();
   }
 };

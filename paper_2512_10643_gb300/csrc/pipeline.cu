@@ -253,13 +253,19 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     // diagonal blocks per bond and every product a quarter of the dense one
     CK(M->tens_mixed.alloc(sizeof(double2) * M->ttot, s));
     double2* Ah = M->tens_mixed.as<double2>();
+    const long long ne = (long long)(N + 1) * cap;
+    CK(M->gscale.alloc(sizeof(double) * 2 * ne, s));
+    CK(launch_gauge_scale(M->ba.E, ne, M->gscale.as<double>(), s));
+    COUNT_LAUNCH(1);
+    const double* Gup = M->gscale.as<double>();
+    const double* Gdn = Gup + ne;
     {
       // every site in one launch
       std::vector<GaugeTask> gt(N);
       int gmax = 1;
       for (int m = 0; m < N; ++m) {
         gt[m] = GaugeTask{M->tensors.as<double2>() + M->toff[m], M->D[m], M->D[m + 1],
-                          M->ba.E + (size_t)m * cap, M->ba.E + (size_t)(m + 1) * cap, Ah + M->toff[m],
+                          Gup + (size_t)m * cap, Gdn + (size_t)(m + 1) * cap, Ah + M->toff[m],
                           parity_site(M, m)};
         gmax = std::max(gmax, M->D[m] * d * M->D[m + 1]);
       }
@@ -315,7 +321,9 @@ int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
   CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
   COUNT_LAUNCH(2);
   if (M->precision == GBSMPS_PREC_MIXED) {   // the normalised first tensor in the energy gauge
-    CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], M->ba.E, M->ba.E + cap,
+    const double* Gup = M->gscale.as<double>();
+    const double* Gdn = Gup + (long long)(N + 1) * cap;
+    CK(launch_energy_gauge(M->tensors.as<double2>(), 1, d, M->D[1], Gup, Gdn + cap,
                            parity_site(M, 0), M->tens_mixed.as<double2>(), s));
     COUNT_LAUNCH(1);
   }
