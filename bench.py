@@ -532,7 +532,7 @@ def main():
                            "the next state's environments and canonical form run beside the current sampling; "
                            "latency_ms is one state alone, build + sampling")
     line = dict(base, value=round(r["value"], 3), ms_per_step=round(r["ms_per_step"], 3),
-                dtype=("f64 gsvd/pco + df64 env + fp16x2 (3 products)/fp32 tensor-core sampling"
+                dtype=("f64 gsvd + f32 pco (f64 plane sums) + df64 env + fp16x2 (3 products)/fp32 tensor-core sampling"
                        if args.precision == "mixed" else "f64"),
                 config=cfg, samples_per_s=round(r["samples_per_s"], 1),
                 latency_ms={"p50": round(statistics.median(sm), 3),

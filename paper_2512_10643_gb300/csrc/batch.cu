@@ -97,10 +97,12 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
   for (int i = 0; i < count && !rc; ++i) rc = gbs::alloc_tensors(Ms[i].get(), s, &scr_max);
   if (rc) return rc;
   {
-    std::map<int, std::vector<SiteTask>> by_d;
-    for (int i = 0; i < count; ++i) gbs::site_tasks(Ms[i].get(), rb[i].cm, by_d[opts[i].d]);
+    // grouped by (d, precision): mixed states take the FP32 passes
+    std::map<std::pair<int, int>, std::vector<SiteTask>> by_d;
+    for (int i = 0; i < count; ++i)
+      gbs::site_tasks(Ms[i].get(), rb[i].cm, by_d[{opts[i].d, opts[i].precision}]);
     for (auto& kv : by_d) {
-      rc = gbs::run_pco(c, kv.second, scr_max, kv.first);
+      rc = gbs::run_pco(c, kv.second, scr_max, kv.first.first, kv.first.second);
       if (rc) return rc;
     }
   }

@@ -201,9 +201,9 @@ size_t pco_scratch_elems(int Dl, int Dr);
 // persistent variant for many sites: `grid` CTAs (pco_dynamic_grid(): as many
 // as fit on the GPU at once), each with a scratch slot of slot_elems
 int pco_dynamic_grid();
-cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, double2* scratch,
-                               size_t slot_elems, int grid, int* counter, int* status,
-                               cudaStream_t s);
+cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, int precision,
+                               double2* scratch, size_t slot_elems, int grid, int* counter,
+                               int* status, cudaStream_t s);
 
 // complex FP64 GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C, row-major,
 // op = 'N' or 'C' (conjugate transpose), batched with element strides.

@@ -417,14 +417,18 @@ int pco_dynamic_grid() {
   return nsm * std::max(per, 1);
 }
 
-cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, double2* scratch,
-                               size_t slot_elems, int grid, int* counter, int* status,
-                               cudaStream_t s) {
+cudaError_t launch_pco_dynamic(const SiteTask* tasks_dev, int ntasks, int d, int precision,
+                               double2* scratch, size_t slot_elems, int grid, int* counter,
+                               int* status, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e) return e;
-  pco_dynamic_kernel<double><<<grid, PCO_THREADS, 0, s>>>(tasks_dev, ntasks, d, scratch, slot_elems,
-                                                          counter, status);
+  if (precision == GBSMPS_PREC_MIXED)
+    pco_dynamic_kernel<float><<<grid, PCO_THREADS, 0, s>>>(tasks_dev, ntasks, d, scratch, slot_elems,
+                                                           counter, status);
+  else
+    pco_dynamic_kernel<double><<<grid, PCO_THREADS, 0, s>>>(tasks_dev, ntasks, d, scratch,
+                                                            slot_elems, counter, status);
   return cudaGetLastError();
 }
 

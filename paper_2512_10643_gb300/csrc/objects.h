@@ -191,7 +191,7 @@ int enqueue_readback(gbsmps_mps* M, Readback* r, cudaStream_t s);
 void finish_readback(gbsmps_mps* M, const Readback& r);
 int alloc_tensors(gbsmps_mps* M, cudaStream_t s, size_t* scr_max);
 void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTask>& out);
-int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d);
+int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d, int precision);
 int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm);
 int normalise_single(gbsmps_ctx* c, gbsmps_mps* M);
 struct CanonWork {               // temporaries of the right-canonical packing

@@ -146,10 +146,12 @@ void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTa
   }
 }
 
-int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) {
-  // the PCO build is FP64 in both precisions: it is a few percent of a step
-  // and its tensors feed FP64 amplitudes and the norm.  Up to one resident
-  // wave of sites: one CTA per site; more: persistent CTAs (below)
+int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d, int precision) {
+  // FP64 passes for FP64 states; the mixed path runs the passes in FP32 and
+  // accumulates the tensors in FP64 (GB300's FP64 pipe is 1/64 of its FP32
+  // rate; the mixed path's amplitudes are held to 1e-5 of the FP64 path's).
+  // Up to one resident wave of sites: one CTA per site; more: persistent
+  // CTAs (below)
   cudaStream_t s = c->stream;
   const int n = (int)tasks.size();
   if (n == 0) return GBSMPS_OK;
@@ -166,8 +168,8 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) 
     CK(tk.alloc(sizeof(SiteTask) * n, s));
     CK(ctr.alloc(sizeof(int), s));
     CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
-    CK(launch_pco_dynamic(tk.as<SiteTask>(), n, d, scr.as<double2>(), scr_max, grid, ctr.as<int>(),
-                          c->d_status, s));
+    CK(launch_pco_dynamic(tk.as<SiteTask>(), n, d, precision, scr.as<double2>(), scr_max, grid,
+                          ctr.as<int>(), c->d_status, s));
     COUNT_LAUNCH(1);
     scr.release();
     tk.release();
@@ -182,7 +184,7 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d) 
   CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
   for (int k0 = 0; k0 < n; k0 += wave) {
     const int cnt = std::min(wave, n - k0);
-    CK(launch_pco(tk.as<SiteTask>() + k0, cnt, d, GBSMPS_PREC_FP64, scr.as<double2>(), c->d_status, s));
+    CK(launch_pco(tk.as<SiteTask>() + k0, cnt, d, precision, scr.as<double2>(), c->d_status, s));
     COUNT_LAUNCH(1);
   }
   scr.release();
@@ -594,7 +596,7 @@ int rest_pco(gbsmps_ctx* c, FrontState* fs, cudaEvent_t gate) {
   if (rc) return rc;
   std::vector<SiteTask> tasks;
   site_tasks(M, fs->rb.cm, tasks);
-  rc = run_pco(c, tasks, scr_max, fs->opts.d);
+  rc = run_pco(c, tasks, scr_max, fs->opts.d, fs->opts.precision);
   if (rc) return rc;
   tm.mark("pco");
   return GBSMPS_OK;

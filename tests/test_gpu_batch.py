@@ -84,8 +84,13 @@ def test_batch_matches_single_builds(ctx, precisions):
             m.release()
 
 
-def test_batch_against_oracle(ctx):
-    states = _batch_states()[:4]
+@pytest.mark.parametrize("prec", [g.PREC_MIXED, g.PREC_FP64])
+def test_batch_against_oracle(ctx, prec):
+    """FP64 states: fidelity 1e-10 and amplitudes 1e-9 of the largest.  Mixed
+    states run the PCO products in FP32 (Eq. 17 with FP32 sums), so they are
+    held to the mixed contract: amplitudes within 1e-6 of the largest (the
+    contract allows 1e-5), fidelity 1 - 1e-8."""
+    states = _batch_states((prec,))[:4]
     for w, o in states:
         o["lambda2_freeze"] = _freeze_for(w)
     batch = g.MPS.batch(ctx, [np.ascontiguousarray(w.gamma) for w, _ in states],
@@ -96,12 +101,13 @@ def test_batch_against_oracle(ctx):
                                lambda2_freeze=opts["lambda2_freeze"])
             assert list(mb.info["bond_dims"]) == ref.bond_dims
             T = OM.normalise(ref.tensors)
-            assert OM.fidelity(mb.tensors(), T) >= 1 - 1e-10
+            fid_tol, amp_tol = (1e-10, 1e-9) if prec == g.PREC_FP64 else (1e-8, 1e-6)
+            assert OM.fidelity(mb.tensors(), T) >= 1 - fid_tol
             pats = wl.random_patterns(48, w.N, opts["d"], seed=90 + k)
             pats[0] = 0
             got = mb.amplitudes(pats)
             want = OM.amplitudes(T, pats)
-            assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max() + 1e-11 * np.abs(want).max()
+            assert np.abs(got - want).max() <= amp_tol * np.abs(want).max()
     finally:
         for m in batch:
             m.release()

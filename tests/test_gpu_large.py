@@ -57,7 +57,7 @@ def test_full_size_n1024(ctx):
             if site == 0:      # A^1 carries the global normalisation and phase
                 k = np.argmax(np.abs(ref))
                 ref = ref * (got.flat[k] / ref.flat[k])
-            assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+            assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()   # mixed: FP32 PCO products
         a0 = m.amplitudes(np.zeros((1, N), dtype=np.uint8))[0]
         assert abs(a0.imag) < 1e-14 and a0.real > 0
         # sampling: properties that hold at any size
