@@ -207,9 +207,11 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   const double2* R = m->env.as<double2>();
   const double2 one = cmk(1, 0), zero = cmk(0, 0);
   StageTimer tm(s);
-  // mixed path: per parity group the fp16 state planes (current and next
-  // bond), sample indices, W and chunk norms; group row counts per bond
-  DevBuf cv[6], csid[6], cw[2], cpart[2], ccnt, crest;
+  // mixed path: per parity class the fp16 state planes of the current and
+  // the next bond (row s = sample s), the class lists of sample indices
+  // (current, next, rest), the per-sample scales (current, next), W and the
+  // chunk norms per group; list counts per bond
+  DevBuf cv[4], csid[6], crs[2], cw[2], cpart[2], ccnt, crest;
   const char* tce = getenv("GBSMPS_TC");
   const int use_tc = !(tce && tce[0] == '0');
   // the p = 0 pre-pass (on unless GBSMPS_P0PASS=0): block 0 of every sample
@@ -221,9 +223,9 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   for (int64_t s0 = 0; s0 < S; s0 += chunk) {
     const int cs = (int)std::min<int64_t>(chunk, S - s0);
     if (m->precision == GBSMPS_PREC_MIXED) {
-      // right-canonical tensors: one two-group tensor-core GEMM per site,
-      // q_p = |w_p|^2 from the chunk norms, each sample appended to the group
-      // of its next parity class
+      // right-canonical tensors: per site a two-group tensor-core GEMM over
+      // the class lists (block 0 first with the pre-pass), q_p = |w_p|^2 from
+      // the chunk norms, each sample appended to the list of its next class
       const int Spad = (int)((chunk + 127) / 128 * 128);
       int Kpmax = 64, Npmax = 128;
       for (int i = 0; i < N; ++i)
@@ -232,11 +234,10 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           Npmax = std::max(Npmax, m->sg[i].Np[pi]);
         }
       if (!ccnt.p) {
-        for (int k = 0; k < (p0pass ? 6 : 4); ++k) {
-          CK(cv[k].alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
-          CK(csid[k].alloc(sizeof(int) * (size_t)Spad, s));
-        }
+        for (int k = 0; k < 4; ++k) CK(cv[k].alloc(sizeof(__half) * 2 * (size_t)Spad * Kpmax, s));
+        for (int k = 0; k < 6; ++k) CK(csid[k].alloc(sizeof(int) * (size_t)Spad, s));
         for (int k = 0; k < 2; ++k) {
+          CK(crs[k].alloc(sizeof(float) * (size_t)Spad, s));
           CK(cw[k].alloc(sizeof(float) * (size_t)chunk * Npmax, s));
           CK(cpart[k].alloc(sizeof(float) * (size_t)chunk * (Npmax / 32), s));
         }
@@ -247,47 +248,48 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
       int* rcnt = crest.as<int>();
       CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
       CK(cudaMemsetAsync(rcnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
-      int cur[2] = {0, 1}, nxt[2] = {2, 3};
+      int cur[2] = {0, 1}, nxt[2] = {2, 3};   // planes
+      int lc[2] = {0, 1}, ln[2] = {2, 3};     // lists
+      int rc = 0, rn = 1;                     // scales
       CK(launch_sampler_init(cv[cur[0]].as<__half>(), (long long)Spad * m->sg[0].Kp[0], Spad,
-                             m->sg[0].Kp[0], csid[cur[0]].as<int>(), cnt, cs, s));
+                             m->sg[0].Kp[0], csid[lc[0]].as<int>(), crs[rc].as<float>(), cnt, cs, s));
       COUNT_LAUNCH(1);
       for (int site = 0; site < N; ++site) {
         const gbsmps_mps::SiteGroups& G = m->sg[site];
-        unsigned char mapA[2][128];
         TcGroup tg[2];
         SelGroup sl[2];
         NextGroup ng[2];
         for (int pi = 0; pi < 2; ++pi) {
-          if (canon_make_map(mapA[pi], cv[cur[pi]].p, G.Kp[pi], Spad))
-            return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
-          tg[pi] = TcGroup{G.Kp[pi] / 64, G.Np[pi] / 128, cnt + 2 * site + pi, cs, cw[pi].as<float>(),
-                           (long long)G.Np[pi], cpart[pi].as<float>(), (long long)(G.Np[pi] / 32)};
-          sl[pi] = SelGroup{cnt + 2 * site + pi, csid[cur[pi]].as<int>(), cw[pi].as<float2>(),
+          const int Kpn = site + 1 < N ? m->sg[site + 1].Kp[pi] : 64;
+          tg[pi] = TcGroup{G.Kp[pi] / 64, G.Np[pi] / 128, cnt + 2 * site + pi, cs,
+                           csid[lc[pi]].as<int>(), cv[cur[pi]].as<__half>(), (long long)Spad * G.Kp[pi],
+                           crs[rc].as<float>(), cw[pi].as<float>(), (long long)G.Np[pi],
+                           cpart[pi].as<float>(), (long long)(G.Np[pi] / 32), nullptr, 0, 0, 0};
+          sl[pi] = SelGroup{cnt + 2 * site + pi, csid[lc[pi]].as<int>(), cw[pi].as<float2>(),
                             (long long)(G.Np[pi] / 2), cpart[pi].as<float>(),
                             (long long)(G.Np[pi] / 32), G.w[pi], G.w[pi ^ 1]};
-          const int Kpn = site + 1 < N ? m->sg[site + 1].Kp[pi] : 64;
           ng[pi] = NextGroup{cv[nxt[pi]].as<__half>(), (long long)Spad * Kpn, Kpn,
-                             csid[nxt[pi]].as<int>(), m->pcnt[2 * (site + 1) + pi]};
+                             csid[ln[pi]].as<int>(), m->pcnt[2 * (site + 1) + pi], crs[rn].as<float>()};
         }
         const __half* B0 = m->bpack.as<__half>() + G.boff[0];
         const __half* B1 = m->bpack.as<__half>() + G.boff[1];
         const long long bpl0 = (long long)G.Np[0] * G.Kp[0], bpl1 = (long long)G.Np[1] * G.Kp[1];
         const double* uu = du ? du + (size_t)s0 * N : nullptr;
         if (p0pass) {
-          // block 0 only (the first column tiles of each group's planes)
+          // block 0 only (the first column tiles of each group's planes),
+          // written as the next state of the same class
           TcGroup ta[2] = {tg[0], tg[1]};
           RestGroup rg[2];
-          unsigned char mapR[2][128];
           for (int pi = 0; pi < 2; ++pi) {
             ta[pi].ntn = std::min(G.Np[pi] / 128, (2 * G.w[pi] + 127) / 128);
-            rg[pi] = RestGroup{cv[cur[pi]].as<__half>(), cv[4 + pi].as<__half>(), (long long)Spad * G.Kp[pi],
-                               G.Kp[pi], csid[4 + pi].as<int>(), rcnt + 2 * site + pi};
-            if (canon_make_map(mapR[pi], cv[4 + pi].p, G.Kp[pi], Spad))
-              return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for the sample state");
+            ta[pi].W = nullptr;
+            ta[pi].Vn = ng[pi].V;
+            ta[pi].vnpl = ng[pi].vpl;
+            ta[pi].Kpn = ng[pi].Kp;
+            ta[pi].wv = 2 * G.w[pi];
+            rg[pi] = RestGroup{csid[4 + pi].as<int>(), rcnt + 2 * site + pi};
           }
-          CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), ta[0], ta[1],
-                               cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0],
-                               cv[cur[1]].as<__half>(), (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1,
+          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), ta[0], ta[1], B0, bpl0, B1, bpl1,
                                use_tc, status, sm_reserve, s));
           CK(launch_select_pre(cs, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), rg[0], rg[1],
                                m->creg.as<unsigned long long>(), 1e-10, uu, N, site, seed,
@@ -298,21 +300,18 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           SelGroup sb[2] = {sl[0], sl[1]};
           for (int pi = 0; pi < 2; ++pi) {
             tb[pi].cnt = rcnt + 2 * site + pi;
+            tb[pi].rows = csid[4 + pi].as<int>();
             sb[pi].cnt = rcnt + 2 * site + pi;
             sb[pi].sid = csid[4 + pi].as<int>();
           }
-          CK(launch_canon_gemm(mapR[0], G.map[0].data(), mapR[1], G.map[1].data(), tb[0], tb[1],
-                               cv[4].as<__half>(), (long long)Spad * G.Kp[0], cv[5].as<__half>(),
-                               (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1, use_tc, status,
-                               sm_reserve, s));
+          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), tb[0], tb[1], B0, bpl0, B1, bpl1,
+                               use_tc, status, sm_reserve, s));
           CK(launch_select_groups(cs, d, sb[0], sb[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
                                   site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
                                   dfl ? dfl + s0 : nullptr, 1e-5, s));
           COUNT_LAUNCH(1);
         } else {
-          CK(launch_canon_gemm(mapA[0], G.map[0].data(), mapA[1], G.map[1].data(), tg[0], tg[1],
-                               cv[cur[0]].as<__half>(), (long long)Spad * G.Kp[0],
-                               cv[cur[1]].as<__half>(), (long long)Spad * G.Kp[1], B0, bpl0, B1, bpl1,
+          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), tg[0], tg[1], B0, bpl0, B1, bpl1,
                                use_tc, status, sm_reserve, s));
           CK(launch_select_groups(cs, d, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
                                   site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
@@ -320,6 +319,8 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           COUNT_LAUNCH(1);
         }
         std::swap(cur, nxt);
+        std::swap(lc, ln);
+        std::swap(rc, rn);
       }
       if (g_tc_trace.on.load()) {
         // algorithmic work of the GEMMs: 8 real flops per complex product of a
@@ -374,6 +375,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   ub.release(); obuf.release(); fbuf.release(); vb.release(); wb.release(); yb.release();
   for (auto& b : cv) b.release();
   for (auto& b : csid) b.release();
+  for (auto& b : crs) b.release();
   for (auto& b : cw) b.release();
   for (auto& b : cpart) b.release();
   ccnt.release();
@@ -620,7 +622,7 @@ size_t gbsmps_estimate_bytes(int32_t N, const gbsmps_opts* o, int64_t S) {
     b += n * 2.0 * 2.0 * npg * kp * 2.0;                      // packed fp16 planes
     b += 2.0 * 8.0 * d * c2 + 2.0 * (64 << 20);               // transform buffers, split-K
     const double sp = std::ceil(S / 128.0) * 128.0;
-    b += 4.0 * (2.0 * sp * kp * 2.0 + 4.0 * sp);              // state planes, sample indices
+    b += 4.0 * 2.0 * sp * kp * 2.0 + 8.0 * 4.0 * sp;          // state planes; lists, scales
     b += 2.0 * (S * npg * 4.0 + S * (npg / 32.0) * 4.0);      // W, chunk norms
   } else {
     const double per = d * chi;

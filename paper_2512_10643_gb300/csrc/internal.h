@@ -357,12 +357,21 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
 // pi states of bond m, and column block p over the class pi^(p&1) states of
 // bond m+1, padded to 16 complex columns (widths wself for even p, wother for
 // odd p, blocks in p order).
+// The state planes are indexed by sample: row s of a class's planes holds
+// sample s's state whenever s is in that class's list, so a pass moves only
+// sample indices, never a state row.  A stored state may carry a per-sample
+// scale (the p = 0 pre-pass stores w_0 and its 1 / |w_0| beside it).
 struct TcGroup {          // one group of the two-group sampler GEMM
   int nkb, ntn;           // K blocks of 64 and N tiles of 128 (real fp16 elements)
   const int* cnt;         // rows of the group (device; nullptr: mcap)
   int mcap;               // row capacity
-  float* W; long long ldw;       // output rows, real floats per row
+  const int* rows;        // state row (sample index) of each GEMM row
+  const __half* A; long long apl;  // state planes: row stride nkb * 64, plane stride apl
+  const float* rsc;       // per-sample scale of the stored states (nullptr: 1)
+  float* W; long long ldw;       // output rows, real floats per row (nullptr: Vn instead)
   float* part; long long ldp;    // per-row norms of 32-real-column chunks
+  __half* Vn; long long vnpl;    // else: output written as fp16 planes into row rows[i] of Vn
+  int Kpn, wv;            // (row stride Kpn; real columns >= wv written as zeros, >= Kpn skipped)
 };
 struct SelGroup {         // one group as the selection pass reads it
   const int* cnt; const int* sid;
@@ -371,12 +380,11 @@ struct SelGroup {         // one group as the selection pass reads it
   int wself, wother;
 };
 struct NextGroup {        // one class of the next bond as the selection pass writes it
-  __half* V; long long vpl; int Kp; int* sid; int D;
+  __half* V; long long vpl; int Kp;  // sample-indexed state planes
+  int* sid; int D;                   // the class's sample list (appended to)
+  float* rs;                         // per-sample scale of the stored states
 };
 struct RestGroup {        // the samples of one group that the p = 0 pre-pass leaves
-  const __half* Vc;       // the group's current state planes (plane stride vpl, row Kp)
-  __half* V;              // their copies for the full pass (same layout)
-  long long vpl; int Kp;
   int* sid; int* cnt;
 };
 cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, const NextGroup& n0,
@@ -385,19 +393,18 @@ cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, 
                               const double* u, int ustride, int site, uint64_t seed,
                               uint64_t counter0, uint8_t* out, int N, double margin, cudaStream_t s);
 cudaError_t launch_parity_classes(BondArrays ba, int nb, cudaStream_t s);
-cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* mapA1,
-                              const void* mapB1, const TcGroup& g0, const TcGroup& g1,
-                              const __half* A0, long long apl0, const __half* A1, long long apl1,
-                              const __half* B0, long long bpl0, const __half* B1, long long bpl1,
-                              int use_tc, int* status, int sm_reserve, cudaStream_t s);
+cudaError_t launch_canon_gemm(const void* mapB0, const void* mapB1, const TcGroup& g0,
+                              const TcGroup& g1, const __half* B0, long long bpl0, const __half* B1,
+                              long long bpl1, int use_tc, int* status, int sm_reserve,
+                              cudaStream_t s);
 struct PackJob {          // the planes of one (site, group) from its compact tensor
   const float2* At;       // kc rows of length K
   int kc, kr0, kr1, K, w0, w1, Kp, Np;
   __half* Bp; long long bpl;
 };
 cudaError_t launch_pack_compact_batch(const PackJob* jobs_dev, int njobs, int d, cudaStream_t s);
-cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
-                                cudaStream_t s);
+cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, float* rs,
+                                int* cnt, int S, cudaStream_t s);
 cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelGroup& g1,
                                  const NextGroup& n0, const NextGroup& n1, int* cnt_next,
                                  const double* u, int ustride, int site, uint64_t seed,

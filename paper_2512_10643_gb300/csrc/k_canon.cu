@@ -10,23 +10,28 @@
 // a selection pass that reads only the chosen block of W.
 //
 // The GEMM runs on the 5th-generation tensor cores.  Both operands are
-// bounded by 1 in magnitude (vt is a unit vector, the rows of the packed At
-// are orthonormal), and each is stored as two fp16 planes, x = h + 2^-11 l
+// bounded by 1 in magnitude (vt has norm at most 1, the rows of the packed
+// At are orthonormal), and each is stored as two fp16 planes, x = h + 2^-11 l
 // with h = fp16(x), l = fp16(2^11 (x - h)): 22 significant bits above the
 // fp16 normal range and an absolute floor near 2^-35 below it.  The product
 // is h_a h_b + 2^-11 (h_a l_b + l_a h_b) (the dropped l_a l_b term is
 // 2^-22 of the scale), three tcgen05.mma per K step into two FP32
 // accumulators in tensor memory.  The kernel is persistent and
-// warp-specialised: one thread issues TMA loads of 128 x 64 tiles of both
-// planes (128-byte swizzle) into a three-stage ring, one thread issues the
-// MMAs (M = N = 128, K = 16), and eight epilogue warps (two per lane quadrant
-// of tensor memory, each with half the columns) drain the other of two
-// accumulator buffers (tcgen05.ld, W = hh + 2^-11 x, per-tile row norms,
-// rows transposed through shared memory into 128-byte coalesced stores), so
-// the epilogue of one tile overlaps the MMAs of the next.  Every wait on an
-// mbarrier is bounded in time; on a timeout the kernel records ST_TIMEOUT,
-// waits (bounded) for its own copies and MMAs in flight, and frees its
-// tensor memory.
+// warp-specialised: one warp loads a three-stage ring (a TMA copy of the
+// 128 x 64 packed-tensor tile of both planes, and a gather of the 128 state
+// rows by sample index with 16-byte cp.async copies into the same
+// 128-byte-swizzled layout), one thread issues the MMAs (M = N = 128,
+// K = 16), and eight epilogue warps (two per lane quadrant of tensor memory,
+// each with half the columns) drain the other of two accumulator buffers
+// (tcgen05.ld, W = s (hh + 2^-11 x) with the row's stored scale s, per-tile
+// row norms, rows transposed through shared memory into coalesced stores:
+// FP32 rows of W, or fp16 planes straight into the sampled rows of the next
+// bond's state), so the epilogue of one tile overlaps the MMAs of the next.
+// The state rows never move: row s of a class's planes is sample s, and the
+// passes exchange lists of sample indices.  Every wait on an mbarrier is
+// bounded in time; on a timeout the kernel records ST_TIMEOUT, waits
+// (bounded) for its own copies and MMAs in flight, and frees its tensor
+// memory.
 #include "internal.h"
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -46,7 +51,8 @@ constexpr int EPI_LD = 16;                        // floats per staged row (16 c
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_LD * 4;
 constexpr int NBAR = 2 * TSTAGES + 2 + 2 + 1;     // full, empty, acc full, acc empty, drain
 constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue warps
+constexpr int NPROD = TSTAGES;                    // load warps: warp 0 and the last two, one per stage
+constexpr int TC_THREADS = 32 * (2 + EPI_WARPS + NPROD - 1);   // + MMA warp, epilogue warps
 constexpr int TMEM_COLS = 4 * TBN;                // 2 buffers x (hh, cross) accumulators
 constexpr float LO_SCALE = 2048.f, LO_INV = 1.f / 2048.f;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
@@ -96,6 +102,23 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "%4, %5}], [%2];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
+}
+// 16-byte gathered copy into shared memory; src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+// makes this thread's completed shared-memory writes visible to the async
+// proxy (the tensor cores read their operands through it)
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -169,8 +192,7 @@ __device__ __forceinline__ int group_rows(const TcGroup& g) {
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
-                     const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
+canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
                      const TcGroup g0, const TcGroup g1, int* status) {
   extern __shared__ __align__(1024) uint8_t smraw[];
   const uint32_t raw = su32(smraw);
@@ -187,7 +209,7 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
   const int ntiles = T0 + ((M1 + TBM - 1) / TBM) * g1.ntn;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TSTAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
+      mbar_init(full0 + 8 * s, 2);                   // B copy (tx bytes) + A gather
       mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -207,29 +229,70 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  if (warp == 0) {
-    if (lane == 0) {                                  // TMA producer
-      int g = 0;
-      bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileRef tr = tile_of(t, T0, g0.ntn, g1.ntn);
-        const int m0 = tr.m0, n0 = tr.nb * TBN, nkb = tr.g ? g1.nkb : g0.nkb;
-        const CUtensorMap* mA = tr.g ? &tmA1 : &tmA0;
-        const CUtensorMap* mB = tr.g ? &tmB1 : &tmB0;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
-          const int st = g % TSTAGES, r = g / TSTAGES;
-          if (r > 0 && !mbar_wait(empty0 + 8 * st, (r - 1) & 1)) {
-            set_status(status, ST_TIMEOUT);
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-          const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
-          tma_load_3d(sA, mA, full0 + 8 * st, kb * TBK, m0, 0);    // box: both planes
-          tma_load_3d(sB, mB, full0 + 8 * st, kb * TBK, n0, 0);
-        }
+  if (warp == 0 || warp >= 2 + EPI_WARPS) {
+    // Loads.  Stage g of the ring belongs to load warp g % NPROD (warp 0,
+    // then the warps after the epilogue warps).  Lane 0 issues the TMA copy
+    // of the packed-tensor tile (B); the warp gathers the 128 state rows of
+    // the A tile by sample index, 16 bytes a lane (eight lanes per 128-byte
+    // row, four rows per instruction), into the 128-byte-swizzled layout TMA
+    // would write: chunk j of row r at r * 128 + 16 (j ^ (r & 7)).  Rows past
+    // the group's count read zeros.  Once its copies have landed the warp
+    // makes them visible to the async proxy and releases the stage, so every
+    // stage of the ring can be in flight at once.
+    const int pid = warp == 0 ? 0 : warp - (1 + EPI_WARPS);
+    int g = 0;
+    bool ok = true;
+    const int j = lane & 7;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileRef tr = tile_of(t, T0, g0.ntn, g1.ntn);
+      const TcGroup& gg = tr.g ? g1 : g0;
+      const int Mg = tr.g ? M1 : M0;
+      const int m0 = tr.m0, n0 = tr.nb * TBN, nkb = gg.nkb;
+      const long long Kp = (long long)nkb * TBK;
+      const CUtensorMap* mB = tr.g ? &tmB1 : &tmB0;
+      int ridx[4];                                    // sample of row m0 + lane + 32 k
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = m0 + lane + 32 * k;
+        ridx[k] = r < Mg ? gg.rows[r] : -1;
       }
-      // the last copy issued into each stage has landed before the CTA exits
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        if (g % NPROD != pid) continue;
+        const int st = g % TSTAGES, r = g / TSTAGES;
+        const bool free_ = r == 0 || mbar_wait(empty0 + 8 * st, (r - 1) & 1);
+        if (!__all_sync(0xffffffffu, free_)) {
+          if (lane == 0) set_status(status, ST_TIMEOUT);
+          ok = false;
+          break;
+        }
+        const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + NPL * PLANE_BYTES;
+        if (lane == 0) {
+          mbar_expect_tx(full0 + 8 * st, NPL * PLANE_BYTES);
+          tma_load_3d(sB, mB, full0 + 8 * st, kb * TBK, n0, 0);    // box: both planes
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {                 // rows 32 k .. 32 k + 31
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int row = 32 * k + (lane >> 3) + 4 * i;
+            const int src = __shfl_sync(0xffffffffu, ridx[k], row & 31);
+            const __half* p = gg.A + (long long)max(src, 0) * Kp + kb * TBK + 8 * j;
+            const uint32_t dst = sA + row * 128 + ((j ^ (row & 7)) << 4);
+            const uint32_t nb = src >= 0 ? 16u : 0u;
+            cp_async16(dst, p, nb);
+            cp_async16(dst + PLANE_BYTES, p + gg.apl, nb);
+          }
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full0 + 8 * st);
+      }
+    }
+    cp_async_wait<0>();
+    if (warp == 0 && lane == 0) {
+      // the last TMA copy issued into each stage has landed before the CTA exits
       for (int st = 0; st < TSTAGES && st < g; ++st) {
         const int last = st + TSTAGES * ((g - 1 - st) / TSTAGES);
         if (!mbar_wait(full0 + 8 * st, (last / TSTAGES) & 1)) set_status(status, ST_TIMEOUT);
@@ -279,7 +342,7 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
         if (!mbar_wait(drain, 0)) set_status(status, ST_TIMEOUT);
       }
     }
-  } else {                                            // epilogue warps
+  } else if (warp >= 2 && warp < 2 + EPI_WARPS) {    // epilogue warps
     const int q = warp & 3;                           // TMEM lanes 32q .. 32q + 31
     const int cb = ((warp - 2) >> 2) * (TBN / 2);     // this warp's half of the columns
     float* stg = epi + (warp - 2) * 32 * EPI_LD;
@@ -296,9 +359,16 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
       const TcGroup& gg = tr.g ? g1 : g0;
       const int M = tr.g ? M1 : M0;
       float* __restrict__ W = gg.W;
+      const bool vout = W == nullptr;                 // fp16 planes into the sampled rows
       const long long ldw = gg.ldw;
       const int nb = tr.nb, n0 = nb * TBN;
       const int rbase = tr.m0 + q * 32;
+      int smp = 0;                                    // sample of this lane's row
+      float rsc = 1.f;
+      if (rbase + lane < M) {
+        smp = gg.rows[rbase + lane];
+        if (gg.rsc) rsc = gg.rsc[smp];
+      }
 #pragma unroll 1
       for (int c0 = cb; c0 < cb + TBN / 2; c0 += 32) {
         float nrm = 0.f;
@@ -315,19 +385,43 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int k = 16 * hf + 4 * j + e;
-              v[e] = fmaf(LO_INV, __uint_as_float(x[k]), __uint_as_float(h[k]));
+              v[e] = rsc * fmaf(LO_INV, __uint_as_float(x[k]), __uint_as_float(h[k]));
               nrm = fmaf(v[e], v[e], nrm);
             }
-            srow[j ^ ((lane >> 1) & 3)] = make_float4(v[0], v[1], v[2], v[3]);
+            if (!vout) {
+              srow[j ^ ((lane >> 1) & 3)] = make_float4(v[0], v[1], v[2], v[3]);
+            } else {                                  // {h01, h23, l01, l23} of four columns
+              const bool in = n0 + c0 + 16 * hf + 4 * j < gg.wv;
+              __half hh[4], ll[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) split2(in ? v[e] : 0.f, hh[e], ll[e]);
+              const __half2 a0 = __halves2half2(hh[0], hh[1]), a1 = __halves2half2(hh[2], hh[3]);
+              const __half2 b0 = __halves2half2(ll[0], ll[1]), b1 = __halves2half2(ll[2], ll[3]);
+              uint4 pk;
+              pk.x = *reinterpret_cast<const uint32_t*>(&a0);
+              pk.y = *reinterpret_cast<const uint32_t*>(&a1);
+              pk.z = *reinterpret_cast<const uint32_t*>(&b0);
+              pk.w = *reinterpret_cast<const uint32_t*>(&b1);
+              reinterpret_cast<uint4*>(srow)[j ^ ((lane >> 1) & 3)] = pk;
+            }
           }
           __syncwarp();
 #pragma unroll
           for (int it = 0; it < 4; ++it) {
             const int r = it * 8 + (lane >> 2), c4 = lane & 3;
+            const int sr = __shfl_sync(0xffffffffu, smp, r);
             const float4 val = *reinterpret_cast<const float4*>(stg + r * EPI_LD + 4 * (c4 ^ ((r >> 1) & 3)));
-            if (rbase + r < M)
-              *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + n0 + c0 + 16 * hf + c4 * 4) =
-                  val;
+            const int col = n0 + c0 + 16 * hf + c4 * 4;
+            if (rbase + r < M) {
+              if (!vout) {
+                *reinterpret_cast<float4*>(W + (long long)(rbase + r) * ldw + col) = val;
+              } else if (col < gg.Kpn) {
+                __half* dst = gg.Vn + (long long)sr * gg.Kpn + col;
+                *reinterpret_cast<uint2*>(dst) = make_uint2(__float_as_uint(val.x), __float_as_uint(val.y));
+                *reinterpret_cast<uint2*>(dst + gg.vnpl) =
+                    make_uint2(__float_as_uint(val.z), __float_as_uint(val.w));
+              }
+            }
           }
           __syncwarp();
         }
@@ -350,44 +444,49 @@ canon_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_cons
 }
 
 // SIMT reference on the same packed planes (cross-check of the tcgen05 path):
-// the same three products, FP32 accumulation in k order; rows beyond the
+// the same three products, FP32 accumulation in k order, the same scale and
+// outputs; one thread per row and 32-real-column chunk; rows beyond the
 // group's device-side count are skipped
-__global__ void canon_gemm_ref_kernel(const __half* __restrict__ Ap, long long apl, int Kp,
-                                      const __half* __restrict__ Bp, long long bpl, int Np,
-                                      float2* __restrict__ W, long long ldw, const TcGroup g) {
-  const int M = group_rows(g);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * (Np / 2);
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int row = idx / (Np / 2), nc = idx % (Np / 2);
-    const __half* ah = Ap + (long long)row * Kp;
-    const __half* al = ah + apl;
-    float hh[2] = {0.f, 0.f}, xx[2] = {0.f, 0.f};
-    for (int c = 0; c < 2; ++c) {
-      const __half* bh = Bp + (long long)(2 * nc + c) * Kp;
-      const __half* bl = bh + bpl;
-      for (int k = 0; k < Kp; ++k) {
-        const float a0 = __half2float(ah[k]), a1 = __half2float(al[k]);
-        const float b0 = __half2float(bh[k]), b1 = __half2float(bl[k]);
-        hh[c] = fmaf(a0, b0, hh[c]);
-        xx[c] = fmaf(a0, b1, fmaf(a1, b0, xx[c]));
-      }
-    }
-    W[(long long)row * ldw + nc] = make_float2(fmaf(LO_INV, xx[0], hh[0]), fmaf(LO_INV, xx[1], hh[1]));
-  }
-}
-
-__global__ void canon_part_ref_kernel(const float2* __restrict__ W, long long ldw, int nchunks,
+__global__ void canon_gemm_ref_kernel(const __half* __restrict__ Bp, long long bpl, int Np,
                                       const TcGroup g) {
   const int M = group_rows(g);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * nchunks;
+  const int Kp = g.nkb * TBK, nch = Np / 32;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)M * nch;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int row = idx / nchunks, c = idx % nchunks;
-    float s = 0.f;
-    for (int j = 0; j < 16; ++j) {
-      float2 v = W[(long long)row * ldw + c * 16 + j];
-      s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+    const int row = idx / nch, c = idx % nch;
+    const int smp = g.rows[row];
+    const float sc = g.rsc ? g.rsc[smp] : 1.f;
+    const __half* ah = g.A + (long long)smp * Kp;
+    const __half* al = ah + g.apl;
+    float nrm = 0.f;
+    for (int jj = 0; jj < 16; ++jj) {
+      const int nc = 16 * c + jj;
+      float hh[2] = {0.f, 0.f}, xx[2] = {0.f, 0.f};
+      for (int e = 0; e < 2; ++e) {
+        const __half* bh = Bp + (long long)(2 * nc + e) * Kp;
+        const __half* bl = bh + bpl;
+        for (int k = 0; k < Kp; ++k) {
+          const float a0 = __half2float(ah[k]), a1 = __half2float(al[k]);
+          const float b0 = __half2float(bh[k]), b1 = __half2float(bl[k]);
+          hh[e] = fmaf(a0, b0, hh[e]);
+          xx[e] = fmaf(a0, b1, fmaf(a1, b0, xx[e]));
+        }
+      }
+      const float vr = sc * fmaf(LO_INV, xx[0], hh[0]), vi = sc * fmaf(LO_INV, xx[1], hh[1]);
+      nrm = fmaf(vi, vi, fmaf(vr, vr, nrm));
+      if (g.W) {
+        reinterpret_cast<float2*>(g.W)[(long long)row * (g.ldw / 2) + nc] = make_float2(vr, vi);
+      } else if (2 * nc < g.Kpn) {
+        const bool in = 2 * nc < g.wv;
+        __half hr[NPL], hi[NPL];
+        split2(in ? vr : 0.f, hr[0], hr[1]);
+        split2(in ? vi : 0.f, hi[0], hi[1]);
+        for (int pl = 0; pl < NPL; ++pl)
+          *reinterpret_cast<__half2*>(g.Vn + pl * g.vnpl + (long long)smp * g.Kpn + 2 * nc) =
+              __halves2half2(hr[pl], hi[pl]);
+      }
     }
-    g.part[(long long)row * g.ldp + c] = s;
+    g.part[(long long)row * g.ldp + c] = nrm;
   }
 }
 
@@ -458,15 +557,18 @@ __global__ void pack_compact_batch_kernel(const PackJob* __restrict__ jobs, int 
 }
 
 // first site: every sample in group 0 (D_0 = 1, the vacuum) with vt = [1]
-__global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt,
-                                    int S) {
+__global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, int* sid, float* rs,
+                                    int* cnt, int S) {
   const long long total = (long long)Spad * Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int k = idx % Kp;
     for (int sp = 0; sp < NPL; ++sp)
       V[sp * vpl + idx] = __float2half_rn((sp == 0 && k == 0) ? 1.f : 0.f);
-    if (k == 0 && idx / Kp < S) sid[idx / Kp] = (int)(idx / Kp);
+    if (k == 0 && idx / Kp < S) {
+      sid[idx / Kp] = (int)(idx / Kp);
+      rs[idx / Kp] = 1.f;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) { cnt[0] = S; cnt[1] = 0; }
 }
@@ -478,9 +580,10 @@ __global__ void sampler_init_kernel(__half* V, long long vpl, int Spad, int Kp, 
 // with u Z < C_p (C the running sum in p order, Z the total), and flags the
 // draw if u Z lies within flag_tol Z of any C_p.  The warp reserves its rows
 // of each next group with one atomic per group, then copies the 32 chosen
-// blocks w_{p*} / sqrt(q_{p*}) as fp16 planes (coalesced, sample by sample).
-// The row order inside a group depends on the order of the reservations;
-// every row carries its sample index, and no arithmetic depends on the row.
+// blocks w_{p*} / sqrt(q_{p*}) as fp16 planes (coalesced, sample by sample)
+// into row s (the sample's index) of the next class's planes, with scale 1.
+// The order of a next list depends on the order of the reservations; no
+// arithmetic depends on it.
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_SPW_DEFAULT = 4;   // samples per warp (the warp copies their rows one by one)
 __global__ void __launch_bounds__(SEL_THREADS)
@@ -566,46 +669,46 @@ select_groups_kernel(int S, int spw, int d, const SelGroup g0, const SelGroup g1
       __half hr[NPL], hi[NPL];
       split2(v.x * iv, hr[0], hr[1]);
       split2(v.y * iv, hi[0], hi[1]);
-      for (int pl = 0; pl < NPL; ++pl) {
-        __half2 x;
-        x.x = hr[pl]; x.y = hi[pl];
-        *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)po * ng.Kp + 2 * b) = x;
-      }
+      for (int pl = 0; pl < NPL; ++pl)
+        *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)sd * ng.Kp + 2 * b) =
+            __halves2half2(hr[pl], hi[pl]);
     }
-    if (lane == 0) ng.sid[po] = sd;
+    if (lane == 0) {
+      ng.sid[po] = sd;
+      ng.rs[sd] = 1.f;
+    }
   }
 }
 
 // The p = 0 pre-pass of a site.  In right-canonical form the weights of a
 // sample add up to its squared norm, sum_p q_p = |vt|^2 = 1 (to the rounding
 // of the planes and transforms), so the rule "first p with u Z < C_p" picks
-// p = 0 whenever u < q_0 - margin, margin >= |Z - 1|.  Here only block 0 of
-// each group has been multiplied (W holds it, and its chunk norms).  One
-// lane per sample (spw per warp): a draw below q_0 - margin emits p = 0 and appends
-// w_0 / sqrt(q_0) to the next group of the same class; every other sample
-// (and every sample when the build's largest Cholesky regulariser exceeds
-// reg_ok, which bounds |Z - 1|) is copied to a rest group for the full pass.
-// Such a sample's draw is not flagged here; the full pass flags it.  One
-// atomic per destination and warp; the warp copies the rows.
+// p = 0 whenever u < q_0 - margin, margin >= |Z - 1|.  Only block 0 of each
+// group has been multiplied: its chunk norms give q_0, and the GEMM has
+// already stored w_0 in the sample's row of the next planes of the same
+// class.  One lane per sample: a draw below q_0 - margin emits p = 0,
+// records the row's scale 1 / sqrt(q_0) and appends the sample to the next
+// list of its class; every other sample (and every sample when the build's
+// largest Cholesky regulariser exceeds reg_ok, which bounds |Z - 1|) is
+// appended to the rest list for the full pass, which draws and flags it.
+// No state row moves; one atomic per destination list and warp.
 __global__ void __launch_bounds__(SEL_THREADS)
-select_pre_kernel(int S, int spw, const SelGroup g0, const SelGroup g1, const NextGroup n0,
+select_pre_kernel(int S, const SelGroup g0, const SelGroup g1, const NextGroup n0,
                   const NextGroup n1, int* cnt_next, const RestGroup r0, const RestGroup r1,
                   const unsigned long long* __restrict__ regmax, double reg_ok,
                   const double* __restrict__ u, int ustride, int site, uint64_t seed,
                   uint64_t counter0, uint8_t* __restrict__ out, int N, double margin) {
   const int lane = threadIdx.x & 31;
-  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long t = wg * spw + lane;          // lanes 0 .. spw-1 take a sample each
-  if (wg * spw >= S) return;                    // whole warps only: the warp syncs below
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t - lane >= S) return;                     // whole warps only: the warp syncs below
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
   const int grp = t >= M0 ? 1 : 0;
   const int r = (int)(t - (grp ? M0 : 0));
-  const bool active = lane < spw && t < S && r < (grp ? M1 : M0);
+  const bool active = t < S && r < (grp ? M1 : M0);
   const SelGroup& g = grp ? g1 : g0;
   const bool reg_good = __longlong_as_double((long long)*regmax) <= reg_ok;
   bool cut = false;
   int s = 0;
-  float inv = 0.f;
   if (active) {
     s = g.sid[r];
     const float* ps = g.part + (long long)r * g.ldp;
@@ -616,12 +719,11 @@ select_pre_kernel(int S, int spw, const SelGroup g0, const SelGroup g1, const Ne
     const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
     cut = reg_good && q0 > 0.f && uu < (double)q0 - margin;
     if (cut) {
-      inv = rsqrtf(q0);
       out[(size_t)s * N + site] = 0;
+      (grp ? n1 : n0).rs[s] = rsqrtf(q0);
     }
   }
-  // rows: the next group of the same class (cut) or the rest group (not cut)
-  int pos = 0;
+  // the next list of the same class (cut) or the rest list (not cut)
   for (int c = 0; c < 4; ++c) {
     const bool mine = active && grp == (c & 1) && cut == (c < 2);
     const unsigned m = __ballot_sync(0xffffffffu, mine);
@@ -629,42 +731,9 @@ select_pre_kernel(int S, int spw, const SelGroup g0, const SelGroup g1, const Ne
     int base = 0;
     if (lane == __ffs(m) - 1) base = atomicAdd(c < 2 ? cnt_next + (c & 1) : ((c & 1) ? r1.cnt : r0.cnt), __popc(m));
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (mine) pos = base + __popc(m & ((1u << lane) - 1u));
-  }
-  unsigned todo = __ballot_sync(0xffffffffu, active && pos < S);
-  while (todo) {
-    const int src = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const int rr = __shfl_sync(0xffffffffu, r, src);
-    const int gg = __shfl_sync(0xffffffffu, grp, src);
-    const int po = __shfl_sync(0xffffffffu, pos, src);
-    const int sd = __shfl_sync(0xffffffffu, s, src);
-    const bool ct = __shfl_sync(0xffffffffu, cut ? 1 : 0, src) != 0;
-    const float iv = __shfl_sync(0xffffffffu, inv, src);
-    if (ct) {                                     // w_0 / sqrt(q_0) into the next group gg
-      const SelGroup& G = gg ? g1 : g0;
-      const NextGroup& ng = gg ? n1 : n0;
-      const float2* wr = G.W + (long long)rr * G.ldw;
-      for (int b = lane; b < ng.Kp / 2; b += 32) {
-        const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
-        __half hr[NPL], hi[NPL];
-        split2(v.x * iv, hr[0], hr[1]);
-        split2(v.y * iv, hi[0], hi[1]);
-        for (int pl = 0; pl < NPL; ++pl) {
-          __half2 x;
-          x.x = hr[pl]; x.y = hi[pl];
-          *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)po * ng.Kp + 2 * b) = x;
-        }
-      }
-      if (lane == 0) ng.sid[po] = sd;
-    } else {                                      // the state row into the rest group gg
-      const RestGroup& R = gg ? r1 : r0;
-      for (int pl = 0; pl < NPL; ++pl) {
-        const uint4* a = reinterpret_cast<const uint4*>(R.Vc + pl * R.vpl + (long long)rr * R.Kp);
-        uint4* b = reinterpret_cast<uint4*>(R.V + pl * R.vpl + (long long)po * R.Kp);
-        for (int k = lane; k < R.Kp / 8; k += 32) b[k] = a[k];
-      }
-      if (lane == 0) R.sid[po] = sd;
+    if (mine) {
+      const int pos = base + __popc(m & ((1u << lane) - 1u));
+      if (pos < S) (c < 2 ? ((c & 1) ? n1.sid : n0.sid) : ((c & 1) ? r1.sid : r0.sid))[pos] = s;
     }
   }
 }
@@ -802,17 +871,21 @@ int canon_make_map(void* map128, const void* planes, int Kp, long long rows) {
   return r == CUDA_SUCCESS ? 0 : 3;
 }
 
-cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* mapA1,
-                              const void* mapB1, const TcGroup& g0, const TcGroup& g1,
-                              const __half* A0, long long apl0, const __half* A1, long long apl1,
-                              const __half* B0, long long bpl0, const __half* B1, long long bpl1,
-                              int use_tc, int* status, int sm_reserve, cudaStream_t s) {
-  COUNT_LAUNCH(1);
+cudaError_t launch_canon_gemm(const void* mapB0, const void* mapB1, const TcGroup& g0,
+                              const TcGroup& g1, const __half* B0, long long bpl0, const __half* B1,
+                              long long bpl1, int use_tc, int* status, int sm_reserve,
+                              cudaStream_t s) {
   // the row counts live on the device: the launch is sized for the capacity
   // and the kernel's tiles stop at the counts (the trace adds the
   // algorithmic work once the counts are known)
+  for (int gi = 0; gi < 2; ++gi) {
+    const TcGroup& g = gi ? g1 : g0;
+    if (!g.rows || !g.A || !g.part || (!g.W && !g.Vn)) return cudaErrorInvalidValue;
+    if (!g.W && g.ntn > 0 && (g.Kpn % 64 || g.Kpn > g.ntn * TBN)) return cudaErrorInvalidValue;
+  }
   cudaEvent_t tr0 = g_tc_trace.begin(s);
   if (use_tc) {
+    COUNT_LAUNCH(1);
     static std::atomic<int> nsm[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -827,30 +900,22 @@ cudaError_t launch_canon_gemm(const void* mapA0, const void* mapB0, const void* 
       if (e) return e;
       nsm[dev].store(n);
     }
-    CUtensorMap a0, b0, a1, b1;
-    memcpy(&a0, mapA0, sizeof(CUtensorMap));
+    CUtensorMap b0, b1;
     memcpy(&b0, mapB0, sizeof(CUtensorMap));
-    memcpy(&a1, mapA1, sizeof(CUtensorMap));
     memcpy(&b1, mapB1, sizeof(CUtensorMap));
     const long long cap = ((long long)(g0.mcap + TBM - 1) / TBM) * g0.ntn +
                           ((long long)(g1.mcap + TBM - 1) / TBM) * g1.ntn;
     const int grid = (int)std::max<long long>(
         1, std::min<long long>(std::max(1, nsm[dev].load() - std::max(0, sm_reserve)), cap));
-    canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(a0, b0, a1, b1, g0, g1, status);
+    canon_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(b0, b1, g0, g1, status);
   } else {
     for (int gi = 0; gi < 2; ++gi) {
       const TcGroup& g = gi ? g1 : g0;
-      const int Kp = g.nkb * TBK, Np = g.ntn * TBN;
-      long long n = (long long)g.mcap * (Np / 2);
+      const int Np = g.ntn * TBN;
+      long long n = (long long)g.mcap * (Np / 32);
       int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 16384));
-      canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(gi ? A1 : A0, gi ? apl1 : apl0, Kp, gi ? B1 : B0,
-                                                    gi ? bpl1 : bpl0, Np,
-                                                    reinterpret_cast<float2*>(g.W), g.ldw / 2, g);
-      long long n2 = (long long)g.mcap * (Np / 32);
-      int b2 = (int)std::max<long long>(1, std::min<long long>((n2 + 255) / 256, 8192));
-      canon_part_ref_kernel<<<b2, 256, 0, s>>>(reinterpret_cast<const float2*>(g.W), g.ldw / 2,
-                                               Np / 32, g);
-      COUNT_LAUNCH(gi ? 2 : 1);
+      canon_gemm_ref_kernel<<<blocks, 256, 0, s>>>(gi ? B1 : B0, gi ? bpl1 : bpl0, Np, g);
+      COUNT_LAUNCH(1);
     }
   }
   g_tc_trace.end(tr0, s, 0.0, 0.0);
@@ -871,11 +936,11 @@ cudaError_t launch_pack_compact_batch(const PackJob* jobs_dev, int njobs, int d,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, int* cnt, int S,
-                                cudaStream_t s) {
+cudaError_t launch_sampler_init(__half* V, long long vpl, int Spad, int Kp, int* sid, float* rs,
+                                int* cnt, int S, cudaStream_t s) {
   long long total = (long long)Spad * Kp;
   int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8192));
-  sampler_init_kernel<<<blocks, 256, 0, s>>>(V, vpl, Spad, Kp, sid, cnt, S);
+  sampler_init_kernel<<<blocks, 256, 0, s>>>(V, vpl, Spad, Kp, sid, rs, cnt, S);
   return cudaGetLastError();
 }
 
@@ -901,24 +966,23 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
   return cudaGetLastError();
 }
 
-// Both factor kernels fit on an SM beside a sampler GEMM CTA (218 KB of
-// shared memory, 320 threads x 112 registers), so they may run while another
-// state is sampled: 256 threads each, and shared memory for the largest
-// block only.
 cudaError_t launch_select_pre(int Scap, const SelGroup& g0, const SelGroup& g1, const NextGroup& n0,
                               const NextGroup& n1, int* cnt_next, const RestGroup& r0,
                               const RestGroup& r1, const unsigned long long* regmax, double reg_ok,
                               const double* u, int ustride, int site, uint64_t seed,
                               uint64_t counter0, uint8_t* out, int N, double margin, cudaStream_t s) {
-  const int spw = sel_spw();
-  long long threads = ((long long)Scap + spw - 1) / spw * 32;
-  int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
-  select_pre_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, spw, g0, g1, n0, n1, cnt_next, r0, r1, regmax,
+  const long long threads = ((long long)Scap + 31) / 32 * 32;   // one lane per sample
+  const int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
+  select_pre_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, g0, g1, n0, n1, cnt_next, r0, r1, regmax,
                                                    reg_ok, u, ustride, site, seed, counter0, out, N,
                                                    margin);
   return cudaGetLastError();
 }
 
+// Both factor kernels fit on an SM beside a sampler GEMM CTA (218 KB of
+// shared memory, 320 threads x 112 registers), so they may run while another
+// state is sampled: 256 threads each, and shared memory for the largest
+// block only.
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, unsigned long long* regmax, int* status,
                         cudaStream_t s) {
