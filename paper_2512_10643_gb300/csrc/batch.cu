@@ -158,7 +158,6 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
     std::vector<EnvJob> ej(nm);
     std::vector<NormJob> nj(nm);
     int maxN = 0, maxD = 1;
-    const double2 one = cmk(1.0, 0.0);
     for (size_t k = 0; k < nm; ++k) {
       gbsmps_mps* M = Ms[mixed[k]].get();
       const int N = M->N;
@@ -168,7 +167,8 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
       if (rc) return rc;
       CK(xs[k].alloc(sizeof(double2) * ((size_t)M->d * M->maxD * M->maxD + 8), s));
       double2* R = M->env.as<double2>();
-      CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+      static const float4 one_pair = make_float4(1.f, 0.f, 0.f, 0.f);   // R_N = 1 as a pair
+      CK(cudaMemcpyAsync(R + M->eoff[N], &one_pair, sizeof(float4), cudaMemcpyHostToDevice, s));
       const long long* toff_d = offs[k].as<long long>();
       ej[k] = EnvJob{N, M->d, M->ba.D, toff_d, toff_d + N, M->tens_mixed.as<double2>(), R,
                      xs[k].as<double2>(), M->ba.pcnt};

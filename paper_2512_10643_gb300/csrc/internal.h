@@ -326,6 +326,9 @@ struct DfSub {
   int herm;                // C Hermitian (M == N): lower triangle computed, mirrored
   int asplit = 0, bsplit = 0, csplit = 0;   // A, B, C as double-float pairs (df_pack)
 };
+// The workspace starts with DFG_CNT_BYTES of tile counters, which the caller
+// zeroes once; every launch leaves them zero.  Partials follow.
+constexpr size_t DFG_CNT_BYTES = 256 << 10;
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes);
 // herm: C (square) is Hermitian; only i >= j is computed, C[j][i] = conj(C[i][j])
@@ -336,7 +339,8 @@ struct EnvJob {
   const long long* toff;   // tensor offsets [N]
   const long long* eoff;   // environment offsets [N + 1]
   const double2* Ah;       // energy-gauge tensors
-  double2* R;              // environments (R^N = 1 on entry), two parity blocks per bond
+  double2* R;              // environments, two parity blocks per bond, as double-float pairs
+                           // (R^0 in FP64; R^N = 1 on entry)
   double2* X;              // scratch, >= d maxD^2 complex
   const int* pc;           // parity class sizes [2 (N + 1)] (device); Ah is parity-compact
 };
@@ -410,6 +414,7 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  const double* u, int ustride, int site, uint64_t seed,
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s);
+// src: the environments as double-float pairs (one float4 per complex element)
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, unsigned long long* regmax, int* status,
                         cudaStream_t s);

@@ -739,8 +739,8 @@ select_pre_kernel(int S, const SelGroup g0, const SelGroup g1, const NextGroup n
 }
 
 // ---------------------------------------------------------------- Cholesky
-// one CTA per bond: R + delta 1 = L L^dag (lower, FP64 complex), R overwritten
-// by L.  delta = reg * max diag(R) regularises the bond states the truncated
+// one CTA per bond: R + delta 1 = L L^dag (lower, FP64 complex) from the
+// environment stored as double-float pairs, written to dst.  delta = reg * max diag(R) regularises the bond states the truncated
 // right part barely reaches (near-null directions of R, which the mixed
 // path's FP32-accurate environments resolve only to ~1e-7 |R|): a sampled
 // state carries no weight there, so the weights q_p / Z move by O(delta)
@@ -750,14 +750,14 @@ __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict
                             double* __restrict__ dused, unsigned long long* regmax, int* status) {
   const int b = b0 + blockIdx.x;
   const int D = Dv[b];
-  const double2* Sm = src + off[b];
+  const float4* Sm = reinterpret_cast<const float4*>(src) + off[b];
   double2* R = dst + off[b];
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double dmax, lkk_s, il_s;
   __shared__ bool piv_ok;
   if (tid == 0) {
     double m = 0.0;
-    for (int i = 0; i < D; ++i) m = fmax(m, Sm[(long long)i * D + i].x);
+    for (int i = 0; i < D; ++i) m = fmax(m, df_unpack(Sm[(long long)i * D + i]).x);
     dmax = m;
   }
   __syncthreads();
@@ -768,7 +768,7 @@ __global__ void chol_kernel(const double2* __restrict__ src, double2* __restrict
   for (int attempt = 0; attempt < 5 && !okf; ++attempt, reg *= 100.0) {
     delta = reg * dmax;
     for (long long idx = tid; idx < (long long)D * D; idx += nt) {
-      double2 v = Sm[idx];
+      double2 v = df_unpack(Sm[idx]);
       if (idx / D == idx % D) v.x += delta;
       R[idx] = v;
     }

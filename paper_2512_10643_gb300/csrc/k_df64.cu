@@ -7,9 +7,10 @@
 // double-float numbers x = hi + lo (two FP32 words, ~44 significant bits):
 // every real multiply-add forms the product exactly with FMA (p = ah bh,
 // e = fma(ah, bh, -p) + ah bl + al bh) and adds it with Knuth's TwoSum.
-// Operands are read in FP64 and split into (hi, lo) on the way to shared
-// memory; partial sums over k-chunks (split-K, for parallelism in the short
-// sequential products) are written as FP64 and reduced in FP64.  Tiles of
+// Operands are read as stored pairs, or in FP64 and split into (hi, lo) on
+// the way to shared memory; partial sums over k-chunks (split-K, for
+// parallelism in the short sequential products) are written as pairs and
+// summed in k order by the last CTA of each output tile.  Tiles of
 // TM x TN complex outputs (16 to 64 square), 8 complex k per stage, 256
 // threads.  Two drivers: a grouped launch of many independent products (one
 // environment step of one state on its parity blocks), and a persistent
@@ -38,6 +39,21 @@ __device__ __forceinline__ void df_mac(float& h, float& l, float xh, float xl, f
   const float v = t - h;
   const float err = (h - (t - v)) + (p - v);
   l += err + e;
+  h = t;
+}
+
+// s + e = h + l exactly (TwoSum), s = fl(h + l): a normalised pair
+__device__ __forceinline__ void df_norm(float h, float l, float& s, float& e) {
+  s = h + l;
+  const float v = s - h;
+  e = (h - (s - v)) + (l - v);
+}
+// (h, l) += (xh, xl) in double-float arithmetic (TwoSum on the high words)
+__device__ __forceinline__ void df_acc(float& h, float& l, float xh, float xl) {
+  const float t = h + xh;
+  const float v = t - h;
+  const float err = (h - (t - v)) + (xh - v);
+  l += err + xl;
   h = t;
 }
 
@@ -153,17 +169,20 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
     for (int c = 0; c < RN; ++c) {
       const int gj = j0 + tx + 16 * c;
       if (gj >= p.N) continue;
-      const double2 v = make_double2((double)ah[r][c][0] + (double)al[r][c][0],
-                                     (double)ah[r][c][1] + (double)al[r][c][1]);
-      if (p.herm) {
-        if (gi < gj) continue;
-        if (p.mirror && gi > gj) {
-          if (p.csplit) reinterpret_cast<float4*>(p.C)[(long long)gj * p.ldc + gi] = df_pack(cconj(v));
-          else p.C[(long long)gj * p.ldc + gi] = cconj(v);
-        }
+      if (p.herm && gi < gj) continue;
+      if (p.csplit) {                             // normalised pairs, no FP64 arithmetic
+        float4 w;
+        df_norm(ah[r][c][0], al[r][c][0], w.x, w.y);
+        df_norm(ah[r][c][1], al[r][c][1], w.z, w.w);
+        if (p.herm && p.mirror && gi > gj)
+          reinterpret_cast<float4*>(p.C)[(long long)gj * p.ldc + gi] = make_float4(w.x, w.y, -w.z, -w.w);
+        reinterpret_cast<float4*>(p.C)[(long long)gi * p.ldc + gj] = w;
+      } else {
+        const double2 v = make_double2((double)ah[r][c][0] + (double)al[r][c][0],
+                                       (double)ah[r][c][1] + (double)al[r][c][1]);
+        if (p.herm && p.mirror && gi > gj) p.C[(long long)gj * p.ldc + gi] = cconj(v);
+        p.C[(long long)gi * p.ldc + gj] = v;
       }
-      if (p.csplit) reinterpret_cast<float4*>(p.C)[(long long)gi * p.ldc + gj] = df_pack(v);
-      else p.C[(long long)gi * p.ldc + gj] = v;
     }
   }
 }
@@ -171,18 +190,23 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
 // Many independent products C_i = op(A_i) op(B_i) in one launch (the blocks
 // of a parity-compact environment step).  CTAs are dealt to the products in
 // order (c0 = first CTA of a product); each product has its own tile grid and
-// k split, and partials of split products go to a workspace that the grouped
-// reduction sums in k order.
+// k split.  A CTA of a split product writes its partial tile as double-float
+// pairs to the workspace, then takes a ticket from the tile's counter; the
+// CTA that draws the last ticket sums the tile's partials in k order
+// (double-float additions), writes the output and resets the counter, so no
+// FP64 arithmetic and no second launch are needed.  No CTA waits for another.
 constexpr int DFG_MAX = 40;
 struct DfProb {
   DfTile t;                 // operands, dims, ops; C / ldc = the final output
   int K, ksplit, kchunk, tn;
   long long c0;             // first CTA of this product
-  long long part;           // its partials in the workspace (ksplit > 1)
+  long long part;           // its partials in the workspace (ksplit > 1), in complex elements
+  int cbase;                // its tile counters (ksplit > 1)
 };
 struct DfGroup {
   int np;
-  double2* work;
+  float4* work;             // partials, one pair of pairs per complex element
+  int* cnt;                 // tile counters: zero between launches
   DfProb p[DFG_MAX];
 };
 
@@ -190,6 +214,7 @@ template <int TM, int TN>
 __global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_constant__ DfGroup g) {
   __shared__ __align__(16) float As[DK][TM + 1][4];
   __shared__ __align__(16) float Bs[DK][TN + 1][4];
+  __shared__ int last;
   const long long b = blockIdx.x;
   int lo = 0, hi = g.np - 1;
   while (lo < hi) {                           // last product with c0 <= b
@@ -203,34 +228,54 @@ __global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_co
   const int i0 = (int)(tl / P.tn) * TM, j0 = (int)(tl % P.tn) * TN;
   const int kbeg = kz * P.kchunk, kend = min(P.K, kbeg + P.kchunk);
   DfTile t = P.t;
-  if (P.ksplit > 1) {
-    t.C = g.work + P.part + (long long)kz * t.M * t.N;
+  const bool split = P.ksplit > 1;
+  const long long MN = (long long)t.M * t.N;
+  if (split) {
+    t.C = reinterpret_cast<double2*>(g.work + P.part + (long long)kz * MN);
     t.ldc = t.N;
     t.mirror = 0;
-    t.csplit = 0;
+    t.csplit = 1;
   }
   df_tile<TM, TN>(t, i0, j0, kbeg, kend, As, Bs);
-}
-
-__global__ void df_reduce_grouped_kernel(const __grid_constant__ DfGroup g) {
-  const DfProb& P = g.p[blockIdx.y];
-  if (P.ksplit <= 1) return;
-  const long long M = P.t.M, N = P.t.N, n = M * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / N, c = i % N;
-    if (P.t.herm && r < c) continue;
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < P.ksplit; ++k) s = cadd(s, g.work[P.part + k * n + i]);
-    if (P.t.csplit) {
-      float4* C4 = reinterpret_cast<float4*>(P.t.C);
-      C4[r * P.t.ldc + c] = df_pack(s);
-      if (P.t.herm && r > c) C4[c * P.t.ldc + r] = df_pack(cconj(s));
+  if (!split || (t.herm && i0 + TM - 1 < j0)) return;   // (a tile above a Hermitian diagonal: unused)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(g.cnt + P.cbase + tl, 1) == P.ksplit - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const DfTile& o = P.t;
+  for (int e = threadIdx.x; e < TM * TN; e += blockDim.x) {
+    const int gi = i0 + e / TN, gj = j0 + e % TN;
+    if (gi >= o.M || gj >= o.N || (o.herm && gi < gj)) continue;
+    const float4* src = g.work + P.part + (long long)gi * o.N + gj;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int k0 = 0; k0 < P.ksplit; k0 += 8) {     // eight loads in flight, summed in k order
+      float4 w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = k0 + k < P.ksplit ? __ldcg(src + (long long)(k0 + k) * MN) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k0 + k >= P.ksplit) break;
+        df_acc(rh, rl, w[k].x, w[k].y);
+        df_acc(ih, il, w[k].z, w[k].w);
+      }
+    }
+    if (o.csplit) {
+      float4 w;
+      df_norm(rh, rl, w.x, w.y);
+      df_norm(ih, il, w.z, w.w);
+      float4* C4 = reinterpret_cast<float4*>(o.C);
+      C4[(long long)gi * o.ldc + gj] = w;
+      if (o.herm && gi > gj) C4[(long long)gj * o.ldc + gi] = make_float4(w.x, w.y, -w.z, -w.w);
     } else {
-      P.t.C[r * P.t.ldc + c] = s;
-      if (P.t.herm && r > c) P.t.C[c * P.t.ldc + r] = cconj(s);
+      const double2 v = make_double2((double)rh + (double)rl, (double)ih + (double)il);
+      o.C[(long long)gi * o.ldc + gj] = v;
+      if (o.herm && gi > gj) o.C[(long long)gj * o.ldc + gi] = cconj(v);
     }
   }
+  if (threadIdx.x == 0) g.cnt[P.cbase + tl] = 0;
 }
 
 // Right-environment chains of many states in one persistent cooperative
@@ -271,7 +316,8 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
             p = DfTile{kl[c], kr[cr], 0, 0, A + off, Kc[c],
                        J.R + J.eoff[m + 1] + (cr ? (long long)kr[0] * kr[0] : 0), kr[cr], J.X + off,
                        Kc[c]};
-            p.asplit = 1;                                    // Ahat and X as pairs, R in FP64
+            p.asplit = 1;                                    // Ahat, R and X as pairs
+            p.bsplit = 1;
             p.csplit = 1;
             K = kr[cr];
           } else {
@@ -281,6 +327,7 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
                        J.R + J.eoff[m] + (c ? (long long)kl[0] * kl[0] : 0), kl[c], 1, 1};
             p.asplit = 1;
             p.bsplit = 1;
+            p.csplit = m > 0 ? 1 : 0;                        // R^0 (the squared norm) in FP64
             K = (int)Kc[c];                                  // R^m is Hermitian
           }
           if (p.M <= 0 || p.N <= 0) continue;
@@ -317,11 +364,14 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
     if (subs[i].M > 0 && subs[i].N > 0) live.push_back(subs[i]);
   for (size_t g0 = 0; g0 < live.size(); g0 += DFG_MAX) {
     const int np = (int)std::min<size_t>(DFG_MAX, live.size() - g0);
-    // tile shape: 64 x 64 when that already gives two waves, else 32 x 32
-    long long t64 = 0;
+    // tile shape: the largest of 64, 32 and 16 square that still gives two
+    // waves of tiles (16 x 16 for the 144-mode chi = 256 chain: 19.6 ms
+    // against 20.2 ms with 32 x 32)
+    long long t64 = 0, t32 = 0;
     for (int i = 0; i < np; ++i) {
       const DfSub& u = live[g0 + i];
       t64 += (long long)((u.M + 63) / 64) * ((u.N + 63) / 64);
+      t32 += (long long)((u.M + 31) / 32) * ((u.N + 31) / 32);
     }
     // Knobs.  GBSMPS_DFG_TILE = 16, 32 or 64 forces the tile shape, a pure
     // performance choice: every output sums k in the same order and the k
@@ -337,8 +387,9 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
     const int env_tile = knob("GBSMPS_DFG_TILE", 0);
     const int env_waves = std::max(1, knob("GBSMPS_DFG_WAVES", 8));
     const int env_mink = std::max(1, knob("GBSMPS_DFG_MINK", 4));
-    const int T = env_tile == 16 || env_tile == 32 || env_tile == 64 ? env_tile
-                                                                     : (t64 >= 2LL * nsm ? 64 : 32);
+    const int T = env_tile == 16 || env_tile == 32 || env_tile == 64
+                      ? env_tile
+                      : (t64 >= 2LL * nsm ? 64 : (t32 >= 2LL * nsm ? 32 : 16));
     long long tref = 0;                           // the k split follows a fixed 32 x 32 tiling
     for (int i = 0; i < np; ++i) {
       const DfSub& u = live[g0 + i];
@@ -350,9 +401,13 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
     int target = (int)std::max<long long>(1, ((long long)env_waves * nsm + tref - 1) / tref);
     DfGroup G;
     G.np = np;
-    G.work = reinterpret_cast<double2*>(work);
+    // workspace: tile counters (zeroed by the caller once), then partials
+    if (work && work_bytes <= DFG_CNT_BYTES) return cudaErrorInvalidValue;
+    G.cnt = reinterpret_cast<int*>(work);
+    G.work = work ? reinterpret_cast<float4*>(static_cast<char*>(work) + DFG_CNT_BYTES) : nullptr;
+    const size_t part_bytes = work ? work_bytes - DFG_CNT_BYTES : 0;
     for (;;) {
-      long long c0 = 0, part = 0;
+      long long c0 = 0, part = 0, ncnt = 0;
       for (int i = 0; i < np; ++i) {
         const DfSub& u = live[g0 + i];
         DfProb& P = G.p[i];
@@ -368,11 +423,18 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
         P.tn = (u.N + T - 1) / T;
         P.c0 = c0;
         P.part = part;
-        c0 += (long long)((u.M + T - 1) / T) * P.tn * ks;
-        if (ks > 1) part += (long long)ks * u.M * u.N;
+        P.cbase = (int)ncnt;
+        const long long tiles = (long long)((u.M + T - 1) / T) * P.tn;
+        c0 += tiles * ks;
+        if (ks > 1) {
+          part += (long long)ks * u.M * u.N;
+          ncnt += tiles;
+        }
       }
-      if ((size_t)part * sizeof(double2) <= work_bytes || target == 1) {
-        if ((size_t)part * sizeof(double2) > work_bytes) return cudaErrorInvalidValue;
+      const bool fits = (size_t)part * sizeof(float4) <= part_bytes &&
+                        (size_t)ncnt * sizeof(int) <= DFG_CNT_BYTES;
+      if (fits || target == 1) {
+        if (!fits) return cudaErrorInvalidValue;
         if (c0 > 0x7fffffffLL) return cudaErrorInvalidValue;
         if (T == 64)
           zgemm_df64_grouped_kernel<64, 64><<<(unsigned)c0, 256, 0, s>>>(G);
@@ -381,10 +443,6 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
         else
           zgemm_df64_grouped_kernel<16, 16><<<(unsigned)c0, 256, 0, s>>>(G);
         COUNT_LAUNCH(1);
-        if (part > 0) {
-          df_reduce_grouped_kernel<<<dim3(64, np), 256, 0, s>>>(G);
-          COUNT_LAUNCH(1);
-        }
         break;
       }
       target = std::max(1, target / 2);

@@ -219,17 +219,19 @@ int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2
     for (int p = 0; p < d; ++p) {
       const int cr = c ^ (p & 1);
       const long long off = (c ? o1 : 0) + pk_off(p, Dr, P.kr, c);
-      // Ahat and X as double-float pairs, R in FP64
+      // Ahat, R (bonds 1 .. N) and X as double-float pairs
       sub.push_back(DfSub{0, 0, P.kl[c], P.kr[cr], P.kr[cr], A + off, K[c],
                           Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0,
-                          1, 0, 1});
+                          1, 1, 1});
     }
   CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
   sub.clear();
   for (int c = 0; c < 2; ++c) {
     const long long off = c ? o1 : 0;
+    // R_m as pairs too, but R_0 (the squared norm) in FP64
     sub.push_back(DfSub{0, 1, P.kl[c], P.kl[c], (int)K[c], X + off, K[c], A + off, K[c],
-                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1, 1, 1, 0});
+                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1, 1, 1,
+                        m > 0 ? 1 : 0});
   }
   CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
   return GBSMPS_OK;
@@ -240,7 +242,12 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
   const int N = M->N, d = M->d, cap = M->ba.cap;
   double2* R = M->env.as<double2>();
   const double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
-  CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
+  // R_N = 1 (as a double-float pair on the mixed path)
+  static const float4 one_pair = make_float4(1.f, 0.f, 0.f, 0.f);
+  if (M->precision == GBSMPS_PREC_MIXED)
+    CK(cudaMemcpyAsync(R + M->eoff[N], &one_pair, sizeof(float4), cudaMemcpyHostToDevice, s));
+  else
+    CK(cudaMemcpyAsync(R + M->eoff[N], &one, sizeof(double2), cudaMemcpyHostToDevice, s));
   size_t xmax = 0;
   for (int m = 0; m < N; ++m) xmax = std::max(xmax, (size_t)M->D[m] * d * M->D[m + 1]);
   DevBuf xb;
@@ -279,9 +286,10 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
       gb.release();
     }
     tm.mark("energy_gauge");
-    const size_t wbytes = (size_t)64 << 20;      // split-K partials (FP64-reduced)
+    const size_t wbytes = ((size_t)64 << 20) + DFG_CNT_BYTES;   // tile counters, split-K partials
     DevBuf kw;
     CK(kw.alloc(wbytes, s));
+    CK(cudaMemsetAsync(kw.p, 0, DFG_CNT_BYTES, s));
     // (plain FP32 products were measured at 4.4e-5 (N = 144) and 2.8e-4
     // (N = 1024) amplitude error against FP64: the norm needs more bits)
     for (int m = N - 1; m >= 0; --m) {
