@@ -398,6 +398,15 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
                                const double* const* gammas, const gbsmps_opts* opts, int64_t S,
                                const uint64_t* seeds, const uint64_t* counter0s,
                                uint8_t* const* outs, int mem_kind) {
+  // SMs the sampler's persistent GEMM leaves to the next state's chain and
+  // build while it runs (a performance knob, GBSMPS_STREAM_RESERVE: the
+  // patterns do not depend on it)
+  const char* sre = getenv("GBSMPS_STREAM_RESERVE");
+  const int stream_reserve = sre ? std::max(0, std::min(128, atoi(sre))) : 24;
+  // the sampler's stream priority against the next build's (GBSMPS_STREAM_PRIO:
+  // 1 = the sampler first, 0 = equal)
+  const char* spe = getenv("GBSMPS_STREAM_PRIO");
+  const bool sampler_hi = spe ? atoi(spe) != 0 : true;
   if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
   if (count < 0) return fail(GBSMPS_ERR_ARG, "count < 0");
   if (count == 0) return GBSMPS_OK;
@@ -415,8 +424,9 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   }
   CK(cudaSetDevice(c->device));
   // Per state the build runs in four parts: the front (validation, GSVD
-  // chain on one SM, bases) on one of three contexts of its own, launched two
-  // states ahead; then on c's stream the PCO build, the environments and the
+  // chain on one SM, bases) on one of NF contexts of its own, launched NF - 1
+  // states ahead (a chain takes about one step, so it gets NF - 2 steps of
+  // slack); then on c's stream the PCO build, the environments and the
   // canonical form.  Iteration k runs PCO(k+1) alone, then the sampling of
   // state k (its own stream, high priority, own status word) beside the
   // environments and the canonical form of state k+1.  The PCO's CTAs hold
@@ -429,16 +439,19 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     if (e != cudaSuccess && rc == GBSMPS_OK) rc = fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
     return e == cudaSuccess;
   };
-  constexpr int NF = 3;
+  // fronts run NF - 1 states ahead (GBSMPS_STREAM_AHEAD, 1 .. NFMAX - 1)
+  constexpr int NFMAX = 6;
+  const char* sae = getenv("GBSMPS_STREAM_AHEAD");
+  const int NF = 1 + (sae ? std::max(1, std::min(NFMAX - 1, atoi(sae))) : 3);
   cudaStream_t ss = nullptr;
   cudaEvent_t pco_done = nullptr, sampled = nullptr;
-  gbsmps_ctx cf[NF];
-  DevBuf st, fst, g[NF];
-  gbs::FrontState fs[NF];
+  gbsmps_ctx cf[NFMAX];
+  DevBuf st, fst, g[NFMAX];
+  gbs::FrontState fs[NFMAX];
   gbsmps_mps* cur = nullptr;
   int lo = 0, hi = 0;
   bool ok = ck(cudaDeviceGetStreamPriorityRange(&lo, &hi)) &&
-            ck(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, hi)) &&
+            ck(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, sampler_hi ? hi : lo)) &&
             ck(cudaEventCreateWithFlags(&pco_done, cudaEventDisableTiming)) &&
             ck(cudaEventCreateWithFlags(&sampled, cudaEventDisableTiming)) &&
             ck(st.alloc(sizeof(int), c->stream)) && ck(fst.alloc(NF * sizeof(int), c->stream)) &&
@@ -467,18 +480,18 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     }
     return keep(gbs::build_front(x, Ns[k], dg, &opts[k], &fs[k % NF]));
   };
-  if (ok) ok = front(0) && (count < 2 || front(1));
+  for (int i = 0; i < std::min(count, NF - 1) && ok; ++i) ok = front(i);
   // state 0 alone
   if (ok) ok = keep(gbs::rest_pco(c, &fs[0], nullptr)) && keep(gbs::rest_env(c, &fs[0])) &&
                keep(gbs::rest_canon(c, &fs[0], nullptr, &cur));
   for (int k = 0; k < count && ok; ++k) {
     // state k is built; state k-1's sampling finished before it was handed over
-    if (k + 2 < count && !front(k + 2)) break;
+    if (k + NF - 1 < count && !front(k + NF - 1)) break;
     // (sampling k-1 has finished: the loop waited for it)
     if (k + 1 < count && !keep(gbs::rest_pco(c, &fs[(k + 1) % NF], nullptr))) break;
     // the sampling starts after PCO(k+1): no long CTA beside the sampler
     if (!ck(cudaEventRecord(pco_done, c->stream)) || !ck(cudaStreamWaitEvent(ss, pco_done, 0))) break;
-    if (!keep(gbs::sample_impl(cur, ss, st.as<int>(), k + 1 < count ? 1 : 0, 0, S, seeds[k],
+    if (!keep(gbs::sample_impl(cur, ss, st.as<int>(), k + 1 < count ? stream_reserve : 0, 0, S, seeds[k],
                                counter0s[k], nullptr, outs[k], nullptr, mem_kind)))
       break;
     if (!ck(cudaEventRecord(sampled, ss))) break;
@@ -499,7 +512,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     if (cf[i].stream) ck(cudaStreamSynchronize(cf[i].stream));
   delete cur;
   for (auto& f : fs) f.M.reset();
-  int hst[1 + NF] = {0};
+  int hst[1 + NFMAX] = {0};
   if (st.p) ck(cudaMemcpyAsync(hst, st.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (fst.p) ck(cudaMemcpyAsync(hst + 1, fst.p, NF * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   ck(cudaStreamSynchronize(c->stream));
