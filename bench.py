@@ -32,9 +32,16 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# DRAM bytes (read + write) per launch of the dominant kernel at 100,000
-# samples from an ncu capture of the current kernel (None until one is taken)
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch from an ncu capture of the current
+# kernels (None until one is taken): the sampler GEMM at 100,000 samples, and
+# the environment GEMM of the 144-mode workload (the same at any sample count)
+TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69031.8 + 37266.3) MB over 1152 launches
+ENV_TRAFFIC_BYTES_PER_LAUNCH = 4.99e6       # (7187.4 + 0.1) MB over 1440 launches
+# A double-float multiply-add (2 flops of the FP64 algorithm) costs 12 FP32
+# instructions: the exact product by FMA (4, with the low words) and Knuth's
+# TwoSum into the (hi, lo) accumulator (6) plus the low-word update (2)
+DF64_FP32_INSTR_PER_FMA = 12
+FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -233,40 +240,78 @@ def run_gpu(args, rank, local, ws, dist):
     g.gbsmps_trace(ctx.h, True)
     step(10_000)
     torch.cuda.synchronize(dev)
-    tr = g.gbsmps_trace_read(ctx.h)
+    tr = g.gbsmps_trace_read_kernel(ctx.h, 0)
+    te = g.gbsmps_trace_read_kernel(ctx.h, 1)
     g.gbsmps_trace(ctx.h, False)
     peaks, src = measured_peaks()
+    step_ms_avg = total_ms / args.steps
+    # the sampler GEMM against the tensor roof
     ach_tflops = tr["flops"] / (tr["ms"] / 1e3) / 1e12 if tr["ms"] > 0 else 0.0
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     n_launch = max(tr["launches"], 1)
-    roof = {"kernel": "canon_gemm_tc_kernel (persistent tcgen05 + TMA split-FP16 complex GEMM over "
-                      "both photon-parity groups, two launches per site: W_0 = Vt At^m[0] for every "
-                      "sample, then W = Vt At^m for the samples the p = 0 pre-pass leaves; 100k samples)",
-            "bound": "tensor", "achieved": round(ach_tflops, 3), "peak": peak,
-            "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json x 1 "
-                            "(nominal dense fp16/bf16 ratio)"),
-            "unit": "TFLOP/s", "frac": round(ach_tflops / peak, 5),
-            "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None or S != 100_000
-                        else TRAFFIC_BYTES_PER_LAUNCH),
-            "algorithmic_flops_per_launch": tr["flops"] / n_launch,
-            "algorithmic_flops_def": ("8 real flops per complex product of the nonzero parity blocks "
-                                      "the sampler multiplies: block p = 0 of every sample "
-                                      "(8 D_{m-1,c} D_{m,c}) plus all blocks of the samples the p = 0 "
-                                      "pre-pass leaves (8 D_{m-1,c} sum_p D_{m,c^(p&1)}); two launches "
-                                      "per site"),
-            "avg_launch_ms": tr["ms"] / n_launch,
-            "launches_per_step": tr["launches"],
-            "share_of_step": round(tr["ms"] / (total_ms / args.steps), 4),
-            "split_products": 3,
-            "issued_fp16_tflops": round(3 * ach_tflops, 3),
-            "issued_frac": round(3 * ach_tflops / peak, 5)}
-    if roof["traffic"] is not None and tr["ms"] > 0:
-        # the same launches against the HBM roof (the W stores dominate)
-        hbm, hsrc = peaks.get("hbm_gbs", 6800.0), src
-        gbs = roof["traffic"] / (tr["ms"] / n_launch / 1e3) / 1e9
-        roof["dram_gbs"] = round(gbs, 1)
-        roof["dram_frac"] = round(gbs / hbm, 4)
-        roof["dram_peak_source"] = f"hbm_gbs of {hsrc} MEASURED_PEAKS.json"
+    roof_s = {"kernel": "canon_gemm_tc_kernel (persistent tcgen05 split-FP16 complex GEMM over "
+                        "both photon-parity groups, A rows gathered by sample index, B by TMA; two "
+                        "launches per site: W_0 = Vt At^m[0] for every sample, written as the next "
+                        "state, then W = Vt At^m for the samples the p = 0 pre-pass leaves; 100k samples)",
+              "bound": "tensor", "achieved": round(ach_tflops, 3), "peak": peak,
+              "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json x 1 "
+                              "(nominal dense fp16/bf16 ratio)"),
+              "unit": "TFLOP/s", "frac": round(ach_tflops / peak, 5),
+              "traffic": (None if TRAFFIC_BYTES_PER_LAUNCH is None or S != 100_000
+                          else TRAFFIC_BYTES_PER_LAUNCH),
+              "algorithmic_flops_per_launch": tr["flops"] / n_launch,
+              "algorithmic_bytes_per_launch": tr["bytes"] / n_launch,
+              "algorithmic_flops_def": ("8 real flops per complex product of the nonzero parity blocks "
+                                        "the sampler multiplies: block p = 0 of every sample "
+                                        "(8 D_{m-1,c} D_{m,c}) plus all blocks of the samples the p = 0 "
+                                        "pre-pass leaves (8 D_{m-1,c} sum_p D_{m,c^(p&1)}); two launches "
+                                        "per site"),
+              "avg_launch_ms": tr["ms"] / n_launch,
+              "launches_per_step": tr["launches"],
+              "ms_per_state": round(tr["ms"], 3),
+              "share_of_step": round(tr["ms"] / step_ms_avg, 4),
+              "split_products": 3,
+              "issued_fp16_tflops": round(3 * ach_tflops, 3),
+              "issued_frac": round(3 * ach_tflops / peak, 5)}
+    if roof_s["traffic"] is not None and tr["ms"] > 0:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        gbs = roof_s["traffic"] / (tr["ms"] / n_launch / 1e3) / 1e9
+        roof_s.update(dram_gbs=round(gbs, 1), dram_frac=round(gbs / hbm, 4),
+                      dram_peak_source=f"hbm_gbs of {src} MEASURED_PEAKS.json")
+    # the environment GEMM against the FP32 pipe's double-float roof
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fmax = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
+    df_peak = nsm * FP32_LANES_PER_SM * fmax * 2.0 / DF64_FP32_INSTR_PER_FMA / 1e12
+    ne = max(te["launches"], 1)
+    ach_df = te["flops"] / (te["ms"] / 1e3) / 1e12 if te["ms"] > 0 else 0.0
+    roof_e = {"kernel": "zgemm_df64_grouped_kernel (double-float complex GEMM on the FP32 pipes, "
+                        "right-environment chain R_m = sum_p Ahat^m[p] R_{m+1} Ahat^m[p]^dag on the "
+                        "parity blocks; two grouped launches per site, split-K partials summed in k "
+                        "order by each tile's last CTA)",
+              "bound": "alu", "achieved": round(ach_df, 4), "peak": round(df_peak, 3),
+              "peak_source": (f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                              f"{fmax / 1e6:.0f} MHz (max SM clock) x 2 flops / "
+                              f"{DF64_FP32_INSTR_PER_FMA} FP32 instructions per double-float "
+                              "multiply-add"),
+              "unit": "TFLOP/s", "frac": round(ach_df / df_peak, 5) if df_peak > 0 else None,
+              "traffic": ENV_TRAFFIC_BYTES_PER_LAUNCH,
+              "algorithmic_flops_per_launch": te["flops"] / ne,
+              "algorithmic_bytes_per_launch": te["bytes"] / ne,
+              "algorithmic_flops_def": ("8 real flops per complex multiply-add of the parity-block "
+                                        "products: X_c[:, p] = Ahat_c[:, p] R_{c^(p&1)} (kl_c kr^2 "
+                                        "per block) and R_c = X_c Ahat_c^dag on its lower triangle "
+                                        "(kl_c (kl_c + 1) / 2 K_c)"),
+              "avg_launch_ms": te["ms"] / ne,
+              "launches_per_step": te["launches"],
+              "ms_per_state": round(te["ms"], 3),
+              "share_of_step": round(te["ms"] / step_ms_avg, 4)}
+    # the roofline object follows the kernel with the most device time per
+    # state on the step's critical path (the Gaussian-SVD chains run on one
+    # SM beside the step), the other is reported beside it
+    if te["ms"] >= tr["ms"]:
+        roof, roof_other = roof_e, dict(roof_s, name="sampler")
+    else:
+        roof, roof_other = roof_s, dict(roof_e, name="environments")
 
     # build-only throughput and the FP64 GPU path for comparison
     res = {}
@@ -347,7 +392,7 @@ def run_gpu(args, rank, local, ws, dist):
     ctx.close()
     return dict(value=value, samples_per_s=samples_per_s, step_ms=step_ms, launches=launches,
                 ms_per_step=total_s * 1e3 / args.steps, pipelined=pipelined,
-                roof=roof, clocks=clk.summary(), e2e=e2e, **res)
+                roof=roof, roof_other=roof_other, clocks=clk.summary(), e2e=e2e, **res)
 
 
 # --------------------------------------------------------------------------- batched build
@@ -538,7 +583,8 @@ def main():
                 latency_ms={"p50": round(statistics.median(sm), 3),
                             "p99": round(sm[min(len(sm) - 1, int(0.99 * len(sm)))], 3)},
                 build_ms=round(r.get("build_ms", 0.0), 3),
-                roofline=r["roof"], cpu_baseline=cpu, e2e=r["e2e"], gpu_launches=r["launches"],
+                roofline=r["roof"], roofline_other=r["roof_other"], cpu_baseline=cpu, e2e=r["e2e"],
+                gpu_launches=r["launches"],
                 clocks=r["clocks"])
     if "fp64_gpu" in r:
         line["fp64_gpu"] = r["fp64_gpu"]

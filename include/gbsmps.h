@@ -251,6 +251,19 @@ int gbsmps_trace(gbsmps_ctx_t ctx, int enable);
 int gbsmps_trace_read(gbsmps_ctx_t ctx, double* total_ms, int64_t* launches,
                       double* flops, double* bytes);
 
+/* The same record for one of two traced kernels: which = 0, the sampler GEMM
+ * above (gbsmps_trace_read); which = 1, the double-float complex GEMM of the
+ * right-environment chain R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (the norm,
+ * and the standard MPS sampling that Sec. I and Sec. III defer to; two
+ * grouped launches per site), whose
+ * work counts 8 real flops per complex multiply-add of the lower triangle
+ * of a Hermitian result and of every element otherwise, and whose bytes are
+ * the operands and results at 16 bytes per complex element.  Recording is
+ * switched on and cleared for both by gbsmps_trace.  GBSMPS_ERR_ARG for
+ * another `which`.  Not part of the numerical path. */
+int gbsmps_trace_read_kernel(gbsmps_ctx_t ctx, int32_t which, double* total_ms,
+                             int64_t* launches, double* flops, double* bytes);
+
 /* ---- serving: continuous batching of build + sampling requests -----------
  * Not a step of the paper's method: a request loop around it.  A server owns
  * `slots` worker threads, each with its own non-blocking CUDA stream and

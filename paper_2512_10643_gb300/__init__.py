@@ -93,6 +93,7 @@ def lib():
         "gbsmps_build_site_noalloc": (C.c_int, [vp, i32, i32, i32, vp, dbl, i32, vp, i32, vp, i32, vp]),
         "gbsmps_trace": (C.c_int, [vp, C.c_int]),
         "gbsmps_trace_read": (C.c_int, [vp, vp, vp, vp, vp]),
+        "gbsmps_trace_read_kernel": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp]),
         "gbsmps_server_opts_default": (C.c_int, [C.POINTER(ServerOpts)]),
         "gbsmps_server_create": (C.c_int, [C.c_int, C.POINTER(ServerOpts), C.POINTER(vp)]),
         "gbsmps_server_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(i64)]),
@@ -332,6 +333,15 @@ def gbsmps_trace_read(ctx):
     ms, fl, by = C.c_double(), C.c_double(), C.c_double()
     n = C.c_int64()
     _check(lib().gbsmps_trace_read(ctx, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)))
+    return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+
+
+def gbsmps_trace_read_kernel(ctx, which: int):
+    """which = 0: the sampler GEMM (as gbsmps_trace_read); 1: the environment GEMM."""
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    _check(lib().gbsmps_trace_read_kernel(ctx, int(which), C.byref(ms), C.byref(n), C.byref(fl),
+                                          C.byref(by)))
     return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
 
 

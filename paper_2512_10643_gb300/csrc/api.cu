@@ -13,6 +13,7 @@
 
 std::atomic<unsigned long long> g_kernel_launches{0};
 KernelTrace g_tc_trace;
+KernelTrace g_env_trace;
 
 thread_local std::string g_detail;
 
@@ -331,19 +332,30 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
         CK(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(hrest.data(), rcnt, sizeof(int) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        double f = 0.0;
+        // bytes: the gathered state rows (two fp16 planes), the packed
+        // tensor's planes, and the outputs (the next state's planes for the
+        // pre-pass, FP32 rows of W otherwise) with their chunk norms
+        double f = 0.0, by = 0.0;
         for (int site = 0; site < N; ++site)
           for (int pi = 0; pi < 2; ++pi) {
+            const gbsmps_mps::SiteGroups& G = m->sg[site];
             double cols = 0.0;
             for (int p = 0; p < d; ++p) cols += m->pcnt[2 * (site + 1) + (pi ^ (p & 1))];
             const double kl = m->pcnt[2 * site + pi];
-            if (p0pass)
-              f += 8.0 * kl * (hcnt[2 * site + pi] * (double)m->pcnt[2 * (site + 1) + pi] +
-                               hrest[2 * site + pi] * cols);
-            else
-              f += 8.0 * hcnt[2 * site + pi] * kl * cols;
+            const double rows = hcnt[2 * site + pi], rest = hrest[2 * site + pi];
+            const double Kp = G.Kp[pi], Np = G.Np[pi];
+            if (p0pass) {
+              const double Np0 = 128.0 * std::min(G.Np[pi] / 128, (2 * G.w[pi] + 127) / 128);
+              const double Kpn = site + 1 < N ? m->sg[site + 1].Kp[pi] : 64;
+              f += 8.0 * kl * (rows * (double)m->pcnt[2 * (site + 1) + pi] + rest * cols);
+              by += rows * (4.0 * Kp + 4.0 * Kpn + Np0 / 8.0) + 4.0 * Np0 * Kp;
+              by += rest * (4.0 * Kp + 4.0 * Np + Np / 8.0) + (rest > 0 ? 4.0 * Np * Kp : 0.0);
+            } else {
+              f += 8.0 * rows * kl * cols;
+              by += rows * (4.0 * Kp + 4.0 * Np + Np / 8.0) + 4.0 * Np * Kp;
+            }
           }
-        g_tc_trace.add_work(f, 0.0);
+        g_tc_trace.add_work(f, by);
       }
       continue;
     }
@@ -672,6 +684,8 @@ int gbsmps_trace(gbsmps_ctx_t c, int enable) {
   if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
   g_tc_trace.reset();
   g_tc_trace.on = enable != 0;
+  g_env_trace.reset();
+  g_env_trace.on = enable != 0;
   return GBSMPS_OK;
 }
 
@@ -682,6 +696,18 @@ int gbsmps_trace_read(gbsmps_ctx_t c, double* total_ms, int64_t* launches, doubl
   if (launches) *launches = g_tc_trace.launches;
   if (flops) *flops = g_tc_trace.flops;
   if (bytes) *bytes = g_tc_trace.bytes;
+  return GBSMPS_OK;
+}
+
+int gbsmps_trace_read_kernel(gbsmps_ctx_t c, int32_t which, double* total_ms, int64_t* launches,
+                             double* flops, double* bytes) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  if (which != 0 && which != 1) return fail(GBSMPS_ERR_ARG, "which must be 0 or 1");
+  KernelTrace& t = which ? g_env_trace : g_tc_trace;
+  if (total_ms) *total_ms = t.total_ms();
+  if (launches) *launches = t.launches;
+  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes;
   return GBSMPS_OK;
 }
 

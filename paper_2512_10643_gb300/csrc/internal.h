@@ -151,7 +151,8 @@ struct KernelTrace {
     ev.clear(); flops = bytes = 0.0; launches = 0;
   }
 };
-extern KernelTrace g_tc_trace;    // the tcgen05 sampler GEMM (dominant kernel)
+extern KernelTrace g_tc_trace;    // the tcgen05 sampler GEMM
+extern KernelTrace g_env_trace;   // the double-float environment GEMM
 
 // ---- launchers (each returns cudaError_t of the launch) -------------------
 // g_kernel_launches counts every kernel the library enqueues.

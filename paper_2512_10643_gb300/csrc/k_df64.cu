@@ -436,12 +436,21 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       if (fits || target == 1) {
         if (!fits) return cudaErrorInvalidValue;
         if (c0 > 0x7fffffffLL) return cudaErrorInvalidValue;
+        double fl = 0.0, by = 0.0;               // algorithmic work, for the trace
+        for (int i = 0; i < np; ++i) {
+          const DfSub& u = live[g0 + i];
+          const double outs = u.herm ? 0.5 * u.M * (u.M + 1.0) : (double)u.M * u.N;
+          fl += 8.0 * outs * u.K;
+          by += 16.0 * ((double)u.M * u.K + (double)u.K * u.N + outs);
+        }
+        cudaEvent_t tr0 = g_env_trace.begin(s);
         if (T == 64)
           zgemm_df64_grouped_kernel<64, 64><<<(unsigned)c0, 256, 0, s>>>(G);
         else if (T == 32)
           zgemm_df64_grouped_kernel<32, 32><<<(unsigned)c0, 256, 0, s>>>(G);
         else
           zgemm_df64_grouped_kernel<16, 16><<<(unsigned)c0, 256, 0, s>>>(G);
+        g_env_trace.end(tr0, s, fl, by);
         COUNT_LAUNCH(1);
         break;
       }
