@@ -78,11 +78,15 @@ struct DfTile {
 
 // TM x TN tile on 16 x 16 threads, (TM/16) x (TN/16) outputs each.  Every
 // output sums k in the same order whatever the tile shape, so the result does
-// not depend on it (the shape is a pure performance choice).
-template <int TM, int TN>
+// not depend on it (the shape is a pure performance choice).  Stages of DK k
+// run through two shared-memory buffers: the next stage's operands are read
+// into registers before the current stage's arithmetic and stored to the
+// other buffer after it, so one barrier per stage suffices.
+template <int TM, int TN, int SK = DK>
 __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbeg, int kend,
-                                        float (*As)[TM + 1][4], float (*Bs)[TN + 1][4]) {
+                                        float (*As)[SK][TM + 1][4], float (*Bs)[SK][TN + 1][4]) {
   constexpr int RM = TM / 16, RN = TN / 16;
+  constexpr int NA = (SK * TM + 255) / 256, NB = (SK * TN + 255) / 256;   // elements per thread
   // Hermitian result: a tile strictly above the diagonal is never needed
   // (its elements are the mirrors of lower ones), whatever the tile shape
   if (p.herm && i0 + TM - 1 < j0) return;
@@ -97,55 +101,91 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
       ah[r][c][0] = ah[r][c][1] = 0.f;
       al[r][c][0] = al[r][c][1] = 0.f;
     }
-  for (int k0 = kbeg; k0 < kend; k0 += DK) {
-    for (int e = tid; e < DK * TM; e += 256) {
-      int kk, ii;
-      if (p.opa == 0) { ii = e / DK; kk = e % DK; } else { kk = e / TM; ii = e % TM; }
-      const int gi = i0 + ii, gk = k0 + kk;
+  float4 ra[NA], rb[NB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + 256 * q;
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gi < p.M && gk < kend) {
-        const long long at = p.opa == 0 ? (long long)gi * p.lda + gk : (long long)gk * p.lda + gi;
-        if (p.asplit) {
-          w = reinterpret_cast<const float4*>(A)[at];
-        } else {
-          const double2 v = A[at];
-          const Df re = df_split(v.x), im = df_split(v.y);
-          w = make_float4(re.h, re.l, im.h, im.l);
+      if (e < SK * TM) {
+        int kk, ii;
+        if (p.opa == 0) { ii = e / SK; kk = e % SK; } else { kk = e / TM; ii = e % TM; }
+        const int gi = i0 + ii, gk = k0 + kk;
+        if (gi < p.M && gk < kend) {
+          const long long at = p.opa == 0 ? (long long)gi * p.lda + gk : (long long)gk * p.lda + gi;
+          if (p.asplit) {
+            w = reinterpret_cast<const float4*>(A)[at];
+          } else {
+            const double2 v = A[at];
+            const Df re = df_split(v.x), im = df_split(v.y);
+            w = make_float4(re.h, re.l, im.h, im.l);
+          }
+          if (p.opa) { w.z = -w.z; w.w = -w.w; }
         }
-        if (p.opa) { w.z = -w.z; w.w = -w.w; }
       }
-      *reinterpret_cast<float4*>(&As[kk][ii][0]) = w;
+      ra[q] = w;
     }
-    for (int e = tid; e < DK * TN; e += 256) {
-      int kk, jj;
-      if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / DK; kk = e % DK; }
-      const int gj = j0 + jj, gk = k0 + kk;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gj < p.N && gk < kend) {
-        const long long at = p.opb == 0 ? (long long)gk * p.ldb + gj : (long long)gj * p.ldb + gk;
-        if (p.bsplit) {
-          w = reinterpret_cast<const float4*>(B)[at];
-        } else {
-          const double2 v = B[at];
-          const Df re = df_split(v.x), im = df_split(v.y);
-          w = make_float4(re.h, re.l, im.h, im.l);
+      if (e < SK * TN) {
+        int kk, jj;
+        if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / SK; kk = e % SK; }
+        const int gj = j0 + jj, gk = k0 + kk;
+        if (gj < p.N && gk < kend) {
+          const long long at = p.opb == 0 ? (long long)gk * p.ldb + gj : (long long)gj * p.ldb + gk;
+          if (p.bsplit) {
+            w = reinterpret_cast<const float4*>(B)[at];
+          } else {
+            const double2 v = B[at];
+            const Df re = df_split(v.x), im = df_split(v.y);
+            w = make_float4(re.h, re.l, im.h, im.l);
+          }
+          if (p.opb) { w.z = -w.z; w.w = -w.w; }
         }
-        if (p.opb) { w.z = -w.z; w.w = -w.w; }
       }
-      *reinterpret_cast<float4*>(&Bs[kk][jj][0]) = w;
+      rb[q] = w;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + 256 * q;
+      if (e < SK * TM) {
+        const int kk = p.opa == 0 ? e % SK : e / TM, ii = p.opa == 0 ? e / SK : e % TM;
+        *reinterpret_cast<float4*>(&As[buf][kk][ii][0]) = ra[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
+      if (e < SK * TN) {
+        const int kk = p.opb == 0 ? e / TN : e % SK, jj = p.opb == 0 ? e % TN : e / SK;
+        *reinterpret_cast<float4*>(&Bs[buf][kk][jj][0]) = rb[q];
+      }
+    }
+  };
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += SK, buf ^= 1) {
+    const bool more = k0 + SK < kend;
+    if (more) load(k0 + SK);                 // in flight during the arithmetic below
 #pragma unroll 2
-    for (int kk = 0; kk < DK; ++kk) {
+    for (int kk = 0; kk < SK; ++kk) {
       float a[RM][4], b[RN][4];
 #pragma unroll
       for (int r = 0; r < RM; ++r) {
-        const float4 v = *reinterpret_cast<const float4*>(&As[kk][ty + 16 * r][0]);
+        const float4 v = *reinterpret_cast<const float4*>(&As[buf][kk][ty + 16 * r][0]);
         a[r][0] = v.x; a[r][1] = v.y; a[r][2] = v.z; a[r][3] = v.w;
       }
 #pragma unroll
       for (int c = 0; c < RN; ++c) {
-        const float4 v = *reinterpret_cast<const float4*>(&Bs[kk][tx + 16 * c][0]);
+        const float4 v = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx + 16 * c][0]);
         b[c][0] = v.x; b[c][1] = v.y; b[c][2] = v.z; b[c][3] = v.w;
       }
 #pragma unroll
@@ -159,6 +199,8 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
           df_mac(ah[r][c][1], al[r][c][1], a[r][2], a[r][3], b[c][0], b[c][1]);
         }
     }
+    // the other buffer was last read before the previous barrier
+    if (more) store(buf ^ 1);
     __syncthreads();
   }
 #pragma unroll
@@ -210,10 +252,16 @@ struct DfGroup {
   DfProb p[DFG_MAX];
 };
 
-template <int TM, int TN>
-__global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_constant__ DfGroup g) {
-  __shared__ __align__(16) float As[DK][TM + 1][4];
-  __shared__ __align__(16) float Bs[DK][TN + 1][4];
+constexpr int RED_ILP = 4;                    // partial loads in flight per thread in a tile's reduction
+
+// Resident CTAs per SM the register allocation is held to (measured for the
+// 144-mode chi = 256 chain with 16 x 16 tiles: 4, 5, 6, 8 CTAs give 18.7,
+// 17.3, 16.5, 17.8 ms)
+
+template <int TM, int TN, int SK>
+__global__ void __launch_bounds__(256, TM == 16 ? 6 : (TM == 32 ? 4 : 2)) zgemm_df64_grouped_kernel(const __grid_constant__ DfGroup g) {
+  __shared__ __align__(16) float As[2][SK][TM + 1][4];
+  __shared__ __align__(16) float Bs[2][SK][TN + 1][4];
   __shared__ int last;
   const long long b = blockIdx.x;
   int lo = 0, hi = g.np - 1;
@@ -236,7 +284,7 @@ __global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_co
     t.mirror = 0;
     t.csplit = 1;
   }
-  df_tile<TM, TN>(t, i0, j0, kbeg, kend, As, Bs);
+  df_tile<TM, TN, SK>(t, i0, j0, kbeg, kend, As, Bs);
   if (!split || (t.herm && i0 + TM - 1 < j0)) return;   // (a tile above a Hermitian diagonal: unused)
   __threadfence();
   __syncthreads();
@@ -250,13 +298,13 @@ __global__ void __launch_bounds__(256) zgemm_df64_grouped_kernel(const __grid_co
     if (gi >= o.M || gj >= o.N || (o.herm && gi < gj)) continue;
     const float4* src = g.work + P.part + (long long)gi * o.N + gj;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    for (int k0 = 0; k0 < P.ksplit; k0 += 8) {     // eight loads in flight, summed in k order
-      float4 w[8];
+    for (int k0 = 0; k0 < P.ksplit; k0 += RED_ILP) {   // RED_ILP loads in flight, summed in k order
+      float4 w[RED_ILP];
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < RED_ILP; ++k)
         w[k] = k0 + k < P.ksplit ? __ldcg(src + (long long)(k0 + k) * MN) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < RED_ILP; ++k) {
         if (k0 + k >= P.ksplit) break;
         df_acc(rh, rl, w[k].x, w[k].y);
         df_acc(ih, il, w[k].z, w[k].w);
@@ -289,8 +337,8 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
                                                        int maxN) {
   // rows padded by one 16-byte element: the k-major fills of A (and of B^dag)
   // then fall into different banks
-  __shared__ __align__(16) float As[DK][TM + 1][4];
-  __shared__ __align__(16) float Bs[DK][TN + 1][4];
+  __shared__ __align__(16) float As[2][DK][TM + 1][4];
+  __shared__ __align__(16) float Bs[2][DK][TN + 1][4];
   cg::grid_group grid = cg::this_grid();
   for (int k = 0; k < maxN; ++k) {
     for (int phase = 0; phase < 2; ++phase) {
@@ -387,6 +435,9 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
     const int env_tile = knob("GBSMPS_DFG_TILE", 0);
     const int env_waves = std::max(1, knob("GBSMPS_DFG_WAVES", 8));
     const int env_mink = std::max(1, knob("GBSMPS_DFG_MINK", 4));
+    // k per shared-memory stage of the 16 x 16 tiles (GBSMPS_DFG_SK = 8 or 16;
+    // the k order of every sum is the same)
+    const int env_sk = knob("GBSMPS_DFG_SK", 8) == 16 ? 16 : 8;
     const int T = env_tile == 16 || env_tile == 32 || env_tile == 64
                       ? env_tile
                       : (t64 >= 2LL * nsm ? 64 : (t32 >= 2LL * nsm ? 32 : 16));
@@ -445,11 +496,13 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
         }
         cudaEvent_t tr0 = g_env_trace.begin(s);
         if (T == 64)
-          zgemm_df64_grouped_kernel<64, 64><<<(unsigned)c0, 256, 0, s>>>(G);
+          zgemm_df64_grouped_kernel<64, 64, DK><<<(unsigned)c0, 256, 0, s>>>(G);
         else if (T == 32)
-          zgemm_df64_grouped_kernel<32, 32><<<(unsigned)c0, 256, 0, s>>>(G);
+          zgemm_df64_grouped_kernel<32, 32, DK><<<(unsigned)c0, 256, 0, s>>>(G);
+        else if (env_sk == 8)
+          zgemm_df64_grouped_kernel<16, 16, 8><<<(unsigned)c0, 256, 0, s>>>(G);
         else
-          zgemm_df64_grouped_kernel<16, 16><<<(unsigned)c0, 256, 0, s>>>(G);
+          zgemm_df64_grouped_kernel<16, 16, 16><<<(unsigned)c0, 256, 0, s>>>(G);
         g_env_trace.end(tr0, s, fl, by);
         COUNT_LAUNCH(1);
         break;
