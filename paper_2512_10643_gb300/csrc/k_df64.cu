@@ -101,80 +101,104 @@ __device__ __forceinline__ void df_tile(const DfTile& p, int i0, int j0, int kbe
       ah[r][c][0] = ah[r][c][1] = 0.f;
       al[r][c][0] = al[r][c][1] = 0.f;
     }
+  // Each thread's share of a stage: fixed (row, k) slots of the A and B
+  // tiles.  Their addresses, shared-memory places and row bounds are set
+  // once here; a stage only advances the pointers by SK k.
   float4 ra[NA], rb[NB];
-  auto load = [&](int k0) {
+  const float4* pa[NA];
+  const double2* pa64[NA];
+  long long sa[NA];                          // element step per stage
+  int ka[NA], sta[NA];                       // k within the stage; shared-memory slot (kk * (TM + 1) + ii)
+  bool va[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int e = tid + 256 * q;
+    int kk = 0, ii = 0;
+    if (p.opa == 0) { ii = e / SK; kk = e % SK; } else { kk = e / TM; ii = e % TM; }
+    const int gi = i0 + ii;
+    va[q] = e < SK * TM && gi < p.M;
+    ka[q] = kk;
+    sta[q] = kk * (TM + 1) + ii;
+    const long long at = va[q] ? (p.opa == 0 ? (long long)gi * p.lda + kbeg + kk
+                                             : (long long)(kbeg + kk) * p.lda + gi)
+                               : 0;
+    sa[q] = p.opa == 0 ? SK : (long long)SK * p.lda;
+    pa[q] = reinterpret_cast<const float4*>(A) + at;
+    pa64[q] = A + at;
+  }
+  const float4* pb[NB];
+  const double2* pb64[NB];
+  long long sb[NB];
+  int kb[NB], stb[NB];
+  bool vb[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int e = tid + 256 * q;
+    int kk = 0, jj = 0;
+    if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / SK; kk = e % SK; }
+    const int gj = j0 + jj;
+    vb[q] = e < SK * TN && gj < p.N;
+    kb[q] = kk;
+    stb[q] = kk * (TN + 1) + jj;
+    const long long at = vb[q] ? (p.opb == 0 ? (long long)(kbeg + kk) * p.ldb + gj
+                                             : (long long)gj * p.ldb + kbeg + kk)
+                               : 0;
+    sb[q] = p.opb == 0 ? (long long)SK * p.ldb : SK;
+    pb[q] = reinterpret_cast<const float4*>(B) + at;
+    pb64[q] = B + at;
+  }
+  const bool nega = p.opa != 0, negb = p.opb != 0;
+  // operands of the stage starting at k0 (stage index st = (k0 - kbeg) / SK)
+  auto load = [&](int k0, long long st) {
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
-      const int e = tid + 256 * q;
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < SK * TM) {
-        int kk, ii;
-        if (p.opa == 0) { ii = e / SK; kk = e % SK; } else { kk = e / TM; ii = e % TM; }
-        const int gi = i0 + ii, gk = k0 + kk;
-        if (gi < p.M && gk < kend) {
-          const long long at = p.opa == 0 ? (long long)gi * p.lda + gk : (long long)gk * p.lda + gi;
-          if (p.asplit) {
-            w = reinterpret_cast<const float4*>(A)[at];
-          } else {
-            const double2 v = A[at];
-            const Df re = df_split(v.x), im = df_split(v.y);
-            w = make_float4(re.h, re.l, im.h, im.l);
-          }
-          if (p.opa) { w.z = -w.z; w.w = -w.w; }
+      if (va[q] && k0 + ka[q] < kend) {
+        if (p.asplit) {
+          w = pa[q][st * sa[q]];
+        } else {
+          const double2 v = pa64[q][st * sa[q]];
+          const Df re = df_split(v.x), im = df_split(v.y);
+          w = make_float4(re.h, re.l, im.h, im.l);
         }
+        if (nega) { w.z = -w.z; w.w = -w.w; }
       }
       ra[q] = w;
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-      const int e = tid + 256 * q;
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < SK * TN) {
-        int kk, jj;
-        if (p.opb == 0) { kk = e / TN; jj = e % TN; } else { jj = e / SK; kk = e % SK; }
-        const int gj = j0 + jj, gk = k0 + kk;
-        if (gj < p.N && gk < kend) {
-          const long long at = p.opb == 0 ? (long long)gk * p.ldb + gj : (long long)gj * p.ldb + gk;
-          if (p.bsplit) {
-            w = reinterpret_cast<const float4*>(B)[at];
-          } else {
-            const double2 v = B[at];
-            const Df re = df_split(v.x), im = df_split(v.y);
-            w = make_float4(re.h, re.l, im.h, im.l);
-          }
-          if (p.opb) { w.z = -w.z; w.w = -w.w; }
+      if (vb[q] && k0 + kb[q] < kend) {
+        if (p.bsplit) {
+          w = pb[q][st * sb[q]];
+        } else {
+          const double2 v = pb64[q][st * sb[q]];
+          const Df re = df_split(v.x), im = df_split(v.y);
+          w = make_float4(re.h, re.l, im.h, im.l);
         }
+        if (negb) { w.z = -w.z; w.w = -w.w; }
       }
       rb[q] = w;
     }
   };
   auto store = [&](int buf) {
 #pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      const int e = tid + 256 * q;
-      if (e < SK * TM) {
-        const int kk = p.opa == 0 ? e % SK : e / TM, ii = p.opa == 0 ? e / SK : e % TM;
-        *reinterpret_cast<float4*>(&As[buf][kk][ii][0]) = ra[q];
-      }
-    }
+    for (int q = 0; q < NA; ++q)
+      if (tid + 256 * q < SK * TM) *reinterpret_cast<float4*>(&As[buf][0][0][0] + 4 * sta[q]) = ra[q];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int e = tid + 256 * q;
-      if (e < SK * TN) {
-        const int kk = p.opb == 0 ? e / TN : e % SK, jj = p.opb == 0 ? e % TN : e / SK;
-        *reinterpret_cast<float4*>(&Bs[buf][kk][jj][0]) = rb[q];
-      }
-    }
+    for (int q = 0; q < NB; ++q)
+      if (tid + 256 * q < SK * TN) *reinterpret_cast<float4*>(&Bs[buf][0][0][0] + 4 * stb[q]) = rb[q];
   };
   if (kbeg < kend) {
-    load(kbeg);
+    load(kbeg, 0);
     store(0);
   }
   __syncthreads();
   int buf = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += SK, buf ^= 1) {
+  long long st = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += SK, buf ^= 1, ++st) {
     const bool more = k0 + SK < kend;
-    if (more) load(k0 + SK);                 // in flight during the arithmetic below
+    if (more) load(k0 + SK, st + 1);         // in flight during the arithmetic below
 #pragma unroll 2
     for (int kk = 0; kk < SK; ++kk) {
       float a[RM][4], b[RN][4];
