@@ -415,6 +415,14 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  const double* u, int ustride, int site, uint64_t seed,
                                  uint64_t counter0, uint8_t* out, int N, uint8_t* flags,
                                  double flag_tol, cudaStream_t s);
+// Factor and inverse of every diagonal block in one launch, each block in
+// shared memory (double-float arithmetic): for blocks of at most
+// chol_inv_smem's limit (chol_inv_smem(maxd) == 0 above it); L and L^{-1}
+// are written in FP64 like launch_chol and launch_trinv
+size_t chol_inv_smem(int maxd);
+cudaError_t launch_chol_inv(const double2* src, double2* L, double2* X, const long long* off,
+                            const int* Dv, int b0, int nb, int maxd, double* dused,
+                            unsigned long long* regmax, int* status, cudaStream_t s);
 // src: the environments as double-float pairs (one float4 per complex element)
 cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, const int* Dv,
                         int b0, int nb, double* dused, unsigned long long* regmax, int* status,

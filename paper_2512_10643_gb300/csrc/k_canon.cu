@@ -834,6 +834,186 @@ __global__ void trinv_kernel(const double2* __restrict__ Lb, double2* __restrict
   }
 }
 
+// ---------------------------------------------------------------- fused factor + inverse
+// One CTA per diagonal parity block of a bond, the block held in shared
+// memory as a packed lower triangle of double-float pairs (row i at
+// i (i + 1) / 2; {re_h, re_l, im_h, im_l} per element): R + delta 1 = L L^dag
+// by right-looking Cholesky, L written out in FP64, then L^{-1} in place by
+// forward substitution (row i of X = L^{-1}: X_ii = 1 / L_ii,
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj), written out in FP64.  Square
+// roots and reciprocals of the pivots are FP64 (one thread per pivot); the
+// updates are double-float multiply-adds on the FP32 pipes.  The
+// regulariser search and its bookkeeping are those of chol_kernel.
+constexpr int CI_THREADS = 512;
+constexpr int CI_KS = 4;                  // k slices per row of the inverse (partial sums)
+constexpr int CI_MAXD = 160;              // largest block: (160 * 161 / 2 + 4 * 160) * 16 B of shared memory
+__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+// (h, l) += x y for double-float x, y (exact product by FMA, TwoSum)
+__device__ __forceinline__ void ci_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float t = h + p;
+  const float v = t - h;
+  l += ((h - (t - v)) + (p - v)) + e;
+  h = t;
+}
+__device__ __forceinline__ void ci_norm(float& h, float& l) {
+  const float s = h + l;
+  const float v = s - h;
+  l = (h - (s - v)) + (l - v);
+  h = s;
+}
+// v -= a conj(c)  (all double-float complex)
+__device__ __forceinline__ void ci_sub_aconjc(float4& v, const float4 a, const float4 c) {
+  ci_mac(v.x, v.y, -a.x, -a.y, c.x, c.y);        // re -= ar cr
+  ci_mac(v.x, v.y, -a.z, -a.w, c.z, c.w);        // re -= ai ci
+  ci_mac(v.z, v.w, -a.z, -a.w, c.x, c.y);        // im -= ai cr
+  ci_mac(v.z, v.w, a.x, a.y, c.z, c.w);          // im += ar ci
+  ci_norm(v.x, v.y);
+  ci_norm(v.z, v.w);
+}
+// s += a b  (double-float complex accumulators, left unnormalised)
+__device__ __forceinline__ void ci_cmac(float4& s, const float4 a, const float4 b) {
+  ci_mac(s.x, s.y, a.x, a.y, b.x, b.y);
+  ci_mac(s.x, s.y, -a.z, -a.w, b.z, b.w);
+  ci_mac(s.z, s.w, a.x, a.y, b.z, b.w);
+  ci_mac(s.z, s.w, a.z, a.w, b.x, b.y);
+}
+__device__ __forceinline__ float4 ci_scale(const float4 a, float sh, float sl) {   // a * real (sh, sl)
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  ci_mac(r.x, r.y, a.x, a.y, sh, sl);
+  ci_mac(r.z, r.w, a.z, a.w, sh, sl);
+  ci_norm(r.x, r.y);
+  ci_norm(r.z, r.w);
+  return r;
+}
+__device__ __forceinline__ float4 ci_pack_real(double x) {
+  const float h = (float)x;
+  return make_float4(h, (float)(x - (double)h), 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(CI_THREADS)
+chol_inv_kernel(const float4* __restrict__ src, double2* __restrict__ Lout, double2* __restrict__ Xout,
+                const long long* __restrict__ off, const int* __restrict__ Dv, int b0,
+                double* __restrict__ dused, unsigned long long* regmax, int* status) {
+  extern __shared__ float4 cism[];
+  const int b = b0 + blockIdx.x;
+  const int D = Dv[b];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  float4* P = cism;                              // packed lower triangle
+  float4* part = cism + tri(D);                  // CI_KS x D partial sums of the inverse
+  const float4* Sm = src + off[b];
+  __shared__ double dmax;
+  __shared__ float ilh, ill;
+  __shared__ bool piv_ok;
+  if (D <= 0 || D > CI_MAXD) {                  // (the launcher sizes for the largest block)
+    if (tid == 0) {
+      if (D > CI_MAXD) set_status(status, ST_BOUNDS);
+      dused[b] = 0.0;
+    }
+    return;
+  }
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < D; ++i) m = fmax(m, df_unpack(Sm[(long long)i * D + i]).x);
+    dmax = m;
+  }
+  __syncthreads();
+  double reg = 1e-12, delta = 0.0;
+  bool okf = false;
+  for (int attempt = 0; attempt < 5 && !okf; ++attempt, reg *= 100.0) {
+    delta = reg * dmax;
+    for (int i = warp; i < D; i += nw)
+      for (int j = lane; j <= i; j += 32) {
+        float4 v = Sm[(long long)i * D + j];
+        if (i == j) v = ci_pack_real(df_unpack(v).x + delta);
+        P[tri(i) + j] = v;
+      }
+    __syncthreads();
+    okf = true;
+    for (int k = 0; k < D; ++k) {
+      if (tid == 0) {                            // the pivot, in FP64
+        const float4 d = P[tri(k) + k];
+        const double akk = (double)d.x + (double)d.y;
+        piv_ok = akk > 0.0;
+        if (piv_ok) {
+          const double lkk = sqrt(akk), il = 1.0 / lkk;
+          P[tri(k) + k] = ci_pack_real(lkk);
+          ilh = (float)il;
+          ill = (float)(il - (double)ilh);
+        }
+      }
+      __syncthreads();
+      if (!piv_ok) { okf = false; break; }      // same value in every thread
+      const float sh = ilh, sl = ill;
+      for (int i = k + 1 + tid; i < D; i += nt) P[tri(i) + k] = ci_scale(P[tri(i) + k], sh, sl);
+      __syncthreads();
+      // trailing lower triangle: rows by warp, columns by lane
+      for (int i = k + 1 + warp; i < D; i += nw) {
+        const float4 a = P[tri(i) + k];
+        for (int j = k + 1 + lane; j <= i; j += 32) {
+          float4 v = P[tri(i) + j];
+          ci_sub_aconjc(v, a, P[tri(j) + k]);
+          P[tri(i) + j] = v;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+  if (!okf && tid == 0) set_status(status, ST_NUMERIC);
+  if (tid == 0) {
+    const double rel = okf ? delta / fmax(dmax, 1e-300) : -1.0;
+    dused[b] = rel;
+    if (regmax) atomicMax(regmax, (unsigned long long)__double_as_longlong(okf ? rel : 1e300));
+  }
+  double2* L = Lout + off[b];
+  double2* X = Xout + off[b];
+  for (long long idx = tid; idx < (long long)D * D; idx += nt) {
+    const int i = (int)(idx / D), j = (int)(idx % D);
+    L[idx] = j <= i ? df_unpack(P[tri(i) + j]) : cmk(0.0, 0.0);
+  }
+  if (!okf) return;
+  // L^{-1} in place, row by row
+  for (int i = 0; i < D; ++i) {
+    // partial sums y_j = sum_{k = j + s, j + s + KS, ..} L_ik X_kj, k < i
+    for (int e = tid; e < i * CI_KS; e += nt) {
+      const int j = e / CI_KS, sl = e % CI_KS;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = j + sl; k < i; k += CI_KS) ci_cmac(acc, P[tri(i) + k], P[tri(k) + j]);
+      part[sl * D + j] = acc;
+    }
+    if (tid == 0) {
+      const float4 d = P[tri(i) + i];
+      const double xi = 1.0 / ((double)d.x + (double)d.y);
+      ilh = (float)xi;
+      ill = (float)(xi - (double)ilh);
+    }
+    __syncthreads();
+    const float xh = ilh, xl = ill;
+    for (int j = tid; j <= i; j += nt) {
+      if (j == i) {
+        P[tri(i) + i] = make_float4(xh, xl, 0.f, 0.f);
+      } else {
+        float4 y = part[j];
+        for (int q = 1; q < CI_KS; ++q) {
+          const float4 w = part[q * D + j];
+          ci_mac(y.x, y.y, w.x, w.y, 1.f, 0.f);
+          ci_mac(y.z, y.w, w.z, w.w, 1.f, 0.f);
+        }
+        P[tri(i) + j] = ci_scale(y, -xh, -xl);
+      }
+    }
+    __syncthreads();
+  }
+  for (long long idx = tid; idx < (long long)D * D; idx += nt) {
+    const int i = (int)(idx / D), j = (int)(idx % D);
+    X[idx] = j <= i ? df_unpack(P[tri(i) + j]) : cmk(0.0, 0.0);
+  }
+}
+
 typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -988,6 +1168,29 @@ cudaError_t launch_chol(const double2* src, double2* dst, const long long* off, 
                         cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
   chol_kernel<<<nb, 256, 0, s>>>(src, dst, off, Dv, b0, dused, regmax, status);
+  return cudaGetLastError();
+}
+
+size_t chol_inv_smem(int maxd) {
+  if (maxd < 1 || maxd > CI_MAXD) return 0;
+  return sizeof(float4) * ((size_t)maxd * (maxd + 1) / 2 + (size_t)CI_KS * maxd);
+}
+
+cudaError_t launch_chol_inv(const double2* src, double2* L, double2* X, const long long* off,
+                            const int* Dv, int b0, int nb, int maxd, double* dused,
+                            unsigned long long* regmax, int* status, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  const size_t smem = chol_inv_smem(maxd);
+  if (!smem) return cudaErrorInvalidValue;
+  static std::atomic<int> attr_set{0};
+  if (!attr_set.load()) {
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_inv_smem(CI_MAXD));
+    if (e) return e;
+    attr_set.store(1);
+  }
+  chol_inv_kernel<<<nb, CI_THREADS, smem, s>>>(reinterpret_cast<const float4*>(src), L, X, off, Dv, b0,
+                                               dused, regmax, status);
   return cudaGetLastError();
 }
 

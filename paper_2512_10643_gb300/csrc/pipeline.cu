@@ -402,17 +402,24 @@ int canon_prepare(gbsmps_mps* M, CanonWork* w, cudaStream_t s) {
 }
 
 int canon_bonds(gbsmps_ctx* c, gbsmps_mps* M, CanonWork* w, int b0, int nb, cudaStream_t s) {
-  // FP64, one SM per diagonal block of R (a double-float form on the FP32
-  // pipes was measured slower: these loops are bound by dependency latency
-  // and barriers, and double-float multiplies the instructions on the
-  // critical path)
+  // one CTA per diagonal parity block of R: factor and inverse together in
+  // shared memory with double-float updates when the blocks fit (classes of
+  // up to 160 states), else the FP64 kernels in global memory
   if (nb <= 0) return GBSMPS_OK;
   const long long* off = M->eoff_dev.as<long long>();
   const int* dims = reinterpret_cast<const int*>(off + 2 * (M->N + 1));
-  CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), off, dims, 2 * b0, 2 * nb,
-                 w->du.as<double>(), M->creg.as<unsigned long long>(), c->d_status, s));
   int maxd = 1;
   for (int b = b0; b < b0 + nb; ++b) maxd = std::max({maxd, M->pcnt[2 * b], M->pcnt[2 * b + 1]});
+  const char* ce = getenv("GBSMPS_CHOL_SMEM");
+  if (chol_inv_smem(maxd) && !(ce && ce[0] == '0')) {
+    CK(launch_chol_inv(M->env.as<double2>(), M->lchol.as<double2>(), M->linv.as<double2>(), off, dims,
+                       2 * b0, 2 * nb, maxd, w->du.as<double>(), M->creg.as<unsigned long long>(),
+                       c->d_status, s));
+    COUNT_LAUNCH(1);
+    return GBSMPS_OK;
+  }
+  CK(launch_chol(M->env.as<double2>(), M->lchol.as<double2>(), off, dims, 2 * b0, 2 * nb,
+                 w->du.as<double>(), M->creg.as<unsigned long long>(), c->d_status, s));
   CK(launch_trinv(M->lchol.as<double2>(), M->linv.as<double2>(), off, dims, 2 * b0, 2 * nb, maxd, s));
   COUNT_LAUNCH(2);
   return GBSMPS_OK;

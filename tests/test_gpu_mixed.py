@@ -157,3 +157,29 @@ def test_p0_prepass_draws_the_full_pass_patterns(ctx, monkeypatch):
         assert (a == c).all(axis=1).mean() > 0.98
     finally:
         m.release()
+
+
+def test_factor_paths_agree(ctx, monkeypatch):
+    """The Cholesky factors and inverses of the environments' parity blocks
+    come from one shared-memory double-float kernel when the blocks fit and
+    from the FP64 global-memory kernels otherwise (GBSMPS_CHOL_SMEM=0 forces
+    those): the same regulariser is chosen and the same samples are drawn
+    from the same uniforms, except draws flagged at a CDF boundary."""
+    w = wl.small(28, 17, d=6, chi=96, depth=6, rlo=0.1, rhi=0.45)
+    opts = dict(d=6, chi_max=96, eps_trunc=1e-12, lambda2_freeze=1e-9, precision=g.PREC_MIXED)
+    S = 4000
+    u = wl.uniforms(S, 28, seed=71)
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GBSMPS_CHOL_SMEM", flag)
+        m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **opts)
+        try:
+            f = np.zeros(S, dtype=np.uint8)
+            res.append((m.sample(S, uniforms=u, flags=f), f))
+        finally:
+            m.release()
+    (s1, f1), (s0, f0) = res
+    ok = (f1 == 0) & (f0 == 0)
+    assert ok.mean() > 0.98
+    assert np.array_equal(s1[ok], s0[ok])
+    assert np.all(s1.astype(int).sum(1) % 2 == 0)
