@@ -33,7 +33,7 @@
 
 namespace {
 
-constexpr int PCO_THREADS = 512;
+constexpr int PCO_THREADS = 1024;   // one CTA per site: 512, 768, 1024 threads measured 5.0, 4.4, 4.1 ms (N = 144)
 constexpr int SQ_N = 260;
 constexpr int GE = 258;     // occupation-count table per mode: v = 0..257
 
@@ -282,7 +282,7 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
 
 // one CTA per site, scratch at the task's own offset
 template <typename T>
-__global__ void __launch_bounds__(PCO_THREADS)
+__global__ void __launch_bounds__(PCO_THREADS, 1)
 pco_kernel(const SiteTask* __restrict__ tasks, int d, double2* __restrict__ scratch_base,
            int* status) {
   __shared__ PcoSmem sm;
