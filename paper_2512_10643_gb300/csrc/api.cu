@@ -418,7 +418,11 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   // the sampler's stream priority against the next build's (GBSMPS_STREAM_PRIO:
   // 1 = the sampler first, 0 = equal)
   const char* spe = getenv("GBSMPS_STREAM_PRIO");
-  const bool sampler_hi = spe ? atoi(spe) != 0 : true;
+  // GBSMPS_STREAM_BUILD_PRIO=1: the builds' parts run on a stream of the
+  // highest priority instead of c's, and the sampler on the lowest
+  const char* bpe = getenv("GBSMPS_STREAM_BUILD_PRIO");
+  const bool build_hi = bpe ? atoi(bpe) != 0 : false;
+  const bool sampler_hi = build_hi ? false : (spe ? atoi(spe) != 0 : true);
   if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
   if (count < 0) return fail(GBSMPS_ERR_ARG, "count < 0");
   if (count == 0) return GBSMPS_OK;
@@ -458,6 +462,8 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   cudaStream_t ss = nullptr;
   cudaEvent_t pco_done = nullptr, sampled = nullptr;
   gbsmps_ctx cf[NFMAX];
+  gbsmps_ctx cbx;                        // the builds' own context when build_hi
+  gbsmps_ctx* cb = c;
   DevBuf st, fst, g[NFMAX];
   gbs::FrontState fs[NFMAX];
   gbsmps_mps* cur = nullptr;
@@ -474,6 +480,12 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     cf[i].d_status = fst.as<int>() + i;
     ok = ck(cudaStreamCreateWithFlags(&cf[i].stream, cudaStreamNonBlocking)) &&
          (mem_kind == GBSMPS_MEM_DEVICE || ck(g[i].alloc(gmax, c->stream)));
+  }
+  if (ok && build_hi) {
+    cbx.device = c->device;
+    cbx.d_status = c->d_status;
+    ok = ck(cudaStreamCreateWithPriority(&cbx.stream, cudaStreamNonBlocking, hi));
+    if (ok) cb = &cbx;
   }
   ok = ok && ck(cudaStreamSynchronize(c->stream));
   auto keep = [&](int r) {
@@ -494,15 +506,15 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   };
   for (int i = 0; i < std::min(count, NF - 1) && ok; ++i) ok = front(i);
   // state 0 alone
-  if (ok) ok = keep(gbs::rest_pco(c, &fs[0], nullptr)) && keep(gbs::rest_env(c, &fs[0])) &&
-               keep(gbs::rest_canon(c, &fs[0], nullptr, &cur));
+  if (ok) ok = keep(gbs::rest_pco(cb, &fs[0], nullptr)) && keep(gbs::rest_env(cb, &fs[0])) &&
+               keep(gbs::rest_canon(cb, &fs[0], nullptr, &cur));
   for (int k = 0; k < count && ok; ++k) {
     // state k is built; state k-1's sampling finished before it was handed over
     if (k + NF - 1 < count && !front(k + NF - 1)) break;
     // (sampling k-1 has finished: the loop waited for it)
-    if (k + 1 < count && !keep(gbs::rest_pco(c, &fs[(k + 1) % NF], nullptr))) break;
+    if (k + 1 < count && !keep(gbs::rest_pco(cb, &fs[(k + 1) % NF], nullptr))) break;
     // the sampling starts after PCO(k+1): no long CTA beside the sampler
-    if (!ck(cudaEventRecord(pco_done, c->stream)) || !ck(cudaStreamWaitEvent(ss, pco_done, 0))) break;
+    if (!ck(cudaEventRecord(pco_done, cb->stream)) || !ck(cudaStreamWaitEvent(ss, pco_done, 0))) break;
     if (!keep(gbs::sample_impl(cur, ss, st.as<int>(), k + 1 < count ? stream_reserve : 0, 0, S, seeds[k],
                                counter0s[k], nullptr, outs[k], nullptr, mem_kind)))
       break;
@@ -511,8 +523,8 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     if (k + 1 < count) {
       // beside sampling k: every CTA of these parts fits on an SM next to a
       // sampler GEMM CTA, or is short
-      if (!keep(gbs::rest_env(c, &fs[(k + 1) % NF]))) break;
-      if (!keep(gbs::rest_canon(c, &fs[(k + 1) % NF], nullptr, &next))) break;
+      if (!keep(gbs::rest_env(cb, &fs[(k + 1) % NF]))) break;
+      if (!keep(gbs::rest_canon(cb, &fs[(k + 1) % NF], nullptr, &next))) break;
     }
     // state k's MPS is freed once its sampling is done
     if (!ck(cudaStreamSynchronize(ss))) break;
@@ -520,6 +532,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
     cur = next;
   }
   if (ss) ck(cudaStreamSynchronize(ss));
+  if (cbx.stream) ck(cudaStreamSynchronize(cbx.stream));
   for (int i = 0; i < NF; ++i)
     if (cf[i].stream) ck(cudaStreamSynchronize(cf[i].stream));
   delete cur;
@@ -536,6 +549,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   ck(cudaStreamSynchronize(c->stream));
   for (int i = 0; i < NF; ++i)
     if (cf[i].stream) { cudaStreamDestroy(cf[i].stream); cf[i].stream = nullptr; }
+  if (cbx.stream) { cudaStreamDestroy(cbx.stream); cbx.stream = nullptr; }
   if (sampled) cudaEventDestroy(sampled);
   if (pco_done) cudaEventDestroy(pco_done);
   if (ss) cudaStreamDestroy(ss);
