@@ -592,90 +592,94 @@ select_groups_kernel(int S, int spw, int d, const SelGroup g0, const SelGroup g1
                      int site, uint64_t seed, uint64_t counter0, uint8_t* __restrict__ out, int N,
                      uint8_t* flags, double flag_tol) {
   const int lane = threadIdx.x & 31;
-  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long t = wg * spw + lane;          // lanes 0 .. spw-1 take a sample each
-  if (wg * spw >= S) return;                    // whole warps only: the warp syncs below
   const int M0 = max(0, min(*g0.cnt, S)), M1 = max(0, min(*g1.cnt, S));
-  const int grp = t >= M0 ? 1 : 0;
-  const int r = (int)(t - (grp ? M0 : 0));
-  const bool active = lane < spw && t < S && r < (grp ? M1 : M0);
-  const SelGroup& g = grp ? g1 : g0;
-  int pstar = 0, np = 0, s = 0;
-  float inv = 0.f;
-  if (active) {
-    s = g.sid[r];
-    const float* ps = g.part + (long long)r * g.ldp;
-    const int P2 = g.wself + g.wother;
-    auto qp = [&](int p) {
-      const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
-      const int nch = ((p & 1) ? g.wother : g.wself) / 16;
-      float q = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < nch; ++k) q += ps[c0 + k];
-      return q;
-    };
-    // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
-    // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway
-    float Z = 0.f;
-    for (int p = 0; p < d; ++p) Z += qp(p);
-    const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
-    const float tt = (float)uu * Z;
-    const float ftol = (float)flag_tol * Z;
-    float C = 0.f, qsel = 0.f;
-    int plast = 0;
-    bool flag = false;
-    pstar = -1;
-    for (int p = 0; p < d; ++p) {
-      const float q = qp(p);
-      C += q;
-      if (fabsf(tt - C) <= ftol) flag = true;
-      if (q > 0.f) plast = p;
-      if (pstar < 0 && tt < C) { pstar = p; qsel = q; }
+  // warps stride over the spw-sample groups up to the device-side counts
+  // (the grid is sized for a few waves, not for S)
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+       wg * spw < (long long)M0 + M1; wg += nwarps) {   // warp-uniform: the warp syncs below
+    const long long t = wg * spw + lane;          // lanes 0 .. spw-1 take a sample each
+    const int grp = t >= M0 ? 1 : 0;
+    const int r = (int)(t - (grp ? M0 : 0));
+    const bool active = lane < spw && t < S && r < (grp ? M1 : M0);
+    const SelGroup& g = grp ? g1 : g0;
+    int pstar = 0, np = 0, s = 0;
+    float inv = 0.f;
+    if (active) {
+      s = g.sid[r];
+      const float* ps = g.part + (long long)r * g.ldp;
+      const int P2 = g.wself + g.wother;
+      auto qp = [&](int p) {
+        const int c0 = ((p >> 1) * P2 + ((p & 1) ? g.wself : 0)) / 16;
+        const int nch = ((p & 1) ? g.wother : g.wself) / 16;
+        float q = 0.f;
+  #pragma unroll 8
+        for (int k = 0; k < nch; ++k) q += ps[c0 + k];
+        return q;
+      };
+      // FP32 weights: W is FP32-accurate, and a draw whose margin to a CDF
+      // boundary is below flag_tol Z (>> FP32 rounding) is flagged anyway
+      float Z = 0.f;
+      for (int p = 0; p < d; ++p) Z += qp(p);
+      const double uu = u ? u[(size_t)s * ustride + site] : philox_uniform(seed, counter0 + s, (uint32_t)site);
+      const float tt = (float)uu * Z;
+      const float ftol = (float)flag_tol * Z;
+      float C = 0.f, qsel = 0.f;
+      int plast = 0;
+      bool flag = false;
+      pstar = -1;
+      for (int p = 0; p < d; ++p) {
+        const float q = qp(p);
+        C += q;
+        if (fabsf(tt - C) <= ftol) flag = true;
+        if (q > 0.f) plast = p;
+        if (pstar < 0 && tt < C) { pstar = p; qsel = q; }
+      }
+      if (pstar < 0) { pstar = plast; qsel = qp(pstar); }
+      inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
+      np = grp ^ (pstar & 1);
+      out[(size_t)s * N + site] = (uint8_t)pstar;
+      if (flags && flag) flags[s] = 1;
     }
-    if (pstar < 0) { pstar = plast; qsel = qp(pstar); }
-    inv = qsel > 0.f ? rsqrtf(qsel) : 0.f;
-    np = grp ^ (pstar & 1);
-    out[(size_t)s * N + site] = (uint8_t)pstar;
-    if (flags && flag) flags[s] = 1;
-  }
-  // rows in the next groups: one atomic per group and warp
-  int pos = 0;
-  for (int c = 0; c < 2; ++c) {
-    const unsigned m = __ballot_sync(0xffffffffu, active && np == c);
-    if (!m) continue;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(cnt_next + c, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (active && np == c) pos = base + __popc(m & ((1u << lane) - 1u));
-  }
-  // the warp copies each active lane's chosen block into its next group
-  unsigned todo = __ballot_sync(0xffffffffu, active && pos < S);
-  while (todo) {
-    const int src = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const int rr = __shfl_sync(0xffffffffu, r, src);
-    const int gg = __shfl_sync(0xffffffffu, grp, src);
-    const int ps = __shfl_sync(0xffffffffu, pstar, src);
-    const int nn = __shfl_sync(0xffffffffu, np, src);
-    const int po = __shfl_sync(0xffffffffu, pos, src);
-    const int sd = __shfl_sync(0xffffffffu, s, src);
-    const float iv = __shfl_sync(0xffffffffu, inv, src);
-    const SelGroup& G = gg ? g1 : g0;
-    const NextGroup& ng = nn ? n1 : n0;
-    const int P2 = G.wself + G.wother;
-    const float2* wr = G.W + (long long)rr * G.ldw + (long long)(ps >> 1) * P2 + ((ps & 1) ? G.wself : 0);
-    for (int b = lane; b < ng.Kp / 2; b += 32) {
-      const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
-      __half hr[NPL], hi[NPL];
-      split2(v.x * iv, hr[0], hr[1]);
-      split2(v.y * iv, hi[0], hi[1]);
-      for (int pl = 0; pl < NPL; ++pl)
-        *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)sd * ng.Kp + 2 * b) =
-            __halves2half2(hr[pl], hi[pl]);
+    // rows in the next groups: one atomic per group and warp
+    int pos = 0;
+    for (int c = 0; c < 2; ++c) {
+      const unsigned m = __ballot_sync(0xffffffffu, active && np == c);
+      if (!m) continue;
+      int base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(cnt_next + c, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (active && np == c) pos = base + __popc(m & ((1u << lane) - 1u));
     }
-    if (lane == 0) {
-      ng.sid[po] = sd;
-      ng.rs[sd] = 1.f;
+    // the warp copies each active lane's chosen block into its next group
+    unsigned todo = __ballot_sync(0xffffffffu, active && pos < S);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int rr = __shfl_sync(0xffffffffu, r, src);
+      const int gg = __shfl_sync(0xffffffffu, grp, src);
+      const int ps = __shfl_sync(0xffffffffu, pstar, src);
+      const int nn = __shfl_sync(0xffffffffu, np, src);
+      const int po = __shfl_sync(0xffffffffu, pos, src);
+      const int sd = __shfl_sync(0xffffffffu, s, src);
+      const float iv = __shfl_sync(0xffffffffu, inv, src);
+      const SelGroup& G = gg ? g1 : g0;
+      const NextGroup& ng = nn ? n1 : n0;
+      const int P2 = G.wself + G.wother;
+      const float2* wr = G.W + (long long)rr * G.ldw + (long long)(ps >> 1) * P2 + ((ps & 1) ? G.wself : 0);
+      for (int b = lane; b < ng.Kp / 2; b += 32) {
+        const float2 v = b < ng.D ? wr[b] : make_float2(0.f, 0.f);
+        __half hr[NPL], hi[NPL];
+        split2(v.x * iv, hr[0], hr[1]);
+        split2(v.y * iv, hi[0], hi[1]);
+        for (int pl = 0; pl < NPL; ++pl)
+          *reinterpret_cast<__half2*>(ng.V + pl * ng.vpl + (long long)sd * ng.Kp + 2 * b) =
+              __halves2half2(hr[pl], hi[pl]);
+      }
+      if (lane == 0) {
+        ng.sid[po] = sd;
+        ng.rs[sd] = 1.f;
+      }
     }
   }
 }
@@ -1139,7 +1143,16 @@ cudaError_t launch_select_groups(int Scap, int d, const SelGroup& g0, const SelG
                                  double flag_tol, cudaStream_t s) {
   const int spw = sel_spw();
   long long threads = ((long long)Scap + spw - 1) / spw * 32;   // spw samples per warp
-  int blocks = (int)((threads + SEL_THREADS - 1) / SEL_THREADS);
+  static std::atomic<int> nsm{0};
+  if (!nsm.load()) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      nsm.store(n);
+  }
+  // at most four CTAs per SM: the warps loop over the counts on the device
+  const long long cap = 4LL * std::max(1, nsm.load());
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((threads + SEL_THREADS - 1) / SEL_THREADS, cap));
   select_groups_kernel<<<blocks, SEL_THREADS, 0, s>>>(Scap, spw, d, g0, g1, n0, n1, cnt_next, u,
                                                       ustride, site, seed, counter0, out, N, flags,
                                                       flag_tol);
