@@ -35,8 +35,8 @@ WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) thro
 # DRAM bytes (read + write) per launch from an ncu capture of the current
 # kernels (None until one is taken): the sampler GEMM at 100,000 samples, and
 # the environment GEMM of the 144-mode workload (the same at any sample count)
-TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69031.8 + 37266.3) MB over 1152 launches
-ENV_TRAFFIC_BYTES_PER_LAUNCH = 4.99e6       # (7187.4 + 0.1) MB over 1440 launches
+TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69032.0 + 37278.6) MB over 1152 launches
+ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.01e6       # (7214.2 + 0.1) MB over 1440 launches
 # A double-float multiply-add (2 flops of the FP64 algorithm) costs 12 FP32
 # instructions: the exact product by FMA (4, with the low words) and Knuth's
 # TwoSum into the (hi, lo) accumulator (6) plus the low-word update (2)
