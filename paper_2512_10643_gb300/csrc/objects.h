@@ -124,6 +124,7 @@ struct gbsmps_mps {
   DevBuf tensors, env, gsvd, bonds;
   DevBuf tens_mixed;        // mixed path: tensors in the energy gauge (parity-compact pairs)
   DevBuf gscale;            // mixed path: e^{+E/2} then e^{-E/2} of every bond's states
+  DevBuf vacamp;            // mixed path: the all-vacuum amplitude from the environment chain (FP64)
   // mixed path, right-canonical sampler: Cholesky factors of the environments,
   // their inverses, and every site's canonical tensor as fp16 planes + TMA map
   DevBuf eoff_dev, lchol, linv, bpack;
@@ -144,6 +145,7 @@ struct gbsmps_mps {
   ~gbsmps_mps() {
     tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
     gscale.release();
+    vacamp.release();
     eoff_dev.release(); lchol.release(); linv.release(); bpack.release(); creg.release();
   }
 };

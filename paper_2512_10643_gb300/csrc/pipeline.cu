@@ -205,8 +205,13 @@ ParitySite parity_site(const gbsmps_mps* M, int m) {
 // one step of the parity-compact environment chain: R_m from R_{m+1}.
 // Product 1, per class c and p: X_c[:, block p] = Ahat_c[:, block p] R_{m+1, c^(p&1)};
 // product 2, per class c: R_{m, c} = X_c Ahat_c^dag (Hermitian)
+// One step of the environment chain on the parity blocks.  With ui set it
+// also carries the all-vacuum amplitude from the right: uo = Ahat^m[0] ui on
+// the class-0 states (the vacuum pattern keeps every bond state in the even
+// class; in the energy gauge the end bonds' energies are 0, so at m = 0 the
+// product is the amplitude itself), written as pairs, or in FP64 at m = 0.
 int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2* X, void* work,
-                    size_t wbytes, cudaStream_t s) {
+                    size_t wbytes, cudaStream_t s, const double2* ui, double2* uo) {
   const int d = M->d;
   const ParitySite P = parity_site(M, m);
   const int Dr = P.kr[0] + P.kr[1];
@@ -224,6 +229,8 @@ int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2
                           Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0,
                           1, 1, 1});
     }
+  if (ui && uo)       // block p = 0 of class 0: the first kr[0] columns of its rows
+    sub.push_back(DfSub{0, 0, P.kl[0], 1, P.kr[0], A, K[0], ui, 1, uo, 1, 0, 1, 1, m > 0 ? 1 : 0});
   CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
   sub.clear();
   for (int c = 0; c < 2; ++c) {
@@ -287,16 +294,26 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     }
     tm.mark("energy_gauge");
     const size_t wbytes = ((size_t)64 << 20) + DFG_CNT_BYTES;   // tile counters, split-K partials
-    DevBuf kw;
+    DevBuf kw, ub;
     CK(kw.alloc(wbytes, s));
     CK(cudaMemsetAsync(kw.p, 0, DFG_CNT_BYTES, s));
+    // the all-vacuum amplitude rides along: u_N = 1, u_m = Ahat^m[0] u_{m+1}
+    CK(ub.alloc(sizeof(float4) * 2 * ((size_t)M->maxD + 8), s));
+    CK(M->vacamp.alloc(sizeof(double2), s));
+    double2* ua = ub.as<double2>();
+    double2* ubn = ua + M->maxD + 8;
+    static const float4 one_u = make_float4(1.f, 0.f, 0.f, 0.f);
+    CK(cudaMemcpyAsync(ua, &one_u, sizeof(float4), cudaMemcpyHostToDevice, s));
     // (plain FP32 products were measured at 4.4e-5 (N = 144) and 2.8e-4
     // (N = 1024) amplitude error against FP64: the norm needs more bits)
     for (int m = N - 1; m >= 0; --m) {
-      const int rc = env_step_blocks(M, m, Ah, R, X, kw.p, wbytes, s);
+      const int rc = env_step_blocks(M, m, Ah, R, X, kw.p, wbytes, s, ua,
+                                     m > 0 ? ubn : M->vacamp.as<double2>());
       if (rc) return rc;
+      std::swap(ua, ubn);
     }
     kw.release();
+    ub.release();
   } else {
     for (int m = N - 1; m >= 0; --m) {
       int Dl = M->D[m], Dr = M->D[m + 1];
@@ -323,10 +340,14 @@ int normalise_single(gbsmps_ctx* c, gbsmps_mps* M) {
   double2* amp0 = awork + 2 * M->maxD;
   double2* fac = amp0 + 1;
   uint8_t* zpat = reinterpret_cast<uint8_t*>(fac + 2);
-  CK(cudaMemsetAsync(zpat, 0, N, s));
-  ChainView cv{N, d, M->D.data(), M->toff.data(), M->tensors.as<double2>()};
-  CK(launch_amplitudes(cv, 1, zpat, amp0, awork, M->maxD, s));
-  COUNT_LAUNCH(2 + N);
+  if (M->precision == GBSMPS_PREC_MIXED && M->vacamp.p) {
+    amp0 = M->vacamp.as<double2>();          // carried along the environment chain
+  } else {
+    CK(cudaMemsetAsync(zpat, 0, N, s));
+    ChainView cv{N, d, M->D.data(), M->toff.data(), M->tensors.as<double2>()};
+    CK(launch_amplitudes(cv, 1, zpat, amp0, awork, M->maxD, s));
+    COUNT_LAUNCH(2 + N);
+  }
   CK(launch_norm_phase(R + M->eoff[0], amp0, fac, c->d_status, s));
   CK(launch_zscale(M->tensors.as<double2>(), (size_t)M->D[0] * d * M->D[1], fac, s));
   COUNT_LAUNCH(2);
