@@ -414,7 +414,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   // build while it runs (a performance knob, GBSMPS_STREAM_RESERVE: the
   // patterns do not depend on it)
   const char* sre = getenv("GBSMPS_STREAM_RESERVE");
-  const int stream_reserve = sre ? std::max(0, std::min(128, atoi(sre))) : 24;
+  const int stream_reserve = sre ? std::max(0, std::min(128, atoi(sre))) : 36;
   // the sampler's stream priority against the next build's (GBSMPS_STREAM_PRIO:
   // 1 = the sampler first, 0 = equal)
   const char* spe = getenv("GBSMPS_STREAM_PRIO");
