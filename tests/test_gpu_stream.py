@@ -102,3 +102,26 @@ def test_stream_empty_and_bad_arguments(ctx):
     with pytest.raises(g.GbsmpsError):
         g.gbsmps_build_sample_stream(ctx.h, [np.ascontiguousarray(w.gamma)], [bad], 4, [1], [0],
                                      [np.zeros((4, 8), dtype=np.uint8)])
+
+
+@pytest.mark.parametrize("knobs", [
+    {"GBSMPS_STREAM_AHEAD": "1", "GBSMPS_STREAM_RESERVE": "0"},
+    {"GBSMPS_STREAM_AHEAD": "5", "GBSMPS_STREAM_RESERVE": "76", "GBSMPS_STREAM_BUILD_PRIO": "1"},
+])
+def test_stream_knobs_keep_the_patterns(ctx, monkeypatch, knobs):
+    """The stream's look-ahead, the SMs the sampler leaves free and the
+    streams' priorities are scheduling choices: the patterns stay
+    byte-for-byte those of separate calls."""
+    states = _states()
+    S = 2000
+    seeds = [21, 22, 23, 24]
+    c0s = [0, 1, 2, 3]
+    want = _separate(ctx, states, S, seeds, c0s)
+    for k, v in knobs.items():
+        monkeypatch.setenv(k, v)
+    opts = [g.opts_default(**o) for _, o in states]
+    gam_h = [np.ascontiguousarray(w.gamma) for w, _ in states]
+    outs = [np.zeros((S, w.N), dtype=np.uint8) for w, _ in states]
+    g.gbsmps_build_sample_stream(ctx.h, gam_h, opts, S, seeds, c0s, outs)
+    for k in range(len(states)):
+        assert np.array_equal(outs[k], want[k]), f"state {k}"
