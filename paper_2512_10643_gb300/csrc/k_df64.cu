@@ -457,7 +457,7 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       return e ? atoi(e) : dflt;
     };
     const int env_tile = knob("GBSMPS_DFG_TILE", 0);
-    const int env_waves = std::max(1, knob("GBSMPS_DFG_WAVES", 8));
+    const int env_waves = std::max(1, knob("GBSMPS_DFG_WAVES", 4));
     const int env_mink = std::max(1, knob("GBSMPS_DFG_MINK", 4));
     // k per shared-memory stage of the 16 x 16 tiles (GBSMPS_DFG_SK = 8 or 16;
     // the k order of every sum is the same)
@@ -470,9 +470,10 @@ cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, 
       const DfSub& u = live[g0 + i];
       tref += (long long)((u.M + 31) / 32) * ((u.N + 31) / 32);
     }
-    // k split toward eight waves of CTAs (measured: 29 -> 21 ms for the
-    // 144-mode chain against two waves), chunks of >= 4 stages, within the
-    // workspace
+    // k split toward four waves of CTAs of the 32 x 32 reference tiling
+    // (144-mode chain: 29 ms at two waves with the first form of this
+    // kernel; now 16.9 ms at four against 17.1 at eight), chunks of >= 4
+    // stages, within the workspace
     int target = (int)std::max<long long>(1, ((long long)env_waves * nsm + tref - 1) / tref);
     DfGroup G;
     G.np = np;
