@@ -16,8 +16,12 @@ Modules
              fidelity
   hafnian  : brute-force hafnian amplitudes (exact reference for tiny cases)
 
-Functions whose result is not pinned by an independent check say
-"parity unpinned" in their docstring.
+Every public function is pinned by a check that does not reuse its own code
+path (closed forms, brute-force hafnians, dense inner products and matrix
+exponentials, identities of App. A); a function without such a pin would say
+"parity unpinned" in its docstring, and none does.  ``gaussian.williamson_sqrt``
+is a second valid FP64 route to the Williamson form, kept to measure how far
+the MPS of a given covariance matrix is determined in FP64 at all.
 """
 from . import gaussian, basis, pco, mps, hafnian  # noqa: F401
 from .mps import build_mps, amplitudes, sample, environments, fidelity, normalise  # noqa: F401

@@ -91,6 +91,30 @@ def williamson(gamma: np.ndarray):
     return D, S
 
 
+def williamson_sqrt(gamma: np.ndarray):
+    """A second valid FP64 route to Eq. (symDiag), used to measure how far the
+    Williamson factor of a given Gamma is determined in FP64 at all.  Instead
+    of the Cholesky factor it takes the symmetric square root V^{1/2} (from
+    the symmetric eigendecomposition of V = 2 Gamma, the textbook
+    construction): K = V^{-1/2} Omega V^{-1/2}, i K Hermitian with eigenvalues
+    +-1/D, and S = V^{1/2} O diag(D, D)^{-1/2} with O built from the unit
+    eigenvectors exactly as in ``williamson``.  Any other valid route gives the
+    same D and the same S up to the rounding of the eigenvectors, which is
+    large only for nearly degenerate D."""
+    n = gamma.shape[0] // 2
+    V = 2.0 * gamma
+    ev, E = np.linalg.eigh(V)
+    Vh = (E * np.sqrt(ev)) @ E.T
+    Vmh = (E / np.sqrt(ev)) @ E.T
+    K = Vmh @ omega(n) @ Vmh
+    evk, W = np.linalg.eigh(1j * K)
+    D = 1.0 / evk[n:]
+    Wp = W[:, n:]
+    O = np.concatenate([np.sqrt(2.0) * Wp.imag, np.sqrt(2.0) * Wp.real], axis=1)
+    S = Vh @ O @ np.diag(np.concatenate([D, D]) ** -0.5)
+    return D, S
+
+
 def uv_from_s(S: np.ndarray):
     """Bogoliubov matrices of the modes b with quadratures R_b = S^{-1} R.
     From R = S R_b and a = (x + i p)/sqrt 2 one gets a = U b + V^* b^dag with
@@ -170,7 +194,7 @@ class Cut:
 
 
 def gsvd_chain(gamma: np.ndarray, lambda2_freeze: float = 1e-13,
-               ne_max: int = 64, keep_matrices: bool = False):
+               ne_max: int = 64, keep_matrices: bool = False, route=None):
     """Iterative GSVD (Sec. II B): at step m the residual state lives on
     (r_{m-1}, a_m..a_N).  Its reduced covariance on L_m = (r_{m-1}, a_m) is
     Williamson-diagonalised; active modes (Lambda^2 > lambda2_freeze, the D*
@@ -180,7 +204,9 @@ def gsvd_chain(gamma: np.ndarray, lambda2_freeze: float = 1e-13,
     (Eqs. (SVD3)-(bond)), whose covariance is
         [[D_active/2, S^{-1}_active Gamma_{L,R}], [..., Gamma_RR]].
     The last step converts the pure residual on (r_{N-1}, a_N) to its paired
-    form directly."""
+    form directly.  ``route`` selects the Williamson construction
+    (``williamson`` by default, ``williamson_sqrt`` for the second route)."""
+    route = williamson if route is None else route
     N = gamma.shape[0] // 2
     cuts = []
     n_in = 0
@@ -210,7 +236,7 @@ def gsvd_chain(gamma: np.ndarray, lambda2_freeze: float = 1e-13,
             cuts.append(Cut(n_in=n_in, n_out=0, D=np.ones(nL), lam2=np.zeros(0),
                             Q=Q, c=1.0))
             break
-        D, S = williamson(gl)
+        D, S = route(gl)
         U, V = uv_from_s(S)
         U, V = canonical_gauge(U, V)
         lam2 = lambda2_from_d(D)

@@ -53,11 +53,12 @@ def vacuum_basis() -> Basis:
 
 
 def build_mps(gamma: np.ndarray, d: int, chi: int, eps: float = 0.0,
-              lambda2_freeze: float = 1e-13, sites=None) -> MPS:
+              lambda2_freeze: float = 1e-13, sites=None, route=None) -> MPS:
     """Unnormalised MPS of the pure Gaussian state with covariance gamma.
     ``sites`` restricts the PCO build to a subset of site indices (the others
-    are left as None), for bounded-cost checks on large states."""
-    cuts = gaussian.gsvd_chain(gamma, lambda2_freeze=lambda2_freeze)
+    are left as None), for bounded-cost checks on large states; ``route``
+    picks the Williamson construction of the GSVD chain (default: Cholesky)."""
+    cuts = gaussian.gsvd_chain(gamma, lambda2_freeze=lambda2_freeze, route=route)
     N = len(cuts)
     bases = [vacuum_basis()]
     epss = []
@@ -137,8 +138,9 @@ def sample(tensors, u: np.ndarray, R=None):
     for m in range(N):
         A = tensors[m]
         d = A.shape[1]
-        W = np.einsum("sa,apb->spb", v, A)
-        Y = W @ R[m + 1]
+        Dl, Dr = A.shape[0], A.shape[2]
+        W = (v @ A.reshape(Dl, d * Dr)).reshape(S, d, Dr)      # w_p = v A^m[p]
+        Y = (W.reshape(S * d, Dr) @ R[m + 1]).reshape(S, d, Dr)
         q = np.maximum(0.0, np.real(np.sum(Y * W.conj(), axis=2)))
         Z = q.sum(axis=1)
         Cp = np.cumsum(q, axis=1)

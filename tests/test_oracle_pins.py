@@ -16,6 +16,16 @@ from oracle import mps as M
 from oracle import pco as P
 
 
+def compositions(n, total, cap):
+    """Every n-tuple of integers in [0, cap] with sum <= total."""
+    if n == 0:
+        yield ()
+        return
+    for k in range(min(total, cap) + 1):
+        for rest in compositions(n - 1, total - k, cap):
+            yield (k,) + rest
+
+
 def tmsv_gamma(r):
     """Two-mode squeezed vacuum as a 50:50 beamsplitter on an x- and a
     p-squeezed vacuum (input convention of the workloads module)."""
@@ -25,12 +35,13 @@ def tmsv_gamma(r):
 
 
 # ---------------------------------------------------------------- P10
+@pytest.mark.parametrize("route", [G.williamson, G.williamson_sqrt])
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_williamson_bogoliubov_identities(seed):
+def test_williamson_bogoliubov_identities(seed, route):
     w = wl.small(6, seed, depth=6, rlo=0.2, rhi=0.7)
     sub = [0, 1, 2, 6, 7, 8]
     g = w.gamma[np.ix_(sub, sub)]          # mixed 3-mode reduced state
-    D, S = G.williamson(g)
+    D, S = route(g)
     Om = G.omega(3)
     assert np.abs(S @ Om @ S.T - Om).max() < 1e-12
     assert np.abs(0.5 * S @ np.diag(np.r_[D, D]) @ S.T - g).max() < 1e-12
@@ -151,7 +162,8 @@ def test_pr1_fidelity_vs_hafnian_within_truncation():
     w = wl.config("pr1_n8")
     mps = M.build_mps(w.gamma, d=8, chi=64)
     T = M.normalise(mps.tensors)
-    pats = [n for n in itertools.product(range(8), repeat=8) if sum(n) <= 6 and sum(n) % 2 == 0]
+    pats = [n for n in compositions(8, 8, 7) if sum(n) % 2 == 0]
+    assert len(pats) == 8510
     ex = np.array([H.amplitude(w.Q, n) for n in pats])
     got = M.amplitudes(T, pats)
     f = abs(np.vdot(ex, got)) ** 2 / (np.vdot(ex, ex).real * np.vdot(got, got).real)
@@ -349,3 +361,177 @@ def test_gsvd_chain_reproduces_state_on_random_instances():
     got = M.amplitudes(T, pats)
     # compare ratios to the vacuum (normalisation-free)
     assert np.abs(got / got[0] - ex / ex[0]).max() < 1e-9
+
+
+# ---------------------------------------------------------------- O9: overlap and fidelity
+def _rotated_squeezed(r, phi):
+    """x-squeezed vacuum of strength r behind the phase shifter e^{i phi}:
+    paired-form coefficient q = -e^{2 i phi} tanh r."""
+    return wl.squeezed_state(np.array([r]), np.array([[np.exp(1j * phi)]]))
+
+
+@pytest.mark.parametrize("r1,p1,r2,p2", [(0.3, 0.0, 0.7, 0.0), (0.5, 0.3, 0.5, 1.1),
+                                         (0.8, -0.4, 0.2, 0.9), (0.6, 0.7, 0.4, 0.2)])
+def test_overlap_closed_form_single_mode(r1, p1, r2, p2):
+    """Two single-mode squeezed vacua with paired-form coefficients
+    q_j = -e^{i t_j} tanh r_j.  Expanding both states in Fock states and
+    summing sum_k C(2k, k) x^k = (1 - 4x)^{-1/2}:
+        <z1|z2> = (cosh r1 cosh r2)^{-1/2} (1 - e^{i(t2 - t1)} tanh r1 tanh r2)^{-1/2}
+    (principal root, both vacuum amplitudes real positive), so
+    |<z1|z2>|^2 = 1/|cosh r1 cosh r2 - e^{i(t2-t1)} sinh r1 sinh r2|, which is
+    1/cosh(r1 - r2) for t1 = t2.  A missing conjugation in the sweep turns
+    t2 - t1 into t2 + t1 and fails the cases with t1 != 0."""
+    ga, qa = _rotated_squeezed(r1, p1)
+    gb, qb = _rotated_squeezed(r2, p2)
+    ta = M.normalise(M.build_mps(ga, d=90, chi=1).tensors)
+    tb = M.normalise(M.build_mps(gb, d=90, chi=1).tensors)
+    t1, t2 = np.angle(-qa[0, 0]), np.angle(-qb[0, 0])
+    c1, c2, s1, s2 = np.cosh(r1), np.cosh(r2), np.sinh(r1), np.sinh(r2)
+    f_ex = 1.0 / abs(c1 * c2 - np.exp(1j * (t2 - t1)) * s1 * s2)
+    if p1 == p2 == 0.0:
+        assert abs(f_ex - 1 / np.cosh(r1 - r2)) < 1e-15
+    assert abs(M.fidelity(ta, tb) - f_ex) < 1e-12
+    ov_ex = (c1 * c2) ** -0.5 * (1 - np.exp(1j * (t2 - t1)) * np.tanh(r1) * np.tanh(r2)) ** -0.5
+    assert abs(M.overlap(ta, tb) - ov_ex) < 1e-12
+    assert abs(M.overlap(tb, ta) - np.conj(ov_ex)) < 1e-12
+
+
+@pytest.mark.parametrize("seeds", [(41, 42), (43, 44)])
+def test_overlap_equals_dense_inner_product(seeds):
+    """Two different entangled 4-mode states (different bond bases): the
+    transfer-matrix <a|b> equals sum_n conj(a_n) b_n over the whole truncated
+    Fock space, each amplitude from the plain matrix chain; the fidelity
+    equals |<a|b>|^2/(<a|a><b|b>) of the dense vectors."""
+    wa = wl.small(4, seeds[0], d=4, depth=4, rlo=0.3, rhi=0.7)
+    wb = wl.small(4, seeds[1], d=4, depth=4, rlo=0.3, rhi=0.7)
+    ta = M.build_mps(wa.gamma, d=4, chi=30).tensors
+    tb = M.build_mps(wb.gamma, d=4, chi=30).tensors
+    pats = list(itertools.product(range(4), repeat=4))
+    va = M.amplitudes(ta, pats)
+    vb = M.amplitudes(tb, pats)
+    ab = np.vdot(va, vb)
+    scale = np.linalg.norm(va) * np.linalg.norm(vb)
+    assert abs(M.overlap(ta, tb) - ab) <= 1e-13 * scale
+    assert abs(M.overlap(tb, ta) - np.conj(ab)) <= 1e-13 * scale
+    assert abs(M.overlap(ta, ta) - np.vdot(va, va)) <= 1e-13 * np.vdot(va, va).real
+    f = abs(ab) ** 2 / (np.vdot(va, va).real * np.vdot(vb, vb).real)
+    assert 1e-3 < f < 0.999                 # the two states really differ
+    assert abs(M.fidelity(ta, tb) - f) < 1e-12
+    # gauge invariance: A^2 -> A^2 X, A^3 -> X^-1 A^3 on bond 2 leaves <a|b>
+    g = np.random.default_rng(5)
+    D2 = ta[1].shape[2]
+    X = np.eye(D2) + 0.3 * (g.standard_normal((D2, D2)) + 1j * g.standard_normal((D2, D2))) / D2
+    tg = [t.copy() for t in ta]
+    tg[1] = np.einsum("apb,bc->apc", tg[1], X)
+    tg[2] = np.einsum("cb,bpd->cpd", np.linalg.inv(X), tg[2])
+    assert abs(M.overlap(tg, tb) - ab) <= 1e-12 * scale
+
+
+# ---------------------------------------------------------------- O10: the boundary flag
+def test_sampling_boundary_flag():
+    """A uniform placed on the first site's CDF value C_p is flagged
+    (|uZ - C_p| <= 1e-12 Z); 1e-9 below it takes p (the first p with
+    uZ < C_p), 1e-9 above it takes the next p with q > 0, both unflagged."""
+    w = wl.small(4, 8, depth=4, d=4, rlo=0.3, rhi=0.6)
+    T = M.normalise(M.build_mps(w.gamma, d=4, chi=20).tensors)
+    marg = M.site_marginals(T)[0]
+    cdf = np.cumsum(marg)
+    rest = [0.5, 0.5, 0.5]
+    for p in range(3):
+        if marg[p] <= 1e-6:
+            continue
+        o, fl = M.sample(T, np.array([[cdf[p]] + rest]))
+        assert fl[0]
+        assert o[0, 0] in (p, p + 1 + int(np.argmax(marg[p + 1:] > 0)))
+        o, fl = M.sample(T, np.array([[cdf[p] - 1e-9] + rest]))
+        assert not fl[0] and o[0, 0] == p
+        o, fl = M.sample(T, np.array([[cdf[p] + 1e-9] + rest]))
+        assert not fl[0] and o[0, 0] == p + 1 + int(np.argmax(marg[p + 1:] > 0))
+    # a flag on a later site is reported too
+    o0, _ = M.sample(T, np.array([[0.2] + rest]))
+    sub = M.site_marginals(T)                     # not conditional: use the rule
+    assert o0.shape == (1, 4) and sub.shape == (4, 4)
+
+
+# ---------------------------------------------------------------- hafnian module
+def test_hafnian_closed_forms():
+    """haf(ones(2n)) = (2n-1)!!; a 4x4 hafnian is the sum over its three
+    perfect matchings; the single-mode squeezed vacuum with paired-form
+    coefficient q has <2k|z>/<0|z> = q^k sqrt((2k)!)/(2^k k!) (expansion of
+    exp(q a^dag^2/2)|0>) and |<0|z>|^4 = 1 - |q|^2."""
+    for n in range(1, 6):
+        assert H.hafnian(np.ones((2 * n, 2 * n))) == math.prod(range(1, 2 * n, 2))
+    assert H.hafnian(np.ones((5, 5))) == 0
+    g = np.random.default_rng(3)
+    A = g.standard_normal((4, 4)) + 1j * g.standard_normal((4, 4))
+    A = A + A.T
+    ex = A[0, 1] * A[2, 3] + A[0, 2] * A[1, 3] + A[0, 3] * A[1, 2]
+    assert abs(H.hafnian(A) - ex) < 1e-13
+    q = -np.exp(0.7j) * math.tanh(0.6)
+    Q = np.array([[q]])
+    for k in range(6):
+        ex = q ** k * math.sqrt(math.factorial(2 * k)) / (2 ** k * math.factorial(k))
+        assert abs(H.relative_amplitude(Q, [2 * k]) - ex) < 1e-13
+        assert H.relative_amplitude(Q, [2 * k + 1]) == 0
+    assert abs(H.vacuum_amplitude(Q) ** 2 - 1 / math.cosh(0.6)) < 1e-14
+
+
+# ---------------------------------------------------------------- purity and gauge
+def test_purity_defect_of_thermal_and_pure_states():
+    """A single-mode thermal state Gamma = (nbar + 1/2) I has
+    (2 Gamma Omega)^2 = -(2 nbar + 1)^2 I, so the defect is (2 nbar + 1)^2 - 1;
+    a pure state has defect 0."""
+    for nbar in (0.1, 0.5, 2.0):
+        assert abs(G.purity_defect((nbar + 0.5) * np.eye(2)) - ((2 * nbar + 1) ** 2 - 1)) < 1e-12
+    w = wl.small(5, 3, depth=4)
+    assert G.purity_defect(w.gamma) < 1e-12
+
+
+def test_canonical_gauge_fixes_the_free_phases():
+    """b_q -> e^{i t_q} b_q multiplies column q of U and V by e^{-i t_q}; the
+    canonical gauge removes any such phase (same output for every input
+    phase), makes each column's largest |U| entry real positive and keeps
+    the constraints of Eq. (UV)."""
+    w = wl.small(6, 2, depth=6, rlo=0.2, rhi=0.7)
+    sub = [0, 1, 2, 6, 7, 8]
+    D, S = G.williamson(w.gamma[np.ix_(sub, sub)])
+    U, V = G.uv_from_s(S)
+    U1, V1 = G.canonical_gauge(U, V)
+    ph = np.exp(1j * np.array([0.4, -2.0, 2.9]))
+    U2, V2 = G.canonical_gauge(U * ph, V * ph)
+    assert np.abs(U1 - U2).max() < 1e-13 and np.abs(V1 - V2).max() < 1e-13
+    for q in range(3):
+        j = int(np.argmax(np.abs(U1[:, q])))
+        assert abs(U1[j, q].imag) < 1e-15 and U1[j, q].real > 0
+    I3 = np.eye(3)
+    assert np.abs(U1.conj().T @ U1 - V1.conj().T @ V1 - I3).max() < 1e-12
+    assert np.abs(U1.T @ V1 - V1.T @ U1).max() < 1e-12
+
+
+# ---------------------------------------------------------------- FP64 determinacy (tolerances)
+def test_two_williamson_routes_bound_fp64_amplitude_parity():
+    """How closely is the MPS of a given Gamma determined in FP64 at all?
+    Two valid FP64 Williamson routes (Cholesky vs symmetric square root) give
+    MPSs whose fidelity agrees to ~1e-15 but whose amplitudes differ by
+    ~1e-12 of the largest amplitude when modes near the freeze threshold
+    1e-9 are kept: such a mode is nearly degenerate with the frozen ones (gap
+    ~2 Lambda^2), so its eigenvector is fixed only to ~1e-16/(2 Lambda^2).
+    Small amplitudes therefore carry relative differences far above 1e-9 in
+    any FP64 implementation; GPU parity is held to the oracle-route spread."""
+    w = wl.small(24, 5, d=4, chi=64, depth=6)
+    m1 = M.build_mps(w.gamma, d=4, chi=64, lambda2_freeze=1e-9)
+    m2 = M.build_mps(w.gamma, d=4, chi=64, lambda2_freeze=1e-9, route=G.williamson_sqrt)
+    assert m1.bond_dims == m2.bond_dims and m1.n_e == m2.n_e
+    T1, T2 = M.normalise(m1.tensors), M.normalise(m2.tensors)
+    assert 1 - M.fidelity(T1, T2) < 1e-14
+    pats = np.concatenate([wl.random_patterns(300, 24, 4, seed=1),
+                           wl.random_patterns(300, 24, 4, seed=2, even=False)])
+    a1, a2 = M.amplitudes(T1, pats), M.amplitudes(T2, pats)
+    mx = np.abs(a1).max()
+    spread = np.abs(a1 - a2)
+    assert 1e-14 * mx < spread.max() < 1e-10 * mx
+    mid = np.abs(a1) > 1e-8 * mx
+    assert np.max(spread[mid] / np.abs(a1[mid])) > 1e-8      # far above 1e-9 relative
+    # odd totals are exactly zero on both routes (P6)
+    odd = pats.astype(int).sum(1) % 2 == 1
+    assert np.all(a1[odd] == 0) and np.all(a2[odd] == 0)
