@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,11 +38,67 @@ WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) thro
 # the environment GEMM of the 144-mode workload (the same at any sample count)
 TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69032.0 + 37278.6) MB over 1152 launches
 ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.01e6       # (7214.2 + 0.1) MB over 1440 launches
+# the PCO build's DRAM bytes per launch (one launch per 144-mode build); None
+# until a capture of the current kernel is taken
+PCO_TRAFFIC_BYTES_PER_LAUNCH = None
 # A double-float multiply-add (2 flops of the FP64 algorithm) costs 12 FP32
 # instructions: the exact product by FMA (4, with the low words) and Knuth's
 # TwoSum into the (hi, lo) accumulator (6) plus the low-word update (2)
 DF64_FP32_INSTR_PER_FMA = 12
 FP32_LANES_PER_SM = 128
+
+
+def pco_update_count(occ_l, occ_r, d, Q=None):
+    """Algorithmic work of one PCO tensor build as the paper's algorithms do
+    it (Sec. II C, App. B Algs. 2, 4, 5 and the physical-mode PCOs): the
+    number of (target, source) complex updates over the tensor
+    C[alpha, p, beta] summed over every PCO zeta <= zeta' with a nonzero
+    coupling Q[zeta, zeta'] (all of them when Q is None).  With
+    N_q(k) = #{states with n_q >= k} (d - k for the physical mode) a cross
+    PCO between two index spaces makes sum_k N_q(k) N_q'(k) x (size of the
+    third space) updates, an intra PCO (Alg. 4, composed vector set)
+    sum_k #{n_q >= k and n_q' >= k} x (the other two), a duplicate PCO
+    (Alg. 5) sum_{k even} N_q(k) x (the other two).  occ_l (D_l, n_l) and
+    occ_r (D_r, n_r) are the kept occupation vectors of the two bonds."""
+    import numpy as np
+    occ_l = np.asarray(occ_l, dtype=np.int64).reshape(len(occ_l), -1)
+    occ_r = np.asarray(occ_r, dtype=np.int64).reshape(len(occ_r), -1)
+    Dl, nl = occ_l.shape
+    Dr, nr = occ_r.shape
+    K = max(d, int(occ_l.max(initial=0)), int(occ_r.max(initial=0)))
+    ks = np.arange(1, K + 1)
+
+    def nge(col):
+        return (col[None, :] >= ks[:, None]).sum(axis=1)
+
+    Nl = [nge(occ_l[:, q]) for q in range(nl)]
+    Nr = [nge(occ_r[:, q]) for q in range(nr)]
+    Np = np.maximum(d - ks, 0)
+    a = nl
+    on = (lambda z1, z2: True) if Q is None else (lambda z1, z2: Q[z1, z2] != 0)
+    U = 0
+    for q in range(nl):
+        if on(q, a):
+            U += int((Nl[q] * Np).sum()) * Dr
+    for q in range(nr):
+        if on(a, a + 1 + q):
+            U += int((Nr[q] * Np).sum()) * Dl
+    if on(a, a):
+        U += int(Np[1::2].sum()) * Dl * Dr
+    for q in range(nl):
+        for qq in range(nr):
+            if on(q, a + 1 + qq):
+                U += int((Nl[q] * Nr[qq]).sum()) * d
+    for occ, N, off, other in ((occ_l, Nl, 0, d * Dr), (occ_r, Nr, a + 1, d * Dl)):
+        n = occ.shape[1]
+        for q in range(n):
+            for qq in range(q + 1, n):
+                if on(off + q, off + qq):
+                    both = np.minimum(occ[:, q], occ[:, qq])
+                    U += int(nge(both).sum()) * other
+            if on(off + q, off + q):
+                U += int(N[q][1::2].sum()) * other
+    return U
 
 
 def parse():
@@ -61,9 +118,17 @@ def parse():
     ap.add_argument("--batch-states", type=int, default=64)
     ap.add_argument("--ref-budget", type=float, default=20.0,
                     help="seconds of oracle work behind the CPU baseline / reference arm")
-    ap.add_argument("--serving-requests", type=int, default=24)
-    ap.add_argument("--serving-rate", type=float, default=4.0)
+    ap.add_argument("--serving-requests", type=int, default=100,
+                    help="requests per arrival rate")
+    ap.add_argument("--serving-rates", default="3,6,12",
+                    help="comma-separated Poisson arrival rates (1/s), one serving run each")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-batch", type=int, default=8,
+                    help="most queued requests one serving slot builds in one batched call")
+    ap.add_argument("--latency-runs", type=int, default=100,
+                    help="one-state runs behind latency_ms (p99 is then not the maximum)")
+    ap.add_argument("--large", type=int, default=1,
+                    help="1: add the 1024-mode configuration (build + 1M samples) to the line")
     ap.add_argument("--profile-pass", default=None, choices=["build", "sample"],
                     help="run one build of the workload (and one sampling of --samples) on "
                          "cuda:0 and exit without a JSON line: a short, fixed launch sequence "
@@ -226,19 +291,18 @@ def run_gpu(args, rank, local, ws, dist):
     total_s = max_over_ranks(total_ms / 1e3, dist)
     value = N * args.steps * ws / total_s
     samples_per_s = S * args.steps * ws / total_s
-    if pipelined:
-        # latency of one state alone (build + sampling, nothing overlapped)
-        lat = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        barrier()
-        with torch.cuda.stream(stream):
-            lat[0].record(stream)
-            for i in range(args.steps):
-                step(args.warmup + args.steps + i)
-                lat[i + 1].record(stream)
-        barrier()
-        step_ms = [lat[i].elapsed_time(lat[i + 1]) for i in range(args.steps)]
-    else:
-        step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    # latency of one state alone (build + sampling, nothing overlapped), over
+    # enough runs that the 99th percentile is not simply the largest one
+    nlat = max(args.latency_runs, 1)
+    lat = [torch.cuda.Event(enable_timing=True) for _ in range(nlat + 1)]
+    barrier()
+    with torch.cuda.stream(stream):
+        lat[0].record(stream)
+        for i in range(nlat):
+            step(args.warmup + args.steps + i)
+            lat[i + 1].record(stream)
+    barrier()
+    step_ms = [lat[i].elapsed_time(lat[i + 1]) for i in range(nlat)]
 
     # dominant kernel, traced over one extra step outside the timed region
     g.gbsmps_trace(ctx.h, True)
@@ -246,7 +310,15 @@ def run_gpu(args, rank, local, ws, dist):
     torch.cuda.synchronize(dev)
     tr = g.gbsmps_trace_read_kernel(ctx.h, 0)
     te = g.gbsmps_trace_read_kernel(ctx.h, 1)
+    tp = g.gbsmps_trace_read_kernel(ctx.h, 2)
     g.gbsmps_trace(ctx.h, False)
+    # the PCO build's algorithmic work: the paper's update count from the
+    # kept bases of the same state
+    mb = g.MPS.from_cov(ctx, gam, **opts)
+    occs = [g.gbsmps_get_basis(mb.h, b)[0] for b in range(N + 1)]
+    mb.release()
+    U = sum(pco_update_count(occs[m], occs[m + 1], w.d) for m in range(N))
+    out_entries = sum(occs[m].shape[0] * w.d * occs[m + 1].shape[0] for m in range(N))
     peaks, src = measured_peaks()
     step_ms_avg = total_ms / args.steps
     # the sampler GEMM against the tensor roof
@@ -282,22 +354,29 @@ def run_gpu(args, rank, local, ws, dist):
         gbs = roof_s["traffic"] / (tr["ms"] / n_launch / 1e3) / 1e9
         roof_s.update(dram_gbs=round(gbs, 1), dram_frac=round(gbs / hbm, 4),
                       dram_peak_source=f"hbm_gbs of {src} MEASURED_PEAKS.json")
-    # the environment GEMM against the FP32 pipe's double-float roof
+    # the environment GEMM against the FP32 pipes it runs on: algorithmic
+    # flops counted once (x1), the double-float emulation cost shown apart
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
-    df_peak = nsm * FP32_LANES_PER_SM * fmax * 2.0 / DF64_FP32_INSTR_PER_FMA / 1e12
+    fp32_peak = nsm * FP32_LANES_PER_SM * fmax * 2.0 / 1e12
     ne = max(te["launches"], 1)
     ach_df = te["flops"] / (te["ms"] / 1e3) / 1e12 if te["ms"] > 0 else 0.0
     roof_e = {"kernel": "zgemm_df64_grouped_kernel (double-float complex GEMM on the FP32 pipes, "
                         "right-environment chain R_m = sum_p Ahat^m[p] R_{m+1} Ahat^m[p]^dag on the "
                         "parity blocks; two grouped launches per site, split-K partials summed in k "
                         "order by each tile's last CTA)",
-              "bound": "alu", "achieved": round(ach_df, 4), "peak": round(df_peak, 3),
+              "bound": "alu", "achieved": round(ach_df, 4), "peak": round(fp32_peak, 3),
               "peak_source": (f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                              f"{fmax / 1e6:.0f} MHz (max SM clock) x 2 flops / "
-                              f"{DF64_FP32_INSTR_PER_FMA} FP32 instructions per double-float "
-                              "multiply-add"),
-              "unit": "TFLOP/s", "frac": round(ach_df / df_peak, 5) if df_peak > 0 else None,
+                              f"{fmax / 1e6:.0f} MHz (max SM clock) x 2 flops per FMA: the FP32 pipes "
+                              "the kernel runs on; achieved counts the FP64 algorithm's flops once"),
+              "unit": "TFLOP/s", "frac": round(ach_df / fp32_peak, 5) if fp32_peak > 0 else None,
+              "issued_fp32_instr_per_fma": DF64_FP32_INSTR_PER_FMA,
+              "issued_frac": round(ach_df * DF64_FP32_INSTR_PER_FMA / 2.0 / (fp32_peak / 2.0), 4)
+              if fp32_peak > 0 else None,
+              "issued_frac_def": ("FP32 instructions issued for the double-float arithmetic "
+                                  f"({DF64_FP32_INSTR_PER_FMA} per real multiply-add: exact product "
+                                  "by FMA and TwoSum accumulation) over the FP32 lanes' instruction "
+                                  "rate"),
               "traffic": ENV_TRAFFIC_BYTES_PER_LAUNCH,
               "algorithmic_flops_per_launch": te["flops"] / ne,
               "algorithmic_bytes_per_launch": te["bytes"] / ne,
@@ -309,6 +388,39 @@ def run_gpu(args, rank, local, ws, dist):
               "launches_per_step": te["launches"],
               "ms_per_state": round(te["ms"], 3),
               "share_of_step": round(te["ms"] / step_ms_avg, 4)}
+    # the PCO tensor build against the HBM roof of the paper's algorithm:
+    # U (target, source) updates, each a source read, a target read and a
+    # target write of one complex number in the pass precision (complex64 in
+    # mixed builds, complex128 in FP64 ones), plus the tensors written once
+    # as complex128
+    cbytes = 8 if prec == g.PREC_MIXED else 16
+    alg_b = U * 3 * cbytes + out_entries * 16
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach_p = alg_b / (tp["ms"] / 1e3) / 1e9 if tp["ms"] > 0 else 0.0
+    roof_p = {"kernel": ("pco_kernel<%s> (one CTA of 1024 threads per site: one-sided PCOs on "
+                         "vectors, cross PCOs in place by level, physical PCOs as d - 1 passes of "
+                         "l_L + l_R with odd-parity entries skipped; FP32 passes with FP64 plane "
+                         "sums in mixed builds)") % ("float" if prec == g.PREC_MIXED else "double"),
+              "bound": "hbm", "achieved": round(ach_p, 1), "peak": hbm,
+              "peak_source": f"hbm_gbs of {src} MEASURED_PEAKS.json", "unit": "GB/s",
+              "frac": round(ach_p / hbm, 4),
+              "traffic": PCO_TRAFFIC_BYTES_PER_LAUNCH,
+              "updates_per_state": U, "updates_per_s": round(U / (tp["ms"] / 1e3), 1) if tp["ms"] > 0 else None,
+              "algorithmic_bytes_per_launch": alg_b / max(tp["launches"], 1),
+              "algorithmic_bytes_def": ("the paper's update count U (Algs. 2, 4, 5 and the physical "
+                                        "PCOs: (target, source, kappa) trip counts of the vector sets "
+                                        "with the kappa match, counted from the kept bases) x (source "
+                                        f"read + target read + target write) x {cbytes} B + the "
+                                        "tensors written once (d D_l D_r x 16 B)"),
+              "paper_estimate": "O(n_e^2 n~ d D^2) per tensor (Sec. II C)",
+              "avg_launch_ms": tp["ms"] / max(tp["launches"], 1),
+              "launches_per_step": tp["launches"], "ms_per_state": round(tp["ms"], 3),
+              "share_of_step": round(tp["ms"] / step_ms_avg, 4),
+              "note": ("the kernel regroups the PCOs (one-sided products on vectors, the physical "
+                       "PCOs as d - 1 combined passes) and keeps its working set on chip and in "
+                       "L2, so it moves far fewer bytes than the paper's algorithm would: frac "
+                       "near or above 1 means it runs at or faster than that algorithm at the "
+                       "HBM roof; traffic is its measured DRAM bytes per launch")}
     # the roofline object follows the kernel with the most device time per
     # state on the step's critical path (the Gaussian-SVD chains run on one
     # SM beside the step), the other is reported beside it
@@ -365,6 +477,10 @@ def run_gpu(args, rank, local, ws, dist):
                 "tensors_per_s": round(N / (s64_ms_step / 1e3), 3),
                 "samples_per_s": round(S / (s64_ms_step / 1e3), 1),
                 "sample": f"FP64 build timed in full; sampling timed on {S64} samples and scaled to {S}",
+                "note": ("the plain FP64 GPU path: FP64 PCO passes, dense FP64 environments (no "
+                         "parity blocks, no energy gauge), sampling by dense w R w^dag per sample "
+                         "(no right-canonical form, no p = 0 pre-pass); the ratio to the mixed "
+                         "path includes these algorithmic changes as well as the precision"),
                 "mixed_vs_fp64_amp_max_rel_err": float(rel[big].max()),
                 "mixed_vs_fp64_amp_max_abs_err_rel_to_max": float(np.abs(amp_mixed - amp64).max() / np.abs(amp64).max()),
                 "shared_seed_sample_agreement": agree}
@@ -396,7 +512,66 @@ def run_gpu(args, rank, local, ws, dist):
     ctx.close()
     return dict(value=value, samples_per_s=samples_per_s, step_ms=step_ms, launches=launches,
                 ms_per_step=total_s * 1e3 / args.steps, pipelined=pipelined,
-                roof=roof, roof_other=roof_other, clocks=clk.summary(), e2e=e2e, **res)
+                roof=roof, roof_other=roof_other, roof_pco=roof_p, clocks=clk.summary(), e2e=e2e,
+                **res)
+
+
+# --------------------------------------------------------------------------- large configuration
+def run_large(args, dev):
+    """The 1024-mode configuration (r~U(0.05,0.25), depth-32 brick wall,
+    d = 4, chi = 512) in mixed precision: one build and 1,000,000 samples,
+    each timed with CUDA events on the launching stream, and the sampler
+    GEMM traced over the sampling (its tensor-roof fraction)."""
+    import numpy as np
+    import torch
+
+    import paper_2512_10643_gb300 as g
+    import workloads as wl
+
+    w = wl.config("n1024_d4_chi512")
+    S = 1_000_000
+    stream = torch.cuda.Stream(device=dev)
+    ctx = g.Context(dev, stream.cuda_stream)
+    gam = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(f"cuda:{dev}")
+    out = torch.empty((S, w.N), dtype=torch.uint8, device=f"cuda:{dev}")
+    opts = dict(d=w.d, chi_max=w.chi, eps_trunc=w.eps, lambda2_freeze=w.freeze,
+                precision=g.PREC_MIXED)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    g.gbsmps_trace(ctx.h, True)
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        m = g.MPS.from_cov(ctx, gam, **opts)
+        ev[1].record(stream)
+        m.sample(S, seed=77, counter0=0, out=out)
+        ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    tr = g.gbsmps_trace_read_kernel(ctx.h, 0)
+    g.gbsmps_trace(ctx.h, False)
+    build_ms, sample_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    photons = out.to(torch.int64).sum(dim=1)
+    even = bool((photons % 2 == 0).all().item())
+    mean_ph = float(photons.float().mean().item())
+    dims = [int(x) for x in m.info["bond_dims"]]
+    m.release()
+    ctx.close()
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    ach = tr["flops"] / (tr["ms"] / 1e3) / 1e12 if tr["ms"] > 0 else 0.0
+    return {"workload": ("1024-mode pure Gaussian state: squeezed vacua r~U(0.05,0.25) through a "
+                         "depth-32 brick-wall network; d=4, chi=512, eps=1e-12, lambda2_freeze=1e-9; "
+                         "mixed precision; Gamma on the device"),
+            "build_ms": round(build_ms, 2), "sample_ms": round(sample_ms, 2), "samples": S,
+            "tensors_per_s_build": round(w.N / (build_ms / 1e3), 1),
+            "samples_per_s": round(S / (sample_ms / 1e3), 1),
+            "tensors_per_s_whole": round(w.N / ((build_ms + sample_ms) / 1e3), 1),
+            "max_bond_dim": max(dims), "mean_photons": round(mean_ph, 3),
+            "all_samples_even": even,
+            "sampler_gemm": {"ms": round(tr["ms"], 2), "launches": tr["launches"],
+                             "achieved_tflops": round(ach, 3), "peak": peak,
+                             "frac": round(ach / peak, 5), "issued_frac": round(3 * ach / peak, 5),
+                             "share_of_sampling": round(tr["ms"] / sample_ms, 4) if sample_ms > 0 else None,
+                             "peak_source": f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json"}}
 
 
 # --------------------------------------------------------------------------- batched build
@@ -452,7 +627,7 @@ def run_batched(args, dev):
 
 
 # --------------------------------------------------------------------------- serving
-def run_serving(args, dev):
+def run_serving(args, dev, rate):
     """Poisson-arriving build + sampling requests through the library's
     request loop (gbsmps_server_*): N log-uniform in [32, 512], r~U(0.05,0.4),
     depth N/16, d in {4, 6}, chi in {64..512}, 1e3..1e5 samples each.
@@ -460,10 +635,10 @@ def run_serving(args, dev):
     import paper_2512_10643_gb300 as g
     import workloads as wl
 
-    reqs = wl.serving(args.serving_requests, args.serving_rate)
+    reqs = wl.serving(args.serving_requests, rate)
     t0 = time.perf_counter()
     ids = []
-    with g.Server(dev, slots=args.serving_slots) as srv:
+    with g.Server(dev, slots=args.serving_slots, batch_max=args.serving_batch) as srv:
         start = time.perf_counter()
         for t_arr, w, S in reqs:
             delay = t_arr - (time.perf_counter() - start)
@@ -476,8 +651,10 @@ def run_serving(args, dev):
         infos = [srv.wait(i)[1] for i in ids]
         st = srv.stats()
     busy = st["busy_s"]
-    return {"requests": len(reqs), "arrival_rate_hz": args.serving_rate,
-            "slots": args.serving_slots, "completed": st["completed"], "failed": st["failed"],
+    return {"requests": len(reqs), "arrival_rate_hz": rate,
+            "slots": args.serving_slots, "batch_max": args.serving_batch,
+            "mean_batch": round(sum(x["batch"] for x in infos) / max(len(infos), 1), 2),
+            "completed": st["completed"], "failed": st["failed"],
             "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2),
                            "mean": round(st["mean_ms"], 2)},
             "tensors_per_s": round(st["tensors"] / busy, 2) if busy > 0 else None,
@@ -616,9 +793,13 @@ def main():
                        if args.precision == "mixed" else "f64"),
                 config=cfg, samples_per_s=round(r["samples_per_s"], 1),
                 latency_ms={"p50": round(statistics.median(sm), 3),
-                            "p99": round(sm[min(len(sm) - 1, int(0.99 * len(sm)))], 3)},
+                            "p99": round(sm[min(len(sm) - 1, max(0, int(math.ceil(0.99 * len(sm))) - 1))], 3),
+                            "runs": len(sm), "max": round(sm[-1], 3),
+                            "def": "one state alone: build + 100k samples, nothing overlapped; "
+                                   "nearest-rank quantiles"},
                 build_ms=round(r.get("build_ms", 0.0), 3),
-                roofline=r["roof"], roofline_other=r["roof_other"], cpu_baseline=cpu, e2e=r["e2e"],
+                roofline=r["roof"], roofline_other=r["roof_other"], roofline_pco=r["roof_pco"],
+                cpu_baseline=cpu, e2e=r["e2e"],
                 gpu_launches=r["launches"],
                 clocks=r["clocks"])
     if "fp64_gpu" in r:
@@ -629,11 +810,19 @@ def main():
             line["batched"] = run_batched(args, local)
         except Exception as e:          # noqa: BLE001
             line["batched"] = {"error": f"{type(e).__name__}: {e}"}
-    if ws == 1 and args.serving_requests > 0:
+    if ws == 1 and args.large:
         try:
-            line["serving"] = run_serving(args, local)
+            line["large"] = run_large(args, local)
         except Exception as e:          # noqa: BLE001
-            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
+            line["large"] = {"error": f"{type(e).__name__}: {e}"}
+    if ws == 1 and args.serving_requests > 0:
+        sweep = []
+        for rate in [float(x) for x in args.serving_rates.split(",") if x.strip()]:
+            try:
+                sweep.append(run_serving(args, local, rate))
+            except Exception as e:          # noqa: BLE001
+                sweep.append({"arrival_rate_hz": rate, "error": f"{type(e).__name__}: {e}"})
+        line["serving"] = sweep
     print(json.dumps(line))
 
 

@@ -148,6 +148,15 @@ int gbsmps_get_tensor(gbsmps_mps_t mps, int32_t site, void* dst,
  * (r_{m-1}, a_m, l_m), row stride 2 NE_MAX + 1), c_m[N].  Host outputs. */
 int gbsmps_get_gsvd(gbsmps_mps_t mps, double* lam2, double* Qm, double* c_m);
 
+/* The kept basis of bond b (0..N; bond b is the cut after site b-1, bonds 0
+ * and N hold only the vacuum), Sec. II C "The kept subspace and projection":
+ * occ[D_b * n_e_b] uint8, row j = the occupation vector n_beta of kept state
+ * j over the n_e_b Schmidt modes of the cut (E order, ties lexicographic;
+ * index 0 is the vacuum), and E[D_b] its entanglement energy
+ * E_beta = sum_q n_q (-ln Lambda_q^2).  Host outputs, either may be NULL;
+ * sizes from gbsmps_info.  Synchronises.  Errors: ARG (bond range). */
+int gbsmps_get_basis(gbsmps_mps_t mps, int32_t bond, uint8_t* occ, double* E);
+
 /* Amplitudes <n_1..n_N|psi> (Eq. (Am_definition) contracted along the chain)
  * of P patterns (P x N uint8, row-major) into out (P x 2 doubles).  Patterns
  * with any n_i >= d give 0.  P = 0 is a no-op.  Errors: ARG, CUDA. */
@@ -251,16 +260,19 @@ int gbsmps_trace(gbsmps_ctx_t ctx, int enable);
 int gbsmps_trace_read(gbsmps_ctx_t ctx, double* total_ms, int64_t* launches,
                       double* flops, double* bytes);
 
-/* The same record for one of two traced kernels: which = 0, the sampler GEMM
- * above (gbsmps_trace_read); which = 1, the double-float complex GEMM of the
- * right-environment chain R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (the norm,
- * and the standard MPS sampling that Sec. I and Sec. III defer to; two
+/* The same record for one of three traced kernels: which = 0, the sampler
+ * GEMM above (gbsmps_trace_read); which = 1, the double-float complex GEMM of
+ * the right-environment chain R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (the
+ * norm, and the standard MPS sampling that Sec. I and Sec. III defer to; two
  * grouped launches per site), whose
  * work counts 8 real flops per complex multiply-add of the lower triangle
  * of a Hermitian result and of every element otherwise, and whose bytes are
- * the operands and results at 16 bytes per complex element.  Recording is
- * switched on and cleared for both by gbsmps_trace.  GBSMPS_ERR_ARG for
- * another `which`.  Not part of the numerical path. */
+ * the operands and results at 16 bytes per complex element; which = 2, the
+ * PCO tensor build of a state (Sec. II C, App. B; one launch per wave of
+ * sites), time and launch count only (its algorithmic work is counted by the
+ * caller from the kept bases, gbsmps_get_basis).  Recording is switched on
+ * and cleared for all three by gbsmps_trace.  GBSMPS_ERR_ARG for another
+ * `which`.  Not part of the numerical path. */
 int gbsmps_trace_read_kernel(gbsmps_ctx_t ctx, int32_t which, double* total_ms,
                              int64_t* launches, double* flops, double* bytes);
 
@@ -275,9 +287,16 @@ int gbsmps_trace_read_kernel(gbsmps_ctx_t ctx, int32_t which, double* total_ms,
  * (gbsmps_sample, Philox keyed by seed/counter0) on its slot's stream, with
  * the MPS resident on the device in between, and writes the S x N patterns to
  * req.out; jobs on different slots overlap on the GPU, and a job's result is
- * bitwise the result of the same calls made alone.  The caller keeps
- * req.gamma and req.out valid until the job is done.  Latency is submit ->
- * done on the server's monotonic clock. */
+ * bitwise the result of the same calls made alone.  With batch_max > 1 a
+ * slot that admits a job also admits up to batch_max - 1 more admissible
+ * queued jobs and builds them all in one gbsmps_build_batch call (every GSVD
+ * chain in one launch, every PCO tensor together, the environment chains in
+ * one persistent launch), then samples them one after another, each job
+ * completing when its own patterns are out; the environment products of a
+ * batch sum in another order, so such a result equals the job run alone up
+ * to rounding (samples bit-exact except draws that req.flags marks).  The
+ * caller keeps req.gamma, req.out and req.flags valid until the job is done.
+ * Latency is submit -> done on the server's monotonic clock. */
 typedef struct gbsmps_server* gbsmps_server_t;
 
 typedef struct {
@@ -289,6 +308,8 @@ typedef struct {
                                     N x this many seconds and writes zeros
                                     (tests of the scheduler without a device);
                                     needs hbm_budget > 0                        */
+  int32_t batch_max;             /* jobs one slot builds in one batched call
+                                    (1..64), default 1                          */
 } gbsmps_server_opts;
 
 typedef struct {
@@ -298,6 +319,8 @@ typedef struct {
   int64_t samples;       /* S >= 0                                              */
   uint64_t seed, counter0;
   uint8_t* out;          /* host S x N uint8, written by the job                */
+  uint8_t* flags;        /* optional host S bytes: 1 where a draw lay within the
+                            sampler's boundary window (as gbsmps_sample)       */
 } gbsmps_request;
 
 typedef struct {
@@ -307,6 +330,7 @@ typedef struct {
   double t_submit, t_admit, t_done;   /* seconds since server creation          */
   size_t hbm_bytes;      /* admission estimate                                  */
   char detail[128];      /* error detail of a failed job                        */
+  int32_t batch;         /* jobs built in the same batched call (1: alone)      */
 } gbsmps_job_info;
 
 typedef struct {

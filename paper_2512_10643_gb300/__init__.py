@@ -28,13 +28,13 @@ QS = 2 * NE_MAX + 1
 
 class ServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_size_t),
-                ("simulate_s_per_tensor", C.c_double)]
+                ("simulate_s_per_tensor", C.c_double), ("batch_max", C.c_int32)]
 
 
 class JobInfo(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("slot", C.c_int32),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
-                ("hbm_bytes", C.c_size_t), ("detail", C.c_char * 128)]
+                ("hbm_bytes", C.c_size_t), ("detail", C.c_char * 128), ("batch", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -59,7 +59,8 @@ class Opts(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("gamma", C.c_void_p), ("N", C.c_int32), ("opts", Opts), ("samples", C.c_int64),
-                ("seed", C.c_uint64), ("counter0", C.c_uint64), ("out", C.c_void_p)]
+                ("seed", C.c_uint64), ("counter0", C.c_uint64), ("out", C.c_void_p),
+                ("flags", C.c_void_p)]
 
 
 _lib = None
@@ -83,6 +84,7 @@ def lib():
         "gbsmps_info": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "gbsmps_get_tensor": (C.c_int, [vp, i32, vp, C.c_size_t, C.c_int]),
         "gbsmps_get_gsvd": (C.c_int, [vp, vp, vp, vp]),
+        "gbsmps_get_basis": (C.c_int, [vp, i32, vp, vp]),
         "gbsmps_amplitudes": (C.c_int, [vp, i64, vp, vp, C.c_int]),
         "gbsmps_sample": (C.c_int, [vp, i64, u64, u64, vp, vp, vp, C.c_int]),
         "gbsmps_release": (C.c_int, [vp]),
@@ -256,6 +258,17 @@ def gbsmps_get_gsvd(mps):
     return lam2[:(N - 1) * NE_MAX].reshape(max(N - 1, 0), NE_MAX), Qm.reshape(N, QS, QS), cm
 
 
+def gbsmps_get_basis(mps, bond: int):
+    """(occ uint8 (D_b, n_e_b), E float64 (D_b,)) of the kept basis of bond b."""
+    info = gbsmps_info(mps)
+    D = int(info["bond_dims"][bond])
+    ne = 0 if bond in (0, info["N"]) else int(info["n_e"][bond - 1])
+    occ = np.zeros((D, ne), dtype=np.uint8)
+    E = np.zeros(D, dtype=np.float64)
+    _check(lib().gbsmps_get_basis(mps, int(bond), occ.ctypes.data if ne else None, E.ctypes.data))
+    return occ, E
+
+
 def gbsmps_amplitudes(mps, patterns, out=None):
     P = patterns.shape[0]
     if out is None:
@@ -337,7 +350,8 @@ def gbsmps_trace_read(ctx):
 
 
 def gbsmps_trace_read_kernel(ctx, which: int):
-    """which = 0: the sampler GEMM (as gbsmps_trace_read); 1: the environment GEMM."""
+    """which = 0: the sampler GEMM (as gbsmps_trace_read); 1: the environment
+    GEMM; 2: the PCO tensor build (time and launches only)."""
     ms, fl, by = C.c_double(), C.c_double(), C.c_double()
     n = C.c_int64()
     _check(lib().gbsmps_trace_read_kernel(ctx, int(which), C.byref(ms), C.byref(n), C.byref(fl),
@@ -412,10 +426,11 @@ class Server:
     memory into `slots` concurrent streams; results land in host arrays."""
 
     def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 0,
-                 simulate_s_per_tensor: float = 0.0):
+                 simulate_s_per_tensor: float = 0.0, batch_max: int = 1):
         o = ServerOpts()
         _check(lib().gbsmps_server_opts_default(C.byref(o)))
         o.slots, o.hbm_budget, o.simulate_s_per_tensor = slots, hbm_budget, simulate_s_per_tensor
+        o.batch_max = batch_max
         self.h = C.c_void_p()
         _check(lib().gbsmps_server_create(device, C.byref(o), C.byref(self.h)))
         self._keep = {}
@@ -428,24 +443,28 @@ class Server:
             gamma = np.ascontiguousarray(gamma, dtype=np.float64)
             N = gamma.shape[0] // 2
         out = np.zeros((samples, N), dtype=np.uint8)
+        flags = np.zeros(samples, dtype=np.uint8)
         r = Request()
         r.gamma = gamma.ctypes.data if gamma is not None else None
         r.N, r.opts, r.samples, r.seed, r.counter0 = N, opts_default(**opts), samples, seed, counter0
         r.out = out.ctypes.data if samples else None
+        r.flags = flags.ctypes.data if samples else None
         jid = C.c_int64()
         _check(lib().gbsmps_server_submit(self.h, C.byref(r), C.byref(jid)))
-        self._keep[jid.value] = (gamma, out)
+        self._keep[jid.value] = (gamma, out, flags)
         return jid.value
 
     def wait(self, jid: int, timeout_s: float = -1.0):
-        """(samples, info dict) of request jid; raises on a failed job."""
+        """(samples, info dict) of request jid; raises on a failed job.  The
+        info dict carries the job's boundary flags under "flags"."""
         info = JobInfo()
         rc = lib().gbsmps_server_wait(self.h, jid, timeout_s, C.byref(info))
         d = {k: getattr(info, k) for k, _ in JobInfo._fields_ if k != "detail"}
         d["detail"] = info.detail.decode(errors="replace")
         if rc != OK:
             raise GbsmpsError(rc, f"{lib().gbsmps_strerror(rc).decode()} ({d['detail']})")
-        gamma, out = self._keep.pop(jid)
+        gamma, out, flags = self._keep.pop(jid)
+        d["flags"] = flags
         return out, d
 
     def drain(self, timeout_s: float = -1.0):

@@ -14,6 +14,7 @@
 std::atomic<unsigned long long> g_kernel_launches{0};
 KernelTrace g_tc_trace;
 KernelTrace g_env_trace;
+KernelTrace g_pco_trace;
 
 thread_local std::string g_detail;
 
@@ -134,6 +135,27 @@ int gbsmps_get_gsvd(gbsmps_mps_t m, double* lam2, double* Qm, double* c_m) {
   if (Qm) CK(cudaMemcpyAsync(Qm, m->Qm, sizeof(double2) * (size_t)m->N * QS * QS, cudaMemcpyDeviceToHost, s));
   if (c_m) CK(cudaMemcpyAsync(c_m, m->cm, sizeof(double) * m->N, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return GBSMPS_OK;
+}
+
+int gbsmps_get_basis(gbsmps_mps_t m, int32_t bond, uint8_t* occ, double* E) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  if (bond < 0 || bond > m->N) return fail(GBSMPS_ERR_ARG, "bond out of range");
+  CK(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = m->ctx->stream;
+  const int D = m->D[bond];
+  const int ne = (bond == 0 || bond == m->N) ? 0 : m->ne[bond];
+  const size_t cap = (size_t)m->ba.cap;
+  std::vector<uint8_t> rows((size_t)D * NEM);
+  if (occ && ne > 0)
+    CK(cudaMemcpyAsync(rows.data(), m->ba.occ + (size_t)bond * cap * NEM, rows.size(),
+                       cudaMemcpyDeviceToHost, s));
+  if (E) CK(cudaMemcpyAsync(E, m->ba.E + (size_t)bond * cap, sizeof(double) * D,
+                            cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (occ)
+    for (int j = 0; j < D; ++j)
+      for (int q = 0; q < ne; ++q) occ[(size_t)j * ne + q] = rows[(size_t)j * NEM + q];
   return GBSMPS_OK;
 }
 
@@ -700,6 +722,8 @@ int gbsmps_trace(gbsmps_ctx_t c, int enable) {
   g_tc_trace.on = enable != 0;
   g_env_trace.reset();
   g_env_trace.on = enable != 0;
+  g_pco_trace.reset();
+  g_pco_trace.on = enable != 0;
   return GBSMPS_OK;
 }
 
@@ -716,8 +740,8 @@ int gbsmps_trace_read(gbsmps_ctx_t c, double* total_ms, int64_t* launches, doubl
 int gbsmps_trace_read_kernel(gbsmps_ctx_t c, int32_t which, double* total_ms, int64_t* launches,
                              double* flops, double* bytes) {
   if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
-  if (which != 0 && which != 1) return fail(GBSMPS_ERR_ARG, "which must be 0 or 1");
-  KernelTrace& t = which ? g_env_trace : g_tc_trace;
+  if (which < 0 || which > 2) return fail(GBSMPS_ERR_ARG, "which must be 0, 1 or 2");
+  KernelTrace& t = which == 2 ? g_pco_trace : which == 1 ? g_env_trace : g_tc_trace;
   if (total_ms) *total_ms = t.total_ms();
   if (launches) *launches = t.launches;
   if (flops) *flops = t.flops;

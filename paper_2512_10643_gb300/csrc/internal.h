@@ -153,6 +153,7 @@ struct KernelTrace {
 };
 extern KernelTrace g_tc_trace;    // the tcgen05 sampler GEMM
 extern KernelTrace g_env_trace;   // the double-float environment GEMM
+extern KernelTrace g_pco_trace;   // the PCO tensor build
 
 // ---- launchers (each returns cudaError_t of the launch) -------------------
 // g_kernel_launches counts every kernel the library enqueues.

@@ -297,6 +297,13 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
   const bool ok = jacobi_sweeps<double2, false>(sm, H, W, n, conv64, 1e-300 + 0.25 * conv64,
                                                 MAX_SWEEPS);
+  // then one sweep more over every nonzero pair, with no stop test: the
+  // criterion above leaves off-diagonal elements up to ~n eps ||H||_F, which
+  // turn the eigenvectors of a nearly degenerate pair (gap g) by ~that / g
+  // (1e-8 at g ~ 5e-7, a mode kept just above the freeze threshold); one
+  // more sweep takes every element to the rounding floor of a single sweep,
+  // where the eigenvectors are as well determined as FP64 allows
+  jacobi_sweeps<double2, false>(sm, H, W, n, -1.0, 1e-300, 1);
   for (int i = tid; i < n; i += nt) sm.ev[i] = H[i * LD + i].x;
   __syncthreads();
   return ok;

@@ -84,9 +84,13 @@ int noalloc_build_site(int device, cudaStream_t s, int* status_dev, int32_t nl, 
   // every entry the kernels read is written here first: the array keeps the
   // previous call's contents
   if (nl) repack_occ_kernel<<<(Dl * NEM + 255) / 256, 256, 0, s>>>(occ_l, Dl, nl, base + o_occl);
-  else cudaMemsetAsync(base + o_occl, 0, (size_t)Dl * NEM, s);
-  if (nr) repack_occ_kernel<<<(Dr * NEM + 255) / 256, 256, 0, s>>>(occ_r, Dr, nr, base + o_occr);
-  else cudaMemsetAsync(base + o_occr, 0, (size_t)Dr * NEM, s);
+  else e = cudaMemsetAsync(base + o_occl, 0, (size_t)Dl * NEM, s);
+  if (!e) {
+    if (nr) repack_occ_kernel<<<(Dr * NEM + 255) / 256, 256, 0, s>>>(occ_r, Dr, nr, base + o_occr);
+    else e = cudaMemsetAsync(base + o_occr, 0, (size_t)Dr * NEM, s);
+  }
+  if (!e) e = cudaGetLastError();
+  if (e) return na_fail(GBSMPS_ERR_CUDA, cudaGetErrorString(e));
   COUNT_LAUNCH((nl ? 1 : 0) + (nr ? 1 : 0));
   e = launch_maps_brute(base + o_occl, Dl, nl, reinterpret_cast<int*>(base + o_lowl), Dl, status_dev, s);
   if (!e) e = launch_maps_brute(base + o_occr, Dr, nr, reinterpret_cast<int*>(base + o_lowr), Dr, status_dev, s);

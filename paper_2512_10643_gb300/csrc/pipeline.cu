@@ -168,8 +168,10 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d, 
     CK(tk.alloc(sizeof(SiteTask) * n, s));
     CK(ctr.alloc(sizeof(int), s));
     CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
+    cudaEvent_t tr0 = g_pco_trace.begin(s);
     CK(launch_pco_dynamic(tk.as<SiteTask>(), n, d, precision, scr.as<double2>(), scr_max, grid,
                           ctr.as<int>(), c->d_status, s));
+    g_pco_trace.end(tr0, s, 0.0, 0.0);
     COUNT_LAUNCH(1);
     scr.release();
     tk.release();
@@ -184,7 +186,9 @@ int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d, 
   CK(cudaMemcpyAsync(tk.p, tasks.data(), sizeof(SiteTask) * n, cudaMemcpyHostToDevice, s));
   for (int k0 = 0; k0 < n; k0 += wave) {
     const int cnt = std::min(wave, n - k0);
+    cudaEvent_t tr0 = g_pco_trace.begin(s);
     CK(launch_pco(tk.as<SiteTask>() + k0, cnt, d, precision, scr.as<double2>(), c->d_status, s));
+    g_pco_trace.end(tr0, s, 0.0, 0.0);
     COUNT_LAUNCH(1);
   }
   scr.release();

@@ -11,7 +11,10 @@
 // slot's stream (Gamma in, MPS built and kept on the device, samples drawn,
 // patterns copied out) through the public entry points, so its result does
 // not depend on what else runs: the kernels of concurrent jobs only share the
-// GPU.  Completion times give the per-request latency (submit to done).
+// GPU.  With batch_max > 1 a slot takes up to batch_max admissible jobs at
+// once and builds them in one batched call (gbsmps_build_batch), then samples
+// each; under load this turns many small launches into few large ones.
+// Completion times give the per-request latency (submit to done).
 #include "gbsmps.h"
 
 #include <cuda_runtime.h>
@@ -85,63 +88,107 @@ struct gbsmps_server {
     return nullptr;
   }
 
-  int run(Job& j, int slot) {
-    if (opts.simulate_s_per_tensor > 0.0) {
-      std::this_thread::sleep_for(std::chrono::duration<double>(opts.simulate_s_per_tensor * j.req.N));
-      if (j.req.out) std::fill(j.req.out, j.req.out + (size_t)j.req.samples * j.req.N, (uint8_t)0);
-      return GBSMPS_OK;
+  // a job's end: its memory returns to the budget, its record is final
+  void finish(Job& j, int rc) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= j.est;
+      --running;
+      j.info.t_done = now_s() - t0;
+      j.info.error = rc;
+      j.info.state = rc ? 3 : 2;
+      if (rc) std::snprintf(j.info.detail, sizeof(j.info.detail), "%s", gbsmps_last_error_detail());
+      if (rc) {
+        ++failed;
+      } else {
+        ++completed;
+        lat_ms.push_back(1e3 * (j.info.t_done - j.info.t_submit));
+        tensors += j.req.N;
+        samples += (double)j.req.samples;
+      }
+      last_done = std::max(last_done, j.info.t_done);
     }
-    gbsmps_mps_t m = nullptr;
-    int rc = gbsmps_build_from_cov(ctxs[slot], j.req.N, j.req.gamma, GBSMPS_MEM_HOST, &j.req.opts, &m);
-    if (rc) return rc;
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+
+  int sample_one(Job& j, gbsmps_mps_t m) {
+    int rc = GBSMPS_OK;
     if (j.req.samples > 0)
-      rc = gbsmps_sample(m, j.req.samples, j.req.seed, j.req.counter0, nullptr, j.req.out, nullptr,
-                         GBSMPS_MEM_HOST);
-    int rc2 = gbsmps_release(m);
+      rc = gbsmps_sample(m, j.req.samples, j.req.seed, j.req.counter0, nullptr, j.req.out,
+                         j.req.flags, GBSMPS_MEM_HOST);
+    const int rc2 = gbsmps_release(m);
     return rc ? rc : rc2;
+  }
+
+  void run(std::vector<std::shared_ptr<Job>>& js, int slot) {
+    if (opts.simulate_s_per_tensor > 0.0) {
+      double n = 0.0;
+      for (auto& j : js) n += j->req.N;
+      std::this_thread::sleep_for(std::chrono::duration<double>(opts.simulate_s_per_tensor * n));
+      for (auto& j : js) {
+        if (j->req.out) std::fill(j->req.out, j->req.out + (size_t)j->req.samples * j->req.N, (uint8_t)0);
+        if (j->req.flags) std::fill(j->req.flags, j->req.flags + (size_t)j->req.samples, (uint8_t)0);
+        finish(*j, GBSMPS_OK);
+      }
+      return;
+    }
+    if (js.size() == 1) {
+      Job& j = *js[0];
+      gbsmps_mps_t m = nullptr;
+      int rc = gbsmps_build_from_cov(ctxs[slot], j.req.N, j.req.gamma, GBSMPS_MEM_HOST, &j.req.opts, &m);
+      if (!rc) rc = sample_one(j, m);
+      finish(j, rc);
+      return;
+    }
+    const int n = (int)js.size();
+    std::vector<int32_t> Ns(n);
+    std::vector<const double*> gs(n);
+    std::vector<gbsmps_opts> os(n);
+    std::vector<gbsmps_mps_t> hs(n, nullptr);
+    for (int k = 0; k < n; ++k) {
+      Ns[k] = js[k]->req.N;
+      gs[k] = js[k]->req.gamma;
+      os[k] = js[k]->req.opts;
+    }
+    const int rc = gbsmps_build_batch(ctxs[slot], n, Ns.data(), gs.data(), GBSMPS_MEM_HOST, os.data(),
+                                      hs.data());
+    for (int k = 0; k < n; ++k) finish(*js[k], rc ? rc : sample_one(*js[k], hs[k]));
   }
 
   void worker(int slot) {
     if (opts.simulate_s_per_tensor <= 0.0) cudaSetDevice(device);
     for (;;) {
-      std::shared_ptr<Job> j;
+      std::vector<std::shared_ptr<Job>> js;
       {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
           if (stop && queue.empty()) return;
-          j = pick();
-          if (j) break;
+          auto j = pick();
+          if (j) { js.push_back(j); break; }
           cv_work.wait(lk);
         }
-        in_use += j->est;
-        peak = std::max(peak, in_use);
-        ++running;
-        j->info.state = 1;
-        j->info.slot = slot;
-        j->info.t_admit = now_s() - t0;
-        if (first_admit < 0.0) first_admit = j->info.t_admit;
-      }
-      const int rc = run(*j, slot);
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        in_use -= j->est;
-        --running;
-        j->info.t_done = now_s() - t0;
-        j->info.error = rc;
-        j->info.state = rc ? 3 : 2;
-        if (rc) std::snprintf(j->info.detail, sizeof(j->info.detail), "%s", gbsmps_last_error_detail());
-        if (rc) {
-          ++failed;
-        } else {
-          ++completed;
-          lat_ms.push_back(1e3 * (j->info.t_done - j->info.t_submit));
-          tensors += j->req.N;
-          samples += (double)j->req.samples;
+        // more admissible jobs ride along, up to batch_max: each admitted
+        // job's estimate is reserved before the next one is looked for, so
+        // a batch admits a job only while it still fits the budget
+        in_use += js[0]->est;
+        while ((int)js.size() < opts.batch_max) {
+          auto j = pick();
+          if (!j) break;
+          in_use += j->est;
+          js.push_back(j);
         }
-        last_done = std::max(last_done, j->info.t_done);
+        peak = std::max(peak, in_use);
+        for (auto& j : js) {
+          ++running;
+          j->info.state = 1;
+          j->info.slot = slot;
+          j->info.batch = (int32_t)js.size();
+          j->info.t_admit = now_s() - t0;
+          if (first_admit < 0.0) first_admit = j->info.t_admit;
+        }
       }
-      cv_done.notify_all();
-      cv_work.notify_all();
+      run(js, slot);
     }
   }
 };
@@ -153,12 +200,14 @@ int gbsmps_server_opts_default(gbsmps_server_opts* o) {
   o->slots = 4;
   o->hbm_budget = 0;
   o->simulate_s_per_tensor = 0.0;
+  o->batch_max = 1;
   return GBSMPS_OK;
 }
 
 int gbsmps_server_create(int device, const gbsmps_server_opts* o, gbsmps_server_t* out) {
   if (!o || !out) return GBSMPS_ERR_ARG;
   if (o->slots < 1 || o->slots > 64) return GBSMPS_ERR_ARG;
+  if (o->batch_max < 1 || o->batch_max > 64) return GBSMPS_ERR_ARG;
   auto srv = std::make_unique<gbsmps_server>();
   srv->device = device;
   srv->opts = *o;
@@ -208,6 +257,7 @@ int gbsmps_server_submit(gbsmps_server_t srv, const gbsmps_request* req, int64_t
   j->est = est;
   j->info.hbm_bytes = est;
   j->info.slot = -1;
+  j->info.batch = 0;
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return GBSMPS_ERR_STATE;

@@ -28,6 +28,75 @@ def ctx():
     c.close()
 
 
+def _freeze(w):
+    for f in (w.freeze, 1e-8, 1e-7):
+        cuts = G.gsvd_chain(w.gamma, lambda2_freeze=f)
+        if all(not np.any(np.abs((c.D - 1) / (c.D + 1) - f) <= 1e-14 + 1e-3 * f) for c in cuts[:-1]):
+            return f, cuts
+    raise AssertionError("no unambiguous freeze threshold")
+
+
+def test_prefix_64_modes_vs_oracle(ctx):
+    """The first 64 modes of the 1024-mode state (mixed precision) against the
+    FP64 oracle's own build of that prefix (GSVD chain over all cuts, kept
+    bases and PCO tensors of sites 1..64):
+    * the kept bases of bonds 1..64 are the same occupation vectors in the
+      same order, with the same entanglement energies;
+    * the tensors are equal entry by entry (1e-5 of the largest entry: the
+      FP32 PCO passes) at the sites whose two cuts have separated symplectic
+      spectra (there the canonical gauge fixes the Schmidt modes);
+    * prefix marginals P(n_1..n_64) = v R_65 v^dag, v = A^1[n_1]..A^64[n_64],
+      with R_65 = diag(e^{-E_beta}) (the paper's gauge, Eq. (SVD3): the right
+      environment of a cut is diagonal with the Schmidt weights), as ratios
+      to the all-vacuum prefix, agree within 1e-5 (gauge invariant up to
+      rotations among degenerate Schmidt modes, which leave R_65 unchanged)."""
+    w = wl.config("n1024_d4_chi512")
+    freeze, cuts = _freeze(w)
+    K = 64
+    bases = [M.vacuum_basis()] + [B.kept_basis(c.lam2, w.chi, w.eps) for c in cuts[:K]]
+    T = [P.local_tensor(cuts[m].Q, bases[m], bases[m + 1], w.d, cuts[m].c) for m in range(K)]
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=w.d, chi_max=w.chi, eps_trunc=w.eps,
+                       lambda2_freeze=freeze, precision=g.PREC_MIXED)
+    try:
+        for b in range(1, K + 1):
+            occ, E = g.gbsmps_get_basis(m.h, b)
+            assert np.array_equal(occ.astype(np.int64), bases[b].occ), b
+            assert np.allclose(E, bases[b].E, rtol=1e-9, atol=1e-12), b
+        G_T = [m.tensor(site) for site in range(K)]
+
+        def gap(c):
+            D = c.D
+            return min((D[q] - D[q + 1] for q in range(min(c.n_out, len(D) - 1))), default=np.inf)
+
+        sep = [s for s in range(1, K) if gap(cuts[s]) > 1e-5 and gap(cuts[s - 1]) > 1e-5]
+        assert len(sep) >= 5
+        terr = max(np.abs(G_T[s] - T[s]).max() / np.abs(T[s]).max() for s in sep)
+        pats = np.concatenate([wl.random_patterns(200, K, w.d, seed=31),
+                               wl.random_patterns(60, K, w.d, seed=32, even=False)])
+        pats[0] = 0
+        wE = np.exp(-bases[K].E)
+
+        def marg(TT):
+            out = []
+            for n in pats:
+                v = np.ones(1, dtype=np.complex128)
+                for site in range(K):
+                    v = v @ TT[site][:, int(n[site]), :]
+                out.append(float(np.sum(np.abs(v) ** 2 * wE)))
+            out = np.array(out)
+            return out / out[0]
+
+        r_o, r_g = marg(T), marg(G_T)
+        err = np.abs(r_g - r_o)
+        print("prefix: separated sites", sep, "tensor err", terr, "marginal ratio err (rel to max)",
+              err.max() / r_o.max(), "max rel where >= 1e-4 max",
+              (err / r_o)[r_o >= 1e-4 * r_o.max()].max())
+        assert terr <= 1e-5
+        assert np.all(err <= 1e-5 * r_o + 1e-8 * r_o.max())
+    finally:
+        m.release()
+
+
 def test_full_size_n1024(ctx):
     w = wl.config("n1024_d4_chi512")
     N, d, chi = w.N, w.d, w.chi

@@ -1,5 +1,6 @@
-"""Mixed-precision path (FP32 PCO build, split-BF16 tensor-core environments
-and sampling in the energy gauge, FP64 Gaussian SVD) against the FP64 oracle.
+"""Mixed-precision path (FP32 PCO passes with FP64 plane sums, double-float
+environments on the FP32 pipes in the energy gauge, split-FP16 tensor-core
+sampler in right-canonical form, FP64 Gaussian SVD) against the FP64 oracle.
 Tolerances: amplitude error <= 1e-5 relative (floor 1e-8 of the largest
 amplitude), fidelity >= 1 - 1e-8, samples bit-exact except draws flagged
 within 1e-5 Z of a CDF boundary."""
@@ -99,9 +100,9 @@ def test_mixed_vs_fp64_gpu_full_size(ctx):
 
 
 def test_tcgen05_gemm_matches_simt_reference(ctx, monkeypatch):
-    """The tcgen05/TMA sampler GEMM and a SIMT GEMM over the same packed bf16
-    planes draw the same samples from the same uniforms (only draws within
-    the mixed boundary window may differ)."""
+    """The tcgen05/TMA sampler GEMM and a SIMT GEMM over the same packed
+    split-FP16 planes draw the same samples from the same uniforms (only draws
+    within the mixed boundary window may differ)."""
     w = wl.small(20, 6, d=5, chi=96, depth=6, rlo=0.2, rhi=0.5)
     m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=5, chi_max=96, eps_trunc=1e-12,
                        lambda2_freeze=1e-9, precision=g.PREC_MIXED)

@@ -66,3 +66,31 @@ def test_failed_request_reports_and_server_continues():
         out, info = srv.wait(b, 120)
         assert info["state"] == 2 and out.shape == (100, 10)
         assert srv.stats()["failed"] == 1
+
+
+def test_batched_serving_within_tolerance():
+    """batch_max > 1: queued requests are built together in one batched call.
+    The batch sums the environment products in another order, so a result
+    equals the request run alone up to rounding: samples bit-exact except
+    draws that either side flags at a CDF boundary."""
+    reqs = _requests()
+    alone = []
+    with g.Context(0) as ctx:
+        for w, S, opts, seed in reqs:
+            m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **opts)
+            try:
+                f = np.zeros(S, dtype=np.uint8)
+                alone.append((m.sample(S, seed=seed, counter0=5, flags=f), f))
+            finally:
+                m.release()
+    with g.Server(0, slots=1, batch_max=8) as srv:
+        ids = [srv.submit(w.gamma, S, seed=seed, counter0=5, **opts) for w, S, opts, seed in reqs]
+        res = [srv.wait(i, timeout_s=300) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["hbm_in_use"] == 0
+    assert max(info["batch"] for _, info in res) >= 2           # batches formed
+    for (out, info), (ref, rf) in zip(res, alone):
+        ok = (info["flags"] == 0) & (rf == 0)
+        assert ok.mean() > 0.97
+        assert np.array_equal(out[ok], ref[ok])
+        assert np.all(out.astype(int).sum(1) % 2 == 0)

@@ -32,13 +32,16 @@ def test_trace_both_kernels(ctx):
             m.release()
         s = g.gbsmps_trace_read_kernel(ctx.h, 0)
         e = g.gbsmps_trace_read_kernel(ctx.h, 1)
+        p = g.gbsmps_trace_read_kernel(ctx.h, 2)
         assert s["launches"] == g.gbsmps_trace_read(ctx.h)["launches"]
         # two sampler launches per site (pre-pass and rest), two environment
-        # launches per site
+        # launches per site, one PCO launch for the whole state (24 sites:
+        # one wave of CTAs)
         assert s["launches"] == 2 * w.N and e["launches"] == 2 * w.N
+        assert p["launches"] == 1 and p["ms"] > 0
         for t in (s, e):
             assert t["ms"] > 0 and t["flops"] > 0 and t["bytes"] > 0
     finally:
         g.gbsmps_trace(ctx.h, False)
     with pytest.raises(g.GbsmpsError):
-        g.gbsmps_trace_read_kernel(ctx.h, 2)
+        g.gbsmps_trace_read_kernel(ctx.h, 3)

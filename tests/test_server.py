@@ -101,3 +101,23 @@ def test_latency_stats_nearest_rank():
     assert st["p50_ms"] == pytest.approx(lat[2], abs=1e-6)
     assert st["p99_ms"] == pytest.approx(lat[4], abs=1e-6)
     assert lat[4] > 4 * lat[0] * 0.8
+
+
+def test_batched_admission_groups_queued_jobs():
+    """With batch_max > 1 a slot that admits a job takes the admissible
+    queued jobs with it (one batched build), never more than batch_max, and
+    never beyond the memory budget; alone in the queue a job runs alone."""
+    budget = 5 * _est(40, 64)
+    with g.Server(slots=1, hbm_budget=budget, simulate_s_per_tensor=1e-3, batch_max=4) as s:
+        first = s.submit(None, 10, N=40, d=4, chi_max=64)
+        time.sleep(0.01)                         # the first one starts alone
+        ids = [s.submit(None, 10, N=40, d=4, chi_max=64) for _ in range(9)]
+        infos = [s.wait(i, timeout_s=60)[1] for i in [first] + ids]
+        st = s.stats()
+    assert infos[0]["batch"] == 1
+    sizes = [x["batch"] for x in infos[1:]]
+    assert max(sizes) == 4 and all(1 <= b <= 4 for b in sizes)
+    assert st["completed"] == 10 and st["hbm_peak"] <= budget and st["hbm_in_use"] == 0
+    assert sum(1 for b in sizes if b == 4) >= 4
+    with pytest.raises(g.GbsmpsError):
+        g.Server(slots=1, hbm_budget=budget, simulate_s_per_tensor=1e-3, batch_max=0)

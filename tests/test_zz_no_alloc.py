@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import basis as B
+from oracle import mps as M
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +30,10 @@ def _case(seed, nl, nr, chil, chir):
     n = nl + 1 + nr
     Q = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) * 0.35
     Q = 0.5 * (Q + Q.T)
-    bl = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nl))[::-1], chil)
-    br = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nr))[::-1], chir)
-    return Q, bl.occ.astype(np.uint8), br.occ.astype(np.uint8)
+    bl = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nl))[::-1], chil) if nl else M.vacuum_basis()
+    br = B.kept_basis(np.sort(r.uniform(0.05, 0.4, nr))[::-1], chir) if nr else M.vacuum_basis()
+    return (Q, bl.occ.astype(np.uint8).reshape(bl.D, nl),
+            br.occ.astype(np.uint8).reshape(br.D, nr))
 
 
 def test_no_alloc_matches_allocating_entry_twice(ctx):
@@ -46,6 +48,26 @@ def test_no_alloc_matches_allocating_entry_twice(ctx):
         out = torch.full((ol.shape[0], d, orr.shape[0], 2), float("nan"), dtype=torch.float64, device=dev)
         g.gbsmps_build_site_noalloc(ctx.h, Qd, c, torch.from_numpy(ol).to(dev),
                                     torch.from_numpy(orr).to(dev), d, out)
+        got = out.cpu().numpy().view(np.complex128)[..., 0]
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_no_alloc_boundary_sites_and_precisions(ctx, precision):
+    """A first site (no left modes: its occupation block is cleared in the
+    static array instead of repacked), a last site (no right modes) and a
+    middle site, in FP64 and in mixed precision (FP32 passes), each against
+    the allocating entry in the same precision, two calls in a row."""
+    import torch
+    dev = torch.device("cuda:0")
+    for seed, nl, nr, d, chil, chir, c in ((3, 0, 3, 6, 1, 70, 1.1), (4, 2, 0, 5, 50, 1, 0.9),
+                                           (5, 2, 2, 4, 30, 30, 1.0)):
+        Q, ol, orr = _case(seed, nl, nr, chil, chir)
+        ref = g.gbsmps_build_site(ctx.h, Q, c, ol, orr, d, precision=precision)
+        Qd = torch.from_numpy(np.ascontiguousarray(Q).view(np.float64).reshape(Q.shape + (2,))).to(dev)
+        out = torch.full((ol.shape[0], d, orr.shape[0], 2), float("nan"), dtype=torch.float64, device=dev)
+        g.gbsmps_build_site_noalloc(ctx.h, Qd, c, torch.from_numpy(ol).to(dev),
+                                    torch.from_numpy(orr).to(dev), d, out, precision=precision)
         got = out.cpu().numpy().view(np.complex128)[..., 0]
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
