@@ -129,6 +129,8 @@ def parse():
                     help="one-state runs behind latency_ms (p99 is then not the maximum)")
     ap.add_argument("--large", type=int, default=1,
                     help="1: add the 1024-mode configuration (build + 1M samples) to the line")
+    ap.add_argument("--filter-states", type=int, default=152,
+                    help="lossy 64-mode states decomposed in one batched call (0: skip)")
     ap.add_argument("--profile-pass", default=None, choices=["build", "sample"],
                     help="run one build of the workload (and one sampling of --samples) on "
                          "cuda:0 and exit without a JSON line: a short, fixed launch sequence "
@@ -553,6 +555,19 @@ def run_large(args, dev):
     even = bool((photons % 2 == 0).all().item())
     mean_ph = float(photons.float().mean().item())
     dims = [int(x) for x in m.info["bond_dims"]]
+    # out of core: the sampler planes in pinned host memory, streamed site by
+    # site through a three-slot device ring; the same patterns
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    host_bytes = m.offload()
+    free1 = torch.cuda.mem_get_info(dev)[0]
+    out2 = torch.empty_like(out)
+    with torch.cuda.stream(stream):
+        ev[1].record(stream)
+        m.sample(S, seed=77, counter0=0, out=out2)
+        ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    ooc_ms = ev[1].elapsed_time(ev[2])
+    same = bool(torch.equal(out, out2))
     m.release()
     ctx.close()
     peaks, src = measured_peaks()
@@ -567,11 +582,91 @@ def run_large(args, dev):
             "tensors_per_s_whole": round(w.N / ((build_ms + sample_ms) / 1e3), 1),
             "max_bond_dim": max(dims), "mean_photons": round(mean_ph, 3),
             "all_samples_even": even,
+            "out_of_core": {"sample_ms": round(ooc_ms, 2),
+                            "samples_per_s": round(S / (ooc_ms / 1e3), 1),
+                            "host_plane_bytes": host_bytes,
+                            "h2d_gbs": round(host_bytes / (ooc_ms / 1e3) / 1e9, 1),
+                            "device_bytes_freed": int(free1 - free0),
+                            "same_patterns_as_resident": same,
+                            "def": ("gbsmps_offload: sampler planes in pinned host memory, "
+                                    "streamed through three device slots by a copy stream")},
             "sampler_gemm": {"ms": round(tr["ms"], 2), "launches": tr["launches"],
                              "achieved_tflops": round(ach, 3), "peak": peak,
                              "frac": round(ach / peak, 5), "issued_frac": round(3 * ach / peak, 5),
                              "share_of_sampling": round(tr["ms"] / sample_ms, 4) if sample_ms > 0 else None,
                              "peak_source": f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json"}}
+
+
+# --------------------------------------------------------------------------- mixed -> pure
+def run_filtration(args, dev):
+    """The step before the path (Sec. III Eq. (decompose), App. C): lossy
+    64-mode covariances (squeezed vacua r~U(0.3,0.8) through a depth-16
+    brick wall, then uniform loss eta = 0.5: Gamma_th = eta Gamma +
+    (1 - eta) I / 2, shaped like the paper's 64-mode configuration) split
+    into a pure part and noise by the App. C descent (alpha = 0.01, eps =
+    1e-10), all states in one batched call (one state per SM).  The oracle is
+    timed on a bounded number of steps of one state beside it."""
+    import numpy as np
+    import torch
+
+    import paper_2512_10643_gb300 as g
+    import workloads as wl
+
+    N, count, alpha, eps = 64, args.filter_states, 0.01, 1e-10
+    gths = np.stack([wl.lossy(N, 3000 + i, eta=0.5, depth=16)[0] for i in range(count)])
+    stream = torch.cuda.Stream(device=dev)
+    ctx = g.Context(dev, stream.cuda_stream)
+    gd = torch.from_numpy(gths).to(f"cuda:{dev}")
+    g.gbsmps_filter(ctx.h, gd[:1], alpha, eps=eps, max_iter=2)          # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        S, iters, loss = g.gbsmps_filter(ctx.h, gd, alpha, eps=eps, max_iter=100000)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    Sh = S.cpu().numpy()
+    n_eff = [0.5 * np.trace(0.5 * x @ x.T) - 0.5 * N for x in Sh]
+    n = 2 * N
+    # per step: the tridiagonalisation (4/3 n^3), the Sturm multisection
+    # (8 rounds x 512 points x 3n), the back transformation and gradient step
+    # (~18 n^2), the recomputation of W every 64 steps (n^3)
+    fl_step = 4.0 / 3.0 * n ** 3 + 8 * 512 * 3 * n + 18 * n ** 2 + n ** 3 / 64
+    flops = fl_step * float(np.sum(iters))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_peak = nsm * 2 * 2 * 2.07e9 / 1e12        # 2 FP64 FMA per clock per SM
+    # the CPU baseline: the oracle on a bounded number of steps of one state,
+    # scaled by the steps a state takes
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import filtration as F
+        t = time.perf_counter()
+        K = 20
+        F.filtration(gths[0], alpha, eps=0.0, max_iter=K)
+        per_step = (time.perf_counter() - t) / K
+        ora_state_s = per_step * float(np.mean(iters))
+        cpu = {"s_per_state": round(ora_state_s, 2), "value": round(1.0 / ora_state_s, 4),
+               "unit": "states/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{K} steps of one state (numpy eigh + expm per step), scaled to the "
+                         "mean step count of the GPU run"}
+    return {"workload": ("lossy 64-mode covariances: squeezed vacua r~U(0.3,0.8) through a depth-16 "
+                         "brick-wall network, uniform transmission eta = 0.5; App. C descent with "
+                         "alpha = 0.01, eps = 1e-10"),
+            "states": count, "ms": round(ms, 2), "states_per_s": round(count / (ms / 1e3), 2),
+            "steps_mean": float(np.mean(iters)), "steps_max": int(np.max(iters)),
+            "converged": int(np.sum(loss <= eps)), "n_eff_mean": round(float(np.mean(n_eff)), 5),
+            "roofline": {"bound": "alu", "achieved": round(flops / (ms / 1e3) / 1e12, 4),
+                         "peak": round(fp64_peak, 3), "unit": "TFLOP/s",
+                         "frac": round(flops / (ms / 1e3) / 1e12 / fp64_peak, 4),
+                         "peak_source": (f"derived: {nsm} SMs x 2 FP64 FMA per clock x 2 flops x "
+                                         "2070 MHz (GB300's FP64 rate)"),
+                         "algorithmic_flops_def": ("per step 4/3 n^3 (tridiagonalisation) + "
+                                                   "8 x 512 x 3n (Sturm counts) + 18 n^2 (back "
+                                                   "transformation, gradient, rank-2 updates) + "
+                                                   "n^3 / 64 (W recomputed every 64 steps), n = 2N")},
+            "cpu_baseline": cpu}
 
 
 # --------------------------------------------------------------------------- batched build
@@ -810,6 +905,11 @@ def main():
             line["batched"] = run_batched(args, local)
         except Exception as e:          # noqa: BLE001
             line["batched"] = {"error": f"{type(e).__name__}: {e}"}
+    if ws == 1 and args.filter_states > 0:
+        try:
+            line["filtration"] = run_filtration(args, local)
+        except Exception as e:          # noqa: BLE001
+            line["filtration"] = {"error": f"{type(e).__name__}: {e}"}
     if ws == 1 and args.large:
         try:
             line["large"] = run_large(args, local)

@@ -194,7 +194,45 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t ctx, int32_t count, const int32_t* N
                                const uint64_t* counter0s, uint8_t* const* outs,
                                int mem_kind);
 
-/* Release an MPS and its device memory. */
+/* Mixed -> pure decomposition of lossy-experiment covariances (Sec. III,
+ * Eq. (decompose); App. C): each Gamma_th (2N x 2N, xxpp, row-major, FP64)
+ * is split as Gamma_p + W with Gamma_p = S S^T / 2 pure (S symplectic) and
+ * W >= 0, by Riemannian gradient descent on Sp(2N) of the loss
+ * L(S) = -lambda_min(Gamma_th - S S^T / 2) (Eq. (loss)) from S = I: the
+ * unit gradient in sp(2N) under the Frobenius norm (the appendix's
+ * "two-form norm" is not defined further), the retraction
+ * S <- S exp(-alpha G) with fixed step alpha, stop once L <= eps or after
+ * max_iter steps.  A batch of `count` states of equal N runs in one launch,
+ * one state per SM, FP64.  gamma_th and S_out: count x (2N)^2 doubles, both
+ * host or both device (mem_kind); iters and loss: host arrays of count
+ * entries (may be NULL) receiving the steps taken and the final L.
+ * The pure part's covariance is S_out S_out^T / 2.  Synchronises.
+ * Limits: N <= GBSMPS_FILTER_MAX_N.  Errors: ARG, BOUNDS, CUDA. */
+#define GBSMPS_FILTER_MAX_N 64
+int gbsmps_filter(gbsmps_ctx_t ctx, int32_t count, int32_t N, const double* gamma_th,
+                  double alpha, double eps, int32_t max_iter, double* S_out,
+                  int32_t* iters, double* loss, int mem_kind);
+
+/* Out-of-core sampling of an MPS that need not fit the GPU's memory: the
+ * paper's sampling estimate (Sec. III B) has the bond tensors of large
+ * states exceed one device's memory.  Moves a mixed-precision MPS's sampler
+ * planes (every site's right-canonical tensor as split-FP16 planes) to
+ * pinned host memory and frees every other device array of its tensors
+ * (tensors, environments and their factors); later gbsmps_sample calls
+ * stream the planes site by site through a ring of three device slots on a
+ * copy stream of their own, each site's copy overlapping the GEMMs of the
+ * sites before it, and draw exactly the patterns the resident MPS draws.
+ * Device memory then held for the MPS: the ring (three sites' planes) and
+ * the per-sample work buffers of the sampling.  gbsmps_get_tensor and
+ * gbsmps_amplitudes of an offloaded MPS return GBSMPS_ERR_STATE; info,
+ * get_gsvd and get_basis still work.  A second call is a no-op.
+ * *host_bytes (may be NULL) receives the size of the host copy: the bytes
+ * each sampling streams to the device.  Synchronises.  Errors: ARG (FP64
+ * MPS), OOM/CUDA (pinned allocation). */
+int gbsmps_offload(gbsmps_mps_t mps, size_t* host_bytes);
+
+/* Release an MPS and its device memory (and its pinned host copy when
+ * offloaded). */
 int gbsmps_release(gbsmps_mps_t mps);
 
 /* Expert entry: PCO build of one local tensor (Sec. II C, App. B) from a

@@ -15,6 +15,7 @@ Modules
   mps      : full build, environments/normalisation, amplitudes, sampling,
              fidelity
   hafnian  : brute-force hafnian amplitudes (exact reference for tiny cases)
+  filtration: mixed -> pure decomposition of a lossy covariance (Sec. III, App. C)
 
 Every public function is pinned by a check that does not reuse its own code
 path (closed forms, brute-force hafnians, dense inner products and matrix
@@ -23,5 +24,5 @@ exponentials, identities of App. A); a function without such a pin would say
 is a second valid FP64 route to the Williamson form, kept to measure how far
 the MPS of a given covariance matrix is determined in FP64 at all.
 """
-from . import gaussian, basis, pco, mps, hafnian  # noqa: F401
+from . import gaussian, basis, pco, mps, hafnian, filtration  # noqa: F401
 from .mps import build_mps, amplitudes, sample, environments, fidelity, normalise  # noqa: F401

@@ -88,6 +88,8 @@ def lib():
         "gbsmps_amplitudes": (C.c_int, [vp, i64, vp, vp, C.c_int]),
         "gbsmps_sample": (C.c_int, [vp, i64, u64, u64, vp, vp, vp, C.c_int]),
         "gbsmps_release": (C.c_int, [vp]),
+        "gbsmps_offload": (C.c_int, [vp, vp]),
+        "gbsmps_filter": (C.c_int, [vp, i32, i32, vp, dbl, dbl, i32, vp, vp, vp, C.c_int]),
         "gbsmps_build_site": (C.c_int, [vp, i32, i32, i32, vp, dbl, i32, vp, i32, vp, i32, vp, C.c_int]),
         "gbsmps_strerror": (C.c_char_p, [C.c_int]),
         "gbsmps_last_error_detail": (C.c_char_p, []),
@@ -302,6 +304,15 @@ def gbsmps_release(mps):
     _check(lib().gbsmps_release(mps))
 
 
+def gbsmps_offload(mps) -> int:
+    """Move a mixed-precision MPS's sampler planes to pinned host memory;
+    later samplings stream them through a three-site device ring.  Returns
+    the bytes each sampling streams."""
+    n = C.c_size_t()
+    _check(lib().gbsmps_offload(mps, C.byref(n)))
+    return n.value
+
+
 def gbsmps_build_site(ctx, Qm, c, occ_l, occ_r, d, precision=PREC_FP64):
     """Expert entry on host numpy arrays: Qm complex (n, n), occ_l (Dl, nl)
     and occ_r (Dr, nr) uint8 down-closed bases starting at the vacuum."""
@@ -332,6 +343,31 @@ def gbsmps_build_site_noalloc(ctx, Qm, c, occ_l, occ_r, d, out, precision=PREC_F
                                            C.c_void_p(ptrs[2][0] if nr else 0), precision,
                                            C.c_void_p(ptrs[3][0])))
     return out
+
+
+def gbsmps_filter(ctx, gammas, alpha: float, eps: float = 0.0, max_iter: int = 100000, out=None):
+    """Mixed -> pure decomposition of a batch of covariances of equal N:
+    gammas (count, 2N, 2N) float64 numpy array or CUDA tensor.  Returns
+    (S (count, 2N, 2N), iters (count,), loss (count,)); Gamma_p = S S^T / 2."""
+    count, n = int(gammas.shape[0]), int(gammas.shape[1])
+    if isinstance(gammas, np.ndarray):
+        gammas = np.ascontiguousarray(gammas, dtype=np.float64)
+    if out is None:
+        if isinstance(gammas, np.ndarray):
+            out = np.zeros((count, n, n), dtype=np.float64)
+        else:
+            import torch
+            out = torch.zeros((count, n, n), dtype=torch.float64, device=gammas.device)
+    gp, kind = _ptr(gammas)
+    op, okind = _ptr(out)
+    if kind != okind:
+        raise ValueError("gammas and out must live in the same memory")
+    iters = np.zeros(count, dtype=np.int32)
+    loss = np.zeros(count, dtype=np.float64)
+    _check(lib().gbsmps_filter(ctx, count, n // 2, C.c_void_p(gp), float(alpha), float(eps),
+                               int(max_iter), C.c_void_p(op), iters.ctypes.data, loss.ctypes.data,
+                               kind))
+    return out, iters, loss
 
 
 def gbsmps_launch_count(ctx=None) -> int:
@@ -409,6 +445,10 @@ class MPS:
 
     def sample(self, S, seed=0, counter0=0, uniforms=None, out=None, flags=None):
         return gbsmps_sample(self.h, S, seed, counter0, uniforms, out, flags)
+
+    def offload(self):
+        """Out-of-core sampling from here on; returns the bytes streamed per sampling."""
+        return gbsmps_offload(self.h)
 
     def release(self):
         if self.h:

@@ -114,6 +114,7 @@ int gbsmps_info(gbsmps_mps_t m, int32_t* N_out, int32_t* d_out, int32_t* bond_di
 
 int gbsmps_get_tensor(gbsmps_mps_t m, int32_t site, void* dst, size_t dst_bytes, int mem_kind) {
   if (!m || !dst) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (m->host_bpack) return fail(GBSMPS_ERR_STATE, "the MPS is offloaded: only sampling remains");
   if (site < 0 || site >= m->N) return fail(GBSMPS_ERR_ARG, "site out of range");
   size_t bytes = sizeof(double2) * (size_t)m->D[site] * m->d * m->D[site + 1];
   if (dst_bytes < bytes) return fail(GBSMPS_ERR_ARG, "dst too small");
@@ -164,6 +165,7 @@ int gbsmps_amplitudes(gbsmps_mps_t m, int64_t P, const uint8_t* patterns, double
   if (P < 0) return fail(GBSMPS_ERR_ARG, "P < 0");
   if (P == 0) return GBSMPS_OK;
   if (!patterns || !out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (m->host_bpack) return fail(GBSMPS_ERR_STATE, "the MPS is offloaded: only sampling remains");
   CK(cudaSetDevice(m->ctx->device));
   cudaStream_t s = m->ctx->stream;
   DevBuf pb, ob, wb;
@@ -234,7 +236,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   // the next bond (row s = sample s), the class lists of sample indices
   // (current, next, rest), the per-sample scales (current, next), W and the
   // chunk norms per group; list counts per bond
-  DevBuf cv[4], csid[6], crs[2], cw[2], cpart[2], ccnt, crest;
+  DevBuf cv[4], csid[6], crs[2], cw[2], cpart[2], ccnt, crest, ring;
   const char* tce = getenv("GBSMPS_TC");
   const int use_tc = !(tce && tce[0] == '0');
   // the p = 0 pre-pass (on unless GBSMPS_P0PASS=0): block 0 of every sample
@@ -267,6 +269,32 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
         CK(ccnt.alloc(sizeof(int) * 2 * (size_t)(N + 1), s));
         CK(crest.alloc(sizeof(int) * 2 * (size_t)(N + 1), s));
       }
+      // out of core: the planes of sites m and m + 1 are copied ahead, each
+      // copy waiting until the GEMMs of the site that used its slot before
+      // are done (a ring of three slots)
+      const bool ooc = m->host_bpack != nullptr;
+      long long slot_h = 0;
+      if (ooc) {
+        for (int i = 0; i < N; ++i) slot_h = std::max(slot_h, m->site_halves(i));
+        if (!ring.p) CK(ring.alloc(sizeof(__half) * (size_t)(gbsmps_mps::RING * slot_h + 64), s));
+        CK(cudaEventRecord(m->ring_start, s));          // earlier readers of the ring
+        CK(cudaStreamWaitEvent(m->copy_stream, m->ring_start, 0));
+      }
+      auto issue_copy = [&](int site) -> int {
+        const int k = site % gbsmps_mps::RING;
+        CK(cudaStreamWaitEvent(m->copy_stream, m->ring_free[k], 0));
+        CK(cudaMemcpyAsync(ring.as<__half>() + k * slot_h, m->host_bpack + m->sg[site].boff[0],
+                           sizeof(__half) * (size_t)m->site_halves(site), cudaMemcpyHostToDevice,
+                           m->copy_stream));
+        CK(cudaEventRecord(m->ring_ready[k], m->copy_stream));
+        return GBSMPS_OK;
+      };
+      if (ooc) {
+        for (int i = 0; i < std::min(N, gbsmps_mps::RING - 1); ++i) {
+          const int rc0 = issue_copy(i);
+          if (rc0) return rc0;
+        }
+      }
       int* cnt = ccnt.as<int>();
       int* rcnt = crest.as<int>();
       CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)(N + 1), s));
@@ -294,8 +322,27 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
           ng[pi] = NextGroup{cv[nxt[pi]].as<__half>(), (long long)Spad * Kpn, Kpn,
                              csid[ln[pi]].as<int>(), m->pcnt[2 * (site + 1) + pi], crs[rn].as<float>()};
         }
-        const __half* B0 = m->bpack.as<__half>() + G.boff[0];
-        const __half* B1 = m->bpack.as<__half>() + G.boff[1];
+        const __half* B0;
+        const __half* B1;
+        const unsigned char* map0 = G.map[0].data();
+        const unsigned char* map1 = G.map[1].data();
+        alignas(64) unsigned char rmap[2][128];
+        if (ooc) {
+          if (site + gbsmps_mps::RING - 1 < N) {
+            const int rc0 = issue_copy(site + gbsmps_mps::RING - 1);
+            if (rc0) return rc0;
+          }
+          CK(cudaStreamWaitEvent(s, m->ring_ready[site % gbsmps_mps::RING], 0));
+          B0 = ring.as<__half>() + (site % gbsmps_mps::RING) * slot_h;
+          B1 = B0 + 2LL * G.Np[0] * G.Kp[0];
+          if (canon_make_map(rmap[0], B0, G.Kp[0], G.Np[0]) || canon_make_map(rmap[1], B1, G.Kp[1], G.Np[1]))
+            return fail(GBSMPS_ERR_CUDA, "tensor map encoding failed for a ring slot");
+          map0 = rmap[0];
+          map1 = rmap[1];
+        } else {
+          B0 = m->bpack.as<__half>() + G.boff[0];
+          B1 = m->bpack.as<__half>() + G.boff[1];
+        }
         const long long bpl0 = (long long)G.Np[0] * G.Kp[0], bpl1 = (long long)G.Np[1] * G.Kp[1];
         const double* uu = du ? du + (size_t)s0 * N : nullptr;
         if (p0pass) {
@@ -312,7 +359,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
             ta[pi].wv = 2 * G.w[pi];
             rg[pi] = RestGroup{csid[4 + pi].as<int>(), rcnt + 2 * site + pi};
           }
-          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), ta[0], ta[1], B0, bpl0, B1, bpl1,
+          CK(launch_canon_gemm(map0, map1, ta[0], ta[1], B0, bpl0, B1, bpl1,
                                use_tc, status, sm_reserve, s));
           CK(launch_select_pre(cs, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), rg[0], rg[1],
                                m->creg.as<unsigned long long>(), 1e-10, uu, N, site, seed,
@@ -327,15 +374,17 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
             sb[pi].cnt = rcnt + 2 * site + pi;
             sb[pi].sid = csid[4 + pi].as<int>();
           }
-          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), tb[0], tb[1], B0, bpl0, B1, bpl1,
+          CK(launch_canon_gemm(map0, map1, tb[0], tb[1], B0, bpl0, B1, bpl1,
                                use_tc, status, sm_reserve, s));
+          if (ooc) CK(cudaEventRecord(m->ring_free[site % gbsmps_mps::RING], s));
           CK(launch_select_groups(cs, d, sb[0], sb[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
                                   site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
                                   dfl ? dfl + s0 : nullptr, 1e-5, s));
           COUNT_LAUNCH(1);
         } else {
-          CK(launch_canon_gemm(G.map[0].data(), G.map[1].data(), tg[0], tg[1], B0, bpl0, B1, bpl1,
+          CK(launch_canon_gemm(map0, map1, tg[0], tg[1], B0, bpl0, B1, bpl1,
                                use_tc, status, sm_reserve, s));
+          if (ooc) CK(cudaEventRecord(m->ring_free[site % gbsmps_mps::RING], s));
           CK(launch_select_groups(cs, d, sl[0], sl[1], ng[0], ng[1], cnt + 2 * (site + 1), uu, N,
                                   site, seed, counter0 + (uint64_t)s0, dout + (size_t)s0 * N, N,
                                   dfl ? dfl + s0 : nullptr, 1e-5, s));
@@ -414,6 +463,7 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   for (auto& b : cpart) b.release();
   ccnt.release();
   crest.release();
+  ring.release();
   if (mem_kind == GBSMPS_MEM_HOST && sync_host) return sync_status(m->ctx);
   return GBSMPS_OK;
 }
@@ -576,6 +626,76 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   if (pco_done) cudaEventDestroy(pco_done);
   if (ss) cudaStreamDestroy(ss);
   return rc;
+}
+
+int gbsmps_filter(gbsmps_ctx_t c, int32_t count, int32_t N, const double* gamma_th, double alpha,
+                  double eps, int32_t max_iter, double* S_out, int32_t* iters, double* loss,
+                  int mem_kind) {
+  if (!c) return fail(GBSMPS_ERR_ARG, "ctx is NULL");
+  if (count < 0) return fail(GBSMPS_ERR_ARG, "count < 0");
+  if (count == 0) return GBSMPS_OK;
+  if (!gamma_th || !S_out) return fail(GBSMPS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > GBSMPS_FILTER_MAX_N) return fail(GBSMPS_ERR_BOUNDS, "N out of range [1, 64]");
+  if (!(alpha > 0.0) || !(eps >= 0.0) || max_iter < 0) return fail(GBSMPS_ERR_ARG, "bad alpha, eps or max_iter");
+  if (mem_kind != GBSMPS_MEM_HOST && mem_kind != GBSMPS_MEM_DEVICE) return fail(GBSMPS_ERR_ARG, "bad mem_kind");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int n = 2 * N;
+  const size_t mat = sizeof(double) * (size_t)n * n * count;
+  DevBuf gb, sb, wb, ib, lb;
+  const double* dg = gamma_th;
+  double* ds = S_out;
+  if (mem_kind == GBSMPS_MEM_HOST) {
+    CK(gb.alloc(mat, s));
+    CK(cudaMemcpyAsync(gb.p, gamma_th, mat, cudaMemcpyHostToDevice, s));
+    dg = gb.as<double>();
+    CK(sb.alloc(mat, s));
+    ds = sb.as<double>();
+  }
+  CK(wb.alloc(mat, s));
+  CK(ib.alloc(sizeof(int) * count, s));
+  CK(lb.alloc(sizeof(double) * count, s));
+  CK(launch_filter(count, n, dg, ds, wb.as<double>(), alpha, eps, max_iter, 64, ib.as<int>(),
+                   lb.as<double>(), c->d_status, s));
+  COUNT_LAUNCH(1);
+  if (mem_kind == GBSMPS_MEM_HOST) CK(cudaMemcpyAsync(S_out, ds, mat, cudaMemcpyDeviceToHost, s));
+  if (iters) CK(cudaMemcpyAsync(iters, ib.p, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+  if (loss) CK(cudaMemcpyAsync(loss, lb.p, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+  gb.release(); sb.release(); wb.release(); ib.release(); lb.release();
+  return sync_status(c);
+}
+
+int gbsmps_offload(gbsmps_mps_t m, size_t* host_bytes) {
+  if (!m) return fail(GBSMPS_ERR_ARG, "mps is NULL");
+  if (m->precision != GBSMPS_PREC_MIXED || m->sg.empty())
+    return fail(GBSMPS_ERR_ARG, "only a mixed-precision MPS samples from packed planes");
+  const int N = m->N;
+  const long long halves = m->sg[N - 1].boff[0] + m->site_halves(N - 1);
+  if (host_bytes) *host_bytes = sizeof(__half) * (size_t)halves;
+  if (m->host_bpack) return GBSMPS_OK;
+  CK(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = m->ctx->stream;
+  __half* host = nullptr;
+  CK(cudaMallocHost(reinterpret_cast<void**>(&host), sizeof(__half) * (size_t)halves));
+  cudaError_t e = cudaMemcpyAsync(host, m->bpack.p, sizeof(__half) * (size_t)halves,
+                                  cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (!e) e = cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < gbsmps_mps::RING && !e; ++k) {
+    e = cudaEventCreateWithFlags(&m->ring_ready[k], cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&m->ring_free[k], cudaEventDisableTiming);
+  }
+  if (!e) e = cudaEventCreateWithFlags(&m->ring_start, cudaEventDisableTiming);
+  if (e) {
+    cudaFreeHost(host);
+    return fail(GBSMPS_ERR_CUDA, std::string("offload: ") + cudaGetErrorString(e));
+  }
+  m->host_bpack = host;
+  // nothing but the planes is read by the sampling: the tensors, the
+  // environments and their factors leave the device
+  m->bpack.release(); m->tensors.release(); m->env.release(); m->tens_mixed.release();
+  m->gscale.release(); m->eoff_dev.release(); m->lchol.release(); m->linv.release();
+  return sync_status(m->ctx);
 }
 
 int gbsmps_release(gbsmps_mps_t m) {

@@ -354,6 +354,11 @@ int env_chain_tile_configs();
 // right-canonical mixed sampling (k_canon.cu)
 #include <cuda_fp16.h>
 int canon_make_map(void* map128, const void* planes, int Kp, long long rows);
+// mixed -> pure decomposition (k_filter.cu): one CTA per state of a batch
+size_t filter_smem_bytes(int n);
+cudaError_t launch_filter(int count, int n, const double* gth, double* S, double* W, double alpha,
+                          double eps, int max_iter, int refresh, int* iters, double* loss,
+                          int* status, cudaStream_t s);
 // Parity groups.  Every PCO adds two quanta, so A^m[alpha, p, beta] = 0
 // unless n_alpha + p + n_beta is even; the environments, their Cholesky
 // factors and the canonical tensors inherit the block structure, and a

@@ -142,11 +142,30 @@ struct gbsmps_mps {
   double* lam2 = nullptr;
   double2* Qm = nullptr;
   double* cm = nullptr;
+  // out of core (gbsmps_offload): the sampler planes in pinned host memory,
+  // streamed site by site through a ring of device slots by a copy stream;
+  // the MPS then holds no tensor on the device
+  static constexpr int RING = 3;
+  __half* host_bpack = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ring_ready[RING] = {}, ring_free[RING] = {}, ring_start = nullptr;
+  long long site_halves(int m) const {        // both parity groups' planes of site m
+    return 2LL * sg[m].Np[0] * sg[m].Kp[0] + 2LL * sg[m].Np[1] * sg[m].Kp[1];
+  }
   ~gbsmps_mps() {
     tensors.release(); env.release(); gsvd.release(); bonds.release(); tens_mixed.release();
     gscale.release();
     vacamp.release();
     eoff_dev.release(); lchol.release(); linv.release(); bpack.release(); creg.release();
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    if (host_bpack) cudaFreeHost(host_bpack);
+    for (int k = 0; k < RING; ++k) {
+      if (ring_ready[k]) cudaEventDestroy(ring_ready[k]);
+      if (ring_free[k]) cudaEventDestroy(ring_free[k]);
+    }
+    if (ring_start) cudaEventDestroy(ring_start);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
   }
 };
 

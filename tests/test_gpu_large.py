@@ -61,7 +61,10 @@ def test_prefix_64_modes_vs_oracle(ctx):
         for b in range(1, K + 1):
             occ, E = g.gbsmps_get_basis(m.h, b)
             assert np.array_equal(occ.astype(np.int64), bases[b].occ), b
-            assert np.allclose(E, bases[b].E, rtol=1e-9, atol=1e-12), b
+            # E = sum_q n_q (-ln Lambda_q^2): a mode kept just above the freeze
+            # threshold has Lambda^2 ~ 1e-9 known to ~1e-13 absolute, so its
+            # -ln Lambda^2 only to ~1e-4
+            assert np.allclose(E, bases[b].E, rtol=1e-9, atol=1e-3), b
         G_T = [m.tensor(site) for site in range(K)]
 
         def gap(c):
@@ -71,9 +74,18 @@ def test_prefix_64_modes_vs_oracle(ctx):
         sep = [s for s in range(1, K) if gap(cuts[s]) > 1e-5 and gap(cuts[s - 1]) > 1e-5]
         assert len(sep) >= 5
         terr = max(np.abs(G_T[s] - T[s]).max() / np.abs(T[s]).max() for s in sep)
-        pats = np.concatenate([wl.random_patterns(200, K, w.d, seed=31),
-                               wl.random_patterns(60, K, w.d, seed=32, even=False)])
-        pats[0] = 0
+        # few-photon prefixes: one or two photon pairs, each on a mode and a
+        # neighbour within three modes (squeezing makes photons in pairs of
+        # nearby modes here), so most marginals lie within a few decades of
+        # the vacuum's
+        rs = np.random.default_rng(31)
+        pats = np.zeros((260, K), dtype=np.uint8)
+        for row in pats[1:]:
+            for _ in range(int(rs.integers(1, 3))):
+                j = int(rs.integers(0, K - 4))
+                k = j + int(rs.integers(0, 4))
+                row[j] = min(row[j] + 1, w.d - 1)
+                row[k] = min(row[k] + 1, w.d - 1)
         wE = np.exp(-bases[K].E)
 
         def marg(TT):
@@ -88,9 +100,11 @@ def test_prefix_64_modes_vs_oracle(ctx):
 
         r_o, r_g = marg(T), marg(G_T)
         err = np.abs(r_g - r_o)
+        big = r_o >= 1e-4 * r_o.max()
         print("prefix: separated sites", sep, "tensor err", terr, "marginal ratio err (rel to max)",
-              err.max() / r_o.max(), "max rel where >= 1e-4 max",
-              (err / r_o)[r_o >= 1e-4 * r_o.max()].max())
+              err.max() / r_o.max(), "max rel where >= 1e-4 max", (err / r_o)[big].max(),
+              "patterns there", int(big.sum()))
+        assert big.sum() >= 80
         assert terr <= 1e-5
         assert np.all(err <= 1e-5 * r_o + 1e-8 * r_o.max())
     finally:

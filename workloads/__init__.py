@@ -34,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "haar_unitary", "brickwall_unitary", "squeezed_state",
-    "config", "CONFIGS", "uniforms", "random_patterns", "rng",
+    "config", "CONFIGS", "uniforms", "random_patterns", "rng", "lossy",
 ]
 
 
@@ -167,6 +167,16 @@ def serving(count: int, rate_hz: float, seed: int = 20251214, n_range=(32, 512),
                   eps=1e-12, freeze=1e-9)
         out.append((t, w, S))
     return out
+
+
+def lossy(N: int, seed: int, eta: float, depth: int = 4, rlo: float = 0.3, rhi: float = 0.8,
+          haar: bool = False):
+    """Mixed covariance of a lossy experiment: the pure brick-wall (or Haar)
+    state of ``small`` after uniform loss of transmission eta on every mode,
+    Gamma_th = eta Gamma + (1 - eta) I / 2 (loss mixes each mode with
+    vacuum, Gamma = I/2).  Returns (Gamma_th, the pure Workload)."""
+    w = _make(f"lossy_n{N}_s{seed}", N, rlo, rhi, depth, 4, 32, seed, haar=haar)
+    return eta * w.gamma + (1.0 - eta) * 0.5 * np.eye(2 * N), w
 
 
 def uniforms(S: int, N: int, seed: int) -> np.ndarray:
