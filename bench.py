@@ -40,7 +40,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69032.0 + 37278.6) MB over 1152 la
 ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.01e6       # (7214.2 + 0.1) MB over 1440 launches
 # the PCO build's DRAM bytes per launch (one launch per 144-mode build); None
 # until a capture of the current kernel is taken
-PCO_TRAFFIC_BYTES_PER_LAUNCH = None
+PCO_TRAFFIC_BYTES_PER_LAUNCH = 3.7256e9     # (1561.573 + 2164.040) MB, one launch per build
 # A double-float multiply-add (2 flops of the FP64 algorithm) costs 12 FP32
 # instructions: the exact product by FMA (4, with the low words) and Knuth's
 # TwoSum into the (hi, lo) accumulator (6) plus the low-word update (2)
@@ -131,7 +131,7 @@ def parse():
                     help="1: add the 1024-mode configuration (build + 1M samples) to the line")
     ap.add_argument("--filter-states", type=int, default=152,
                     help="lossy 64-mode states decomposed in one batched call (0: skip)")
-    ap.add_argument("--profile-pass", default=None, choices=["build", "sample"],
+    ap.add_argument("--profile-pass", default=None, choices=["build", "sample", "filter"],
                     help="run one build of the workload (and one sampling of --samples) on "
                          "cuda:0 and exit without a JSON line: a short, fixed launch sequence "
                          "for profiler captures")
@@ -826,6 +826,14 @@ def profile_pass(args):
     import paper_2512_10643_gb300 as g
     import workloads as wl
 
+    if args.profile_pass == "filter":
+        # eight lossy 64-mode states, 20 steps of the App. C descent
+        gths = np.stack([wl.lossy(64, 3000 + i, eta=0.5, depth=16)[0] for i in range(8)])
+        ctx = g.Context(0)
+        S, it, loss = g.gbsmps_filter(ctx.h, gths, 0.01, eps=1e-10, max_iter=20)
+        ctx.close()
+        print("steps", int(it.sum()), "loss", float(loss.max()))
+        return
     w = wl.config(WORKLOAD)
     ctx = g.Context(0)
     prec = g.PREC_MIXED if args.precision == "mixed" else g.PREC_FP64
