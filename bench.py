@@ -33,14 +33,16 @@ METRIC = "MPS tensors/s & samples/s vs plain FP64 GPU path at fixed fidelity; p5
 WORKLOAD = "n144_d6_chi256"
 WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) through a depth-12 "
                  "brick-wall beamsplitter network; d=6, chi=256, eps=1e-12, lambda2_freeze=1e-9")
-# DRAM bytes (read + write) per launch from an ncu capture of the current
-# kernels (None until one is taken): the sampler GEMM at 100,000 samples, and
-# the environment GEMM of the 144-mode workload (the same at any sample count)
-TRAFFIC_BYTES_PER_LAUNCH = 92.3e6          # (69032.0 + 37278.6) MB over 1152 launches
-ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.01e6       # (7214.2 + 0.1) MB over 1440 launches
-# the PCO build's DRAM bytes per launch (one launch per 144-mode build); None
-# until a capture of the current kernel is taken
-PCO_TRAFFIC_BYTES_PER_LAUNCH = 3.7256e9     # (1561.573 + 2164.040) MB, one launch per build
+# DRAM bytes (read + write) per launch from one-kernel ncu captures of the
+# current kernels (profiles/): the sampler GEMM at 100,000 samples (the mean
+# of a site's pre-pass launch, 169.6 MB, and its rest launch, 13.5 MB), and
+# the environment GEMM of the 144-mode workload (product 1, 3.7 MB, and
+# product 2, 6.7 MB, of one step; its operands stay in L2)
+TRAFFIC_BYTES_PER_LAUNCH = 91.6e6
+ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.18e6
+# the PCO build's DRAM bytes per launch (one launch per 144-mode build), from
+# a one-kernel capture of the current kernel: (1704.4 + 1979.8) MB
+PCO_TRAFFIC_BYTES_PER_LAUNCH = 3.6842e9
 # A double-float multiply-add (2 flops of the FP64 algorithm) costs 12 FP32
 # instructions: the exact product by FMA (4, with the low words) and Knuth's
 # TwoSum into the (hi, lo) accumulator (6) plus the low-word update (2)
@@ -631,9 +633,9 @@ def run_filtration(args, dev):
     n_eff = [0.5 * np.trace(0.5 * x @ x.T) - 0.5 * N for x in Sh]
     n = 2 * N
     # per step: the tridiagonalisation (4/3 n^3), the Sturm multisection
-    # (8 rounds x 512 points x 3n), the back transformation and gradient step
+    # (11 rounds x 32 points x 3n), the back transformation and gradient step
     # (~18 n^2), the recomputation of W every 64 steps (n^3)
-    fl_step = 4.0 / 3.0 * n ** 3 + 8 * 512 * 3 * n + 18 * n ** 2 + n ** 3 / 64
+    fl_step = 4.0 / 3.0 * n ** 3 + 11 * 32 * 3 * n + 18 * n ** 2 + n ** 3 / 64
     flops = fl_step * float(np.sum(iters))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp64_peak = nsm * 2 * 2 * 2.07e9 / 1e12        # 2 FP64 FMA per clock per SM
@@ -663,7 +665,7 @@ def run_filtration(args, dev):
                          "peak_source": (f"derived: {nsm} SMs x 2 FP64 FMA per clock x 2 flops x "
                                          "2070 MHz (GB300's FP64 rate)"),
                          "algorithmic_flops_def": ("per step 4/3 n^3 (tridiagonalisation) + "
-                                                   "8 x 512 x 3n (Sturm counts) + 18 n^2 (back "
+                                                   "11 x 32 x 3n (Sturm counts) + 18 n^2 (back "
                                                    "transformation, gradient, rank-2 updates) + "
                                                    "n^3 / 64 (W recomputed every 64 steps), n = 2N")},
             "cpu_baseline": cpu}

@@ -208,7 +208,29 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   const int N = m->N, d = m->d;
   // samples are processed in chunks that bound the W/Y work buffers
   const size_t per = (size_t)d * m->maxD;
-  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)((size_t)6 << 30) / (int64_t)(sizeof(double2) * 2 * per + 32 * m->maxD)));
+  int64_t chunk;
+  if (m->precision == GBSMPS_PREC_MIXED) {
+    // per sample: four state planes (two fp16 planes of up to Kp halves each),
+    // six index lists, two scales, and per parity group a row of W and its
+    // chunk norms; up to 32 GB of them per chunk (a chunk re-runs every site,
+    // and an offloaded MPS streams its planes once per chunk)
+    int Kpm = 64, Npm = 128;
+    for (int i = 0; i < N; ++i)
+      for (int pi = 0; pi < 2; ++pi) {
+        Kpm = std::max(Kpm, m->sg[i].Kp[pi]);
+        Npm = std::max(Npm, m->sg[i].Np[pi]);
+      }
+    const double ps = 2.0 * 2.0 * 4.0 * Kpm + 4.0 * 6.0 + 4.0 * 2.0 + 2.0 * (4.0 * Npm + 4.0 * (Npm / 32));
+    chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(32.0 * (double)(1ll << 30) / ps)));
+  } else {
+    chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)((size_t)6 << 30) / (int64_t)(sizeof(double2) * 2 * per + 32 * m->maxD)));
+  }
+  // GBSMPS_SAMPLE_CHUNK caps the samples per chunk (the patterns do not
+  // depend on it: every sample's arithmetic is its own)
+  if (const char* ce = getenv("GBSMPS_SAMPLE_CHUNK")) {
+    const long long cap = atoll(ce);
+    if (cap > 0) chunk = std::min<int64_t>(chunk, cap);
+  }
   DevBuf ub, obuf, fbuf, vb, wb, yb;
   if (m->precision != GBSMPS_PREC_MIXED) {
     CK(vb.alloc(sizeof(double2) * 2 * (size_t)chunk * m->maxD, s));

@@ -194,6 +194,11 @@ struct SiteTask {       // one local tensor to build
   const uint8_t* occr; const int* lowr; int capr;   // right basis
   double2* out;         // Dl x d x Dr
   size_t scratch_off;   // offset (complex elements) into the scratch arena
+  // photon-number parity classes of the two bonds (optional): the kept
+  // states of each bond listed even class first, and the class sizes
+  const int* pl = nullptr;
+  const int* pr = nullptr;
+  int kl[2] = {0, 0}, kr[2] = {0, 0};
 };
 cudaError_t launch_maps_brute(const uint8_t* occ, int D, int n, int* low, int cap,
                               int* status, cudaStream_t s);

@@ -422,14 +422,17 @@ __global__ void __launch_bounds__(256) env_chain_kernel(const EnvJob* __restrict
 
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes) {
-  static std::atomic<int> nsm_cache{0};
-  int nsm = nsm_cache.load();
+  // SM count of the current device, cached per device index
+  static std::atomic<int> nsm_cache[64];
+  int dev = 0;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed) return ed;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int nsm = nsm_cache[dev].load();
   if (!nsm) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (!e) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e) return e;
-    nsm_cache.store(nsm);
+    ed = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ed) return ed;
+    nsm_cache[dev].store(nsm);
   }
   std::vector<DfSub> live;
   for (int i = 0; i < n; ++i)

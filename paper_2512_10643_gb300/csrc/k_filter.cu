@@ -11,8 +11,8 @@
 //    recomputed from S, so rounding cannot drift.
 //  * The lowest eigenpair of W: Householder tridiagonalisation of a copy in
 //    shared memory; the smallest eigenvalue of the tridiagonal matrix by
-//    multisection of Sturm counts (every thread counts at one point of the
-//    current interval per round); its eigenvector by inverse iteration
+//    multisection of Sturm counts (one warp, a lane per point of the current
+//    interval, eleven rounds); its eigenvector by inverse iteration
 //    (Gaussian elimination with partial pivoting on the tridiagonal); the
 //    reflectors applied back.
 //  * The gradient: with u = S^T v0, u^ = u / |u| and a^ = Omega^T u^ (a unit
@@ -81,9 +81,9 @@ __global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(const FilterArgs 
   double* p = ah + n;
   double* q = p + n;
   double* w = q + n;
-  double* red = w + n;                // FT_NW
+  double* vv = w + n;                 // the current Householder vector, contiguous
+  double* red = vv + n;               // FT_NW
   double* scal = red + FT_NW;         // 8 scalars
-  int* ibuf = reinterpret_cast<int*>(scal + 8);   // [0]: first point with count >= 1
   const double* G = a.gth + (size_t)blockIdx.x * n * n;
   double* S = a.S + (size_t)blockIdx.x * n * n;
   double* W = a.W + (size_t)blockIdx.x * n * n;
@@ -127,27 +127,29 @@ __global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(const FilterArgs 
       const double ah_ = x0 >= 0.0 ? -nrm : nrm;
       const double v0 = x0 - ah_;
       const double t = 2.0 / (tail + v0 * v0);
+      // v (kept in column k for the back transformation, and contiguous in
+      // vv: a column of A is one shared-memory bank)
+      for (int r = tid; r < m; r += FT_THREADS) vv[r] = r == 0 ? v0 : A[(size_t)(k + 1 + r) * n + k];
       __syncthreads();                            // everyone read x0 before it is overwritten
       if (tid == 0) { e[k] = ah_; tau[k] = t; A[(size_t)(k + 1) * n + k] = v0; }
-      __syncthreads();
       // p = t A_sub v  (one warp per row of the trailing block)
       for (int r = wid; r < m; r += FT_NW) {
-        const int i = k + 1 + r;
+        const double* row = A + (size_t)(k + 1 + r) * n + k + 1;
         double s = 0.0;
-        for (int c = lane; c < m; c += 32) s += A[(size_t)i * n + k + 1 + c] * A[(size_t)(k + 1 + c) * n + k];
+        for (int c = lane; c < m; c += 32) s = fma(row[c], vv[c], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) p[r] = t * s;
       }
       __syncthreads();
       double kp = 0.0;
-      for (int r = tid; r < m; r += FT_THREADS) kp += p[r] * A[(size_t)(k + 1 + r) * n + k];
+      for (int r = tid; r < m; r += FT_THREADS) kp += p[r] * vv[r];
       const double K = 0.5 * t * ft_sum(kp, red);
-      for (int r = tid; r < m; r += FT_THREADS) w[r] = p[r] - K * A[(size_t)(k + 1 + r) * n + k];
+      for (int r = tid; r < m; r += FT_THREADS) w[r] = p[r] - K * vv[r];
       __syncthreads();
-      for (int idx = tid; idx < m * m; idx += FT_THREADS) {
-        const int r = idx / m, c = idx % m;
-        const double vr = A[(size_t)(k + 1 + r) * n + k], vc = A[(size_t)(k + 1 + c) * n + k];
-        A[(size_t)(k + 1 + r) * n + k + 1 + c] -= vr * w[c] + w[r] * vc;
+      for (int r = wid; r < m; r += FT_NW) {      // A_sub -= v w^T + w v^T, a warp per row
+        double* row = A + (size_t)(k + 1 + r) * n + k + 1;
+        const double vr = vv[r], wr = w[r];
+        for (int c = lane; c < m; c += 32) row[c] = fma(-vr, w[c], fma(-wr, vv[c], row[c]));
       }
       __syncthreads();
     }
@@ -172,22 +174,23 @@ __global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(const FilterArgs 
     }
     __syncthreads();
     // ---- smallest eigenvalue: multisection of Sturm counts -----------------
-    for (int round = 0; round < 8; ++round) {
-      const double lo = scal[0], hi = scal[1];
-      if (tid == 0) ibuf[0] = FT_THREADS;
-      __syncthreads();
-      const double xt = lo + (hi - lo) * (double)(tid + 1) / (double)(FT_THREADS + 1);
-      if (sturm_count(d, e, n, xt, scal[2]) >= 1) atomicMin(&ibuf[0], tid);
-      __syncthreads();
-      if (tid == 0) {
-        const int t0 = ibuf[0];
-        const double nlo = t0 == 0 ? lo : lo + (hi - lo) * (double)t0 / (double)(FT_THREADS + 1);
-        const double nhi = t0 >= FT_THREADS ? hi : lo + (hi - lo) * (double)(t0 + 1) / (double)(FT_THREADS + 1);
-        scal[0] = nlo;
-        scal[1] = nhi;
+    // one warp, 32 points a round (each count is n dependent FP64 divisions,
+    // and GB300's FP64 pipe is narrow): 33^11 > 1e16 narrows the Gershgorin
+    // interval to the rounding of the counts
+    if (wid == 0) {
+      double lo = scal[0], hi = scal[1];
+      for (int round = 0; round < 11; ++round) {
+        const double xt = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(d, e, n, xt, scal[2]) >= 1);
+        const int t0 = hit ? __ffs(hit) - 1 : 32;
+        const double nlo = t0 == 0 ? lo : lo + (hi - lo) * (double)t0 / 33.0;
+        const double nhi = t0 >= 32 ? hi : lo + (hi - lo) * (double)(t0 + 1) / 33.0;
+        lo = nlo;
+        hi = nhi;
       }
-      __syncthreads();
+      if (lane == 0) { scal[0] = lo; scal[1] = hi; }
     }
+    __syncthreads();
     const double lam = 0.5 * (scal[0] + scal[1]);
     L = -lam;
     if (L <= a.eps || it >= a.max_iter) break;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(const FilterArgs 
 }  // namespace
 
 size_t filter_smem_bytes(int n) {
-  return sizeof(double) * ((size_t)n * n + 10 * (size_t)n + FT_NW + 8) + sizeof(int) * 4;
+  return sizeof(double) * ((size_t)n * n + 11 * (size_t)n + FT_NW + 8);
 }
 
 cudaError_t launch_filter(int count, int n, const double* gth, double* S, double* W, double alpha,

@@ -253,11 +253,33 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
     }
     __syncthreads();
     const T inv_s = s > 0 ? (T)sm.ik[s] : (T)1;
-    for (size_t idx = tid; idx < DD; idx += nt) {
-      const int mu = idx / Dr, nu = idx % Dr;
+    // from s = 2 on only the entries with n_mu + s + n_nu even are non-zero
+    // in W_s (every PCO adds two quanta); every other entry of W_s, of the
+    // planes p = s + 2k (written as zeros at s = p mod 2) and of the buffer
+    // W_s overwrites (W_{s-2}) is zero already.  With the bonds' parity
+    // lists the pass walks only those entries: rows of class c with the
+    // columns of class c ^ (s & 1), a contiguous run of each list.
+    const bool by_class = s >= 2 && t.pl != nullptr;
+    const int sp = s & 1;
+    const size_t n0 = (size_t)t.kl[0] * t.kr[sp], n1 = (size_t)t.kl[1] * t.kr[sp ^ 1];
+    const size_t nent = by_class ? n0 + n1 : DD;
+    for (size_t idx = tid; idx < nent; idx += nt) {
+      int mu, nu;
+      if (by_class) {
+        const int c = idx < n0 ? 0 : 1;
+        const size_t e = c ? idx - n0 : idx;
+        const int cr = c ^ sp;
+        const int kc = t.kr[cr];
+        mu = t.pl[(c ? t.kl[0] : 0) + (int)(e / kc)];
+        nu = t.pr[(cr ? t.kr[0] : 0) + (int)(e % kc)];
+      } else {
+        mu = idx / Dr;
+        nu = idx % Dr;
+      }
+      const size_t ent = (size_t)mu * Dr + nu;
       C2 y;
       if (s == 0) {
-        y = Wp[idx];
+        y = Wp[ent];
       } else {
         C2 acc = zero;
         const int cl = lcnt[mu], cr = rcnt[nu];
@@ -266,7 +288,7 @@ __device__ void pco_site(PcoSmem& sm, const SiteTask& t, int d, double2* __restr
         for (int e = 0; e < cr; ++e)
           cfma(acc, rc[(size_t)nu * NEM + e], Wp[(size_t)mu * Dr + rs[(size_t)nu * NEM + e]]);
         y = cscale(acc, inv_s);
-        if (s + 1 < d) Wn[idx] = y;
+        if (s + 1 < d) Wn[ent] = y;
       }
       const double2 yd = to_d(y);
       for (int k = 0; k <= kmx; ++k) {

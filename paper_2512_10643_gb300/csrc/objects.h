@@ -157,9 +157,11 @@ struct gbsmps_mps {
     gscale.release();
     vacamp.release();
     eoff_dev.release(); lchol.release(); linv.release(); bpack.release(); creg.release();
-    if (copy_stream) cudaStreamSynchronize(copy_stream);
-    if (ctx) cudaStreamSynchronize(ctx->stream);
-    if (host_bpack) cudaFreeHost(host_bpack);
+    if (host_bpack) {            // pinned memory: no copy or sampling may still read it
+      if (copy_stream) cudaStreamSynchronize(copy_stream);
+      if (ctx) cudaStreamSynchronize(ctx->stream);
+      cudaFreeHost(host_bpack);
+    }
     for (int k = 0; k < RING; ++k) {
       if (ring_ready[k]) cudaEventDestroy(ring_ready[k]);
       if (ring_free[k]) cudaEventDestroy(ring_free[k]);

@@ -142,6 +142,12 @@ void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTa
     t.capr = cap;
     t.out = M->tensors.as<double2>() + M->toff[m];
     t.scratch_off = 0;
+    if ((int)M->pcnt.size() == 2 * (N + 1)) {
+      t.pl = M->ba.pidx + (size_t)m * cap;
+      t.pr = M->ba.pidx + (size_t)(m + 1) * cap;
+      t.kl[0] = M->pcnt[2 * m]; t.kl[1] = M->pcnt[2 * m + 1];
+      t.kr[0] = M->pcnt[2 * m + 2]; t.kr[1] = M->pcnt[2 * m + 3];
+    }
     out.push_back(t);
   }
 }

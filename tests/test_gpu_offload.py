@@ -82,3 +82,30 @@ def test_offload_rejects_fp64(ctx):
         m.tensor(0)                                   # still resident
     finally:
         m.release()
+
+
+@pytest.mark.parametrize("offload", [False, True])
+def test_chunked_sampling_equals_one_chunk(ctx, monkeypatch, offload):
+    """Samples are processed in chunks (GBSMPS_SAMPLE_CHUNK caps their size);
+    every sample's arithmetic is its own and its Philox counter is its global
+    index, so the patterns do not depend on the chunking, resident or
+    offloaded (an offloaded MPS streams its planes once per chunk)."""
+    w = wl.small(24, 8, d=6, chi=64, depth=5, rlo=0.1, rhi=0.45)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), d=6, chi_max=64, eps_trunc=1e-12,
+                       lambda2_freeze=1e-9, precision=g.PREC_MIXED)
+    try:
+        if offload:
+            m.offload()
+        S = 3000
+        u = wl.uniforms(S, 24, seed=81)
+        monkeypatch.delenv("GBSMPS_SAMPLE_CHUNK", raising=False)
+        f1 = np.zeros(S, dtype=np.uint8)
+        a = m.sample(S, uniforms=u, flags=f1)
+        p = m.sample(S, seed=3, counter0=11)
+        monkeypatch.setenv("GBSMPS_SAMPLE_CHUNK", "700")
+        f2 = np.zeros(S, dtype=np.uint8)
+        b = m.sample(S, uniforms=u, flags=f2)
+        q = m.sample(S, seed=3, counter0=11)
+        assert np.array_equal(a, b) and np.array_equal(f1, f2) and np.array_equal(p, q)
+    finally:
+        m.release()
