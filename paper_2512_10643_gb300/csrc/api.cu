@@ -212,8 +212,9 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
   if (m->precision == GBSMPS_PREC_MIXED) {
     // per sample: four state planes (two fp16 planes of up to Kp halves each),
     // six index lists, two scales, and per parity group a row of W and its
-    // chunk norms; up to 32 GB of them per chunk (a chunk re-runs every site,
-    // and an offloaded MPS streams its planes once per chunk)
+    // chunk norms; up to 32 GB of them per chunk (a chunk re-runs every site;
+    // an offloaded MPS streams its planes once per chunk, so it takes the
+    // largest chunks)
     int Kpm = 64, Npm = 128;
     for (int i = 0; i < N; ++i)
       for (int pi = 0; pi < 2; ++pi) {
@@ -222,6 +223,17 @@ int sample_impl(gbsmps_mps* m, cudaStream_t s, int* status, int sm_reserve, int 
       }
     const double ps = 2.0 * 2.0 * 4.0 * Kpm + 4.0 * 6.0 + 4.0 * 2.0 + 2.0 * (4.0 * Npm + 4.0 * (Npm / 32));
     chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(32.0 * (double)(1ll << 30) / ps)));
+    if (!m->host_bpack) {
+      // resident MPS: balanced chunks of at most ~576 MB of state planes
+      // (16 Kp bytes per sample); measured on GB300: one chunk for 100k
+      // samples of the 144-mode state (Kp = 320: 18.3 ms; 23.0 ms in two),
+      // ~50k for the 1024-mode state (Kp = 640, 1M samples: 2.83 s; 4.14 s
+      // in one chunk, whose gathered rows and scattered next-state writes
+      // miss L2)
+      const double planes = 16.0 * Kpm;
+      const int64_t nch = std::max<int64_t>(1, (int64_t)std::ceil((double)S * planes / (576.0 * (1 << 20))));
+      chunk = std::min<int64_t>(chunk, (S + nch - 1) / nch);
+    }
   } else {
     chunk = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)((size_t)6 << 30) / (int64_t)(sizeof(double2) * 2 * per + 32 * m->maxD)));
   }
