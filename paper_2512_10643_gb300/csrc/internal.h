@@ -338,6 +338,36 @@ struct DfSub {
 constexpr size_t DFG_CNT_BYTES = 256 << 10;
 cudaError_t launch_zgemm_df64_grouped(const DfSub* subs, int n, cudaStream_t s, void* work,
                                       size_t work_bytes);
+// The same products on the tensor cores with exact accumulation (k_envtc.cu):
+// operands sliced into bf16 integer planes; arenas and tensor maps per
+// launch slot (0: Ahat R, 1: X Ahat^dag), sized once per build from the
+// products of every step.
+constexpr int ETC_MAX = 16;           // products per launch
+struct EtcNeeds {
+  bool ok = true;
+  int W[2] = {0, 0};                  // real k (bf16 per arena row)
+  long long rowsA[2] = {0, 0}, rowsB[2] = {0, 0}, expo[2] = {0, 0};
+  long long part = 0;                 // split-K partials (complex elements)
+};
+void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, EtcNeeds* acc);   // maxima
+size_t envtc_arena_bytes(int W, long long rows);
+struct EnvTcPlan {
+  alignas(64) unsigned char mapA[2][128], mapB[2][128];
+  int W[2] = {0, 0};
+  long long rowsA[2] = {0, 0}, rowsB[2] = {0, 0};
+  void* arenaA[2] = {nullptr, nullptr};
+  void* arenaB[2] = {nullptr, nullptr};
+  int* expo[2] = {nullptr, nullptr};
+  long long expo_cap[2] = {0, 0};
+  float4* work = nullptr;             // split-K partials: (Re pair, Im pair) per element
+  long long work_cap = 0;
+};
+int envtc_setup(EnvTcPlan* P, int slot, int W, long long rowsA, long long rowsB, void* arenaA,
+                void* arenaB);
+// one environment step (both products); cudaErrorNotSupported (nothing
+// enqueued) when a product does not fit the plan
+cudaError_t launch_envtc_step(const EnvTcPlan& P, const DfSub* s1, int n1, const DfSub* s2, int n2,
+                              int* status, cudaStream_t s);
 // herm: C (square) is Hermitian; only i >= j is computed, C[j][i] = conj(C[i][j])
 // one state of the batched persistent environment chain (device pointers)
 struct EnvJob {

@@ -220,8 +220,8 @@ ParitySite parity_site(const gbsmps_mps* M, int m) {
 // the class-0 states (the vacuum pattern keeps every bond state in the even
 // class; in the energy gauge the end bonds' energies are 0, so at m = 0 the
 // product is the amplitude itself), written as pairs, or in FP64 at m = 0.
-int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2* X, void* work,
-                    size_t wbytes, cudaStream_t s, const double2* ui, double2* uo) {
+void env_subs(const gbsmps_mps* M, int m, const double2* Ah, double2* R, double2* X,
+              const double2* ui, double2* uo, std::vector<DfSub>& s1, std::vector<DfSub>& s2) {
   const int d = M->d;
   const ParitySite P = parity_site(M, m);
   const int Dr = P.kr[0] + P.kr[1];
@@ -229,28 +229,101 @@ int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2
   const long long o1 = (long long)P.kl[0] * K[0];
   const double2* A = Ah + M->toff[m];
   const double2* Rr = R + M->eoff[m + 1];
-  std::vector<DfSub> sub;
+  s1.clear();
+  s2.clear();
   for (int c = 0; c < 2; ++c)
     for (int p = 0; p < d; ++p) {
       const int cr = c ^ (p & 1);
       const long long off = (c ? o1 : 0) + pk_off(p, Dr, P.kr, c);
       // Ahat, R (bonds 1 .. N) and X as double-float pairs
-      sub.push_back(DfSub{0, 0, P.kl[c], P.kr[cr], P.kr[cr], A + off, K[c],
-                          Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0,
-                          1, 1, 1});
+      s1.push_back(DfSub{0, 0, P.kl[c], P.kr[cr], P.kr[cr], A + off, K[c],
+                         Rr + (cr ? (long long)P.kr[0] * P.kr[0] : 0), P.kr[cr], X + off, K[c], 0,
+                         1, 1, 1});
     }
   if (ui && uo)       // block p = 0 of class 0: the first kr[0] columns of its rows
-    sub.push_back(DfSub{0, 0, P.kl[0], 1, P.kr[0], A, K[0], ui, 1, uo, 1, 0, 1, 1, m > 0 ? 1 : 0});
-  CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
-  sub.clear();
+    s1.push_back(DfSub{0, 0, P.kl[0], 1, P.kr[0], A, K[0], ui, 1, uo, 1, 0, 1, 1, m > 0 ? 1 : 0});
   for (int c = 0; c < 2; ++c) {
     const long long off = c ? o1 : 0;
     // R_m as pairs too, but R_0 (the squared norm) in FP64
-    sub.push_back(DfSub{0, 1, P.kl[c], P.kl[c], (int)K[c], X + off, K[c], A + off, K[c],
-                        R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1, 1, 1,
-                        m > 0 ? 1 : 0});
+    s2.push_back(DfSub{0, 1, P.kl[c], P.kl[c], (int)K[c], X + off, K[c], A + off, K[c],
+                       R + M->eoff[m] + (c ? (long long)P.kl[0] * P.kl[0] : 0), P.kl[c], 1, 1, 1,
+                       m > 0 ? 1 : 0});
   }
-  CK(launch_zgemm_df64_grouped(sub.data(), (int)sub.size(), s, work, wbytes));
+}
+
+// One step of the environment chain on the parity blocks.  With ui set it
+// also carries the all-vacuum amplitude from the right: uo = Ahat^m[0] ui on
+// the class-0 states (the vacuum pattern keeps every bond state in the even
+// class; in the energy gauge the end bonds' energies are 0, so at m = 0 the
+// product is the amplitude itself), written as pairs, or in FP64 at m = 0.
+// The products run on the tensor cores when a plan is given (and they fit
+// it), else in double-float on the FP32 pipes.
+int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2* X, void* work,
+                    size_t wbytes, cudaStream_t s, const double2* ui, double2* uo,
+                    const EnvTcPlan* tp, int* status) {
+  std::vector<DfSub> s1, s2;
+  env_subs(M, m, Ah, R, X, ui, uo, s1, s2);
+  if (tp) {
+    const cudaError_t e =
+        launch_envtc_step(*tp, s1.data(), (int)s1.size(), s2.data(), (int)s2.size(), status, s);
+    if (e != cudaErrorNotSupported) {
+      CK(e);
+      return GBSMPS_OK;
+    }
+  }
+  CK(launch_zgemm_df64_grouped(s1.data(), (int)s1.size(), s, work, wbytes));
+  CK(launch_zgemm_df64_grouped(s2.data(), (int)s2.size(), s, work, wbytes));
+  return GBSMPS_OK;
+}
+
+// The exact-accumulation tensor-core products are the default; GBSMPS_ENV_TC=0
+// selects the double-float GEMM on the FP32 pipes.
+bool env_tc_enabled() {
+  const char* e = getenv("GBSMPS_ENV_TC");
+  return !(e && e[0] == '0');
+}
+
+// arenas, exponents, partials and counters for every step of one chain
+struct EnvTcBufs {
+  EnvTcPlan plan;
+  DevBuf arA[2], arB[2], ex, wk;
+  ~EnvTcBufs() { release(); }
+  void release() {
+    for (int k = 0; k < 2; ++k) { arA[k].release(); arB[k].release(); }
+    ex.release(); wk.release();
+  }
+};
+
+int env_tc_prepare(const gbsmps_mps* M, const double2* Ah, double2* R, double2* X,
+                   const double2* ui, double2* uo, EnvTcBufs& B, cudaStream_t s, bool* ok) {
+  EtcNeeds nd;
+  std::vector<DfSub> s1, s2;
+  for (int m = M->N - 1; m >= 0; --m) {
+    env_subs(M, m, Ah, R, X, ui, uo, s1, s2);
+    envtc_needs(s1.data(), (int)s1.size(), s2.data(), (int)s2.size(), &nd);
+  }
+  *ok = nd.ok;
+  if (!nd.ok) return GBSMPS_OK;
+  EnvTcPlan& P = B.plan;
+  for (int k = 0; k < 2; ++k) {
+    const size_t ba = envtc_arena_bytes(nd.W[k], nd.rowsA[k]);
+    const size_t bb = envtc_arena_bytes(nd.W[k], nd.rowsB[k]);
+    CK(B.arA[k].alloc(ba, s));
+    CK(B.arB[k].alloc(bb, s));
+    // padding rows are never written by the slicing: zero them once
+    CK(cudaMemsetAsync(B.arA[k].p, 0, ba, s));
+    CK(cudaMemsetAsync(B.arB[k].p, 0, bb, s));
+    if (envtc_setup(&P, k, nd.W[k], nd.rowsA[k], nd.rowsB[k], B.arA[k].p, B.arB[k].p))
+      return GBSMPS_ERR_CUDA;
+  }
+  CK(B.ex.alloc(sizeof(int) * (nd.expo[0] + nd.expo[1] + 2), s));
+  P.expo[0] = B.ex.as<int>();
+  P.expo[1] = P.expo[0] + nd.expo[0] + 1;
+  P.expo_cap[0] = nd.expo[0];
+  P.expo_cap[1] = nd.expo[1];
+  CK(B.wk.alloc(sizeof(float4) * (nd.part + 1), s));
+  P.work = B.wk.as<float4>();
+  P.work_cap = nd.part;
   return GBSMPS_OK;
 }
 
@@ -316,12 +389,22 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     CK(cudaMemcpyAsync(ua, &one_u, sizeof(float4), cudaMemcpyHostToDevice, s));
     // (plain FP32 products were measured at 4.4e-5 (N = 144) and 2.8e-4
     // (N = 1024) amplitude error against FP64: the norm needs more bits)
+    // exact-accumulation tensor-core products (the plan is sized from the
+    // products of every step before the first)
+    EnvTcBufs tcb;
+    bool use_tc = env_tc_enabled();
+    if (use_tc) {
+      const int rc = env_tc_prepare(M, Ah, R, X, ua, ubn, tcb, s, &use_tc);
+      if (rc) return rc;
+    }
     for (int m = N - 1; m >= 0; --m) {
       const int rc = env_step_blocks(M, m, Ah, R, X, kw.p, wbytes, s, ua,
-                                     m > 0 ? ubn : M->vacamp.as<double2>());
+                                     m > 0 ? ubn : M->vacamp.as<double2>(),
+                                     use_tc ? &tcb.plan : nullptr, c->d_status);
       if (rc) return rc;
       std::swap(ua, ubn);
     }
+    tcb.release();
     kw.release();
     ub.release();
   } else {
