@@ -44,6 +44,7 @@
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -126,6 +127,9 @@ __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_cons
   // a register copy: the stores below go through generic pointers, which
   // would otherwise make every field a reload from parameter space
   const SlJob J = js.j[find_job(js, blockIdx.x)];
+  // launched as a programmatic dependent: no global access before the wait
+  griddep_wait();
+  griddep_launch();
   const long long bl = blockIdx.x - J.b0;
   const int segs = (J.K + SL_THREADS - 1) / SL_THREADS;
   const int r = (int)(bl / segs), seg = (int)(bl % segs);
@@ -300,6 +304,9 @@ envtc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  // the setup above overlaps the preceding kernel; no global access before the wait
+  griddep_wait();
+  griddep_launch();
   if (warp == 0) {
     if (lane == 0) {                                  // loads: both operands' seven planes per stage
       int i = 0;
@@ -484,6 +491,8 @@ __global__ void __launch_bounds__(RED_THREADS) etc_reduce_kernel(const __grid_co
     if (rs.j[mid].e0 <= t) lo = mid; else hi = mid - 1;
   }
   const RedJob J = rs.j[lo];
+  griddep_wait();
+  griddep_launch();
   const long long x = t - J.e0;
   const long long MN = (long long)J.M * J.N;
   const bool live = x < MN && !(J.herm && (x % J.N) > (x / J.N));
@@ -680,11 +689,27 @@ void add_slice_jobs(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* 
   }
 }
 
+// every launch of a step is a programmatic dependent of the one before it
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_slices(const SlSet& js, long long blocks, cudaStream_t s) {
   if (js.n == 0 || blocks == 0) return cudaSuccess;
-  etc_slice_kernel<<<(unsigned)blocks, SL_THREADS, 0, s>>>(js);
   COUNT_LAUNCH(1);
-  return cudaGetLastError();
+  return launch_pdl(etc_slice_kernel, (unsigned)blocks, SL_THREADS, 0, s, js);
 }
 
 cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* L, int np,
@@ -731,17 +756,16 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   memcpy(&ma, P.mapA[slot], sizeof(CUtensorMap));
   memcpy(&mb, P.mapB[slot], sizeof(CUtensorMap));
   cudaEvent_t tr0 = g_env_trace.begin(s);
-  envtc_kernel<<<(unsigned)units, E_THREADS, E_SMEM, s>>>(ma, mb, G, status);
+  e = launch_pdl(envtc_kernel, (unsigned)units, E_THREADS, E_SMEM, s, ma, mb, G, status);
   COUNT_LAUNCH(1);
-  e = cudaGetLastError();
   if (e) return e;
   if (rs.n) {
     // threads per output: enough loads in flight for the longest k split
     const int split = maxks >= 16 ? 4 : maxks >= 8 ? 2 : 1;
     const long long thr = elems * split;
-    etc_reduce_kernel<<<(unsigned)((thr + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0, s>>>(rs, split);
+    e = launch_pdl(etc_reduce_kernel, (unsigned)((thr + RED_THREADS - 1) / RED_THREADS), RED_THREADS, 0,
+                   s, rs, split);
     COUNT_LAUNCH(1);
-    e = cudaGetLastError();
   }
   g_env_trace.end(tr0, s, fl, by);
   return e;
@@ -788,10 +812,11 @@ int envtc_setup(EnvTcPlan* P, int slot, int W, long long rowsA, long long rowsB,
 }
 
 // One environment step: X = Ahat R (products s1), R_m = X Ahat^dag (s2).
-// Launches: slices of s1's operands and of s2's B (Ahat rows, independent of
-// X), the first GEMM (and its k-split reduction), slices of X, the second
-// GEMM (and reduction).  cudaErrorNotSupported (nothing enqueued) when a
-// product does not fit the plan; the caller then takes the double-float GEMM.
+// Launches, each a programmatic dependent of the one before: slices of s1's
+// operands and of s2's B (Ahat rows, independent of X), the first GEMM (and
+// its k-split reduction), slices of X, the second GEMM (and reduction).
+// cudaErrorNotSupported (nothing enqueued) when a product does not fit the
+// plan; the caller then takes the double-float GEMM.
 cudaError_t launch_envtc_step(const EnvTcPlan& P, const DfSub* s1, int n1, const DfSub* s2, int n2,
                               int* status, cudaStream_t s) {
   Lay L1[ETC_MAX], L2[ETC_MAX];

@@ -1,7 +1,10 @@
 """Batched build (gbsmps_build_batch): every state of a batch of uneven N,
 chi, d and precision must match the same state built alone (the GSVD and PCO
 stages run the same per-state arithmetic; only the environment products are
-summed in another order) and the oracle."""
+summed in another order) and the oracle.  A batch runs its environment chains
+in double-float arithmetic, so the single builds it is compared with take the
+double-float products too (GBSMPS_ENV_TC=0); test_gpu_envtc.py compares those
+with the tensor-core products of a default single build."""
 import numpy as np
 import pytest
 
@@ -52,7 +55,8 @@ def _batch_states(precisions=(g.PREC_MIXED,)):
 
 
 @pytest.mark.parametrize("precisions", [(g.PREC_MIXED,), (g.PREC_MIXED, g.PREC_FP64)])
-def test_batch_matches_single_builds(ctx, precisions):
+def test_batch_matches_single_builds(ctx, precisions, monkeypatch):
+    monkeypatch.setenv("GBSMPS_ENV_TC", "0")
     states = _batch_states(precisions)
     batch = g.MPS.batch(ctx, [np.ascontiguousarray(w.gamma) for w, _ in states],
                         [o for _, o in states])

@@ -1,0 +1,85 @@
+"""Environment products on the tensor cores (exact accumulation of bf16
+integer slices) against the double-float products on the FP32 pipes: the same
+mixed-precision single build with GBSMPS_ENV_TC=1 (the default) and =0.
+
+Both compute R_m = sum_p Ahat[p] R_{m+1} Ahat[p]^dag (Sec. II B, the
+normalisation of the MPS) to about 44 bits per step, so their difference is a
+rounding-level spread, far below the FP32 PCO passes that set the mixed path's
+error against FP64 (7e-9 of the largest amplitude at N = 144): canonical
+tensors, amplitudes and samples drawn from shared uniforms are compared."""
+import numpy as np
+import pytest
+
+import paper_2512_10643_gb300 as g
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+def _states():
+    rs = np.random.default_rng(11)
+    out = []
+    for i in range(7):
+        N = int(rs.integers(8, 41))
+        d = int(rs.choice([4, 6]))
+        chi = int(rs.choice([16, 32, 64]))
+        w = wl.small(N, 700 + i, d=d, chi=chi, depth=max(1, N // 8), rlo=0.1, rhi=0.5)
+        out.append((w, dict(d=d, chi_max=chi, eps_trunc=1e-12, lambda2_freeze=1e-8,
+                            precision=g.PREC_MIXED)))
+    w = wl.config("n144_d6_chi256")
+    out.append((w, dict(d=w.d, chi_max=w.chi, eps_trunc=w.eps, lambda2_freeze=w.freeze,
+                        precision=g.PREC_MIXED)))
+    w1 = wl.small(1, 5, d=4, chi=4, depth=1)          # one mode: no environment product
+    out.append((w1, dict(d=4, chi_max=4, precision=g.PREC_MIXED)))
+    return out
+
+
+def _build(ctx, w, opts, monkeypatch, tc):
+    monkeypatch.setenv("GBSMPS_ENV_TC", "1" if tc else "0")
+    return g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **opts)
+
+
+def test_tensor_core_environments_match_double_float(ctx, monkeypatch):
+    worst = {"tensor": 0.0, "amp": 0.0}
+    for k, (w, opts) in enumerate(_states()):
+        mt = _build(ctx, w, opts, monkeypatch, True)
+        md = _build(ctx, w, opts, monkeypatch, False)
+        try:
+            assert np.array_equal(mt.info["bond_dims"], md.info["bond_dims"])
+            for m in range(0, w.N, max(1, w.N // 24)):
+                tt, td = mt.tensor(m), md.tensor(m)
+                err = np.abs(tt - td).max() / max(np.abs(td).max(), 1e-300)
+                worst["tensor"] = max(worst["tensor"], err)
+                assert err <= 1e-8, (w.N, m, err)
+            pats = wl.random_patterns(200, w.N, opts["d"], seed=k, max_total=8)
+            pats[0] = 0
+            at, ad = mt.amplitudes(pats), md.amplitudes(pats)
+            at = at.cpu().numpy() if hasattr(at, "cpu") else np.asarray(at)
+            ad = ad.cpu().numpy() if hasattr(ad, "cpu") else np.asarray(ad)
+            err = np.abs(at - ad).max() / np.abs(ad).max()
+            worst["amp"] = max(worst["amp"], err)
+            assert err <= 1e-10, (w.N, err)
+            u = wl.uniforms(2000, w.N, seed=50 + k)
+            ft = np.zeros(2000, np.uint8)
+            fd = np.zeros(2000, np.uint8)
+            st = mt.sample(2000, uniforms=u, flags=ft)
+            sd = md.sample(2000, uniforms=u, flags=fd)
+            st = st.cpu().numpy() if hasattr(st, "cpu") else np.asarray(st)
+            sd = sd.cpu().numpy() if hasattr(sd, "cpu") else np.asarray(sd)
+            ok = (ft == 0) & (fd == 0)
+            assert ok.mean() > 0.95
+            assert np.array_equal(st[ok], sd[ok])
+        finally:
+            mt.release()
+            md.release()
+    print("tensor-core vs double-float environments, largest relative differences:", worst)
