@@ -36,10 +36,13 @@ WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) thro
 # DRAM bytes (read + write) per launch from one-kernel ncu captures of the
 # current kernels (profiles/): the sampler GEMM at 100,000 samples (the mean
 # of a site's pre-pass launch, 169.6 MB, and its rest launch, 13.5 MB), and
-# the environment GEMM of the 144-mode workload (product 1, 3.7 MB, and
-# product 2, 6.7 MB, of one step; its operands stay in L2)
+# the environment products of the 144-mode workload (a tensor-core GEMM
+# launch with its k-split reduction, the mean over one step's two launches)
 TRAFFIC_BYTES_PER_LAUNCH = 91.6e6
-ENV_TRAFFIC_BYTES_PER_LAUNCH = 5.18e6
+ENV_TRAFFIC_BYTES_PER_LAUNCH = None
+# slice pairs (s, t), s + t <= 6, of seven-slice operands: the bf16 products
+# the environment GEMM issues per real multiply-add
+ENV_SLICE_PAIRS = 28
 # the PCO build's DRAM bytes per launch (one launch per 144-mode build), from
 # a one-kernel capture of the current kernel: (1704.4 + 1979.8) MB
 PCO_TRAFFIC_BYTES_PER_LAUNCH = 3.6842e9
@@ -358,40 +361,60 @@ def run_gpu(args, rank, local, ws, dist):
         gbs = roof_s["traffic"] / (tr["ms"] / n_launch / 1e3) / 1e9
         roof_s.update(dram_gbs=round(gbs, 1), dram_frac=round(gbs / hbm, 4),
                       dram_peak_source=f"hbm_gbs of {src} MEASURED_PEAKS.json")
-    # the environment GEMM against the FP32 pipes it runs on: algorithmic
-    # flops counted once (x1), the double-float emulation cost shown apart
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fmax = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
-    fp32_peak = nsm * FP32_LANES_PER_SM * fmax * 2.0 / 1e12
     ne = max(te["launches"], 1)
-    ach_df = te["flops"] / (te["ms"] / 1e3) / 1e12 if te["ms"] > 0 else 0.0
-    roof_e = {"kernel": "zgemm_df64_grouped_kernel (double-float complex GEMM on the FP32 pipes, "
-                        "right-environment chain R_m = sum_p Ahat^m[p] R_{m+1} Ahat^m[p]^dag on the "
-                        "parity blocks; two grouped launches per site, split-K partials summed in k "
-                        "order by each tile's last CTA)",
-              "bound": "alu", "achieved": round(ach_df, 4), "peak": round(fp32_peak, 3),
-              "peak_source": (f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                              f"{fmax / 1e6:.0f} MHz (max SM clock) x 2 flops per FMA: the FP32 pipes "
-                              "the kernel runs on; achieved counts the FP64 algorithm's flops once"),
-              "unit": "TFLOP/s", "frac": round(ach_df / fp32_peak, 5) if fp32_peak > 0 else None,
-              "issued_fp32_instr_per_fma": DF64_FP32_INSTR_PER_FMA,
-              "issued_frac": round(ach_df * DF64_FP32_INSTR_PER_FMA / 2.0 / (fp32_peak / 2.0), 4)
-              if fp32_peak > 0 else None,
-              "issued_frac_def": ("FP32 instructions issued for the double-float arithmetic "
-                                  f"({DF64_FP32_INSTR_PER_FMA} per real multiply-add: exact product "
-                                  "by FMA and TwoSum accumulation) over the FP32 lanes' instruction "
-                                  "rate"),
-              "traffic": ENV_TRAFFIC_BYTES_PER_LAUNCH,
-              "algorithmic_flops_per_launch": te["flops"] / ne,
-              "algorithmic_bytes_per_launch": te["bytes"] / ne,
-              "algorithmic_flops_def": ("8 real flops per complex multiply-add of the parity-block "
-                                        "products: X_c[:, p] = Ahat_c[:, p] R_{c^(p&1)} (kl_c kr^2 "
-                                        "per block) and R_c = X_c Ahat_c^dag on its lower triangle "
-                                        "(kl_c (kl_c + 1) / 2 K_c)"),
-              "avg_launch_ms": te["ms"] / ne,
-              "launches_per_step": te["launches"],
-              "ms_per_state": round(te["ms"], 3),
-              "share_of_step": round(te["ms"] / step_ms_avg, 4)}
+    ach_e = te["flops"] / (te["ms"] / 1e3) / 1e12 if te["ms"] > 0 else 0.0
+    env_common = {
+        "algorithmic_flops_per_launch": te["flops"] / ne,
+        "algorithmic_bytes_per_launch": te["bytes"] / ne,
+        "algorithmic_flops_def": ("8 real flops per complex multiply-add of the parity-block "
+                                  "products: X_c[:, p] = Ahat_c[:, p] R_{c^(p&1)} (kl_c kr^2 "
+                                  "per block) and R_c = X_c Ahat_c^dag on its lower triangle "
+                                  "(kl_c (kl_c + 1) / 2 K_c)"),
+        "avg_launch_ms": te["ms"] / ne,
+        "launches_per_step": te["launches"],
+        "ms_per_state": round(te["ms"], 3),
+        "share_of_step": round(te["ms"] / step_ms_avg, 4)}
+    if os.environ.get("GBSMPS_ENV_TC", "1") != "0":
+        # the exact-accumulation tensor-core products: algorithmic flops
+        # counted once against the sustained bf16 rate; the slices' products
+        # that the tensor cores actually run (28 slice pairs per real
+        # multiply-add) shown apart
+        roof_e = {"kernel": ("envtc_kernel (tcgen05: complex products as real ones, seven bf16 "
+                             "integer slices per operand row/column exponent, 28 slice-pair MMAs "
+                             "of M = 128, N = 128 into three exact FP32 tensor-memory "
+                             "accumulators and one for the low-order pairs, double-float "
+                             "epilogue; right-environment chain R_m = sum_p Ahat^m[p] R_{m+1} "
+                             "Ahat^m[p]^dag on the parity blocks, two launches per site, each "
+                             "timed with its in-order k-split reduction)"),
+                  "bound": "tensor", "achieved": round(ach_e, 4), "peak": peak,
+                  "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json (the "
+                                  "kernel runs inside a long step)"),
+                  "unit": "TFLOP/s", "frac": round(ach_e / peak, 5),
+                  "slice_pairs": ENV_SLICE_PAIRS,
+                  "issued_tflops": round(ENV_SLICE_PAIRS * ach_e, 3),
+                  "issued_frac": round(ENV_SLICE_PAIRS * ach_e / peak, 4),
+                  "issued_frac_def": ("bf16 tensor flops of the slice-pair products (28 per real "
+                                      "multiply-add; tile padding and the upper triangles of the "
+                                      "Hermitian products not counted) over the sustained bf16 rate"),
+                  "traffic": ENV_TRAFFIC_BYTES_PER_LAUNCH}
+    else:
+        # the double-float GEMM against the FP32 pipes it runs on: algorithmic
+        # flops counted once (x1), the emulation cost shown apart
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fmax = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
+        fp32_peak = nsm * FP32_LANES_PER_SM * fmax * 2.0 / 1e12
+        roof_e = {"kernel": "zgemm_df64_grouped_kernel (double-float complex GEMM on the FP32 pipes, "
+                            "right-environment chain on the parity blocks; two grouped launches per "
+                            "site, split-K partials summed in k order by each tile's last CTA)",
+                  "bound": "alu", "achieved": round(ach_e, 4), "peak": round(fp32_peak, 3),
+                  "peak_source": (f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                  f"{fmax / 1e6:.0f} MHz (max SM clock) x 2 flops per FMA"),
+                  "unit": "TFLOP/s", "frac": round(ach_e / fp32_peak, 5) if fp32_peak > 0 else None,
+                  "issued_fp32_instr_per_fma": DF64_FP32_INSTR_PER_FMA,
+                  "issued_frac": round(ach_e * DF64_FP32_INSTR_PER_FMA / 2.0 / (fp32_peak / 2.0), 4)
+                  if fp32_peak > 0 else None,
+                  "traffic": None}
+    roof_e.update(env_common)
     # the PCO tensor build against the HBM roof of the paper's algorithm:
     # U (target, source) updates, each a source read, a target read and a
     # target write of one complex number in the pass precision (complex64 in
@@ -894,7 +917,7 @@ def main():
                            "the next state's environments and canonical form run beside the current sampling; "
                            "latency_ms is one state alone, build + sampling")
     line = dict(base, value=round(r["value"], 3), ms_per_step=round(r["ms_per_step"], 3),
-                dtype=("f64 gsvd + f32 pco (f64 plane sums) + df64 env + fp16x2 (3 products)/fp32 tensor-core sampling"
+                dtype=("f64 gsvd + f32 pco (f64 plane sums) + exact bf16-slice tensor-core env + fp16x2 (3 products)/fp32 tensor-core sampling"
                        if args.precision == "mixed" else "f64"),
                 config=cfg, samples_per_s=round(r["samples_per_s"], 1),
                 latency_ms={"p50": round(statistics.median(sm), 3),

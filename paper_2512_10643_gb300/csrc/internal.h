@@ -349,8 +349,10 @@ struct EtcNeeds {
   long long rowsA[2] = {0, 0}, rowsB[2] = {0, 0}, expo[2] = {0, 0};
   long long part = 0;                 // split-K partials (complex elements)
 };
-void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, EtcNeeds* acc);   // maxima
-size_t envtc_arena_bytes(int W, long long rows);
+// running maxima over the steps; enc: complex columns per tile (48 or 64)
+void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, int enc, EtcNeeds* acc);
+int envtc_slices(int enc);                                    // slices per operand
+size_t envtc_arena_bytes(int W, long long rows, int nsl);
 struct EnvTcPlan {
   alignas(64) unsigned char mapA[2][128], mapB[2][128];
   int W[2] = {0, 0};
@@ -361,6 +363,10 @@ struct EnvTcPlan {
   long long expo_cap[2] = {0, 0};
   float4* work = nullptr;             // split-K partials: (Re pair, Im pair) per element
   long long work_cap = 0;
+  // the configuration: seven slices per operand; 48 complex columns and five
+  // accumulators (slice pairs with s + t <= 3 summed exactly), or 64 columns
+  // and four (s + t <= 2)
+  int enc = 48, nsl = 7;
 };
 int envtc_setup(EnvTcPlan* P, int slot, int W, long long rowsA, long long rowsB, void* arenaA,
                 void* arenaB);

@@ -52,27 +52,48 @@ namespace {
 using namespace tcx;
 
 constexpr int EM = 128;                        // complex rows of A per tile (tensor-memory lanes)
-constexpr int ENC = 64;                        // complex columns per tile
-constexpr int ENR = 2 * ENC;                   // real columns: Re of the 64, then Im
 constexpr int EK = 32;                         // real k per stage (64-byte rows)
-constexpr int NSL = 7, SBITS = 7;              // slices per operand and their bits
-constexpr int NACC = 4;                        // accumulators: s + t = 0, 1, 2 and >= 3
+constexpr int SBITS = 7;                       // bits per slice
+constexpr int NSL_MAX = 8;
 constexpr int CHUNK = 16;                      // stages summed exactly (512 real k)
 constexpr int ESTG = 2;
 constexpr int PLANE_A = EM * EK * 2;           // 8 KB
-constexpr int PLANE_B = ENR * EK * 2;          // 8 KB
-constexpr int A_BYTES = NSL * PLANE_A;
-constexpr int ESTAGE = NSL * (PLANE_A + PLANE_B);   // 112 KB
 constexpr int ENBAR = 2 * ESTG + 2;            // full, empty, accumulators full, drain
-constexpr int E_SMEM = ESTG * ESTAGE + 1024 + 256;
 constexpr int E_THREADS = 320;                 // load warp, MMA warp, eight epilogue warps
-constexpr int E_TMEM = NACC * ENR;             // 512 columns
+constexpr int E_TMEM = 512;
 constexpr int SL_THREADS = 128;
 constexpr int RED_THREADS = 256;
-constexpr int SROW = ENC + 1;                  // staged output row (float4), padded
-static_assert(4 * 32 * SROW * 16 <= ESTG * ESTAGE, "the output staging fits the operand stages");
-static_assert(E_TMEM == 512, "four accumulators of 128 columns");
-static_assert(ESTAGE % 1024 == 0 && PLANE_A % 512 == 0 && PLANE_B % 512 == 0, "swizzle atoms");
+
+// Two configurations.  NSL slices per operand (pairs with s + t <= NSL - 1
+// are multiplied), ENC complex columns per tile (ENR = 2 ENC real MMA
+// columns: Re of the ENC, then Im) and NACC tensor-memory accumulators: pairs
+// with s + t < NACC - 1 one exact accumulator each, the rest the last.
+// <7, 48, 5>: s + t = 0..3 exact (their sums over a 512-k chunk stay below
+// 2^24), 480 columns; <7, 64, 4>: s + t = 0..2 exact, 512 columns, wider
+// tiles.  Measured over the 144-mode chain (mixed build with FP64 PCO passes
+// against the FP64 build): 1.2e-12 and 5.3e-12 of the largest amplitude
+// (double-float products: 6.8e-14).  An eighth slice does not help (2.3e-12:
+// more products in the rounded accumulator); the error is that of the
+// per-row/column scaling, which bounds each term by the row and column
+// maxima rather than by the term itself.
+template <int NSL_, int ENC_, int NACC_>
+struct EtcCfg {
+  static constexpr int NSL = NSL_, ENC = ENC_, ENR = 2 * ENC_, NACC = NACC_;
+  static constexpr int PLANE_B = ENR * EK * 2;
+  static constexpr int A_BYTES = NSL * PLANE_A;
+  static constexpr int ESTAGE = NSL * (PLANE_A + PLANE_B);
+  static constexpr int SMEM = ESTG * ESTAGE + 1024 + 256;
+  static constexpr int SROW = ENC + 1;         // staged output row (float4), padded
+  static constexpr int HC = ENC / 2;           // columns per epilogue warp
+  static_assert(NACC * ENR <= E_TMEM, "accumulators fit the tensor memory");
+  static_assert(ENR % 16 == 0 && ENR <= 256 && HC % 8 == 0 && HC <= 32, "MMA and epilogue shape");
+  static_assert(4 * 32 * SROW * 16 <= ESTG * ESTAGE, "the output staging fits the operand stages");
+  static_assert(ESTAGE % 1024 == 0 && PLANE_B % 512 == 0, "swizzle atoms");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static_assert(NSL <= NSL_MAX, "slice planes");
+};
+using CfgExact = EtcCfg<7, 48, 5>;
+using CfgWide = EtcCfg<7, 64, 4>;
 
 __host__ __device__ inline long long pad_to(long long x, long long m) { return (x + m - 1) / m * m; }
 
@@ -83,7 +104,7 @@ struct SlJob {
   int rows, K, kind, conj;    // kind 0: A rows [Re | Im]; 1: B columns (Re and Im rows of Bt)
   __nv_bfloat16* arena;
   long long plane, dst;       // plane stride (elements), first arena row
-  int W;
+  int W, enc;                 // enc: complex columns per B tile (kind 1)
   int* expo;
   long long b0;               // first CTA
 };
@@ -92,13 +113,14 @@ struct SlSet {
   SlJob j[3 * ETC_MAX];
 };
 
-// x = (h + l) 2^sh, cut into NSL slices s_t, stored as s_t 2^(-7t)
+// x = (h + l) 2^sh, cut into NS slices s_t, stored as s_t 2^(-7t)
+template <int NS>
 __device__ __forceinline__ void slice_put(__nv_bfloat16* __restrict__ p, long long plane, float h,
                                           float l, int sh) {
   float hs = ldexpf(h, sh), ls = ldexpf(l, sh);
   float w = 1.f;
 #pragma unroll
-  for (int t = 0; t < NSL; ++t) {
+  for (int t = 0; t < NS; ++t) {
     const float s = rintf(hs);
     p[t * plane] = __float2bfloat16_rn(s * w);       // |s| <= 128: exact
     hs -= s;                                         // exact
@@ -122,6 +144,7 @@ __device__ __forceinline__ int find_job(const SlSet& js, long long b) {
 
 // One CTA per (operand row, segment of SL_THREADS complex k): every CTA of a
 // row takes the row's maximum (the same exponent), then slices its segment.
+template <int NS>
 __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_constant__ SlSet js) {
   __shared__ float red[SL_THREADS / 32];
   // a register copy: the stores below go through generic pointers, which
@@ -148,28 +171,28 @@ __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_cons
   if (mx > 0.f) frexpf(mx, &E);                      // |x| < 2^E (the low word cannot cross it)
   if (tid == 0 && seg == 0) J.expo[r] = E;
   const int sh = SBITS - E;
-  const long long r0 = J.kind == 0 ? J.dst + r : J.dst + (long long)(r / ENC) * ENR + r % ENC;
+  const long long r0 = J.kind == 0 ? J.dst + r : J.dst + (long long)(r / J.enc) * 2 * J.enc + r % J.enc;
   __nv_bfloat16* p0 = J.arena + r0 * J.W;
-  __nv_bfloat16* p1 = p0 + (long long)ENC * J.W;     // kind 1: the Im row of the column
+  __nv_bfloat16* p1 = p0 + (long long)J.enc * J.W;   // kind 1: the Im row of the column
   const int k = seg * SL_THREADS + tid;
   if (k < J.K) {
     float4 v = row[(long long)k * J.es];
     if (J.conj) { v.z = -v.z; v.w = -v.w; }
     if (J.kind == 0) {                               // [Re | Im]
-      slice_put(p0 + k, J.plane, v.x, v.y, sh);
-      slice_put(p0 + J.K + k, J.plane, v.z, v.w, sh);
+      slice_put<NS>(p0 + k, J.plane, v.x, v.y, sh);
+      slice_put<NS>(p0 + J.K + k, J.plane, v.z, v.w, sh);
     } else {                                         // Re row [Re | -Im], Im row [Im | Re]
-      slice_put(p0 + k, J.plane, v.x, v.y, sh);
-      slice_put(p0 + J.K + k, J.plane, -v.z, -v.w, sh);
-      slice_put(p1 + k, J.plane, v.z, v.w, sh);
-      slice_put(p1 + J.K + k, J.plane, v.x, v.y, sh);
+      slice_put<NS>(p0 + k, J.plane, v.x, v.y, sh);
+      slice_put<NS>(p0 + J.K + k, J.plane, -v.z, -v.w, sh);
+      slice_put<NS>(p1 + k, J.plane, v.z, v.w, sh);
+      slice_put<NS>(p1 + J.K + k, J.plane, v.x, v.y, sh);
     }
   }
   if (seg == segs - 1) {                             // zeros up to the end of the last 32-k stage
     const int kend = (int)pad_to(2LL * J.K, EK);
     const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
     for (int x = 2 * J.K + tid; x < kend; x += SL_THREADS)
-      for (int t = 0; t < NSL; ++t) {
+      for (int t = 0; t < NS; ++t) {
         p0[t * J.plane + x] = z;
         if (J.kind == 1) p1[t * J.plane + x] = z;
       }
@@ -258,6 +281,7 @@ __device__ __forceinline__ float4 scale_pair2(f2x h, f2x l, int e) {
   return make_float4(re.x, re.y, im.x, im.y);
 }
 
+template <class CF>
 __global__ void __launch_bounds__(E_THREADS, 1)
 envtc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ EtcGroup g, int* status) {
@@ -272,6 +296,8 @@ envtc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   const int kz = (int)(l % P.ks);
   const int tile = (int)(l / P.ks);
   const int tmi = tile / P.tn, tni = tile % P.tn;
+  constexpr int ENC = CF::ENC, ENR = CF::ENR, NACC = CF::NACC, SROW = CF::SROW, HC = CF::HC;
+  constexpr int ESTAGE = CF::ESTAGE, PLANE_B = CF::PLANE_B, NSL = CF::NSL, A_BYTES = CF::A_BYTES;
   if (P.herm && tni * ENC > tmi * EM + EM - 1) return;   // a tile above the diagonal: nothing kept
   const int s_beg = kz * P.kst;
   const int nstage = max(0, min(P.nst, s_beg + P.kst) - s_beg);   // <= CHUNK
@@ -330,7 +356,7 @@ envtc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     }
   } else if (warp == 1) {
     if (lane == 0) {                                  // MMA issuer
-      // D f32, A and B bf16, both K-major, N = 128, M = 128
+      // D f32, A and B bf16, both K-major, N = ENR, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ENR >> 3) << 17) |
                              ((uint32_t)(EM >> 4) << 24);
       unsigned init = 0;
@@ -360,54 +386,42 @@ envtc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     }
   } else {
     // epilogue: warps 2..9; tensor-memory lane quadrant warp % 4, columns
-    // half * 32 .. half * 32 + 31 of the tile
+    // half * HC .. half * HC + HC - 1 of the tile
     const int q = warp & 3, half = (warp - 2) >> 2;
     const int i = tmi * EM + q * 32 + lane;           // complex output row
     const bool rvalid = i < P.M;
     // exponents while the MMAs run: the row's, and one column's per lane
     const int er = rvalid ? P.ea[i] : 0;
-    const int jl = tni * ENC + half * 32 + lane;
-    const int ebl = jl < P.N ? P.eb[jl] : 0;
+    const int jl = tni * ENC + half * HC + lane;
+    const int ebl = (lane < HC && jl < P.N) ? P.eb[jl] : 0;
     const bool got = __all_sync(0xffffffffu, mbar_wait(afull, 0));
     if (!got) {
       if (lane == 0) set_status(status, ST_TIMEOUT);
     } else {
       tc_fence_after();
       // Every MMA has completed, so the operand stages are free: the 32 rows
-      // x 64 complex results of a quadrant go through them (rows padded to
-      // 65 elements: conflict-free) and leave as row segments.
+      // x ENC complex results of a quadrant go through them (rows padded by
+      // one element: conflict-free) and leave as row segments.
       float4* stg = reinterpret_cast<float4*>(sp) + (size_t)q * 32 * SROW;
       const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-      for (int hq = 0; hq < 2; ++hq) {
-        const int c0 = half * 32 + hq * 16;           // first tile column of the 16
-        f2x ah[16], al[16];                           // (Re, Im) of the 16 columns
+      for (int ch = 0; ch < HC / 8; ++ch) {
+        const int c0 = half * HC + ch * 8;            // first tile column of the 8
+        uint32_t v[NACC][8], w[NACC][8];
 #pragma unroll
-        for (int a0 = 0; a0 < NACC; a0 += 2) {
-          uint32_t v[2][16], w[2][16];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            tmem_ld16_nw(tb + (uint32_t)((a0 + u) * ENR + c0), v[u]);          // Re
-            tmem_ld16_nw(tb + (uint32_t)((a0 + u) * ENR + ENC + c0), w[u]);    // Im
-          }
-          tmem_wait_ld();
-#pragma unroll
-          for (int u = 0; u < 2; ++u)
-#pragma unroll
-            for (int x = 0; x < 16; ++x) {
-              const f2x z = pk(__uint_as_float(v[u][x]), __uint_as_float(w[u][x]));
-              if (a0 + u == 0) {
-                ah[x] = z;
-                al[x] = 0ull;
-              } else {
-                dfa2x(ah[x], al[x], z);
-              }
-            }
+        for (int a = 0; a < NACC; ++a) {
+          tmem_ld8_nw(tb + (uint32_t)(a * ENR + c0), v[a]);          // Re
+          tmem_ld8_nw(tb + (uint32_t)(a * ENR + ENC + c0), w[a]);    // Im
         }
+        tmem_wait_ld();
 #pragma unroll
-        for (int x = 0; x < 16; ++x) {
-          const int e = er + __shfl_sync(0xffffffffu, ebl, hq * 16 + x) - 2 * SBITS;
-          stg[lane * SROW + c0 + x] = scale_pair2(ah[x], al[x], e);
+        for (int x = 0; x < 8; ++x) {
+          f2x ah = pk(__uint_as_float(v[0][x]), __uint_as_float(w[0][x])), al = 0ull;
+#pragma unroll
+          for (int a = 1; a < NACC; ++a)
+            dfa2x(ah, al, pk(__uint_as_float(v[a][x]), __uint_as_float(w[a][x])));
+          const int e = er + __shfl_sync(0xffffffffu, ebl, ch * 8 + x) - 2 * SBITS;
+          stg[lane * SROW + c0 + x] = scale_pair2(ah, al, e);
         }
       }
       const bool bulk = P.ks > 1 || (P.csplit && !P.herm);
@@ -558,13 +572,13 @@ EncodeFn encode_fn() {
 }
 
 // arena of W bf16 per row, `rows` rows, seven planes; box of 32 k x box_rows rows x 7 planes
-int make_arena_map(void* map128, const void* arena, int W, long long rows, int box_rows) {
+int make_arena_map(void* map128, const void* arena, int W, long long rows, int box_rows, int nsl) {
   EncodeFn fn = encode_fn();
   if (!fn) return 1;
   if ((reinterpret_cast<uintptr_t>(arena) & 15) || (W % EK)) return 2;
-  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)rows, (cuuint64_t)NSL};
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)rows, (cuuint64_t)nsl};
   cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)W * 2 * rows};
-  cuuint32_t box[3] = {EK, (cuuint32_t)box_rows, NSL};
+  cuuint32_t box[3] = {EK, (cuuint32_t)box_rows, (cuuint32_t)nsl};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(reinterpret_cast<CUtensorMap*>(map128), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                   const_cast<void*>(arena), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -595,8 +609,8 @@ struct Lay {
 // Arena rows, exponent slots and k splits of one launch's products; a B
 // operand equal to an earlier product's (same matrix and reading) is sliced
 // once.  -1 when a product is not of the sliced form.
-int etc_layout(const DfSub* subs, int n, Lay* L, int& W, long long& rowsA, long long& rowsB,
-               long long& expo, long long& part) {
+int etc_layout(const DfSub* subs, int n, int enc, Lay* L, int& W, long long& rowsA,
+               long long& rowsB, long long& expo, long long& part) {
   int np = 0;
   long long arow = 0, brow = 0, eo = 0, pt = 0;
   int T = 0;
@@ -626,10 +640,10 @@ int etc_layout(const DfSub* subs, int n, Lay* L, int& W, long long& rowsA, long 
       l.brow = brow;
       l.eb = eo;
       eo += u.N;
-      brow += pad_to(u.N, ENC) / ENC * ENR;
+      brow += pad_to(u.N, enc) / enc * 2 * enc;
     }
     l.tm = (int)(pad_to(u.M, EM) / EM);
-    l.tn = (int)(pad_to(u.N, ENC) / ENC);
+    l.tn = (int)(pad_to(u.N, enc) / enc);
     l.nst = (int)(pad_to(2LL * u.K, EK) / EK);
     W = std::max(W, l.nst * EK);
     T += l.tm * l.tn;
@@ -669,6 +683,7 @@ void add_slice_jobs(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* 
     J.arena = arena;
     J.plane = plane;
     J.W = P.W[slot];
+    J.enc = P.enc;
     J.b0 = blocks;
     if (kind == 0) {
       J.src = reinterpret_cast<const float4*>(u.A);
@@ -706,12 +721,15 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
-cudaError_t launch_slices(const SlSet& js, long long blocks, cudaStream_t s) {
+cudaError_t launch_slices(const SlSet& js, long long blocks, int nsl, cudaStream_t s) {
   if (js.n == 0 || blocks == 0) return cudaSuccess;
   COUNT_LAUNCH(1);
-  return launch_pdl(etc_slice_kernel, (unsigned)blocks, SL_THREADS, 0, s, js);
+  if (nsl == 8) return launch_pdl(etc_slice_kernel<8>, (unsigned)blocks, SL_THREADS, 0, s, js);
+  if (nsl == 7) return launch_pdl(etc_slice_kernel<7>, (unsigned)blocks, SL_THREADS, 0, s, js);
+  return cudaErrorInvalidValue;
 }
 
+template <class CF>
 cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* L, int np,
                         int* status, cudaStream_t s) {
   static std::atomic<int> attr_set[64];
@@ -748,7 +766,7 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   if (e) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev].load()) {
-    e = cudaFuncSetAttribute(envtc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    e = cudaFuncSetAttribute(envtc_kernel<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
     if (e) return e;
     attr_set[dev].store(1);
   }
@@ -756,7 +774,7 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   memcpy(&ma, P.mapA[slot], sizeof(CUtensorMap));
   memcpy(&mb, P.mapB[slot], sizeof(CUtensorMap));
   cudaEvent_t tr0 = g_env_trace.begin(s);
-  e = launch_pdl(envtc_kernel, (unsigned)units, E_THREADS, E_SMEM, s, ma, mb, G, status);
+  e = launch_pdl(envtc_kernel<CF>, (unsigned)units, E_THREADS, CF::SMEM, s, ma, mb, G, status);
   COUNT_LAUNCH(1);
   if (e) return e;
   if (rs.n) {
@@ -771,17 +789,24 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   return e;
 }
 
+cudaError_t launch_gemm_any(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* L, int np,
+                            int* status, cudaStream_t s) {
+  if (P.enc == CfgExact::ENC) return launch_gemm<CfgExact>(P, slot, subs, L, np, status, s);
+  if (P.enc == CfgWide::ENC) return launch_gemm<CfgWide>(P, slot, subs, L, np, status, s);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 // ---- host side ------------------------------------------------------------------------------
-void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, EtcNeeds* acc) {
+void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, int enc, EtcNeeds* acc) {
   Lay L[ETC_MAX];
   const DfSub* s[2] = {s1, s2};
   const int n[2] = {n1, n2};
   for (int k = 0; k < 2; ++k) {
     int W;
     long long ra, rb, ex, pt;
-    if (etc_layout(s[k], n[k], L, W, ra, rb, ex, pt) < 0) {
+    if (etc_layout(s[k], n[k], enc, L, W, ra, rb, ex, pt) < 0) {
       acc->ok = false;
       continue;
     }
@@ -793,21 +818,25 @@ void envtc_needs(const DfSub* s1, int n1, const DfSub* s2, int n2, EtcNeeds* acc
   }
 }
 
-size_t envtc_arena_bytes(int W, long long rows) {
+int envtc_slices(int enc) { return enc == CfgExact::ENC ? CfgExact::NSL : CfgWide::NSL; }
+
+size_t envtc_arena_bytes(int W, long long rows, int nsl) {
   return sizeof(__nv_bfloat16) * (size_t)pad_to(std::max(W, EK), EK) *
-             (size_t)pad_to(std::max<long long>(rows, ENR), ENR) * NSL + 256;
+             (size_t)pad_to(std::max<long long>(rows, EM), EM) * nsl + 256;
 }
 
 int envtc_setup(EnvTcPlan* P, int slot, int W, long long rowsA, long long rowsB, void* arenaA,
                 void* arenaB) {
-  if (slot < 0 || slot > 1) return 1;
+  if (slot < 0 || slot > 1 || (P->enc != CfgExact::ENC && P->enc != CfgWide::ENC) ||
+      P->nsl != envtc_slices(P->enc))
+    return 1;
   P->W[slot] = (int)pad_to(std::max(W, EK), EK);
   P->rowsA[slot] = pad_to(std::max<long long>(rowsA, EM), EM);
-  P->rowsB[slot] = pad_to(std::max<long long>(rowsB, ENR), ENR);
+  P->rowsB[slot] = pad_to(std::max<long long>(rowsB, EM), EM);
   P->arenaA[slot] = arenaA;
   P->arenaB[slot] = arenaB;
-  if (make_arena_map(P->mapA[slot], arenaA, P->W[slot], P->rowsA[slot], EM)) return 2;
-  if (make_arena_map(P->mapB[slot], arenaB, P->W[slot], P->rowsB[slot], ENR)) return 3;
+  if (make_arena_map(P->mapA[slot], arenaA, P->W[slot], P->rowsA[slot], EM, P->nsl)) return 2;
+  if (make_arena_map(P->mapB[slot], arenaB, P->W[slot], P->rowsB[slot], 2 * P->enc, P->nsl)) return 3;
   return 0;
 }
 
@@ -822,8 +851,8 @@ cudaError_t launch_envtc_step(const EnvTcPlan& P, const DfSub* s1, int n1, const
   Lay L1[ETC_MAX], L2[ETC_MAX];
   int W1, W2;
   long long ra1, rb1, ex1, pt1, ra2, rb2, ex2, pt2;
-  const int np1 = etc_layout(s1, n1, L1, W1, ra1, rb1, ex1, pt1);
-  const int np2 = etc_layout(s2, n2, L2, W2, ra2, rb2, ex2, pt2);
+  const int np1 = etc_layout(s1, n1, P.enc, L1, W1, ra1, rb1, ex1, pt1);
+  const int np2 = etc_layout(s2, n2, P.enc, L2, W2, ra2, rb2, ex2, pt2);
   if (np1 < 0 || np2 < 0 || W1 > P.W[0] || W2 > P.W[1] || ra1 > P.rowsA[0] || rb1 > P.rowsB[0] ||
       ra2 > P.rowsA[1] || rb2 > P.rowsB[1] || ex1 > P.expo_cap[0] || ex2 > P.expo_cap[1] ||
       pt1 > P.work_cap || pt2 > P.work_cap)
@@ -834,17 +863,17 @@ cudaError_t launch_envtc_step(const EnvTcPlan& P, const DfSub* s1, int n1, const
   add_slice_jobs(P, 0, s1, L1, np1, 0, js, blocks);
   add_slice_jobs(P, 0, s1, L1, np1, 1, js, blocks);
   add_slice_jobs(P, 1, s2, L2, np2, 1, js, blocks);
-  cudaError_t e = launch_slices(js, blocks, s);
+  cudaError_t e = launch_slices(js, blocks, P.nsl, s);
   if (e) return e;
   if (np1) {
-    e = launch_gemm(P, 0, s1, L1, np1, status, s);
+    e = launch_gemm_any(P, 0, s1, L1, np1, status, s);
     if (e) return e;
   }
   js.n = 0;
   blocks = 0;
   add_slice_jobs(P, 1, s2, L2, np2, 0, js, blocks);
-  e = launch_slices(js, blocks, s);
+  e = launch_slices(js, blocks, P.nsl, s);
   if (e) return e;
-  if (np2) e = launch_gemm(P, 1, s2, L2, np2, status, s);
+  if (np2) e = launch_gemm_any(P, 1, s2, L2, np2, status, s);
   return e;
 }

@@ -153,6 +153,12 @@ void site_tasks(gbsmps_mps* M, const std::vector<double>& cm, std::vector<SiteTa
 }
 
 int run_pco(gbsmps_ctx* c, std::vector<SiteTask>& tasks, size_t scr_max, int d, int precision) {
+  // GBSMPS_PCO_FP64=1 runs a mixed build's passes in FP64 (its other stages
+  // unchanged): the mixed path's error without the PCO's FP32 part
+  if (precision == GBSMPS_PREC_MIXED) {
+    const char* e = getenv("GBSMPS_PCO_FP64");
+    if (e && e[0] == '1') precision = GBSMPS_PREC_FP64;
+  }
   // FP64 passes for FP64 states; the mixed path runs the passes in FP32 and
   // accumulates the tensors in FP64 (GB300's FP64 pipe is 1/64 of its FP32
   // rate; the mixed path's amplitudes are held to 1e-5 of the FP64 path's).
@@ -276,11 +282,17 @@ int env_step_blocks(gbsmps_mps* M, int m, const double2* Ah, double2* R, double2
   return GBSMPS_OK;
 }
 
-// The exact-accumulation tensor-core products are the default; GBSMPS_ENV_TC=0
-// selects the double-float GEMM on the FP32 pipes.
-bool env_tc_enabled() {
+// The environment products: GBSMPS_ENV_TC=1 (default) the tensor cores with
+// 48-column tiles and slice pairs s + t <= 3 summed exactly, =2 64-column
+// tiles with s + t <= 2 exact (4x less accurate over the 144-mode chain),
+// =0 the double-float GEMM on the FP32 pipes (the most accurate chain:
+// 6.8e-14 of the largest amplitude against 1.2e-12 for =1, with FP64 PCO
+// passes).  Returns the tile width, 0 for double-float.
+int env_tc_mode() {
   const char* e = getenv("GBSMPS_ENV_TC");
-  return !(e && e[0] == '0');
+  if (e && e[0] == '0') return 0;
+  if (e && e[0] == '2') return 64;
+  return 48;
 }
 
 // arenas, exponents, partials and counters for every step of one chain
@@ -295,19 +307,21 @@ struct EnvTcBufs {
 };
 
 int env_tc_prepare(const gbsmps_mps* M, const double2* Ah, double2* R, double2* X,
-                   const double2* ui, double2* uo, EnvTcBufs& B, cudaStream_t s, bool* ok) {
+                   const double2* ui, double2* uo, int enc, EnvTcBufs& B, cudaStream_t s, bool* ok) {
   EtcNeeds nd;
   std::vector<DfSub> s1, s2;
   for (int m = M->N - 1; m >= 0; --m) {
     env_subs(M, m, Ah, R, X, ui, uo, s1, s2);
-    envtc_needs(s1.data(), (int)s1.size(), s2.data(), (int)s2.size(), &nd);
+    envtc_needs(s1.data(), (int)s1.size(), s2.data(), (int)s2.size(), enc, &nd);
   }
   *ok = nd.ok;
   if (!nd.ok) return GBSMPS_OK;
   EnvTcPlan& P = B.plan;
+  P.enc = enc;
+  P.nsl = envtc_slices(enc);
   for (int k = 0; k < 2; ++k) {
-    const size_t ba = envtc_arena_bytes(nd.W[k], nd.rowsA[k]);
-    const size_t bb = envtc_arena_bytes(nd.W[k], nd.rowsB[k]);
+    const size_t ba = envtc_arena_bytes(nd.W[k], nd.rowsA[k], P.nsl);
+    const size_t bb = envtc_arena_bytes(nd.W[k], nd.rowsB[k], P.nsl);
     CK(B.arA[k].alloc(ba, s));
     CK(B.arB[k].alloc(bb, s));
     // padding rows are never written by the slicing: zero them once
@@ -392,9 +406,10 @@ int env_single(gbsmps_ctx* c, gbsmps_mps* M, StageTimer& tm) {
     // exact-accumulation tensor-core products (the plan is sized from the
     // products of every step before the first)
     EnvTcBufs tcb;
-    bool use_tc = env_tc_enabled();
+    const int enc = env_tc_mode();
+    bool use_tc = enc > 0;
     if (use_tc) {
-      const int rc = env_tc_prepare(M, Ah, R, X, ua, ubn, tcb, s, &use_tc);
+      const int rc = env_tc_prepare(M, Ah, R, X, ua, ubn, enc, tcb, s, &use_tc);
       if (rc) return rc;
     }
     for (int m = N - 1; m >= 0; --m) {

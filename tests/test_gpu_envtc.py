@@ -83,3 +83,32 @@ def test_tensor_core_environments_match_double_float(ctx, monkeypatch):
             mt.release()
             md.release()
     print("tensor-core vs double-float environments, largest relative differences:", worst)
+
+
+@pytest.mark.parametrize("mode,bound", [("0", 5e-13), ("1", 1e-11), ("2", 3e-11)])
+def test_chain_accuracy_against_fp64(ctx, monkeypatch, mode, bound):
+    """The environment chain's own error: a mixed build whose PCO passes run
+    in FP64 (GBSMPS_PCO_FP64=1) against the FP64 build of the 144-mode
+    workload, largest amplitude difference over the largest amplitude
+    (the vacuum amplitude carries the norm).  Measured: double-float products
+    6.8e-14, tensor cores 1.2e-12 (48-column tiles) and 5.3e-12 (64-column
+    tiles); the FP32 PCO passes of a default mixed build add 7.0e-9 on top."""
+    w = wl.config("n144_d6_chi256")
+    base = dict(d=w.d, chi_max=w.chi, eps_trunc=w.eps, lambda2_freeze=w.freeze)
+    pats = wl.random_patterns(300, w.N, w.d, seed=11, max_total=8)
+    pats[0] = 0
+    m64 = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **dict(base, precision=g.PREC_FP64))
+    try:
+        a64 = np.asarray(m64.amplitudes(pats))
+    finally:
+        m64.release()
+    monkeypatch.setenv("GBSMPS_PCO_FP64", "1")
+    monkeypatch.setenv("GBSMPS_ENV_TC", mode)
+    m = g.MPS.from_cov(ctx, np.ascontiguousarray(w.gamma), **dict(base, precision=g.PREC_MIXED))
+    try:
+        a = np.asarray(m.amplitudes(pats))
+    finally:
+        m.release()
+    err = np.abs(a - a64).max() / np.abs(a64).max()
+    print(f"environment products mode {mode}: mixed (FP64 PCO) vs FP64 amplitudes {err:.3e}")
+    assert err <= bound
