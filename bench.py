@@ -36,10 +36,11 @@ WORKLOAD_DESC = ("144-mode pure Gaussian state: squeezed vacua r~U(0.1,0.4) thro
 # DRAM bytes (read + write) per launch from one-kernel ncu captures of the
 # current kernels (profiles/): the sampler GEMM at 100,000 samples (the mean
 # of a site's pre-pass launch, 169.6 MB, and its rest launch, 13.5 MB), and
-# the environment products of the 144-mode workload (a tensor-core GEMM
-# launch with its k-split reduction, the mean over one step's two launches)
+# the environment products of the 144-mode workload (one product pass:
+# slicing, GEMM and k-split reduction, the mean over two steps' four passes;
+# cold-cache, so an upper bound: the bench run keeps them in L2)
 TRAFFIC_BYTES_PER_LAUNCH = 91.6e6
-ENV_TRAFFIC_BYTES_PER_LAUNCH = None
+ENV_TRAFFIC_BYTES_PER_LAUNCH = 25.8e6
 # slice pairs (s, t), s + t <= 6, of seven-slice operands: the bf16 products
 # the environment GEMM issues per real multiply-add
 ENV_SLICE_PAIRS = 28
@@ -381,11 +382,12 @@ def run_gpu(args, rank, local, ws, dist):
         # multiply-add) shown apart
         roof_e = {"kernel": ("envtc_kernel (tcgen05: complex products as real ones, seven bf16 "
                              "integer slices per operand row/column exponent, 28 slice-pair MMAs "
-                             "of M = 128, N = 128 into three exact FP32 tensor-memory "
+                             "of M = 128, N = 96 into four exact FP32 tensor-memory "
                              "accumulators and one for the low-order pairs, double-float "
                              "epilogue; right-environment chain R_m = sum_p Ahat^m[p] R_{m+1} "
-                             "Ahat^m[p]^dag on the parity blocks, two launches per site, each "
-                             "timed with its in-order k-split reduction)"),
+                             "Ahat^m[p]^dag on the parity blocks; two product passes per site, "
+                             "each timed from its operands' slicing through the GEMM to its "
+                             "in-order k-split reduction)"),
                   "bound": "tensor", "achieved": round(ach_e, 4), "peak": peak,
                   "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json (the "
                                   "kernel runs inside a long step)"),

@@ -299,13 +299,15 @@ int gbsmps_trace_read(gbsmps_ctx_t ctx, double* total_ms, int64_t* launches,
                       double* flops, double* bytes);
 
 /* The same record for one of three traced kernels: which = 0, the sampler
- * GEMM above (gbsmps_trace_read); which = 1, the double-float complex GEMM of
- * the right-environment chain R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (the
- * norm, and the standard MPS sampling that Sec. I and Sec. III defer to; two
- * grouped launches per site), whose
- * work counts 8 real flops per complex multiply-add of the lower triangle
- * of a Hermitian result and of every element otherwise, and whose bytes are
- * the operands and results at 16 bytes per complex element; which = 2, the
+ * GEMM above (gbsmps_trace_read); which = 1, the products of the
+ * right-environment chain R_m = sum_p A^m[p] R_{m+1} A^m[p]^dag (the norm,
+ * and the standard MPS sampling that Sec. I and Sec. III defer to), two
+ * traced passes per site: on the tensor cores (the default) each pass is
+ * the slicing of its operands, the GEMM and the k-split reduction; with
+ * GBSMPS_ENV_TC=0 each is one grouped double-float GEMM launch.  The work
+ * counts 8 real flops per complex multiply-add of the lower triangle of a
+ * Hermitian result and of every element otherwise, and the bytes are the
+ * operands and results at 16 bytes per complex element; which = 2, the
  * PCO tensor build of a state (Sec. II C, App. B; one launch per wave of
  * sites), time and launch count only (its algorithmic work is counted by the
  * caller from the kept bases, gbsmps_get_basis).  Recording is switched on

@@ -387,7 +387,9 @@ def gbsmps_trace_read(ctx):
 
 def gbsmps_trace_read_kernel(ctx, which: int):
     """which = 0: the sampler GEMM (as gbsmps_trace_read); 1: the environment
-    GEMM; 2: the PCO tensor build (time and launches only)."""
+    products (two passes per site: slicing, GEMM and k-split reduction on the
+    tensor cores, or one double-float GEMM launch); 2: the PCO tensor build
+    (time and launches only)."""
     ms, fl, by = C.c_double(), C.c_double(), C.c_double()
     n = C.c_int64()
     _check(lib().gbsmps_trace_read_kernel(ctx, int(which), C.byref(ms), C.byref(n), C.byref(fl),

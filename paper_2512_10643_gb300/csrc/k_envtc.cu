@@ -731,7 +731,7 @@ cudaError_t launch_slices(const SlSet& js, long long blocks, int nsl, cudaStream
 
 template <class CF>
 cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* L, int np,
-                        int* status, cudaStream_t s) {
+                        int* status, cudaStream_t s, double& fl, double& by) {
   static std::atomic<int> attr_set[64];
   EtcGroup G;
   RedSet rs;
@@ -739,7 +739,6 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   rs.n = 0;
   long long units = 0, elems = 0;
   int maxks = 1;
-  double fl = 0.0, by = 0.0;
   for (int q = 0; q < np; ++q) {
     const Lay& l = L[q];
     const DfSub& u = subs[l.sub];
@@ -773,7 +772,6 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
   CUtensorMap ma, mb;
   memcpy(&ma, P.mapA[slot], sizeof(CUtensorMap));
   memcpy(&mb, P.mapB[slot], sizeof(CUtensorMap));
-  cudaEvent_t tr0 = g_env_trace.begin(s);
   e = launch_pdl(envtc_kernel<CF>, (unsigned)units, E_THREADS, CF::SMEM, s, ma, mb, G, status);
   COUNT_LAUNCH(1);
   if (e) return e;
@@ -785,14 +783,13 @@ cudaError_t launch_gemm(const EnvTcPlan& P, int slot, const DfSub* subs, const L
                    s, rs, split);
     COUNT_LAUNCH(1);
   }
-  g_env_trace.end(tr0, s, fl, by);
   return e;
 }
 
 cudaError_t launch_gemm_any(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* L, int np,
-                            int* status, cudaStream_t s) {
-  if (P.enc == CfgExact::ENC) return launch_gemm<CfgExact>(P, slot, subs, L, np, status, s);
-  if (P.enc == CfgWide::ENC) return launch_gemm<CfgWide>(P, slot, subs, L, np, status, s);
+                            int* status, cudaStream_t s, double& fl, double& by) {
+  if (P.enc == CfgExact::ENC) return launch_gemm<CfgExact>(P, slot, subs, L, np, status, s, fl, by);
+  if (P.enc == CfgWide::ENC) return launch_gemm<CfgWide>(P, slot, subs, L, np, status, s, fl, by);
   return cudaErrorInvalidValue;
 }
 
@@ -857,23 +854,26 @@ cudaError_t launch_envtc_step(const EnvTcPlan& P, const DfSub* s1, int n1, const
       ra2 > P.rowsA[1] || rb2 > P.rowsB[1] || ex1 > P.expo_cap[0] || ex2 > P.expo_cap[1] ||
       pt1 > P.work_cap || pt2 > P.work_cap)
     return cudaErrorNotSupported;
+  // traced per product pass: its slicing, GEMM and k-split reduction
   SlSet js;
   long long blocks = 0;
+  double fl = 0.0, by = 0.0;
   js.n = 0;
   add_slice_jobs(P, 0, s1, L1, np1, 0, js, blocks);
   add_slice_jobs(P, 0, s1, L1, np1, 1, js, blocks);
   add_slice_jobs(P, 1, s2, L2, np2, 1, js, blocks);
+  cudaEvent_t tr0 = g_env_trace.begin(s);
   cudaError_t e = launch_slices(js, blocks, P.nsl, s);
+  if (!e && np1) e = launch_gemm_any(P, 0, s1, L1, np1, status, s, fl, by);
+  g_env_trace.end(tr0, s, fl, by);
   if (e) return e;
-  if (np1) {
-    e = launch_gemm_any(P, 0, s1, L1, np1, status, s);
-    if (e) return e;
-  }
   js.n = 0;
   blocks = 0;
+  fl = by = 0.0;
   add_slice_jobs(P, 1, s2, L2, np2, 0, js, blocks);
+  tr0 = g_env_trace.begin(s);
   e = launch_slices(js, blocks, P.nsl, s);
-  if (e) return e;
-  if (np2) e = launch_gemm_any(P, 1, s2, L2, np2, status, s);
+  if (!e && np2) e = launch_gemm_any(P, 1, s2, L2, np2, status, s, fl, by);
+  g_env_trace.end(tr0, s, fl, by);
   return e;
 }
