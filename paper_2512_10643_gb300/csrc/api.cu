@@ -520,7 +520,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   // build while it runs (a performance knob, GBSMPS_STREAM_RESERVE: the
   // patterns do not depend on it)
   const char* sre = getenv("GBSMPS_STREAM_RESERVE");
-  const int stream_reserve = sre ? std::max(0, std::min(128, atoi(sre))) : 36;
+  const int stream_reserve = sre ? std::max(0, std::min(128, atoi(sre))) : 12;
   // the sampler's stream priority against the next build's (GBSMPS_STREAM_PRIO:
   // 1 = the sampler first, 0 = equal)
   const char* spe = getenv("GBSMPS_STREAM_PRIO");
@@ -547,8 +547,8 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   CK(cudaSetDevice(c->device));
   // Per state the build runs in four parts: the front (validation, GSVD
   // chain on one SM, bases) on one of NF contexts of its own, launched NF - 1
-  // states ahead (a chain takes about one step, so it gets NF - 2 steps of
-  // slack); then on c's stream the PCO build, the environments and the
+  // states ahead (it has NF - 2 steps before its PCO; a 144-mode chain takes
+  // about two); then on c's stream the PCO build, the environments and the
   // canonical form.  Iteration k runs PCO(k+1) alone, then the sampling of
   // state k (its own stream, high priority, own status word) beside the
   // environments and the canonical form of state k+1.  The PCO's CTAs hold
@@ -564,7 +564,7 @@ int gbsmps_build_sample_stream(gbsmps_ctx_t c, int32_t count, const int32_t* Ns,
   // fronts run NF - 1 states ahead (GBSMPS_STREAM_AHEAD, 1 .. NFMAX - 1)
   constexpr int NFMAX = 6;
   const char* sae = getenv("GBSMPS_STREAM_AHEAD");
-  const int NF = 1 + (sae ? std::max(1, std::min(NFMAX - 1, atoi(sae))) : 3);
+  const int NF = 1 + (sae ? std::max(1, std::min(NFMAX - 1, atoi(sae))) : 4);
   cudaStream_t ss = nullptr;
   cudaEvent_t pco_done = nullptr, sampled = nullptr;
   gbsmps_ctx cf[NFMAX];
