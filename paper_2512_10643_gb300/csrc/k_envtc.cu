@@ -62,6 +62,7 @@ constexpr int ENBAR = 2 * ESTG + 2;            // full, empty, accumulators full
 constexpr int E_THREADS = 320;                 // load warp, MMA warp, eight epilogue warps
 constexpr int E_TMEM = 512;
 constexpr int SL_THREADS = 128;
+constexpr int SL_K = 2 * SL_THREADS;            // complex k per slicing CTA (two per thread)
 constexpr int RED_THREADS = 256;
 
 // Two configurations.  NSL slices per operand (pairs with s + t <= NSL - 1
@@ -97,6 +98,36 @@ using CfgWide = EtcCfg<7, 64, 4>;
 
 __host__ __device__ inline long long pad_to(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// Packed pairs of FP32 values (Blackwell's f32x2 add/sub/mul, each lane
+// correctly rounded): the slicing cuts the Re and Im parts of an element,
+// and the epilogue folds the Re and Im values of a column, together at half
+// the instruction count.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk(float a, float b) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float2 upk(f2x v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 // ---- slicing ------------------------------------------------------------------
 struct SlJob {
   const float4* src;          // double-float complex pairs; element (r, k) at src[r * ld + k * es]
@@ -113,22 +144,27 @@ struct SlSet {
   SlJob j[3 * ETC_MAX];
 };
 
-// x = (h + l) 2^sh, cut into NS slices s_t, stored as s_t 2^(-7t)
-template <int NS>
-__device__ __forceinline__ void slice_put(__nv_bfloat16* __restrict__ p, long long plane, float h,
-                                          float l, int sh) {
-  float hs = ldexpf(h, sh), ls = ldexpf(l, sh);
+// (re, im) = (v.x + v.y, v.z + v.w) 2^sh, each cut into NS slices s_t,
+// handed over as bf16 values s_t 2^(-7t) (put(t, re_t, im_t)); the pair's
+// arithmetic runs packed.  Cutting -x gives the negated slices of x (round
+// to nearest even and TwoSum are odd functions), so a negated part is stored
+// from the same slices.
+template <int NS, class Put>
+__device__ __forceinline__ void slice_pair(float4 v, int sh, Put&& put) {
+  f2x hs = pk(ldexpf(v.x, sh), ldexpf(v.z, sh)), ls = pk(ldexpf(v.y, sh), ldexpf(v.w, sh));
+  const f2x k128 = pk((float)(1 << SBITS), (float)(1 << SBITS));
   float w = 1.f;
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
-    const float s = rintf(hs);
-    p[t * plane] = __float2bfloat16_rn(s * w);       // |s| <= 128: exact
-    hs -= s;                                         // exact
-    const float u = hs + ls;                         // TwoSum: (hs, ls) renormalised exactly
-    const float v = u - hs;
-    const float e = (hs - (u - v)) + (ls - v);
-    hs = u * (float)(1 << SBITS);
-    ls = e * (float)(1 << SBITS);
+    const float2 h2 = upk(hs);
+    const float sr = rintf(h2.x), si = rintf(h2.y);
+    put(t, __float2bfloat16_rn(sr * w), __float2bfloat16_rn(si * w));   // |s| <= 128: exact
+    hs = sub2(hs, pk(sr, si));                        // exact
+    const f2x u = add2(hs, ls);                       // TwoSum: (hs, ls) renormalised exactly
+    const f2x vv = sub2(u, hs);
+    const f2x e = add2(sub2(hs, sub2(u, vv)), sub2(ls, vv));
+    hs = mul2(u, k128);
+    ls = mul2(e, k128);
     w *= 1.f / (float)(1 << SBITS);
   }
 }
@@ -142,8 +178,9 @@ __device__ __forceinline__ int find_job(const SlSet& js, long long b) {
   return lo;
 }
 
-// One CTA per (operand row, segment of SL_THREADS complex k): every CTA of a
-// row takes the row's maximum (the same exponent), then slices its segment.
+// One CTA per (operand row, segment of SL_K complex k): every CTA of a row
+// takes the row's maximum (the same exponent), then slices its segment, two
+// consecutive k per thread so that the planes are written as bf16 pairs.
 template <int NS>
 __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_constant__ SlSet js) {
   __shared__ float red[SL_THREADS / 32];
@@ -154,7 +191,7 @@ __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_cons
   griddep_wait();
   griddep_launch();
   const long long bl = blockIdx.x - J.b0;
-  const int segs = (J.K + SL_THREADS - 1) / SL_THREADS;
+  const int segs = (J.K + SL_K - 1) / SL_K;
   const int r = (int)(bl / segs), seg = (int)(bl % segs);
   const int tid = threadIdx.x;
   const float4* row = J.src + (long long)r * J.ld;
@@ -174,18 +211,36 @@ __global__ void __launch_bounds__(SL_THREADS) etc_slice_kernel(const __grid_cons
   const long long r0 = J.kind == 0 ? J.dst + r : J.dst + (long long)(r / J.enc) * 2 * J.enc + r % J.enc;
   __nv_bfloat16* p0 = J.arena + r0 * J.W;
   __nv_bfloat16* p1 = p0 + (long long)J.enc * J.W;   // kind 1: the Im row of the column
-  const int k = seg * SL_THREADS + tid;
-  if (k < J.K) {
-    float4 v = row[(long long)k * J.es];
-    if (J.conj) { v.z = -v.z; v.w = -v.w; }
-    if (J.kind == 0) {                               // [Re | Im]
-      slice_put<NS>(p0 + k, J.plane, v.x, v.y, sh);
-      slice_put<NS>(p0 + J.K + k, J.plane, v.z, v.w, sh);
-    } else {                                         // Re row [Re | -Im], Im row [Im | Re]
-      slice_put<NS>(p0 + k, J.plane, v.x, v.y, sh);
-      slice_put<NS>(p0 + J.K + k, J.plane, -v.z, -v.w, sh);
-      slice_put<NS>(p1 + k, J.plane, v.z, v.w, sh);
-      slice_put<NS>(p1 + J.K + k, J.plane, v.x, v.y, sh);
+  const int k0 = seg * SL_K + 2 * tid;
+  if (k0 < J.K) {
+    const bool two = k0 + 1 < J.K;
+    float4 v0 = row[(long long)k0 * J.es];
+    float4 v1 = two ? row[(long long)(k0 + 1) * J.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (J.conj) { v0.z = -v0.z; v0.w = -v0.w; v1.z = -v1.z; v1.w = -v1.w; }
+    __nv_bfloat16 re0[NS], im0[NS], re1[NS], im1[NS];
+    slice_pair<NS>(v0, sh, [&](int t, __nv_bfloat16 re, __nv_bfloat16 im) { re0[t] = re; im0[t] = im; });
+    slice_pair<NS>(v1, sh, [&](int t, __nv_bfloat16 re, __nv_bfloat16 im) { re1[t] = re; im1[t] = im; });
+    const long long pl = J.plane;
+    // a pair of k at an even offset as one 4-byte store, else one by one
+    auto put2 = [&](__nv_bfloat16* p, long long off, __nv_bfloat16 a, __nv_bfloat16 b) {
+      if (two && !(off & 1)) {
+        *reinterpret_cast<__nv_bfloat162*>(p + off) = __halves2bfloat162(a, b);
+      } else {
+        p[off] = a;
+        if (two) p[off + 1] = b;
+      }
+    };
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      if (J.kind == 0) {                             // [Re | Im]
+        put2(p0, t * pl + k0, re0[t], re1[t]);
+        put2(p0, t * pl + J.K + k0, im0[t], im1[t]);
+      } else {                                       // Re row [Re | -Im], Im row [Im | Re]
+        put2(p0, t * pl + k0, re0[t], re1[t]);
+        put2(p0, t * pl + J.K + k0, __hneg(im0[t]), __hneg(im1[t]));
+        put2(p1, t * pl + k0, im0[t], im1[t]);
+        put2(p1, t * pl + J.K + k0, re0[t], re1[t]);
+      }
     }
   }
   if (seg == segs - 1) {                             // zeros up to the end of the last 32-k stage
@@ -228,35 +283,6 @@ __device__ __forceinline__ float2 df_norm(float h, float l) {
   return make_float2(s, (h - (s - v)) + (l - v));
 }
 
-// Packed pairs of FP32 values (Blackwell's f32x2 add/sub/mul, each lane
-// correctly rounded): the epilogue folds the Re and Im values of a column
-// together, at half the instruction count.
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x pk(float a, float b) {
-  f2x d;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
-  return d;
-}
-__device__ __forceinline__ float2 upk(f2x v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-__device__ __forceinline__ f2x add2(f2x a, f2x b) {
-  f2x d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
-  f2x d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
-  f2x d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 __device__ __forceinline__ void dfa2x(f2x& h, f2x& l, f2x x) {   // (h, l) += x lane-wise, TwoSum
   const f2x t = add2(h, x);
   const f2x v = sub2(t, h);
@@ -700,7 +726,7 @@ void add_slice_jobs(const EnvTcPlan& P, int slot, const DfSub* subs, const Lay* 
       J.expo = P.expo[slot] + l.eb;
     }
     js.j[js.n++] = J;
-    blocks += (long long)J.rows * ((J.K + SL_THREADS - 1) / SL_THREADS);
+    blocks += (long long)J.rows * ((J.K + SL_K - 1) / SL_K);
   }
 }
 
