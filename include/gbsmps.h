@@ -61,9 +61,11 @@ extern "C" {
 /* Arithmetic of the tensor build, environments and sampling.  The Gaussian
  * SVD, symplectic orthogonalisation and normalisation are FP64 in both. */
 #define GBSMPS_PREC_FP64 0
-#define GBSMPS_PREC_MIXED 1   /* double-float environments (FP32 pipes) and
-                                 split-FP16 tcgen05 sampling GEMMs; the PCO
-                                 build stays FP64 */
+#define GBSMPS_PREC_MIXED 1   /* FP32 PCO passes with FP64 output sums,
+                                 environments on the tensor cores with exact
+                                 accumulation of bf16 integer slices (double-
+                                 float on the FP32 pipes with GBSMPS_ENV_TC=0),
+                                 split-FP16 tcgen05 sampling GEMMs */
 
 /* Largest number of entangled mode pairs at one cut (n_e of Sec. II A). */
 #define GBSMPS_NE_MAX 24

@@ -157,9 +157,10 @@ def test_env_tile_shapes_give_identical_results(ctx, monkeypatch):
 
 def test_df64_tile_shapes_give_identical_results(ctx, monkeypatch):
     """The tile shape and the k depth of a shared-memory stage of the
-    environment chain's grouped double-float launches cannot change a bit:
-    every output sums k in the same order, and the k split follows a fixed
-    reference tiling, not the tile."""
+    environment chain's grouped double-float launches (GBSMPS_ENV_TC=0)
+    cannot change a bit: every output sums k in the same order, and the k
+    split follows a fixed reference tiling, not the tile."""
+    monkeypatch.setenv("GBSMPS_ENV_TC", "0")
     w = wl.small(24, 31, d=5, chi=64, depth=4, rlo=0.1, rhi=0.5)
     opts = dict(d=5, chi_max=64, eps_trunc=1e-12, lambda2_freeze=1e-8, precision=g.PREC_MIXED)
     u = wl.uniforms(300, 24, seed=3)

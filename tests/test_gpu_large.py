@@ -144,11 +144,11 @@ def test_full_size_n1024(ctx):
         a0 = m.amplitudes(np.zeros((1, N), dtype=np.uint8))[0]
         # The vacuum amplitude is real and positive by the gauge of A^1 (reading
         # A6), which divides out the phase that the environment chain carries
-        # along; what is left is that chain's rounding.  A tensor-core step
-        # differs from the double-float one by ~3e-14 relative (4.8e-12 over
-        # the 144 steps of the 144-mode state, test_gpu_envtc.py), so the bound
-        # allows 2^-42 (2.3e-13) per step: N 2^-42 |a0| (measured 2.5e-11
-        # relative at N = 1024, the double-float products 6e-12).
+        # along; what is left is that chain's rounding.  The tensor-core chain
+        # is within 1.2e-12 of the FP64 build over the 144 steps of the
+        # 144-mode state (test_gpu_envtc.py), ~1e-14 a step; the bound allows
+        # 2^-42 (2.3e-13) a step: N 2^-42 |a0| (measured 2.5e-11 relative at
+        # N = 1024, the double-float products 6e-12).
         assert a0.real > 0 and abs(a0.imag) <= N * 2.0 ** -42 * abs(a0)
         # sampling: properties that hold at any size
         S = 20000

@@ -1,6 +1,7 @@
-"""Mixed-precision path (FP32 PCO passes with FP64 plane sums, double-float
-environments on the FP32 pipes in the energy gauge, split-FP16 tensor-core
-sampler in right-canonical form, FP64 Gaussian SVD) against the FP64 oracle.
+"""Mixed-precision path (FP32 PCO passes with FP64 plane sums, environments in
+the energy gauge on the tensor cores with exact accumulation of bf16 integer
+slices, split-FP16 tensor-core sampler in right-canonical form, FP64 Gaussian
+SVD) against the FP64 oracle.
 Tolerances: amplitude error <= 1e-5 relative (floor 1e-8 of the largest
 amplitude), fidelity >= 1 - 1e-8, samples bit-exact except draws flagged
 within 1e-5 Z of a CDF boundary."""
