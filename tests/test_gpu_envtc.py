@@ -112,3 +112,26 @@ def test_chain_accuracy_against_fp64(ctx, monkeypatch, mode, bound):
     err = np.abs(a - a64).max() / np.abs(a64).max()
     print(f"environment products mode {mode}: mixed (FP64 PCO) vs FP64 amplitudes {err:.3e}")
     assert err <= bound
+
+
+@pytest.mark.parametrize("N,d,chi,seed", [(2, 2, 1, 1), (2, 3, 2, 2), (3, 8, 4, 3), (4, 2, 8, 4),
+                                          (5, 3, 3, 5), (6, 8, 8, 6), (6, 4, 5, 7)])
+def test_tiny_and_odd_shapes(ctx, monkeypatch, N, d, chi, seed):
+    """Products far below a tile (one or two rows and columns, K of 1 to a
+    few dozen, odd K), photon cutoffs 2, 3 and 8 and bond dimension 1: the
+    tensor-core environments agree with the double-float ones like the
+    larger states (amplitudes within 1e-10 of the largest)."""
+    w = wl.small(N, 900 + seed, d=d, chi=chi, depth=2, rlo=0.2, rhi=0.6)
+    opts = dict(d=d, chi_max=chi, eps_trunc=1e-12, lambda2_freeze=1e-8, precision=g.PREC_MIXED)
+    mt = _build(ctx, w, opts, monkeypatch, True)
+    md = _build(ctx, w, opts, monkeypatch, False)
+    try:
+        pats = wl.random_patterns(64, N, d, seed=seed, max_total=6)
+        pats[0] = 0
+        at, ad = np.asarray(mt.amplitudes(pats)), np.asarray(md.amplitudes(pats))
+        assert np.abs(at - ad).max() <= 1e-10 * np.abs(ad).max()
+        for m in range(N):
+            assert np.abs(mt.tensor(m) - md.tensor(m)).max() <= 1e-8 * np.abs(md.tensor(m)).max()
+    finally:
+        mt.release()
+        md.release()
