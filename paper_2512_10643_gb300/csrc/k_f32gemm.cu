@@ -7,7 +7,10 @@
 // one FP64-reduced partial per 16-deep stage to match that, which costs far
 // more than it saves on these small products.  Operands are FP64 or FP32 in
 // memory and FP32 in shared memory; output FP32.  Batched by strides.
-// Tile: 64 x 64 complex outputs, 16 complex k per stage, 256 threads of 4 x 4.
+// Tile: 64 x 64 complex outputs, 16 complex k per stage, 256 threads of 4 x 4;
+// the next stage's operands are read into registers while the current one is
+// multiplied, then stored to the other of two shared-memory buffers (one
+// barrier per stage).
 #include "internal.h"
 #include <algorithm>
 
@@ -33,37 +36,54 @@ __device__ __forceinline__ void store(float2* c, float2 v) { *c = v; }
 template <typename TA, typename TB, typename TC>
 __device__ __forceinline__ void f32_tile(const F32Args& p, const TA* __restrict__ A,
                                          const TB* __restrict__ B, TC* __restrict__ C, int i0, int j0,
-                                         float2 (*As)[FM + 1], float2 (*Bs)[FN + 1]) {
+                                         float2 (*As)[FK][FM + 1], float2 (*Bs)[FK][FN + 1]) {
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float2 acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < p.K; k0 += FK) {
-    for (int e = tid; e < FM * FK; e += 256) {
+  constexpr int NL = FM * FK / 256;                  // elements of each operand per thread and stage
+  float2 ra[NL], rb[NL];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q;
       const int ii = e / FK, kk = e % FK, gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < p.M && gk < p.K) ? tof(A[(long long)gi * p.lda + gk]) : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < FK * FN; e += 256) {
-      int kk, jj;
-      if (p.opb == 0) { kk = e / FN; jj = e % FN; } else { jj = e / FK; kk = e % FK; }
-      const int gj = j0 + jj, gk = k0 + kk;
+      ra[q] = (gi < p.M && gk < p.K) ? tof(A[(long long)gi * p.lda + gk]) : make_float2(0.f, 0.f);
+      int kb, jj;
+      if (p.opb == 0) { kb = e / FN; jj = e % FN; } else { jj = e / FK; kb = e % FK; }
+      const int gj = j0 + jj, gkb = k0 + kb;
       float2 v = make_float2(0.f, 0.f);
-      if (gj < p.N && gk < p.K) {
-        if (p.opb == 0) v = tof(B[(long long)gk * p.ldb + gj]);
-        else { v = tof(B[(long long)gj * p.ldb + gk]); v.y = -v.y; }   // B^dag
+      if (gj < p.N && gkb < p.K) {
+        if (p.opb == 0) v = tof(B[(long long)gkb * p.ldb + gj]);
+        else { v = tof(B[(long long)gj * p.ldb + gkb]); v.y = -v.y; }   // B^dag
       }
-      Bs[kk][jj] = v;
+      rb[q] = v;
     }
-    __syncthreads();
+  };
+  auto put = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q;
+      As[buf][e % FK][e / FK] = ra[q];
+      if (p.opb == 0) Bs[buf][e / FN][e % FN] = rb[q];
+      else Bs[buf][e % FK][e / FK] = rb[q];
+    }
+  };
+  fetch(0);
+  put(0);
+  __syncthreads();
+  for (int k0 = 0, buf = 0; k0 < p.K; k0 += FK, buf ^= 1) {
+    const bool more = k0 + FK < p.K;
+    if (more) fetch(k0 + FK);
 #pragma unroll 4
     for (int kk = 0; kk < FK; ++kk) {
       float2 a[4], b[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][kk][tx + 16 * c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -72,6 +92,7 @@ __device__ __forceinline__ void f32_tile(const F32Args& p, const TA* __restrict_
           acc[r][c].y = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acc[r][c].y));
         }
     }
+    if (more) put(buf ^ 1);
     __syncthreads();
   }
 #pragma unroll
@@ -88,8 +109,8 @@ __device__ __forceinline__ void f32_tile(const F32Args& p, const TA* __restrict_
 
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
-  __shared__ float2 As[FK][FM + 1];     // padded rows: the k-fastest fills hit distinct banks
-  __shared__ float2 Bs[FK][FN + 1];
+  __shared__ float2 As[2][FK][FM + 1];  // padded rows: the k-fastest fills hit distinct banks
+  __shared__ float2 Bs[2][FK][FN + 1];
   const long long bz = blockIdx.z;
   f32_tile<TA, TB, TC>(p, reinterpret_cast<const TA*>(p.A) + bz * p.sA,
                        reinterpret_cast<const TB*>(p.B) + bz * p.sB,
@@ -101,8 +122,8 @@ __global__ void __launch_bounds__(256) zgemm_f32_kernel(F32Args p) {
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) zgemm_f32_grouped_kernel(const F32Prob* __restrict__ probs,
                                                                  int np) {
-  __shared__ float2 As[FK][FM + 1];
-  __shared__ float2 Bs[FK][FN + 1];
+  __shared__ float2 As[2][FK][FM + 1];
+  __shared__ float2 Bs[2][FK][FN + 1];
   const long long b = blockIdx.x;
   int lo = 0, hi = np - 1;
   while (lo < hi) {
