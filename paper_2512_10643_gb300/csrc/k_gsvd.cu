@@ -24,6 +24,12 @@ constexpr int LD = N2M;
 constexpr int CHAIN_THREADS = 256;
 static_assert(CHAIN_THREADS == 256, "the spreads over sub-partitions, q = 8 lane + warp, assume 8 warps");
 constexpr int MAX_SWEEPS = 40;
+// final FP64 sweep: pairs whose rotation angle |h_pq| / |h_qq - h_pp| is below
+// this are left alone.  The stop criterion of the FP64 sweeps already leaves
+// angles up to ~1e-13 on pairs with gaps ~0.1; the final sweep is for nearly
+// degenerate pairs (gap < 1e-3 at the residual |h_pq| ~ 1e-16), whose angle
+// is far above it
+constexpr double JAC_THETA = 1e-13;
 
 struct ChainSmem {
   double A[N2M * N2M];      // V = 2 Gamma_LL -> L -> S^{-1} active rows
@@ -40,11 +46,11 @@ struct ChainSmem {
   double Dq[NLM];
   double rsD[NLM];          // sqrt(2 / D_q)
   double2 pinv;             // Gauss-Jordan: inverse of the current pivot
-  int rp[NLM], rq[NLM];
-  double rcs[NLM], rsn[NLM];
-  double2 rph[NLM];
-  float fcs[NLM], fsn[NLM];  // FP32 stage: the same, kept in FP32 (no conversions)
-  float2 fph[NLM];
+  double rcs[2][NLM], rsn[2][NLM];   // Jacobi rotations of a round (two rounds' tables)
+  double2 rph[2][NLM];
+  float fcs[2][NLM], fsn[2][NLM];    // FP32 stage: the same, kept in FP32 (no conversions)
+  float2 fph[2][NLM];
+  unsigned short blk[NLM * (NLM + 1) / 2];   // upper 2 x 2 blocks (k << 8) | l, k <= l
   double2 fac[NLM];
   double red[CHAIN_THREADS];
   int ival[4];
@@ -58,17 +64,6 @@ __device__ double block_sum(double v, double* red) {
   __syncthreads();
   double r = 0.0;
   for (int w = 0; w < nw; ++w) r += red[w];
-  __syncthreads();
-  return r;
-}
-
-__device__ double block_max(double v, double* red) {
-  const int t = threadIdx.x, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((t & 31) == 0) red[t >> 5] = v;
-  __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
 }
@@ -90,144 +85,357 @@ __device__ __forceinline__ double rcp_fp64(double a) {
   return x;
 }
 
-// Sweeps of the cyclic complex Jacobi method on the n x n Hermitian H (ld LD,
-// storage precision of T2), accumulating W <- W J.  Round-robin ordering:
-// every round rotates n/2 disjoint index pairs at once.  Before each sweep
-// the largest off-diagonal |Re| + |Im| is compared with conv; returns true
-// once it is below, false after max_sweeps sweeps.
-//
-// The rotation for a pair is computed in FP32 from the current 2x2 block
-// (angle accurate to ~1e-7 relative).  In the FP64 stage its (cos, sin) and
-// phase are then brought to unit modulus by two Newton steps in FP64, so
-// every applied J is unitary to FP64 rounding and the similarity is exact;
-// an approximate angle only leaves ~1e-7 of the rotated element behind,
-// which the next sweep removes.
-template <typename T2, bool WARP>
-__device__ bool jacobi_sweeps(ChainSmem& sm, T2* H, T2* W, int n, double conv, double skip,
-                              int max_sweeps) {
-  using R = decltype(T2{}.x);
-  constexpr bool wide = sizeof(R) == 8;
-  // WARP: warp 0 alone runs the sweeps; otherwise the whole block.  (The
-  // block form is faster for both stages at these sizes: the phases are
-  // latency-bound, and more threads means fewer dependent steps per thread.)
-  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
-  const int nt = WARP ? 32 : blockDim.x;
-  const int half = n / 2;
-  auto team_sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
-  // rotation parameters live in FP64 for the FP64 stage and in FP32 for the
-  // FP32 stage, so neither stage converts between the two in its loops
-  auto rot = [&](int k, R& cs, R& sn, R& px, R& py) {
-    if constexpr (wide) { cs = sm.rcs[k]; sn = sm.rsn[k]; px = sm.rph[k].x; py = sm.rph[k].y; }
-    else { cs = sm.fcs[k]; sn = sm.fsn[k]; px = sm.fph[k].x; py = sm.fph[k].y; }
-  };
-  for (int sweep = 0;; ++sweep) {
-    R loc = 0;
-    for (int idx = tid; idx < n * n; idx += nt) {
-      int i = idx / n, j = idx % n;
-      if (i < j) {
-        T2 v = H[i * LD + j];
-        loc = fmax(loc, fabs(v.x) + fabs(v.y));
-      }
+// Rotation J of a Jacobi pair (p, q), p < q: columns (p, q) of X J are
+// (cs x_p - sn ph x_q, sn x_p + cs ph x_q), i.e. J = [[cs, sn], [-sn ph, cs ph]]
+// with |ph| = 1; sn == 0 is the identity.
+template <typename R>
+struct JRot {
+  R cs, sn, px, py;
+};
+
+// one output of a pair rotation applied to the pair (v0, v1): s = 0 gives
+// cs v0 - sn (ph v1), s = 1 gives sn v0 + cs (ph v1).  The column update of
+// X J uses ph; the row update of J^dag X uses conj(ph).
+template <typename T2, typename R>
+__device__ __forceinline__ T2 jmix(T2 v0, T2 v1, int s, const JRot<R>& J) {
+  const R wx = J.px * v1.x - J.py * v1.y, wy = J.px * v1.y + J.py * v1.x;
+  if (s == 0) return T2{J.cs * v0.x - J.sn * wx, J.cs * v0.y - J.sn * wy};
+  return T2{J.sn * v0.x + J.cs * wx, J.sn * v0.y + J.cs * wy};
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 cconj2(T2 v) { return T2{v.x, -v.y}; }
+
+template <typename R>
+__device__ __forceinline__ R rabs(R v) {
+  if constexpr (sizeof(R) == 8) return fabs(v);
+  else return fabsf(v);
+}
+
+// rotation tables, double-buffered by round parity: FP64 parameters for the
+// FP64 stage, FP32 ones for the FP32 stage (neither stage converts in its loops)
+template <typename R>
+__device__ __forceinline__ JRot<R> jrot_load(const ChainSmem& sm, int b, int k) {
+  if constexpr (sizeof(R) == 8) return JRot<R>{sm.rcs[b][k], sm.rsn[b][k], sm.rph[b][k].x, sm.rph[b][k].y};
+  else return JRot<R>{sm.fcs[b][k], sm.fsn[b][k], sm.fph[b][k].x, sm.fph[b][k].y};
+}
+
+// The round-robin pairing: round r pairs (a, b) with a = (r + k) mod (n - 1)
+// and b = n - 1 for k = 0, else (r - k) mod (n - 1); every pair of indices
+// meets once in n - 1 rounds.  (p, q) = (min, max) of pair k.
+__device__ __forceinline__ void jpair(int r, int k, int n, int& p, int& q) {
+  const int nm1 = n - 1;
+  int a = r + k;
+  if (a >= nm1) a -= nm1;
+  int b = nm1;
+  if (k != 0) {
+    b = r - k + nm1;
+    if (b >= nm1) b -= nm1;
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+// the inverse: index x is slot s (0: p, 1: q) of pair k in round r
+__device__ __forceinline__ void jowner(int r, int x, int n, int& k, int& s) {
+  const int nm1 = n - 1, half = n >> 1;
+  if (x == nm1) { k = 0; s = 1; return; }
+  int ka = x - r;
+  if (ka < 0) ka += nm1;
+  int partner;
+  if (ka < half) {                     // x = a of pair ka
+    k = ka;
+    partner = nm1;
+    if (ka != 0) { partner = r - ka; if (partner < 0) partner += nm1; }
+  } else {                             // x = b of pair n - 1 - ka
+    k = nm1 - ka;
+    partner = r + k;
+    if (partner >= nm1) partner -= nm1;
+  }
+  s = x < partner ? 0 : 1;
+}
+
+// Knuth's TwoSum in FP32: s + e = a + b exactly (round-to-nearest intrinsics,
+// so that nothing is contracted or reassociated)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (c0, s0) with c0^2 + s0^2 = 1 - e, |e| ~ 2^-23, scaled onto the unit circle
+// in FP64: (c, s) = (c0, s0) (1 - e)^{-1/2} with (1 - e)^{-1/2} - 1 =
+// e/2 + 3e^2/8 + O(e^3) formed in FP32 from error-free products and sums
+// (Dekker's product by FMA, TwoSum), to ~1e-22 absolute; the only FP64
+// operations are the conversions, one addition and the two FMAs
+// c0 + c0 D, s0 + s0 D, each rounded once: c^2 + s^2 = 1 to FP64 rounding.
+__device__ __forceinline__ void unit_fp64(float c0, float s0, double& c, double& s) {
+  const float p1 = __fmul_rn(c0, c0), q1 = fmaf(c0, c0, -p1);
+  const float p2 = __fmul_rn(s0, s0), q2 = fmaf(s0, s0, -p2);
+  // e = 1 - p1 - p2 - q1 - q2 as eh + el: the large terms and the rounding
+  // error of 1 - p1 (up to 2^-25 when p1 < 1/2) each enter a TwoSum, so only
+  // errors of order 2^-48 are added in plain FP32
+  float a, ea, b, eb, s1, t1, s2, t2, eh, t3;
+  two_sum_f(1.0f, -p1, a, ea);
+  two_sum_f(a, -p2, b, eb);
+  two_sum_f(ea, -q1, s1, t1);
+  two_sum_f(s1, -q2, s2, t2);
+  two_sum_f(b, s2, eh, t3);
+  const float el = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(t3, eb));
+  float dh, dl;
+  two_sum_f(__fmul_rn(0.5f, eh), __fmul_rn(0.375f, __fmul_rn(eh, eh)), dh, dl);
+  dl = __fadd_rn(dl, __fmul_rn(0.5f, el));
+  const double D = (double)dh + (double)dl;
+  const double cd = (double)c0, sd = (double)s0;
+  c = fma(cd, D, cd);
+  s = fma(sd, D, sd);
+}
+
+// FP32 rotation angle of a pair with off-diagonal entry (fx, fy) and
+// dd = h_qq - h_pp: J = [[fc, fs], [-fs g, fc g]] with g = e^{-i phi},
+// h_pq = |h| e^{i phi}, t = fs / fc = tan of the angle that annihilates h_pq
+// (the smaller root of t^2 + 2 tau t - 1 = 0, tau = dd / (2 |h|)).  Returns
+// false (identity) when |Re| + |Im| <= skip or <= theta |dd|.  Accurate to
+// ~1e-7 relative (fast reciprocal square roots and divisions): the next
+// sweep removes what an approximate angle leaves behind.
+__device__ __forceinline__ bool jangle(float fx, float fy, float dd, float skip, float theta,
+                                       float& fc, float& fs, float& gx, float& gy) {
+  const float mag = fabsf(fx) + fabsf(fy);
+  if (!(mag > skip) || (theta > 0.0f && mag <= theta * fabsf(dd))) return false;
+  if (mag < 0x1p-60f) { fx *= 0x1p100f; fy *= 0x1p100f; dd *= 0x1p100f; }   // keep |h|^2 normal
+  const float im = rsqrtf(fmaf(fx, fx, fy * fy));   // 1 / |h|
+  gx = fx * im;
+  gy = -fy * im;
+  const float tau = dd * (0.5f * im);
+  const float at = fabsf(tau);
+  float t;
+  if (at > 1e18f) {
+    t = __fdividef(0.5f, tau);
+  } else {
+    const float u = fmaf(tau, tau, 1.0f);
+    t = copysignf(__fdividef(1.0f, at + u * rsqrtf(u)), tau);
+  }
+  fc = rsqrtf(fmaf(t, t, 1.0f));
+  fs = t * fc;
+  return true;
+}
+
+// Rotation of pair k (p, q) from the entries of the matrix it acts on
+// (dd = h_qq - h_pp, h_pq = (hx, hy)), into table b.  In the FP64 stage the
+// FP32 (cos, sin) and phase are put on the unit circle in FP64 (unit_fp64),
+// so every applied J is unitary to FP64 rounding and the similarity is exact.
+template <typename R>
+__device__ __forceinline__ bool jrot_setup(ChainSmem& sm, int b, int k, R dd, R hx, R hy,
+                                           float skip, float theta) {
+  float fc = 1.0f, fs = 0.0f, gx = 1.0f, gy = 0.0f;
+  const bool go = jangle((float)hx, (float)hy, (float)dd, skip, theta, fc, fs, gx, gy);
+  if constexpr (sizeof(R) == 8) {
+    double cs = 1.0, sn = 0.0, phx = 1.0, phy = 0.0;
+    if (go) {
+      unit_fp64(fc, fs, cs, sn);
+      unit_fp64(gx, gy, phx, phy);
     }
-    double gmax;
-    if (WARP) {
-      double l = loc;
-      for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
-      gmax = l;
-    } else {
-      gmax = block_max((double)loc, sm.red);
+    sm.rcs[b][k] = cs; sm.rsn[b][k] = sn; sm.rph[b][k] = cmk(phx, phy);
+  } else {
+    sm.fcs[b][k] = fc; sm.fsn[b][k] = fs; sm.fph[b][k] = make_float2(gx, gy);
+  }
+  return go;
+}
+
+// rotation of pair k of round r into table b, from the matrix H the round acts on
+template <typename T2, typename R>
+__device__ __forceinline__ bool jrot_direct(ChainSmem& sm, const T2* __restrict__ H, int b, int r,
+                                            int k, int n, float skip, float theta) {
+  int p, q;
+  jpair(r, k, n, p, q);
+  const T2 h = H[p * LD + q];
+  return jrot_setup<R>(sm, b, k, H[q * LD + q].x - H[p * LD + p].x, h.x, h.y, skip, theta);
+}
+
+// Entry (x, y) of J^dag H J from H before the rotations J of a round: x is
+// slot sa of the round's pair (pa, qa) with rotation Ja, y slot sb of pair
+// (pb, qb) with Jb.  The same operations in the same order as the block update.
+template <typename T2, typename R>
+__device__ __forceinline__ T2 jelem(const T2* __restrict__ H, int pa, int qa, JRot<R> Ja, int sa,
+                                    int pb, int qb, const JRot<R>& Jb, int sb) {
+  T2 x0 = H[pa * LD + pb], x1 = H[qa * LD + pb];
+  const T2 y0 = H[pa * LD + qb], y1 = H[qa * LD + qb];
+  if (Jb.sn != (R)0) {
+    x0 = jmix(x0, y0, sb, Jb);
+    x1 = jmix(x1, y1, sb, Jb);
+  } else if (sb) {
+    x0 = y0;
+    x1 = y1;
+  }
+  if (Ja.sn == (R)0) return sa ? x1 : x0;
+  Ja.py = -Ja.py;
+  return jmix(x0, x1, sa, Ja);
+}
+
+// One item of round r's update from Hc into Hn with the rotations of table b:
+// j < nb is the two-sided update J_k^dag B J_l of the upper 2 x 2 block
+// sm.blk[j] = (k, l) of the round's pairs (the lower block mirrored), j >= nb
+// is W <- W J in place on row i of W for the pairs g, g + G, ..
+template <typename T2, typename R>
+__device__ __forceinline__ void jround_item(const ChainSmem& sm, const T2* __restrict__ Hc,
+                                            T2* __restrict__ Hn, T2* __restrict__ W, int r, int b,
+                                            int j, int nb, int n, int half, int G, unsigned inv_n) {
+  if (j < nb) {
+    const int kl = sm.blk[j], k = kl >> 8, l = kl & 255;
+    int pk, qk, pl, ql;
+    jpair(r, k, n, pk, qk);
+    jpair(r, l, n, pl, ql);
+    JRot<R> Jk = jrot_load<R>(sm, b, k);
+    const JRot<R> Jl = jrot_load<R>(sm, b, l);
+    T2 h00 = Hc[pk * LD + pl], h01 = Hc[pk * LD + ql];
+    T2 h10 = Hc[qk * LD + pl], h11 = Hc[qk * LD + ql];
+    if (Jl.sn != (R)0) {                          // columns: X = B J_l
+      const T2 a0 = jmix(h00, h01, 0, Jl), a1 = jmix(h00, h01, 1, Jl);
+      const T2 c0 = jmix(h10, h11, 0, Jl), c1 = jmix(h10, h11, 1, Jl);
+      h00 = a0; h01 = a1; h10 = c0; h11 = c1;
     }
-    if (gmax <= conv) return true;
-    if (sweep == max_sweeps) return false;
-    for (int r = 0; r < n - 1; ++r) {
-      // pair k is set up by lane k / 4 of warp k % 4 (block form): the
-      // set-up's FP64 steps then run on all four SM sub-partitions
-      const int k = WARP ? tid : (tid < 128 ? (((tid & 31) << 2) | (tid >> 5)) : half);
-      if (k < half) {
-        const int a = (r + k) % (n - 1);
-        const int b = (k == 0) ? (n - 1) : (r - k + n - 1) % (n - 1);
-        const int p = min(a, b), q = max(a, b);
-        const T2 c = H[p * LD + q];
-        const float fx = (float)c.x, fy = (float)c.y;
-        const float mf = hypotf(fx, fy);
-        float fc = 1.0f, fs = 0.0f, gx = 1.0f, gy = 0.0f;
-        if (mf > (float)skip) {
-          gx = fx / mf; gy = -fy / mf;                          // e^{-i phi}
-          float tau = (float)(H[q * LD + q].x - H[p * LD + p].x) / (2.0f * mf);
-          float t;
-          if (fabsf(tau) > 1e18f) t = 0.5f / tau;
-          else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-          fc = rsqrtf(fmaf(t, t, 1.0f));
-          fs = t * fc;
-        }
-        sm.rp[k] = p; sm.rq[k] = q;
-        if constexpr (wide) {
-          double cs = fc, sn = fs, phx = gx, phy = gy;
-          if (fs != 0.0f) {
-            for (int it = 0; it < 2; ++it) {
-              double g = 1.5 - 0.5 * (cs * cs + sn * sn);
-              cs *= g; sn *= g;
-              double h = 1.5 - 0.5 * (phx * phx + phy * phy);
-              phx *= h; phy *= h;
-            }
-          }
-          sm.rcs[k] = cs; sm.rsn[k] = sn; sm.rph[k] = cmk(phx, phy);
-        } else {
-          sm.fcs[k] = fc; sm.fsn[k] = fs; sm.fph[k] = make_float2(gx, gy);
-        }
-      }
-      team_sync();
-      // columns: X = H J, W = W J with J = [[cs, sn], [-sn ph, cs ph]]
-      for (int idx = tid; idx < half * n; idx += nt) {
-        const int k = idx / n, i = idx % n;
-        R cs, sn, px, py;
-        rot(k, cs, sn, px, py);
-        if (sn == (R)0) continue;
-        const int p = sm.rp[k], q = sm.rq[k];
-        T2 hp = H[i * LD + p], hq = H[i * LD + q];
-        R qx = px * hq.x - py * hq.y, qy = px * hq.y + py * hq.x;
-        H[i * LD + p] = T2{cs * hp.x - sn * qx, cs * hp.y - sn * qy};
-        H[i * LD + q] = T2{sn * hp.x + cs * qx, sn * hp.y + cs * qy};
-        T2 wp = W[i * LD + p], wq = W[i * LD + q];
-        qx = px * wq.x - py * wq.y; qy = px * wq.y + py * wq.x;
-        W[i * LD + p] = T2{cs * wp.x - sn * qx, cs * wp.y - sn * qy};
-        W[i * LD + q] = T2{sn * wp.x + cs * qx, sn * wp.y + cs * qy};
-      }
-      team_sync();
-      // rows: H = J^dag X
-      for (int idx = tid; idx < half * n; idx += nt) {
-        const int k = idx / n, j = idx % n;
-        R cs, sn, px, py;
-        rot(k, cs, sn, px, py);
-        if (sn == (R)0) continue;
-        py = -py;
-        const int p = sm.rp[k], q = sm.rq[k];
-        T2 xp = H[p * LD + j], xq = H[q * LD + j];
-        R qx = px * xq.x - py * xq.y, qy = px * xq.y + py * xq.x;
-        H[p * LD + j] = T2{cs * xp.x - sn * qx, cs * xp.y - sn * qy};
-        H[q * LD + j] = T2{sn * xp.x + cs * qx, sn * xp.y + cs * qy};
-      }
-      team_sync();
+    if (Jk.sn != (R)0) {                          // rows: J_k^dag X
+      Jk.py = -Jk.py;
+      const T2 a0 = jmix(h00, h10, 0, Jk), a1 = jmix(h00, h10, 1, Jk);
+      const T2 c0 = jmix(h01, h11, 0, Jk), c1 = jmix(h01, h11, 1, Jk);
+      h00 = a0; h10 = a1; h01 = c0; h11 = c1;
+    }
+    if (k == l) {                                 // Hermitian diagonal block
+      h00.y = (R)0; h11.y = (R)0; h10 = cconj2(h01);
+    }
+    Hn[pk * LD + pl] = h00; Hn[pk * LD + ql] = h01;
+    Hn[qk * LD + pl] = h10; Hn[qk * LD + ql] = h11;
+    if (k != l) {
+      Hn[pl * LD + pk] = cconj2(h00); Hn[ql * LD + pk] = cconj2(h01);
+      Hn[pl * LD + qk] = cconj2(h10); Hn[ql * LD + qk] = cconj2(h11);
+    }
+  } else {
+    const int jw = j - nb;
+    const int g = (int)(((unsigned)jw * inv_n) >> 20), i = jw - g * n;   // jw / n, jw % n
+    for (int l = g; l < half; l += G) {
+      const JRot<R> Jl = jrot_load<R>(sm, b, l);
+      if (Jl.sn == (R)0) continue;
+      int pl, ql;
+      jpair(r, l, n, pl, ql);
+      const T2 wp = W[i * LD + pl], wq = W[i * LD + ql];
+      W[i * LD + pl] = jmix(wp, wq, 0, Jl);
+      W[i * LD + ql] = jmix(wp, wq, 1, Jl);
     }
   }
 }
 
-// Eigen-decomposition of the n x n Hermitian H (FP64, ld LD).  On return H is
-// diagonal (ev), W holds the eigenvectors as columns.  Stage 1: Jacobi in
+// Sweeps of the cyclic complex Jacobi method on the n x n Hermitian matrix in
+// Hc (n even, ld LD, storage precision of T2; both triangles kept), with Hn
+// as the second buffer of a ping-pong, accumulating W <- W J.  Every round
+// rotates the n/2 disjoint pairs of the round-robin ordering at once, as one
+// two-sided update J^dag H J of the 2 x 2 blocks of the round's pairs (the
+// upper blocks computed, the lower ones mirrored) written to the other
+// buffer, with the columns of W updated in place.
+//
+// FUSED (the FP32 stage): two warps set up the next round's rotations while
+// the other six update, from the same pre-round matrix (the three entries
+// each pair needs, through this round's rotations), so one barrier separates
+// the rounds.  Otherwise (the FP64 stage, whose updates keep the SM's FP64
+// pipes busy and would delay such a set-up): all eight warps update, then the
+// next round is set up from the updated matrix, two barriers per round (a
+// round whose rotations are all the identity is not applied).
+//
+// Before each sweep every off-diagonal entry is tested: |h_ij| <= conv, or
+// |h_ij| <= theta |h_jj - h_ii|, for all i < j ends the sweeps (returns
+// true); false after max_sweeps sweeps.  *Hout is the buffer that holds the
+// result.  A pair is rotated only if |h_pq| > skip and > theta |h_qq - h_pp|
+// (|h| = |Re| + |Im| in both tests).
+template <typename T2, bool FUSED>
+__device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W, int n,
+                              double conv_d, double skip_d, double theta_d, int max_sweeps,
+                              T2** Hout) {
+  using R = decltype(T2{}.x);
+  const R conv = (R)conv_d, theta = (R)theta_d;
+  const float skip = (float)skip_d, theta_f = (float)theta_d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int half = n >> 1, nm1 = n - 1;
+  const int nb = half * (half + 1) / 2;                  // upper 2 x 2 blocks (sm.blk)
+  // FUSED: warps 6 and 7 set up rotations (pair k on lane k / 2 of warp
+  // 6 + k % 2), warps 0..5 update.  Otherwise pair k is set up by lane k / 8
+  // of warp k % 8 (the set-up's FP64 steps on all four SM sub-partitions).
+  constexpr int NU = FUSED ? 192 : CHAIN_THREADS;
+  const bool setter = FUSED ? warp >= 6 : false;
+  const int ks = FUSED ? (setter ? (lane << 1) | (warp - 6) : NLM) : (lane << 3) | warp;
+  const int G = max(1, min(half, (NU - nb) / n));       // pair groups per W row
+  const int nitems = nb + n * G;
+  const unsigned inv_n = ((1u << 20) + (unsigned)n - 1u) / (unsigned)n;   // jw / n for jw < 2048
+  for (int sweep = 0;; ++sweep) {
+    bool viol = false;
+    for (int i = warp; i < n; i += 8) {
+      const R di = Hc[i * LD + i].x;
+      for (int j = lane; j < n; j += 32) {
+        if (j <= i) continue;
+        const T2 v = Hc[i * LD + j];
+        const R mag = rabs(v.x) + rabs(v.y);
+        if (mag > conv && !(theta > (R)0 && mag <= theta * rabs(Hc[j * LD + j].x - di))) viol = true;
+      }
+    }
+    if (ks < half) jrot_direct<T2, R>(sm, Hc, 0, 0, ks, n, skip, theta_f);   // round 0
+    const bool any = __syncthreads_or(viol) != 0;
+    if (!any) { *Hout = Hc; return true; }
+    if (sweep == max_sweeps) { *Hout = Hc; return false; }
+    bool upd = true;                         // does the round rotate any pair
+    for (int r = 0; r < nm1; ++r) {
+      const int b = r & 1;
+      if (FUSED && setter) {
+        if (ks < half && r + 1 < nm1) {
+          int p, q, k1, s1, k2, s2, pa, qa, pb, qb;
+          jpair(r + 1, ks, n, p, q);
+          jowner(r, p, n, k1, s1);
+          jowner(r, q, n, k2, s2);
+          jpair(r, k1, n, pa, qa);
+          jpair(r, k2, n, pb, qb);
+          const JRot<R> Ja = jrot_load<R>(sm, b, k1), Jb = jrot_load<R>(sm, b, k2);
+          const T2 hpp = jelem<T2, R>(Hc, pa, qa, Ja, s1, pa, qa, Ja, s1);
+          const T2 hqq = jelem<T2, R>(Hc, pb, qb, Jb, s2, pb, qb, Jb, s2);
+          const T2 hpq = jelem<T2, R>(Hc, pa, qa, Ja, s1, pb, qb, Jb, s2);
+          jrot_setup<R>(sm, b ^ 1, ks, hqq.x - hpp.x, hpq.x, hpq.y, skip, theta_f);
+        }
+      } else if (upd) {
+        for (int j = tid; j < nitems; j += NU)
+          jround_item<T2, R>(sm, Hc, Hn, W, r, b, j, nb, n, half, G, inv_n);
+      }
+      if (FUSED || upd) {
+        __syncthreads();
+        T2* t = Hc; Hc = Hn; Hn = t;
+      }
+      if (!FUSED && r + 1 < nm1) {             // a round of identities is skipped
+        bool go = false;
+        if (ks < half) go = jrot_direct<T2, R>(sm, Hc, b ^ 1, r + 1, ks, n, skip, theta_f);
+        upd = __syncthreads_or(go) != 0;
+      }
+    }
+  }
+}
+
+// Eigen-decomposition of the n x n Hermitian H = i K (K real, antisymmetric;
+// FP64, ld LD, n even).  On return the eigenvalues are in sm.ev and W holds
+// the eigenvectors as columns; H and T are overwritten.  Stage 1: Jacobi in
 // FP32 on a copy until the off-diagonal falls to ~4e-6 of ||H||_F (FP32
 // updates run at the full FP32 rate).  Stage 2: the FP32 eigenvectors are
 // made unitary in FP64 by two Newton-Schulz steps W <- W (3 - W^dag W) / 2,
 // H is transformed to W^dag H W, and FP64 Jacobi sweeps (typically two)
-// finish the diagonalisation with W accumulating.  Returns false if the
-// FP64 stage does not reach 2.5e-16 n ||H||_F within MAX_SWEEPS.
+// finish the diagonalisation with W accumulating.  Returns false if the FP64
+// stage does not reach 2.5e-16 n ||H||_F within MAX_SWEEPS.
 __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int half = n >> 1;
   double2* H = sm.H;
   double2* W = sm.W;
   double2* T = sm.T;
   float2* H32 = reinterpret_cast<float2*>(sm.T);
   float2* W32 = H32 + N2M * N2M;
+  float2* H32b = reinterpret_cast<float2*>(sm.B);       // L^{-1} is no longer needed here
+  for (int k = tid; k < half; k += nt) {                  // the upper 2 x 2 blocks (k <= l)
+    const int base = k * half - k * (k - 1) / 2;
+    for (int l = k; l < half; ++l) sm.blk[base + l - k] = (unsigned short)((k << 8) | l);
+  }
   double loc = 0.0;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
@@ -240,48 +448,71 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   // threshold Jacobi: a pair whose element is already far below the stage's
   // stop criterion is left alone (no work), the check still covers it
   const double conv32 = 4e-6 * normF, conv64 = 2.5e-16 * n * normF;
-  jacobi_sweeps<float2, false>(sm, H32, W32, n, conv32, 1e-300 + 0.025 * conv32, 12);
+  float2* H32o;
+  jacobi_sweeps<float2, true>(sm, H32, H32b, W32, n, conv32, 1e-300 + 0.025 * conv32, 0.0, 12, &H32o);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
     const float2 w = W32[i * LD + j];
     W[i * LD + j] = cmk(w.x, w.y);
   }
   __syncthreads();
+  // Newton-Schulz, W <- W (3 - W^dag W) / 2 = W - W (W^dag W - 1) / 2, twice:
+  // the residual R = W^dag W - 1 in FP64 (upper triangle, Hermitian), the
+  // correction product W R in FP32 (R is ~1e-6, then ~1e-12: the FP32
+  // rounding of the product, ~6e-8 of it, stays below the next residual and
+  // then below FP64 rounding), applied in FP64
+  float2* Rf = H32b;                                         // FP32 copy of R
   for (int it = 0; it < 2; ++it) {
-    for (int idx = tid; idx < n * n; idx += nt) {          // T = W^dag W
+    for (int idx = tid; idx < n * n; idx += nt) {
       const int i = idx / n, j = idx % n;
-      double2 s = cmk(0, 0);
+      if (i > j) continue;
+      double2 s = cmk(i == j ? -1.0 : 0.0, 0.0);
       for (int k = 0; k < n; ++k) cfma(s, cconj(W[k * LD + i]), W[k * LD + j]);
-      T[i * LD + j] = s;
+      Rf[i * LD + j] = make_float2((float)s.x, (float)s.y);
+      Rf[j * LD + i] = make_float2((float)s.x, -(float)s.y);
     }
     __syncthreads();
-    for (int row = warp; row < n; row += nw) {               // W <- W (3 - T) / 2, row-wise
-      double2 o0 = cmk(0, 0), o1 = cmk(0, 0);
+    for (int row = warp; row < n; row += nw) {               // row-wise: read, then write
+      float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
       const int j0 = lane, j1 = lane + 32;
       for (int k = 0; k < n; ++k) {
-        const double2 w = W[row * LD + k];
+        const double2 wd = W[row * LD + k];
+        const float wx = (float)wd.x, wy = (float)wd.y;
         if (j0 < n) {
-          double2 m = cscale(T[k * LD + j0], -0.5);
-          if (k == j0) m.x += 1.5;
-          cfma(o0, w, m);
+          const float2 r = Rf[k * LD + j0];
+          o0.x = fmaf(wx, r.x, fmaf(-wy, r.y, o0.x));
+          o0.y = fmaf(wx, r.y, fmaf(wy, r.x, o0.y));
         }
         if (j1 < n) {
-          double2 m = cscale(T[k * LD + j1], -0.5);
-          if (k == j1) m.x += 1.5;
-          cfma(o1, w, m);
+          const float2 r = Rf[k * LD + j1];
+          o1.x = fmaf(wx, r.x, fmaf(-wy, r.y, o1.x));
+          o1.y = fmaf(wx, r.y, fmaf(wy, r.x, o1.y));
         }
       }
       __syncwarp();
-      if (j0 < n) W[row * LD + j0] = o0;
-      if (j1 < n) W[row * LD + j1] = o1;
+      if (j0 < n) {
+        const double2 w = W[row * LD + j0];
+        W[row * LD + j0] = cmk(w.x - 0.5 * (double)o0.x, w.y - 0.5 * (double)o0.y);
+      }
+      if (j1 < n) {
+        const double2 w = W[row * LD + j1];
+        W[row * LD + j1] = cmk(w.x - 0.5 * (double)o1.x, w.y - 0.5 * (double)o1.y);
+      }
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < n * n; idx += nt) {            // T = H W
+  // T = H W with H = i K purely imaginary (K = L^{-1} Omega L^{-T} real):
+  // T = i K W, two real multiply-adds per term
+  for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
-    double2 s = cmk(0, 0);
-    for (int k = 0; k < n; ++k) cfma(s, H[i * LD + k], W[k * LD + j]);
-    T[i * LD + j] = s;
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double kk = H[i * LD + k].y;
+      const double2 w = W[k * LD + j];
+      sx = fma(-kk, w.y, sx);
+      sy = fma(kk, w.x, sy);
+    }
+    T[i * LD + j] = cmk(sx, sy);
   }
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += nt) {            // H = W^dag T (Hermitian: i <= j)
@@ -295,16 +526,20 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   }
   __syncthreads();
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
-  const bool ok = jacobi_sweeps<double2, false>(sm, H, W, n, conv64, 1e-300 + 0.25 * conv64,
-                                                MAX_SWEEPS);
-  // then one sweep more over every nonzero pair, with no stop test: the
-  // criterion above leaves off-diagonal elements up to ~n eps ||H||_F, which
-  // turn the eigenvectors of a nearly degenerate pair (gap g) by ~that / g
-  // (1e-8 at g ~ 5e-7, a mode kept just above the freeze threshold); one
-  // more sweep takes every element to the rounding floor of a single sweep,
-  // where the eigenvectors are as well determined as FP64 allows
-  jacobi_sweeps<double2, false>(sm, H, W, n, -1.0, 1e-300, 1);
-  for (int i = tid; i < n; i += nt) sm.ev[i] = H[i * LD + i].x;
+  double2* Hc;
+  const bool ok = jacobi_sweeps<double2, false>(sm, H, T, W, n, conv64, 1e-300 + 0.25 * conv64, 0.0,
+                                         MAX_SWEEPS, &Hc);
+  // then one sweep more over every pair whose rotation angle is above
+  // JAC_THETA, with no stop test: the criterion above leaves off-diagonal
+  // elements up to ~n eps ||H||_F, which turn the eigenvectors of a nearly
+  // degenerate pair (gap g) by ~that / g (1e-8 at g ~ 5e-7, a mode kept just
+  // above the freeze threshold); one more sweep takes every such element to
+  // the rounding floor of a single sweep, where the eigenvectors are as well
+  // determined as FP64 allows (pairs whose angle is below JAC_THETA are left:
+  // their rotation would change nothing above the sweep's own rounding)
+  double2* Hf;
+  jacobi_sweeps<double2, false>(sm, Hc, Hc == H ? T : H, W, n, 1e-300, 1e-300, JAC_THETA, 1, &Hf);
+  for (int i = tid; i < n; i += nt) sm.ev[i] = Hf[i * LD + i].x;
   __syncthreads();
   return ok;
 }
