@@ -221,14 +221,16 @@ __device__ __forceinline__ bool jangle(float fx, float fy, float dd, float skip,
 }
 
 // Rotation of pair k (p, q) from the entries of the matrix it acts on
-// (dd = h_qq - h_pp, h_pq = (hx, hy)), into table b.  In the FP64 stage the
-// FP32 (cos, sin) and phase are put on the unit circle in FP64 (unit_fp64),
-// so every applied J is unitary to FP64 rounding and the similarity is exact.
+// (dd = h_qq - h_pp, h_pq = (hx, hy)), into table b.  The FP32 parameters
+// are always stored; in the FP64 stage the FP32 (cos, sin) and phase are
+// also put on the unit circle in FP64 (unit_fp64), so every applied J is
+// unitary to FP64 rounding and the similarity is exact.
 template <typename R>
-__device__ __forceinline__ bool jrot_setup(ChainSmem& sm, int b, int k, R dd, R hx, R hy,
-                                           float skip, float theta) {
+__device__ __forceinline__ bool jrot_put(ChainSmem& sm, int b, int k, float dd, float hx, float hy,
+                                         float skip, float theta) {
   float fc = 1.0f, fs = 0.0f, gx = 1.0f, gy = 0.0f;
-  const bool go = jangle((float)hx, (float)hy, (float)dd, skip, theta, fc, fs, gx, gy);
+  const bool go = jangle(hx, hy, dd, skip, theta, fc, fs, gx, gy);
+  sm.fcs[b][k] = fc; sm.fsn[b][k] = fs; sm.fph[b][k] = make_float2(gx, gy);
   if constexpr (sizeof(R) == 8) {
     double cs = 1.0, sn = 0.0, phx = 1.0, phy = 0.0;
     if (go) {
@@ -236,8 +238,6 @@ __device__ __forceinline__ bool jrot_setup(ChainSmem& sm, int b, int k, R dd, R 
       unit_fp64(gx, gy, phx, phy);
     }
     sm.rcs[b][k] = cs; sm.rsn[b][k] = sn; sm.rph[b][k] = cmk(phx, phy);
-  } else {
-    sm.fcs[b][k] = fc; sm.fsn[b][k] = fs; sm.fph[b][k] = make_float2(gx, gy);
   }
   return go;
 }
@@ -249,17 +249,17 @@ __device__ __forceinline__ bool jrot_direct(ChainSmem& sm, const T2* __restrict_
   int p, q;
   jpair(r, k, n, p, q);
   const T2 h = H[p * LD + q];
-  return jrot_setup<R>(sm, b, k, H[q * LD + q].x - H[p * LD + p].x, h.x, h.y, skip, theta);
+  return jrot_put<R>(sm, b, k, (float)(H[q * LD + q].x - H[p * LD + p].x), (float)h.x, (float)h.y,
+                     skip, theta);
 }
 
-// Entry (x, y) of J^dag H J from H before the rotations J of a round: x is
-// slot sa of the round's pair (pa, qa) with rotation Ja, y slot sb of pair
-// (pb, qb) with Jb.  The same operations in the same order as the block update.
+// Entry (x, y) of J^dag B J for the 2 x 2 block B = [[x0, y0], [x1, y1]]
+// (rows pa, qa of a round's pair with rotation Ja, columns pb, qb of a pair
+// with Jb; x is slot sa, y slot sb).  The same operations in the same order
+// as the block update.
 template <typename T2, typename R>
-__device__ __forceinline__ T2 jelem(const T2* __restrict__ H, int pa, int qa, JRot<R> Ja, int sa,
-                                    int pb, int qb, const JRot<R>& Jb, int sb) {
-  T2 x0 = H[pa * LD + pb], x1 = H[qa * LD + pb];
-  const T2 y0 = H[pa * LD + qb], y1 = H[qa * LD + qb];
+__device__ __forceinline__ T2 jelem4(T2 x0, T2 x1, T2 y0, T2 y1, JRot<R> Ja, int sa,
+                                     const JRot<R>& Jb, int sb) {
   if (Jb.sn != (R)0) {
     x0 = jmix(x0, y0, sb, Jb);
     x1 = jmix(x1, y1, sb, Jb);
@@ -270,6 +270,58 @@ __device__ __forceinline__ T2 jelem(const T2* __restrict__ H, int pa, int qa, JR
   if (Ja.sn == (R)0) return sa ? x1 : x0;
   Ja.py = -Ja.py;
   return jmix(x0, x1, sa, Ja);
+}
+
+template <typename T2, typename R>
+__device__ __forceinline__ T2 jelem(const T2* __restrict__ H, int pa, int qa, const JRot<R>& Ja,
+                                    int sa, int pb, int qb, const JRot<R>& Jb, int sb) {
+  return jelem4<T2, R>(H[pa * LD + pb], H[qa * LD + pb], H[pa * LD + qb], H[qa * LD + qb], Ja, sa,
+                       Jb, sb);
+}
+
+__device__ __forceinline__ float2 tof2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// change of the diagonal entry h_pp of a pair (p, q) under its rotation J:
+// h'_pp = h_pp + d, h'_qq = h_qq - d, d = sn^2 (h_qq - h_pp) - 2 cs sn Re(ph h_pq)
+__device__ __forceinline__ float jdiag_shift(const JRot<float>& J, float dlt, float2 h) {
+  if (J.sn == 0.0f) return 0.0f;
+  const float re = J.px * h.x - J.py * h.y;
+  return J.sn * (J.sn * dlt - 2.0f * J.cs * re);
+}
+
+// The next round's rotation of pair k (FUSED set-up), from the matrix H that
+// round r acts on and round r's rotations (table b).  FP32 stage: the three
+// entries through the rotations, in FP32.  FP64 stage: FP64 only where
+// cancellation needs it, so that the set-up ends within the round's FP64
+// updates: the diagonal difference h'_qq - h'_pp is the FP64 difference of
+// the current entries plus the FP32 shifts of both (jdiag_shift, from FP64
+// differences), and h'_pq, an entry of the 2 x 2 block of two different
+// pairs of round r (off-diagonal entries only: no cancellation), is formed
+// in FP32.  The angle is an FP32 quantity in either stage.
+template <typename T2, typename R>
+__device__ __forceinline__ bool jsetup_next(ChainSmem& sm, const T2* __restrict__ H, int r, int b,
+                                            int k, int n, float skip, float theta) {
+  int p, q, k1, s1, k2, s2, pa, qa, pb, qb;
+  jpair(r + 1, k, n, p, q);
+  jowner(r, p, n, k1, s1);
+  jowner(r, q, n, k2, s2);
+  jpair(r, k1, n, pa, qa);
+  jpair(r, k2, n, pb, qb);
+  const JRot<float> Ja = jrot_load<float>(sm, b, k1), Jb = jrot_load<float>(sm, b, k2);
+  if constexpr (sizeof(R) == 4) {
+    const T2 hpp = jelem<T2, R>(H, pa, qa, Ja, s1, pa, qa, Ja, s1);
+    const T2 hqq = jelem<T2, R>(H, pb, qb, Jb, s2, pb, qb, Jb, s2);
+    const T2 hpq = jelem<T2, R>(H, pa, qa, Ja, s1, pb, qb, Jb, s2);
+    return jrot_put<R>(sm, b ^ 1, k, hqq.x - hpp.x, hpq.x, hpq.y, skip, theta);
+  } else {
+    const float dA = jdiag_shift(Ja, (float)(H[qa * LD + qa].x - H[pa * LD + pa].x), tof2(H[pa * LD + qa]));
+    const float dB = jdiag_shift(Jb, (float)(H[qb * LD + qb].x - H[pb * LD + pb].x), tof2(H[pb * LD + qb]));
+    const float dp = s1 ? -dA : dA, dq = s2 ? -dB : dB;
+    const float dd = (float)(H[q * LD + q].x - H[p * LD + p].x) + (dq - dp);
+    const float2 hpq = jelem4<float2, float>(tof2(H[pa * LD + pb]), tof2(H[qa * LD + pb]),
+                                             tof2(H[pa * LD + qb]), tof2(H[qa * LD + qb]), Ja, s1, Jb, s2);
+    return jrot_put<R>(sm, b ^ 1, k, dd, hpq.x, hpq.y, skip, theta);
+  }
 }
 
 // One item of round r's update from Hc into Hn with the rotations of table b:
@@ -332,13 +384,12 @@ __device__ __forceinline__ void jround_item(const ChainSmem& sm, const T2* __res
 // upper blocks computed, the lower ones mirrored) written to the other
 // buffer, with the columns of W updated in place.
 //
-// FUSED (the FP32 stage): two warps set up the next round's rotations while
-// the other six update, from the same pre-round matrix (the three entries
-// each pair needs, through this round's rotations), so one barrier separates
-// the rounds.  Otherwise (the FP64 stage, whose updates keep the SM's FP64
-// pipes busy and would delay such a set-up): all eight warps update, then the
-// next round is set up from the updated matrix, two barriers per round (a
-// round whose rotations are all the identity is not applied).
+// FUSED: two warps set up the next round's rotations while the other six
+// update, from the same pre-round matrix (the entries each pair needs,
+// through this round's rotations: jsetup_next), so one barrier separates the
+// rounds.  Otherwise all eight warps update, then the next round is set up
+// from the updated matrix, two barriers per round.  Either way a round whose
+// rotations are all the identity is not applied.
 //
 // Before each sweep every off-diagonal entry is tested: |h_ij| <= conv, or
 // |h_ij| <= theta |h_jj - h_ii|, for all i < j ends the sweeps (returns
@@ -382,32 +433,27 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W,
     bool upd = true;                         // does the round rotate any pair
     for (int r = 0; r < nm1; ++r) {
       const int b = r & 1;
+      bool go_next = false;
       if (FUSED && setter) {
-        if (ks < half && r + 1 < nm1) {
-          int p, q, k1, s1, k2, s2, pa, qa, pb, qb;
-          jpair(r + 1, ks, n, p, q);
-          jowner(r, p, n, k1, s1);
-          jowner(r, q, n, k2, s2);
-          jpair(r, k1, n, pa, qa);
-          jpair(r, k2, n, pb, qb);
-          const JRot<R> Ja = jrot_load<R>(sm, b, k1), Jb = jrot_load<R>(sm, b, k2);
-          const T2 hpp = jelem<T2, R>(Hc, pa, qa, Ja, s1, pa, qa, Ja, s1);
-          const T2 hqq = jelem<T2, R>(Hc, pb, qb, Jb, s2, pb, qb, Jb, s2);
-          const T2 hpq = jelem<T2, R>(Hc, pa, qa, Ja, s1, pb, qb, Jb, s2);
-          jrot_setup<R>(sm, b ^ 1, ks, hqq.x - hpp.x, hpq.x, hpq.y, skip, theta_f);
-        }
+        if (ks < half && r + 1 < nm1) go_next = jsetup_next<T2, R>(sm, Hc, r, b, ks, n, skip, theta_f);
       } else if (upd) {
         for (int j = tid; j < nitems; j += NU)
           jround_item<T2, R>(sm, Hc, Hn, W, r, b, j, nb, n, half, G, inv_n);
       }
-      if (FUSED || upd) {
-        __syncthreads();
-        T2* t = Hc; Hc = Hn; Hn = t;
-      }
-      if (!FUSED && r + 1 < nm1) {             // a round of identities is skipped
-        bool go = false;
-        if (ks < half) go = jrot_direct<T2, R>(sm, Hc, b ^ 1, r + 1, ks, n, skip, theta_f);
-        upd = __syncthreads_or(go) != 0;
+      if (FUSED) {                             // a round of identities is skipped
+        const bool nxt = __syncthreads_or(go_next) != 0;
+        if (upd) { T2* t = Hc; Hc = Hn; Hn = t; }
+        upd = nxt;
+      } else {
+        if (upd) {
+          __syncthreads();
+          T2* t = Hc; Hc = Hn; Hn = t;
+        }
+        if (r + 1 < nm1) {
+          bool go = false;
+          if (ks < half) go = jrot_direct<T2, R>(sm, Hc, b ^ 1, r + 1, ks, n, skip, theta_f);
+          upd = __syncthreads_or(go) != 0;
+        }
       }
     }
   }
@@ -527,7 +573,7 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   __syncthreads();
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
   double2* Hc;
-  const bool ok = jacobi_sweeps<double2, false>(sm, H, T, W, n, conv64, 1e-300 + 0.25 * conv64, 0.0,
+  const bool ok = jacobi_sweeps<double2, true>(sm, H, T, W, n, conv64, 1e-300 + 0.25 * conv64, 0.0,
                                          MAX_SWEEPS, &Hc);
   // then one sweep more over every pair whose rotation angle is above
   // JAC_THETA, with no stop test: the criterion above leaves off-diagonal
@@ -538,7 +584,7 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   // determined as FP64 allows (pairs whose angle is below JAC_THETA are left:
   // their rotation would change nothing above the sweep's own rounding)
   double2* Hf;
-  jacobi_sweeps<double2, false>(sm, Hc, Hc == H ? T : H, W, n, 1e-300, 1e-300, JAC_THETA, 1, &Hf);
+  jacobi_sweeps<double2, true>(sm, Hc, Hc == H ? T : H, W, n, 1e-300, 1e-300, JAC_THETA, 1, &Hf);
   for (int i = tid; i < n; i += nt) sm.ev[i] = Hf[i * LD + i].x;
   __syncthreads();
   return ok;
