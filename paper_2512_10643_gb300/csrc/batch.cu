@@ -77,7 +77,9 @@ extern "C" int gbsmps_build_batch(gbsmps_ctx_t c, int32_t count, const int32_t* 
     DevBuf jb;
     rc = upload(jb, cj, s);
     if (rc) { release_inputs(); return rc; }
-    CK(launch_gsvd_chain_batch(jb.as<ChainJob>(), count, c->d_status, s));
+    int maxN = 0;
+    for (const ChainJob& j : cj) maxN = std::max(maxN, j.N);
+    CK(launch_gsvd_chain_batch(jb.as<ChainJob>(), count, maxN, c->d_status, s));
     COUNT_LAUNCH(1);
     jb.release();
   }

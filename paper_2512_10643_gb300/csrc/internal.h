@@ -175,7 +175,7 @@ struct ChainJob {
   double2* Qm;
   double* cm;
 };
-cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int* status,
+cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int maxN, int* status,
                                     cudaStream_t s);
 cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
                               double lambda2_freeze, double* Gscratch,

@@ -8,7 +8,10 @@
 // active b modes with the rest are carried to the next cut (the b modes are
 // renamed r_m, Eqs. (SVD3)-(bond)).  Because the brick-wall and Haar
 // workloads have banded covariance (zero beyond a mode distance bw), only
-// the bw modes to the right of the cut are carried.
+// the bw modes to the right of the cut are carried.  The chain keeps only
+// what the next cut needs; each cut's U^{-1}, c_m and Q^m are formed after
+// it, all cuts at once (qm_kernel), from the U, V it leaves in the site's
+// Q^m slot.
 //
 // Williamson form: V = 2 Gamma_LL = L L^T (Cholesky); K = L^{-1} Omega L^{-T}
 // is antisymmetric with eigenvalues +-i/D; the Hermitian i K is
@@ -23,6 +26,7 @@ namespace {
 constexpr int LD = N2M;
 constexpr int CHAIN_THREADS = 256;
 static_assert(CHAIN_THREADS == 256, "the spreads over sub-partitions, q = 8 lane + warp, assume 8 warps");
+static_assert(NLM <= 32, "the gauge and the active-mode count keep one mode per lane");
 constexpr int MAX_SWEEPS = 40;
 // final FP64 sweep: pairs whose rotation angle |h_pq| / |h_qq - h_pp| is below
 // this are left alone.  The stop criterion of the FP64 sweeps already leaves
@@ -593,7 +597,8 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
 // Inverse of the n x n complex matrix M (ld NLM) into Inv (ld NLM) by
 // Gauss-Jordan elimination with partial pivoting; M is destroyed.  Returns
 // log|det M| in sm.dval[0]; sets ival[0] = 1 on a zero pivot.
-__device__ void cinv(ChainSmem& sm, double2* M, double2* Inv, int n) {
+template <typename Smem>
+__device__ void cinv(Smem& sm, double2* M, double2* Inv, int n) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int idx = tid; idx < n * n; idx += nt) {
     int i = idx / n, j = idx % n;
@@ -821,66 +826,52 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
     }
     __syncthreads();
     // ---- canonical gauge: largest |U_jq| of each column real positive ----
-    for (int q = (tid & 31) * 8 + (tid >> 5); q < nL; q += nt) {   // spread over sub-partitions
-      int jb = 0;
-      double best = -1.0;
-      for (int j = 0; j < nL; ++j) {
-        double v = cabs2(sm.U[j * NLM + q]);
-        if (v > best) { best = v; jb = j; }
-      }
-      double2 u = sm.U[jb * NLM + q];
-      const double img = rsqrt_fp64(best);
-      double2 ph = cmk(u.x * img, -u.y * img);
-      for (int j = 0; j < nL; ++j) {
-        sm.U[j * NLM + q] = cmul(sm.U[j * NLM + q], ph);
-        sm.V[j * NLM + q] = cmul(sm.V[j * NLM + q], ph);
+    // (warp w takes columns w, w + 8, ..; lane j holds |U_jq|^2 and a
+    // butterfly keeps the largest, the first index among equal ones: the
+    // choice of a serial scan with a strict comparison, in FP64)
+    {
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int q = warp; q < nL; q += (nt >> 5)) {
+        double best = lane < nL ? cabs2(sm.U[lane * NLM + q]) : -1.0;
+        int jb = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+          const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+          const int j2 = __shfl_xor_sync(0xffffffffu, jb, o);
+          if (v2 > best || (v2 == best && j2 < jb)) { best = v2; jb = j2; }
+        }
+        const double2 u = sm.U[jb * NLM + q];
+        const double img = rsqrt_fp64(best);
+        const double2 ph = cmk(u.x * img, -u.y * img);
+        __syncwarp();                        // every lane has read U_{jb q}
+        if (lane < nL) {
+          sm.U[lane * NLM + q] = cmul(sm.U[lane * NLM + q], ph);
+          sm.V[lane * NLM + q] = cmul(sm.V[lane * NLM + q], ph);
+        }
       }
     }
-    if (tid == 0) {
-      int na = 0;
-      // Lambda^2 = (D - 1) / (D + 1) > freeze, without the division (D + 1 > 0)
-      while (na < nL && sm.Dq[na] - 1.0 > freeze * (sm.Dq[na] + 1.0)) ++na;
-      if (na > NEM) { set_status(status, ST_BOUNDS); na = NEM; }
-      sm.ival[2] = na;
+    if (tid < 32) {
+      // active modes: the leading run of Lambda^2 = (D - 1) / (D + 1) > freeze
+      // over D descending, without the division (D + 1 > 0)
+      const bool act = tid < nL && sm.Dq[tid] - 1.0 > freeze * (sm.Dq[tid] + 1.0);
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      int na = __ffs(~m) - 1;
+      if (tid == 0) {
+        if (na > NEM) { set_status(status, ST_BOUNDS); na = NEM; }
+        sm.ival[2] = na;
+      }
     }
     __syncthreads();
     const int na = sm.ival[2];
-    // ---- U^{-1} and |det U| ----------------------------------------------
-    for (int idx = tid; idx < nL * nL; idx += nt) {        // work copy, ld NLM
-      int i = idx / nL, j = idx % nL;
-      sm.H[i * NLM + j] = sm.U[i * NLM + j];
-    }
-    __syncthreads();
-    cinv(sm, sm.H, sm.Ui, nL);
-    if (tid == 0) {
-      if (sm.ival[0]) set_status(status, ST_NUMERIC);
-      cm[m] = exp(-0.5 * sm.dval[0]);
-    }
-    // ---- local paired form Q^m over (r_{m-1}, a_m, l_m), App. A ----------
-    double2* Qo = Qm + (size_t)m * QS * QS;
-    const int nq = nL + na;
-    for (int idx = tid; idx < nq * nq; idx += nt) {
-      int i = idx / nq, j = idx % nq;
-      double2 v = cmk(0, 0);
-      if (i < nL && j < nL) {            // U^-dag V^dag: sum_k conj(Ui_ki) conj(V_jk)
-        for (int k = 0; k < nL; ++k) cfma(v, cconj(sm.Ui[k * NLM + i]), cconj(sm.V[j * NLM + k]));
-        double2 w = cmk(0, 0);
-        for (int k = 0; k < nL; ++k) cfma(w, cconj(sm.Ui[k * NLM + j]), cconj(sm.V[i * NLM + k]));
-        v = cscale(cadd(v, w), 0.5);
-      } else if (i < nL) {               // U^-dag restricted: conj(Ui_{q i})
-        v = cconj(sm.Ui[(j - nL) * NLM + i]);
-      } else if (j < nL) {               // U^-* : conj(Ui_{q j})
-        v = cconj(sm.Ui[(i - nL) * NLM + j]);
-      } else {                           // -V^T U^-dag: -sum_k V_kq conj(Ui_q'k)
-        int q = i - nL, qp = j - nL;
-        double2 w = cmk(0, 0);
-        for (int k = 0; k < nL; ++k) {
-          cfma(v, sm.V[k * NLM + q], cconj(sm.Ui[qp * NLM + k]));
-          cfma(w, sm.V[k * NLM + qp], cconj(sm.Ui[q * NLM + k]));
-        }
-        v = cscale(cadd(v, w), -0.5);
+    // ---- U, V to site m's Q^m slot: U^{-1}, c_m and Q^m (App. A) are not
+    // needed by later cuts and are formed after the chain, all cuts at once
+    // (qm_kernel); the first 2 NLM^2 entries of the slot hold U, then V
+    {
+      double2* Qo = Qm + (size_t)m * QS * QS;
+      for (int idx = tid; idx < nL * nL; idx += nt) {
+        const int i = idx / nL, j = idx % nL;
+        Qo[i * NLM + j] = sm.U[i * NLM + j];
+        Qo[NLM * NLM + i * NLM + j] = sm.V[i * NLM + j];
       }
-      Qo[i * QS + j] = v;
     }
     // ---- rows of S^{-1} for the active b modes (into A) -------------------
     for (int idx = tid; idx < na * nL; idx += nt) {
@@ -944,6 +935,83 @@ gsvd_chain_batch_kernel(const ChainJob* __restrict__ jobs, int* status) {
   const ChainJob j = jobs[blockIdx.x];
   chain_body(*reinterpret_cast<ChainSmem*>(smraw), j.gamma, j.N, j.bw, j.freeze, j.G, j.ba, j.Qm,
              j.cm, status);
+}
+
+// Shared memory of qm_kernel: the Bogoliubov matrices of one cut, the work
+// copy and inverse of U, and cinv's scratch.
+struct QmSmem {
+  double2 H[NLM * NLM];
+  double2 U[NLM * NLM];
+  double2 V[NLM * NLM];
+  double2 Ui[NLM * NLM];
+  double2 fac[NLM];
+  double2 pinv;
+  int ival[4];
+  double dval[4];
+};
+
+// Cut m's local paired form Q^m over (r_{m-1}, a_m, l_m) and c_m = |det U|^{-1/2}
+// (App. A) from the gauge-fixed U, V that the chain left in the first
+// 2 NLM^2 entries of the site's Q^m slot: U^{-1} by Gauss-Jordan with
+// partial pivoting, then the four blocks of Q^m, written over the slot.
+__device__ void qm_body(QmSmem& sm, int m, const int* __restrict__ ne, double2* __restrict__ Qm,
+                        double* __restrict__ cm, int* status) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nL = ne[m] + 1, na = ne[m + 1];
+  double2* Qo = Qm + (size_t)m * QS * QS;
+  for (int idx = tid; idx < nL * nL; idx += nt) {
+    const int i = idx / nL, j = idx % nL;
+    const double2 u = Qo[i * NLM + j];
+    sm.U[i * NLM + j] = u;
+    sm.H[i * NLM + j] = u;
+    sm.V[i * NLM + j] = Qo[NLM * NLM + i * NLM + j];
+  }
+  __syncthreads();
+  cinv(sm, sm.H, sm.Ui, nL);
+  if (tid == 0) {
+    if (sm.ival[0]) set_status(status, ST_NUMERIC);
+    cm[m] = exp(-0.5 * sm.dval[0]);
+  }
+    const int nq = nL + na;
+    for (int idx = tid; idx < nq * nq; idx += nt) {
+      int i = idx / nq, j = idx % nq;
+      double2 v = cmk(0, 0);
+      if (i < nL && j < nL) {            // U^-dag V^dag: sum_k conj(Ui_ki) conj(V_jk)
+        for (int k = 0; k < nL; ++k) cfma(v, cconj(sm.Ui[k * NLM + i]), cconj(sm.V[j * NLM + k]));
+        double2 w = cmk(0, 0);
+        for (int k = 0; k < nL; ++k) cfma(w, cconj(sm.Ui[k * NLM + j]), cconj(sm.V[i * NLM + k]));
+        v = cscale(cadd(v, w), 0.5);
+      } else if (i < nL) {               // U^-dag restricted: conj(Ui_{q i})
+        v = cconj(sm.Ui[(j - nL) * NLM + i]);
+      } else if (j < nL) {               // U^-* : conj(Ui_{q j})
+        v = cconj(sm.Ui[(i - nL) * NLM + j]);
+      } else {                           // -V^T U^-dag: -sum_k V_kq conj(Ui_q'k)
+        int q = i - nL, qp = j - nL;
+        double2 w = cmk(0, 0);
+        for (int k = 0; k < nL; ++k) {
+          cfma(v, sm.V[k * NLM + q], cconj(sm.Ui[qp * NLM + k]));
+          cfma(w, sm.V[k * NLM + qp], cconj(sm.Ui[q * NLM + k]));
+        }
+        v = cscale(cadd(v, w), -0.5);
+      }
+      Qo[i * QS + j] = v;
+    }
+}
+
+// all cuts of one state, one CTA each (the last site's Q is the chain's)
+__global__ void __launch_bounds__(CHAIN_THREADS)
+qm_kernel(const int* __restrict__ ne, double2* __restrict__ Qm, double* __restrict__ cm, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  qm_body(*reinterpret_cast<QmSmem*>(smraw), blockIdx.x, ne, Qm, cm, status);
+}
+
+// many states: CTA (m, b) takes cut m of state b, if the state has it
+__global__ void __launch_bounds__(CHAIN_THREADS)
+qm_batch_kernel(const ChainJob* __restrict__ jobs, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ChainJob& j = jobs[blockIdx.y];
+  if ((int)blockIdx.x >= j.N - 1) return;
+  qm_body(*reinterpret_cast<QmSmem*>(smraw), blockIdx.x, j.ba.ne, j.Qm, j.cm, status);
 }
 
 // ---- input checks -----------------------------------------------------------
@@ -1118,10 +1186,14 @@ cudaError_t launch_gsvd_chain(const double* gamma, int N, const int* bw,
   if (e) return e;
   gsvd_chain_kernel<<<1, CHAIN_THREADS, smem, s>>>(gamma, N, bw, lambda2_freeze, Gscratch,
                                                    ba, Qm, cm, status);
+  e = cudaGetLastError();
+  if (e || N < 2) return e;
+  qm_kernel<<<N - 1, CHAIN_THREADS, sizeof(QmSmem), s>>>(ba.ne, Qm, cm, status);
+  COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int* status,
+cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int maxN, int* status,
                                     cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   size_t smem = sizeof(ChainSmem);
@@ -1129,5 +1201,10 @@ cudaError_t launch_gsvd_chain_batch(const ChainJob* jobs_dev, int count, int* st
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   gsvd_chain_batch_kernel<<<count, CHAIN_THREADS, smem, s>>>(jobs_dev, status);
+  e = cudaGetLastError();
+  if (e || maxN < 2) return e;
+  if (count > 65535) return cudaErrorInvalidValue;
+  qm_batch_kernel<<<dim3(maxN - 1, count), CHAIN_THREADS, sizeof(QmSmem), s>>>(jobs_dev, status);
+  COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
