@@ -718,56 +718,67 @@ __device__ void chain_body(ChainSmem& sm, const double* __restrict__ gam, int N,
       if (tid == 0) cm[m] = 1.0;
       break;
     }
-    // ---- Cholesky of V = 2 Gamma_LL (lower, in place) -------------------
+    // ---- Cholesky of V = 2 Gamma_LL (lower, in place), right-looking ----
+    // One barrier per column: step k updates the trailing matrix with the
+    // raw column k times 1/a_kk (= r_k^2, r_k = a_kk^{-1/2} in sm.ev[k]) and
+    // scales column k - 1 by r_{k-1} (nothing reads it in step k); thread 0,
+    // which updates a_{k+1,k+1} first, then forms r_{k+1} for the next step.
     for (int idx = tid; idx < n2 * n2; idx += nt) sm.A[(idx / n2) * LD + idx % n2] *= 2.0;
     __syncthreads();
+    if (tid == 0) {                    // 1/sqrt(a_00) by Newton from FP32
+      double a = sm.A[0];
+      if (!(a > 0.0)) { set_status(status, ST_NUMERIC); a = 1e-300; }
+      sm.ev[0] = rsqrt_fp64(a);
+    }
+    __syncthreads();
     for (int k = 0; k < n2; ++k) {
-      if (tid == 0) {                  // one thread: 1/sqrt(akk) by Newton from FP32
-        double akk = sm.A[k * LD + k];
-        if (!(akk > 0.0)) { set_status(status, ST_NUMERIC); akk = 1e-300; }
-        const double r = rsqrt_fp64(akk);
-        sm.dval[2] = akk * r;
-        sm.dval[3] = r;
+      const double rk = sm.ev[k], ir2 = rk * rk;
+      if (k > 0) {
+        const double rp = sm.ev[k - 1];
+        for (int i = k - 1 + tid; i < n2; i += nt) sm.A[i * LD + k - 1] *= rp;
       }
-      __syncthreads();
-      const double ilkk = sm.dval[3];
-      for (int i = k + 1 + tid; i < n2; i += nt) sm.A[i * LD + k] *= ilkk;
-      if (tid == 0) sm.A[k * LD + k] = sm.dval[2];
-      __syncthreads();
       const int w = n2 - k - 1;
-      for (int idx = tid; idx < w * w; idx += nt) {
-        int i = k + 1 + idx / w, j = k + 1 + idx % w;
-        if (j <= i) sm.A[i * LD + j] -= sm.A[i * LD + k] * sm.A[j * LD + k];
+      for (int idx = tid; idx < w * w; idx += nt) {   // idx 0 (thread 0): a_{k+1,k+1}
+        const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+        if (j <= i) sm.A[i * LD + j] = fma(-sm.A[i * LD + k] * ir2, sm.A[j * LD + k], sm.A[i * LD + j]);
+      }
+      if (tid == 0 && w > 0) {
+        double a = sm.A[(k + 1) * LD + k + 1];
+        if (!(a > 0.0)) { set_status(status, ST_NUMERIC); a = 1e-300; }
+        sm.ev[k + 1] = rsqrt_fp64(a);
       }
       __syncthreads();
     }
     for (int idx = tid; idx < n2 * n2; idx += nt) {
-      int i = idx / n2, j = idx % n2;
+      const int i = idx / n2, j = idx % n2;
       if (j > i) sm.A[i * LD + j] = 0.0;
+      else if (j == n2 - 1) sm.A[i * LD + j] *= sm.ev[n2 - 1];   // the last column
     }
     __syncthreads();
-    // ---- L^{-1} by forward substitution, one column per thread ----------
-    // (the diagonal's inverses first, one FP64 division each; column j runs
-    // on lane j / 8 of warp j % 8, so the columns' FP64 work is spread over
-    // the SM's four sub-partitions)
-    for (int i = tid; i < n2; i += nt) sm.ev[i] = 1.0 / sm.A[i * LD + i];
+    // ---- L^{-1} into B, right-looking: B holds 1 - (eliminated rows); row
+    // k is final once rows < k are eliminated from it, X_kj = B_kj / L_kk
+    // (1/L_kk = r_k from the Cholesky).  Step k eliminates row k from the
+    // rows below (B_ij -= L_ik r_k B_kj, j <= k) and scales row k - 1 by
+    // r_{k-1} (nothing reads it in step k): one barrier per row.
+    for (int idx = tid; idx < n2 * n2; idx += nt) {
+      const int i = idx / n2, j = idx % n2;
+      sm.B[i * LD + j] = (i == j) ? 1.0 : 0.0;
+    }
     __syncthreads();
-    {
-      const int j = (tid >> 5) + 8 * (tid & 31);
-      if (j < n2 && tid < 256) {
-        for (int i = 0; i < n2; ++i) {
-          double x;
-          if (i < j) x = 0.0;
-          else if (i == j) x = sm.ev[i];
-          else {
-            double acc = 0.0;
-            for (int k = j; k < i; ++k) acc += sm.A[i * LD + k] * sm.B[k * LD + j];
-            x = -acc * sm.ev[i];
-          }
-          sm.B[i * LD + j] = x;
-        }
+    for (int k = 0; k < n2; ++k) {
+      const double rk = sm.ev[k];
+      if (k > 0) {
+        const double rp = sm.ev[k - 1];
+        for (int j = tid; j < k; j += nt) sm.B[(k - 1) * LD + j] *= rp;
       }
+      const int w = n2 - k - 1, h = k + 1;               // rows k+1 .., columns 0 .. k
+      for (int idx = tid; idx < w * h; idx += nt) {
+        const int i = k + 1 + idx / h, j = idx % h;
+        sm.B[i * LD + j] = fma(-sm.A[i * LD + k] * rk, sm.B[k * LD + j], sm.B[i * LD + j]);
+      }
+      __syncthreads();
     }
+    for (int j = tid; j < n2; j += nt) sm.B[(n2 - 1) * LD + j] *= sm.ev[n2 - 1];   // the last row
     __syncthreads();
     // ---- H = i K, K = L^{-1} Omega L^{-T} --------------------------------
     for (int idx = tid; idx < n2 * n2; idx += nt) {
