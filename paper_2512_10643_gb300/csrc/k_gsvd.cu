@@ -469,7 +469,7 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W,
 // FP32 on a copy until the off-diagonal falls to ~4e-6 of ||H||_F (FP32
 // updates run at the full FP32 rate).  Stage 2: the FP32 eigenvectors are
 // made unitary in FP64 by two Newton-Schulz steps W <- W (3 - W^dag W) / 2,
-// H is transformed to W^dag H W, and FP64 Jacobi sweeps (typically two)
+// H is transformed to W^dag H W, and FP64 Jacobi sweeps (two or three)
 // finish the diagonalisation with W accumulating.  Returns false if the FP64
 // stage does not reach 2.5e-16 n ||H||_F within MAX_SWEEPS.
 __device__ bool jacobi_herm(ChainSmem& sm, int n) {
