@@ -293,7 +293,7 @@ __device__ __forceinline__ float jdiag_shift(const JRot<float>& J, float dlt, fl
   return J.sn * (J.sn * dlt - 2.0f * J.cs * re);
 }
 
-// The next round's rotation of pair k (FUSED set-up), from the matrix H that
+// The next round's rotation of pair k (by a set-up warp), from the matrix H that
 // round r acts on and round r's rotations (table b).  FP32 stage: the three
 // entries through the rotations, in FP32.  FP64 stage: FP64 only where
 // cancellation needs it, so that the set-up ends within the round's FP64
@@ -388,19 +388,18 @@ __device__ __forceinline__ void jround_item(const ChainSmem& sm, const T2* __res
 // upper blocks computed, the lower ones mirrored) written to the other
 // buffer, with the columns of W updated in place.
 //
-// FUSED: two warps set up the next round's rotations while the other six
-// update, from the same pre-round matrix (the entries each pair needs,
-// through this round's rotations: jsetup_next), so one barrier separates the
-// rounds.  Otherwise all eight warps update, then the next round is set up
-// from the updated matrix, two barriers per round.  Either way a round whose
-// rotations are all the identity is not applied.
+// Two warps set up the next round's rotations while the other six update,
+// from the same pre-round matrix (the entries each pair needs, through this
+// round's rotations: jsetup_next), so one barrier separates the rounds; a
+// round whose rotations are all the identity is not applied (the barrier's
+// OR-reduction says so).
 //
 // Before each sweep every off-diagonal entry is tested: |h_ij| <= conv, or
 // |h_ij| <= theta |h_jj - h_ii|, for all i < j ends the sweeps (returns
 // true); false after max_sweeps sweeps.  *Hout is the buffer that holds the
 // result.  A pair is rotated only if |h_pq| > skip and > theta |h_qq - h_pp|
 // (|h| = |Re| + |Im| in both tests).
-template <typename T2, bool FUSED>
+template <typename T2>
 __device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W, int n,
                               double conv_d, double skip_d, double theta_d, int max_sweeps,
                               T2** Hout) {
@@ -410,12 +409,11 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int half = n >> 1, nm1 = n - 1;
   const int nb = half * (half + 1) / 2;                  // upper 2 x 2 blocks (sm.blk)
-  // FUSED: warps 6 and 7 set up rotations (pair k on lane k / 2 of warp
-  // 6 + k % 2), warps 0..5 update.  Otherwise pair k is set up by lane k / 8
-  // of warp k % 8 (the set-up's FP64 steps on all four SM sub-partitions).
-  constexpr int NU = FUSED ? 192 : CHAIN_THREADS;
-  const bool setter = FUSED ? warp >= 6 : false;
-  const int ks = FUSED ? (setter ? (lane << 1) | (warp - 6) : NLM) : (lane << 3) | warp;
+  // warps 6 and 7 set up rotations (pair k on lane k / 2 of warp 6 + k % 2),
+  // warps 0..5 update
+  constexpr int NU = 192;
+  const bool setter = warp >= 6;
+  const int ks = setter ? (lane << 1) | (warp - 6) : NLM;
   const int G = max(1, min(half, (NU - nb) / n));       // pair groups per W row
   const int nitems = nb + n * G;
   const unsigned inv_n = ((1u << 20) + (unsigned)n - 1u) / (unsigned)n;   // jw / n for jw < 2048
@@ -438,27 +436,15 @@ __device__ bool jacobi_sweeps(ChainSmem& sm, T2* Hc, T2* Hn, T2* __restrict__ W,
     for (int r = 0; r < nm1; ++r) {
       const int b = r & 1;
       bool go_next = false;
-      if (FUSED && setter) {
+      if (setter) {
         if (ks < half && r + 1 < nm1) go_next = jsetup_next<T2, R>(sm, Hc, r, b, ks, n, skip, theta_f);
       } else if (upd) {
         for (int j = tid; j < nitems; j += NU)
           jround_item<T2, R>(sm, Hc, Hn, W, r, b, j, nb, n, half, G, inv_n);
       }
-      if (FUSED) {                             // a round of identities is skipped
-        const bool nxt = __syncthreads_or(go_next) != 0;
-        if (upd) { T2* t = Hc; Hc = Hn; Hn = t; }
-        upd = nxt;
-      } else {
-        if (upd) {
-          __syncthreads();
-          T2* t = Hc; Hc = Hn; Hn = t;
-        }
-        if (r + 1 < nm1) {
-          bool go = false;
-          if (ks < half) go = jrot_direct<T2, R>(sm, Hc, b ^ 1, r + 1, ks, n, skip, theta_f);
-          upd = __syncthreads_or(go) != 0;
-        }
-      }
+      const bool nxt = __syncthreads_or(go_next) != 0;   // a round of identities is skipped
+      if (upd) { T2* t = Hc; Hc = Hn; Hn = t; }
+      upd = nxt;
     }
   }
 }
@@ -499,7 +485,7 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   // stop criterion is left alone (no work), the check still covers it
   const double conv32 = 4e-6 * normF, conv64 = 2.5e-16 * n * normF;
   float2* H32o;
-  jacobi_sweeps<float2, true>(sm, H32, H32b, W32, n, conv32, 1e-300 + 0.025 * conv32, 0.0, 12, &H32o);
+  jacobi_sweeps<float2>(sm, H32, H32b, W32, n, conv32, 1e-300 + 0.025 * conv32, 0.0, 12, &H32o);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
     const float2 w = W32[i * LD + j];
@@ -577,7 +563,7 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   __syncthreads();
   // stop at a few units of the FP64 rounding floor of one sweep (~n eps ||H||_F)
   double2* Hc;
-  const bool ok = jacobi_sweeps<double2, true>(sm, H, T, W, n, conv64, 1e-300 + 0.25 * conv64, 0.0,
+  const bool ok = jacobi_sweeps<double2>(sm, H, T, W, n, conv64, 1e-300 + 0.25 * conv64, 0.0,
                                          MAX_SWEEPS, &Hc);
   // then one sweep more over every pair whose rotation angle is above
   // JAC_THETA, with no stop test: the criterion above leaves off-diagonal
@@ -588,7 +574,7 @@ __device__ bool jacobi_herm(ChainSmem& sm, int n) {
   // determined as FP64 allows (pairs whose angle is below JAC_THETA are left:
   // their rotation would change nothing above the sweep's own rounding)
   double2* Hf;
-  jacobi_sweeps<double2, true>(sm, Hc, Hc == H ? T : H, W, n, 1e-300, 1e-300, JAC_THETA, 1, &Hf);
+  jacobi_sweeps<double2>(sm, Hc, Hc == H ? T : H, W, n, 1e-300, 1e-300, JAC_THETA, 1, &Hf);
   for (int i = tid; i < n; i += nt) sm.ev[i] = Hf[i * LD + i].x;
   __syncthreads();
   return ok;
