@@ -843,6 +843,52 @@ def oracle_step_estimate(budget_s=20.0):
             "sample": sample_desc, "cores": os.cpu_count(), "measured_s": time.perf_counter() - t0}
 
 
+def oracle_config_timings(budget_s=8.0):
+    """The FP64 oracle timed on the small configuration (the 8-mode state
+    through a Haar unitary, d = 8, chi = 64: the full build) and on the
+    64-site prefix of the 1024-mode configuration (its GSVD chain over all
+    cuts, the kept bases of bonds 1..64, and the PCO build of prefix sites
+    at the full bond dimension within budget_s, scaled to the 64 sites)."""
+    import workloads as wl
+    from oracle import basis as B
+    from oracle import gaussian as G
+    from oracle import mps as M
+    from oracle import pco as P
+
+    out = {}
+    w = wl.config("pr1_n8")
+    t0 = time.perf_counter()
+    mps = M.build_mps(w.gamma, d=w.d, chi=w.chi)
+    M.normalise(mps.tensors)
+    t = time.perf_counter() - t0
+    out["c1"] = {"tensors_per_s": round(w.N / t, 3), "build_s": round(t, 3),
+                 "sample": f"full oracle build of the {w.N}-mode state (d = {w.d}, chi = {w.chi})"}
+    w = wl.config("n1024_d4_chi512")
+    K = 64
+    t0 = time.perf_counter()
+    cuts = G.gsvd_chain(w.gamma, lambda2_freeze=w.freeze)
+    t_chain = time.perf_counter() - t0
+    bases = [M.vacuum_basis()] + [B.kept_basis(c.lam2, w.chi, w.eps) for c in cuts[:K]]
+    t_bases = time.perf_counter() - t0 - t_chain
+    t_pco, n_pco = 0.0, 0
+    for s in range(K - 1, -1, -1):          # the last prefix sites: full bond dimension
+        t = time.perf_counter()
+        P.local_tensor(cuts[s].Q, bases[s], bases[s + 1], w.d, cuts[s].c)
+        t_pco += time.perf_counter() - t
+        n_pco += 1
+        if t_pco > budget_s:
+            break
+    prefix_s = t_chain + t_bases + K * t_pco / n_pco
+    out["c4_prefix"] = {"tensors_per_s": round(K / prefix_s, 4),
+                        "gsvd_cuts_per_s": round((w.N - 1) / t_chain, 1),
+                        "prefix_s": round(prefix_s, 2),
+                        "sample": (f"oracle GSVD chain over all {w.N - 1} cuts ({t_chain:.2f}s), kept bases "
+                                   f"of bonds 1..{K} ({t_bases:.2f}s), PCO build of the last {n_pco} prefix "
+                                   f"sites at D = {bases[K].D} ({t_pco / n_pco:.2f}s/site), scaled to the "
+                                   f"{K}-site prefix")}
+    return out
+
+
 def profile_pass(args):
     """One build (and one sampling) of the workload, nothing else timed or
     printed but a checksum: the launch sequence a profiler capture skips
@@ -912,7 +958,8 @@ def main():
         est = oracle_step_estimate(args.ref_budget)
         cpu = {"value": round(est["value"], 6), "unit": "tensors/s", "cores": est["cores"],
                "kind": "oracle", "sample": est["sample"],
-               "samples_per_s": round(est["samples_per_s"], 3)}
+               "samples_per_s": round(est["samples_per_s"], 3),
+               "configs": oracle_config_timings()}
     sm = sorted(r["step_ms"])
     if r["pipelined"]:
         cfg["pipeline"] = ("one stream of steps: the next states' Gaussian-SVD chains (one SM) and "
